@@ -1,0 +1,748 @@
+/*
+ * storm_oracle.c -- FP64 CPU oracle for one STORM sampling-based MPC step.
+ *
+ * TEST INFRASTRUCTURE ONLY (see storm_oracle.h).  Plain, slow, sequential C in
+ * double precision; every loop runs in the order the definition is written.
+ * No blocking, fusion or reordering: a reader should be able to hold each
+ * routine next to the paper's equation and check it by eye.
+ *
+ * Parity status of each routine is stated in its comment ("pinned by ...").
+ */
+#include "storm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Noise: counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).    */
+/* The paper draws Gaussian controls around the mean (Sec. 4, Algorithm 1,    */
+/* sample_controls) but fixes no generator; Philox is this project's choice,  */
+/* implemented from its published definition.  Pinned by the published        */
+/* known-answer vector and, on the GPU, by cuRAND's Philox4_32_10 stream.     */
+/* ------------------------------------------------------------------------- */
+
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u; /* Weyl key schedule */
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    memcpy(out, c, sizeof(c));
+}
+
+/* 23 high bits of a word, centred in their cell: never 0, never 1. */
+double orc_uniform_from_bits(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+/* Box-Muller transform (Box & Muller 1958). */
+void orc_box_muller(double u1, double u2, double* z0, double* z1)
+{
+    const double r = sqrt(-2.0 * log(u1));
+    *z0 = r * cos(2.0 * ORC_PI * u2);
+    *z1 = r * sin(2.0 * ORC_PI * u2);
+}
+
+/*
+ * eps[e], e in [0, count): Philox block e/4 with counter
+ * (e/4, step, (instance << 8) | iter, tag) and key (seed lo, seed hi);
+ * words (x0, x1) give lanes 0/1 and (x2, x3) lanes 2/3 through Box-Muller.
+ */
+void orc_noise_philox(uint64_t seed, uint32_t step, uint32_t instance, uint32_t iter,
+                      uint32_t tag, long long count, double* eps)
+{
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (long long e = 0; e < count; ++e) {
+        const uint32_t ctr[4] = {(uint32_t)(e / 4), step, (instance << 8) | iter, tag};
+        uint32_t x[4];
+        orc_philox4x32_10(ctr, key, x);
+        const int lane = (int)(e % 4);
+        const int pair = lane / 2;
+        double z0, z1;
+        orc_box_muller(orc_uniform_from_bits(x[2 * pair]),
+                       orc_uniform_from_bits(x[2 * pair + 1]), &z0, &z1);
+        eps[e] = (lane % 2 == 0) ? z0 : z1;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Halton low-discrepancy noise (Sec. 4.3, "Sampling Strategy"): point i has  */
+/* coordinate phi_{p_k}(i) in the k-th prime base, phi_b(i) = sum_a i_a b^-a. */
+/* Reading: unscrambled, point index i = n + 1 (skips i = 0, where the normal */
+/* quantile is -inf), dimension k = s*d + j, mapped to N(0,1) by the normal   */
+/* quantile, drawn once.  Pinned by exact radical-inverse values.             */
+/* ------------------------------------------------------------------------- */
+
+double orc_radical_inverse(uint64_t i, int base)
+{
+    double f = 1.0 / base, r = 0.0;
+    while (i > 0) {
+        r += (double)(i % (uint64_t)base) * f;
+        i /= (uint64_t)base;
+        f /= base;
+    }
+    return r;
+}
+
+int orc_nth_prime(int n) /* n = 0 -> 2 */
+{
+    int count = -1;
+    for (int c = 2;; ++c) {
+        int is_prime = 1;
+        for (int q = 2; q * q <= c; ++q)
+            if (c % q == 0) {
+                is_prime = 0;
+                break;
+            }
+        if (is_prime && ++count == n) return c;
+    }
+}
+
+/* Standard normal quantile: bisection on Phi(x) = erfc(-x/sqrt 2)/2. */
+double orc_norm_ppf(double p)
+{
+    if (!(p > 0.0 && p < 1.0)) return p <= 0.0 ? -INFINITY : INFINITY;
+    double lo = -40.0, hi = 40.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (0.5 * erfc(-mid / sqrt(2.0)) < p)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+void orc_noise_halton(int N, int S, int d, double* eps)
+{
+    for (int n = 0; n < N; ++n)
+        for (int s = 0; s < S; ++s)
+            for (int j = 0; j < d; ++j) {
+                const int dim = s * d + j;
+                const double w = orc_radical_inverse((uint64_t)n + 1, orc_nth_prime(dim));
+                eps[((long long)n * S + s) * d + j] = orc_norm_ppf(w);
+            }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cubic B-spline smoothing (Sec. 4.3): the S sampled knots are the control   */
+/* points of a clamped uniform cubic B-spline, evaluated at x_h = h/(H-1).    */
+/* Basis by the Cox-de Boor recursion.  Pinned by partition of unity, end     */
+/* interpolation and the closed-form uniform cubic blending polynomials.      */
+/* ------------------------------------------------------------------------- */
+
+static double knot(int i, int S)
+{
+    if (i <= 3) return 0.0;
+    if (i >= S) return 1.0;
+    return (double)(i - 3) / (double)(S - 3);
+}
+
+static double cox_de_boor(int i, int p, double x, int S)
+{
+    if (p == 0) {
+        /* right end x = 1 belongs to the last non-empty span [t_{S-1}, t_S) */
+        if (x >= 1.0) return (i == S - 1) ? 1.0 : 0.0;
+        return (knot(i, S) <= x && x < knot(i + 1, S)) ? 1.0 : 0.0;
+    }
+    double a = 0.0, b = 0.0;
+    const double den_a = knot(i + p, S) - knot(i, S);
+    const double den_b = knot(i + p + 1, S) - knot(i + 1, S);
+    if (den_a > 0.0) a = (x - knot(i, S)) / den_a * cox_de_boor(i, p - 1, x, S);
+    if (den_b > 0.0) b = (knot(i + p + 1, S) - x) / den_b * cox_de_boor(i + 1, p - 1, x, S);
+    return a + b;
+}
+
+void orc_bspline_basis(int H, int S, double* B)
+{
+    for (int h = 0; h < H; ++h) {
+        const double x = (H > 1) ? (double)h / (double)(H - 1) : 0.0;
+        for (int s = 0; s < S; ++s) B[h * S + s] = cox_de_boor(s, 3, x, S);
+    }
+}
+
+/* u_{n,h} = mu_h + sigma o (B eps_n)_h ; null particles get u = 0 (Sec. 4.3). */
+void orc_smooth_controls(const orc_params* P, int d, const double* mu, const double* sigma,
+                         const double* eps, double* u)
+{
+    const int N = P->N, H = P->H, S = P->n_knots > 0 ? P->n_knots : P->H;
+    double* B = NULL;
+    if (P->n_knots > 0) {
+        B = (double*)malloc(sizeof(double) * H * S);
+        orc_bspline_basis(H, S, B);
+    }
+    for (int n = 0; n < N; ++n)
+        for (int h = 0; h < H; ++h)
+            for (int j = 0; j < d; ++j) {
+                double e;
+                if (B) {
+                    e = 0.0;
+                    for (int s = 0; s < S; ++s)
+                        e += B[h * S + s] * eps[((long long)n * S + s) * d + j];
+                } else {
+                    e = eps[((long long)n * H + h) * d + j];
+                }
+                const long long idx = ((long long)n * H + h) * d + j;
+                u[idx] = (n < P->n_null) ? 0.0 : mu[h * d + j] + sigma[j] * e;
+            }
+    free(B);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tensorised integration, Eq. 7: theta_ddot = u,                              */
+/* theta_dot = theta_dot_init + S_l(1) diag(dt) theta_ddot,                    */
+/* theta = theta_init + S_l(1) diag(dt) theta_dot, with S_l(1) the inclusive   */
+/* lower-triangular matrix of ones (written out as its product).  Pinned by    */
+/* the constant-acceleration closed form.                                      */
+/* ------------------------------------------------------------------------- */
+void orc_integrate(int H, int d, const double* dt, const double* state, const double* u,
+                   double* theta, double* theta_dot)
+{
+    for (int j = 0; j < d; ++j) {
+        for (int h = 0; h < H; ++h) {
+            double v = state[d + j];
+            for (int k = 0; k < H; ++k) {
+                const double S_l = (k <= h) ? 1.0 : 0.0;
+                v += S_l * dt[k] * u[k * d + j];
+            }
+            theta_dot[h * d + j] = v;
+        }
+        for (int h = 0; h < H; ++h) {
+            double q = state[j];
+            for (int k = 0; k < H; ++k) {
+                const double S_l = (k <= h) ? 1.0 : 0.0;
+                q += S_l * dt[k] * theta_dot[k * d + j];
+            }
+            theta[h * d + j] = q;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Forward kinematics, Eq. 8: X = FK(theta).  Modified DH (Craig):            */
+/* T_i = T_{i-1} RotX(alpha_{i-1}) TransX(a_{i-1}) RotZ(theta_i+off_i)        */
+/* TransZ(d_i), T_0 = I; the end-effector frame is T_d.  frames holds         */
+/* (d+1) row-major 4x4 matrices.  Pinned by the zero-configuration closed     */
+/* form, single-joint Rodrigues rotation and orthonormality.                  */
+/* ------------------------------------------------------------------------- */
+
+static void mat4_mul(const double* A, const double* B, double* C)
+{
+    double T[16];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 4; ++k) s += A[r * 4 + k] * B[k * 4 + c];
+            T[r * 4 + c] = s;
+        }
+    memcpy(C, T, sizeof(T));
+}
+
+static void mat4_identity(double* A)
+{
+    memset(A, 0, 16 * sizeof(double));
+    A[0] = A[5] = A[10] = A[15] = 1.0;
+}
+
+static void rot_x(double a, double* A)
+{
+    mat4_identity(A);
+    A[5] = cos(a);
+    A[6] = -sin(a);
+    A[9] = sin(a);
+    A[10] = cos(a);
+}
+
+static void rot_z(double a, double* A)
+{
+    mat4_identity(A);
+    A[0] = cos(a);
+    A[1] = -sin(a);
+    A[4] = sin(a);
+    A[5] = cos(a);
+}
+
+static void trans(double x, double y, double z, double* A)
+{
+    mat4_identity(A);
+    A[3] = x;
+    A[7] = y;
+    A[11] = z;
+}
+
+void orc_fk(const orc_robot* R, const double* theta, double* frames)
+{
+    const int d = R->dof;
+    mat4_identity(frames);
+    for (int i = 1; i <= d; ++i) {
+        const double* row = R->dh + (i - 1) * 4; /* a_{i-1}, alpha_{i-1}, d_i, offset_i */
+        double Ra[16], Ta[16], Rt[16], Td[16], A[16];
+        rot_x(row[1], Ra);
+        trans(row[0], 0.0, 0.0, Ta);
+        rot_z(theta[i - 1] + row[3], Rt);
+        trans(0.0, 0.0, row[2], Td);
+        mat4_mul(Ra, Ta, A);
+        mat4_mul(A, Rt, A);
+        mat4_mul(A, Td, A);
+        mat4_mul(frames + (i - 1) * 16, A, frames + i * 16);
+    }
+}
+
+/* Geometric Jacobian, Eq. 8: column i = [z_i x (p_ee - o_i); z_i] in the world
+ * frame, z_i / o_i the axis and origin of joint frame i.  J is 6 x d. Pinned by
+ * central finite differences of orc_fk. */
+void orc_jacobian(const orc_robot* R, const double* frames, double* J)
+{
+    const int d = R->dof;
+    const double* Te = frames + d * 16;
+    const double p[3] = {Te[3], Te[7], Te[11]};
+    for (int i = 1; i <= d; ++i) {
+        const double* T = frames + i * 16;
+        const double z[3] = {T[2], T[6], T[10]};
+        const double r[3] = {p[0] - T[3], p[1] - T[7], p[2] - T[11]};
+        const int c = i - 1;
+        J[0 * d + c] = z[1] * r[2] - z[2] * r[1];
+        J[1 * d + c] = z[2] * r[0] - z[0] * r[2];
+        J[2 * d + c] = z[0] * r[1] - z[1] * r[0];
+        J[3 * d + c] = z[0];
+        J[4 * d + c] = z[1];
+        J[5 * d + c] = z[2];
+    }
+}
+
+/* Determinant by LU with partial pivoting. */
+double orc_det(int n, const double* A)
+{
+    double M[64];
+    memcpy(M, A, sizeof(double) * n * n);
+    double det = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[r * n + c]) > fabs(M[piv * n + c])) piv = r;
+        if (M[piv * n + c] == 0.0) return 0.0;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) {
+                const double t = M[c * n + k];
+                M[c * n + k] = M[piv * n + k];
+                M[piv * n + k] = t;
+            }
+            det = -det;
+        }
+        det *= M[c * n + c];
+        for (int r = c + 1; r < n; ++r) {
+            const double f = M[r * n + c] / M[c * n + c];
+            for (int k = c; k < n; ++k) M[r * n + k] -= f * M[c * n + k];
+        }
+    }
+    return det;
+}
+
+/* Manipulability score (Sec. 4.2, Eq. 12; Yoshikawa): sqrt(det(J J^T)).
+ * Reading: the garbled "sqrt(J J^T)" is the square root of the determinant. */
+double orc_manipulability(const double* J, int d)
+{
+    double JJt[36];
+    for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += J[r * d + k] * J[c * d + k];
+            JJt[r * 6 + c] = s;
+        }
+    const double det = orc_det(6, JJt);
+    return sqrt(det > 0.0 ? det : 0.0);
+}
+
+/* Rotation matrix -> unit quaternion (w, x, y, z), Shepperd's method. */
+void orc_quat_from_rot(const double* Rm, double* q)
+{
+    const double m00 = Rm[0], m01 = Rm[1], m02 = Rm[2];
+    const double m10 = Rm[3], m11 = Rm[4], m12 = Rm[5];
+    const double m20 = Rm[6], m21 = Rm[7], m22 = Rm[8];
+    const double tr = m00 + m11 + m22;
+    if (tr >= m00 && tr >= m11 && tr >= m22) {
+        const double s = 2.0 * sqrt(1.0 + tr);
+        q[0] = 0.25 * s;
+        q[1] = (m21 - m12) / s;
+        q[2] = (m02 - m20) / s;
+        q[3] = (m10 - m01) / s;
+    } else if (m00 >= m11 && m00 >= m22) {
+        const double s = 2.0 * sqrt(1.0 + m00 - m11 - m22);
+        q[0] = (m21 - m12) / s;
+        q[1] = 0.25 * s;
+        q[2] = (m01 + m10) / s;
+        q[3] = (m02 + m20) / s;
+    } else if (m11 >= m22) {
+        const double s = 2.0 * sqrt(1.0 + m11 - m00 - m22);
+        q[0] = (m02 - m20) / s;
+        q[1] = (m01 + m10) / s;
+        q[2] = 0.25 * s;
+        q[3] = (m12 + m21) / s;
+    } else {
+        const double s = 2.0 * sqrt(1.0 + m22 - m00 - m11);
+        q[0] = (m10 - m01) / s;
+        q[1] = (m02 + m20) / s;
+        q[2] = (m12 + m21) / s;
+        q[3] = 0.25 * s;
+    }
+}
+
+/* Unit quaternion (w, x, y, z), normalised first -> rotation matrix. */
+void orc_rot_from_quat(const double* q_in, double* Rm)
+{
+    const double n = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] +
+                          q_in[3] * q_in[3]);
+    const double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;
+    Rm[0] = 1 - 2 * (y * y + z * z);
+    Rm[1] = 2 * (x * y - w * z);
+    Rm[2] = 2 * (x * z + w * y);
+    Rm[3] = 2 * (x * y + w * z);
+    Rm[4] = 1 - 2 * (x * x + z * z);
+    Rm[5] = 2 * (y * z - w * x);
+    Rm[6] = 2 * (x * z - w * y);
+    Rm[7] = 2 * (y * z + w * x);
+    Rm[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Collision (Sec. 4.2, Eqs. 13-14).  The paper's learned self-collision      */
+/* network and point-cloud classifier are replaced by exact link-sphere       */
+/* geometry.  Reading: signed distance positive when apart; the cost is the   */
+/* penetration depth max(0, -min sd).  Self pairs are given as a list.        */
+/* Pinned by brute force over a dense box-surface grid and on-axis cases.     */
+/* ------------------------------------------------------------------------- */
+
+static void sphere_center(const orc_robot* R, const double* frames, int s, double* c)
+{
+    const double* T = frames + R->sphere_link[s] * 16;
+    const double* p = R->sphere + s * 4;
+    for (int r = 0; r < 3; ++r)
+        c[r] = T[r * 4 + 0] * p[0] + T[r * 4 + 1] * p[1] + T[r * 4 + 2] * p[2] + T[r * 4 + 3];
+}
+
+/* Exact signed distance from point p to an axis-aligned box (negative inside). */
+double orc_box_sdf(const double* p, const double* box)
+{
+    double q[3], out = 0.0, inside = -INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        q[k] = fabs(p[k] - box[k]) - box[3 + k];
+        const double pos = q[k] > 0.0 ? q[k] : 0.0;
+        out += pos * pos;
+        if (q[k] > inside) inside = q[k];
+    }
+    return sqrt(out) + (inside < 0.0 ? inside : 0.0);
+}
+
+double orc_self_min_sd(const orc_robot* R, const double* frames)
+{
+    double best = INFINITY;
+    for (int k = 0; k < R->n_pairs; ++k) {
+        const int a = R->pairs[2 * k], b = R->pairs[2 * k + 1];
+        double ca[3], cb[3];
+        sphere_center(R, frames, a, ca);
+        sphere_center(R, frames, b, cb);
+        const double dist = sqrt((ca[0] - cb[0]) * (ca[0] - cb[0]) +
+                                 (ca[1] - cb[1]) * (ca[1] - cb[1]) +
+                                 (ca[2] - cb[2]) * (ca[2] - cb[2]));
+        const double sd = dist - R->sphere[a * 4 + 3] - R->sphere[b * 4 + 3];
+        if (sd < best) best = sd;
+    }
+    return best;
+}
+
+double orc_world_min_sd(const orc_robot* R, const orc_world* W, const double* frames)
+{
+    double best = INFINITY;
+    for (int s = 0; s < R->n_spheres; ++s) {
+        double c[3];
+        sphere_center(R, frames, s, c);
+        const double r = R->sphere[s * 4 + 3];
+        for (int b = 0; b < W->n_boxes; ++b) {
+            const double sd = orc_box_sdf(c, W->boxes + b * 6) - r;
+            if (sd < best) best = sd;
+        }
+        for (int o = 0; o < W->n_spheres; ++o) {
+            const double* S = W->spheres + o * 4;
+            const double dist = sqrt((c[0] - S[0]) * (c[0] - S[0]) + (c[1] - S[1]) * (c[1] - S[1]) +
+                                     (c[2] - S[2]) * (c[2] - S[2]));
+            const double sd = dist - r - S[3];
+            if (sd < best) best = sd;
+        }
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Running cost, Eq. 15, with the terms of Eqs. 9-14:                         */
+/*  pos   (Eq. 9)  || alpha_2 o R_g^T (d_ee - d_g) ||_2                        */
+/*  rot   (Eq. 9)  QUAT: 1 - |q_ee . q_g|; FROBENIUS: ||(I - R_g^T R_ee) diag(alpha_1)||_F */
+/*  stop  (Eq. 10) || max(0, |theta_dot| - theta_dot_max,h) ||_2 with         */
+/*                 theta_dot_max = S_u(1) qdd_max dt (inclusive upper ones)    */
+/*  joint (Eq. 11) || max(0, th_min' - theta) + max(0, theta - th_max') ||_2  */
+/*  manip (Eq. 12) (1 - m) if m < k_m else 0, m = sqrt(det J J^T)             */
+/*  self/world (Eqs. 13-14) penetration depths of the link spheres            */
+/*  smooth        ||u_h - u_{h-1}||^2, u_{-1} = theta_ddot_init (not in the   */
+/*                paper; a configurable extra term, weight 0 disables it)     */
+/* terms[ORC_NTERMS] receives the unweighted terms in that order.             */
+/* ------------------------------------------------------------------------- */
+void orc_running_cost(const orc_robot* R, const orc_world* W, const orc_params* P,
+                      const double* goal, int h, const double* theta_h,
+                      const double* theta_dot_h, const double* u_h, const double* u_prev,
+                      double* terms, double* total)
+{
+    const int d = R->dof, H = P->H;
+    double* frames = (double*)malloc(sizeof(double) * 16 * (d + 1));
+    double J[6 * 8];
+    orc_fk(R, theta_h, frames);
+    orc_jacobian(R, frames, J);
+    const double* Te = frames + d * 16;
+    const double Ree[9] = {Te[0], Te[1], Te[2], Te[4], Te[5], Te[6], Te[8], Te[9], Te[10]};
+    double Rg[9];
+    orc_rot_from_quat(goal + 3, Rg);
+
+    /* position: R_g^T (d_ee - d_g), weighted per goal-frame axis */
+    const double dp[3] = {Te[3] - goal[0], Te[7] - goal[1], Te[11] - goal[2]};
+    double c_pos = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        const double e = Rg[0 * 3 + i] * dp[0] + Rg[1 * 3 + i] * dp[1] + Rg[2 * 3 + i] * dp[2];
+        c_pos += (P->pos_axis_w[i] * e) * (P->pos_axis_w[i] * e);
+    }
+    c_pos = sqrt(c_pos);
+
+    double c_rot = 0.0;
+    if (P->rot_mode == ORC_ROT_QUAT) {
+        double qe[4], qg[4];
+        orc_quat_from_rot(Ree, qe);
+        const double ng = sqrt(goal[3] * goal[3] + goal[4] * goal[4] + goal[5] * goal[5] +
+                               goal[6] * goal[6]);
+        for (int i = 0; i < 4; ++i) qg[i] = goal[3 + i] / ng;
+        c_rot = 1.0 - fabs(qe[0] * qg[0] + qe[1] * qg[1] + qe[2] * qg[2] + qe[3] * qg[3]);
+    } else {
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double RtR = 0.0;
+                for (int k = 0; k < 3; ++k) RtR += Rg[k * 3 + r] * Ree[k * 3 + c];
+                const double E = ((r == c) ? 1.0 : 0.0) - RtR;
+                c_rot += (E * P->rot_axis_w[c]) * (E * P->rot_axis_w[c]);
+            }
+        c_rot = sqrt(c_rot);
+    }
+
+    double vmax = 0.0; /* (S_u(1) qdd_max dt)_h */
+    for (int k = 0; k < H; ++k) vmax += (k >= h ? 1.0 : 0.0) * P->qdd_max * P->dt[k];
+    double c_stop = 0.0, c_joint = 0.0, c_smooth = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const double vs = fabs(theta_dot_h[j]) - vmax;
+        if (vs > 0.0) c_stop += vs * vs;
+        const double range = R->q_max[j] - R->q_min[j];
+        const double lo = R->q_min[j] + P->k_jl * range;
+        const double hi = R->q_max[j] - P->k_jl * range;
+        const double vj = (theta_h[j] < lo ? lo - theta_h[j] : 0.0) +
+                          (theta_h[j] > hi ? theta_h[j] - hi : 0.0);
+        c_joint += vj * vj;
+        const double du = u_h[j] - u_prev[j];
+        c_smooth += du * du;
+    }
+    c_stop = sqrt(c_stop);
+    c_joint = sqrt(c_joint);
+
+    const double m = orc_manipulability(J, d);
+    const double c_manip = (m < P->k_m) ? 1.0 - m : 0.0;
+
+    const double sd_self = orc_self_min_sd(R, frames);
+    const double sd_world = orc_world_min_sd(R, W, frames);
+    const double c_self = sd_self < 0.0 ? -sd_self : 0.0;
+    const double c_world = sd_world < 0.0 ? -sd_world : 0.0;
+
+    terms[0] = c_pos;
+    terms[1] = c_rot;
+    terms[2] = c_stop;
+    terms[3] = c_joint;
+    terms[4] = c_manip;
+    terms[5] = c_self;
+    terms[6] = c_world;
+    terms[7] = c_smooth;
+    *total = P->w_pos * c_pos + P->w_rot * c_rot + P->w_stop * c_stop + P->w_joint * c_joint +
+             P->w_manip * c_manip + P->w_coll * (c_self + c_world) + P->w_smooth * c_smooth;
+    free(frames);
+}
+
+/* ------------------------------------------------------------------------- */
+/* generate_rollouts (Algorithm 1) for one optimisation iteration: controls,  */
+/* integration (Eq. 7), per-step costs (Eq. 15) and the discounted total      */
+/* C_n = sum_h gamma^h c_{n,h} (Eq. 2, terminal cost read as the running cost */
+/* at h = H-1).  Any output pointer may be NULL.                              */
+/*   ee: N x H x 12 (row-major 3x4 [R | p]); terms: N x H x ORC_NTERMS         */
+/* ------------------------------------------------------------------------- */
+int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
+                const double* state, const double* goal, const double* mu,
+                const double* sigma, const double* eps, double* u_out, double* theta_out,
+                double* theta_dot_out, double* ee_out, double* terms_out, double* cost_out,
+                double* Ctot)
+{
+    const int N = P->N, H = P->H, d = R->dof;
+    if (N <= 0 || H <= 0 || d <= 0 || d > 8) return -1;
+    double* u = (double*)malloc(sizeof(double) * (size_t)N * H * d);
+    double* th = (double*)malloc(sizeof(double) * (size_t)H * d);
+    double* thd = (double*)malloc(sizeof(double) * (size_t)H * d);
+    double* frames = (double*)malloc(sizeof(double) * 16 * (d + 1));
+    orc_smooth_controls(P, d, mu, sigma, eps, u);
+    for (int n = 0; n < N; ++n) {
+        const double* un = u + (size_t)n * H * d;
+        orc_integrate(H, d, P->dt, state, un, th, thd);
+        double C = 0.0;
+        for (int h = 0; h < H; ++h) {
+            double terms[ORC_NTERMS], c;
+            const double* uprev = (h == 0) ? state + 2 * d : un + (h - 1) * d;
+            orc_running_cost(R, W, P, goal, h, th + h * d, thd + h * d, un + h * d, uprev, terms,
+                             &c);
+            C += pow(P->gamma, (double)h) * c;
+            const size_t nh = (size_t)n * H + h;
+            if (terms_out) memcpy(terms_out + nh * ORC_NTERMS, terms, sizeof(terms));
+            if (cost_out) cost_out[nh] = c;
+            if (ee_out) {
+                orc_fk(R, th + h * d, frames);
+                const double* Te = frames + d * 16;
+                for (int k = 0; k < 12; ++k) ee_out[nh * 12 + k] = Te[k];
+            }
+        }
+        if (theta_out) memcpy(theta_out + (size_t)n * H * d, th, sizeof(double) * H * d);
+        if (theta_dot_out) memcpy(theta_dot_out + (size_t)n * H * d, thd, sizeof(double) * H * d);
+        if (Ctot) Ctot[n] = C;
+    }
+    if (u_out) memcpy(u_out, u, sizeof(double) * (size_t)N * H * d);
+    free(u);
+    free(th);
+    free(thd);
+    free(frames);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* update_distribution, Eqs. 4-6.  w_i = exp(-C_i / beta), evaluated as       */
+/* exp(-(C_i - min C)/beta) (the common factor cancels in the normalised      */
+/* weights).  mu <- (1-a_mu) mu + a_mu sum w u / sum w;                        */
+/* sigma_j^2 <- (1-a_s) sigma_j^2 + a_s (1/H) sum_h sum_i w (u - mu_new)^2 /   */
+/* sum w (diagonal, shared over the horizon: Sec. 4.3 covariance              */
+/* parameterisation); sigma_j >= sigma_min.  beta = 0 selects the argmin      */
+/* (lowest index on ties); non-finite costs get weight 0.  Returns 1 and      */
+/* leaves mu, sigma unchanged if no cost is finite.  Pinned by the MPPI       */
+/* special cases (one particle, zero temperature, equal costs, unit sum).     */
+/* ------------------------------------------------------------------------- */
+int orc_update(const orc_params* P, int d, const double* Ctot, const double* u, double* mu,
+               double* sigma, double* weights)
+{
+    const int N = P->N, H = P->H;
+    double m = INFINITY;
+    int arg = -1;
+    for (int n = 0; n < N; ++n)
+        if (isfinite(Ctot[n]) && Ctot[n] < m) {
+            m = Ctot[n];
+            arg = n;
+        }
+    if (arg < 0) return 1;
+    double* w = (double*)malloc(sizeof(double) * N);
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) {
+        if (!isfinite(Ctot[n]))
+            w[n] = 0.0;
+        else if (P->beta > 0.0)
+            w[n] = exp(-(Ctot[n] - m) / P->beta);
+        else
+            w[n] = (n == arg) ? 1.0 : 0.0;
+        s += w[n];
+    }
+    for (int n = 0; n < N; ++n) w[n] /= s;
+    for (int h = 0; h < H; ++h)
+        for (int j = 0; j < d; ++j) {
+            double acc = 0.0;
+            for (int n = 0; n < N; ++n) acc += w[n] * u[((size_t)n * H + h) * d + j];
+            mu[h * d + j] = (1.0 - P->alpha_mu) * mu[h * d + j] + P->alpha_mu * acc;
+        }
+    for (int j = 0; j < d; ++j) {
+        double acc = 0.0;
+        for (int h = 0; h < H; ++h)
+            for (int n = 0; n < N; ++n) {
+                const double e = u[((size_t)n * H + h) * d + j] - mu[h * d + j];
+                acc += w[n] * e * e;
+            }
+        double var = (1.0 - P->alpha_sigma) * sigma[j] * sigma[j] + P->alpha_sigma * acc / H;
+        if (var < P->sigma_min * P->sigma_min) var = P->sigma_min * P->sigma_min;
+        sigma[j] = sqrt(var);
+    }
+    if (weights) memcpy(weights, w, sizeof(double) * N);
+    free(w);
+    return 0;
+}
+
+/* shift (Algorithm 1, Sec. 4): mu_h <- mu_{h+1}; the appended default is zero
+ * acceleration.  The per-joint sigma is left as it is. */
+void orc_shift(int H, int d, double* mu)
+{
+    for (int h = 0; h + 1 < H; ++h)
+        for (int j = 0; j < d; ++j) mu[h * d + j] = mu[(h + 1) * d + j];
+    for (int j = 0; j < d; ++j) mu[(H - 1) * d + j] = 0.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One control step of Algorithm 1: shift (skipped at step 0), K iterations   */
+/* of sample_controls / generate_rollouts / update_distribution, then         */
+/* next_command = the first action of the mean.  Returns the OR of update     */
+/* statuses (1 = degenerate: all costs non-finite).                            */
+/* ------------------------------------------------------------------------- */
+int orc_step(const orc_robot* R, const orc_world* W, const orc_params* P,
+             const double* state, const double* goal, uint32_t step, double* mu,
+             double* sigma, double* cmd, double* best_cost)
+{
+    const int N = P->N, H = P->H, d = R->dof;
+    const int S = P->n_knots > 0 ? P->n_knots : H;
+    const long long count = (long long)N * S * d;
+    double* eps = (double*)malloc(sizeof(double) * (size_t)count);
+    double* u = (double*)malloc(sizeof(double) * (size_t)N * H * d);
+    double* C = (double*)malloc(sizeof(double) * N);
+    int status = 0;
+    if (step > 0) orc_shift(H, d, mu);
+    if (P->sampler == ORC_SAMPLER_HALTON) orc_noise_halton(N, S, d, eps);
+    for (int k = 0; k < P->K; ++k) {
+        if (P->sampler == ORC_SAMPLER_PHILOX)
+            orc_noise_philox(P->seed, step, P->instance, (uint32_t)k, 0u, count, eps);
+        if (orc_rollout(R, W, P, state, goal, mu, sigma, eps, u, NULL, NULL, NULL, NULL, NULL, C))
+            status |= 2;
+        status |= orc_update(P, d, C, u, mu, sigma, NULL);
+        if (best_cost) {
+            double m = INFINITY;
+            for (int n = 0; n < N; ++n)
+                if (C[n] < m) m = C[n];
+            *best_cost = m;
+        }
+    }
+    for (int j = 0; j < d; ++j) cmd[j] = mu[j];
+    free(eps);
+    free(u);
+    free(C);
+    return status;
+}
