@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the STORM control step on B300.
+
+Workload: the paper-scale control step -- 7-DOF seeded modified-DH chain, 500
+particles x horizon 30, 6-knot cubic B-spline noise, 3 MPPI iterations with
+mean + diagonal covariance update and shift, every cost term including 49 link
+spheres against 20 boxes + 10 spheres.  Synthetic, seeded inputs (no dataset).
+
+One JSON line on rank 0:
+  value  rollout-steps/s (N * H * K per control step / device time per step),
+         inputs resident in HBM, each step timed with CUDA events on the
+         controller's stream, L2 flushed (256 MB write) before every step
+  e2e    the same metric through the host API storm_step in a closed loop
+         (pinned H2D of state + goal, D2H of the command, host wall clock)
+  latency_ms  p50 / p99 of the device-timed step
+  roofline    the rollout kernel (ALU bound) against the FP32 FMA peak
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+
+--impl reference times the FP64 oracle (the reference arm of this project) on
+the same workload, each step a bounded particle sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2104_13542_b300 import workloads as W  # noqa: E402
+
+METRIC = "MPC step latency p50/p99 (ms) and rollout-steps/s, 500x30 7-DOF, vs oracle"
+UNIT = "rollout-steps/s"
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def algorithmic_flops_per_item(p: W.Params, robot: W.Robot, world: W.World) -> float:
+    """FP32 flops of one (particle, step) item of the rollout kernel, counted
+    from the method (FMA = 2 flops), not from the instruction stream.
+
+    FK 48/joint, sphere centres 18/sphere, Jacobian 12/joint, manipulability
+    by Gram-Schmidt 28 k + 22 per row k, pose + rotation + stop + joint +
+    smoothness 100, world collision 14 per sphere-box and 8 per
+    sphere-sphere check, self collision 8 per pair, plus the per-particle
+    noise smoothing (2 S d H / H) and integration (4 d).
+    """
+    d, M, P = robot.dof, robot.spheres.shape[0], robot.pairs.shape[0]
+    B, O = world.boxes.shape[0], world.spheres.shape[0]
+    S = p.n_knots if p.n_knots > 0 else 1
+    manip = sum(28 * k + 22 for k in range(6)) if p.w_manip else 0
+    return (48 * d + 18 * M + 12 * d + manip + 100 + M * (14 * B + 8 * O) + 8 * P +
+            2 * S * d + 4 * d)
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks + throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def goals_for(ctl, robot, seed: int, count: int):
+    """Reachable goal poses X_g = FK(theta_g), theta_g ~ U[-2.24, 2.24]."""
+    import torch
+    rng = np.random.default_rng([seed, 99])
+    th = rng.uniform(-2.24, 2.24, (count, robot.dof)).astype(np.float32)
+    ee = ctl.forward_kinematics(torch.as_tensor(th, device="cuda")).cpu().numpy()
+    goals = []
+    for T in ee:
+        Rm, p = T[:, :3].astype(np.float64), T[:, 3]
+        # rotation -> quaternion (w, x, y, z) for the goal input format
+        w = math.sqrt(max(0.0, 1 + Rm[0, 0] + Rm[1, 1] + Rm[2, 2])) / 2
+        x = math.copysign(math.sqrt(max(0.0, 1 + Rm[0, 0] - Rm[1, 1] - Rm[2, 2])) / 2, Rm[2, 1] - Rm[1, 2])
+        y = math.copysign(math.sqrt(max(0.0, 1 - Rm[0, 0] + Rm[1, 1] - Rm[2, 2])) / 2, Rm[0, 2] - Rm[2, 0])
+        z = math.copysign(math.sqrt(max(0.0, 1 - Rm[0, 0] - Rm[1, 1] + Rm[2, 2])) / 2, Rm[1, 0] - Rm[0, 1])
+        goals.append(np.array([p[0], p[1], p[2], w, x, y, z], dtype=np.float32))
+    return goals
+
+
+def run_gpu(args, rank, world_size):
+    import torch
+    from paper_2104_13542_b300 import Controller
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    wl = W.config_paper(seed=args.seed + rank)
+    p = wl.params
+    units_per_step = p.N * p.H * p.K
+    ctl = Controller(wl.robot, wl.world, p)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    state0 = wl.state.copy()
+    state0[1:] = 0.0
+    goals = goals_for(ctl, wl.robot, args.seed + rank, 5)
+
+    # ---------------- device-resident timing (value)
+    s_ptr, g_ptr, _ = ctl.device_io_ptrs()
+    import ctypes
+    st_host = np.ascontiguousarray(state0, dtype=np.float32)
+    torch.cuda.synchronize()
+    st_dev = torch.as_tensor(st_host, device="cuda").reshape(-1)
+    gl_dev = torch.as_tensor(goals[0], device="cuda")
+    cmd_dev = torch.zeros(wl.robot.dof, device="cuda")
+    # place the inputs in the handle's own buffers once (resident)
+    ctl.step_async(st_dev, gl_dev, cmd_dev)
+    ctl.sync()
+    for _ in range(args.warmup):
+        ctl.step_resident()
+    ctl.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            with torch.cuda.stream(ctl.stream):
+                flush.fill_(float(i))
+            ev[i][0].record(ctl.stream)
+            ctl.step_resident()
+            ev[i][1].record(ctl.stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    dev_time_s = float(ms.sum() / 1e3)
+    if world_size > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_time_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_time_s = float(t.item())
+    clocks = clk.summary()
+
+    # ---------------- rollout-kernel roofline: kernel time from the step's share
+    # (the rollout kernel alone, timed with events on the controller's stream)
+    from paper_2104_13542_b300.binding import lib
+    rk = []
+    st_d = torch.as_tensor(st_host, device="cuda").reshape(-1)
+    for i in range(max(20, min(args.steps, 200))):
+        with torch.cuda.stream(ctl.stream):
+            flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(ctl.stream)
+        lib().storm_generate_rollouts(ctl.h, ctypes.c_void_p(st_d.data_ptr()),
+                                      ctypes.c_void_p(gl_dev.data_ptr()), 0, 0, None, None, None,
+                                      None, None, None, None)
+        b.record(ctl.stream)
+        rk.append((a, b))
+    torch.cuda.synchronize()
+    rk_ms = float(np.mean([a.elapsed_time(b) for a, b in rk]))
+    flops_launch = algorithmic_flops_per_item(p, wl.robot, wl.world) * p.N * p.H
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
+    peak = fp32_peak_tflops(sm_mhz)
+    achieved = flops_launch / (rk_ms * 1e-3) / 1e12
+
+    # ---------------- end-to-end closed loop through the host API (e2e)
+    ctl.reset()
+    state = state0.astype(np.float32).copy()
+    dt = float(p.dt[0])
+    e2e_ms, pos_err = [], []
+    seg = max(1, (args.steps + args.warmup) // len(goals))
+    for i in range(args.warmup + args.steps):
+        goal = goals[min(i // seg, len(goals) - 1)]
+        with torch.cuda.stream(ctl.stream):
+            flush.fill_(float(i))
+        ctl.stream.synchronize()
+        t0 = time.perf_counter()
+        cmd, info, rc = ctl.step(state, goal)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+        # ideal double-integrator plant
+        state[2] = cmd
+        state[1] = state[1] + dt * cmd
+        state[0] = state[0] + dt * state[1]
+        if (i + 1) % seg == 0 or i == args.warmup + args.steps - 1:
+            ee = ctl.forward_kinematics(torch.as_tensor(state[0:1], device="cuda")).cpu().numpy()[0]
+            pos_err.append(float(np.linalg.norm(ee[:, 3] - goal[:3])))
+    e2e_ms = np.array(e2e_ms)
+    e2e_time_s = float(e2e_ms.sum() / 1e3)
+    if world_size > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_time_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_time_s = float(t.item())
+
+    res = dict(
+        value=units_per_step * args.steps * world_size / dev_time_s,
+        ms_per_step=float(ms.mean()),
+        latency_ms={"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                    "max": float(ms.max())},
+        e2e={"value": units_per_step * args.steps * world_size / e2e_time_s, "unit": UNIT,
+             "h2d_bytes_per_step": 4 * (3 * wl.robot.dof + 7),
+             "d2h_bytes_per_step": 4 * wl.robot.dof + 16,
+             "latency_ms": {"p50": float(np.percentile(e2e_ms, 50)),
+                            "p99": float(np.percentile(e2e_ms, 99))},
+             "closed_loop_final_pos_err_m": pos_err},
+        roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                  "frac": achieved / peak, "traffic": None,
+                  "kernel": "k_rollout", "kernel_ms": rk_ms, "flops_per_launch": flops_launch,
+                  "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                f"{sm_mhz:.0f} MHz (fallback-free unit count; SM max clock)"},
+        clocks=clocks,
+        gpu_launches=(1 + 2 * p.K) * args.steps,
+        wall_s=wall,
+    )
+    ctl.close()
+    return res, wl
+
+
+def cpu_baseline(wl, budget_s: float = 12.0, n_sample: int | None = None):
+    """Time the FP64 oracle's control step on a bounded particle sample."""
+    import oracle
+    p = wl.params
+    n = n_sample or p.N
+    ps = p.replace(N=n)
+    orc = oracle.Oracle(wl.robot, wl.world, ps)
+    mu, sig = np.zeros((p.H, wl.robot.dof)), np.full(wl.robot.dof, p.sigma_init)
+    times = []
+    t_start = time.perf_counter()
+    step = 0
+    while True:
+        t0 = time.perf_counter()
+        _, mu, sig, _, _ = orc.step(wl.state, wl.goal, step, mu, sig)
+        times.append(time.perf_counter() - t0)
+        step += 1
+        if time.perf_counter() - t_start > budget_s or step >= 50:
+            break
+    t = np.array(times)
+    return {"value": n * p.H * p.K / float(t.mean()), "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{len(t)} control steps of the FP64 oracle with {n} of {p.N} particles "
+                      f"(H={p.H}, K={p.K}), single thread",
+            "latency_ms": {"p50": float(np.percentile(t, 50) * 1e3),
+                           "p99": float(np.percentile(t, 99) * 1e3)}}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, bounded samples."""
+    import oracle
+    wl = W.config_paper(seed=args.seed)
+    p = wl.params
+    n = args.ref_particles
+    ps = p.replace(N=n)
+    orc = oracle.Oracle(wl.robot, wl.world, ps)
+    mu, sig = np.zeros((p.H, wl.robot.dof)), np.full(wl.robot.dof, p.sigma_init)
+    for w in range(args.warmup):
+        _, mu, sig, _, _ = orc.step(wl.state, wl.goal, w, mu, sig)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        _, mu, sig, _, _ = orc.step(wl.state, wl.goal, args.warmup + i, mu, sig)
+        times.append(time.perf_counter() - t0)
+    t = np.array(times)
+    value = n * p.H * p.K * len(t) / float(t.sum())
+    sample = (f"each step: one FP64 oracle control step on {n} of the {p.N} particles "
+              f"(H={p.H}, K={p.K}), single thread")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(t.mean() * 1e3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "N": p.N, "H": p.H, "K": p.K, "dof": wl.robot.dof,
+                       "sample_particles": n},
+            "latency_ms": {"p50": float(np.percentile(t, 50) * 1e3),
+                           "p99": float(np.percentile(t, 99) * 1e3)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--ref-particles", type=int, default=25)
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", 0))
+    world_size = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)))
+        return
+
+    if world_size > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    res, wl = run_gpu(args, rank, world_size)
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    p = wl.params
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world_size,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "N": p.N, "H": p.H, "K": p.K, "dof": wl.robot.dof,
+                   "knots": p.n_knots, "spheres": int(wl.robot.spheres.shape[0]),
+                   "self_pairs": int(wl.robot.pairs.shape[0]),
+                   "boxes": int(wl.world.boxes.shape[0]),
+                   "obstacle_spheres": int(wl.world.spheres.shape[0]),
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world_size}"},
+        "latency_ms": res["latency_ms"], "e2e": res["e2e"], "roofline": res["roofline"],
+        "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
+    }
+    if world_size == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget_s)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * storm.h -- C ABI of the B300 (sm_103a) STORM control-step library.
+ *
+ * The library runs the data-parallel hot path of joint-space sampling-based MPC
+ * (Bhardwaj et al., arXiv 2104.13542, Algorithm 1): shift, then K iterations of
+ * sample_controls -> generate_rollouts -> update_distribution, then
+ * next_command.  All of it runs in hand-written CUDA kernels on one GPU.
+ *
+ * Conventions
+ *  - Every entry point returns an int status: 0 = STORM_OK, < 0 = error,
+ *    > 0 = warning.  No C++ exception crosses this boundary.  After an error
+ *    storm_last_error() describes it.
+ *  - The handle owns all device memory it allocates.  Pointers passed to
+ *    storm_create are deep-copied; the caller may free them after the call.
+ *  - Model parameters (robot, world, params) are double precision at the
+ *    boundary and rounded once to float on the device.  Per-step data (state,
+ *    goal, command, distribution) are float.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the device that was current at storm_create.  Device
+ *    work is enqueued on the handle's stream (the one given to storm_create,
+ *    or a private non-blocking stream when NULL was given).
+ *  - A handle may be used by one host thread at a time.
+ *
+ * Array layouts are row-major (C order):
+ *    state    3 x dof  (theta, theta_dot, theta_ddot)               Sec. 3 / Eq. 7
+ *    goal     7        (x, y, z, qw, qx, qy, qz) goal pose X_g      Eq. 9
+ *    mean     H x dof  mean control sequence mu (joint accel.)      Sec. 4, Eq. 4
+ *    sigma    dof      per-joint standard deviation                 Sec. 4.3, Eq. 5
+ *    u        N x H x dof sampled controls                          Algorithm 1
+ *    ee       N x H x 12  end-effector pose as row-major 3x4 [R | p] Eq. 8
+ *    terms    N x H x 8   unweighted cost terms, order:
+ *                         pos, rot, stop, joint, manip, self, world, smooth
+ *    cost     N x H       weighted running cost c_hat             Eq. 15
+ *    Ctot     N           discounted total C_hat                  Eq. 2
+ */
+#ifndef STORM_H
+#define STORM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STORM_MAX_DOF 7
+#define STORM_MAX_H 64
+#define STORM_MAX_SPHERES 64
+#define STORM_MAX_PAIRS 2048
+#define STORM_MAX_OBSTACLES 64 /* per kind: boxes, spheres */
+#define STORM_MAX_N 16384
+#define STORM_NTERMS 8
+
+typedef struct storm_handle storm_handle;
+
+enum storm_status {
+    STORM_OK = 0,
+    STORM_WARN_DEGENERATE = 1, /* an iteration had no finite total cost; mu, sigma kept */
+    STORM_ERR_INVALID_ARG = -1,
+    STORM_ERR_CUDA = -2,
+    STORM_ERR_OOM = -3,
+    STORM_ERR_NONFINITE = -4, /* a non-finite value in the state or goal input */
+    STORM_ERR_TIMEOUT = -5,
+    STORM_ERR_STATE = -6 /* a checkpoint blob that does not match this handle */
+};
+
+enum storm_sampler { STORM_SAMPLER_PHILOX = 0, STORM_SAMPLER_HALTON = 1 };
+enum storm_rot_mode { STORM_ROT_QUAT = 0, STORM_ROT_FROBENIUS = 1 };
+
+/* Serial revolute chain in modified Denavit-Hartenberg form (Craig), with link
+ * spheres for collision (Sec. 3.1 kinematic model, Eq. 8; Eqs. 13-14 with the
+ * learned checks replaced by exact sphere geometry). */
+typedef struct {
+    int dof;                  /* d, 1..STORM_MAX_DOF */
+    const double* dh;         /* d x 4: a_{i-1}, alpha_{i-1}, d_i, theta_offset_i */
+    const double* q_min;      /* d joint limits (Eq. 11) */
+    const double* q_max;      /* d */
+    int n_spheres;            /* M, 0..STORM_MAX_SPHERES */
+    const int* sphere_link;   /* M: frame 0..d the sphere is fixed to (0 = base) */
+    const double* spheres;    /* M x 4: centre in that frame, radius */
+    int n_pairs;              /* P, 0..STORM_MAX_PAIRS */
+    const int* pairs;         /* P x 2 sphere indices checked for self-collision */
+} storm_robot;
+
+/* Obstacles: axis-aligned boxes and spheres in the world frame. */
+typedef struct {
+    int n_boxes;              /* 0..STORM_MAX_OBSTACLES */
+    const double* boxes;      /* B x 6: cx, cy, cz, hx, hy, hz (half extents) */
+    int n_spheres;            /* 0..STORM_MAX_OBSTACLES */
+    const double* spheres;    /* S x 4: cx, cy, cz, r */
+} storm_world;
+
+typedef struct {
+    int N;                    /* particles, 1..STORM_MAX_N */
+    int H;                    /* horizon, 1..STORM_MAX_H */
+    int K;                    /* optimisation iterations per step, 1..255 */
+    int n_knots;              /* 0: no smoothing; else 4..H cubic B-spline knots (Sec. 4.3) */
+    int sampler;              /* storm_sampler (Sec. 4.3) */
+    int n_null;               /* particles 0..n_null-1 are zero-acceleration ("null") */
+    const double* dt;         /* H time steps (Eq. 7) */
+    double beta;              /* temperature (Eq. 6); 0 selects the argmin particle */
+    double gamma;             /* discount (Eq. 2) */
+    double alpha_mu;          /* mean step size (Eq. 4) */
+    double alpha_sigma;       /* covariance step size (Eq. 5) */
+    double sigma_init;        /* initial per-joint sigma */
+    double sigma_min;         /* floor on sigma after each update */
+    double w_pos, w_rot, w_stop, w_joint, w_manip, w_coll, w_smooth; /* Eq. 15 weights */
+    double pos_axis_w[3];     /* alpha_2 of Eq. 9: goal-frame position axis weights */
+    double rot_axis_w[3];     /* alpha_1 of Eq. 9 (STORM_ROT_FROBENIUS only) */
+    int rot_mode;             /* storm_rot_mode */
+    double k_jl;              /* joint-limit safety ratio (Eq. 11) */
+    double k_m;               /* manipulability threshold (Eq. 12) */
+    double qdd_max;           /* max acceleration of the stop cost (Eq. 10) */
+    uint64_t seed;            /* Philox key */
+    uint32_t instance;        /* Philox stream id (< 2^24) */
+} storm_params;
+
+typedef struct {
+    float best_cost;          /* min C_hat of the last iteration */
+    float mean_weighted_cost; /* sum_n w_n C_hat_n of the last iteration */
+    int status;               /* storm_status of the step */
+    uint32_t step;            /* index of the step just taken */
+} storm_step_info;
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Validate and upload robot / world / params, build the device tables
+ * (B-spline basis, discounts, stop-velocity limits, Halton noise) and set
+ * mu = 0, sigma = sigma_init, step = 0.  `cuda_stream` is a cudaStream_t or
+ * NULL.  On error *out is NULL.  Errors: INVALID_ARG (sizes out of range,
+ * NULL required pointer, bad sphere link / pair index), CUDA, OOM. */
+int storm_create(const storm_robot* robot, const storm_world* world,
+                 const storm_params* params, void* cuda_stream, storm_handle** out);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void storm_destroy(storm_handle* h);
+
+const char* storm_status_string(int status);
+/* Message of the last error on this handle (never NULL). */
+const char* storm_last_error(const storm_handle* h);
+
+/* mu = 0, sigma = sigma_init, step counter = 0. */
+int storm_reset(storm_handle* h);
+
+/* ---------------------------------------------------------------- control step */
+
+/* One control step of Algorithm 1 from host buffers: state (3 x dof, host),
+ * goal (7, host) -> cmd (dof, host) = first action of the optimised mean
+ * (next_command).  Copies in and out through pinned staging inside the call
+ * and waits for completion.  `info` may be NULL.  Errors: INVALID_ARG,
+ * NONFINITE (state or goal), CUDA; returns WARN_DEGENERATE when an iteration
+ * had no finite total cost. */
+int storm_step(storm_handle* h, const float* state, const float* goal, float* cmd,
+               storm_step_info* info);
+
+/* The same step on device buffers, enqueued on the handle's stream without
+ * waiting: state_dev (3 x dof), goal_dev (7), cmd_dev (dof).  Passing the
+ * pointers from storm_device_io() avoids two device-to-device copies.  Call
+ * storm_sync() to wait and read the step's status. */
+int storm_step_async(storm_handle* h, const float* state_dev, const float* goal_dev,
+                     float* cmd_dev);
+
+/* Wait for the handle's stream; `info` (nullable) receives the last step's info. */
+int storm_sync(storm_handle* h, storm_step_info* info);
+
+/* The handle's own device input/output buffers (state 3 x dof, goal 7, cmd dof). */
+int storm_device_io(storm_handle* h, float** state_dev, float** goal_dev, float** cmd_dev);
+
+/* ---------------------------------------------------------------- stages */
+
+/* shift (Algorithm 1): mu_h <- mu_{h+1}, mu_{H-1} <- 0; sigma unchanged. */
+int storm_shift(storm_handle* h);
+
+/* The standard-normal noise of sample_controls (Sec. 4.3, Algorithm 1) for
+ * iteration `iter` of control step `step`, before smoothing and scaling:
+ * eps_dev (device, N x S x dof with S = n_knots, or H without smoothing).
+ * Philox sampler: element e is lane e % 4 of Philox4x32-10 block e / 4 with
+ * counter (e / 4, step, instance << 8 | iter, 0) and key (seed lo, seed hi),
+ * lanes (0, 1) and (2, 3) Box-Muller pairs of 23-bit centred uniforms.
+ * Halton sampler: the table drawn at storm_create.  Enqueued (no wait). */
+int storm_sample_noise(storm_handle* h, uint32_t step, int iter, float* eps_dev);
+
+/* sample_controls + generate_rollouts (Algorithm 1; Eqs. 2, 7-15) for
+ * iteration `iter` of control step `step` on the current distribution, from
+ * device state_dev / goal_dev.  The noise is the Philox stream of (step, iter)
+ * or the Halton table.  Outputs are device buffers in the layouts above; any
+ * of them may be NULL except that u_dev and Ctot_dev are always written when
+ * given.  Enqueued on the handle's stream (no wait). */
+int storm_generate_rollouts(storm_handle* h, const float* state_dev, const float* goal_dev,
+                            uint32_t step, int iter, float* u_dev, float* theta_dev,
+                            float* theta_dot_dev, float* ee_dev, float* terms_dev,
+                            float* cost_dev, float* Ctot_dev);
+
+/* update_distribution (Eqs. 4-6) of the handle's mu, sigma from device totals
+ * Ctot_dev (N) and controls u_dev (N x H x dof).  weights_dev (N, nullable)
+ * receives the normalised weights.  Enqueued (no wait); a degenerate update
+ * is reported by the next storm_sync / storm_step. */
+int storm_update_distribution(storm_handle* h, const float* Ctot_dev, const float* u_dev,
+                              float* weights_dev);
+
+/* Host copies of mu (H x dof) and sigma (dof); either may be NULL.  Waits. */
+int storm_get_distribution(storm_handle* h, float* mean, float* sigma);
+int storm_set_distribution(storm_handle* h, const float* mean, const float* sigma);
+
+/* Replace the obstacles (counts within the STORM_MAX_OBSTACLES limits). */
+int storm_set_world(storm_handle* h, const storm_world* world);
+
+/* Batched forward kinematics (Eq. 8) on device buffers: theta_dev (count x dof)
+ * -> ee_dev (count x 12, row-major [R | p]).  Enqueued (no wait). */
+int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count, float* ee_dev);
+
+/* ---------------------------------------------------------------- checkpoint */
+
+/* Serialise mu, sigma and the step counter (the Philox key is fixed by the
+ * params), so that a resumed handle reproduces the same steps bit for bit.
+ * With buf == NULL, *len receives the size needed.  Errors: INVALID_ARG when
+ * *len is too small; STATE when a blob does not match the handle's shape. */
+int storm_get_state(storm_handle* h, void* buf, size_t* len);
+int storm_set_state(storm_handle* h, const void* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STORM_H */

@@ -1,0 +1,360 @@
+"""ctypes binding of ``libstorm_b300.so`` (the C ABI declared in ``include/storm.h``).
+
+Argument marshalling only: every step of the control path runs in the CUDA
+library.  PyTorch supplies device memory and the CUDA stream.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+LIB_PATH = os.path.join(_HERE, "libstorm_b300.so")
+_SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("storm.cu", "storm_device.cuh")] + \
+    [os.path.join(_ROOT, "include", "storm.h")]
+
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-shared"]
+
+STORM_OK = 0
+STORM_WARN_DEGENERATE = 1
+STORM_ERR_INVALID_ARG = -1
+STORM_ERR_CUDA = -2
+STORM_ERR_OOM = -3
+STORM_ERR_NONFINITE = -4
+STORM_ERR_TIMEOUT = -5
+STORM_ERR_STATE = -6
+NTERMS = 8
+
+EXPORTED = [
+    "storm_create", "storm_destroy", "storm_status_string", "storm_last_error", "storm_reset",
+    "storm_step", "storm_step_async", "storm_sync", "storm_device_io", "storm_shift",
+    "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
+    "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
+    "storm_set_state",
+]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile csrc/storm.cu for sm_103a into the package directory."""
+    newest = max(os.path.getmtime(s) for s in _SOURCES)
+    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["nvcc", *NVCC_FLAGS, "-I", os.path.join(_ROOT, "include"), "-o", tmp,
+               os.path.join(_HERE, "csrc", "storm.cu")]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int)
+
+
+class storm_robot(C.Structure):
+    _fields_ = [("dof", C.c_int), ("dh", _dp), ("q_min", _dp), ("q_max", _dp),
+                ("n_spheres", C.c_int), ("sphere_link", _ip), ("spheres", _dp),
+                ("n_pairs", C.c_int), ("pairs", _ip)]
+
+
+class storm_world(C.Structure):
+    _fields_ = [("n_boxes", C.c_int), ("boxes", _dp), ("n_spheres", C.c_int), ("spheres", _dp)]
+
+
+class storm_params(C.Structure):
+    _fields_ = [("N", C.c_int), ("H", C.c_int), ("K", C.c_int), ("n_knots", C.c_int),
+                ("sampler", C.c_int), ("n_null", C.c_int), ("dt", _dp), ("beta", C.c_double),
+                ("gamma", C.c_double), ("alpha_mu", C.c_double), ("alpha_sigma", C.c_double),
+                ("sigma_init", C.c_double), ("sigma_min", C.c_double), ("w_pos", C.c_double),
+                ("w_rot", C.c_double), ("w_stop", C.c_double), ("w_joint", C.c_double),
+                ("w_manip", C.c_double), ("w_coll", C.c_double), ("w_smooth", C.c_double),
+                ("pos_axis_w", C.c_double * 3), ("rot_axis_w", C.c_double * 3),
+                ("rot_mode", C.c_int), ("k_jl", C.c_double), ("k_m", C.c_double),
+                ("qdd_max", C.c_double), ("seed", C.c_uint64), ("instance", C.c_uint32)]
+
+
+class storm_step_info(C.Structure):
+    _fields_ = [("best_cost", C.c_float), ("mean_weighted_cost", C.c_float),
+                ("status", C.c_int), ("step", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.storm_create.argtypes = [C.POINTER(storm_robot), C.POINTER(storm_world),
+                                   C.POINTER(storm_params), vp, C.POINTER(vp)]
+        L.storm_destroy.argtypes = [vp]
+        L.storm_destroy.restype = None
+        L.storm_status_string.argtypes = [C.c_int]
+        L.storm_status_string.restype = C.c_char_p
+        L.storm_last_error.argtypes = [vp]
+        L.storm_last_error.restype = C.c_char_p
+        L.storm_reset.argtypes = [vp]
+        L.storm_step.argtypes = [vp, _fp, _fp, _fp, C.POINTER(storm_step_info)]
+        L.storm_step_async.argtypes = [vp, vp, vp, vp]
+        L.storm_sync.argtypes = [vp, C.POINTER(storm_step_info)]
+        L.storm_device_io.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+        L.storm_shift.argtypes = [vp]
+        L.storm_generate_rollouts.argtypes = [vp, vp, vp, C.c_uint32, C.c_int, vp, vp, vp, vp, vp,
+                                              vp, vp]
+        L.storm_update_distribution.argtypes = [vp, vp, vp, vp]
+        L.storm_sample_noise.argtypes = [vp, C.c_uint32, C.c_int, vp]
+        L.storm_get_distribution.argtypes = [vp, _fp, _fp]
+        L.storm_set_distribution.argtypes = [vp, _fp, _fp]
+        L.storm_set_world.argtypes = [vp, C.POINTER(storm_world)]
+        L.storm_forward_kinematics.argtypes = [vp, vp, C.c_int, vp]
+        L.storm_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.storm_set_state.argtypes = [vp, vp, C.c_size_t]
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().storm_status_string(int(code)).decode()
+
+
+class StormError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{status_string(code)} ({code}): {msg}")
+        self.code = code
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _p(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def _dptr(t):
+    """Raw device pointer of a CUDA tensor, or None."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class _Marshal:
+    """Keeps the numpy buffers behind the ctypes structs alive."""
+
+    def __init__(self):
+        self.keep = []
+
+    def hold(self, a):
+        self.keep.append(a)
+        return a
+
+    def robot(self, r):
+        dh = self.hold(_f64(r.dh))
+        qmin, qmax = self.hold(_f64(r.q_min)), self.hold(_f64(r.q_max))
+        link = self.hold(np.ascontiguousarray(r.sphere_link, dtype=np.int32))
+        sph = self.hold(_f64(r.spheres).reshape(-1, 4))
+        pairs = self.hold(np.ascontiguousarray(np.asarray(r.pairs, dtype=np.int32).reshape(-1, 2)))
+        return storm_robot(dh.shape[0], _p(dh), _p(qmin), _p(qmax), sph.shape[0], _p(link, _ip),
+                           _p(sph), pairs.shape[0], _p(pairs, _ip))
+
+    def world(self, w):
+        boxes = self.hold(_f64(w.boxes).reshape(-1, 6))
+        sph = self.hold(_f64(w.spheres).reshape(-1, 4))
+        return storm_world(boxes.shape[0], _p(boxes), sph.shape[0], _p(sph))
+
+    def params(self, p):
+        dt = self.hold(_f64(p.dt))
+        s = storm_params()
+        s.N, s.H, s.K, s.n_knots, s.sampler, s.n_null = p.N, p.H, p.K, p.n_knots, p.sampler, p.n_null
+        s.dt = _p(dt)
+        s.beta, s.gamma, s.alpha_mu, s.alpha_sigma = p.beta, p.gamma, p.alpha_mu, p.alpha_sigma
+        s.sigma_init, s.sigma_min = p.sigma_init, p.sigma_min
+        s.w_pos, s.w_rot, s.w_stop, s.w_joint = p.w_pos, p.w_rot, p.w_stop, p.w_joint
+        s.w_manip, s.w_coll, s.w_smooth = p.w_manip, p.w_coll, p.w_smooth
+        s.pos_axis_w[:] = list(p.pos_axis_w)
+        s.rot_axis_w[:] = list(p.rot_axis_w)
+        s.rot_mode, s.k_jl, s.k_m, s.qdd_max = p.rot_mode, p.k_jl, p.k_m, p.qdd_max
+        s.seed, s.instance = int(p.seed), int(p.instance)
+        return s
+
+
+class Controller:
+    """One STORM MPC handle (``storm_create`` ... ``storm_destroy``)."""
+
+    def __init__(self, robot, world, params, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("STORM controller needs a CUDA device")
+        self.torch = torch
+        self.params = params
+        self.d = int(robot.dh.shape[0])
+        self.N, self.H = int(params.N), int(params.H)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        m = _Marshal()
+        r, w, p = m.robot(robot), m.world(world), m.params(params)
+        h = C.c_void_p()
+        rc = lib().storm_create(C.byref(r), C.byref(w), C.byref(p),
+                                C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise StormError(rc, "storm_create failed (see stderr)")
+        self.h = h
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, rc, allow_warn=True):
+        if rc < 0 or (rc > 0 and not allow_warn):
+            raise StormError(rc, lib().storm_last_error(self.h).decode())
+        return rc
+
+    def _join(self):
+        """Make the handle's stream wait for work queued on torch's current stream."""
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def _empty(self, *shape):
+        with self.torch.cuda.stream(self.stream):
+            return self.torch.empty(shape, dtype=self.torch.float32, device="cuda")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().storm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ control step
+    def step(self, state, goal):
+        """Host-buffer control step -> (cmd (d,), info dict, status)."""
+        st = _f32(state).reshape(-1)
+        g = _f32(goal).reshape(-1)
+        if st.size != 3 * self.d or g.size != 7:
+            raise ValueError("state must have 3*dof values and goal 7")
+        cmd = np.zeros(self.d, dtype=np.float32)
+        info = storm_step_info()
+        rc = lib().storm_step(self.h, _p(st, _fp), _p(g, _fp), _p(cmd, _fp), C.byref(info))
+        self._check(rc)
+        return cmd, dict(best_cost=info.best_cost, mean_weighted_cost=info.mean_weighted_cost,
+                         status=info.status, step=info.step), rc
+
+    def step_async(self, state_dev, goal_dev, cmd_dev):
+        self._join()
+        self._check(lib().storm_step_async(self.h, _dptr(state_dev), _dptr(goal_dev),
+                                           _dptr(cmd_dev)))
+
+    def sync(self):
+        info = storm_step_info()
+        rc = self._check(lib().storm_sync(self.h, C.byref(info)))
+        return dict(best_cost=info.best_cost, mean_weighted_cost=info.mean_weighted_cost,
+                    status=info.status, step=info.step), rc
+
+    def device_io_ptrs(self):
+        s, g, c = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        self._check(lib().storm_device_io(self.h, C.byref(s), C.byref(g), C.byref(c)))
+        return s.value, g.value, c.value
+
+    def step_resident(self):
+        """Step on inputs already in the handle's own device buffers (no copies)."""
+        s, g, c = self.device_io_ptrs()
+        self._check(lib().storm_step_async(self.h, C.c_void_p(s), C.c_void_p(g), C.c_void_p(c)))
+
+    # ------------------------------------------------------------------ stages
+    def shift(self):
+        self._check(lib().storm_shift(self.h))
+
+    @property
+    def n_noise(self):
+        return self.params.n_knots if self.params.n_knots > 0 else self.H
+
+    def sample_noise(self, step: int, it: int):
+        eps = self._empty(self.N, self.n_noise, self.d)
+        self._check(lib().storm_sample_noise(self.h, int(step), int(it), _dptr(eps)))
+        self.stream.synchronize()
+        return eps
+
+    def generate_rollouts(self, state_dev, goal_dev, step: int, it: int, debug: bool = True):
+        N, H, d = self.N, self.H, self.d
+        out = dict(u=self._empty(N, H, d), C=self._empty(N))
+        if debug:
+            out.update(theta=self._empty(N, H, d), theta_dot=self._empty(N, H, d),
+                       ee=self._empty(N, H, 3, 4), terms=self._empty(N, H, NTERMS),
+                       cost=self._empty(N, H))
+        self._join()
+        g = out.get
+        self._check(lib().storm_generate_rollouts(
+            self.h, _dptr(state_dev), _dptr(goal_dev), int(step), int(it), _dptr(out["u"]),
+            _dptr(g("theta")), _dptr(g("theta_dot")), _dptr(g("ee")), _dptr(g("terms")),
+            _dptr(g("cost")), _dptr(out["C"])))
+        self.stream.synchronize()
+        return out
+
+    def update_distribution(self, C_dev, u_dev, want_weights=True):
+        w = self._empty(self.N) if want_weights else None
+        self._join()
+        self._check(lib().storm_update_distribution(self.h, _dptr(C_dev), _dptr(u_dev), _dptr(w)))
+        self.stream.synchronize()
+        return w
+
+    def get_distribution(self):
+        mu = np.zeros((self.H, self.d), dtype=np.float32)
+        sg = np.zeros(self.d, dtype=np.float32)
+        self._check(lib().storm_get_distribution(self.h, _p(mu, _fp), _p(sg, _fp)))
+        return mu, sg
+
+    def set_distribution(self, mu=None, sigma=None):
+        m = None if mu is None else _f32(mu).reshape(self.H, self.d)
+        s = None if sigma is None else _f32(sigma).reshape(self.d)
+        self._check(lib().storm_set_distribution(self.h, None if m is None else _p(m, _fp),
+                                                 None if s is None else _p(s, _fp)))
+
+    def set_world(self, world):
+        m = _Marshal()
+        w = m.world(world)
+        self._check(lib().storm_set_world(self.h, C.byref(w)))
+
+    def reset(self):
+        self._check(lib().storm_reset(self.h))
+
+    def forward_kinematics(self, theta_dev):
+        n = theta_dev.shape[0]
+        ee = self._empty(n, 3, 4)
+        self._join()
+        self._check(lib().storm_forward_kinematics(self.h, _dptr(theta_dev), int(n), _dptr(ee)))
+        self.stream.synchronize()
+        return ee
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t(0)
+        self._check(lib().storm_get_state(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(lib().storm_get_state(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def set_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(lib().storm_set_state(self.h, buf, len(blob)))

@@ -1,0 +1,1461 @@
+// storm.cu -- kernels, host runtime and C ABI of the B300 STORM control step.
+//
+// Hot path of one control step (Algorithm 1 of the paper):
+//   k_shift                      shift of the mean (skipped at step 0)
+//   K x { k_rollout, k_update }  sample_controls + generate_rollouts, update_distribution
+// The sequence is captured once into a CUDA graph per handle and replayed each
+// step; host<->device traffic per step is one 4*(3d+7)-byte copy in and one
+// 4*d + 16-byte copy out.
+#include "storm.h"
+#include "storm_device.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace storm;
+
+// ============================================================================ layout
+
+struct RolloutLayout {
+    int cent, sph, wsph;                                    // float4 arrays
+    int mu, sigma, eps, u, th, thd, basis, dt, gpow, vmax;  // float arrays
+    int dhx, qlo, qhi, boxes, part, dself, dworld, goal, state;
+    int first, pairs;                                       // int arrays
+    int bytes;
+};
+
+__host__ __device__ inline int take_(int& off, int bytes)
+{
+    const int o = off;
+    off += (bytes + 15) & ~15;
+    return o;
+}
+
+// Shared-memory plan of one rollout CTA (identical on host and device).
+__host__ __device__ inline RolloutLayout rollout_layout(const Problem& pb)
+{
+    RolloutLayout L;
+    int off = 0;
+    const int I = pb.ppc * pb.H;
+    L.cent = take_(off, I * pb.M * 16);
+    L.sph = take_(off, pb.M * 16);
+    L.wsph = take_(off, pb.O * 16);
+    L.mu = take_(off, pb.H * pb.d * 4);
+    L.sigma = take_(off, pb.d * 4);
+    L.eps = take_(off, pb.ppc * pb.S * pb.d * 4);
+    L.u = take_(off, pb.ppc * pb.H * pb.d * 4);
+    L.th = take_(off, pb.ppc * pb.H * pb.d * 4);
+    L.thd = take_(off, pb.ppc * pb.H * pb.d * 4);
+    L.basis = take_(off, pb.spline ? pb.H * pb.S * 4 : 0);
+    L.dt = take_(off, pb.H * 4);
+    L.gpow = take_(off, pb.H * 4);
+    L.vmax = take_(off, pb.H * 4);
+    L.dhx = take_(off, pb.d * 8 * 4);
+    L.qlo = take_(off, pb.d * 4);
+    L.qhi = take_(off, pb.d * 4);
+    L.boxes = take_(off, pb.B * 6 * 4);
+    L.part = take_(off, I * 4);
+    L.dself = take_(off, I * 4);
+    L.dworld = take_(off, I * 4);
+    L.goal = take_(off, 12 * 4);
+    L.state = take_(off, 3 * pb.d * 4);
+    L.first = take_(off, (pb.d + 2) * 4);
+    L.pairs = take_(off, pb.P * 4);
+    L.bytes = off;
+    return L;
+}
+
+struct RolloutOut {
+    float* u;          // N x H x d (required)
+    float* theta;      // optional N x H x d
+    float* theta_dot;  // optional N x H x d
+    float* ee;         // optional N x H x 12
+    float* terms;      // optional N x H x 8
+    float* cost;       // optional N x H
+    float* Ctot;       // N (required)
+};
+
+// ============================================================================ kernels
+
+// sample_controls + generate_rollouts for `ppc` particles per CTA.
+// Phases: stage tables -> noise -> smoothed controls -> per-(particle, joint)
+// integration scan (Eq. 7) -> per-(particle, step) FK, Jacobian and cost terms
+// (Eqs. 8-12, 15) -> link-sphere collision over (step, sphere) and
+// (pair, step) (Eqs. 13-14) -> discounted totals (Eq. 2).
+__global__ void __launch_bounds__(kThreads, 2)
+k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
+          const float* __restrict__ goal, const StepState* __restrict__ st, int step_override,
+          int iter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RolloutLayout L = rollout_layout(pb);
+    float4* s_cent = reinterpret_cast<float4*>(smem + L.cent);
+    float4* s_sph = reinterpret_cast<float4*>(smem + L.sph);
+    float4* s_wsph = reinterpret_cast<float4*>(smem + L.wsph);
+    float* s_mu = reinterpret_cast<float*>(smem + L.mu);
+    float* s_sigma = reinterpret_cast<float*>(smem + L.sigma);
+    float* s_eps = reinterpret_cast<float*>(smem + L.eps);
+    float* s_u = reinterpret_cast<float*>(smem + L.u);
+    float* s_th = reinterpret_cast<float*>(smem + L.th);
+    float* s_thd = reinterpret_cast<float*>(smem + L.thd);
+    float* s_basis = reinterpret_cast<float*>(smem + L.basis);
+    float* s_dt = reinterpret_cast<float*>(smem + L.dt);
+    float* s_gpow = reinterpret_cast<float*>(smem + L.gpow);
+    float* s_vmax = reinterpret_cast<float*>(smem + L.vmax);
+    float* s_dhx = reinterpret_cast<float*>(smem + L.dhx);
+    float* s_qlo = reinterpret_cast<float*>(smem + L.qlo);
+    float* s_qhi = reinterpret_cast<float*>(smem + L.qhi);
+    float* s_boxes = reinterpret_cast<float*>(smem + L.boxes);
+    float* s_part = reinterpret_cast<float*>(smem + L.part);
+    float* s_dself = reinterpret_cast<float*>(smem + L.dself);
+    float* s_dworld = reinterpret_cast<float*>(smem + L.dworld);
+    float* s_goal = reinterpret_cast<float*>(smem + L.goal);
+    float* s_state = reinterpret_cast<float*>(smem + L.state);
+    int* s_first = reinterpret_cast<int*>(smem + L.first);
+    uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.pairs);
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int d = pb.d, H = pb.H, S = pb.S, M = pb.M;
+    const int n0 = blockIdx.x * pb.ppc;
+    const int np = min(pb.ppc, pb.N - n0);
+    if (np <= 0) return;
+    const int I = np * H;
+    const int HD = H * d;
+    const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
+
+    // ---- stage per-problem tables
+    for (int i = tid; i < HD; i += nt) s_mu[i] = pb.mu[i];
+    for (int i = tid; i < d; i += nt) {
+        s_sigma[i] = pb.sigma[i];
+        s_qlo[i] = pb.qlo[i];
+        s_qhi[i] = pb.qhi[i];
+    }
+    for (int i = tid; i < 3 * d; i += nt) s_state[i] = state[i];
+    for (int i = tid; i < H; i += nt) {
+        s_dt[i] = pb.dt[i];
+        s_gpow[i] = pb.gpow[i];
+        s_vmax[i] = pb.vmax[i];
+    }
+    if (pb.spline)
+        for (int i = tid; i < H * S; i += nt) s_basis[i] = pb.basis[i];
+    for (int i = tid; i < d * 8; i += nt) s_dhx[i] = pb.dhx[i];
+    for (int i = tid; i < M; i += nt) s_sph[i] = pb.sph[i];
+    for (int i = tid; i < d + 2; i += nt) s_first[i] = pb.link_first[i];
+    for (int i = tid; i < pb.P; i += nt) s_pairs[i] = pb.pairs[i];
+    for (int i = tid; i < pb.B * 6; i += nt) s_boxes[i] = pb.boxes[i];
+    for (int i = tid; i < pb.O; i += nt) s_wsph[i] = pb.wsph[i];
+    if (tid == 0) {
+        // goal rotation R_g (row-major) from the normalised quaternion, then p_g
+        const float qn = rsqrtf(goal[3] * goal[3] + goal[4] * goal[4] + goal[5] * goal[5] +
+                                goal[6] * goal[6]);
+        const float w = goal[3] * qn, x = goal[4] * qn, y = goal[5] * qn, z = goal[6] * qn;
+        s_goal[0] = 1.f - 2.f * (y * y + z * z);
+        s_goal[1] = 2.f * (x * y - w * z);
+        s_goal[2] = 2.f * (x * z + w * y);
+        s_goal[3] = 2.f * (x * y + w * z);
+        s_goal[4] = 1.f - 2.f * (x * x + z * z);
+        s_goal[5] = 2.f * (y * z - w * x);
+        s_goal[6] = 2.f * (x * z - w * y);
+        s_goal[7] = 2.f * (y * z + w * x);
+        s_goal[8] = 1.f - 2.f * (x * x + y * y);
+        s_goal[9] = goal[0];
+        s_goal[10] = goal[1];
+        s_goal[11] = goal[2];
+    }
+
+    // ---- noise eps[n][s][j] for this CTA's particles
+    const int per = S * d;
+    if (pb.sampler == STORM_SAMPLER_PHILOX) {
+        const uint32_t e0 = static_cast<uint32_t>(n0) * per;
+        const uint32_t e1 = static_cast<uint32_t>(n0 + np) * per;
+        const uint32_t b0 = e0 >> 2, b1 = (e1 + 3) >> 2;
+        const uint32_t c2 = (pb.instance << 8) | static_cast<uint32_t>(iter);
+        for (uint32_t b = b0 + tid; b < b1; b += nt) {
+            const uint4 x = philox4x32_10(make_uint4(b, step, c2, 0u), pb.seed_lo, pb.seed_hi);
+            const float2 z01 = gauss_pair(x.x, x.y);
+            const float2 z23 = gauss_pair(x.z, x.w);
+            const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const uint32_t e = 4 * b + l;
+                if (e >= e0 && e < e1) s_eps[e - e0] = z[l];
+            }
+        }
+    } else {
+        for (int i = tid; i < np * per; i += nt) s_eps[i] = pb.halton[static_cast<size_t>(n0) * per + i];
+    }
+    __syncthreads();
+
+    // ---- controls u = mu + sigma o (B eps), null particles zero
+    for (int i = tid; i < np * HD; i += nt) {
+        const int p = i / HD, r = i - p * HD, h = r / d, j = r - h * d;
+        float e;
+        if (pb.spline) {
+            e = 0.f;
+            for (int s = 0; s < S; ++s) e = fmaf(s_basis[h * S + s], s_eps[(p * S + s) * d + j], e);
+        } else {
+            e = s_eps[(p * H + h) * d + j];
+        }
+        const float uu = (n0 + p < pb.n_null) ? 0.f : fmaf(s_sigma[j], e, s_mu[h * d + j]);
+        s_u[i] = uu;
+        out.u[static_cast<size_t>(n0) * HD + i] = uu;
+    }
+    __syncthreads();
+
+    // ---- integration scan per (particle, joint), Eq. 7
+    for (int t = tid; t < np * d; t += nt) {
+        const int p = t / d, j = t - p * d;
+        float v = s_state[d + j], q = s_state[j];
+        for (int h = 0; h < H; ++h) {
+            const int idx = (p * H + h) * d + j;
+            v = fmaf(s_dt[h], s_u[idx], v);
+            q = fmaf(s_dt[h], v, q);
+            s_thd[idx] = v;
+            s_th[idx] = q;
+        }
+    }
+    __syncthreads();
+    if (out.theta)
+        for (int i = tid; i < np * HD; i += nt) out.theta[static_cast<size_t>(n0) * HD + i] = s_th[i];
+    if (out.theta_dot)
+        for (int i = tid; i < np * HD; i += nt)
+            out.theta_dot[static_cast<size_t>(n0) * HD + i] = s_thd[i];
+
+    // ---- per (particle, step): FK, sphere centres, Jacobian, non-collision costs
+    if (tid < I) {
+        const int p = tid / H, h = tid - p * H;
+        const float* th = s_th + (p * H + h) * d;
+        const float* thd = s_thd + (p * H + h) * d;
+        const float* uh = s_u + (p * H + h) * d;
+        const float* up = (h == 0) ? s_state + 2 * d : uh - d;
+        float4* cent = s_cent + tid * M;
+
+        float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+        float pp[3] = {0.f, 0.f, 0.f};
+        float z[kMaxDof][3], o[kMaxDof][3];
+        for (int s = s_first[0]; s < s_first[1]; ++s) cent[s] = s_sph[s];
+#pragma unroll
+        for (int i = 0; i < kMaxDof; ++i) {
+            if (i < d) {
+                const float* dh = s_dhx + i * 8;
+                dh_step(R, pp, dh[0], dh[1], dh[2], dh[3], th[i] + dh[4]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    z[i][r] = R[r * 3 + 2];
+                    o[i][r] = pp[r];
+                }
+                for (int s = s_first[i + 1]; s < s_first[i + 2]; ++s) {
+                    const float4 q = s_sph[s];
+                    float4 c;
+                    c.x = fmaf(R[0], q.x, fmaf(R[1], q.y, fmaf(R[2], q.z, pp[0])));
+                    c.y = fmaf(R[3], q.x, fmaf(R[4], q.y, fmaf(R[5], q.z, pp[1])));
+                    c.z = fmaf(R[6], q.x, fmaf(R[7], q.y, fmaf(R[8], q.z, pp[2])));
+                    c.w = q.w;
+                    cent[s] = c;
+                }
+            }
+        }
+
+        // geometric Jacobian rows (Eq. 8): [z_i x (p - o_i); z_i]
+        float J[6][kMaxDof];
+#pragma unroll
+        for (int i = 0; i < kMaxDof; ++i) {
+            if (i < d) {
+                const float rx = pp[0] - o[i][0], ry = pp[1] - o[i][1], rz = pp[2] - o[i][2];
+                J[0][i] = z[i][1] * rz - z[i][2] * ry;
+                J[1][i] = z[i][2] * rx - z[i][0] * rz;
+                J[2][i] = z[i][0] * ry - z[i][1] * rx;
+                J[3][i] = z[i][0];
+                J[4][i] = z[i][1];
+                J[5][i] = z[i][2];
+            } else {
+#pragma unroll
+                for (int r = 0; r < 6; ++r) J[r][i] = 0.f;
+            }
+        }
+
+        // pose (Eq. 9): position in the goal frame, weighted per axis
+        const float dx = pp[0] - s_goal[9], dy = pp[1] - s_goal[10], dz = pp[2] - s_goal[11];
+        float c_pos = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float e = pb.pos_w[a] * fmaf(s_goal[a], dx, fmaf(s_goal[3 + a], dy, s_goal[6 + a] * dz));
+            c_pos = fmaf(e, e, c_pos);
+        }
+        c_pos = sqrtf(c_pos);
+        float c_rot = 0.f;
+        if (pb.rot_mode == STORM_ROT_QUAT) {
+            // |q_ee . q_g| = sqrt(1 + tr(R_g^T R_ee)) / 2
+            float tr = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) tr = fmaf(s_goal[k], R[k], tr);
+            c_rot = 1.f - 0.5f * sqrtf(fmaxf(0.f, 1.f + tr));
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float rtr =
+                        fmaf(s_goal[r], R[c], fmaf(s_goal[3 + r], R[3 + c], s_goal[6 + r] * R[6 + c]));
+                    const float e = ((r == c) ? 1.f : 0.f) - rtr;
+                    const float we = e * pb.rot_w[c];
+                    c_rot = fmaf(we, we, c_rot);
+                }
+            c_rot = sqrtf(c_rot);
+        }
+        // stop (Eq. 10), joint limits (Eq. 11), smoothness
+        float c_stop = 0.f, c_joint = 0.f, c_smooth = 0.f;
+        const float vlim = s_vmax[h];
+        for (int j = 0; j < d; ++j) {
+            const float vs = fmaxf(0.f, fabsf(thd[j]) - vlim);
+            c_stop = fmaf(vs, vs, c_stop);
+            const float vj = fmaxf(0.f, s_qlo[j] - th[j]) + fmaxf(0.f, th[j] - s_qhi[j]);
+            c_joint = fmaf(vj, vj, c_joint);
+            const float du = uh[j] - up[j];
+            c_smooth = fmaf(du, du, c_smooth);
+        }
+        c_stop = sqrtf(c_stop);
+        c_joint = sqrtf(c_joint);
+        // manipulability (Eq. 12)
+        float c_manip = 0.f;
+        if (pb.w_manip != 0.f || out.terms) {
+            const float m = manipulability_mgs(J, d);
+            c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
+        }
+        s_part[tid] = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop +
+                      pb.w_joint * c_joint + pb.w_manip * c_manip + pb.w_smooth * c_smooth;
+        s_dself[tid] = 0.f;
+        s_dworld[tid] = 0.f;
+        const size_t g = static_cast<size_t>(n0) * H + tid;
+        if (out.ee) {
+            float* e = out.ee + g * 12;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                e[r * 4 + 0] = R[r * 3 + 0];
+                e[r * 4 + 1] = R[r * 3 + 1];
+                e[r * 4 + 2] = R[r * 3 + 2];
+                e[r * 4 + 3] = pp[r];
+            }
+        }
+        if (out.terms) {
+            float* t = out.terms + g * STORM_NTERMS;
+            t[0] = c_pos;
+            t[1] = c_rot;
+            t[2] = c_stop;
+            t[3] = c_joint;
+            t[4] = c_manip;
+            t[7] = c_smooth;
+        }
+    }
+    __syncthreads();
+
+    // ---- world collision over (step, sphere): penetration depth, Eq. 14 reading
+    if (pb.B + pb.O > 0) {
+        for (int idx = tid; idx < I * M; idx += nt) {
+            const int item = idx / M;
+            const float4 c = s_cent[idx];
+            const float r2 = c.w * c.w;
+            float depth = 0.f;
+            for (int b = 0; b < pb.B; ++b) {
+                const float* bx = s_boxes + b * 6;
+                const float qx = fabsf(c.x - bx[0]) - bx[3];
+                const float qy = fabsf(c.y - bx[1]) - bx[4];
+                const float qz = fabsf(c.z - bx[2]) - bx[5];
+                const float ox = fmaxf(qx, 0.f), oy = fmaxf(qy, 0.f), oz = fmaxf(qz, 0.f);
+                const float out2 = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
+                if (out2 < r2) {
+                    const float sd = sqrtf(out2) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f) - c.w;
+                    depth = fmaxf(depth, -sd);
+                }
+            }
+            for (int k = 0; k < pb.O; ++k) {
+                const float4 w = s_wsph[k];
+                const float ex = c.x - w.x, ey = c.y - w.y, ez = c.z - w.z;
+                const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                const float rs = c.w + w.w;
+                if (dist2 < rs * rs) depth = fmaxf(depth, rs - sqrtf(dist2));
+            }
+            if (depth > 0.f) atomicMax(reinterpret_cast<int*>(s_dworld + item), __float_as_int(depth));
+        }
+    }
+    // ---- self collision over (pair, step), Eq. 13 reading
+    for (int k = tid; k < pb.P; k += nt) {
+        const uint32_t pr = s_pairs[k];
+        const int a = pr & 0xffff, b = pr >> 16;
+        const float rs = s_sph[a].w + s_sph[b].w;
+        const float rs2 = rs * rs;
+        for (int item = 0; item < I; ++item) {
+            const float4 ca = s_cent[item * M + a];
+            const float4 cb = s_cent[item * M + b];
+            const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+            const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (dist2 < rs2)
+                atomicMax(reinterpret_cast<int*>(s_dself + item), __float_as_int(rs - sqrtf(dist2)));
+        }
+    }
+    __syncthreads();
+
+    // ---- running cost (Eq. 15)
+    if (tid < I) {
+        const float c = s_part[tid] + pb.w_coll * (s_dself[tid] + s_dworld[tid]);
+        s_part[tid] = c;
+        const size_t g = static_cast<size_t>(n0) * H + tid;
+        if (out.cost) out.cost[g] = c;
+        if (out.terms) {
+            out.terms[g * STORM_NTERMS + 5] = s_dself[tid];
+            out.terms[g * STORM_NTERMS + 6] = s_dworld[tid];
+        }
+    }
+    __syncthreads();
+    // ---- discounted total (Eq. 2)
+    if (tid < np) {
+        float C = 0.f;
+        for (int h = 0; h < H; ++h) C = fmaf(s_gpow[h], s_part[tid * H + h], C);
+        out.Ctot[n0 + tid] = C;
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum: fixed butterfly per warp, then warp 0 over warps.
+__device__ float block_sum(float v, float* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        float x = lane < nw ? sh[lane] : 0.f;
+        x = warp_sum(x);
+        if (lane == 0) sh[0] = x;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+// update_distribution (Eqs. 4-6) in one CTA: min-shifted exponential weights,
+// weighted mean, weighted per-joint variance about the new mean.  `finalize`
+// marks the last iteration of a control step: it writes next_command and
+// advances the step counter.
+__global__ void __launch_bounds__(kUpdateThreads)
+k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
+         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out, int finalize)
+{
+    extern __shared__ __align__(16) float s_dyn[];
+    __shared__ float s_redf[32];
+    __shared__ int s_redi[32];
+    const int N = pb.N, d = pb.d, O = pb.H * pb.d;
+    const int tid = threadIdx.x, T = blockDim.x;
+    float* s_w = s_dyn;
+    float* s_part = s_w + ((N + 3) & ~3);
+    float* s_mu = s_part + T;
+
+    // ---- min finite cost and its lowest index
+    float bv = INFINITY;
+    int bi = INT_MAX;
+    for (int n = tid; n < N; n += T) {
+        const float c = C[n];
+        if (isfinite(c) && c < bv) {
+            bv = c;
+            bi = n;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov < bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    const int lane = tid & 31, wid = tid >> 5, nw = (T + 31) >> 5;
+    if (lane == 0) {
+        s_redf[wid] = bv;
+        s_redi[wid] = bi;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        bv = lane < nw ? s_redf[lane] : INFINITY;
+        bi = lane < nw ? s_redi[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_redf[0] = bv;
+            s_redi[0] = bi;
+        }
+    }
+    __syncthreads();
+    const float m = s_redf[0];
+    const int arg = s_redi[0];
+    __syncthreads();
+
+    if (arg == INT_MAX) {  // no finite cost: keep the distribution
+        if (tid == 0) {
+            st->status |= STORM_WARN_DEGENERATE;
+            st->best = INFINITY;
+            st->wmean = INFINITY;
+        }
+        if (weights_out)
+            for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
+        if (finalize) {
+            if (tid < d) cmd_out[tid] = pb.mu[tid];
+            if (tid == 0) st->step += 1;
+        }
+        return;
+    }
+
+    // ---- weights w_n = exp(-(C_n - m) / beta), Eq. 6
+    float ls = 0.f, lsc = 0.f;
+    for (int n = tid; n < N; n += T) {
+        const float c = C[n];
+        float w;
+        if (!isfinite(c))
+            w = 0.f;
+        else if (pb.beta > 0.f)
+            w = expf(-(c - m) / pb.beta);
+        else
+            w = (n == arg) ? 1.f : 0.f;
+        s_w[n] = w;
+        ls += w;
+        if (w > 0.f) lsc = fmaf(w, c, lsc);
+    }
+    const float s = block_sum(ls, s_redf);
+    const float sc = block_sum(lsc, s_redf);
+    const float inv_s = 1.f / s;
+    if (weights_out)
+        for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * inv_s;
+
+    // ---- weighted mean, Eq. 4
+    const int nsl = max(1, T / O);
+    if (tid < nsl * O) {
+        const int o = tid % O, sl = tid / O;
+        float acc = 0.f;
+        for (int n = sl; n < N; n += nsl) acc = fmaf(s_w[n], u[static_cast<size_t>(n) * O + o], acc);
+        s_part[sl * O + o] = acc;
+    }
+    __syncthreads();
+    for (int o = tid; o < O; o += T) {
+        float acc = 0.f;
+        for (int sl = 0; sl < nsl; ++sl) acc += s_part[sl * O + o];
+        s_mu[o] = (1.f - pb.alpha_mu) * pb.mu[o] + pb.alpha_mu * (acc * inv_s);
+    }
+    __syncthreads();
+
+    // ---- weighted variance about the new mean, per joint, Eq. 5
+    if (tid < nsl * O) {
+        const int o = tid % O, sl = tid / O;
+        const float mo = s_mu[o];
+        float acc = 0.f;
+        for (int n = sl; n < N; n += nsl) {
+            const float e = u[static_cast<size_t>(n) * O + o] - mo;
+            acc = fmaf(s_w[n] * e, e, acc);
+        }
+        s_part[sl * O + o] = acc;
+    }
+    __syncthreads();
+    if (tid < d) {
+        const int j = tid;
+        float v = 0.f;
+        for (int h = 0; h < pb.H; ++h) {
+            float a = 0.f;
+            for (int sl = 0; sl < nsl; ++sl) a += s_part[sl * O + h * d + j];
+            v += a;
+        }
+        v = v * inv_s / static_cast<float>(pb.H);
+        const float sg = pb.sigma[j];
+        float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
+        var = fmaxf(var, pb.sigma_min * pb.sigma_min);
+        pb.sigma[j] = sqrtf(var);
+    }
+    for (int o = tid; o < O; o += T) pb.mu[o] = s_mu[o];
+    if (tid == 0) {
+        st->best = m;
+        st->wmean = sc * inv_s;
+    }
+    if (finalize) {
+        if (tid < d) cmd_out[tid] = s_mu[tid];
+        if (tid == 0) st->step += 1;
+    }
+}
+
+// Raw noise of sample_controls: one thread per Philox block (4 values).
+__global__ void k_noise(Problem pb, uint32_t step, int iter, float* __restrict__ eps)
+{
+    const uint32_t total = static_cast<uint32_t>(pb.N) * pb.S * pb.d;
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * b >= total) return;
+    if (pb.sampler == STORM_SAMPLER_HALTON) {
+        for (uint32_t e = 4 * b; e < min(4 * b + 4, total); ++e) eps[e] = pb.halton[e];
+        return;
+    }
+    const uint4 x = philox4x32_10(make_uint4(b, step, (pb.instance << 8) | static_cast<uint32_t>(iter), 0u),
+                                  pb.seed_lo, pb.seed_hi);
+    const float2 z01 = gauss_pair(x.x, x.y);
+    const float2 z23 = gauss_pair(x.z, x.w);
+    const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+        if (4 * b + l < total) eps[4 * b + l] = z[l];
+}
+
+// shift (Algorithm 1): mu_h <- mu_{h+1}, mu_{H-1} <- 0.  As the first node of a
+// step it also clears the step status and skips the shift at step 0.
+__global__ void k_shift(Problem pb, StepState* st, int force)
+{
+    const int O = pb.H * pb.d, d = pb.d;
+    const bool do_shift = force || st->step > 0;
+    float v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int o = threadIdx.x + r * blockDim.x;
+        v[r] = (o + d < O) ? pb.mu[o + d] : 0.f;
+    }
+    __syncthreads();
+    if (do_shift) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int o = threadIdx.x + r * blockDim.x;
+            if (o < O) pb.mu[o] = v[r];
+        }
+    }
+    if (threadIdx.x == 0 && !force) st->status = 0;
+}
+
+// Batched forward kinematics (Eq. 8): one thread per configuration.
+__global__ void k_fk(Problem pb, const float* __restrict__ theta, int count, float* __restrict__ ee)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    float p[3] = {0.f, 0.f, 0.f};
+    for (int j = 0; j < pb.d; ++j) {
+        const float* dh = pb.dhx + j * 8;
+        dh_step(R, p, dh[0], dh[1], dh[2], dh[3], theta[static_cast<size_t>(i) * pb.d + j] + dh[4]);
+    }
+    float* e = ee + static_cast<size_t>(i) * 12;
+    for (int r = 0; r < 3; ++r) {
+        e[r * 4 + 0] = R[r * 3 + 0];
+        e[r * 4 + 1] = R[r * 3 + 1];
+        e[r * 4 + 2] = R[r * 3 + 2];
+        e[r * 4 + 3] = p[r];
+    }
+}
+
+// ---------------------------------------------------------------- set-up tables
+
+__device__ double clamped_knot(int i, int S)
+{
+    if (i <= 3) return 0.0;
+    if (i >= S) return 1.0;
+    return static_cast<double>(i - 3) / static_cast<double>(S - 3);
+}
+
+// Non-zero cubic basis functions at x by the triangular (de Boor) scheme,
+// scattered into a full row of S values.
+__device__ void bspline_row(int S, double x, float* row)
+{
+    int span = S - 1;
+    if (x < 1.0)
+        for (int k = 3; k < S; ++k)
+            if (clamped_knot(k, S) <= x && x < clamped_knot(k + 1, S)) {
+                span = k;
+                break;
+            }
+    double Nb[4], left[4], right[4];
+    Nb[0] = 1.0;
+    for (int j = 1; j <= 3; ++j) {
+        left[j] = x - clamped_knot(span + 1 - j, S);
+        right[j] = clamped_knot(span + j, S) - x;
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            const double t = Nb[r] / (right[r + 1] + left[j - r]);
+            Nb[r] = saved + right[r + 1] * t;
+            saved = left[j - r] * t;
+        }
+        Nb[j] = saved;
+    }
+    for (int s = 0; s < S; ++s) row[s] = 0.f;
+    for (int i = 0; i <= 3; ++i) row[span - 3 + i] = static_cast<float>(Nb[i]);
+}
+
+struct InitArgs {
+    const double* dh;     // d x 4
+    const double* q_min;  // d
+    const double* q_max;  // d
+    const double* dt;     // H
+    double k_jl, qdd_max, gamma;
+};
+
+__global__ void k_init_tables(Problem pb, InitArgs a)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float* dhx = const_cast<float*>(pb.dhx);
+    for (int i = tid; i < pb.d; i += nt) {
+        dhx[i * 8 + 0] = static_cast<float>(a.dh[i * 4 + 0]);
+        dhx[i * 8 + 1] = static_cast<float>(cos(a.dh[i * 4 + 1]));
+        dhx[i * 8 + 2] = static_cast<float>(sin(a.dh[i * 4 + 1]));
+        dhx[i * 8 + 3] = static_cast<float>(a.dh[i * 4 + 2]);
+        dhx[i * 8 + 4] = static_cast<float>(a.dh[i * 4 + 3]);
+        dhx[i * 8 + 5] = dhx[i * 8 + 6] = dhx[i * 8 + 7] = 0.f;
+        const double range = a.q_max[i] - a.q_min[i];
+        const_cast<float*>(pb.qlo)[i] = static_cast<float>(a.q_min[i] + a.k_jl * range);
+        const_cast<float*>(pb.qhi)[i] = static_cast<float>(a.q_max[i] - a.k_jl * range);
+    }
+    for (int h = tid; h < pb.H; h += nt) {
+        const_cast<float*>(pb.dt)[h] = static_cast<float>(a.dt[h]);
+        const_cast<float*>(pb.gpow)[h] = static_cast<float>(pow(a.gamma, static_cast<double>(h)));
+        double rest = 0.0;  // (S_u(1) qdd_max dt)_h
+        for (int k = pb.H - 1; k >= h; --k) rest += a.dt[k];
+        const_cast<float*>(pb.vmax)[h] = static_cast<float>(a.qdd_max * rest);
+        if (pb.spline) {
+            const double x = pb.H > 1 ? static_cast<double>(h) / (pb.H - 1) : 0.0;
+            bspline_row(pb.S, x, const_cast<float*>(pb.basis) + h * pb.S);
+        }
+    }
+}
+
+// prime[k] = k-th prime (prime[0] = 2), one thread per dimension.
+__global__ void k_primes(int D, int* prime)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= D) return;
+    int count = -1;
+    for (int c = 2;; ++c) {
+        bool is_p = true;
+        for (int q = 2; q * q <= c; ++q)
+            if (c % q == 0) {
+                is_p = false;
+                break;
+            }
+        if (is_p && ++count == k) {
+            prime[k] = c;
+            return;
+        }
+    }
+}
+
+// Halton noise: point n+1, dimension s*d+j, radical inverse as the exact
+// fraction (digit-reversed numerator) / base^digits, mapped through the
+// standard normal quantile.
+__global__ void k_halton(int N, int S, int d, const int* prime, float* out)
+{
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t total = static_cast<size_t>(N) * S * d;
+    if (i >= total) return;
+    const int dim = static_cast<int>(i % (static_cast<size_t>(S) * d));
+    const uint64_t n = i / (static_cast<size_t>(S) * d) + 1;
+    const uint64_t b = static_cast<uint64_t>(prime[dim]);
+    uint64_t num = 0, den = 1, k = n;
+    while (k > 0) {
+        num = num * b + k % b;
+        den *= b;
+        k /= b;
+    }
+    out[i] = static_cast<float>(normcdfinv(static_cast<double>(num) / static_cast<double>(den)));
+}
+
+// ============================================================================ host runtime
+
+struct storm_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    Problem pb{};
+    int K = 1;
+    int n_spheres_in = 0;
+    size_t rollout_smem = 0, update_smem = 0;
+    int grid = 0;
+    // device allocations
+    void* d_tables = nullptr;  // one block for every table
+    float* d_u = nullptr;
+    float* d_C = nullptr;
+    float* d_io = nullptr;     // state 3d | goal 7 | cmd d | StepState
+    StepState* d_st = nullptr;
+    float* h_io = nullptr;     // pinned mirror of d_io
+    cudaGraphExec_t g_dev = nullptr, g_host = nullptr;
+    std::string err = "no error";
+    std::vector<double> host_sigma_init;
+    double sigma_init = 0.0;
+    // capacity of the world tables
+    int cap_boxes = 0, cap_wsph = 0;
+};
+
+namespace {
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            if (h) h->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return e_ == cudaErrorMemoryAllocation ? STORM_ERR_OOM : STORM_ERR_CUDA;     \
+        }                                                                                \
+    } while (0)
+
+int fail(storm_handle* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+int io_state(const Problem& pb) { return 0; }
+int io_goal(const Problem& pb) { return 3 * pb.d; }
+int io_cmd(const Problem& pb) { return 3 * pb.d + 7; }
+int io_st(const Problem& pb) { return (3 * pb.d + 7 + pb.d + 3) & ~3; }
+int io_floats(const Problem& pb) { return io_st(pb) + 4; }
+
+bool finite_all(const double* p, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+int validate(const storm_robot* r, const storm_world* w, const storm_params* p, std::string& msg)
+{
+    if (!r || !w || !p) return msg = "NULL robot/world/params", STORM_ERR_INVALID_ARG;
+    if (r->dof < 1 || r->dof > STORM_MAX_DOF) return msg = "dof out of range", STORM_ERR_INVALID_ARG;
+    if (!r->dh || !r->q_min || !r->q_max) return msg = "NULL robot table", STORM_ERR_INVALID_ARG;
+    if (!finite_all(r->dh, 4 * r->dof) || !finite_all(r->q_min, r->dof) || !finite_all(r->q_max, r->dof))
+        return msg = "non-finite robot table", STORM_ERR_INVALID_ARG;
+    if (r->n_spheres < 0 || r->n_spheres > STORM_MAX_SPHERES)
+        return msg = "n_spheres out of range", STORM_ERR_INVALID_ARG;
+    if (r->n_spheres > 0 && (!r->sphere_link || !r->spheres))
+        return msg = "NULL sphere table", STORM_ERR_INVALID_ARG;
+    for (int s = 0; s < r->n_spheres; ++s) {
+        if (r->sphere_link[s] < 0 || r->sphere_link[s] > r->dof)
+            return msg = "sphere_link out of range", STORM_ERR_INVALID_ARG;
+        if (!finite_all(r->spheres + 4 * s, 4) || r->spheres[4 * s + 3] < 0)
+            return msg = "bad sphere", STORM_ERR_INVALID_ARG;
+    }
+    if (r->n_pairs < 0 || r->n_pairs > STORM_MAX_PAIRS)
+        return msg = "n_pairs out of range", STORM_ERR_INVALID_ARG;
+    if (r->n_pairs > 0 && !r->pairs) return msg = "NULL pairs", STORM_ERR_INVALID_ARG;
+    for (int k = 0; k < 2 * r->n_pairs; ++k)
+        if (r->pairs[k] < 0 || r->pairs[k] >= r->n_spheres)
+            return msg = "pair index out of range", STORM_ERR_INVALID_ARG;
+    if (w->n_boxes < 0 || w->n_boxes > STORM_MAX_OBSTACLES || w->n_spheres < 0 ||
+        w->n_spheres > STORM_MAX_OBSTACLES)
+        return msg = "obstacle count out of range", STORM_ERR_INVALID_ARG;
+    if ((w->n_boxes > 0 && !w->boxes) || (w->n_spheres > 0 && !w->spheres))
+        return msg = "NULL obstacle table", STORM_ERR_INVALID_ARG;
+    if (!finite_all(w->boxes, 6 * w->n_boxes) || !finite_all(w->spheres, 4 * w->n_spheres))
+        return msg = "non-finite obstacle", STORM_ERR_INVALID_ARG;
+    if (p->N < 1 || p->N > STORM_MAX_N) return msg = "N out of range", STORM_ERR_INVALID_ARG;
+    if (p->H < 1 || p->H > STORM_MAX_H) return msg = "H out of range", STORM_ERR_INVALID_ARG;
+    if (p->K < 1 || p->K > 255) return msg = "K out of range", STORM_ERR_INVALID_ARG;
+    if (p->n_knots != 0 && (p->n_knots < 4 || p->n_knots > p->H || p->H < 2))
+        return msg = "n_knots must be 0 or in [4, H] (H >= 2)", STORM_ERR_INVALID_ARG;
+    if (p->sampler != STORM_SAMPLER_PHILOX && p->sampler != STORM_SAMPLER_HALTON)
+        return msg = "bad sampler", STORM_ERR_INVALID_ARG;
+    if (p->rot_mode != STORM_ROT_QUAT && p->rot_mode != STORM_ROT_FROBENIUS)
+        return msg = "bad rot_mode", STORM_ERR_INVALID_ARG;
+    if (p->n_null < 0 || p->n_null > p->N) return msg = "n_null out of range", STORM_ERR_INVALID_ARG;
+    if (!p->dt || !finite_all(p->dt, p->H)) return msg = "bad dt", STORM_ERR_INVALID_ARG;
+    if (!(p->beta >= 0) || !(p->gamma >= 0) || !(p->sigma_init >= 0) || !(p->sigma_min >= 0))
+        return msg = "bad beta/gamma/sigma", STORM_ERR_INVALID_ARG;
+    if (p->instance >= (1u << 24)) return msg = "instance >= 2^24", STORM_ERR_INVALID_ARG;
+    return STORM_OK;
+}
+
+// Tables live in one device block; offsets in bytes, 256-aligned.
+struct TablePlan {
+    size_t dhx, qlo, qhi, sph, first, pairs, boxes, wsph, dt, gpow, vmax, basis, halton, mu,
+        sigma, prime, raw, total;
+};
+
+TablePlan plan_tables(const Problem& pb, int cap_boxes, int cap_wsph, int raw_doubles)
+{
+    TablePlan t;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    t.dhx = take(pb.d * 8 * 4);
+    t.qlo = take(pb.d * 4);
+    t.qhi = take(pb.d * 4);
+    t.sph = take(std::max(pb.M, 1) * 16);
+    t.first = take((pb.d + 2) * 4);
+    t.pairs = take(std::max(pb.P, 1) * 4);
+    t.boxes = take(std::max(cap_boxes, 1) * 6 * 4);
+    t.wsph = take(std::max(cap_wsph, 1) * 16);
+    t.dt = take(pb.H * 4);
+    t.gpow = take(pb.H * 4);
+    t.vmax = take(pb.H * 4);
+    t.basis = take(pb.spline ? pb.H * pb.S * 4 : 4);
+    t.halton = take(pb.sampler == STORM_SAMPLER_HALTON ? size_t(pb.N) * pb.S * pb.d * 4 : 4);
+    t.mu = take(pb.H * pb.d * 4);
+    t.sigma = take(pb.d * 4);
+    t.prime = take(pb.S * pb.d * 4);
+    t.raw = take(raw_doubles * 8);
+    t.total = off;
+    return t;
+}
+
+int upload_world(storm_handle* h, const storm_world* w)
+{
+    std::vector<float> boxes(6 * std::max(w->n_boxes, 1)), ws(4 * std::max(w->n_spheres, 1));
+    for (int i = 0; i < 6 * w->n_boxes; ++i) boxes[i] = static_cast<float>(w->boxes[i]);
+    for (int i = 0; i < 4 * w->n_spheres; ++i) ws[i] = static_cast<float>(w->spheres[i]);
+    if (w->n_boxes)
+        CK(cudaMemcpyAsync(const_cast<float*>(h->pb.boxes), boxes.data(), 6 * 4 * w->n_boxes,
+                           cudaMemcpyHostToDevice, h->stream));
+    if (w->n_spheres)
+        CK(cudaMemcpyAsync(const_cast<float4*>(h->pb.wsph), ws.data(), 16 * w->n_spheres,
+                           cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->pb.B = w->n_boxes;
+    h->pb.O = w->n_spheres;
+    return STORM_OK;
+}
+
+int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const float* state,
+                   const float* goal, int step_override, int iter)
+{
+    k_rollout<<<h->grid, kThreads, h->rollout_smem, s>>>(h->pb, out, state, goal, h->d_st,
+                                                         step_override, iter);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+int launch_update(storm_handle* h, cudaStream_t s, const float* C, const float* u, float* w,
+                  float* cmd, int finalize)
+{
+    k_update<<<1, kUpdateThreads, h->update_smem, s>>>(h->pb, C, u, w, h->d_st, cmd, finalize);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+// Enqueue the kernels of one control step (device inputs in d_io).
+int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
+{
+    const int O = h->pb.H * h->pb.d;
+    k_shift<<<1, std::max(32, ((O + 3) / 4 + 31) / 32 * 32), 0, s>>>(h->pb, h->d_st, 0);
+    CK(cudaGetLastError());
+    RolloutOut out{h->d_u, nullptr, nullptr, nullptr, nullptr, nullptr, h->d_C};
+    const float* state = h->d_io + io_state(h->pb);
+    const float* goal = h->d_io + io_goal(h->pb);
+    float* cmd = h->d_io + io_cmd(h->pb);
+    for (int k = 0; k < h->K; ++k) {
+        int rc = launch_rollout(h, s, out, state, goal, -1, k);
+        if (rc) return rc;
+        rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1);
+        if (rc) return rc;
+    }
+    return STORM_OK;
+}
+
+// Opt every kernel with dynamic shared memory in to the device maximum, so that
+// handles of different sizes never lower each other's limit.
+int allow_smem(storm_handle* h)
+{
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (h->rollout_smem > size_t(optin) || h->update_smem > size_t(optin))
+        return fail(h, STORM_ERR_INVALID_ARG, "problem needs more shared memory than a CTA has");
+    CK(cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CK(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    return STORM_OK;
+}
+
+void destroy_graphs(storm_handle* h)
+{
+    if (h->g_dev) cudaGraphExecDestroy(h->g_dev);
+    if (h->g_host) cudaGraphExecDestroy(h->g_host);
+    h->g_dev = h->g_host = nullptr;
+}
+
+int build_graphs(storm_handle* h)
+{
+    destroy_graphs(h);
+    for (int with_io = 0; with_io < 2; ++with_io) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = STORM_OK;
+        if (with_io) {
+            const size_t in_bytes = sizeof(float) * (3 * h->pb.d + 7);
+            rc = cudaMemcpyAsync(h->d_io, h->h_io, in_bytes, cudaMemcpyHostToDevice, h->cap_stream)
+                     ? STORM_ERR_CUDA
+                     : STORM_OK;
+        }
+        if (!rc) rc = enqueue_step_kernels(h, h->cap_stream);
+        if (!rc && with_io) {
+            const size_t off = io_cmd(h->pb);
+            const size_t bytes = sizeof(float) * (io_floats(h->pb) - off);
+            rc = cudaMemcpyAsync(h->h_io + off, h->d_io + off, bytes, cudaMemcpyDeviceToHost,
+                                 h->cap_stream)
+                     ? STORM_ERR_CUDA
+                     : STORM_OK;
+        }
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        CK(e);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        (with_io ? h->g_host : h->g_dev) = ex;
+    }
+    // upload the executable graphs once so the first replay is not slower
+    CK(cudaGraphUpload(h->g_dev, h->stream));
+    CK(cudaGraphUpload(h->g_host, h->stream));
+    return STORM_OK;
+}
+
+void free_all(storm_handle* h)
+{
+    destroy_graphs(h);
+    if (h->d_tables) cudaFree(h->d_tables);
+    if (h->d_u) cudaFree(h->d_u);
+    if (h->d_C) cudaFree(h->d_C);
+    if (h->d_io) cudaFree(h->d_io);
+    if (h->h_io) cudaFreeHost(h->h_io);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, const storm_params* p,
+                void* stream)
+{
+    CK(cudaGetDevice(&h->device));
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+
+    Problem& pb = h->pb;
+    pb.N = p->N;
+    pb.H = p->H;
+    pb.d = r->dof;
+    pb.spline = p->n_knots > 0;
+    pb.S = pb.spline ? p->n_knots : p->H;
+    pb.sampler = p->sampler;
+    pb.n_null = p->n_null;
+    pb.rot_mode = p->rot_mode;
+    pb.M = r->n_spheres;
+    pb.P = r->n_pairs;
+    pb.B = w->n_boxes;
+    pb.O = w->n_spheres;
+    pb.beta = static_cast<float>(p->beta);
+    pb.alpha_mu = static_cast<float>(p->alpha_mu);
+    pb.alpha_sigma = static_cast<float>(p->alpha_sigma);
+    pb.sigma_min = static_cast<float>(p->sigma_min);
+    pb.w_pos = static_cast<float>(p->w_pos);
+    pb.w_rot = static_cast<float>(p->w_rot);
+    pb.w_stop = static_cast<float>(p->w_stop);
+    pb.w_joint = static_cast<float>(p->w_joint);
+    pb.w_manip = static_cast<float>(p->w_manip);
+    pb.w_coll = static_cast<float>(p->w_coll);
+    pb.w_smooth = static_cast<float>(p->w_smooth);
+    for (int i = 0; i < 3; ++i) {
+        pb.pos_w[i] = static_cast<float>(p->pos_axis_w[i]);
+        pb.rot_w[i] = static_cast<float>(p->rot_axis_w[i]);
+    }
+    pb.k_m = static_cast<float>(p->k_m);
+    pb.seed_lo = static_cast<uint32_t>(p->seed & 0xffffffffu);
+    pb.seed_hi = static_cast<uint32_t>(p->seed >> 32);
+    pb.instance = p->instance;
+    h->K = p->K;
+    h->sigma_init = p->sigma_init;
+    h->cap_boxes = STORM_MAX_OBSTACLES;
+    h->cap_wsph = STORM_MAX_OBSTACLES;
+
+    // particles per CTA: about 64 (particle, step) items, never above the CTA size
+    pb.ppc = std::max(1, std::min(pb.N, 64 / pb.H));
+    h->grid = (pb.N + pb.ppc - 1) / pb.ppc;
+
+    // spheres sorted by link (stable); pairs remapped to the sorted order
+    std::vector<int> order(pb.M);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return r->sphere_link[a] < r->sphere_link[b]; });
+    std::vector<int> rank(pb.M);
+    for (int i = 0; i < pb.M; ++i) rank[order[i]] = i;
+    std::vector<float> sph(4 * std::max(pb.M, 1));
+    std::vector<int> first(pb.d + 2, 0);
+    for (int i = 0; i < pb.M; ++i) {
+        for (int k = 0; k < 4; ++k) sph[4 * i + k] = static_cast<float>(r->spheres[4 * order[i] + k]);
+        first[r->sphere_link[order[i]] + 1]++;
+    }
+    for (int f = 0; f <= pb.d; ++f) first[f + 1] += first[f];
+    std::vector<uint32_t> pairs(std::max(pb.P, 1));
+    for (int k = 0; k < pb.P; ++k) {
+        uint32_t a = rank[r->pairs[2 * k]], b = rank[r->pairs[2 * k + 1]];
+        if (a > b) std::swap(a, b);
+        pairs[k] = a | (b << 16);
+    }
+
+    // raw doubles for the set-up kernel: dh | q_min | q_max | dt
+    std::vector<double> raw;
+    raw.insert(raw.end(), r->dh, r->dh + 4 * pb.d);
+    raw.insert(raw.end(), r->q_min, r->q_min + pb.d);
+    raw.insert(raw.end(), r->q_max, r->q_max + pb.d);
+    raw.insert(raw.end(), p->dt, p->dt + pb.H);
+
+    const TablePlan t = plan_tables(pb, h->cap_boxes, h->cap_wsph, static_cast<int>(raw.size()));
+    CK(cudaMalloc(&h->d_tables, t.total));
+    char* base = static_cast<char*>(h->d_tables);
+    pb.dhx = reinterpret_cast<float*>(base + t.dhx);
+    pb.qlo = reinterpret_cast<float*>(base + t.qlo);
+    pb.qhi = reinterpret_cast<float*>(base + t.qhi);
+    pb.sph = reinterpret_cast<float4*>(base + t.sph);
+    pb.link_first = reinterpret_cast<int*>(base + t.first);
+    pb.pairs = reinterpret_cast<uint32_t*>(base + t.pairs);
+    pb.boxes = reinterpret_cast<float*>(base + t.boxes);
+    pb.wsph = reinterpret_cast<float4*>(base + t.wsph);
+    pb.dt = reinterpret_cast<float*>(base + t.dt);
+    pb.gpow = reinterpret_cast<float*>(base + t.gpow);
+    pb.vmax = reinterpret_cast<float*>(base + t.vmax);
+    pb.basis = reinterpret_cast<float*>(base + t.basis);
+    pb.halton = reinterpret_cast<float*>(base + t.halton);
+    pb.mu = reinterpret_cast<float*>(base + t.mu);
+    pb.sigma = reinterpret_cast<float*>(base + t.sigma);
+    int* d_prime = reinterpret_cast<int*>(base + t.prime);
+    double* d_raw = reinterpret_cast<double*>(base + t.raw);
+
+    CK(cudaMalloc(&h->d_u, sizeof(float) * size_t(pb.N) * pb.H * pb.d));
+    CK(cudaMalloc(&h->d_C, sizeof(float) * pb.N));
+    CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
+    CK(cudaMallocHost(&h->h_io, sizeof(float) * io_floats(pb)));
+    std::memset(h->h_io, 0, sizeof(float) * io_floats(pb));
+    h->d_st = reinterpret_cast<StepState*>(h->d_io + io_st(pb));
+
+    CK(cudaMemcpyAsync(const_cast<float4*>(pb.sph), sph.data(), 16 * std::max(pb.M, 1),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(const_cast<int*>(pb.link_first), first.data(), 4 * (pb.d + 2),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(const_cast<uint32_t*>(pb.pairs), pairs.data(), 4 * std::max(pb.P, 1),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d_raw, raw.data(), 8 * raw.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->d_io, 0, sizeof(float) * io_floats(pb), h->stream));
+    int rc = upload_world(h, w);
+    if (rc) return rc;
+
+    InitArgs ia{d_raw, d_raw + 4 * pb.d, d_raw + 5 * pb.d, d_raw + 6 * pb.d, p->k_jl, p->qdd_max,
+                p->gamma};
+    k_init_tables<<<1, 64, 0, h->stream>>>(pb, ia);
+    CK(cudaGetLastError());
+    if (pb.sampler == STORM_SAMPLER_HALTON) {
+        const int D = pb.S * pb.d;
+        k_primes<<<(D + 127) / 128, 128, 0, h->stream>>>(D, d_prime);
+        CK(cudaGetLastError());
+        const size_t total = size_t(pb.N) * pb.S * pb.d;
+        k_halton<<<static_cast<unsigned>((total + 255) / 256), 256, 0, h->stream>>>(
+            pb.N, pb.S, pb.d, d_prime, const_cast<float*>(pb.halton));
+        CK(cudaGetLastError());
+    }
+
+    const RolloutLayout L = rollout_layout(pb);
+    h->rollout_smem = L.bytes;
+    h->update_smem = sizeof(float) * (((pb.N + 3) & ~3) + kUpdateThreads + pb.H * pb.d);
+    rc = allow_smem(h);
+    if (rc) return rc;
+    rc = storm_reset(h);
+    if (rc) return rc;
+    return build_graphs(h);
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+const char* storm_status_string(int s)
+{
+    switch (s) {
+    case STORM_OK: return "ok";
+    case STORM_WARN_DEGENERATE: return "warning: no finite total cost; distribution kept";
+    case STORM_ERR_INVALID_ARG: return "invalid argument";
+    case STORM_ERR_CUDA: return "CUDA error";
+    case STORM_ERR_OOM: return "out of device memory";
+    case STORM_ERR_NONFINITE: return "non-finite state or goal";
+    case STORM_ERR_TIMEOUT: return "timeout";
+    case STORM_ERR_STATE: return "checkpoint does not match handle";
+    default: return "unknown status";
+    }
+}
+
+const char* storm_last_error(const storm_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+int storm_create(const storm_robot* robot, const storm_world* world, const storm_params* params,
+                 void* cuda_stream, storm_handle** out)
+{
+    if (!out) return STORM_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string msg;
+    const int v = validate(robot, world, params, msg);
+    if (v) return v;
+    storm_handle* h = new (std::nothrow) storm_handle();
+    if (!h) return STORM_ERR_OOM;
+    const int rc = create_impl(h, robot, world, params, cuda_stream);
+    if (rc) {
+        fprintf(stderr, "storm_create: %s\n", h->err.c_str());
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return STORM_OK;
+}
+
+void storm_destroy(storm_handle* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int storm_reset(storm_handle* h)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    const int O = h->pb.H * h->pb.d;
+    std::vector<float> mu(O, 0.f), sg(h->pb.d, static_cast<float>(h->sigma_init));
+    CK(cudaMemcpyAsync(h->pb.mu, mu.data(), 4 * O, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->pb.sigma, sg.data(), 4 * h->pb.d, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->d_st, 0, sizeof(StepState), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return STORM_OK;
+}
+
+int storm_step(storm_handle* h, const float* state, const float* goal, float* cmd,
+               storm_step_info* info)
+{
+    if (!h || !state || !goal || !cmd) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    const int d = h->pb.d;
+    for (int i = 0; i < 3 * d; ++i)
+        if (!std::isfinite(state[i])) return fail(h, STORM_ERR_NONFINITE, "non-finite state");
+    for (int i = 0; i < 7; ++i)
+        if (!std::isfinite(goal[i])) return fail(h, STORM_ERR_NONFINITE, "non-finite goal");
+    std::memcpy(h->h_io + io_state(h->pb), state, sizeof(float) * 3 * d);
+    std::memcpy(h->h_io + io_goal(h->pb), goal, sizeof(float) * 7);
+    CK(cudaGraphLaunch(h->g_host, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(cmd, h->h_io + io_cmd(h->pb), sizeof(float) * d);
+    const StepState* st = reinterpret_cast<const StepState*>(h->h_io + io_st(h->pb));
+    if (info) {
+        info->best_cost = st->best;
+        info->mean_weighted_cost = st->wmean;
+        info->status = st->status;
+        info->step = st->step - 1;
+    }
+    return st->status;
+}
+
+int storm_step_async(storm_handle* h, const float* state_dev, const float* goal_dev, float* cmd_dev)
+{
+    if (!h || !state_dev || !goal_dev || !cmd_dev) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    const int d = h->pb.d;
+    float* s_in = h->d_io + io_state(h->pb);
+    float* g_in = h->d_io + io_goal(h->pb);
+    float* c_out = h->d_io + io_cmd(h->pb);
+    if (state_dev != s_in)
+        CK(cudaMemcpyAsync(s_in, state_dev, sizeof(float) * 3 * d, cudaMemcpyDeviceToDevice, h->stream));
+    if (goal_dev != g_in)
+        CK(cudaMemcpyAsync(g_in, goal_dev, sizeof(float) * 7, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaGraphLaunch(h->g_dev, h->stream));
+    if (cmd_dev != c_out)
+        CK(cudaMemcpyAsync(cmd_dev, c_out, sizeof(float) * d, cudaMemcpyDeviceToDevice, h->stream));
+    return STORM_OK;
+}
+
+int storm_sync(storm_handle* h, storm_step_info* info)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    StepState st;
+    CK(cudaMemcpyAsync(&st, h->d_st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (info) {
+        info->best_cost = st.best;
+        info->mean_weighted_cost = st.wmean;
+        info->status = st.status;
+        info->step = st.step ? st.step - 1 : 0;
+    }
+    return st.status;
+}
+
+int storm_device_io(storm_handle* h, float** state_dev, float** goal_dev, float** cmd_dev)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    if (state_dev) *state_dev = h->d_io + io_state(h->pb);
+    if (goal_dev) *goal_dev = h->d_io + io_goal(h->pb);
+    if (cmd_dev) *cmd_dev = h->d_io + io_cmd(h->pb);
+    return STORM_OK;
+}
+
+int storm_shift(storm_handle* h)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    const int O = h->pb.H * h->pb.d;
+    k_shift<<<1, std::max(32, ((O + 3) / 4 + 31) / 32 * 32), 0, h->stream>>>(h->pb, h->d_st, 1);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+int storm_sample_noise(storm_handle* h, uint32_t step, int iter, float* eps_dev)
+{
+    if (!h || !eps_dev) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    if (iter < 0 || iter > 255) return fail(h, STORM_ERR_INVALID_ARG, "bad iter");
+    const uint32_t blocks = (static_cast<uint32_t>(h->pb.N) * h->pb.S * h->pb.d + 3) / 4;
+    k_noise<<<(blocks + 255) / 256, 256, 0, h->stream>>>(h->pb, step, iter, eps_dev);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+int storm_generate_rollouts(storm_handle* h, const float* state_dev, const float* goal_dev,
+                            uint32_t step, int iter, float* u_dev, float* theta_dev,
+                            float* theta_dot_dev, float* ee_dev, float* terms_dev,
+                            float* cost_dev, float* Ctot_dev)
+{
+    if (!h || !state_dev || !goal_dev) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    if (iter < 0 || iter > 255 || step > 0x7fffffffu) return fail(h, STORM_ERR_INVALID_ARG, "bad iter/step");
+    RolloutOut out{u_dev ? u_dev : h->d_u, theta_dev, theta_dot_dev, ee_dev, terms_dev, cost_dev,
+                   Ctot_dev ? Ctot_dev : h->d_C};
+    return launch_rollout(h, h->stream, out, state_dev, goal_dev, static_cast<int>(step), iter);
+}
+
+int storm_update_distribution(storm_handle* h, const float* Ctot_dev, const float* u_dev,
+                              float* weights_dev)
+{
+    if (!h || !Ctot_dev || !u_dev) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    return launch_update(h, h->stream, Ctot_dev, u_dev, weights_dev, nullptr, 0);
+}
+
+int storm_get_distribution(storm_handle* h, float* mean, float* sigma)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    if (mean)
+        CK(cudaMemcpyAsync(mean, h->pb.mu, sizeof(float) * h->pb.H * h->pb.d, cudaMemcpyDeviceToHost,
+                           h->stream));
+    if (sigma)
+        CK(cudaMemcpyAsync(sigma, h->pb.sigma, sizeof(float) * h->pb.d, cudaMemcpyDeviceToHost,
+                           h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return STORM_OK;
+}
+
+int storm_set_distribution(storm_handle* h, const float* mean, const float* sigma)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    if (mean)
+        CK(cudaMemcpyAsync(h->pb.mu, mean, sizeof(float) * h->pb.H * h->pb.d, cudaMemcpyHostToDevice,
+                           h->stream));
+    if (sigma)
+        CK(cudaMemcpyAsync(h->pb.sigma, sigma, sizeof(float) * h->pb.d, cudaMemcpyHostToDevice,
+                           h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return STORM_OK;
+}
+
+int storm_set_world(storm_handle* h, const storm_world* world)
+{
+    if (!h || !world) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    if (world->n_boxes < 0 || world->n_boxes > h->cap_boxes || world->n_spheres < 0 ||
+        world->n_spheres > h->cap_wsph)
+        return fail(h, STORM_ERR_INVALID_ARG, "obstacle count out of range");
+    if ((world->n_boxes && !world->boxes) || (world->n_spheres && !world->spheres))
+        return fail(h, STORM_ERR_INVALID_ARG, "NULL obstacle table");
+    if (!finite_all(world->boxes, 6 * world->n_boxes) || !finite_all(world->spheres, 4 * world->n_spheres))
+        return fail(h, STORM_ERR_INVALID_ARG, "non-finite obstacle");
+    CK(cudaStreamSynchronize(h->stream));
+    const int old_B = h->pb.B, old_O = h->pb.O;
+    const int rc = upload_world(h, world);
+    if (rc) return rc;
+    // the counts are baked into the captured graphs and the shared-memory plan
+    if (h->pb.B != old_B || h->pb.O != old_O) {
+        const RolloutLayout L = rollout_layout(h->pb);
+        h->rollout_smem = L.bytes;
+        return build_graphs(h);
+    }
+    return STORM_OK;
+}
+
+int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count, float* ee_dev)
+{
+    if (!h || count < 0 || (count > 0 && (!theta_dev || !ee_dev)))
+        return fail(h, STORM_ERR_INVALID_ARG, "bad argument");
+    if (count == 0) return STORM_OK;
+    k_fk<<<(count + 127) / 128, 128, 0, h->stream>>>(h->pb, theta_dev, count, ee_dev);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+// checkpoint blob: magic, version, N, H, d, step | mu (H*d) | sigma (d)
+static const uint32_t kMagic = 0x4d525453u;  // "STRM"
+
+int storm_get_state(storm_handle* h, void* buf, size_t* len)
+{
+    if (!h || !len) return STORM_ERR_INVALID_ARG;
+    const int O = h->pb.H * h->pb.d;
+    const size_t need = 6 * 4 + 4 * (O + h->pb.d);
+    if (!buf) {
+        *len = need;
+        return STORM_OK;
+    }
+    if (*len < need) return fail(h, STORM_ERR_INVALID_ARG, "buffer too small");
+    StepState st;
+    uint32_t* w = static_cast<uint32_t*>(buf);
+    CK(cudaMemcpyAsync(&st, h->d_st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(w + 6, h->pb.mu, 4 * O, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(w + 6 + O, h->pb.sigma, 4 * h->pb.d, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    w[0] = kMagic;
+    w[1] = 1;
+    w[2] = h->pb.N;
+    w[3] = h->pb.H;
+    w[4] = h->pb.d;
+    w[5] = st.step;
+    *len = need;
+    return STORM_OK;
+}
+
+int storm_set_state(storm_handle* h, const void* buf, size_t len)
+{
+    if (!h || !buf) return STORM_ERR_INVALID_ARG;
+    const int O = h->pb.H * h->pb.d;
+    const size_t need = 6 * 4 + 4 * (O + h->pb.d);
+    const uint32_t* w = static_cast<const uint32_t*>(buf);
+    if (len != need || w[0] != kMagic || w[1] != 1 || w[2] != uint32_t(h->pb.N) ||
+        w[3] != uint32_t(h->pb.H) || w[4] != uint32_t(h->pb.d))
+        return fail(h, STORM_ERR_STATE, "checkpoint does not match this handle");
+    StepState st{w[5], 0, 0.f, 0.f};
+    CK(cudaMemcpyAsync(h->pb.mu, w + 6, 4 * O, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->pb.sigma, w + 6 + O, 4 * h->pb.d, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return STORM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// storm_device.cuh -- device-side building blocks of the STORM control step.
+//
+// Counter-based noise (Philox4x32-10 + Box-Muller), the modified-DH chain
+// step, the manipulability score and the per-problem parameter block that
+// every kernel receives by value.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace storm {
+
+constexpr int kMaxDof = 7;
+constexpr int kThreads = 256;        // rollout CTA size
+constexpr int kUpdateThreads = 1024; // distribution-update CTA size
+
+// Per-problem constants and device table pointers (kernel parameter, by value).
+struct Problem {
+    int N, H, d, S;          // particles, horizon, joints, noise knots (S = H without spline)
+    int spline;              // 1 when the noise is smoothed by the B-spline basis
+    int sampler, n_null, rot_mode;
+    int M, P, B, O;          // link spheres, self pairs, boxes, obstacle spheres
+    int ppc;                 // particles per rollout CTA
+    float beta, alpha_mu, alpha_sigma, sigma_min;
+    float w_pos, w_rot, w_stop, w_joint, w_manip, w_coll, w_smooth;
+    float pos_w[3], rot_w[3];
+    float k_m;
+    uint32_t seed_lo, seed_hi, instance;
+    const float* dhx;        // d x 8: a, cos alpha, sin alpha, d, offset, -, -, -
+    const float* qlo;        // d soft lower limits  q_min + k_jl (q_max - q_min)
+    const float* qhi;        // d soft upper limits  q_max - k_jl (q_max - q_min)
+    const float4* sph;       // M: centre in link frame, radius (sorted by link)
+    const int* link_first;   // d + 2: spheres of frame f are [link_first[f], link_first[f+1])
+    const uint32_t* pairs;   // P: a | b << 16 (sorted sphere indices)
+    const float* boxes;      // B x 6
+    const float4* wsph;      // O
+    const float* dt;         // H
+    const float* gpow;       // H: gamma^h
+    const float* vmax;       // H: qdd_max * sum_{k >= h} dt_k
+    const float* basis;      // H x S B-spline basis (spline only)
+    const float* halton;     // N x S x d normal noise (Halton sampler only)
+    float* mu;               // H x d
+    float* sigma;            // d
+};
+
+// Step bookkeeping kept on the device so captured graphs need no host update.
+struct StepState {
+    uint32_t step;   // index of the next control step
+    int status;      // OR of warnings of the current step
+    float best;      // min total cost of the last iteration
+    float wmean;     // weighted mean total cost of the last iteration
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: ten rounds of two 32x32->64 multiplies with a Weyl key
+// schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 23 high bits, centred: exactly representable in float, strictly inside (0, 1).
+__device__ __forceinline__ float bits_to_unit(uint32_t x)
+{
+    return (static_cast<float>(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+// Box-Muller pair from two words.
+__device__ __forceinline__ float2 gauss_pair(uint32_t a, uint32_t b)
+{
+    const float r = sqrtf(-2.0f * logf(bits_to_unit(a)));
+    float s, c;
+    sincospif(2.0f * bits_to_unit(b), &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+// ---------------------------------------------------------------- kinematics
+// One modified-DH link: T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d),
+// with R row-major 3x3 and p the origin.  In place.
+__device__ __forceinline__ void dh_step(float (&R)[9], float (&p)[3], float a, float ca, float sa,
+                                        float dd, float theta)
+{
+    float st, ct;
+    sincosf(theta, &st, &ct);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float c0 = R[r * 3 + 0], c1 = R[r * 3 + 1], c2 = R[r * 3 + 2];
+        const float x1 = fmaf(ca, c1, sa * c2);
+        const float x2 = fmaf(-sa, c1, ca * c2);
+        p[r] = fmaf(dd, x2, fmaf(a, c0, p[r]));
+        R[r * 3 + 0] = fmaf(ct, c0, st * x1);
+        R[r * 3 + 1] = fmaf(-st, c0, ct * x1);
+        R[r * 3 + 2] = x2;
+    }
+}
+
+// sqrt(det(J J^T)) for a 6 x d Jacobian given as rows, by modified Gram-Schmidt
+// on the six rows: the determinant of the Gram matrix is the product of the
+// squared norms of the orthogonalised rows.
+__device__ __forceinline__ float manipulability_mgs(float (&J)[6][kMaxDof], int d)
+{
+    float m = 1.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int i = 0; i < k; ++i) {
+            float dot = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kMaxDof; ++c)
+                if (c < d) dot = fmaf(J[i][c], J[k][c], dot);
+#pragma unroll
+            for (int c = 0; c < kMaxDof; ++c)
+                if (c < d) J[k][c] = fmaf(-dot, J[i][c], J[k][c]);
+        }
+        float nn = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kMaxDof; ++c)
+            if (c < d) nn = fmaf(J[k][c], J[k][c], nn);
+        const float nk = sqrtf(nn);
+        m *= nk;
+        const float inv = nk > 0.0f ? 1.0f / nk : 0.0f;
+#pragma unroll
+        for (int c = 0; c < kMaxDof; ++c) J[k][c] *= inv;
+    }
+    return m;
+}
+
+}  // namespace storm

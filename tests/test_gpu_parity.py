@@ -1,0 +1,312 @@
+"""Parity of the CUDA control step with the FP64 oracle, through the C ABI.
+
+Stage by stage (noise, rollouts, distribution update, shift, FK) and end to end
+(one and several control steps), on the seeded workloads: the 64 x 20 plain
+MPPI step and the 500 x 30 paper-scale step at full size, plus ragged and
+degenerate variants.  Tolerances are stated in tests/gpu_helpers.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_13542_b300 import Controller, StormError
+from paper_2104_13542_b300 import workloads as W
+
+from gpu_helpers import (TOL_COST, TOL_STATE, TOL_UPDATE, cuda, f32, host, manip_flips,
+                         max_rel, mu_tolerance)
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctl(wl, p=None):
+    return Controller(wl.robot, wl.world, p or wl.params)
+
+
+def _variants():
+    small, paper = W.config_small(0), W.config_paper(0)
+    return {
+        "small": (small, small.params),
+        "paper": (paper, paper.params),
+        "paper_ragged_N37": (paper, paper.params.replace(N=37)),
+        "paper_halton": (paper, paper.params.replace(N=96, sampler=W.SAMPLER_HALTON)),
+        "paper_null_frob": (paper, paper.params.replace(N=64, n_null=5,
+                                                        rot_mode=W.ROT_FROBENIUS,
+                                                        rot_axis_w=(0.5, 1.0, 2.0),
+                                                        pos_axis_w=(1.0, 2.0, 0.5))),
+        "small_H1": (small, small.params.replace(N=16, H=1)),
+        "small_N1": (small, small.params.replace(N=1)),
+        "paper_H50_knots10": (paper, paper.params.replace(N=40, H=50, n_knots=10)),
+    }
+
+
+VARIANTS = _variants()
+
+
+# ----------------------------------------------------------------------------- noise
+
+@pytest.mark.parametrize("name", ["small", "paper", "paper_ragged_N37", "paper_halton"])
+def test_noise_matches_oracle(name):
+    wl, p = VARIANTS[name]
+    orc = oracle.Oracle(wl.robot, wl.world, p)
+    with _ctl(wl, p) as ctl:
+        for step, it in [(0, 0), (3, 2), (17, 1)]:
+            g = host(ctl.sample_noise(step, it))
+            o = orc.noise(step, it)
+            assert g.shape == o.shape
+            err = np.abs(g - o) / np.maximum(1.0, np.abs(o))
+            assert err.max() < 2e-6, (step, it, err.max())
+
+
+# ----------------------------------------------------------------------------- rollouts
+
+def _rollout_pair(wl, p, seed=0, step=2, it=1):
+    orc = oracle.Oracle(wl.robot, wl.world, p)
+    mu = f32(W.make_mean(seed, p.H, 7, 0.5))
+    sig = f32(W.make_sigma(seed, 7))
+    state = f32(W.make_state(seed + 10, 7))
+    goal = f32(wl.goal)
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(mu, sig)
+        g = ctl.generate_rollouts(cuda(state), cuda(goal), step, it)
+        g = {k: host(v) for k, v in g.items()}
+    o = orc.rollout(state, goal, mu, sig, orc.noise(step, it))
+    return orc, g, o
+
+
+@pytest.mark.parametrize("name", list(VARIANTS))
+def test_rollout_stage_parity(name):
+    wl, p = VARIANTS[name]
+    orc, g, o = _rollout_pair(wl, p)
+    assert max_rel(g["u"], o["u"], max(1.0, np.abs(o["u"]).max())) < TOL_STATE
+    assert max_rel(g["theta"], o["theta"], max(1.0, np.abs(o["theta"]).max())) < TOL_STATE
+    assert max_rel(g["theta_dot"], o["theta_dot"], max(1.0, np.abs(o["theta_dot"]).max())) < TOL_STATE
+    assert max_rel(g["ee"], o["ee"], 1.0) < TOL_STATE
+    flip, ok = manip_flips(orc, o["theta"], p.k_m, g["terms"], o["terms"])
+    assert ok and flip.mean() <= 1e-3, f"manipulability branch flips: {flip.sum()}"
+    keep = ~flip
+    cscale = max(1.0, np.abs(o["cost"]).max())
+    for t in range(8):
+        tscale = max(1.0, np.abs(o["terms"][..., t]).max())
+        e = max_rel(g["terms"][..., t][keep], o["terms"][..., t][keep], tscale)
+        assert e < TOL_COST, (W.TERM_NAMES[t], e)
+    assert max_rel(g["cost"][keep], o["cost"][keep], cscale) < TOL_COST
+    rows = ~flip.any(axis=1)
+    assert max_rel(g["C"][rows], o["C"][rows], max(1.0, np.abs(o["C"]).max())) < TOL_COST
+    # discounted total is the gamma-weighted sum of the GPU's own running costs
+    gam = p.gamma ** np.arange(p.H)
+    assert max_rel(g["C"], g["cost"] @ gam, max(1.0, np.abs(g["C"]).max())) < 1e-5
+
+
+def test_rollout_collision_terms_active():
+    """The paper-scale workload exercises every cost term (none identically zero)."""
+    wl, p = VARIANTS["paper"]
+    orc, g, o = _rollout_pair(wl, p, seed=3)
+    for t, name in enumerate(W.TERM_NAMES):
+        if name == "smooth":
+            continue
+        assert (o["terms"][..., t] > 0).any(), name
+        assert (g["terms"][..., t] > 0).any(), name
+
+
+# ----------------------------------------------------------------------------- update
+
+def _update_pair(N, H, beta, C=None, seed=0, **kw):
+    wl = W.config_small(0)
+    p = wl.params.replace(N=N, H=H, beta=beta, **kw)
+    orc = oracle.Oracle(wl.robot, wl.world, p)
+    u = f32(W.make_controls(seed, N, H, 7, 0.7))
+    Cv = f32(W.make_costs(seed, N, 0.0, 30.0) if C is None else C)
+    mu0 = f32(W.make_mean(seed, H, 7))
+    sig0 = f32(W.make_sigma(seed, 7))
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(mu0, sig0)
+        w = host(ctl.update_distribution(cuda(Cv), cuda(u)))
+        mu, sig = ctl.get_distribution()
+        info, st = ctl.sync()
+    omu, osig, ost, ow = orc.update(Cv, u, mu0, sig0)
+    return (mu, sig, w, st), (omu, osig, ow, ost), mu0, sig0, u
+
+
+@pytest.mark.parametrize("N,H,beta,amu,asg", [(64, 20, 0.1, 1.0, 0.5), (500, 30, 10.0, 1.0, 0.5),
+                                              (1000, 30, 1.0, 0.7, 0.3), (37, 7, 3.0, 0.5, 1.0),
+                                              (1, 5, 1.0, 1.0, 0.5), (2048, 10, 2.0, 1.0, 0.5)])
+def test_update_stage_parity(N, H, beta, amu, asg):
+    (mu, sig, w, st), (omu, osig, ow, ost), *_ = _update_pair(N, H, beta, alpha_mu=amu,
+                                                             alpha_sigma=asg)
+    assert st == 0 and ost == 0
+    assert max_rel(w, ow, 1.0) < TOL_UPDATE
+    assert abs(w.sum() - 1.0) < 1e-5
+    assert max_rel(mu, omu, max(1.0, np.abs(omu).max())) < TOL_UPDATE
+    assert max_rel(sig, osig, max(osig.max(), 1e-3)) < TOL_UPDATE
+
+
+def test_update_zero_temperature_and_ties():
+    C = np.full(50, 9.0)
+    C[[7, 30]] = 2.0  # tie: lowest index wins
+    (mu, sig, w, st), (omu, osig, ow, ost), mu0, sig0, u = _update_pair(50, 6, 0.0, C=C)
+    assert np.array_equal(w, np.eye(50)[7])
+    assert np.allclose(mu, u[7], atol=1e-7)
+    assert max_rel(sig, osig, 1.0) < TOL_UPDATE
+
+
+def test_update_nonfinite_costs():
+    C = W.make_costs(1, 40, 0.0, 5.0)
+    C[[3, 11]] = np.inf
+    C[20] = np.nan
+    (mu, sig, w, st), (omu, osig, ow, ost), *_ = _update_pair(40, 6, 1.0, C=C)
+    assert w[3] == 0 and w[11] == 0 and w[20] == 0
+    assert max_rel(mu, omu, max(1.0, np.abs(omu).max())) < TOL_UPDATE
+
+
+def test_update_degenerate_keeps_distribution():
+    C = np.full(16, np.inf)
+    (mu, sig, w, st), (omu, osig, ow, ost), mu0, sig0, _ = _update_pair(16, 5, 1.0, C=C)
+    assert st == 1 and ost == 1
+    assert np.array_equal(mu, mu0.astype(np.float32)) and np.array_equal(sig, sig0.astype(np.float32))
+
+
+# ----------------------------------------------------------------------------- control step
+
+def _step_pair(wl, p, n_steps=1, state_seed=0):
+    orc = oracle.Oracle(wl.robot, wl.world, p)
+    state = f32(W.make_state(state_seed + 20, 7))
+    goal = f32(wl.goal)
+    omu, osig = np.zeros((p.H, 7)), np.full(7, f32(p.sigma_init))
+    res = []
+    with _ctl(wl, p) as ctl:
+        for t in range(n_steps):
+            cmd, info, rc = ctl.step(state, goal)
+            mu, sig = ctl.get_distribution()
+            ocmd, omu, osig, ost, obest = orc.step(state, goal, t, omu, osig)
+            res.append((cmd, info, rc, mu, sig, ocmd, omu.copy(), osig.copy(), ost, obest))
+    return res
+
+
+@pytest.mark.parametrize("name", ["small", "paper", "paper_ragged_N37", "paper_halton",
+                                  "paper_null_frob", "small_N1"])
+def test_step_parity(name):
+    wl, p = VARIANTS[name]
+    (cmd, info, rc, mu, sig, ocmd, omu, osig, ost, obest), = _step_pair(wl, p)
+    assert rc == ost == 0
+    assert info["step"] == 0
+    tol = mu_tolerance([obest, info["mean_weighted_cost"]], p.beta)
+    scale = max(1.0, np.abs(omu).max())
+    assert max_rel(mu, omu, scale) < tol
+    assert max_rel(cmd, ocmd, scale) < tol
+    assert np.array_equal(cmd, mu[0])
+    assert max_rel(sig, osig, max(1e-3, osig.max())) < tol
+    assert abs(info["best_cost"] - obest) <= TOL_COST * max(1.0, abs(obest))
+
+
+def test_multi_step_parity_with_shift():
+    wl, p = VARIANTS["small"]
+    res = _step_pair(wl, p, n_steps=4)
+    for t, (cmd, info, rc, mu, sig, ocmd, omu, osig, ost, obest) in enumerate(res):
+        assert info["step"] == t
+        tol = mu_tolerance([obest], p.beta) * (t + 1)
+        scale = max(1.0, np.abs(omu).max())
+        assert max_rel(mu, omu, scale) < tol, t
+        assert max_rel(sig, osig, max(1e-3, osig.max())) < tol, t
+
+
+def test_shift_stage():
+    wl, p = VARIANTS["small"]
+    mu0 = W.make_mean(4, p.H, 7).astype(np.float32)
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(mu0, np.full(7, 0.2))
+        ctl.shift()
+        mu, sig = ctl.get_distribution()
+    assert np.array_equal(mu[:-1], mu0[1:]) and np.all(mu[-1] == 0)
+    assert np.allclose(sig, 0.2)
+
+
+# ----------------------------------------------------------------------------- other entry points
+
+def test_forward_kinematics_matches_oracle():
+    wl = W.config_paper(2)
+    orc = oracle.from_workload(wl)
+    th = f32(np.random.default_rng(0).uniform(-2.8, 2.8, (1000, 7)))
+    with _ctl(wl) as ctl:
+        ee = host(ctl.forward_kinematics(cuda(th)))
+    o = np.stack([orc.fk(t)[-1][:3] for t in th])
+    assert max_rel(ee, o, 1.0) < TOL_STATE
+
+
+def test_checkpoint_resume_is_bitwise():
+    wl, p = VARIANTS["small"]
+    state, goal = f32(wl.state), f32(wl.goal)
+    with _ctl(wl, p) as a:
+        a.step(state, goal)
+        blob = a.get_state()
+        ref = [a.step(state, goal)[0] for _ in range(3)]
+        mu_a, sig_a = a.get_distribution()
+    with _ctl(wl, p) as b:
+        b.set_state(blob)
+        got = [b.step(state, goal)[0] for _ in range(3)]
+        mu_b, sig_b = b.get_distribution()
+        with pytest.raises(StormError):
+            b.set_state(blob[:-4])
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    assert np.array_equal(mu_a, mu_b) and np.array_equal(sig_a, sig_b)
+
+
+def test_determinism_across_handles():
+    wl, p = VARIANTS["paper"]
+    state, goal = f32(wl.state), f32(wl.goal)
+    outs = []
+    for _ in range(2):
+        with _ctl(wl, p) as c:
+            cmds = [c.step(state, goal)[0] for _ in range(2)]
+            outs.append((cmds, c.get_distribution()))
+    assert all(np.array_equal(x, y) for x, y in zip(outs[0][0], outs[1][0]))
+    assert np.array_equal(outs[0][1][0], outs[1][1][0])
+
+
+def test_set_world_then_rollout_parity():
+    wl = W.config_paper(1)
+    p = wl.params.replace(N=48)
+    new_world = W.make_world(7, n_boxes=5, n_spheres=3)
+    orc = oracle.Oracle(wl.robot, new_world, p)
+    mu, sig = f32(W.make_mean(1, p.H, 7)), f32(W.make_sigma(1, 7))
+    state, goal = f32(wl.state), f32(wl.goal)
+    with _ctl(wl, p) as ctl:
+        ctl.set_world(new_world)
+        ctl.set_distribution(mu, sig)
+        g = {k: host(v) for k, v in ctl.generate_rollouts(cuda(state), cuda(goal), 0, 0).items()}
+    o = orc.rollout(state, goal, mu, sig, orc.noise(0, 0))
+    for t in (5, 6):
+        assert max_rel(g["terms"][..., t], o["terms"][..., t], 1.0) < TOL_COST
+
+
+def test_nonfinite_inputs_rejected():
+    wl, p = VARIANTS["small"]
+    with _ctl(wl, p) as ctl:
+        bad = f32(wl.state).copy()
+        bad[1, 2] = np.nan
+        with pytest.raises(StormError) as e:
+            ctl.step(bad, wl.goal)
+        assert e.value.code == -4
+        g = f32(wl.goal).copy()
+        g[5] = np.inf
+        with pytest.raises(StormError):
+            ctl.step(wl.state, g)
+        cmd, info, rc = ctl.step(wl.state, wl.goal)  # handle still usable
+        assert rc == 0 and info["step"] == 0
+
+
+def test_step_async_device_buffers_match_host_step():
+    wl, p = VARIANTS["paper"]
+    state, goal = f32(wl.state), f32(wl.goal)
+    with _ctl(wl, p) as a:
+        ref = [a.step(state, goal)[0] for _ in range(2)]
+    with _ctl(wl, p) as b:
+        s, g, c = cuda(state), cuda(goal), torch.zeros(7, device="cuda")
+        got = []
+        for _ in range(2):
+            b.step_async(s, g, c)
+            b.sync()
+            got.append(c.cpu().numpy().copy())
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
