@@ -810,6 +810,7 @@ namespace {
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \
         if (e_ != cudaSuccess) {                                                         \
+            (void)cudaGetLastError(); /* do not leave the error for a later check */     \
             if (h) h->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
             return e_ == cudaErrorMemoryAllocation ? STORM_ERR_OOM : STORM_ERR_CUDA;     \
         }                                                                                \
@@ -976,10 +977,16 @@ int allow_smem(storm_handle* h)
 {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (h->rollout_smem > size_t(optin) || h->update_smem > size_t(optin))
+    cudaFuncAttributes ra, ua;
+    CK(cudaFuncGetAttributes(&ra, k_rollout));
+    CK(cudaFuncGetAttributes(&ua, k_update));
+    if (h->rollout_smem + ra.sharedSizeBytes > size_t(optin) ||
+        h->update_smem + ua.sharedSizeBytes > size_t(optin))
         return fail(h, STORM_ERR_INVALID_ARG, "problem needs more shared memory than a CTA has");
-    CK(cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    CK(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CK(cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(ra.sharedSizeBytes)));
+    CK(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(ua.sharedSizeBytes)));
     return STORM_OK;
 }
 

@@ -60,11 +60,11 @@ def test_noise_matches_oracle(name):
 
 # ----------------------------------------------------------------------------- rollouts
 
-def _rollout_pair(wl, p, seed=0, step=2, it=1):
+def _rollout_pair(wl, p, seed=0, step=2, it=1, state=None):
     orc = oracle.Oracle(wl.robot, wl.world, p)
     mu = f32(W.make_mean(seed, p.H, 7, 0.5))
     sig = f32(W.make_sigma(seed, 7))
-    state = f32(W.make_state(seed + 10, 7))
+    state = f32(W.make_state(seed + 10, 7) if state is None else state)
     goal = f32(wl.goal)
     with _ctl(wl, p) as ctl:
         ctl.set_distribution(mu, sig)
@@ -101,7 +101,9 @@ def test_rollout_stage_parity(name):
 def test_rollout_collision_terms_active():
     """The paper-scale workload exercises every cost term (none identically zero)."""
     wl, p = VARIANTS["paper"]
-    orc, g, o = _rollout_pair(wl, p, seed=3)
+    state = W.make_state(13, 7)
+    state[0, 3], state[1, 3] = 2.2, 0.8  # joint 4 heading through its soft limit (2.24)
+    orc, g, o = _rollout_pair(wl, p, seed=3, state=state)
     for t, name in enumerate(W.TERM_NAMES):
         if name == "smooth":
             continue
