@@ -218,6 +218,49 @@ int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count,
 int storm_get_state(storm_handle* h, void* buf, size_t* len);
 int storm_set_state(storm_handle* h, const void* buf, size_t len);
 
+/* ---------------------------------------------------------------- without allocation */
+
+/* Size of the library's static device scratch used by the entry point below. */
+#define STORM_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* generate_rollouts for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this exists for code embedded in a host that owns the
+ * whole GPU memory budget -- a robot runtime or simulator that hands out fixed
+ * buffers at start-up and forbids cudaMalloc afterwards, because an allocation
+ * can synchronise the device and stall a hard-real-time control loop, or can
+ * fail under a fixed memory cap.  Such a caller cannot create a handle
+ * (storm_create allocates), so this call takes the model directly.
+ *
+ * It computes what storm_generate_rollouts computes for Ctot: the discounted
+ * total cost (Eq. 2) of each of the N rollouts sampled from mean_dev / sigma_dev
+ * for iteration `iter` of control step `step`.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine: the derived model tables and the
+ * N x H x dof control batch live in one file-scope static device array of
+ * STORM_NOALLOC_SCRATCH_BYTES (8 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ *
+ *   robot, world, params   host structs, as for storm_create (validated the same way)
+ *   state_dev (3 x dof), goal_dev (7), mean_dev (H x dof), sigma_dev (dof)
+ *                          device inputs, not modified
+ *   Ctot_dev (N)           device output
+ *   cuda_stream            cudaStream_t to enqueue on (NULL = legacy default stream)
+ *
+ * The first call on a device looks up the scratch array's device address with
+ * cudaGetSymbolAddress (with that device current) and raises the rollout
+ * kernel's shared-memory limit; make that first call before any stream capture.
+ * Every call copies the model tables from host memory into the scratch and
+ * rewrites every table the kernel reads, so no earlier contents are relied on.
+ * All calls share the one array: calls whose GPU work overlaps (other streams,
+ * other host threads) race on it and must be serialised by the caller.
+ * Errors: INVALID_ARG (as storm_create, NULL device pointer, bad iter, or a
+ * problem whose tables plus controls exceed the scratch: 4*N*H*dof bytes of
+ * controls plus about 40 KB of tables, e.g. N*H <= ~270,000 at dof 7), CUDA. */
+int storm_rollout_costs_noalloc(const storm_robot* robot, const storm_world* world,
+                                const storm_params* params, const float* state_dev,
+                                const float* goal_dev, const float* mean_dev,
+                                const float* sigma_dev, uint32_t step, int iter,
+                                float* Ctot_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

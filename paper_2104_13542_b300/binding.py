@@ -36,7 +36,7 @@ EXPORTED = [
     "storm_step", "storm_step_async", "storm_sync", "storm_device_io", "storm_shift",
     "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
     "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
-    "storm_set_state",
+    "storm_set_state", "storm_rollout_costs_noalloc",
 ]
 
 
@@ -358,3 +358,20 @@ class Controller:
     def set_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         self._check(lib().storm_set_state(self.h, buf, len(blob)))
+
+
+def rollout_costs_noalloc(robot, world, params, state_dev, goal_dev, mean_dev, sigma_dev,
+                          step: int, it: int, Ctot_dev, stream=None) -> int:
+    """storm_rollout_costs_noalloc: rollout totals with no device allocation in the
+    library (static scratch).  All tensors are caller-owned CUDA tensors."""
+    L = lib()
+    vp = C.c_void_p
+    L.storm_rollout_costs_noalloc.argtypes = [C.POINTER(storm_robot), C.POINTER(storm_world),
+                                              C.POINTER(storm_params), vp, vp, vp, vp,
+                                              C.c_uint32, C.c_int, vp, vp]
+    m = _Marshal()
+    r, w, p = m.robot(robot), m.world(world), m.params(params)
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    return L.storm_rollout_costs_noalloc(C.byref(r), C.byref(w), C.byref(p), _dptr(state_dev),
+                                         _dptr(goal_dev), _dptr(mean_dev), _dptr(sigma_dev),
+                                         int(step), int(it), _dptr(Ctot_dev), s)

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1466,3 +1467,203 @@ int storm_set_state(storm_handle* h, const void* buf, size_t len)
 }
 
 }  // extern "C"
+
+// ============================================================================ no allocation
+//
+// storm_rollout_costs_noalloc: the rollout kernel launched on tables and a
+// control batch that live in this file-scope static array instead of memory
+// from cudaMalloc.  Host code must not use the array's name as a device
+// address; the per-device address comes from cudaGetSymbolAddress.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[STORM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Once per device, with that device current: the scratch address and the
+// rollout kernel's shared-memory opt-in.
+int noalloc_setup(int dev, void** addr, std::string& msg)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            msg = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return STORM_ERR_CUDA;
+        }
+        int optin = 0;
+        cudaFuncAttributes ra;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&ra, k_rollout);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - static_cast<int>(ra.sharedSizeBytes));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            msg = std::string("rollout kernel attribute: ") + cudaGetErrorString(e);
+            return STORM_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *addr = g_noalloc_addr[dev];
+    return STORM_OK;
+}
+
+}  // namespace
+
+extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_world* w,
+                                           const storm_params* p, const float* state_dev,
+                                           const float* goal_dev, const float* mean_dev,
+                                           const float* sigma_dev, uint32_t step, int iter,
+                                           float* Ctot_dev, void* cuda_stream)
+{
+    std::string msg;
+    const int v = validate(r, w, p, msg);
+    if (v) return v;
+    if (!state_dev || !goal_dev || !mean_dev || !sigma_dev || !Ctot_dev) return STORM_ERR_INVALID_ARG;
+    if (iter < 0 || iter > 255 || step > 0x7fffffffu) return STORM_ERR_INVALID_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+    Problem pb{};
+    pb.N = p->N;
+    pb.H = p->H;
+    pb.d = r->dof;
+    pb.spline = p->n_knots > 0;
+    pb.S = pb.spline ? p->n_knots : p->H;
+    pb.sampler = p->sampler;
+    pb.n_null = p->n_null;
+    pb.rot_mode = p->rot_mode;
+    pb.M = r->n_spheres;
+    pb.P = r->n_pairs;
+    pb.B = w->n_boxes;
+    pb.O = w->n_spheres;
+    pb.beta = static_cast<float>(p->beta);
+    pb.w_pos = static_cast<float>(p->w_pos);
+    pb.w_rot = static_cast<float>(p->w_rot);
+    pb.w_stop = static_cast<float>(p->w_stop);
+    pb.w_joint = static_cast<float>(p->w_joint);
+    pb.w_manip = static_cast<float>(p->w_manip);
+    pb.w_coll = static_cast<float>(p->w_coll);
+    pb.w_smooth = static_cast<float>(p->w_smooth);
+    for (int i = 0; i < 3; ++i) {
+        pb.pos_w[i] = static_cast<float>(p->pos_axis_w[i]);
+        pb.rot_w[i] = static_cast<float>(p->rot_axis_w[i]);
+    }
+    pb.k_m = static_cast<float>(p->k_m);
+    pb.seed_lo = static_cast<uint32_t>(p->seed & 0xffffffffu);
+    pb.seed_hi = static_cast<uint32_t>(p->seed >> 32);
+    pb.instance = p->instance;
+    pb.ppc = std::max(1, std::min(pb.N, 64 / pb.H));
+    pb.mu = const_cast<float*>(mean_dev);  // read only by the rollout kernel
+    pb.sigma = const_cast<float*>(sigma_dev);
+
+    // host-side tables: spheres sorted by link, pairs remapped, raw doubles
+    std::vector<int> order(pb.M);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return r->sphere_link[a] < r->sphere_link[b]; });
+    std::vector<int> rank(pb.M);
+    for (int i = 0; i < pb.M; ++i) rank[order[i]] = i;
+    std::vector<float> sph(4 * std::max(pb.M, 1), 0.f);
+    std::vector<int> first(pb.d + 2, 0);
+    for (int i = 0; i < pb.M; ++i) {
+        for (int k = 0; k < 4; ++k) sph[4 * i + k] = static_cast<float>(r->spheres[4 * order[i] + k]);
+        first[r->sphere_link[order[i]] + 1]++;
+    }
+    for (int f = 0; f <= pb.d; ++f) first[f + 1] += first[f];
+    std::vector<uint32_t> pairs(std::max(pb.P, 1), 0u);
+    for (int k = 0; k < pb.P; ++k) {
+        uint32_t a = rank[r->pairs[2 * k]], b = rank[r->pairs[2 * k + 1]];
+        if (a > b) std::swap(a, b);
+        pairs[k] = a | (b << 16);
+    }
+    std::vector<float> boxes(6 * std::max(pb.B, 1), 0.f), ws(4 * std::max(pb.O, 1), 0.f);
+    for (int i = 0; i < 6 * pb.B; ++i) boxes[i] = static_cast<float>(w->boxes[i]);
+    for (int i = 0; i < 4 * pb.O; ++i) ws[i] = static_cast<float>(w->spheres[i]);
+    std::vector<double> raw;
+    raw.insert(raw.end(), r->dh, r->dh + 4 * pb.d);
+    raw.insert(raw.end(), r->q_min, r->q_min + pb.d);
+    raw.insert(raw.end(), r->q_max, r->q_max + pb.d);
+    raw.insert(raw.end(), p->dt, p->dt + pb.H);
+
+    // scratch plan: the model tables, then the N x H x d control batch
+    const TablePlan t = plan_tables(pb, std::max(pb.B, 1), std::max(pb.O, 1), static_cast<int>(raw.size()));
+    const size_t u_off = (t.total + 255) & ~size_t(255);
+    const size_t u_bytes = sizeof(float) * size_t(pb.N) * pb.H * pb.d;
+    if (u_off + u_bytes > STORM_NOALLOC_SCRATCH_BYTES) {
+        fprintf(stderr,
+                "storm_rollout_costs_noalloc: problem needs %zu bytes of scratch, more than the "
+                "%u-byte static scratch\n",
+                u_off + u_bytes, STORM_NOALLOC_SCRATCH_BYTES);
+        return STORM_ERR_INVALID_ARG;
+    }
+    const RolloutLayout L = rollout_layout(pb);
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        (void)cudaGetLastError();
+        return STORM_ERR_CUDA;
+    }
+    void* addr = nullptr;
+    int rc = noalloc_setup(dev, &addr, msg);
+    if (rc) {
+        fprintf(stderr, "storm_rollout_costs_noalloc: %s\n", msg.c_str());
+        return rc;
+    }
+    char* base = static_cast<char*>(addr);
+    pb.dhx = reinterpret_cast<float*>(base + t.dhx);
+    pb.qlo = reinterpret_cast<float*>(base + t.qlo);
+    pb.qhi = reinterpret_cast<float*>(base + t.qhi);
+    pb.sph = reinterpret_cast<float4*>(base + t.sph);
+    pb.link_first = reinterpret_cast<int*>(base + t.first);
+    pb.pairs = reinterpret_cast<uint32_t*>(base + t.pairs);
+    pb.boxes = reinterpret_cast<float*>(base + t.boxes);
+    pb.wsph = reinterpret_cast<float4*>(base + t.wsph);
+    pb.dt = reinterpret_cast<float*>(base + t.dt);
+    pb.gpow = reinterpret_cast<float*>(base + t.gpow);
+    pb.vmax = reinterpret_cast<float*>(base + t.vmax);
+    pb.basis = reinterpret_cast<float*>(base + t.basis);
+    pb.halton = reinterpret_cast<float*>(base + t.halton);
+    int* d_prime = reinterpret_cast<int*>(base + t.prime);
+    double* d_raw = reinterpret_cast<double*>(base + t.raw);
+    float* d_u = reinterpret_cast<float*>(base + u_off);
+
+    cudaError_t e = cudaSuccess;
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
+    };
+    put(const_cast<float4*>(pb.sph), sph.data(), 16 * sph.size() / 4);
+    put(const_cast<int*>(pb.link_first), first.data(), 4 * first.size());
+    put(const_cast<uint32_t*>(pb.pairs), pairs.data(), 4 * pairs.size());
+    put(const_cast<float*>(pb.boxes), boxes.data(), 4 * boxes.size());
+    put(const_cast<float4*>(pb.wsph), ws.data(), 4 * ws.size());
+    put(d_raw, raw.data(), 8 * raw.size());
+    if (e == cudaSuccess) {
+        InitArgs ia{d_raw, d_raw + 4 * pb.d, d_raw + 5 * pb.d, d_raw + 6 * pb.d, p->k_jl,
+                    p->qdd_max, p->gamma};
+        k_init_tables<<<1, 64, 0, stream>>>(pb, ia);
+        if (pb.sampler == STORM_SAMPLER_HALTON) {
+            const int D = pb.S * pb.d;
+            k_primes<<<(D + 127) / 128, 128, 0, stream>>>(D, d_prime);
+            const size_t total = size_t(pb.N) * pb.S * pb.d;
+            k_halton<<<static_cast<unsigned>((total + 255) / 256), 256, 0, stream>>>(
+                pb.N, pb.S, pb.d, d_prime, const_cast<float*>(pb.halton));
+        }
+        RolloutOut out{d_u, nullptr, nullptr, nullptr, nullptr, nullptr, Ctot_dev};
+        const int grid = (pb.N + pb.ppc - 1) / pb.ppc;
+        k_rollout<<<grid, kThreads, L.bytes, stream>>>(pb, out, state_dev, goal_dev, nullptr,
+                                                      static_cast<int>(step), iter);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        fprintf(stderr, "storm_rollout_costs_noalloc: %s\n", cudaGetErrorString(e));
+        return STORM_ERR_CUDA;
+    }
+    return STORM_OK;
+}
