@@ -209,6 +209,24 @@ int storm_set_world(storm_handle* h, const storm_world* world);
  * -> ee_dev (count x 12, row-major [R | p]).  Enqueued (no wait). */
 int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count, float* ee_dev);
 
+/* ---------------------------------------------------------------- launch shape */
+
+/* Rollout launch shape: particles per CTA (1..N) and threads per CTA (a
+ * multiple of 32 in 64..512).  Re-captures the step graph.  Errors:
+ * INVALID_ARG when out of range or when the shape's shared-memory plan does not
+ * fit a CTA. */
+int storm_set_launch(storm_handle* h, int particles_per_cta, int threads_per_cta);
+int storm_get_launch(const storm_handle* h, int* particles_per_cta, int* threads_per_cta);
+
+/* Autotuner: times this handle's rollout kernel (sample_controls +
+ * generate_rollouts) with CUDA events on its stream for every candidate shape
+ * -- particles per CTA 1, 2, 3, 4, 6, 8, 12, 16 (at most N and 512/H) x
+ * threads 128, 256, 512 -- on the state and goal of the handle's input
+ * buffers (call it after a first step), keeps the fastest and re-captures
+ * the step graph.  best_us (nullable) receives the median time of the chosen
+ * shape.  Waits. */
+int storm_autotune(storm_handle* h, float* best_us);
+
 /* ---------------------------------------------------------------- checkpoint */
 
 /* Serialise mu, sigma and the step counter (the Philox key is fixed by the

@@ -36,7 +36,8 @@ EXPORTED = [
     "storm_step", "storm_step_async", "storm_sync", "storm_device_io", "storm_shift",
     "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
     "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
-    "storm_set_state", "storm_rollout_costs_noalloc",
+    "storm_set_state", "storm_rollout_costs_noalloc", "storm_set_launch", "storm_get_launch",
+    "storm_autotune",
 ]
 
 
@@ -121,6 +122,9 @@ def lib():
         L.storm_forward_kinematics.argtypes = [vp, vp, C.c_int, vp]
         L.storm_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.storm_set_state.argtypes = [vp, vp, C.c_size_t]
+        L.storm_set_launch.argtypes = [vp, C.c_int, C.c_int]
+        L.storm_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.storm_autotune.argtypes = [vp, C.POINTER(C.c_float)]
         _lib = L
     return _lib
 
@@ -347,6 +351,19 @@ class Controller:
         self._check(lib().storm_forward_kinematics(self.h, _dptr(theta_dev), int(n), _dptr(ee)))
         self.stream.synchronize()
         return ee
+
+    def set_launch(self, particles_per_cta: int, threads: int):
+        self._check(lib().storm_set_launch(self.h, int(particles_per_cta), int(threads)))
+
+    def get_launch(self):
+        a, b = C.c_int(), C.c_int()
+        self._check(lib().storm_get_launch(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def autotune(self) -> float:
+        t = C.c_float()
+        self._check(lib().storm_autotune(self.h, C.byref(t)))
+        return t.value
 
     def get_state(self) -> bytes:
         n = C.c_size_t(0)

@@ -12,7 +12,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <set>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,10 +28,10 @@ using namespace storm;
 // ============================================================================ layout
 
 struct RolloutLayout {
-    int cent, sph, wsph;                                    // float4 arrays
+    int frame, cent, sph, wsph, boxlh, pblk;                // 16-byte arrays
     int mu, sigma, eps, u, th, thd, basis, dt, gpow, vmax;  // float arrays
     int dhx, qlo, qhi, boxes, part, dself, dworld, goal, state;
-    int first, pairs;                                       // int arrays
+    int first, slink, pairs;                                // int arrays
     int bytes;
 };
 
@@ -46,9 +48,12 @@ __host__ __device__ inline RolloutLayout rollout_layout(const Problem& pb)
     RolloutLayout L;
     int off = 0;
     const int I = pb.ppc * pb.H;
+    L.frame = take_(off, I * (pb.d + 1) * 3 * 16);
     L.cent = take_(off, I * pb.M * 16);
     L.sph = take_(off, pb.M * 16);
     L.wsph = take_(off, pb.O * 16);
+    L.boxlh = take_(off, pb.B * 2 * 16);
+    L.pblk = take_(off, pb.NPB * 16);
     L.mu = take_(off, pb.H * pb.d * 4);
     L.sigma = take_(off, pb.d * 4);
     L.eps = take_(off, pb.ppc * pb.S * pb.d * 4);
@@ -69,6 +74,7 @@ __host__ __device__ inline RolloutLayout rollout_layout(const Problem& pb)
     L.goal = take_(off, 12 * 4);
     L.state = take_(off, 3 * pb.d * 4);
     L.first = take_(off, (pb.d + 2) * 4);
+    L.slink = take_(off, pb.M * 4);
     L.pairs = take_(off, pb.P * 4);
     L.bytes = off;
     return L;
@@ -86,21 +92,25 @@ struct RolloutOut {
 
 // ============================================================================ kernels
 
-// sample_controls + generate_rollouts for `ppc` particles per CTA.
+// sample_controls + generate_rollouts of particles [n0, n0 + np) in one CTA.
 // Phases: stage tables -> noise -> smoothed controls -> per-(particle, joint)
-// integration scan (Eq. 7) -> per-(particle, step) FK, Jacobian and cost terms
-// (Eqs. 8-12, 15) -> link-sphere collision over (step, sphere) and
-// (pair, step) (Eqs. 13-14) -> discounted totals (Eq. 2).
-__global__ void __launch_bounds__(kThreads, 2)
-k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
-          const float* __restrict__ goal, const StepState* __restrict__ st, int step_override,
-          int iter)
+// integration scan (Eq. 7) -> per-(particle, step) FK, Jacobian and
+// non-collision cost terms (Eqs. 8-12), link frames to shared memory ->
+// per-(step, sphere) sphere centre and world collision (Eq. 14 reading) ->
+// per-(pair, step) self collision (Eq. 13 reading) -> running cost (Eq. 15)
+// and discounted totals (Eq. 2).
+__device__ __forceinline__ void rollout_particles(const Problem& pb, const RolloutOut& out,
+                                                  const float* __restrict__ state,
+                                                  const float* __restrict__ goal, uint32_t step,
+                                                  int iter, int n0, int np, unsigned char* smem)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     const RolloutLayout L = rollout_layout(pb);
+    float4* s_frame = reinterpret_cast<float4*>(smem + L.frame);
     float4* s_cent = reinterpret_cast<float4*>(smem + L.cent);
     float4* s_sph = reinterpret_cast<float4*>(smem + L.sph);
     float4* s_wsph = reinterpret_cast<float4*>(smem + L.wsph);
+    float4* s_boxlh = reinterpret_cast<float4*>(smem + L.boxlh);
+    uint4* s_pblk = reinterpret_cast<uint4*>(smem + L.pblk);
     float* s_mu = reinterpret_cast<float*>(smem + L.mu);
     float* s_sigma = reinterpret_cast<float*>(smem + L.sigma);
     float* s_eps = reinterpret_cast<float*>(smem + L.eps);
@@ -121,16 +131,13 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
     float* s_goal = reinterpret_cast<float*>(smem + L.goal);
     float* s_state = reinterpret_cast<float*>(smem + L.state);
     int* s_first = reinterpret_cast<int*>(smem + L.first);
+    int* s_slink = reinterpret_cast<int*>(smem + L.slink);
     uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.pairs);
 
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int d = pb.d, H = pb.H, S = pb.S, M = pb.M;
-    const int n0 = blockIdx.x * pb.ppc;
-    const int np = min(pb.ppc, pb.N - n0);
-    if (np <= 0) return;
+    const int d = pb.d, H = pb.H, S = pb.S, M = pb.M, F = pb.d + 1;
     const int I = np * H;
     const int HD = H * d;
-    const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
 
     // ---- stage per-problem tables
     for (int i = tid; i < HD; i += nt) s_mu[i] = pb.mu[i];
@@ -148,10 +155,25 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
     if (pb.spline)
         for (int i = tid; i < H * S; i += nt) s_basis[i] = pb.basis[i];
     for (int i = tid; i < d * 8; i += nt) s_dhx[i] = pb.dhx[i];
-    for (int i = tid; i < M; i += nt) s_sph[i] = pb.sph[i];
     for (int i = tid; i < d + 2; i += nt) s_first[i] = pb.link_first[i];
+    for (int i = tid; i < M; i += nt) {
+        s_sph[i] = pb.sph[i];
+        int f = 0;
+        while (f < d && i >= pb.link_first[f + 1]) ++f;
+        s_slink[i] = f;
+    }
     for (int i = tid; i < pb.P; i += nt) s_pairs[i] = pb.pairs[i];
-    for (int i = tid; i < pb.B * 6; i += nt) s_boxes[i] = pb.boxes[i];
+    for (int i = tid; i < pb.NPB; i += nt) s_pblk[i] = pb.pblk[i];
+    for (int i = tid; i < pb.B; i += nt) {
+        float b[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            b[k] = pb.boxes[i * 6 + k];
+            s_boxes[i * 6 + k] = b[k];
+        }
+        s_boxlh[2 * i] = make_float4(b[0] - b[3], b[1] - b[4], b[2] - b[5], 0.f);
+        s_boxlh[2 * i + 1] = make_float4(b[0] + b[3], b[1] + b[4], b[2] + b[5], 0.f);
+    }
     for (int i = tid; i < pb.O; i += nt) s_wsph[i] = pb.wsph[i];
     if (tid == 0) {
         // goal rotation R_g (row-major) from the normalised quaternion, then p_g
@@ -230,56 +252,40 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
         for (int i = tid; i < np * HD; i += nt)
             out.theta_dot[static_cast<size_t>(n0) * HD + i] = s_thd[i];
 
-    // ---- per (particle, step): FK, sphere centres, Jacobian, non-collision costs
-    if (tid < I) {
-        const int p = tid / H, h = tid - p * H;
+    // ---- per (particle, step): FK frames, Jacobian, non-collision costs
+    for (int item = tid; item < I; item += nt) {
+        const int p = item / H, h = item - p * H;
         const float* th = s_th + (p * H + h) * d;
         const float* thd = s_thd + (p * H + h) * d;
         const float* uh = s_u + (p * H + h) * d;
         const float* up = (h == 0) ? s_state + 2 * d : uh - d;
-        float4* cent = s_cent + tid * M;
+        float4* fr = s_frame + item * F * 3;
 
         float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
         float pp[3] = {0.f, 0.f, 0.f};
-        float z[kMaxDof][3], o[kMaxDof][3];
-        for (int s = s_first[0]; s < s_first[1]; ++s) cent[s] = s_sph[s];
+        const bool want_manip = pb.w_manip != 0.f || out.terms;
+        GramFactor G;
+        G.zero();
+        fr[0] = make_float4(1.f, 0.f, 0.f, 0.f);
+        fr[1] = make_float4(0.f, 1.f, 0.f, 0.f);
+        fr[2] = make_float4(0.f, 0.f, 1.f, 0.f);
 #pragma unroll
         for (int i = 0; i < kMaxDof; ++i) {
             if (i < d) {
                 const float* dh = s_dhx + i * 8;
                 dh_step(R, pp, dh[0], dh[1], dh[2], dh[3], th[i] + dh[4]);
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    z[i][r] = R[r * 3 + 2];
-                    o[i][r] = pp[r];
+                for (int r = 0; r < 3; ++r)
+                    fr[(i + 1) * 3 + r] = make_float4(R[r * 3 + 0], R[r * 3 + 1], R[r * 3 + 2], pp[r]);
+                if (want_manip) {
+                    // geometric Jacobian column (Eq. 8) about the base origin,
+                    // [o_i x z_i; z_i]: det(J J^T) does not depend on the
+                    // reference point (J(p) = [[I, -[p]x], [0, I]] J(0))
+                    const float zx = R[2], zy = R[5], zz = R[8];
+                    float x[6] = {pp[1] * zz - pp[2] * zy, pp[2] * zx - pp[0] * zz,
+                                  pp[0] * zy - pp[1] * zx, zx, zy, zz};
+                    G.add(x);
                 }
-                for (int s = s_first[i + 1]; s < s_first[i + 2]; ++s) {
-                    const float4 q = s_sph[s];
-                    float4 c;
-                    c.x = fmaf(R[0], q.x, fmaf(R[1], q.y, fmaf(R[2], q.z, pp[0])));
-                    c.y = fmaf(R[3], q.x, fmaf(R[4], q.y, fmaf(R[5], q.z, pp[1])));
-                    c.z = fmaf(R[6], q.x, fmaf(R[7], q.y, fmaf(R[8], q.z, pp[2])));
-                    c.w = q.w;
-                    cent[s] = c;
-                }
-            }
-        }
-
-        // geometric Jacobian rows (Eq. 8): [z_i x (p - o_i); z_i]
-        float J[6][kMaxDof];
-#pragma unroll
-        for (int i = 0; i < kMaxDof; ++i) {
-            if (i < d) {
-                const float rx = pp[0] - o[i][0], ry = pp[1] - o[i][1], rz = pp[2] - o[i][2];
-                J[0][i] = z[i][1] * rz - z[i][2] * ry;
-                J[1][i] = z[i][2] * rx - z[i][0] * rz;
-                J[2][i] = z[i][0] * ry - z[i][1] * rx;
-                J[3][i] = z[i][0];
-                J[4][i] = z[i][1];
-                J[5][i] = z[i][2];
-            } else {
-#pragma unroll
-                for (int r = 0; r < 6; ++r) J[r][i] = 0.f;
             }
         }
 
@@ -327,15 +333,15 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
         c_joint = sqrtf(c_joint);
         // manipulability (Eq. 12)
         float c_manip = 0.f;
-        if (pb.w_manip != 0.f || out.terms) {
-            const float m = manipulability_mgs(J, d);
+        if (want_manip) {
+            const float m = G.sqrt_det();
             c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
         }
-        s_part[tid] = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop +
-                      pb.w_joint * c_joint + pb.w_manip * c_manip + pb.w_smooth * c_smooth;
-        s_dself[tid] = 0.f;
-        s_dworld[tid] = 0.f;
-        const size_t g = static_cast<size_t>(n0) * H + tid;
+        s_part[item] = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop +
+                       pb.w_joint * c_joint + pb.w_manip * c_manip + pb.w_smooth * c_smooth;
+        s_dself[item] = 0.f;
+        s_dworld[item] = 0.f;
+        const size_t g = static_cast<size_t>(n0) * H + item;
         if (out.ee) {
             float* e = out.ee + g * 12;
 #pragma unroll
@@ -358,36 +364,71 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
     }
     __syncthreads();
 
-    // ---- world collision over (step, sphere): penetration depth, Eq. 14 reading
-    if (pb.B + pb.O > 0) {
-        for (int idx = tid; idx < I * M; idx += nt) {
-            const int item = idx / M;
-            const float4 c = s_cent[idx];
-            const float r2 = c.w * c.w;
-            float depth = 0.f;
-            for (int b = 0; b < pb.B; ++b) {
+    // ---- sphere centres and world collision over (step, sphere), Eq. 14 reading:
+    // clamp test d(c, box)^2 < r^2 first, exact signed distance only on contact
+    for (int idx = tid; idx < I * M; idx += nt) {
+        const int item = idx / M, s = idx - item * M;
+        const float4 q = s_sph[s];
+        const float4* T = s_frame + (item * F + s_slink[s]) * 3;
+        const float4 r0 = T[0], r1 = T[1], r2 = T[2];
+        float4 c;
+        c.x = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
+        c.y = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
+        c.z = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
+        c.w = q.w;
+        s_cent[idx] = c;
+        const float r2s = c.w * c.w;
+        float depth = 0.f;
+        for (int b = 0; b < pb.B; ++b) {
+            const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
+            const float ex = c.x - fminf(fmaxf(c.x, lo.x), hi.x);
+            const float ey = c.y - fminf(fmaxf(c.y, lo.y), hi.y);
+            const float ez = c.z - fminf(fmaxf(c.z, lo.z), hi.z);
+            const float out2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (out2 < r2s) {
                 const float* bx = s_boxes + b * 6;
                 const float qx = fabsf(c.x - bx[0]) - bx[3];
                 const float qy = fabsf(c.y - bx[1]) - bx[4];
                 const float qz = fabsf(c.z - bx[2]) - bx[5];
                 const float ox = fmaxf(qx, 0.f), oy = fmaxf(qy, 0.f), oz = fmaxf(qz, 0.f);
-                const float out2 = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
-                if (out2 < r2) {
-                    const float sd = sqrtf(out2) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f) - c.w;
-                    depth = fmaxf(depth, -sd);
-                }
+                const float sd = sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) +
+                                 fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f) - c.w;
+                depth = fmaxf(depth, -sd);
             }
-            for (int k = 0; k < pb.O; ++k) {
-                const float4 w = s_wsph[k];
-                const float ex = c.x - w.x, ey = c.y - w.y, ez = c.z - w.z;
+        }
+        for (int k = 0; k < pb.O; ++k) {
+            const float4 w = s_wsph[k];
+            const float ex = c.x - w.x, ey = c.y - w.y, ez = c.z - w.z;
+            const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            const float rs = c.w + w.w;
+            if (dist2 < rs * rs) depth = fmaxf(depth, rs - sqrtf(dist2));
+        }
+        if (depth > 0.f) atomicMax(reinterpret_cast<int*>(s_dworld + item), __float_as_int(depth));
+    }
+    __syncthreads();
+    // ---- self collision, Eq. 13 reading.  Pair blocks (every sphere of one
+    // link against up to 8 spheres of another) keep the 8 centres in registers
+    // while streaming the first link's spheres; leftover pairs one by one.
+    for (int idx = tid; idx < I * pb.NPB; idx += nt) {
+        const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
+        const uint4 blk = s_pblk[bk];  // a0, a1, b0, nb
+        const float4* ci = s_cent + item * M;
+        float4 cb[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cb[k] = k < static_cast<int>(blk.w) ? ci[blk.z + k] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+        float depth = 0.f;
+        for (uint32_t a = blk.x; a < blk.y; ++a) {
+            const float4 ca = ci[a];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float ex = ca.x - cb[k].x, ey = ca.y - cb[k].y, ez = ca.z - cb[k].z;
                 const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                const float rs = c.w + w.w;
+                const float rs = ca.w + cb[k].w;
                 if (dist2 < rs * rs) depth = fmaxf(depth, rs - sqrtf(dist2));
             }
-            if (depth > 0.f) atomicMax(reinterpret_cast<int*>(s_dworld + item), __float_as_int(depth));
         }
+        if (depth > 0.f) atomicMax(reinterpret_cast<int*>(s_dself + item), __float_as_int(depth));
     }
-    // ---- self collision over (pair, step), Eq. 13 reading
     for (int k = tid; k < pb.P; k += nt) {
         const uint32_t pr = s_pairs[k];
         const int a = pr & 0xffff, b = pr >> 16;
@@ -405,23 +446,36 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
     __syncthreads();
 
     // ---- running cost (Eq. 15)
-    if (tid < I) {
-        const float c = s_part[tid] + pb.w_coll * (s_dself[tid] + s_dworld[tid]);
-        s_part[tid] = c;
-        const size_t g = static_cast<size_t>(n0) * H + tid;
+    for (int item = tid; item < I; item += nt) {
+        const float c = s_part[item] + pb.w_coll * (s_dself[item] + s_dworld[item]);
+        s_part[item] = c;
+        const size_t g = static_cast<size_t>(n0) * H + item;
         if (out.cost) out.cost[g] = c;
         if (out.terms) {
-            out.terms[g * STORM_NTERMS + 5] = s_dself[tid];
-            out.terms[g * STORM_NTERMS + 6] = s_dworld[tid];
+            out.terms[g * STORM_NTERMS + 5] = s_dself[item];
+            out.terms[g * STORM_NTERMS + 6] = s_dworld[item];
         }
     }
     __syncthreads();
     // ---- discounted total (Eq. 2)
-    if (tid < np) {
+    for (int p = tid; p < np; p += nt) {
         float C = 0.f;
-        for (int h = 0; h < H; ++h) C = fmaf(s_gpow[h], s_part[tid * H + h], C);
-        out.Ctot[n0 + tid] = C;
+        for (int h = 0; h < H; ++h) C = fmaf(s_gpow[h], s_part[p * H + h], C);
+        out.Ctot[n0 + p] = C;
     }
+}
+
+__global__ void __launch_bounds__(kMaxThreads)
+k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
+          const float* __restrict__ goal, const StepState* __restrict__ st, int step_override,
+          int iter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n0 = blockIdx.x * pb.ppc;
+    const int np = min(pb.ppc, pb.N - n0);
+    if (np <= 0) return;
+    const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
+    rollout_particles(pb, out, state, goal, step, iter, n0, np, smem);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -449,22 +503,74 @@ __device__ float block_sum(float v, float* sh)
     return sh[0];
 }
 
-// update_distribution (Eqs. 4-6) in one CTA: min-shifted exponential weights,
-// weighted mean, weighted per-joint variance about the new mean.  `finalize`
-// marks the last iteration of a control step: it writes next_command and
-// advances the step counter.
+// Scratch of the multi-CTA distribution update (device, owned by the handle).
+struct UpdateScratch {
+    unsigned int count;  // CTAs finished in the current launch (reset by the last one)
+    unsigned int pad[63];
+    float var[1];        // H x d weighted squared deviations (Eq. 5), grown to H*d
+};
+
+// Block-wide (min value, lowest index) over all threads; result in every thread.
+__device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov < bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        shf[wid] = bv;
+        shi[wid] = bi;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        bv = lane < nw ? shf[lane] : INFINITY;
+        bi = lane < nw ? shi[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            shf[0] = bv;
+            shi[0] = bi;
+        }
+    }
+    __syncthreads();
+    bv = shf[0];
+    bi = shi[0];
+}
+
+// update_distribution (Eqs. 4-6), one CTA per horizon step h.  Every CTA
+// forms the min-shifted exponential weights of all N particles (Eq. 6) in
+// shared memory, then the weighted mean of row h (Eq. 4) and row h's weighted
+// squared deviations about the new mean.  The last CTA to finish sums those
+// over h in fixed order into the per-joint sigma (Eq. 5) and, at the last
+// iteration of a step, writes next_command and advances the step counter.
+// All reductions run in a fixed order: results are bitwise reproducible.
 __global__ void __launch_bounds__(kUpdateThreads)
 k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
-         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out, int finalize)
+         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out,
+         int finalize, UpdateScratch* scr)
 {
-    extern __shared__ __align__(16) float s_dyn[];
+    extern __shared__ __align__(16) float s_w[];  // N weights
     __shared__ float s_redf[32];
     __shared__ int s_redi[32];
-    const int N = pb.N, d = pb.d, O = pb.H * pb.d;
-    const int tid = threadIdx.x, T = blockDim.x;
-    float* s_w = s_dyn;
-    float* s_part = s_w + ((N + 3) & ~3);
-    float* s_mu = s_part + T;
+    __shared__ float s_acc[kMaxDof][33];
+    __shared__ float s_mu[kMaxDof];
+    __shared__ int s_last;
+    const int N = pb.N, d = pb.d, O = pb.H * pb.d, h = blockIdx.x;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
 
     // ---- min finite cost and its lowest index
     float bv = INFINITY;
@@ -476,44 +582,99 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
             bi = n;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov < bv || (ov == bv && oi < bi)) {
-            bv = ov;
-            bi = oi;
+    block_argmin(bv, bi, s_redf, s_redi);
+    const float m = bv;
+    const int arg = bi;
+    const bool degenerate = (arg == INT_MAX);
+
+    float s = 1.f, sc = 0.f;
+    if (!degenerate) {
+        // ---- weights, Eq. 6
+        float ls = 0.f, lsc = 0.f;
+        for (int n = tid; n < N; n += T) {
+            const float c = C[n];
+            float w;
+            if (!isfinite(c))
+                w = 0.f;
+            else if (pb.beta > 0.f)
+                w = expf(-(c - m) / pb.beta);
+            else
+                w = (n == arg) ? 1.f : 0.f;
+            s_w[n] = w;
+            ls += w;
+            if (w > 0.f) lsc = fmaf(w, c, lsc);
         }
-    }
-    const int lane = tid & 31, wid = tid >> 5, nw = (T + 31) >> 5;
-    if (lane == 0) {
-        s_redf[wid] = bv;
-        s_redi[wid] = bi;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        bv = lane < nw ? s_redf[lane] : INFINITY;
-        bi = lane < nw ? s_redi[lane] : INT_MAX;
+        s = block_sum(ls, s_redf);
+        sc = block_sum(lsc, s_redf);
+        const float inv_s = 1.f / s;
+        if (weights_out && h == 0)
+            for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * inv_s;
+
+        // ---- weighted mean of row h, Eq. 4
+        float acc[kMaxDof];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov < bv || (ov == bv && oi < bi)) {
-                bv = ov;
-                bi = oi;
+        for (int j = 0; j < kMaxDof; ++j) acc[j] = 0.f;
+        for (int n = tid; n < N; n += T) {
+            const float w = s_w[n];
+            const float* un = u + static_cast<size_t>(n) * O + h * d;
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j)
+                if (j < d) acc[j] = fmaf(w, un[j], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) {
+            if (j < d) {
+                const float v = warp_sum(acc[j]);
+                if (lane == 0) s_acc[j][wid] = v;
             }
         }
-        if (lane == 0) {
-            s_redf[0] = bv;
-            s_redi[0] = bi;
+        __syncthreads();
+        if (tid < d) {
+            float a = 0.f;
+            for (int k = 0; k < (T >> 5); ++k) a += s_acc[tid][k];
+            const float mnew = (1.f - pb.alpha_mu) * pb.mu[h * d + tid] + pb.alpha_mu * (a * inv_s);
+            s_mu[tid] = mnew;
+            pb.mu[h * d + tid] = mnew;  // row h belongs to this CTA alone
+        }
+        __syncthreads();
+
+        // ---- weighted squared deviation of row h about the new mean, Eq. 5
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) acc[j] = 0.f;
+        for (int n = tid; n < N; n += T) {
+            const float w = s_w[n];
+            const float* un = u + static_cast<size_t>(n) * O + h * d;
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j)
+                if (j < d) {
+                    const float e = un[j] - s_mu[j];
+                    acc[j] = fmaf(w * e, e, acc[j]);
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) {
+            if (j < d) {
+                const float v = warp_sum(acc[j]);
+                if (lane == 0) s_acc[j][wid] = v;
+            }
+        }
+        __syncthreads();
+        if (tid < d) {
+            float a = 0.f;
+            for (int k = 0; k < (T >> 5); ++k) a += s_acc[tid][k];
+            scr->var[h * d + tid] = a;
         }
     }
-    __syncthreads();
-    const float m = s_redf[0];
-    const int arg = s_redi[0];
-    __syncthreads();
 
-    if (arg == INT_MAX) {  // no finite cost: keep the distribution
+    // ---- the last CTA to finish combines the rows
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&scr->count, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (degenerate) {
         if (tid == 0) {
             st->status |= STORM_WARN_DEGENERATE;
             st->best = INFINITY;
@@ -521,85 +682,27 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
         }
         if (weights_out)
             for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
-        if (finalize) {
-            if (tid < d) cmd_out[tid] = pb.mu[tid];
-            if (tid == 0) st->step += 1;
+    } else {
+        if (tid < d) {
+            const int j = tid;
+            float v = 0.f;
+            for (int hh = 0; hh < pb.H; ++hh) v += __ldcg(scr->var + hh * d + j);
+            v = v / s / static_cast<float>(pb.H);
+            const float sg = pb.sigma[j];
+            float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
+            var = fmaxf(var, pb.sigma_min * pb.sigma_min);
+            pb.sigma[j] = sqrtf(var);
         }
-        return;
-    }
-
-    // ---- weights w_n = exp(-(C_n - m) / beta), Eq. 6
-    float ls = 0.f, lsc = 0.f;
-    for (int n = tid; n < N; n += T) {
-        const float c = C[n];
-        float w;
-        if (!isfinite(c))
-            w = 0.f;
-        else if (pb.beta > 0.f)
-            w = expf(-(c - m) / pb.beta);
-        else
-            w = (n == arg) ? 1.f : 0.f;
-        s_w[n] = w;
-        ls += w;
-        if (w > 0.f) lsc = fmaf(w, c, lsc);
-    }
-    const float s = block_sum(ls, s_redf);
-    const float sc = block_sum(lsc, s_redf);
-    const float inv_s = 1.f / s;
-    if (weights_out)
-        for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * inv_s;
-
-    // ---- weighted mean, Eq. 4
-    const int nsl = max(1, T / O);
-    if (tid < nsl * O) {
-        const int o = tid % O, sl = tid / O;
-        float acc = 0.f;
-        for (int n = sl; n < N; n += nsl) acc = fmaf(s_w[n], u[static_cast<size_t>(n) * O + o], acc);
-        s_part[sl * O + o] = acc;
-    }
-    __syncthreads();
-    for (int o = tid; o < O; o += T) {
-        float acc = 0.f;
-        for (int sl = 0; sl < nsl; ++sl) acc += s_part[sl * O + o];
-        s_mu[o] = (1.f - pb.alpha_mu) * pb.mu[o] + pb.alpha_mu * (acc * inv_s);
-    }
-    __syncthreads();
-
-    // ---- weighted variance about the new mean, per joint, Eq. 5
-    if (tid < nsl * O) {
-        const int o = tid % O, sl = tid / O;
-        const float mo = s_mu[o];
-        float acc = 0.f;
-        for (int n = sl; n < N; n += nsl) {
-            const float e = u[static_cast<size_t>(n) * O + o] - mo;
-            acc = fmaf(s_w[n] * e, e, acc);
+        if (tid == 0) {
+            st->best = m;
+            st->wmean = sc / s;
         }
-        s_part[sl * O + o] = acc;
-    }
-    __syncthreads();
-    if (tid < d) {
-        const int j = tid;
-        float v = 0.f;
-        for (int h = 0; h < pb.H; ++h) {
-            float a = 0.f;
-            for (int sl = 0; sl < nsl; ++sl) a += s_part[sl * O + h * d + j];
-            v += a;
-        }
-        v = v * inv_s / static_cast<float>(pb.H);
-        const float sg = pb.sigma[j];
-        float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
-        var = fmaxf(var, pb.sigma_min * pb.sigma_min);
-        pb.sigma[j] = sqrtf(var);
-    }
-    for (int o = tid; o < O; o += T) pb.mu[o] = s_mu[o];
-    if (tid == 0) {
-        st->best = m;
-        st->wmean = sc * inv_s;
     }
     if (finalize) {
-        if (tid < d) cmd_out[tid] = s_mu[tid];
+        if (tid < d) cmd_out[tid] = __ldcg(pb.mu + tid);
         if (tid == 0) st->step += 1;
     }
+    if (tid == 0) scr->count = 0;
 }
 
 // Raw noise of sample_controls: one thread per Philox block (4 values).
@@ -790,12 +893,14 @@ struct storm_handle {
     int n_spheres_in = 0;
     size_t rollout_smem = 0, update_smem = 0;
     int grid = 0;
+    int threads = kThreads;  // rollout CTA size
     // device allocations
     void* d_tables = nullptr;  // one block for every table
     float* d_u = nullptr;
     float* d_C = nullptr;
     float* d_io = nullptr;     // state 3d | goal 7 | cmd d | StepState
     StepState* d_st = nullptr;
+    UpdateScratch* d_upd = nullptr;  // multi-CTA update: counter + H x d partials
     float* h_io = nullptr;     // pinned mirror of d_io
     cudaGraphExec_t g_dev = nullptr, g_host = nullptr;
     std::string err = "no error";
@@ -885,7 +990,7 @@ int validate(const storm_robot* r, const storm_world* w, const storm_params* p, 
 
 // Tables live in one device block; offsets in bytes, 256-aligned.
 struct TablePlan {
-    size_t dhx, qlo, qhi, sph, first, pairs, boxes, wsph, dt, gpow, vmax, basis, halton, mu,
+    size_t dhx, qlo, qhi, sph, first, pairs, pblk, boxes, wsph, dt, gpow, vmax, basis, halton, mu,
         sigma, prime, raw, total;
 };
 
@@ -904,6 +1009,7 @@ TablePlan plan_tables(const Problem& pb, int cap_boxes, int cap_wsph, int raw_do
     t.sph = take(std::max(pb.M, 1) * 16);
     t.first = take((pb.d + 2) * 4);
     t.pairs = take(std::max(pb.P, 1) * 4);
+    t.pblk = take(std::max(pb.NPB, 1) * 16);
     t.boxes = take(std::max(cap_boxes, 1) * 6 * 4);
     t.wsph = take(std::max(cap_wsph, 1) * 16);
     t.dt = take(pb.H * 4);
@@ -939,7 +1045,7 @@ int upload_world(storm_handle* h, const storm_world* w)
 int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const float* state,
                    const float* goal, int step_override, int iter)
 {
-    k_rollout<<<h->grid, kThreads, h->rollout_smem, s>>>(h->pb, out, state, goal, h->d_st,
+    k_rollout<<<h->grid, h->threads, h->rollout_smem, s>>>(h->pb, out, state, goal, h->d_st,
                                                          step_override, iter);
     CK(cudaGetLastError());
     return STORM_OK;
@@ -948,7 +1054,8 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
 int launch_update(storm_handle* h, cudaStream_t s, const float* C, const float* u, float* w,
                   float* cmd, int finalize)
 {
-    k_update<<<1, kUpdateThreads, h->update_smem, s>>>(h->pb, C, u, w, h->d_st, cmd, finalize);
+    k_update<<<h->pb.H, kUpdateThreads, h->update_smem, s>>>(h->pb, C, u, w, h->d_st, cmd, finalize,
+                                                              h->d_upd);
     CK(cudaGetLastError());
     return STORM_OK;
 }
@@ -1045,9 +1152,39 @@ void free_all(storm_handle* h)
     if (h->d_u) cudaFree(h->d_u);
     if (h->d_C) cudaFree(h->d_C);
     if (h->d_io) cudaFree(h->d_io);
+    if (h->d_upd) cudaFree(h->d_upd);
     if (h->h_io) cudaFreeHost(h->h_io);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+// Group self-collision pairs (sorted sphere indices, a < b) by the links of
+// their spheres.  A group that is exactly every sphere of one link against
+// every sphere of another becomes blocks of at most 8 second-link spheres;
+// anything else stays an explicit pair.
+void build_pair_blocks(const std::vector<uint32_t>& pairs, const std::vector<int>& first, int d,
+                       std::vector<uint4>& blocks, std::vector<uint32_t>& rest)
+{
+    auto link_of = [&](int s) {
+        int f = 0;
+        while (f < d && s >= first[f + 1]) ++f;
+        return f;
+    };
+    std::map<std::pair<int, int>, std::vector<uint32_t>> groups;
+    for (uint32_t pr : pairs) groups[{link_of(pr & 0xffff), link_of(pr >> 16)}].push_back(pr);
+    for (auto& g : groups) {
+        const int la = g.first.first, lb = g.first.second;
+        const int na = first[la + 1] - first[la], nb = first[lb + 1] - first[lb];
+        const std::set<uint32_t> uniq(g.second.begin(), g.second.end());
+        const bool complete = la != lb && uniq.size() == g.second.size() &&
+                              static_cast<int>(uniq.size()) == na * nb;
+        if (complete) {
+            for (int b0 = first[lb]; b0 < first[lb + 1]; b0 += 8)
+                blocks.push_back(make_uint4(first[la], first[la + 1], b0, std::min(8, first[lb + 1] - b0)));
+        } else {
+            rest.insert(rest.end(), g.second.begin(), g.second.end());
+        }
+    }
 }
 
 int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, const storm_params* p,
@@ -1117,12 +1254,19 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
         first[r->sphere_link[order[i]] + 1]++;
     }
     for (int f = 0; f <= pb.d; ++f) first[f + 1] += first[f];
-    std::vector<uint32_t> pairs(std::max(pb.P, 1));
+    std::vector<uint32_t> all_pairs(pb.P);
     for (int k = 0; k < pb.P; ++k) {
         uint32_t a = rank[r->pairs[2 * k]], b = rank[r->pairs[2 * k + 1]];
         if (a > b) std::swap(a, b);
-        pairs[k] = a | (b << 16);
+        all_pairs[k] = a | (b << 16);
     }
+    std::vector<uint4> blocks;
+    std::vector<uint32_t> pairs;
+    build_pair_blocks(all_pairs, first, pb.d, blocks, pairs);
+    pb.P = static_cast<int>(pairs.size());
+    pb.NPB = static_cast<int>(blocks.size());
+    pairs.resize(std::max(pb.P, 1));
+    blocks.resize(std::max(pb.NPB, 1));
 
     // raw doubles for the set-up kernel: dh | q_min | q_max | dt
     std::vector<double> raw;
@@ -1140,6 +1284,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     pb.sph = reinterpret_cast<float4*>(base + t.sph);
     pb.link_first = reinterpret_cast<int*>(base + t.first);
     pb.pairs = reinterpret_cast<uint32_t*>(base + t.pairs);
+    pb.pblk = reinterpret_cast<uint4*>(base + t.pblk);
     pb.boxes = reinterpret_cast<float*>(base + t.boxes);
     pb.wsph = reinterpret_cast<float4*>(base + t.wsph);
     pb.dt = reinterpret_cast<float*>(base + t.dt);
@@ -1156,6 +1301,8 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     CK(cudaMalloc(&h->d_C, sizeof(float) * pb.N));
     CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
     CK(cudaMallocHost(&h->h_io, sizeof(float) * io_floats(pb)));
+    CK(cudaMalloc(&h->d_upd, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d));
+    CK(cudaMemsetAsync(h->d_upd, 0, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d, h->stream));
     std::memset(h->h_io, 0, sizeof(float) * io_floats(pb));
     h->d_st = reinterpret_cast<StepState*>(h->d_io + io_st(pb));
 
@@ -1164,6 +1311,8 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     CK(cudaMemcpyAsync(const_cast<int*>(pb.link_first), first.data(), 4 * (pb.d + 2),
                        cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(const_cast<uint32_t*>(pb.pairs), pairs.data(), 4 * std::max(pb.P, 1),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(const_cast<uint4*>(pb.pblk), blocks.data(), 16 * std::max(pb.NPB, 1),
                        cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(d_raw, raw.data(), 8 * raw.size(), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(h->d_io, 0, sizeof(float) * io_floats(pb), h->stream));
@@ -1186,7 +1335,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
 
     const RolloutLayout L = rollout_layout(pb);
     h->rollout_smem = L.bytes;
-    h->update_smem = sizeof(float) * (((pb.N + 3) & ~3) + kUpdateThreads + pb.H * pb.d);
+    h->update_smem = sizeof(float) * ((pb.N + 3) & ~3);
     rc = allow_smem(h);
     if (rc) return rc;
     rc = storm_reset(h);
@@ -1418,6 +1567,89 @@ int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count,
     k_fk<<<(count + 127) / 128, 128, 0, h->stream>>>(h->pb, theta_dev, count, ee_dev);
     CK(cudaGetLastError());
     return STORM_OK;
+}
+
+int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    if (ppc) *ppc = h->pb.ppc;
+    if (threads) *threads = h->threads;
+    return STORM_OK;
+}
+
+static int set_launch_impl(storm_handle* h, int ppc, int threads, bool rebuild)
+{
+    if (ppc < 1 || ppc > h->pb.N || threads < 64 || threads > kMaxThreads || threads % 32)
+        return fail(h, STORM_ERR_INVALID_ARG, "launch shape out of range");
+    Problem trial = h->pb;
+    trial.ppc = ppc;
+    const RolloutLayout L = rollout_layout(trial);
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (L.bytes > optin) return fail(h, STORM_ERR_INVALID_ARG, "launch shape needs too much shared memory");
+    h->pb.ppc = ppc;
+    h->threads = threads;
+    h->grid = (h->pb.N + ppc - 1) / ppc;
+    h->rollout_smem = L.bytes;
+    return rebuild ? build_graphs(h) : STORM_OK;
+}
+
+int storm_set_launch(storm_handle* h, int ppc, int threads)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    return set_launch_impl(h, ppc, threads, true);
+}
+
+int storm_autotune(storm_handle* h, float* best_us)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    const int ppcs[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    const int ths[] = {128, 256, 512};
+    const int old_ppc = h->pb.ppc, old_threads = h->threads;
+    float best = INFINITY;
+    int best_ppc = old_ppc, best_threads = old_threads;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    RolloutOut out{h->d_u, nullptr, nullptr, nullptr, nullptr, nullptr, h->d_C};
+    const float* state = h->d_io + io_state(h->pb);
+    const float* goal = h->d_io + io_goal(h->pb);
+    int rc = STORM_OK;
+    for (int ppc : ppcs) {
+        if (ppc > h->pb.N || ppc * h->pb.H > kMaxThreads) continue;
+        for (int th : ths) {
+            if (set_launch_impl(h, ppc, th, false) != STORM_OK) continue;
+            std::vector<float> t;
+            for (int it = 0; it < 13 && rc == STORM_OK; ++it) {
+                cudaEventRecord(e0, h->stream);
+                rc = launch_rollout(h, h->stream, out, state, goal, 0, 0);
+                cudaEventRecord(e1, h->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = STORM_ERR_CUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (it >= 3) t.push_back(ms * 1e3f);
+            }
+            if (rc) break;
+            std::sort(t.begin(), t.end());
+            const float med = t[t.size() / 2];
+            if (med < best) {
+                best = med;
+                best_ppc = ppc;
+                best_threads = th;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        set_launch_impl(h, old_ppc, old_threads, true);
+        return rc;
+    }
+    if (best_us) *best_us = best;
+    return set_launch_impl(h, best_ppc, best_threads, true);
 }
 
 // checkpoint blob: magic, version, N, H, d, step | mu (H*d) | sigma (d)

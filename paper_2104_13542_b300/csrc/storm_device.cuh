@@ -11,8 +11,9 @@
 namespace storm {
 
 constexpr int kMaxDof = 7;
-constexpr int kThreads = 256;        // rollout CTA size
-constexpr int kUpdateThreads = 1024; // distribution-update CTA size
+constexpr int kThreads = 256;        // default rollout CTA size
+constexpr int kMaxThreads = 512;     // largest rollout CTA size the tuner may pick
+constexpr int kUpdateThreads = 256;  // distribution-update CTA size (one CTA per horizon step)
 
 // Per-problem constants and device table pointers (kernel parameter, by value).
 struct Problem {
@@ -31,7 +32,9 @@ struct Problem {
     const float* qhi;        // d soft upper limits  q_max - k_jl (q_max - q_min)
     const float4* sph;       // M: centre in link frame, radius (sorted by link)
     const int* link_first;   // d + 2: spheres of frame f are [link_first[f], link_first[f+1])
-    const uint32_t* pairs;   // P: a | b << 16 (sorted sphere indices)
+    const uint32_t* pairs;   // P: a | b << 16 (sorted sphere indices), pairs outside blocks
+    int NPB;                 // pair blocks
+    const uint4* pblk;       // NPB: (a0, a1, b0, nb): spheres [a0, a1) x [b0, b0 + nb), nb <= 8
     const float* boxes;      // B x 6
     const float4* wsph;      // O
     const float* dt;         // H
@@ -102,35 +105,45 @@ __device__ __forceinline__ void dh_step(float (&R)[9], float (&p)[3], float a, f
     }
 }
 
-// sqrt(det(J J^T)) for a 6 x d Jacobian given as rows, by modified Gram-Schmidt
-// on the six rows: the determinant of the Gram matrix is the product of the
-// squared norms of the orthogonalised rows.
-__device__ __forceinline__ float manipulability_mgs(float (&J)[6][kMaxDof], int d)
-{
-    float m = 1.0f;
+// Manipulability sqrt(det(J J^T)) (Eq. 12) accumulated one Jacobian column at
+// a time.  R is the upper-triangular 6x6 factor with R^T R = sum_i J_i J_i^T
+// (21 packed entries, row-major upper triangle); adding column x is a
+// rank-one update done with Givens rotations (the QR update of appending a
+// row to the data matrix), which keeps the accuracy of an orthogonal
+// factorisation.  Then det(J J^T) = prod R_kk^2.
+struct GramFactor {
+    float r[21];
+    __device__ __forceinline__ void zero()
+    {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-#pragma unroll
-        for (int i = 0; i < k; ++i) {
-            float dot = 0.0f;
-#pragma unroll
-            for (int c = 0; c < kMaxDof; ++c)
-                if (c < d) dot = fmaf(J[i][c], J[k][c], dot);
-#pragma unroll
-            for (int c = 0; c < kMaxDof; ++c)
-                if (c < d) J[k][c] = fmaf(-dot, J[i][c], J[k][c]);
-        }
-        float nn = 0.0f;
-#pragma unroll
-        for (int c = 0; c < kMaxDof; ++c)
-            if (c < d) nn = fmaf(J[k][c], J[k][c], nn);
-        const float nk = sqrtf(nn);
-        m *= nk;
-        const float inv = nk > 0.0f ? 1.0f / nk : 0.0f;
-#pragma unroll
-        for (int c = 0; c < kMaxDof; ++c) J[k][c] *= inv;
+        for (int k = 0; k < 21; ++k) r[k] = 0.f;
     }
-    return m;
-}
+    // packed index of R[i][j], i <= j
+    __device__ static constexpr int at(int i, int j) { return i * 6 - (i * (i - 1)) / 2 + (j - i); }
+    __device__ __forceinline__ void add(float (&x)[6])
+    {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float a = r[at(k, k)], b = x[k];
+            const float h = sqrtf(fmaf(a, a, b * b));
+            const float inv = h > 0.f ? 1.f / h : 0.f;
+            const float c = h > 0.f ? a * inv : 1.f, s = b * inv;
+            r[at(k, k)] = h;
+#pragma unroll
+            for (int j = k + 1; j < 6; ++j) {
+                const float rkj = r[at(k, j)], xj = x[j];
+                r[at(k, j)] = fmaf(c, rkj, s * xj);
+                x[j] = fmaf(-s, rkj, c * xj);
+            }
+        }
+    }
+    __device__ __forceinline__ float sqrt_det() const
+    {
+        float m = 1.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) m *= r[at(k, k)];
+        return fabsf(m);
+    }
+};
 
 }  // namespace storm

@@ -312,3 +312,34 @@ def test_step_async_device_buffers_match_host_step():
             got.append(c.cpu().numpy().copy())
     for x, y in zip(ref, got):
         assert np.array_equal(x, y)
+
+
+# ----------------------------------------------------------------------------- launch shapes
+
+def test_launch_shapes_are_bitwise_identical_and_autotune():
+    wl = W.config_paper(4)
+    p = wl.params.replace(N=130)
+    state, goal = cuda(f32(wl.state)), cuda(f32(wl.goal))
+    mu, sig = f32(W.make_mean(4, p.H, 7, 0.5)), f32(W.make_sigma(4, 7))
+    ref = None
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(mu, sig)
+        for ppc, threads in [(2, 256), (1, 64), (5, 512), (3, 128), (4, 256)]:
+            ctl.set_launch(ppc, threads)
+            assert ctl.get_launch() == (ppc, threads)
+            g = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 1, 0).items()}
+            if ref is None:
+                ref = g
+            for k in ref:
+                assert np.array_equal(g[k], ref[k]), (ppc, threads, k)
+        with pytest.raises(StormError):
+            ctl.set_launch(0, 256)
+        with pytest.raises(StormError):
+            ctl.set_launch(2, 100)
+        ctl.step(f32(wl.state), f32(wl.goal))
+        t = ctl.autotune()
+        assert 0 < t < 1e4
+        ctl.set_distribution(mu, sig)  # the step above moved the distribution
+        g = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 1, 0).items()}
+        for k in ref:
+            assert np.array_equal(g[k], ref[k]), k
