@@ -117,6 +117,12 @@ def _declare(L):
     L.orc_step.argtypes = [C.POINTER(_Robot), C.POINTER(_World), C.POINTER(_Params), _dp, _dp,
                            C.c_uint32, _dp, _dp, _dp, _dp]
     L.orc_step.restype = C.c_int
+    L.orc_running_cost_grad.argtypes = [C.POINTER(_Robot), C.POINTER(_World), C.POINTER(_Params),
+                                        _dp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_integrate_adjoint.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
+    L.orc_cost_grad.argtypes = [C.POINTER(_Robot), C.POINTER(_World), C.POINTER(_Params), _dp, _dp,
+                                _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_cost_grad.restype = C.c_int
 
 
 def _f64(a):
@@ -181,6 +187,16 @@ def noise_halton(N, S, d) -> np.ndarray:
 def bspline_basis(H, S) -> np.ndarray:
     out = np.zeros((H, S))
     lib().orc_bspline_basis(H, S, _ptr(out))
+    return out
+
+
+def integrate_adjoint(dt, g_theta, g_theta_dot, g_u):
+    dt = _f64(dt)
+    g_theta, g_theta_dot, g_u = _f64(g_theta), _f64(g_theta_dot), _f64(g_u)
+    H, d = g_u.shape
+    out = np.zeros((H, d))
+    lib().orc_integrate_adjoint(H, d, _ptr(dt), _ptr(g_theta), _ptr(g_theta_dot), _ptr(g_u),
+                                _ptr(out))
     return out
 
 
@@ -332,6 +348,29 @@ class Oracle:
         if rc != 0:
             raise ValueError(f"orc_rollout failed: {rc}")
         return out
+
+    def running_cost_grad(self, goal, h, theta_h, theta_dot_h, u_h, u_prev):
+        d = self.d
+        g = [np.zeros(d) for _ in range(4)]
+        lib().orc_running_cost_grad(C.byref(self.R), C.byref(self.W), C.byref(self.P),
+                                    _ptr(_f64(goal)), int(h), _ptr(_f64(theta_h)),
+                                    _ptr(_f64(theta_dot_h)), _ptr(_f64(u_h)), _ptr(_f64(u_prev)),
+                                    *[_ptr(x) for x in g])
+        return g
+
+    def cost_grad(self, state, goal, mu, sigma, eps, per_particle=False):
+        """J(mu) = mean_n C_n and dJ/dmu (H x d), noise eps fixed."""
+        p = self.params
+        grad = np.zeros((p.H, self.d))
+        J = C.c_double()
+        dcdu = np.zeros((p.N, p.H, self.d)) if per_particle else None
+        rc = lib().orc_cost_grad(C.byref(self.R), C.byref(self.W), C.byref(self.P),
+                                 _ptr(_f64(state)), _ptr(_f64(goal)), _ptr(_f64(mu)),
+                                 _ptr(_f64(sigma)), _ptr(_f64(eps)), _ptr(grad), C.byref(J),
+                                 _ptr(dcdu))
+        if rc != 0:
+            raise ValueError("orc_cost_grad failed")
+        return (J.value, grad, dcdu) if per_particle else (J.value, grad)
 
     def update(self, Ctot, u, mu, sigma):
         mu = _f64(mu).copy()

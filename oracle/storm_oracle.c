@@ -746,3 +746,402 @@ int orc_step(const orc_robot* R, const orc_world* W, const orc_params* P,
     free(C);
     return status;
 }
+
+/* ========================================================================= */
+/* Adjoint of the rollout cost with respect to the mean control sequence.    */
+/* The paper optimises the mean by sampling only; this gradient is an added  */
+/* capability.  J(mu) = (1/N) sum_n C_n(u_n), u_n = mu + sigma o eps~_n with */
+/* the noise fixed, so dJ/dmu = (1/N) sum_{n >= n_null} dC_n/du_n.  Every    */
+/* derivative below is the hand-derived derivative of the forward routine   */
+/* above; kinks take the zero subgradient (a norm at 0, a hinge at 0), the   */
+/* min over collision pairs follows its first minimiser, and the            */
+/* manipulability indicator is differentiated only where m < k_m.  Pinned by */
+/* FP64 central finite differences away from kinks and by the explicit       */
+/* transpose of the integration matrices.                                    */
+/* ========================================================================= */
+
+static void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* vee part of tr(A [w]x): returns v with tr(A [w]x) = v . w */
+static void trace_skew(const double* A, double* v)
+{
+    v[0] = A[1 * 3 + 2] - A[2 * 3 + 1];
+    v[1] = A[2 * 3 + 0] - A[0 * 3 + 2];
+    v[2] = A[0 * 3 + 1] - A[1 * 3 + 0];
+}
+
+/* Inverse of an n x n matrix by Gauss-Jordan with partial pivoting; 0 if singular. */
+static int invert(int n, const double* A, double* Ainv)
+{
+    double M[6 * 12];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c)
+            M[r * 2 * n + c] = (c < n) ? A[r * n + c] : ((c - n == r) ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[r * 2 * n + c]) > fabs(M[piv * 2 * n + c])) piv = r;
+        if (M[piv * 2 * n + c] == 0.0) return 0;
+        for (int k = 0; k < 2 * n; ++k) {
+            const double t = M[c * 2 * n + k];
+            M[c * 2 * n + k] = M[piv * 2 * n + k];
+            M[piv * 2 * n + k] = t;
+        }
+        const double inv = 1.0 / M[c * 2 * n + c];
+        for (int k = 0; k < 2 * n; ++k) M[c * 2 * n + k] *= inv;
+        for (int r = 0; r < n; ++r)
+            if (r != c) {
+                const double f = M[r * 2 * n + c];
+                for (int k = 0; k < 2 * n; ++k) M[r * 2 * n + k] -= f * M[c * 2 * n + k];
+            }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ainv[r * n + c] = M[r * 2 * n + n + c];
+    return 1;
+}
+
+/* Add w * (dphi/dc)^T (dc/dtheta) for a point c rigidly attached to frame f:
+ * dc/dtheta_k = z_k x (c - o_k) for joints k = 1..f. */
+static void add_point_grad(const double* frames, int f, const double* c, const double* dphi_dc,
+                           double w, double* g_theta)
+{
+    for (int k = 1; k <= f; ++k) {
+        const double* T = frames + k * 16;
+        const double z[3] = {T[2], T[6], T[10]};
+        const double r[3] = {c[0] - T[3], c[1] - T[7], c[2] - T[11]};
+        double v[3];
+        cross3(z, r, v);
+        g_theta[k - 1] += w * (dphi_dc[0] * v[0] + dphi_dc[1] * v[1] + dphi_dc[2] * v[2]);
+    }
+}
+
+/* Gradient of the running cost c_hat_h (Eq. 15) with respect to theta_h,
+ * theta_dot_h, u_h and u_{h-1}. */
+void orc_running_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
+                           const double* goal, int h, const double* theta_h,
+                           const double* theta_dot_h, const double* u_h, const double* u_prev,
+                           double* g_th, double* g_thd, double* g_u, double* g_up)
+{
+    const int d = R->dof, H = P->H;
+    double* frames = (double*)malloc(sizeof(double) * 16 * (d + 1));
+    double J[6 * 8];
+    orc_fk(R, theta_h, frames);
+    orc_jacobian(R, frames, J);
+    for (int j = 0; j < d; ++j) g_th[j] = g_thd[j] = g_u[j] = g_up[j] = 0.0;
+    const double* Te = frames + d * 16;
+    const double Ree[9] = {Te[0], Te[1], Te[2], Te[4], Te[5], Te[6], Te[8], Te[9], Te[10]};
+    double Rg[9];
+    orc_rot_from_quat(goal + 3, Rg);
+
+    /* position (Eq. 9): d||e||/dp = R_g (alpha_2 o e) / ||e||, then J_v^T */
+    {
+        const double dp[3] = {Te[3] - goal[0], Te[7] - goal[1], Te[11] - goal[2]};
+        double e[3], c = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            e[i] = P->pos_axis_w[i] *
+                   (Rg[0 * 3 + i] * dp[0] + Rg[1 * 3 + i] * dp[1] + Rg[2 * 3 + i] * dp[2]);
+            c += e[i] * e[i];
+        }
+        c = sqrt(c);
+        if (c > 0.0) {
+            double gp[3];
+            for (int r = 0; r < 3; ++r) {
+                gp[r] = 0.0;
+                for (int i = 0; i < 3; ++i) gp[r] += Rg[r * 3 + i] * P->pos_axis_w[i] * e[i] / c;
+            }
+            for (int k = 0; k < d; ++k)
+                g_th[k] += P->w_pos * (gp[0] * J[0 * d + k] + gp[1] * J[1 * d + k] + gp[2] * J[2 * d + k]);
+        }
+    }
+    /* rotation (Eq. 9): dR = [w]x R with w = J_w dtheta */
+    {
+        double gw[3] = {0.0, 0.0, 0.0};
+        if (P->rot_mode == ORC_ROT_QUAT) {
+            /* 1 - |q_ee . q_g| = 1 - sqrt(1 + tr(R_g^T R_ee)) / 2 */
+            double tr = 0.0;
+            for (int k = 0; k < 9; ++k) tr += Rg[k] * Ree[k];
+            if (1.0 + tr > 0.0) {
+                double A[9], v[3]; /* A = R_ee R_g^T */
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) {
+                        A[r * 3 + c] = 0.0;
+                        for (int k = 0; k < 3; ++k) A[r * 3 + c] += Ree[r * 3 + k] * Rg[c * 3 + k];
+                    }
+                trace_skew(A, v);
+                const double dc_dtr = -0.25 / sqrt(1.0 + tr);
+                for (int i = 0; i < 3; ++i) gw[i] = dc_dtr * v[i];
+            }
+        } else {
+            double E[9], c = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int q = 0; q < 3; ++q) {
+                    double RtR = 0.0;
+                    for (int k = 0; k < 3; ++k) RtR += Rg[k * 3 + r] * Ree[k * 3 + q];
+                    E[r * 3 + q] = ((r == q) ? 1.0 : 0.0) - RtR;
+                    c += (E[r * 3 + q] * P->rot_axis_w[q]) * (E[r * 3 + q] * P->rot_axis_w[q]);
+                }
+            c = sqrt(c);
+            if (c > 0.0) {
+                /* dc = (1/c) tr(M^T dE), M = E diag(alpha_1^2), dE = -R_g^T [w]x R_ee
+                 *    = -(1/c) tr(A [w]x) with A = R_ee M^T R_g^T */
+                double Mt[9], A[9], tmp[9], v[3];
+                for (int r = 0; r < 3; ++r)
+                    for (int q = 0; q < 3; ++q)
+                        Mt[q * 3 + r] = E[r * 3 + q] * P->rot_axis_w[q] * P->rot_axis_w[q];
+                for (int r = 0; r < 3; ++r)
+                    for (int q = 0; q < 3; ++q) {
+                        tmp[r * 3 + q] = 0.0;
+                        for (int k = 0; k < 3; ++k) tmp[r * 3 + q] += Ree[r * 3 + k] * Mt[k * 3 + q];
+                    }
+                for (int r = 0; r < 3; ++r)
+                    for (int q = 0; q < 3; ++q) {
+                        A[r * 3 + q] = 0.0;
+                        for (int k = 0; k < 3; ++k) A[r * 3 + q] += tmp[r * 3 + k] * Rg[q * 3 + k];
+                    }
+                trace_skew(A, v);
+                for (int i = 0; i < 3; ++i) gw[i] = -v[i] / c;
+            }
+        }
+        for (int k = 0; k < d; ++k)
+            g_th[k] += P->w_rot * (gw[0] * J[3 * d + k] + gw[1] * J[4 * d + k] + gw[2] * J[5 * d + k]);
+    }
+    /* stop (Eq. 10), joint limits (Eq. 11), smoothness */
+    {
+        double vmax = 0.0;
+        for (int k = 0; k < H; ++k) vmax += (k >= h ? 1.0 : 0.0) * P->qdd_max * P->dt[k];
+        double vs[8], vj[8], cs = 0.0, cj = 0.0;
+        for (int j = 0; j < d; ++j) {
+            vs[j] = fabs(theta_dot_h[j]) - vmax;
+            if (vs[j] < 0.0) vs[j] = 0.0;
+            cs += vs[j] * vs[j];
+            const double range = R->q_max[j] - R->q_min[j];
+            const double lo = R->q_min[j] + P->k_jl * range, hi = R->q_max[j] - P->k_jl * range;
+            vj[j] = (theta_h[j] < lo ? lo - theta_h[j] : 0.0) + (theta_h[j] > hi ? theta_h[j] - hi : 0.0);
+            cj += vj[j] * vj[j];
+            const double du = u_h[j] - u_prev[j];
+            g_u[j] += P->w_smooth * 2.0 * du;
+            g_up[j] -= P->w_smooth * 2.0 * du;
+        }
+        cs = sqrt(cs);
+        cj = sqrt(cj);
+        for (int j = 0; j < d; ++j) {
+            if (cs > 0.0 && vs[j] > 0.0)
+                g_thd[j] += P->w_stop * vs[j] * (theta_dot_h[j] > 0.0 ? 1.0 : -1.0) / cs;
+            if (cj > 0.0 && vj[j] > 0.0) {
+                const double range = R->q_max[j] - R->q_min[j];
+                const double lo = R->q_min[j] + P->k_jl * range;
+                g_th[j] += P->w_joint * vj[j] * (theta_h[j] < lo ? -1.0 : 1.0) / cj;
+            }
+        }
+    }
+    /* manipulability (Eq. 12): dm/dtheta_k = m tr(J0^+ dJ0/dtheta_k), with J0 the
+     * geometric Jacobian about the base origin (same det(J J^T)), columns
+     * [o_i x z_i; z_i]; dz_i/dtheta_k = z_k x z_i and do_i/dtheta_k =
+     * z_k x (o_i - o_k) for k < i, zero otherwise. */
+    {
+        const double m = orc_manipulability(J, d);
+        if (m < P->k_m && m > 0.0 && P->w_manip != 0.0) {
+            double z[8][3], o[8][3], J0[6 * 8], G[36], Gi[36];
+            for (int i = 0; i < d; ++i) {
+                const double* T = frames + (i + 1) * 16;
+                z[i][0] = T[2], z[i][1] = T[6], z[i][2] = T[10];
+                o[i][0] = T[3], o[i][1] = T[7], o[i][2] = T[11];
+                double oz[3];
+                cross3(o[i], z[i], oz);
+                for (int r = 0; r < 3; ++r) {
+                    J0[r * d + i] = oz[r];
+                    J0[(3 + r) * d + i] = z[i][r];
+                }
+            }
+            for (int r = 0; r < 6; ++r)
+                for (int c = 0; c < 6; ++c) {
+                    G[r * 6 + c] = 0.0;
+                    for (int k = 0; k < d; ++k) G[r * 6 + c] += J0[r * d + k] * J0[c * d + k];
+                }
+            if (invert(6, G, Gi)) {
+                double Jp[8 * 6]; /* J0^T G^-1, d x 6 */
+                for (int i = 0; i < d; ++i)
+                    for (int r = 0; r < 6; ++r) {
+                        Jp[i * 6 + r] = 0.0;
+                        for (int k = 0; k < 6; ++k) Jp[i * 6 + r] += J0[k * d + i] * Gi[k * 6 + r];
+                    }
+                for (int k = 0; k < d; ++k) {
+                    double tr = 0.0;
+                    for (int i = k + 1; i < d; ++i) {
+                        double dz[3], doo[3], rel[3], a[3], b[3];
+                        cross3(z[k], z[i], dz);
+                        for (int q = 0; q < 3; ++q) rel[q] = o[i][q] - o[k][q];
+                        cross3(z[k], rel, doo);
+                        cross3(doo, z[i], a);
+                        cross3(o[i], dz, b);
+                        for (int q = 0; q < 3; ++q) {
+                            tr += Jp[i * 6 + q] * (a[q] + b[q]);
+                            tr += Jp[i * 6 + 3 + q] * dz[q];
+                        }
+                    }
+                    g_th[k] += P->w_manip * (-m * tr);
+                }
+            }
+        }
+    }
+    /* self collision (Eq. 13 reading): first minimising pair */
+    if (P->w_coll != 0.0) {
+        double best = INFINITY, na[3] = {0, 0, 0}, ca_b[3], cb_b[3];
+        int ba = -1, bb = -1;
+        for (int k = 0; k < R->n_pairs; ++k) {
+            const int a = R->pairs[2 * k], b = R->pairs[2 * k + 1];
+            double ca[3], cb[3];
+            sphere_center(R, frames, a, ca);
+            sphere_center(R, frames, b, cb);
+            const double dist = sqrt((ca[0] - cb[0]) * (ca[0] - cb[0]) + (ca[1] - cb[1]) * (ca[1] - cb[1]) +
+                                     (ca[2] - cb[2]) * (ca[2] - cb[2]));
+            const double sd = dist - R->sphere[a * 4 + 3] - R->sphere[b * 4 + 3];
+            if (sd < best) {
+                best = sd;
+                ba = a;
+                bb = b;
+                for (int q = 0; q < 3; ++q) {
+                    na[q] = dist > 0.0 ? (ca[q] - cb[q]) / dist : 0.0;
+                    ca_b[q] = ca[q];
+                    cb_b[q] = cb[q];
+                }
+            }
+        }
+        if (ba >= 0 && best < 0.0) {
+            /* c_self = -sd: d(-sd)/dc_a = -n, d(-sd)/dc_b = +n */
+            const double mn[3] = {-na[0], -na[1], -na[2]};
+            add_point_grad(frames, R->sphere_link[ba], ca_b, mn, P->w_coll, g_th);
+            add_point_grad(frames, R->sphere_link[bb], cb_b, na, P->w_coll, g_th);
+        }
+    }
+    /* world collision (Eq. 14 reading): first minimising (sphere, obstacle) */
+    if (P->w_coll != 0.0) {
+        double best = INFINITY, grad_c[3] = {0, 0, 0}, cbest[3];
+        int bs = -1;
+        for (int s = 0; s < R->n_spheres; ++s) {
+            double c[3];
+            sphere_center(R, frames, s, c);
+            const double r = R->sphere[s * 4 + 3];
+            for (int b = 0; b < W->n_boxes; ++b) {
+                const double* box = W->boxes + b * 6;
+                const double sd = orc_box_sdf(c, box) - r;
+                if (sd < best) {
+                    best = sd;
+                    bs = s;
+                    memcpy(cbest, c, sizeof(cbest));
+                    double q[3], out = 0.0;
+                    int kmax = 0;
+                    for (int k = 0; k < 3; ++k) {
+                        q[k] = fabs(c[k] - box[k]) - box[3 + k];
+                        if (q[k] > 0.0) out += q[k] * q[k];
+                        if (q[k] > q[kmax]) kmax = k;
+                    }
+                    out = sqrt(out);
+                    for (int k = 0; k < 3; ++k) {
+                        const double sgn = (c[k] - box[k]) >= 0.0 ? 1.0 : -1.0;
+                        if (out > 0.0)
+                            grad_c[k] = q[k] > 0.0 ? sgn * q[k] / out : 0.0;
+                        else
+                            grad_c[k] = (k == kmax) ? sgn : 0.0;
+                    }
+                }
+            }
+            for (int o = 0; o < W->n_spheres; ++o) {
+                const double* S = W->spheres + o * 4;
+                const double dist = sqrt((c[0] - S[0]) * (c[0] - S[0]) + (c[1] - S[1]) * (c[1] - S[1]) +
+                                         (c[2] - S[2]) * (c[2] - S[2]));
+                const double sd = dist - r - S[3];
+                if (sd < best) {
+                    best = sd;
+                    bs = s;
+                    memcpy(cbest, c, sizeof(cbest));
+                    for (int k = 0; k < 3; ++k) grad_c[k] = dist > 0.0 ? (c[k] - S[k]) / dist : 0.0;
+                }
+            }
+        }
+        if (bs >= 0 && best < 0.0) {
+            const double mg[3] = {-grad_c[0], -grad_c[1], -grad_c[2]};
+            add_point_grad(frames, R->sphere_link[bs], cbest, mg, P->w_coll, g_th);
+        }
+    }
+    free(frames);
+}
+
+/* Adjoint of the integration (Eq. 7) for one particle: given G_theta_h,
+ * G_theta_dot_h, G_u_h (all H x d, already discounted), returns dC/du_k =
+ * G_u_k + dt_k sum_{h>=k} (G_theta_dot_h + dt_h sum_{m>=h} G_theta_m), i.e.
+ * the transposes of the inclusive lower-triangular S_l(1) diag(dt) products. */
+void orc_integrate_adjoint(int H, int d, const double* dt, const double* g_th, const double* g_thd,
+                           const double* g_u, double* dC_du)
+{
+    for (int j = 0; j < d; ++j) {
+        for (int k = 0; k < H; ++k) {
+            /* total derivative with respect to theta_dot_k */
+            double acc = 0.0;
+            for (int h = k; h < H; ++h) {
+                double tv = g_thd[h * d + j];
+                for (int m = h; m < H; ++m) tv += dt[h] * g_th[m * d + j];
+                acc += tv;
+            }
+            dC_du[k * d + j] = g_u[k * d + j] + dt[k] * acc;
+        }
+    }
+}
+
+int orc_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
+                  const double* state, const double* goal, const double* mu, const double* sigma,
+                  const double* eps, double* grad_mu, double* Jval, double* dC_du_out)
+{
+    const int N = P->N, H = P->H, d = R->dof;
+    if (N <= 0 || H <= 0 || d <= 0 || d > 8) return -1;
+    double* u = (double*)malloc(sizeof(double) * (size_t)N * H * d);
+    double* th = (double*)malloc(sizeof(double) * H * d);
+    double* thd = (double*)malloc(sizeof(double) * H * d);
+    double* Gth = (double*)malloc(sizeof(double) * H * d);
+    double* Gthd = (double*)malloc(sizeof(double) * H * d);
+    double* Gu = (double*)malloc(sizeof(double) * H * d);
+    double* dCdu = (double*)malloc(sizeof(double) * H * d);
+    orc_smooth_controls(P, d, mu, sigma, eps, u);
+    for (int k = 0; k < H * d; ++k) grad_mu[k] = 0.0;
+    double Jacc = 0.0;
+    for (int n = 0; n < N; ++n) {
+        const double* un = u + (size_t)n * H * d;
+        orc_integrate(H, d, P->dt, state, un, th, thd);
+        for (int k = 0; k < H * d; ++k) Gth[k] = Gthd[k] = Gu[k] = 0.0;
+        double C = 0.0;
+        for (int h = 0; h < H; ++h) {
+            double terms[ORC_NTERMS], c, gt[8], gtd[8], gu[8], gup[8];
+            const double* uprev = (h == 0) ? state + 2 * d : un + (h - 1) * d;
+            orc_running_cost(R, W, P, goal, h, th + h * d, thd + h * d, un + h * d, uprev, terms, &c);
+            const double gam = pow(P->gamma, (double)h);
+            C += gam * c;
+            orc_running_cost_grad(R, W, P, goal, h, th + h * d, thd + h * d, un + h * d, uprev, gt,
+                                  gtd, gu, gup);
+            for (int j = 0; j < d; ++j) {
+                Gth[h * d + j] += gam * gt[j];
+                Gthd[h * d + j] += gam * gtd[j];
+                Gu[h * d + j] += gam * gu[j];
+                if (h > 0) Gu[(h - 1) * d + j] += gam * gup[j];
+            }
+        }
+        Jacc += C;
+        orc_integrate_adjoint(H, d, P->dt, Gth, Gthd, Gu, dCdu);
+        if (dC_du_out) memcpy(dC_du_out + (size_t)n * H * d, dCdu, sizeof(double) * H * d);
+        if (n >= P->n_null)
+            for (int k = 0; k < H * d; ++k) grad_mu[k] += dCdu[k] / N;
+    }
+    *Jval = Jacc / N;
+    free(u);
+    free(th);
+    free(thd);
+    free(Gth);
+    free(Gthd);
+    free(Gu);
+    free(dCdu);
+    return 0;
+}

@@ -110,6 +110,15 @@ int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
 int orc_update(const orc_params* P, int d, const double* Ctot, const double* u,
                double* mu, double* sigma, double* weights);
 void orc_shift(int H, int d, double* mu);
+void orc_running_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
+                           const double* goal, int h, const double* theta_h,
+                           const double* theta_dot_h, const double* u_h, const double* u_prev,
+                           double* g_theta, double* g_theta_dot, double* g_u, double* g_u_prev);
+void orc_integrate_adjoint(int H, int d, const double* dt, const double* g_theta,
+                           const double* g_theta_dot, const double* g_u, double* dC_du);
+int orc_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
+                  const double* state, const double* goal, const double* mu, const double* sigma,
+                  const double* eps, double* grad_mu, double* J, double* dC_du);
 int orc_step(const orc_robot* R, const orc_world* W, const orc_params* P,
              const double* state, const double* goal, uint32_t step, double* mu,
              double* sigma, double* cmd, double* best_cost);
