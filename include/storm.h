@@ -113,6 +113,8 @@ typedef struct {
     double qdd_max;           /* max acceleration of the stop cost (Eq. 10) */
     uint64_t seed;            /* Philox key */
     uint32_t instance;        /* Philox stream id (< 2^24) */
+    int grad_steps;           /* gradient refinement steps after the K iterations (0..64) */
+    double grad_eta;          /* their step size: mu <- mu - grad_eta * dJ/dmu */
 } storm_params;
 
 typedef struct {
@@ -197,6 +199,22 @@ int storm_generate_rollouts(storm_handle* h, const float* state_dev, const float
  * is reported by the next storm_sync / storm_step. */
 int storm_update_distribution(storm_handle* h, const float* Ctot_dev, const float* u_dev,
                               float* weights_dev);
+
+/* Adjoint of the rollout cost (the paper has no counterpart; it samples
+ * only): J(mu) = (1/N) sum_n C_hat_n(mu + sigma o eps~_n) (Eq. 2) with the
+ * noise of (step, iter) and the handle's sigma fixed, and dJ/dmu (H x dof)
+ * back through the running cost (Eqs. 9-15), the FK / Jacobian (Eq. 8) and
+ * the integration scan (Eq. 7).  Null particles contribute to J but not to
+ * the gradient.  Subgradients: 0 at a norm's or hinge's kink; the collision
+ * minimum follows its minimising pair; the manipulability indicator is
+ * differentiated only where m < k_m.  Device buffers: mean_dev (H x dof, in),
+ * grad_dev (H x dof, out), J_dev (1, out), Ctot_dev (N, out, nullable).
+ * Enqueued (no wait).  With params.grad_steps > 0 every control step ends
+ * with that many refinement steps mu <- mu - grad_eta dJ/dmu, the noise of
+ * step s being iteration K + s. */
+int storm_cost_grad(storm_handle* h, const float* state_dev, const float* goal_dev,
+                    const float* mean_dev, uint32_t step, int iter, float* grad_dev,
+                    float* J_dev, float* Ctot_dev);
 
 /* Host copies of mu (H x dof) and sigma (dof); either may be NULL.  Waits. */
 int storm_get_distribution(storm_handle* h, float* mean, float* sigma);

@@ -72,7 +72,7 @@ class _Params(C.Structure):
                 ("w_smooth", C.c_double), ("pos_axis_w", C.c_double * 3),
                 ("rot_axis_w", C.c_double * 3), ("rot_mode", C.c_int), ("k_jl", C.c_double),
                 ("k_m", C.c_double), ("qdd_max", C.c_double), ("seed", C.c_uint64),
-                ("instance", C.c_uint32)]
+                ("instance", C.c_uint32), ("grad_steps", C.c_int), ("grad_eta", C.c_double)]
 
 
 def _declare(L):
@@ -283,6 +283,7 @@ class Oracle:
         s.rot_axis_w[:] = list(p.rot_axis_w)
         s.rot_mode, s.k_jl, s.k_m, s.qdd_max = p.rot_mode, p.k_jl, p.k_m, p.qdd_max
         s.seed, s.instance = int(p.seed), int(p.instance)
+        s.grad_steps, s.grad_eta = int(p.grad_steps), float(p.grad_eta)
         return s
 
     @property

@@ -740,6 +740,16 @@ int orc_step(const orc_robot* R, const orc_world* W, const orc_params* P,
             *best_cost = m;
         }
     }
+    /* optional gradient refinement: noise of iteration K + g, mu -= eta dJ/dmu */
+    for (int g = 0; g < P->grad_steps; ++g) {
+        double* grad = (double*)malloc(sizeof(double) * H * d);
+        double J;
+        if (P->sampler == ORC_SAMPLER_PHILOX)
+            orc_noise_philox(P->seed, step, P->instance, (uint32_t)(P->K + g), 0u, count, eps);
+        orc_cost_grad(R, W, P, state, goal, mu, sigma, eps, grad, &J, NULL);
+        for (int k = 0; k < H * d; ++k) mu[k] -= P->grad_eta * grad[k];
+        free(grad);
+    }
     for (int j = 0; j < d; ++j) cmd[j] = mu[j];
     free(eps);
     free(u);

@@ -71,6 +71,8 @@ typedef struct {
     double k_jl, k_m, qdd_max;
     uint64_t seed;
     uint32_t instance;
+    int grad_steps;         /* gradient refinement steps after the K iterations */
+    double grad_eta;        /* mu <- mu - grad_eta dJ/dmu */
 } orc_params;
 
 /* ---- noise ---- */

@@ -37,7 +37,7 @@ EXPORTED = [
     "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
     "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
     "storm_set_state", "storm_rollout_costs_noalloc", "storm_set_launch", "storm_get_launch",
-    "storm_autotune",
+    "storm_autotune", "storm_cost_grad",
 ]
 
 
@@ -79,7 +79,8 @@ class storm_params(C.Structure):
                 ("w_manip", C.c_double), ("w_coll", C.c_double), ("w_smooth", C.c_double),
                 ("pos_axis_w", C.c_double * 3), ("rot_axis_w", C.c_double * 3),
                 ("rot_mode", C.c_int), ("k_jl", C.c_double), ("k_m", C.c_double),
-                ("qdd_max", C.c_double), ("seed", C.c_uint64), ("instance", C.c_uint32)]
+                ("qdd_max", C.c_double), ("seed", C.c_uint64), ("instance", C.c_uint32),
+                ("grad_steps", C.c_int), ("grad_eta", C.c_double)]
 
 
 class storm_step_info(C.Structure):
@@ -125,6 +126,7 @@ def lib():
         L.storm_set_launch.argtypes = [vp, C.c_int, C.c_int]
         L.storm_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.storm_autotune.argtypes = [vp, C.POINTER(C.c_float)]
+        L.storm_cost_grad.argtypes = [vp, vp, vp, vp, C.c_uint32, C.c_int, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -197,6 +199,7 @@ class _Marshal:
         s.rot_axis_w[:] = list(p.rot_axis_w)
         s.rot_mode, s.k_jl, s.k_m, s.qdd_max = p.rot_mode, p.k_jl, p.k_m, p.qdd_max
         s.seed, s.instance = int(p.seed), int(p.instance)
+        s.grad_steps, s.grad_eta = int(p.grad_steps), float(p.grad_eta)
         return s
 
 
@@ -317,6 +320,18 @@ class Controller:
         self.stream.synchronize()
         return out
 
+    def cost_grad(self, mean_dev, state_dev, goal_dev, step: int, it: int, want_C=False):
+        """J(mu) (1-element tensor) and dJ/dmu (H x d) for the noise of (step, it)."""
+        grad = self._empty(self.H, self.d)
+        J = self._empty(1)
+        Cn = self._empty(self.N) if want_C else None
+        self._join()
+        self._check(lib().storm_cost_grad(self.h, _dptr(state_dev), _dptr(goal_dev),
+                                          _dptr(mean_dev.contiguous()), int(step), int(it),
+                                          _dptr(grad), _dptr(J), _dptr(Cn)))
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+        return (J, grad, Cn) if want_C else (J, grad)
+
     def update_distribution(self, C_dev, u_dev, want_weights=True):
         w = self._empty(self.N) if want_weights else None
         self._join()
@@ -392,3 +407,35 @@ def rollout_costs_noalloc(robot, world, params, state_dev, goal_dev, mean_dev, s
     return L.storm_rollout_costs_noalloc(C.byref(r), C.byref(w), C.byref(p), _dptr(state_dev),
                                          _dptr(goal_dev), _dptr(mean_dev), _dptr(sigma_dev),
                                          int(step), int(it), _dptr(Ctot_dev), s)
+
+
+def _storm_cost_function():
+    import torch
+
+    class StormCost(torch.autograd.Function):
+        """J(mu) of a controller's rollouts as a differentiable function of the
+        mean control sequence; backward is the library's adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, mean, controller, state_dev, goal_dev, step, it):
+            J, grad = controller.cost_grad(mean.detach().float(), state_dev, goal_dev, step, it)
+            ctx.save_for_backward(grad)
+            return J.reshape(())
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (grad,) = ctx.saved_tensors
+            return gJ * grad, None, None, None, None, None
+
+    return StormCost
+
+
+_StormCost = None
+
+
+def storm_cost(mean, controller, state_dev, goal_dev, step: int = 0, it: int = 0):
+    """Differentiable J(mu): ``storm_cost(mu, ctl, state, goal).backward()``."""
+    global _StormCost
+    if _StormCost is None:
+        _StormCost = _storm_cost_function()
+    return _StormCost.apply(mean, controller, state_dev, goal_dev, step, it)

@@ -705,6 +705,8 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
     if (tid == 0) scr->count = 0;
 }
 
+#include "storm_adjoint.cuh"
+
 // Raw noise of sample_controls: one thread per Philox block (4 values).
 __global__ void k_noise(Problem pb, uint32_t step, int iter, float* __restrict__ eps)
 {
@@ -901,6 +903,10 @@ struct storm_handle {
     float* d_io = nullptr;     // state 3d | goal 7 | cmd d | StepState
     StepState* d_st = nullptr;
     UpdateScratch* d_upd = nullptr;  // multi-CTA update: counter + H x d partials
+    float* d_adj = nullptr;          // adjoint partial rows: N x (H*d + 1)
+    size_t adjoint_smem = 0;
+    int grad_steps = 0;
+    float grad_eta = 0.f;
     float* h_io = nullptr;     // pinned mirror of d_io
     cudaGraphExec_t g_dev = nullptr, g_host = nullptr;
     std::string err = "no error";
@@ -985,6 +991,9 @@ int validate(const storm_robot* r, const storm_world* w, const storm_params* p, 
     if (!(p->beta >= 0) || !(p->gamma >= 0) || !(p->sigma_init >= 0) || !(p->sigma_min >= 0))
         return msg = "bad beta/gamma/sigma", STORM_ERR_INVALID_ARG;
     if (p->instance >= (1u << 24)) return msg = "instance >= 2^24", STORM_ERR_INVALID_ARG;
+    if (p->grad_steps < 0 || p->grad_steps > 64 || p->K + p->grad_steps > 256 ||
+        !std::isfinite(p->grad_eta))
+        return msg = "bad grad_steps / grad_eta", STORM_ERR_INVALID_ARG;
     return STORM_OK;
 }
 
@@ -1060,6 +1069,20 @@ int launch_update(storm_handle* h, cudaStream_t s, const float* C, const float* 
     return STORM_OK;
 }
 
+int launch_adjoint(storm_handle* h, cudaStream_t s, const float* state, const float* goal,
+                   const float* mean, int step_override, int iter, float* grad, float* J, float* Ctot,
+                   float eta, float* cmd, int finalize)
+{
+    const int threads = std::max(64, std::min(128, (h->pb.H + 31) / 32 * 32));
+    k_adjoint<<<h->pb.N, threads, h->adjoint_smem, s>>>(h->pb, mean, state, goal, h->d_st,
+                                                         step_override, iter, h->d_adj, Ctot);
+    CK(cudaGetLastError());
+    k_adjoint_reduce<<<h->pb.H * h->pb.d + 1, 128, 0, s>>>(h->pb, h->d_adj, grad, J, eta, h->d_st,
+                                                           cmd, finalize);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
 // Enqueue the kernels of one control step (device inputs in d_io).
 int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
 {
@@ -1073,7 +1096,12 @@ int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
     for (int k = 0; k < h->K; ++k) {
         int rc = launch_rollout(h, s, out, state, goal, -1, k);
         if (rc) return rc;
-        rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1);
+        rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1 && h->grad_steps == 0);
+        if (rc) return rc;
+    }
+    for (int g = 0; g < h->grad_steps; ++g) {  // gradient refinement of the mean
+        int rc = launch_adjoint(h, s, state, goal, h->pb.mu, -1, h->K + g, nullptr, nullptr,
+                                nullptr, h->grad_eta, cmd, g == h->grad_steps - 1);
         if (rc) return rc;
     }
     return STORM_OK;
@@ -1085,12 +1113,16 @@ int allow_smem(storm_handle* h)
 {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    cudaFuncAttributes ra, ua;
+    cudaFuncAttributes ra, ua, aa;
     CK(cudaFuncGetAttributes(&ra, k_rollout));
     CK(cudaFuncGetAttributes(&ua, k_update));
+    CK(cudaFuncGetAttributes(&aa, k_adjoint));
     if (h->rollout_smem + ra.sharedSizeBytes > size_t(optin) ||
-        h->update_smem + ua.sharedSizeBytes > size_t(optin))
+        h->update_smem + ua.sharedSizeBytes > size_t(optin) ||
+        h->adjoint_smem + aa.sharedSizeBytes > size_t(optin))
         return fail(h, STORM_ERR_INVALID_ARG, "problem needs more shared memory than a CTA has");
+    CK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(aa.sharedSizeBytes)));
     CK(cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             optin - static_cast<int>(ra.sharedSizeBytes)));
     CK(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1153,6 +1185,7 @@ void free_all(storm_handle* h)
     if (h->d_C) cudaFree(h->d_C);
     if (h->d_io) cudaFree(h->d_io);
     if (h->d_upd) cudaFree(h->d_upd);
+    if (h->d_adj) cudaFree(h->d_adj);
     if (h->h_io) cudaFreeHost(h->h_io);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -1232,6 +1265,8 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     pb.seed_hi = static_cast<uint32_t>(p->seed >> 32);
     pb.instance = p->instance;
     h->K = p->K;
+    h->grad_steps = p->grad_steps;
+    h->grad_eta = static_cast<float>(p->grad_eta);
     h->sigma_init = p->sigma_init;
     h->cap_boxes = STORM_MAX_OBSTACLES;
     h->cap_wsph = STORM_MAX_OBSTACLES;
@@ -1302,6 +1337,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
     CK(cudaMallocHost(&h->h_io, sizeof(float) * io_floats(pb)));
     CK(cudaMalloc(&h->d_upd, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d));
+    CK(cudaMalloc(&h->d_adj, sizeof(float) * size_t(pb.N) * (pb.H * pb.d + 1)));
     CK(cudaMemsetAsync(h->d_upd, 0, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d, h->stream));
     std::memset(h->h_io, 0, sizeof(float) * io_floats(pb));
     h->d_st = reinterpret_cast<StepState*>(h->d_io + io_st(pb));
@@ -1336,6 +1372,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     const RolloutLayout L = rollout_layout(pb);
     h->rollout_smem = L.bytes;
     h->update_smem = sizeof(float) * ((pb.N + 3) & ~3);
+    h->adjoint_smem = adjoint_layout(pb).bytes;
     rc = allow_smem(h);
     if (rc) return rc;
     rc = storm_reset(h);
@@ -1501,6 +1538,17 @@ int storm_generate_rollouts(storm_handle* h, const float* state_dev, const float
     RolloutOut out{u_dev ? u_dev : h->d_u, theta_dev, theta_dot_dev, ee_dev, terms_dev, cost_dev,
                    Ctot_dev ? Ctot_dev : h->d_C};
     return launch_rollout(h, h->stream, out, state_dev, goal_dev, static_cast<int>(step), iter);
+}
+
+int storm_cost_grad(storm_handle* h, const float* state_dev, const float* goal_dev,
+                    const float* mean_dev, uint32_t step, int iter, float* grad_dev, float* J_dev,
+                    float* Ctot_dev)
+{
+    if (!h || !state_dev || !goal_dev || !mean_dev || !grad_dev || !J_dev)
+        return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    if (iter < 0 || iter > 255 || step > 0x7fffffffu) return fail(h, STORM_ERR_INVALID_ARG, "bad iter/step");
+    return launch_adjoint(h, h->stream, state_dev, goal_dev, mean_dev, static_cast<int>(step), iter,
+                          grad_dev, J_dev, Ctot_dev, 0.f, nullptr, 0);
 }
 
 int storm_update_distribution(storm_handle* h, const float* Ctot_dev, const float* u_dev,

@@ -1,0 +1,658 @@
+// storm_adjoint.cuh -- adjoint of the rollout cost with respect to the mean.
+//
+// The paper optimises the mean by sampling only; this kernel adds the exact
+// gradient of J(mu) = (1/N) sum_n C_hat_n(mu + sigma o eps~_n) with the noise
+// fixed, back through the running cost (Eqs. 9-15), the kinematics (Eq. 8)
+// and the integration scan (Eq. 7).  Kinks take the zero subgradient, the
+// collision minimum follows its minimiser, and the manipulability indicator
+// is differentiated only where m < k_m.  Included by storm.cu after the
+// rollout kernel.
+#pragma once
+
+struct AdjointLayout {
+    int frame, cent, sph, wsph, boxlh, pblk, keyw, keys;                 // 16/8-byte arrays
+    int mu, sigma, eps, u, th, thd, basis, dt, gpow, vmax, dhx, qlo, qhi;  // float arrays
+    int boxes, cost, goal, state, gth, gthd, gu, gup;
+    int first, slink, pairs;
+    int bytes;
+};
+
+__host__ __device__ inline AdjointLayout adjoint_layout(const Problem& pb)
+{
+    AdjointLayout L;
+    int off = 0;
+    const int I = pb.H;  // one particle per CTA
+    L.frame = take_(off, I * (pb.d + 1) * 3 * 16);
+    L.cent = take_(off, I * pb.M * 16);
+    L.sph = take_(off, pb.M * 16);
+    L.wsph = take_(off, pb.O * 16);
+    L.boxlh = take_(off, pb.B * 2 * 16);
+    L.pblk = take_(off, pb.NPB * 16);
+    L.keyw = take_(off, I * 8);
+    L.keys = take_(off, I * 8);
+    L.mu = take_(off, pb.H * pb.d * 4);
+    L.sigma = take_(off, pb.d * 4);
+    L.eps = take_(off, pb.S * pb.d * 4);
+    L.u = take_(off, pb.H * pb.d * 4);
+    L.th = take_(off, pb.H * pb.d * 4);
+    L.thd = take_(off, pb.H * pb.d * 4);
+    L.basis = take_(off, pb.spline ? pb.H * pb.S * 4 : 0);
+    L.dt = take_(off, pb.H * 4);
+    L.gpow = take_(off, pb.H * 4);
+    L.vmax = take_(off, pb.H * 4);
+    L.dhx = take_(off, pb.d * 8 * 4);
+    L.qlo = take_(off, pb.d * 4);
+    L.qhi = take_(off, pb.d * 4);
+    L.boxes = take_(off, pb.B * 6 * 4);
+    L.cost = take_(off, I * 4);
+    L.goal = take_(off, 12 * 4);
+    L.state = take_(off, 3 * pb.d * 4);
+    L.gth = take_(off, I * pb.d * 4);
+    L.gthd = take_(off, I * pb.d * 4);
+    L.gu = take_(off, I * pb.d * 4);
+    L.gup = take_(off, I * pb.d * 4);
+    L.first = take_(off, (pb.d + 2) * 4);
+    L.slink = take_(off, pb.M * 4);
+    L.pairs = take_(off, pb.P * 4);
+    L.bytes = off;
+    return L;
+}
+
+__device__ __forceinline__ unsigned long long depth_key(float depth, uint32_t idx)
+{
+    return (static_cast<unsigned long long>(__float_as_uint(depth)) << 32) | (0xffffffffu - idx);
+}
+
+// w * g^T dc/dtheta for a point c rigidly attached to frame f (joints 0..f-1
+// move it: dc/dtheta_k = z_k x (c - o_k), z_k / o_k of frame k + 1).
+__device__ __forceinline__ void add_point_grad(const float4* fr, int f, float cx, float cy, float cz,
+                                               float gx, float gy, float gz, float w,
+                                               float (&gth)[kMaxDof])
+{
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k) {
+        if (k < f) {
+            const float4 r0 = fr[(k + 1) * 3 + 0], r1 = fr[(k + 1) * 3 + 1], r2 = fr[(k + 1) * 3 + 2];
+            const float zx = r0.z, zy = r1.z, zz = r2.z;
+            const float rx = cx - r0.w, ry = cy - r1.w, rz = cz - r2.w;
+            const float vx = zy * rz - zz * ry, vy = zz * rx - zx * rz, vz = zx * ry - zy * rx;
+            gth[k] = fmaf(w, gx * vx + gy * vy + gz * vz, gth[k]);
+        }
+    }
+}
+
+// One particle per CTA: forward rollout, per-step gradients, reverse scans,
+// then the CTA's dC/du rows and C go to the partial buffers; the last CTA
+// sums the partials in CTA order into grad = (1/N) sum_{n >= n_null} dC_n/du_n
+// and J = (1/N) sum_n C_n, and with eta != 0 also steps mu <- mu - eta grad.
+__global__ void __launch_bounds__(128)
+k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ state,
+          const float* __restrict__ goal, const StepState* __restrict__ st, int step_override,
+          int iter, float* __restrict__ part, float* __restrict__ Ctot)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const AdjointLayout L = adjoint_layout(pb);
+    float4* s_frame = reinterpret_cast<float4*>(smem + L.frame);
+    float4* s_cent = reinterpret_cast<float4*>(smem + L.cent);
+    float4* s_sph = reinterpret_cast<float4*>(smem + L.sph);
+    float4* s_wsph = reinterpret_cast<float4*>(smem + L.wsph);
+    float4* s_boxlh = reinterpret_cast<float4*>(smem + L.boxlh);
+    uint4* s_pblk = reinterpret_cast<uint4*>(smem + L.pblk);
+    unsigned long long* s_keyw = reinterpret_cast<unsigned long long*>(smem + L.keyw);
+    unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(smem + L.keys);
+    float* s_mu = reinterpret_cast<float*>(smem + L.mu);
+    float* s_sigma = reinterpret_cast<float*>(smem + L.sigma);
+    float* s_eps = reinterpret_cast<float*>(smem + L.eps);
+    float* s_u = reinterpret_cast<float*>(smem + L.u);
+    float* s_th = reinterpret_cast<float*>(smem + L.th);
+    float* s_thd = reinterpret_cast<float*>(smem + L.thd);
+    float* s_basis = reinterpret_cast<float*>(smem + L.basis);
+    float* s_dt = reinterpret_cast<float*>(smem + L.dt);
+    float* s_gpow = reinterpret_cast<float*>(smem + L.gpow);
+    float* s_vmax = reinterpret_cast<float*>(smem + L.vmax);
+    float* s_dhx = reinterpret_cast<float*>(smem + L.dhx);
+    float* s_qlo = reinterpret_cast<float*>(smem + L.qlo);
+    float* s_qhi = reinterpret_cast<float*>(smem + L.qhi);
+    float* s_boxes = reinterpret_cast<float*>(smem + L.boxes);
+    float* s_cost = reinterpret_cast<float*>(smem + L.cost);
+    float* s_goal = reinterpret_cast<float*>(smem + L.goal);
+    float* s_state = reinterpret_cast<float*>(smem + L.state);
+    float* s_gth = reinterpret_cast<float*>(smem + L.gth);
+    float* s_gthd = reinterpret_cast<float*>(smem + L.gthd);
+    float* s_gu = reinterpret_cast<float*>(smem + L.gu);
+    float* s_gup = reinterpret_cast<float*>(smem + L.gup);
+    int* s_first = reinterpret_cast<int*>(smem + L.first);
+    int* s_slink = reinterpret_cast<int*>(smem + L.slink);
+    uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.pairs);
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int d = pb.d, H = pb.H, S = pb.S, M = pb.M, F = pb.d + 1, HD = pb.H * pb.d;
+    const int n = blockIdx.x, I = H;
+    const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
+    const int NO = pb.B + pb.O;
+
+    // ---- stage
+    for (int i = tid; i < HD; i += nt) s_mu[i] = mean[i];
+    for (int i = tid; i < d; i += nt) {
+        s_sigma[i] = pb.sigma[i];
+        s_qlo[i] = pb.qlo[i];
+        s_qhi[i] = pb.qhi[i];
+    }
+    for (int i = tid; i < 3 * d; i += nt) s_state[i] = state[i];
+    for (int i = tid; i < H; i += nt) {
+        s_dt[i] = pb.dt[i];
+        s_gpow[i] = pb.gpow[i];
+        s_vmax[i] = pb.vmax[i];
+        s_keyw[i] = 0ull;
+        s_keys[i] = 0ull;
+    }
+    if (pb.spline)
+        for (int i = tid; i < H * S; i += nt) s_basis[i] = pb.basis[i];
+    for (int i = tid; i < d * 8; i += nt) s_dhx[i] = pb.dhx[i];
+    for (int i = tid; i < d + 2; i += nt) s_first[i] = pb.link_first[i];
+    for (int i = tid; i < M; i += nt) {
+        s_sph[i] = pb.sph[i];
+        int f = 0;
+        while (f < d && i >= pb.link_first[f + 1]) ++f;
+        s_slink[i] = f;
+    }
+    for (int i = tid; i < pb.P; i += nt) s_pairs[i] = pb.pairs[i];
+    for (int i = tid; i < pb.NPB; i += nt) s_pblk[i] = pb.pblk[i];
+    for (int i = tid; i < pb.B; i += nt) {
+        float b[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            b[k] = pb.boxes[i * 6 + k];
+            s_boxes[i * 6 + k] = b[k];
+        }
+        s_boxlh[2 * i] = make_float4(b[0] - b[3], b[1] - b[4], b[2] - b[5], 0.f);
+        s_boxlh[2 * i + 1] = make_float4(b[0] + b[3], b[1] + b[4], b[2] + b[5], 0.f);
+    }
+    for (int i = tid; i < pb.O; i += nt) s_wsph[i] = pb.wsph[i];
+    if (tid == 0) {
+        const float qn = rsqrtf(goal[3] * goal[3] + goal[4] * goal[4] + goal[5] * goal[5] +
+                                goal[6] * goal[6]);
+        const float w = goal[3] * qn, x = goal[4] * qn, y = goal[5] * qn, z = goal[6] * qn;
+        s_goal[0] = 1.f - 2.f * (y * y + z * z);
+        s_goal[1] = 2.f * (x * y - w * z);
+        s_goal[2] = 2.f * (x * z + w * y);
+        s_goal[3] = 2.f * (x * y + w * z);
+        s_goal[4] = 1.f - 2.f * (x * x + z * z);
+        s_goal[5] = 2.f * (y * z - w * x);
+        s_goal[6] = 2.f * (x * z - w * y);
+        s_goal[7] = 2.f * (y * z + w * x);
+        s_goal[8] = 1.f - 2.f * (x * x + y * y);
+        s_goal[9] = goal[0];
+        s_goal[10] = goal[1];
+        s_goal[11] = goal[2];
+    }
+    // ---- noise of particle n (same stream as the rollout)
+    const int per = S * d;
+    if (pb.sampler == STORM_SAMPLER_PHILOX) {
+        const uint32_t e0 = static_cast<uint32_t>(n) * per, e1 = e0 + per;
+        const uint32_t b0 = e0 >> 2, b1 = (e1 + 3) >> 2;
+        const uint32_t c2 = (pb.instance << 8) | static_cast<uint32_t>(iter);
+        for (uint32_t b = b0 + tid; b < b1; b += nt) {
+            const uint4 x = philox4x32_10(make_uint4(b, step, c2, 0u), pb.seed_lo, pb.seed_hi);
+            const float2 z01 = gauss_pair(x.x, x.y);
+            const float2 z23 = gauss_pair(x.z, x.w);
+            const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const uint32_t e = 4 * b + l;
+                if (e >= e0 && e < e1) s_eps[e - e0] = z[l];
+            }
+        }
+    } else {
+        for (int i = tid; i < per; i += nt) s_eps[i] = pb.halton[static_cast<size_t>(n) * per + i];
+    }
+    __syncthreads();
+    for (int i = tid; i < HD; i += nt) {
+        const int h = i / d, j = i - h * d;
+        float e;
+        if (pb.spline) {
+            e = 0.f;
+            for (int s = 0; s < S; ++s) e = fmaf(s_basis[h * S + s], s_eps[s * d + j], e);
+        } else {
+            e = s_eps[h * d + j];
+        }
+        s_u[i] = (n < pb.n_null) ? 0.f : fmaf(s_sigma[j], e, s_mu[i]);
+    }
+    __syncthreads();
+    for (int j = tid; j < d; j += nt) {
+        float v = s_state[d + j], q = s_state[j];
+        for (int h = 0; h < H; ++h) {
+            v = fmaf(s_dt[h], s_u[h * d + j], v);
+            q = fmaf(s_dt[h], v, q);
+            s_thd[h * d + j] = v;
+            s_th[h * d + j] = q;
+        }
+    }
+    __syncthreads();
+
+    // ---- per step h: FK frames, non-collision costs and their gradients
+    for (int h = tid; h < I; h += nt) {
+        const float* th = s_th + h * d;
+        const float* thd = s_thd + h * d;
+        const float* uh = s_u + h * d;
+        const float* up = (h == 0) ? s_state + 2 * d : uh - d;
+        float4* fr = s_frame + h * F * 3;
+        float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+        float pp[3] = {0.f, 0.f, 0.f};
+        GramFactor G;
+        G.zero();
+        fr[0] = make_float4(1.f, 0.f, 0.f, 0.f);
+        fr[1] = make_float4(0.f, 1.f, 0.f, 0.f);
+        fr[2] = make_float4(0.f, 0.f, 1.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < kMaxDof; ++i) {
+            if (i < d) {
+                const float* dh = s_dhx + i * 8;
+                dh_step(R, pp, dh[0], dh[1], dh[2], dh[3], th[i] + dh[4]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    fr[(i + 1) * 3 + r] = make_float4(R[r * 3 + 0], R[r * 3 + 1], R[r * 3 + 2], pp[r]);
+                const float zx = R[2], zy = R[5], zz = R[8];
+                float x[6] = {pp[1] * zz - pp[2] * zy, pp[2] * zx - pp[0] * zz, pp[0] * zy - pp[1] * zx,
+                              zx, zy, zz};
+                G.add(x);
+            }
+        }
+        float gth[kMaxDof], gthd[kMaxDof], gu[kMaxDof], gup[kMaxDof];
+#pragma unroll
+        for (int k = 0; k < kMaxDof; ++k) gth[k] = gthd[k] = gu[k] = gup[k] = 0.f;
+        const float* Rg = s_goal;
+        // position
+        const float dx = pp[0] - Rg[9], dy = pp[1] - Rg[10], dz = pp[2] - Rg[11];
+        float e[3], c_pos = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            e[a] = pb.pos_w[a] * fmaf(Rg[a], dx, fmaf(Rg[3 + a], dy, Rg[6 + a] * dz));
+            c_pos = fmaf(e[a], e[a], c_pos);
+        }
+        c_pos = sqrtf(c_pos);
+        float gp[3] = {0.f, 0.f, 0.f};
+        if (c_pos > 0.f) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                gp[r] = (Rg[r * 3 + 0] * pb.pos_w[0] * e[0] + Rg[r * 3 + 1] * pb.pos_w[1] * e[1] +
+                         Rg[r * 3 + 2] * pb.pos_w[2] * e[2]) / c_pos;
+        }
+        // rotation: d tr(A [w]x) with A built per mode
+        float c_rot = 0.f, gw[3] = {0.f, 0.f, 0.f};
+        if (pb.rot_mode == STORM_ROT_QUAT) {
+            float tr = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) tr = fmaf(Rg[k], R[k], tr);
+            const float s1 = sqrtf(fmaxf(0.f, 1.f + tr));
+            c_rot = 1.f - 0.5f * s1;
+            if (s1 > 0.f) {
+                float A[9];  // R_ee R_g^T
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        A[r * 3 + c] = R[r * 3 + 0] * Rg[c * 3 + 0] + R[r * 3 + 1] * Rg[c * 3 + 1] +
+                                       R[r * 3 + 2] * Rg[c * 3 + 2];
+                const float f = -0.25f / s1;
+                gw[0] = f * (A[5] - A[7]);
+                gw[1] = f * (A[6] - A[2]);
+                gw[2] = f * (A[1] - A[3]);
+            }
+        } else {
+            float E[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float rtr = Rg[r] * R[c] + Rg[3 + r] * R[3 + c] + Rg[6 + r] * R[6 + c];
+                    E[r * 3 + c] = ((r == c) ? 1.f : 0.f) - rtr;
+                    const float we = E[r * 3 + c] * pb.rot_w[c];
+                    c_rot = fmaf(we, we, c_rot);
+                }
+            c_rot = sqrtf(c_rot);
+            if (c_rot > 0.f) {
+                float Mt[9], T[9], A[9];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) Mt[q * 3 + r] = E[r * 3 + q] * pb.rot_w[q] * pb.rot_w[q];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        T[r * 3 + q] = R[r * 3 + 0] * Mt[0 * 3 + q] + R[r * 3 + 1] * Mt[1 * 3 + q] +
+                                       R[r * 3 + 2] * Mt[2 * 3 + q];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        A[r * 3 + q] = T[r * 3 + 0] * Rg[q * 3 + 0] + T[r * 3 + 1] * Rg[q * 3 + 1] +
+                                       T[r * 3 + 2] * Rg[q * 3 + 2];
+                gw[0] = -(A[5] - A[7]) / c_rot;
+                gw[1] = -(A[6] - A[2]) / c_rot;
+                gw[2] = -(A[1] - A[3]) / c_rot;
+            }
+        }
+        // pose gradients through the geometric Jacobian about the end effector
+#pragma unroll
+        for (int k = 0; k < kMaxDof; ++k) {
+            if (k < d) {
+                const float4 r0 = fr[(k + 1) * 3], r1 = fr[(k + 1) * 3 + 1], r2 = fr[(k + 1) * 3 + 2];
+                const float zx = r0.z, zy = r1.z, zz = r2.z;
+                const float rx = pp[0] - r0.w, ry = pp[1] - r1.w, rz = pp[2] - r2.w;
+                const float jx = zy * rz - zz * ry, jy = zz * rx - zx * rz, jz = zx * ry - zy * rx;
+                gth[k] += pb.w_pos * (gp[0] * jx + gp[1] * jy + gp[2] * jz) +
+                          pb.w_rot * (gw[0] * zx + gw[1] * zy + gw[2] * zz);
+            }
+        }
+        // stop, joint limits, smoothness
+        float c_stop = 0.f, c_joint = 0.f, c_smooth = 0.f;
+        const float vlim = s_vmax[h];
+        float vs[kMaxDof], vj[kMaxDof];
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) {
+            vs[j] = vj[j] = 0.f;
+            if (j < d) {
+                vs[j] = fmaxf(0.f, fabsf(thd[j]) - vlim);
+                c_stop = fmaf(vs[j], vs[j], c_stop);
+                vj[j] = fmaxf(0.f, s_qlo[j] - th[j]) + fmaxf(0.f, th[j] - s_qhi[j]);
+                c_joint = fmaf(vj[j], vj[j], c_joint);
+                const float du = uh[j] - up[j];
+                c_smooth = fmaf(du, du, c_smooth);
+                gu[j] += pb.w_smooth * 2.f * du;
+                gup[j] -= pb.w_smooth * 2.f * du;
+            }
+        }
+        c_stop = sqrtf(c_stop);
+        c_joint = sqrtf(c_joint);
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) {
+            if (j < d) {
+                if (c_stop > 0.f && vs[j] > 0.f)
+                    gthd[j] += pb.w_stop * vs[j] * (thd[j] > 0.f ? 1.f : -1.f) / c_stop;
+                if (c_joint > 0.f && vj[j] > 0.f)
+                    gth[j] += pb.w_joint * vj[j] * (th[j] < s_qlo[j] ? -1.f : 1.f) / c_joint;
+            }
+        }
+        // manipulability: dm/dtheta_k = m tr(J0^+ dJ0/dtheta_k), J0 about the base origin;
+        // J0^+ columns from the Givens factor R (R^T R = J0 J0^T): solve R^T y = J0_i, R x = y
+        const float m = G.sqrt_det();
+        float c_manip = 0.f;
+        if (m < pb.k_m) {
+            c_manip = 1.f - m;
+            if (m > 0.f && pb.w_manip != 0.f) {
+                float Jp[kMaxDof][6];
+#pragma unroll
+                for (int i = 0; i < kMaxDof; ++i) {
+                    if (i < d) {
+                        const float4 r0 = fr[(i + 1) * 3], r1 = fr[(i + 1) * 3 + 1], r2 = fr[(i + 1) * 3 + 2];
+                        float x[6] = {r1.w * r2.z - r2.w * r1.z, r2.w * r0.z - r0.w * r2.z,
+                                      r0.w * r1.z - r1.w * r0.z, r0.z, r1.z, r2.z};
+                        float y[6];
+#pragma unroll
+                        for (int a = 0; a < 6; ++a) {  // R^T y = x (R^T lower triangular)
+                            float sacc = x[a];
+#pragma unroll
+                            for (int b = 0; b < a; ++b) sacc = fmaf(-G.r[GramFactor::at(b, a)], y[b], sacc);
+                            y[a] = sacc / G.r[GramFactor::at(a, a)];
+                        }
+#pragma unroll
+                        for (int a = 5; a >= 0; --a) {  // R x = y
+                            float sacc = y[a];
+#pragma unroll
+                            for (int b = a + 1; b < 6; ++b) sacc = fmaf(-G.r[GramFactor::at(a, b)], Jp[i][b], sacc);
+                            Jp[i][a] = sacc / G.r[GramFactor::at(a, a)];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kMaxDof; ++k) {
+                    if (k < d) {
+                        const float4 k0 = fr[(k + 1) * 3], k1 = fr[(k + 1) * 3 + 1], k2 = fr[(k + 1) * 3 + 2];
+                        float tr = 0.f;
+#pragma unroll
+                        for (int i = k + 1; i < kMaxDof; ++i) {
+                            if (i < d) {
+                                const float4 a0 = fr[(i + 1) * 3], a1 = fr[(i + 1) * 3 + 1], a2 = fr[(i + 1) * 3 + 2];
+                                // dz = z_k x z_i ; do = z_k x (o_i - o_k)
+                                const float dzx = k1.z * a2.z - k2.z * a1.z, dzy = k2.z * a0.z - k0.z * a2.z,
+                                            dzz = k0.z * a1.z - k1.z * a0.z;
+                                const float rx = a0.w - k0.w, ry = a1.w - k1.w, rz = a2.w - k2.w;
+                                const float dox = k1.z * rz - k2.z * ry, doy = k2.z * rx - k0.z * rz,
+                                            doz = k0.z * ry - k1.z * rx;
+                                // d(o x z) = do x z + o x dz
+                                const float vx = (doy * a2.z - doz * a1.z) + (a1.w * dzz - a2.w * dzy);
+                                const float vy = (doz * a0.z - dox * a2.z) + (a2.w * dzx - a0.w * dzz);
+                                const float vz = (dox * a1.z - doy * a0.z) + (a0.w * dzy - a1.w * dzx);
+                                tr += Jp[i][0] * vx + Jp[i][1] * vy + Jp[i][2] * vz + Jp[i][3] * dzx +
+                                      Jp[i][4] * dzy + Jp[i][5] * dzz;
+                            }
+                        }
+                        gth[k] -= pb.w_manip * m * tr;
+                    }
+                }
+            }
+        }
+        s_cost[h] = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop + pb.w_joint * c_joint +
+                    pb.w_manip * c_manip + pb.w_smooth * c_smooth;
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) {
+            if (j < d) {
+                s_gth[h * d + j] = gth[j];
+                s_gthd[h * d + j] = gthd[j];
+                s_gu[h * d + j] = gu[j];
+                s_gup[h * d + j] = gup[j];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- sphere centres; world collision with its minimiser (sphere, obstacle)
+    for (int idx = tid; idx < I * M; idx += nt) {
+        const int item = idx / M, s = idx - item * M;
+        const float4 q = s_sph[s];
+        const float4* T = s_frame + (item * F + s_slink[s]) * 3;
+        const float4 r0 = T[0], r1 = T[1], r2 = T[2];
+        float4 c;
+        c.x = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
+        c.y = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
+        c.z = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
+        c.w = q.w;
+        s_cent[idx] = c;
+        float depth = 0.f;
+        int best = -1;
+        for (int b = 0; b < pb.B; ++b) {
+            const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
+            const float ex = c.x - fminf(fmaxf(c.x, lo.x), hi.x);
+            const float ey = c.y - fminf(fmaxf(c.y, lo.y), hi.y);
+            const float ez = c.z - fminf(fmaxf(c.z, lo.z), hi.z);
+            if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < c.w * c.w) {
+                const float* bx = s_boxes + b * 6;
+                const float qx = fabsf(c.x - bx[0]) - bx[3], qy = fabsf(c.y - bx[1]) - bx[4],
+                            qz = fabsf(c.z - bx[2]) - bx[5];
+                const float ox = fmaxf(qx, 0.f), oy = fmaxf(qy, 0.f), oz = fmaxf(qz, 0.f);
+                const float sd = sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) +
+                                 fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f) - c.w;
+                if (-sd > depth) {
+                    depth = -sd;
+                    best = b;
+                }
+            }
+        }
+        for (int k = 0; k < pb.O; ++k) {
+            const float4 w = s_wsph[k];
+            const float ex = c.x - w.x, ey = c.y - w.y, ez = c.z - w.z;
+            const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            const float rs = c.w + w.w;
+            if (dist2 < rs * rs && rs - sqrtf(dist2) > depth) {
+                depth = rs - sqrtf(dist2);
+                best = pb.B + k;
+            }
+        }
+        if (best >= 0)
+            atomicMax(s_keyw + item, depth_key(depth, static_cast<uint32_t>(s * NO + best)));
+    }
+    __syncthreads();
+    // ---- self collision with its minimiser
+    for (int idx = tid; idx < I * pb.NPB; idx += nt) {
+        const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
+        const uint4 blk = s_pblk[bk];
+        const float4* ci = s_cent + item * M;
+        float depth = 0.f;
+        int best = -1;
+        for (uint32_t a = blk.x; a < blk.y; ++a) {
+            const float4 ca = ci[a];
+            for (uint32_t k = 0; k < blk.w; ++k) {
+                const float4 cb = ci[blk.z + k];
+                const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+                const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                const float rs = ca.w + cb.w;
+                if (dist2 < rs * rs && rs - sqrtf(dist2) > depth) {
+                    depth = rs - sqrtf(dist2);
+                    best = static_cast<int>((a - blk.x) * 8 + k);
+                }
+            }
+        }
+        if (best >= 0) atomicMax(s_keys + item, depth_key(depth, static_cast<uint32_t>(bk * 64 + best)));
+    }
+    for (int idx = tid; idx < I * pb.P; idx += nt) {
+        const int item = idx / pb.P, k = idx - item * pb.P;
+        const uint32_t pr = s_pairs[k];
+        const float4 ca = s_cent[item * M + (pr & 0xffff)], cb = s_cent[item * M + (pr >> 16)];
+        const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+        const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float rs = ca.w + cb.w;
+        if (dist2 < rs * rs)
+            atomicMax(s_keys + item, depth_key(rs - sqrtf(dist2), static_cast<uint32_t>((1u << 24) + k)));
+    }
+    __syncthreads();
+
+    // ---- collision gradients of each step's minimiser
+    for (int h = tid; h < I; h += nt) {
+        const float4* fr = s_frame + h * F * 3;
+        float gth[kMaxDof];
+#pragma unroll
+        for (int k = 0; k < kMaxDof; ++k) gth[k] = (k < d) ? s_gth[h * d + k] : 0.f;
+        float dworld = 0.f, dself = 0.f;
+        const unsigned long long kw = s_keyw[h], ks = s_keys[h];
+        if (kw) {
+            dworld = __uint_as_float(static_cast<uint32_t>(kw >> 32));
+            const uint32_t id = 0xffffffffu - static_cast<uint32_t>(kw & 0xffffffffu);
+            const int s = id / NO, ob = id - s * NO;
+            const float4 c = s_cent[h * M + s];
+            float gx, gy, gz;
+            if (ob < pb.B) {
+                const float* bx = s_boxes + ob * 6;
+                const float q[3] = {fabsf(c.x - bx[0]) - bx[3], fabsf(c.y - bx[1]) - bx[4],
+                                    fabsf(c.z - bx[2]) - bx[5]};
+                const float sg[3] = {c.x - bx[0] >= 0.f ? 1.f : -1.f, c.y - bx[1] >= 0.f ? 1.f : -1.f,
+                                     c.z - bx[2] >= 0.f ? 1.f : -1.f};
+                const float ox = fmaxf(q[0], 0.f), oy = fmaxf(q[1], 0.f), oz = fmaxf(q[2], 0.f);
+                const float out = sqrtf(ox * ox + oy * oy + oz * oz);
+                if (out > 0.f) {
+                    gx = sg[0] * ox / out;
+                    gy = sg[1] * oy / out;
+                    gz = sg[2] * oz / out;
+                } else {
+                    const int km = (q[1] > q[0]) ? ((q[2] > q[1]) ? 2 : 1) : ((q[2] > q[0]) ? 2 : 0);
+                    gx = km == 0 ? sg[0] : 0.f;
+                    gy = km == 1 ? sg[1] : 0.f;
+                    gz = km == 2 ? sg[2] : 0.f;
+                }
+            } else {
+                const float4 w = s_wsph[ob - pb.B];
+                const float ex = c.x - w.x, ey = c.y - w.y, ez = c.z - w.z;
+                const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+                const float inv = dist > 0.f ? 1.f / dist : 0.f;
+                gx = ex * inv;
+                gy = ey * inv;
+                gz = ez * inv;
+            }
+            // c_world = -sd: d/dc = -grad sdf
+            add_point_grad(fr, s_slink[s], c.x, c.y, c.z, -gx, -gy, -gz, pb.w_coll, gth);
+        }
+        if (ks) {
+            dself = __uint_as_float(static_cast<uint32_t>(ks >> 32));
+            const uint32_t id = 0xffffffffu - static_cast<uint32_t>(ks & 0xffffffffu);
+            int a, b;
+            if (id >= (1u << 24)) {
+                const uint32_t pr = s_pairs[id - (1u << 24)];
+                a = pr & 0xffff;
+                b = pr >> 16;
+            } else {
+                const uint4 blk = s_pblk[id / 64];
+                const uint32_t r = id % 64;
+                a = blk.x + r / 8;
+                b = blk.z + r % 8;
+            }
+            const float4 ca = s_cent[h * M + a], cb = s_cent[h * M + b];
+            const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+            const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+            const float inv = dist > 0.f ? 1.f / dist : 0.f;
+            const float nx = ex * inv, ny = ey * inv, nz = ez * inv;
+            add_point_grad(fr, s_slink[a], ca.x, ca.y, ca.z, -nx, -ny, -nz, pb.w_coll, gth);
+            add_point_grad(fr, s_slink[b], cb.x, cb.y, cb.z, nx, ny, nz, pb.w_coll, gth);
+        }
+        s_cost[h] += pb.w_coll * (dself + dworld);
+#pragma unroll
+        for (int k = 0; k < kMaxDof; ++k)
+            if (k < d) s_gth[h * d + k] = gth[k];
+    }
+    __syncthreads();
+
+    // ---- reverse scans (adjoint of Eq. 7) per joint; dC/du overwrites u
+    for (int j = tid; j < d; j += nt) {
+        float s1 = 0.f, s2 = 0.f;
+        for (int h = H - 1; h >= 0; --h) {
+            const float g = s_gpow[h];
+            s1 = fmaf(g, s_gth[h * d + j], s1);
+            const float tv = fmaf(s_dt[h], s1, g * s_gthd[h * d + j]);
+            s2 += tv;
+            float gu = g * s_gu[h * d + j];
+            if (h + 1 < H) gu = fmaf(s_gpow[h + 1], s_gup[(h + 1) * d + j], gu);
+            s_u[h * d + j] = fmaf(s_dt[h], s2, gu);
+        }
+    }
+    __syncthreads();
+
+    // ---- this particle's row of partials: dC_n/du_n (zero for null particles), C_n
+    float* row = part + static_cast<size_t>(n) * (HD + 1);
+    for (int o = tid; o < HD; o += nt) row[o] = (n >= pb.n_null) ? s_u[o] : 0.f;
+    if (tid == 0) {
+        float C = 0.f;
+        for (int h = 0; h < H; ++h) C = fmaf(s_gpow[h], s_cost[h], C);
+        row[HD] = C;
+        if (Ctot) Ctot[n] = C;
+    }
+}
+
+// Column sums of the partial rows in a fixed order: block o < H*d gives
+// grad[o] = (1/N) sum_n dC_n/du_n[o] (and with eta != 0 steps mu[o] by
+// -eta grad[o]); block H*d gives J = (1/N) sum_n C_n.  With `finalize` the
+// step ends here: next_command from the refined mean and the step counter.
+__global__ void __launch_bounds__(128)
+k_adjoint_reduce(Problem pb, const float* __restrict__ part, float* __restrict__ grad_out,
+                 float* __restrict__ J_out, float eta, StepState* st, float* __restrict__ cmd_out,
+                 int finalize)
+{
+    __shared__ float sh[32];
+    const int HD = pb.H * pb.d, o = blockIdx.x;
+    float acc = 0.f;
+    for (int n = threadIdx.x; n < pb.N; n += blockDim.x) acc += part[static_cast<size_t>(n) * (HD + 1) + o];
+    const float tot = block_sum(acc, sh) / static_cast<float>(pb.N);
+    if (threadIdx.x != 0) return;
+    if (o < HD) {
+        if (grad_out) grad_out[o] = tot;
+        if (eta != 0.f) {
+            const float m = pb.mu[o] - eta * tot;
+            pb.mu[o] = m;
+            if (finalize && o < pb.d) cmd_out[o] = m;
+        } else if (finalize && o < pb.d) {
+            cmd_out[o] = pb.mu[o];
+        }
+    } else {
+        if (J_out) *J_out = tot;
+        if (finalize) st->step += 1;
+    }
+}

@@ -85,6 +85,8 @@ class Params:
     qdd_max: float = 2.0
     seed: int = 0
     instance: int = 0
+    grad_steps: int = 0
+    grad_eta: float = 0.0
 
     def replace(self, **kw) -> "Params":
         p = dataclasses.replace(self, **kw)
@@ -214,3 +216,12 @@ def config_paper(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
                w_coll=1000.0, w_smooth=0.0, seed=2000 + seed)
     return Workload(f"storm_{N}x{H}_7dof_k3_spline6", robot, world, p, make_state(seed, 7),
                     make_goal(seed))
+
+
+def config_differentiable(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
+    """Differentiable rollout: the paper-scale step followed by 5 gradient steps on
+    the mean, mu <- mu - 0.01 dJ/dmu, J the mean discounted rollout cost."""
+    wl = config_paper(seed, N, H)
+    wl.params = wl.params.replace(grad_steps=5, grad_eta=0.01)
+    wl.name = f"storm_{N}x{H}_7dof_k3_spline6_grad5"
+    return wl
