@@ -245,6 +245,57 @@ int storm_get_launch(const storm_handle* h, int* particles_per_cta, int* threads
  * shape.  Waits. */
 int storm_autotune(storm_handle* h, float* best_us);
 
+/* ---------------------------------------------------------------- batched instances */
+
+/* Many independent controllers of uneven sizes (particles, horizon, joints,
+ * obstacles) stepped together: every kernel of a control step is launched
+ * once for the whole batch, with the rollout work cut into tiles that
+ * persistent CTAs deal out across the GPU.  The paper runs one controller;
+ * batching is an added capability.  Instance i computes exactly what a
+ * handle created from robots[i], worlds[i], params[i] computes (its Philox
+ * stream is params[i].seed / params[i].instance). */
+typedef struct storm_batch storm_batch;
+
+#define STORM_MAX_BATCH 4096
+
+/* count in 1..STORM_MAX_BATCH; arrays of `count` descriptions, validated as in
+ * storm_create.  Errors: INVALID_ARG (with the failing instance in
+ * storm_batch_last_error of a NULL batch being unavailable, the message goes
+ * to stderr), CUDA, OOM. */
+int storm_batch_create(int count, const storm_robot* robots, const storm_world* worlds,
+                       const storm_params* params, void* cuda_stream, storm_batch** out);
+void storm_batch_destroy(storm_batch* b);
+const char* storm_batch_last_error(const storm_batch* b);
+
+/* Sizes of the concatenated per-instance buffers: states (sum 3 dof_i floats),
+ * goals (7 count floats), commands (sum dof_i floats). */
+int storm_batch_sizes(const storm_batch* b, int* state_floats, int* cmd_floats);
+
+/* One control step of every instance from host buffers: states = concatenation
+ * of each instance's 3 x dof_i state, goals = count x 7, cmds (out) =
+ * concatenation of the dof_i commands, statuses (out, nullable) = count
+ * storm_status values.  Waits.  Errors: INVALID_ARG, NONFINITE, CUDA. */
+int storm_batch_step(storm_batch* b, const float* states, const float* goals, float* cmds,
+                     int* statuses);
+
+/* The same step on the inputs already in the batch's device buffers (the last
+ * storm_batch_step's, or written through storm_batch_device_io); enqueued, no
+ * copies, no wait. */
+int storm_batch_step_resident(storm_batch* b);
+int storm_batch_device_io(storm_batch* b, float** states_dev, float** goals_dev, float** cmds_dev);
+int storm_batch_sync(storm_batch* b);
+
+/* Host copies of instance i's mu (H_i x dof_i) and sigma (dof_i); waits. */
+int storm_batch_get_distribution(storm_batch* b, int i, float* mean, float* sigma);
+int storm_batch_set_distribution(storm_batch* b, int i, const float* mean, const float* sigma);
+
+/* Autotuner of the batched rollout: for (particle, step) items per tile of 32,
+ * 48, 64, 96, 128 and 128 / 256 / 512 threads per CTA, rebuilds the tile list
+ * and times the batched rollout kernel with CUDA events on the batch's inputs,
+ * keeps the fastest and re-captures the step graph.  Waits. */
+int storm_batch_autotune(storm_batch* b, float* best_us);
+int storm_batch_get_launch(const storm_batch* b, int* items_per_tile, int* threads);
+
 /* ---------------------------------------------------------------- checkpoint */
 
 /* Serialise mu, sigma and the step counter (the Philox key is fixed by the

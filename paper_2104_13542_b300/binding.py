@@ -37,7 +37,10 @@ EXPORTED = [
     "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
     "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
     "storm_set_state", "storm_rollout_costs_noalloc", "storm_set_launch", "storm_get_launch",
-    "storm_autotune", "storm_cost_grad",
+    "storm_autotune", "storm_cost_grad", "storm_batch_create", "storm_batch_destroy",
+    "storm_batch_last_error", "storm_batch_sizes", "storm_batch_step", "storm_batch_step_resident",
+    "storm_batch_device_io", "storm_batch_sync", "storm_batch_get_distribution",
+    "storm_batch_set_distribution", "storm_batch_autotune", "storm_batch_get_launch",
 ]
 
 
@@ -127,6 +130,22 @@ def lib():
         L.storm_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.storm_autotune.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_cost_grad.argtypes = [vp, vp, vp, vp, C.c_uint32, C.c_int, vp, vp, vp]
+        ip = C.POINTER(C.c_int)
+        L.storm_batch_create.argtypes = [C.c_int, C.POINTER(storm_robot), C.POINTER(storm_world),
+                                         C.POINTER(storm_params), vp, C.POINTER(vp)]
+        L.storm_batch_destroy.argtypes = [vp]
+        L.storm_batch_destroy.restype = None
+        L.storm_batch_last_error.argtypes = [vp]
+        L.storm_batch_last_error.restype = C.c_char_p
+        L.storm_batch_sizes.argtypes = [vp, ip, ip]
+        L.storm_batch_step.argtypes = [vp, _fp, _fp, _fp, ip]
+        L.storm_batch_step_resident.argtypes = [vp]
+        L.storm_batch_device_io.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+        L.storm_batch_sync.argtypes = [vp]
+        L.storm_batch_get_distribution.argtypes = [vp, C.c_int, _fp, _fp]
+        L.storm_batch_set_distribution.argtypes = [vp, C.c_int, _fp, _fp]
+        L.storm_batch_autotune.argtypes = [vp, C.POINTER(C.c_float)]
+        L.storm_batch_get_launch.argtypes = [vp, ip, ip]
         _lib = L
     return _lib
 
@@ -439,3 +458,89 @@ def storm_cost(mean, controller, state_dev, goal_dev, step: int = 0, it: int = 0
     if _StormCost is None:
         _StormCost = _storm_cost_function()
     return _StormCost.apply(mean, controller, state_dev, goal_dev, step, it)
+
+
+class BatchController:
+    """Many uneven controllers stepped together (storm_batch_* C ABI)."""
+
+    def __init__(self, robots, worlds, params, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("STORM batch needs a CUDA device")
+        self.torch = torch
+        n = len(robots)
+        self.n = n
+        self.dofs = [int(r.dh.shape[0]) for r in robots]
+        self.shapes = [(int(p.H), int(r.dh.shape[0])) for r, p in zip(robots, params)]
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        m = _Marshal()
+        R = (storm_robot * n)(*[m.robot(r) for r in robots])
+        Wd = (storm_world * n)(*[m.world(w) for w in worlds])
+        P = (storm_params * n)(*[m.params(p) for p in params])
+        h = C.c_void_p()
+        rc = lib().storm_batch_create(n, R, Wd, P, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise StormError(rc, "storm_batch_create failed (see stderr)")
+        self.h = h
+        a, b = C.c_int(), C.c_int()
+        lib().storm_batch_sizes(self.h, C.byref(a), C.byref(b))
+        self.state_floats, self.cmd_floats = a.value, b.value
+
+    def _check(self, rc):
+        if rc < 0:
+            raise StormError(rc, lib().storm_batch_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().storm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, states, goals):
+        """states: list of (3, dof_i) arrays; goals: (n, 7) -> (list of cmds, statuses)."""
+        st = _f32(np.concatenate([np.asarray(s, np.float32).reshape(-1) for s in states]))
+        g = _f32(goals).reshape(-1)
+        cmds = np.zeros(self.cmd_floats, dtype=np.float32)
+        statuses = np.zeros(self.n, dtype=np.int32)
+        self._check(lib().storm_batch_step(self.h, _p(st, _fp), _p(g, _fp), _p(cmds, _fp),
+                                           statuses.ctypes.data_as(C.POINTER(C.c_int))))
+        out, o = [], 0
+        for d in self.dofs:
+            out.append(cmds[o:o + d].copy())
+            o += d
+        return out, statuses
+
+    def step_resident(self):
+        self._check(lib().storm_batch_step_resident(self.h))
+
+    def sync(self):
+        self._check(lib().storm_batch_sync(self.h))
+
+    def get_distribution(self, i):
+        H, d = self.shapes[i]
+        mu = np.zeros((H, d), dtype=np.float32)
+        sg = np.zeros(d, dtype=np.float32)
+        self._check(lib().storm_batch_get_distribution(self.h, i, _p(mu, _fp), _p(sg, _fp)))
+        return mu, sg
+
+    def autotune(self):
+        t = C.c_float()
+        self._check(lib().storm_batch_autotune(self.h, C.byref(t)))
+        return t.value
+
+    def get_launch(self):
+        a, b = C.c_int(), C.c_int()
+        self._check(lib().storm_batch_get_launch(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value

@@ -558,10 +558,10 @@ __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
 // over h in fixed order into the per-joint sigma (Eq. 5) and, at the last
 // iteration of a step, writes next_command and advances the step counter.
 // All reductions run in a fixed order: results are bitwise reproducible.
-__global__ void __launch_bounds__(kUpdateThreads)
-k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
-         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out,
-         int finalize, UpdateScratch* scr)
+__device__ __forceinline__ void update_row(const Problem& pb, const float* __restrict__ C,
+                                           const float* __restrict__ u, float* __restrict__ weights_out,
+                                           StepState* st, float* __restrict__ cmd_out, int finalize,
+                                           UpdateScratch* scr, int h, unsigned int rows)
 {
     extern __shared__ __align__(16) float s_w[];  // N weights
     __shared__ float s_redf[32];
@@ -569,7 +569,7 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
     __shared__ float s_acc[kMaxDof][33];
     __shared__ float s_mu[kMaxDof];
     __shared__ int s_last;
-    const int N = pb.N, d = pb.d, O = pb.H * pb.d, h = blockIdx.x;
+    const int N = pb.N, d = pb.d, O = pb.H * pb.d;
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
 
     // ---- min finite cost and its lowest index
@@ -670,7 +670,7 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
     // ---- the last CTA to finish combines the rows
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&scr->count, 1u) == gridDim.x - 1);
+    if (tid == 0) s_last = (atomicAdd(&scr->count, 1u) == rows - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -705,6 +705,14 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
     if (tid == 0) scr->count = 0;
 }
 
+__global__ void __launch_bounds__(kUpdateThreads)
+k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
+         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out,
+         int finalize, UpdateScratch* scr)
+{
+    update_row(pb, C, u, weights_out, st, cmd_out, finalize, scr, blockIdx.x, gridDim.x);
+}
+
 #include "storm_adjoint.cuh"
 
 // Raw noise of sample_controls: one thread per Philox block (4 values).
@@ -729,7 +737,7 @@ __global__ void k_noise(Problem pb, uint32_t step, int iter, float* __restrict__
 
 // shift (Algorithm 1): mu_h <- mu_{h+1}, mu_{H-1} <- 0.  As the first node of a
 // step it also clears the step status and skips the shift at step 0.
-__global__ void k_shift(Problem pb, StepState* st, int force)
+__device__ __forceinline__ void shift_body(const Problem& pb, StepState* st, int force)
 {
     const int O = pb.H * pb.d, d = pb.d;
     const bool do_shift = force || st->step > 0;
@@ -749,6 +757,8 @@ __global__ void k_shift(Problem pb, StepState* st, int force)
     }
     if (threadIdx.x == 0 && !force) st->status = 0;
 }
+
+__global__ void k_shift(Problem pb, StepState* st, int force) { shift_body(pb, st, force); }
 
 // Batched forward kinematics (Eq. 8): one thread per configuration.
 __global__ void k_fk(Problem pb, const float* __restrict__ theta, int count, float* __restrict__ ee)
@@ -881,6 +891,73 @@ __global__ void k_halton(int N, int S, int d, const int* prime, float* out)
         k /= b;
     }
     out[i] = static_cast<float>(normcdfinv(static_cast<double>(num) / static_cast<double>(den)));
+}
+
+// ============================================================================ batched instances
+
+// One controller of a batch, as the batched kernels see it (device memory).
+struct BatchInstance {
+    Problem pb;
+    float* u;             // N x H x d
+    float* C;             // N
+    const float* state;   // 3 x d
+    const float* goal;    // 7
+    float* cmd;           // d
+    StepState* st;
+    UpdateScratch* upd;
+    int K;
+    int pad[3];
+};
+
+struct BatchTile {
+    int inst, n0, np, pad;
+};
+
+__device__ __forceinline__ void load_problem(const Problem& src, Problem& dst)
+{
+    const int* a = reinterpret_cast<const int*>(&src);
+    int* b = reinterpret_cast<int*>(&dst);
+    for (int k = threadIdx.x; k < static_cast<int>(sizeof(Problem) / 4); k += blockDim.x) b[k] = a[k];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) k_shift_batch(const BatchInstance* __restrict__ insts)
+{
+    __shared__ Problem s_pb;
+    const BatchInstance& I = insts[blockIdx.x];
+    load_problem(I.pb, s_pb);
+    shift_body(s_pb, I.st, 0);
+}
+
+// Rollout tiles of every instance; persistent CTAs stride over the tile list
+// (sorted by decreasing work, so the stride deals the big tiles first).
+__global__ void __launch_bounds__(kMaxThreads)
+k_rollout_batch(const BatchInstance* __restrict__ insts, const BatchTile* __restrict__ tiles,
+                int n_tiles, int iter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Problem s_pb;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const BatchTile tile = tiles[t];
+        const BatchInstance& I = insts[tile.inst];
+        if (iter >= I.K) continue;
+        load_problem(I.pb, s_pb);
+        RolloutOut out{I.u, nullptr, nullptr, nullptr, nullptr, nullptr, I.C};
+        rollout_particles(s_pb, out, I.state, I.goal, I.st->step, iter, tile.n0, tile.np, smem);
+        __syncthreads();
+    }
+}
+
+// Distribution update of every instance: one CTA per (instance, horizon step).
+__global__ void __launch_bounds__(kUpdateThreads)
+k_update_batch(const BatchInstance* __restrict__ insts, const int2* __restrict__ rows, int iter)
+{
+    __shared__ Problem s_pb;
+    const int2 r = rows[blockIdx.x];
+    const BatchInstance& I = insts[r.x];
+    if (iter >= I.K) return;
+    load_problem(I.pb, s_pb);
+    update_row(s_pb, I.C, I.u, nullptr, I.st, I.cmd, iter == I.K - 1, I.upd, r.y, s_pb.H);
 }
 
 // ============================================================================ host runtime
@@ -1220,19 +1297,22 @@ void build_pair_blocks(const std::vector<uint32_t>& pairs, const std::vector<int
     }
 }
 
-int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, const storm_params* p,
-                void* stream)
-{
-    CK(cudaGetDevice(&h->device));
-    if (stream) {
-        h->stream = static_cast<cudaStream_t>(stream);
-    } else {
-        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
-        h->own_stream = true;
-    }
-    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+// Host-side tables of one problem, before upload.
+struct HostTables {
+    std::vector<float> sph, boxes, wsph;
+    std::vector<int> first;
+    std::vector<uint32_t> pairs;
+    std::vector<uint4> blocks;
+    std::vector<double> raw;  // dh | q_min | q_max | dt, read by the set-up kernel
+    double k_jl = 0, qdd_max = 0, gamma = 0;
+};
 
-    Problem& pb = h->pb;
+// Scalars of the problem and its host tables: spheres sorted by link (stable),
+// pairs remapped to that order and grouped into link-pair blocks.
+void fill_problem(const storm_robot* r, const storm_world* w, const storm_params* p, Problem& pb,
+                  HostTables& ht)
+{
+    pb = Problem{};
     pb.N = p->N;
     pb.H = p->H;
     pb.d = r->dof;
@@ -1242,7 +1322,6 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     pb.n_null = p->n_null;
     pb.rot_mode = p->rot_mode;
     pb.M = r->n_spheres;
-    pb.P = r->n_pairs;
     pb.B = w->n_boxes;
     pb.O = w->n_spheres;
     pb.beta = static_cast<float>(p->beta);
@@ -1264,55 +1343,54 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     pb.seed_lo = static_cast<uint32_t>(p->seed & 0xffffffffu);
     pb.seed_hi = static_cast<uint32_t>(p->seed >> 32);
     pb.instance = p->instance;
-    h->K = p->K;
-    h->grad_steps = p->grad_steps;
-    h->grad_eta = static_cast<float>(p->grad_eta);
-    h->sigma_init = p->sigma_init;
-    h->cap_boxes = STORM_MAX_OBSTACLES;
-    h->cap_wsph = STORM_MAX_OBSTACLES;
-
-    // particles per CTA: about 64 (particle, step) items, never above the CTA size
+    // particles per CTA: about 64 (particle, step) items
     pb.ppc = std::max(1, std::min(pb.N, 64 / pb.H));
-    h->grid = (pb.N + pb.ppc - 1) / pb.ppc;
 
-    // spheres sorted by link (stable); pairs remapped to the sorted order
     std::vector<int> order(pb.M);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return r->sphere_link[a] < r->sphere_link[b]; });
     std::vector<int> rank(pb.M);
     for (int i = 0; i < pb.M; ++i) rank[order[i]] = i;
-    std::vector<float> sph(4 * std::max(pb.M, 1));
-    std::vector<int> first(pb.d + 2, 0);
+    ht.sph.assign(4 * std::max(pb.M, 1), 0.f);
+    ht.first.assign(pb.d + 2, 0);
     for (int i = 0; i < pb.M; ++i) {
-        for (int k = 0; k < 4; ++k) sph[4 * i + k] = static_cast<float>(r->spheres[4 * order[i] + k]);
-        first[r->sphere_link[order[i]] + 1]++;
+        for (int k = 0; k < 4; ++k) ht.sph[4 * i + k] = static_cast<float>(r->spheres[4 * order[i] + k]);
+        ht.first[r->sphere_link[order[i]] + 1]++;
     }
-    for (int f = 0; f <= pb.d; ++f) first[f + 1] += first[f];
-    std::vector<uint32_t> all_pairs(pb.P);
-    for (int k = 0; k < pb.P; ++k) {
+    for (int f = 0; f <= pb.d; ++f) ht.first[f + 1] += ht.first[f];
+    std::vector<uint32_t> all_pairs(r->n_pairs);
+    for (int k = 0; k < r->n_pairs; ++k) {
         uint32_t a = rank[r->pairs[2 * k]], b = rank[r->pairs[2 * k + 1]];
         if (a > b) std::swap(a, b);
         all_pairs[k] = a | (b << 16);
     }
-    std::vector<uint4> blocks;
-    std::vector<uint32_t> pairs;
-    build_pair_blocks(all_pairs, first, pb.d, blocks, pairs);
-    pb.P = static_cast<int>(pairs.size());
-    pb.NPB = static_cast<int>(blocks.size());
-    pairs.resize(std::max(pb.P, 1));
-    blocks.resize(std::max(pb.NPB, 1));
+    ht.blocks.clear();
+    ht.pairs.clear();
+    build_pair_blocks(all_pairs, ht.first, pb.d, ht.blocks, ht.pairs);
+    pb.P = static_cast<int>(ht.pairs.size());
+    pb.NPB = static_cast<int>(ht.blocks.size());
+    ht.pairs.resize(std::max(pb.P, 1));
+    ht.blocks.resize(std::max(pb.NPB, 1));
+    ht.boxes.assign(6 * std::max(pb.B, 1), 0.f);
+    ht.wsph.assign(4 * std::max(pb.O, 1), 0.f);
+    for (int i = 0; i < 6 * pb.B; ++i) ht.boxes[i] = static_cast<float>(w->boxes[i]);
+    for (int i = 0; i < 4 * pb.O; ++i) ht.wsph[i] = static_cast<float>(w->spheres[i]);
+    ht.raw.clear();
+    ht.raw.insert(ht.raw.end(), r->dh, r->dh + 4 * pb.d);
+    ht.raw.insert(ht.raw.end(), r->q_min, r->q_min + pb.d);
+    ht.raw.insert(ht.raw.end(), r->q_max, r->q_max + pb.d);
+    ht.raw.insert(ht.raw.end(), p->dt, p->dt + pb.H);
+    ht.k_jl = p->k_jl;
+    ht.qdd_max = p->qdd_max;
+    ht.gamma = p->gamma;
+}
 
-    // raw doubles for the set-up kernel: dh | q_min | q_max | dt
-    std::vector<double> raw;
-    raw.insert(raw.end(), r->dh, r->dh + 4 * pb.d);
-    raw.insert(raw.end(), r->q_min, r->q_min + pb.d);
-    raw.insert(raw.end(), r->q_max, r->q_max + pb.d);
-    raw.insert(raw.end(), p->dt, p->dt + pb.H);
-
-    const TablePlan t = plan_tables(pb, h->cap_boxes, h->cap_wsph, static_cast<int>(raw.size()));
-    CK(cudaMalloc(&h->d_tables, t.total));
-    char* base = static_cast<char*>(h->d_tables);
+// Point the problem's tables into `base` (laid out by `t`), copy the host tables
+// and enqueue the set-up kernels (derived tables, Halton noise).
+cudaError_t upload_problem(Problem& pb, const HostTables& ht, char* base, const TablePlan& t,
+                           cudaStream_t s)
+{
     pb.dhx = reinterpret_cast<float*>(base + t.dhx);
     pb.qlo = reinterpret_cast<float*>(base + t.qlo);
     pb.qhi = reinterpret_cast<float*>(base + t.qhi);
@@ -1331,7 +1409,57 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     pb.sigma = reinterpret_cast<float*>(base + t.sigma);
     int* d_prime = reinterpret_cast<int*>(base + t.prime);
     double* d_raw = reinterpret_cast<double*>(base + t.raw);
+    cudaError_t e = cudaSuccess;
+    auto put = [&](const void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    put(pb.sph, ht.sph.data(), 4 * ht.sph.size());
+    put(pb.link_first, ht.first.data(), 4 * ht.first.size());
+    put(pb.pairs, ht.pairs.data(), 4 * ht.pairs.size());
+    put(pb.pblk, ht.blocks.data(), 16 * ht.blocks.size());
+    put(pb.boxes, ht.boxes.data(), 4 * ht.boxes.size());
+    put(pb.wsph, ht.wsph.data(), 4 * ht.wsph.size());
+    put(d_raw, ht.raw.data(), 8 * ht.raw.size());
+    if (e != cudaSuccess) return e;
+    InitArgs ia{d_raw, d_raw + 4 * pb.d, d_raw + 5 * pb.d, d_raw + 6 * pb.d, ht.k_jl, ht.qdd_max,
+                ht.gamma};
+    k_init_tables<<<1, 64, 0, s>>>(pb, ia);
+    if (pb.sampler == STORM_SAMPLER_HALTON) {
+        const int D = pb.S * pb.d;
+        k_primes<<<(D + 127) / 128, 128, 0, s>>>(D, d_prime);
+        const size_t total = size_t(pb.N) * pb.S * pb.d;
+        k_halton<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+            pb.N, pb.S, pb.d, d_prime, const_cast<float*>(pb.halton));
+    }
+    return cudaGetLastError();
+}
 
+int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, const storm_params* p,
+                void* stream)
+{
+    CK(cudaGetDevice(&h->device));
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+
+    HostTables ht;
+    Problem& pb = h->pb;
+    fill_problem(r, w, p, pb, ht);
+    h->K = p->K;
+    h->grad_steps = p->grad_steps;
+    h->grad_eta = static_cast<float>(p->grad_eta);
+    h->sigma_init = p->sigma_init;
+    h->cap_boxes = STORM_MAX_OBSTACLES;
+    h->cap_wsph = STORM_MAX_OBSTACLES;
+    h->grid = (pb.N + pb.ppc - 1) / pb.ppc;
+
+    const TablePlan t = plan_tables(pb, h->cap_boxes, h->cap_wsph, static_cast<int>(ht.raw.size()));
+    CK(cudaMalloc(&h->d_tables, t.total));
     CK(cudaMalloc(&h->d_u, sizeof(float) * size_t(pb.N) * pb.H * pb.d));
     CK(cudaMalloc(&h->d_C, sizeof(float) * pb.N));
     CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
@@ -1341,39 +1469,14 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     CK(cudaMemsetAsync(h->d_upd, 0, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d, h->stream));
     std::memset(h->h_io, 0, sizeof(float) * io_floats(pb));
     h->d_st = reinterpret_cast<StepState*>(h->d_io + io_st(pb));
-
-    CK(cudaMemcpyAsync(const_cast<float4*>(pb.sph), sph.data(), 16 * std::max(pb.M, 1),
-                       cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(const_cast<int*>(pb.link_first), first.data(), 4 * (pb.d + 2),
-                       cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(const_cast<uint32_t*>(pb.pairs), pairs.data(), 4 * std::max(pb.P, 1),
-                       cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(const_cast<uint4*>(pb.pblk), blocks.data(), 16 * std::max(pb.NPB, 1),
-                       cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(d_raw, raw.data(), 8 * raw.size(), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(h->d_io, 0, sizeof(float) * io_floats(pb), h->stream));
-    int rc = upload_world(h, w);
-    if (rc) return rc;
-
-    InitArgs ia{d_raw, d_raw + 4 * pb.d, d_raw + 5 * pb.d, d_raw + 6 * pb.d, p->k_jl, p->qdd_max,
-                p->gamma};
-    k_init_tables<<<1, 64, 0, h->stream>>>(pb, ia);
-    CK(cudaGetLastError());
-    if (pb.sampler == STORM_SAMPLER_HALTON) {
-        const int D = pb.S * pb.d;
-        k_primes<<<(D + 127) / 128, 128, 0, h->stream>>>(D, d_prime);
-        CK(cudaGetLastError());
-        const size_t total = size_t(pb.N) * pb.S * pb.d;
-        k_halton<<<static_cast<unsigned>((total + 255) / 256), 256, 0, h->stream>>>(
-            pb.N, pb.S, pb.d, d_prime, const_cast<float*>(pb.halton));
-        CK(cudaGetLastError());
-    }
+    CK(upload_problem(pb, ht, static_cast<char*>(h->d_tables), t, h->stream));
 
     const RolloutLayout L = rollout_layout(pb);
     h->rollout_smem = L.bytes;
     h->update_smem = sizeof(float) * ((pb.N + 3) & ~3);
     h->adjoint_smem = adjoint_layout(pb).bytes;
-    rc = allow_smem(h);
+    int rc = allow_smem(h);
     if (rc) return rc;
     rc = storm_reset(h);
     if (rc) return rc;
@@ -1947,3 +2050,430 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
     }
     return STORM_OK;
 }
+
+// ============================================================================ batch host runtime
+
+struct storm_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    bool own_stream = false;
+    int n = 0, Kmax = 1;
+    int threads = kThreads, items = 64;
+    std::vector<BatchInstance> inst;  // host mirror of d_inst
+    std::vector<int> dof, state_off, cmd_off;
+    std::vector<double> sigma_init;
+    int state_floats = 0, cmd_floats = 0;
+    void* arena = nullptr;
+    BatchInstance* d_inst = nullptr;
+    BatchTile* d_tiles = nullptr;
+    int2* d_rows = nullptr;
+    int n_tiles = 0, n_rows = 0, grid = 0;
+    float* d_in = nullptr;   // states | goals
+    float* d_out = nullptr;  // cmds | StepState x n
+    float* h_in = nullptr;
+    float* h_out = nullptr;
+    size_t rollout_smem = 0, update_smem = 0;
+    cudaGraphExec_t g_host = nullptr, g_dev = nullptr;
+    std::string err = "no error";
+};
+
+namespace {
+
+#define BK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            (void)cudaGetLastError();                                             \
+            b->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return e_ == cudaErrorMemoryAllocation ? STORM_ERR_OOM : STORM_ERR_CUDA; \
+        }                                                                         \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t out_st_offset(const storm_batch* b) { return align256(sizeof(float) * b->cmd_floats); }
+
+// Tiles of `items` (particle, step) work items per CTA, largest first.
+int batch_tiles(storm_batch* b, int items, std::vector<BatchTile>& tiles, size_t& smem)
+{
+    tiles.clear();
+    smem = 0;
+    std::vector<std::pair<double, BatchTile>> w;
+    for (int i = 0; i < b->n; ++i) {
+        Problem pb = b->inst[i].pb;
+        pb.ppc = std::max(1, std::min(pb.N, items / pb.H));
+        b->inst[i].pb.ppc = pb.ppc;
+        smem = std::max(smem, static_cast<size_t>(rollout_layout(pb).bytes));
+        const double per_item = 100.0 + pb.M * (pb.B + pb.O) + 49.0 * pb.NPB + pb.P;
+        for (int n0 = 0; n0 < pb.N; n0 += pb.ppc) {
+            const int np = std::min(pb.ppc, pb.N - n0);
+            w.push_back({np * pb.H * per_item, BatchTile{i, n0, np, 0}});
+        }
+    }
+    std::stable_sort(w.begin(), w.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    for (auto& e : w) tiles.push_back(e.second);
+    return STORM_OK;
+}
+
+int batch_apply_launch(storm_batch* b, int items, int threads)
+{
+    std::vector<BatchTile> tiles;
+    size_t smem = 0;
+    batch_tiles(b, items, tiles, smem);
+    int optin = 0, sms = 0;
+    BK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    cudaFuncAttributes fa;
+    BK(cudaFuncGetAttributes(&fa, k_rollout_batch));
+    if (smem + fa.sharedSizeBytes > size_t(optin)) {
+        b->err = "tile shape needs too much shared memory";
+        return STORM_ERR_INVALID_ARG;
+    }
+    BK(cudaFuncSetAttribute(k_rollout_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(fa.sharedSizeBytes)));
+    int per_sm = 0;
+    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rollout_batch, threads, smem));
+    if (per_sm < 1) {
+        b->err = "tile shape does not fit an SM";
+        return STORM_ERR_INVALID_ARG;
+    }
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    BK(cudaMalloc(&b->d_tiles, sizeof(BatchTile) * tiles.size()));
+    BK(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(),
+                       cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInstance) * b->n,
+                       cudaMemcpyHostToDevice, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    b->n_tiles = static_cast<int>(tiles.size());
+    b->grid = std::min(b->n_tiles, per_sm * sms);
+    b->rollout_smem = smem;
+    b->items = items;
+    b->threads = threads;
+    return STORM_OK;
+}
+
+int batch_enqueue(storm_batch* b, cudaStream_t s)
+{
+    k_shift_batch<<<b->n, 128, 0, s>>>(b->d_inst);
+    BK(cudaGetLastError());
+    for (int k = 0; k < b->Kmax; ++k) {
+        k_rollout_batch<<<b->grid, b->threads, b->rollout_smem, s>>>(b->d_inst, b->d_tiles,
+                                                                    b->n_tiles, k);
+        BK(cudaGetLastError());
+        k_update_batch<<<b->n_rows, kUpdateThreads, b->update_smem, s>>>(b->d_inst, b->d_rows, k);
+        BK(cudaGetLastError());
+    }
+    return STORM_OK;
+}
+
+void batch_destroy_graphs(storm_batch* b)
+{
+    if (b->g_dev) cudaGraphExecDestroy(b->g_dev);
+    if (b->g_host) cudaGraphExecDestroy(b->g_host);
+    b->g_dev = b->g_host = nullptr;
+}
+
+int batch_build_graphs(storm_batch* b)
+{
+    batch_destroy_graphs(b);
+    for (int with_io = 0; with_io < 2; ++with_io) {
+        cudaGraph_t g = nullptr;
+        BK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = STORM_OK;
+        const size_t in_bytes = sizeof(float) * (b->state_floats + 7 * b->n);
+        const size_t out_bytes = out_st_offset(b) + sizeof(StepState) * b->n;
+        if (with_io && cudaMemcpyAsync(b->d_in, b->h_in, in_bytes, cudaMemcpyHostToDevice, b->cap_stream))
+            rc = STORM_ERR_CUDA;
+        if (!rc) rc = batch_enqueue(b, b->cap_stream);
+        if (!rc && with_io &&
+            cudaMemcpyAsync(b->h_out, b->d_out, out_bytes, cudaMemcpyDeviceToHost, b->cap_stream))
+            rc = STORM_ERR_CUDA;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        BK(e);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        BK(e);
+        (with_io ? b->g_host : b->g_dev) = ex;
+    }
+    return STORM_OK;
+}
+
+void batch_free(storm_batch* b)
+{
+    batch_destroy_graphs(b);
+    if (b->arena) cudaFree(b->arena);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_rows) cudaFree(b->d_rows);
+    if (b->d_in) cudaFree(b->d_in);
+    if (b->d_out) cudaFree(b->d_out);
+    if (b->h_in) cudaFreeHost(b->h_in);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+int batch_create_impl(storm_batch* b, int n, const storm_robot* r, const storm_world* w,
+                      const storm_params* p, void* stream)
+{
+    BK(cudaGetDevice(&b->device));
+    if (stream) {
+        b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        BK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    BK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    b->n = n;
+    b->inst.resize(n);
+    std::vector<HostTables> ht(n);
+    std::vector<TablePlan> plans(n);
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        BatchInstance& I = b->inst[i];
+        I = BatchInstance{};
+        fill_problem(r + i, w + i, p + i, I.pb, ht[i]);
+        I.K = p[i].K;
+        b->Kmax = std::max(b->Kmax, I.K);
+        b->dof.push_back(r[i].dof);
+        b->sigma_init.push_back(p[i].sigma_init);
+        b->state_off.push_back(b->state_floats);
+        b->cmd_off.push_back(b->cmd_floats);
+        b->state_floats += 3 * r[i].dof;
+        b->cmd_floats += r[i].dof;
+        plans[i] = plan_tables(I.pb, std::max(I.pb.B, 1), std::max(I.pb.O, 1),
+                               static_cast<int>(ht[i].raw.size()));
+        off[i] = total;
+        const Problem& pb = I.pb;
+        total += align256(plans[i].total) + align256(sizeof(float) * size_t(pb.N) * pb.H * pb.d) +
+                 align256(sizeof(float) * pb.N) +
+                 align256(sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d);
+        b->update_smem = std::max(b->update_smem, sizeof(float) * ((pb.N + 3) & ~size_t(3)));
+    }
+    BK(cudaMalloc(&b->arena, total));
+    BK(cudaMemsetAsync(b->arena, 0, total, b->stream));
+    const size_t out_bytes = out_st_offset(b) + sizeof(StepState) * n;
+    BK(cudaMalloc(&b->d_in, sizeof(float) * (b->state_floats + 7 * n)));
+    BK(cudaMalloc(&b->d_out, out_bytes));
+    BK(cudaMallocHost(&b->h_in, sizeof(float) * (b->state_floats + 7 * n)));
+    BK(cudaMallocHost(&b->h_out, out_bytes));
+    BK(cudaMemsetAsync(b->d_in, 0, sizeof(float) * (b->state_floats + 7 * n), b->stream));
+    BK(cudaMemsetAsync(b->d_out, 0, out_bytes, b->stream));
+    StepState* st = reinterpret_cast<StepState*>(reinterpret_cast<char*>(b->d_out) + out_st_offset(b));
+    std::vector<int2> rows;
+    for (int i = 0; i < n; ++i) {
+        BatchInstance& I = b->inst[i];
+        char* base = static_cast<char*>(b->arena) + off[i];
+        BK(upload_problem(I.pb, ht[i], base, plans[i], b->stream));
+        char* q = base + align256(plans[i].total);
+        I.u = reinterpret_cast<float*>(q);
+        q += align256(sizeof(float) * size_t(I.pb.N) * I.pb.H * I.pb.d);
+        I.C = reinterpret_cast<float*>(q);
+        q += align256(sizeof(float) * I.pb.N);
+        I.upd = reinterpret_cast<UpdateScratch*>(q);
+        I.state = b->d_in + b->state_off[i];
+        I.goal = b->d_in + b->state_floats + 7 * i;
+        I.cmd = b->d_out + b->cmd_off[i];
+        I.st = st + i;
+        std::vector<float> sg(I.pb.d, static_cast<float>(p[i].sigma_init));
+        BK(cudaMemcpyAsync(I.pb.sigma, sg.data(), 4 * I.pb.d, cudaMemcpyHostToDevice, b->stream));
+        for (int hh = 0; hh < I.pb.H; ++hh) rows.push_back(make_int2(i, hh));
+    }
+    b->n_rows = static_cast<int>(rows.size());
+    BK(cudaMalloc(&b->d_rows, sizeof(int2) * rows.size()));
+    BK(cudaMemcpyAsync(b->d_rows, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice,
+                       b->stream));
+    BK(cudaMalloc(&b->d_inst, sizeof(BatchInstance) * n));
+    int optin = 0;
+    BK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    cudaFuncAttributes ua;
+    BK(cudaFuncGetAttributes(&ua, k_update_batch));
+    if (b->update_smem + ua.sharedSizeBytes > size_t(optin)) {
+        b->err = "update needs too much shared memory";
+        return STORM_ERR_INVALID_ARG;
+    }
+    BK(cudaFuncSetAttribute(k_update_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(ua.sharedSizeBytes)));
+    const int rc = batch_apply_launch(b, 64, kThreads);
+    if (rc) return rc;
+    return batch_build_graphs(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* storm_batch_last_error(const storm_batch* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+int storm_batch_create(int count, const storm_robot* robots, const storm_world* worlds,
+                       const storm_params* params, void* cuda_stream, storm_batch** out)
+{
+    if (!out) return STORM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 1 || count > STORM_MAX_BATCH || !robots || !worlds || !params)
+        return STORM_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        std::string msg;
+        const int v = validate(robots + i, worlds + i, params + i, msg);
+        if (v) {
+            fprintf(stderr, "storm_batch_create: instance %d: %s\n", i, msg.c_str());
+            return v;
+        }
+    }
+    storm_batch* b = new (std::nothrow) storm_batch();
+    if (!b) return STORM_ERR_OOM;
+    const int rc = batch_create_impl(b, count, robots, worlds, params, cuda_stream);
+    if (rc) {
+        fprintf(stderr, "storm_batch_create: %s\n", b->err.c_str());
+        batch_free(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return STORM_OK;
+}
+
+void storm_batch_destroy(storm_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
+}
+
+int storm_batch_sizes(const storm_batch* b, int* state_floats, int* cmd_floats)
+{
+    if (!b) return STORM_ERR_INVALID_ARG;
+    if (state_floats) *state_floats = b->state_floats;
+    if (cmd_floats) *cmd_floats = b->cmd_floats;
+    return STORM_OK;
+}
+
+int storm_batch_step(storm_batch* b, const float* states, const float* goals, float* cmds,
+                     int* statuses)
+{
+    if (!b || !states || !goals || !cmds) return STORM_ERR_INVALID_ARG;
+    for (int i = 0; i < b->state_floats; ++i)
+        if (!std::isfinite(states[i])) return b->err = "non-finite state", STORM_ERR_NONFINITE;
+    for (int i = 0; i < 7 * b->n; ++i)
+        if (!std::isfinite(goals[i])) return b->err = "non-finite goal", STORM_ERR_NONFINITE;
+    std::memcpy(b->h_in, states, sizeof(float) * b->state_floats);
+    std::memcpy(b->h_in + b->state_floats, goals, sizeof(float) * 7 * b->n);
+    BK(cudaGraphLaunch(b->g_host, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    std::memcpy(cmds, b->h_out, sizeof(float) * b->cmd_floats);
+    const StepState* st =
+        reinterpret_cast<const StepState*>(reinterpret_cast<const char*>(b->h_out) + out_st_offset(b));
+    int worst = STORM_OK;
+    for (int i = 0; i < b->n; ++i) {
+        if (statuses) statuses[i] = st[i].status;
+        worst = std::max(worst, st[i].status);
+    }
+    return worst;
+}
+
+int storm_batch_step_resident(storm_batch* b)
+{
+    if (!b) return STORM_ERR_INVALID_ARG;
+    BK(cudaGraphLaunch(b->g_dev, b->stream));
+    return STORM_OK;
+}
+
+int storm_batch_device_io(storm_batch* b, float** states_dev, float** goals_dev, float** cmds_dev)
+{
+    if (!b) return STORM_ERR_INVALID_ARG;
+    if (states_dev) *states_dev = b->d_in;
+    if (goals_dev) *goals_dev = b->d_in + b->state_floats;
+    if (cmds_dev) *cmds_dev = b->d_out;
+    return STORM_OK;
+}
+
+int storm_batch_sync(storm_batch* b)
+{
+    if (!b) return STORM_ERR_INVALID_ARG;
+    BK(cudaStreamSynchronize(b->stream));
+    return STORM_OK;
+}
+
+int storm_batch_get_distribution(storm_batch* b, int i, float* mean, float* sigma)
+{
+    if (!b || i < 0 || i >= b->n) return STORM_ERR_INVALID_ARG;
+    const Problem& pb = b->inst[i].pb;
+    if (mean) BK(cudaMemcpyAsync(mean, pb.mu, 4 * pb.H * pb.d, cudaMemcpyDeviceToHost, b->stream));
+    if (sigma) BK(cudaMemcpyAsync(sigma, pb.sigma, 4 * pb.d, cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    return STORM_OK;
+}
+
+int storm_batch_set_distribution(storm_batch* b, int i, const float* mean, const float* sigma)
+{
+    if (!b || i < 0 || i >= b->n) return STORM_ERR_INVALID_ARG;
+    const Problem& pb = b->inst[i].pb;
+    if (mean) BK(cudaMemcpyAsync(pb.mu, mean, 4 * pb.H * pb.d, cudaMemcpyHostToDevice, b->stream));
+    if (sigma) BK(cudaMemcpyAsync(pb.sigma, sigma, 4 * pb.d, cudaMemcpyHostToDevice, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    return STORM_OK;
+}
+
+int storm_batch_get_launch(const storm_batch* b, int* items, int* threads)
+{
+    if (!b) return STORM_ERR_INVALID_ARG;
+    if (items) *items = b->items;
+    if (threads) *threads = b->threads;
+    return STORM_OK;
+}
+
+int storm_batch_autotune(storm_batch* b, float* best_us)
+{
+    if (!b) return STORM_ERR_INVALID_ARG;
+    BK(cudaStreamSynchronize(b->stream));
+    const int items_c[] = {32, 48, 64, 96, 128};
+    const int threads_c[] = {128, 256, 512};
+    const int old_items = b->items, old_threads = b->threads;
+    float best = INFINITY;
+    int bi = old_items, bt = old_threads;
+    cudaEvent_t e0, e1;
+    BK(cudaEventCreate(&e0));
+    BK(cudaEventCreate(&e1));
+    for (int it : items_c)
+        for (int th : threads_c) {
+            if (batch_apply_launch(b, it, th) != STORM_OK) continue;
+            std::vector<float> t;
+            for (int r = 0; r < 8; ++r) {
+                cudaEventRecord(e0, b->stream);
+                k_rollout_batch<<<b->grid, b->threads, b->rollout_smem, b->stream>>>(
+                    b->d_inst, b->d_tiles, b->n_tiles, 0);
+                cudaEventRecord(e1, b->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    b->err = "autotune launch failed";
+                    return STORM_ERR_CUDA;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r >= 2) t.push_back(ms * 1e3f);
+            }
+            std::sort(t.begin(), t.end());
+            if (t[t.size() / 2] < best) {
+                best = t[t.size() / 2];
+                bi = it;
+                bt = th;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int rc = batch_apply_launch(b, bi, bt);
+    if (rc) return rc;
+    if (best_us) *best_us = best;
+    return batch_build_graphs(b);
+}
+
+}  // extern "C"

@@ -225,3 +225,26 @@ def config_differentiable(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
     wl.params = wl.params.replace(grad_steps=5, grad_eta=0.01)
     wl.name = f"storm_{N}x{H}_7dof_k3_spline6_grad5"
     return wl
+
+
+def config_batch(seed: int = 0, count: int = 256) -> list:
+    """Batched uneven MPC: `count` independent instances, particles ~ U{64..1024},
+    horizon ~ U{10..50}, 6 or 7 joints, 0..64 obstacles (boxes and spheres), each
+    with its own robot, world, start, goal and Philox stream; one MPPI iteration."""
+    rng = np.random.default_rng([seed, 10])
+    out = []
+    for i in range(count):
+        N = int(rng.integers(64, 1025))
+        H = int(rng.integers(10, 51))
+        dof = int(rng.choice([6, 7]))
+        n_obs = int(rng.integers(0, 65))
+        s = 100_000 + 1000 * seed + i
+        robot = make_robot(s, dof)
+        world = make_world(s, n_boxes=(n_obs + 1) // 2, n_spheres=n_obs // 2)
+        p = Params(N=N, H=H, K=1, n_knots=6, dt=np.full(H, 0.02), beta=10.0, gamma=0.99,
+                   alpha_mu=1.0, alpha_sigma=0.5, sigma_init=0.5, w_pos=150.0, w_rot=20.0,
+                   w_stop=10.0, w_joint=100.0, w_manip=30.0, w_coll=1000.0, w_smooth=0.0,
+                   seed=3000 + seed, instance=i)
+        out.append(Workload(f"batch{i}_{N}x{H}_{dof}dof_{n_obs}obs", robot, world, p,
+                            make_state(s, dof), make_goal(s)))
+    return out

@@ -116,3 +116,19 @@ def test_oracle_and_library_share_nothing():
     for py in ("binding.py", "__init__.py", "workloads.py"):
         src = open(os.path.join(ROOT, "paper_2104_13542_b300", py)).read()
         assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_batch_create_rejects_bad_instance(L):
+    wls = [W.config_paper(0, N=8, H=10), W.config_paper(1, N=8, H=10)]
+    m = binding._Marshal()
+    wls[1].params = wls[1].params.replace(K=0)
+    R = (binding.storm_robot * 2)(*[m.robot(w.robot) for w in wls])
+    Wd = (binding.storm_world * 2)(*[m.world(w.world) for w in wls])
+    P = (binding.storm_params * 2)(*[m.params(w.params) for w in wls])
+    h = C.c_void_p()
+    L.storm_batch_create.argtypes = [C.c_int, C.POINTER(binding.storm_robot),
+                                     C.POINTER(binding.storm_world), C.POINTER(binding.storm_params),
+                                     C.c_void_p, C.POINTER(C.c_void_p)]
+    assert L.storm_batch_create(2, R, Wd, P, None, C.byref(h)) == binding.STORM_ERR_INVALID_ARG
+    assert L.storm_batch_create(0, R, Wd, P, None, C.byref(h)) == binding.STORM_ERR_INVALID_ARG
+    assert h.value is None

@@ -1,0 +1,94 @@
+"""Batched uneven instances: every instance of a batch step equals the same
+instance stepped alone by its own handle (bitwise: the same kernels in another
+launch order), and matches the FP64 oracle within the tolerance model."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_13542_b300 import BatchController, Controller
+from paper_2104_13542_b300 import workloads as W
+
+from gpu_helpers import f32, max_rel, mu_tolerance
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(count, seed=0):
+    wls = W.config_batch(seed, count)
+    # keep the oracle affordable: cap the particle count of the parity batch
+    for wl in wls:
+        wl.params = wl.params.replace(N=min(wl.params.N, 160))
+    return wls
+
+
+def test_batch_equals_individual_handles_bitwise():
+    wls = _batch(10, seed=1)
+    states = [f32(wl.state) for wl in wls]
+    goals = np.stack([f32(wl.goal) for wl in wls])
+    with BatchController([w.robot for w in wls], [w.world for w in wls],
+                         [w.params for w in wls]) as b:
+        steps = [b.step(states, goals) for _ in range(2)]
+        dists = [b.get_distribution(i) for i in range(len(wls))]
+    for i, wl in enumerate(wls):
+        with Controller(wl.robot, wl.world, wl.params) as c:
+            ref = [c.step(states[i], goals[i])[0] for _ in range(2)]
+            mu, sg = c.get_distribution()
+        for t in range(2):
+            assert np.array_equal(steps[t][0][i], ref[t]), (i, t)
+        assert np.array_equal(dists[i][0], mu) and np.array_equal(dists[i][1], sg)
+    assert all(np.all(s[1] == 0) for s in steps)
+
+
+def test_batch_matches_oracle_per_instance():
+    wls = _batch(8, seed=2)
+    states = [f32(wl.state) for wl in wls]
+    goals = np.stack([f32(wl.goal) for wl in wls])
+    with BatchController([w.robot for w in wls], [w.world for w in wls],
+                         [w.params for w in wls]) as b:
+        cmds, st = b.step(states, goals)
+        dists = [b.get_distribution(i) for i in range(len(wls))]
+    for i, wl in enumerate(wls):
+        p = wl.params
+        o = oracle.Oracle(wl.robot, wl.world, p)
+        ocmd, omu, osig, ost, obest = o.step(states[i], goals[i], 0, np.zeros((p.H, wl.robot.dof)),
+                                             np.full(wl.robot.dof, f32(p.sigma_init)))
+        tol = mu_tolerance([obest], p.beta)
+        scale = max(1.0, np.abs(omu).max())
+        assert max_rel(dists[i][0], omu, scale) < tol, (i, wl.name)
+        assert max_rel(cmds[i], ocmd, scale) < tol, (i, wl.name)
+        assert max_rel(dists[i][1], osig, max(1e-3, osig.max())) < tol, (i, wl.name)
+
+
+def test_batch_autotune_keeps_results():
+    wls = _batch(6, seed=3)
+    states = [f32(wl.state) for wl in wls]
+    goals = np.stack([f32(wl.goal) for wl in wls])
+    args = ([w.robot for w in wls], [w.world for w in wls], [w.params for w in wls])
+    with BatchController(*args) as b:
+        ref, _ = b.step(states, goals)
+    with BatchController(*args) as b:
+        t = b.autotune()
+        assert 0 < t < 1e5
+        items, threads = b.get_launch()
+        assert items in (32, 48, 64, 96, 128) and threads in (128, 256, 512)
+        got, _ = b.step(states, goals)
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+
+
+def test_full_size_batch_runs():
+    wls = W.config_batch(0, 256)
+    states = [f32(wl.state) for wl in wls]
+    goals = np.stack([f32(wl.goal) for wl in wls])
+    with BatchController([w.robot for w in wls], [w.world for w in wls],
+                         [w.params for w in wls]) as b:
+        cmds, st = b.step(states, goals)
+        cmds2, st2 = b.step(states, goals)
+        # spot-check three instances against their own handles
+        for i in (0, 97, 255):
+            wl = wls[i]
+            with Controller(wl.robot, wl.world, wl.params) as c:
+                r1 = c.step(states[i], goals[i])[0]
+                r2 = c.step(states[i], goals[i])[0]
+            assert np.array_equal(cmds[i], r1) and np.array_equal(cmds2[i], r2)
+    assert len(cmds) == 256 and all(np.all(np.isfinite(c)) for c in cmds)
