@@ -123,6 +123,14 @@ def _declare(L):
     L.orc_cost_grad.argtypes = [C.POINTER(_Robot), C.POINTER(_World), C.POINTER(_Params), _dp, _dp,
                                 _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_cost_grad.restype = C.c_int
+    L.orc_mlp_param_count.restype = C.c_long
+    L.orc_bf16_round.argtypes = [C.c_float]
+    L.orc_bf16_round.restype = C.c_float
+    L.orc_mlp_forward.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, _dp]
+    L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int, C.c_int, C.c_int, _dp]
+    L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_self_min_sd_theta.argtypes = [C.POINTER(_Robot), _dp]
+    L.orc_self_min_sd_theta.restype = C.c_double
 
 
 def _f64(a):
@@ -188,6 +196,31 @@ def bspline_basis(H, S) -> np.ndarray:
     out = np.zeros((H, S))
     lib().orc_bspline_basis(H, S, _ptr(out))
     return out
+
+
+def mlp_param_count() -> int:
+    return int(lib().orc_mlp_param_count())
+
+
+def bf16_round(x: float) -> float:
+    return float(lib().orc_bf16_round(float(x)))
+
+
+def mlp_forward(params, theta, bf16=True) -> np.ndarray:
+    params, theta = _f64(params), _f64(theta)
+    B, dof = theta.shape
+    y = np.zeros(B)
+    lib().orc_mlp_forward(_ptr(params), _ptr(theta), B, dof, int(bf16), _ptr(y))
+    return y
+
+
+def mlp_loss_grad(params, theta, target, bf16=True):
+    params, theta, target = _f64(params), _f64(theta), _f64(target)
+    B, dof = theta.shape
+    g = np.zeros(mlp_param_count())
+    loss = lib().orc_mlp_loss_grad(_ptr(params), _ptr(theta), _ptr(target), B, dof, int(bf16),
+                                   _ptr(g))
+    return loss, g
 
 
 def integrate_adjoint(dt, g_theta, g_theta_dot, g_u):
@@ -314,6 +347,9 @@ class Oracle:
     def self_min_sd(self, theta) -> float:
         frames = self.fk(theta)
         return lib().orc_self_min_sd(C.byref(self.R), _ptr(frames))
+
+    def self_min_sd_theta(self, theta) -> float:
+        return lib().orc_self_min_sd_theta(C.byref(self.R), _ptr(_f64(theta)))
 
     def world_min_sd(self, theta) -> float:
         frames = self.fk(theta)

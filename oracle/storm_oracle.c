@@ -1155,3 +1155,168 @@ int orc_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
     free(dCdu);
     return 0;
 }
+
+/* ========================================================================= */
+/* Self-collision surrogate network.  The paper learns the closest distance  */
+/* between links with an MLP (Sec. 4.2, Eq. 13); this is the network of the */
+/* surrogate workload: encoded joints -> 256 -> 256 -> 256 -> 1 with ReLU.   */
+/* Encoding: x_j = theta_j / 3 (j < dof), x_7 = 1 (so the first layer's      */
+/* bias is its weight column 7), other inputs 0 (16 inputs).                 */
+/* Flat parameters (row-major, out x in): W1 256x16 | W2 256x256 | b2 256 |   */
+/* W3 256x256 | b3 256 | w4 256 | b4 1.                                      */
+/* With bf16 != 0 the routine rounds, exactly where a BF16 tensor-core      */
+/* implementation stores an operand, to the nearest BF16 (ties to even):    */
+/* W1..W3, the inputs, the hidden activations a1, a2, a3 and the back-      */
+/* propagated deltas; sums stay in double.  Pinned by finite differences    */
+/* (bf16 = 0) and a hand-computed tiny network.                              */
+/* ========================================================================= */
+
+#define H_ ORC_MLP_HID
+#define I_ ORC_MLP_IN
+
+long orc_mlp_param_count(void) { return (long)H_ * I_ + 2L * (H_ * H_ + H_) + H_ + 1; }
+
+/* Round to the nearest bfloat16 (ties to even) through binary32. */
+float orc_bf16_round(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x; /* inf / nan unchanged */
+    const uint32_t lsb = (u >> 16) & 1u;
+    u = (u + 0x7fffu + lsb) & 0xffff0000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+static double q(double v, int bf16) { return bf16 ? (double)orc_bf16_round((float)v) : v; }
+
+void orc_mlp_encode(const double* theta, int dof, double* x)
+{
+    for (int i = 0; i < I_; ++i) x[i] = 0.0;
+    for (int j = 0; j < dof && j < 7; ++j) x[j] = theta[j] / 3.0;
+    x[7] = 1.0;
+}
+
+typedef struct {
+    const double *W1, *W2, *b2, *W3, *b3, *w4, *b4;
+} mlp_view;
+
+static mlp_view mlp_split(const double* p)
+{
+    mlp_view v;
+    v.W1 = p;
+    v.W2 = v.W1 + H_ * I_;
+    v.b2 = v.W2 + H_ * H_;
+    v.W3 = v.b2 + H_;
+    v.b3 = v.W3 + H_ * H_;
+    v.w4 = v.b3 + H_;
+    v.b4 = v.w4 + H_;
+    return v;
+}
+
+/* one sample: activations a1, a2, a3 (H_ each) and output */
+static double mlp_one(const mlp_view* v, const double* x_in, int bf16, double* a1, double* a2,
+                      double* a3)
+{
+    double x[I_];
+    for (int i = 0; i < I_; ++i) x[i] = q(x_in[i], bf16);
+    for (int n = 0; n < H_; ++n) {
+        double z = 0.0;
+        for (int k = 0; k < I_; ++k) z += q(v->W1[n * I_ + k], bf16) * x[k];
+        a1[n] = q(z > 0.0 ? z : 0.0, bf16);
+    }
+    for (int n = 0; n < H_; ++n) {
+        double z = 0.0;
+        for (int k = 0; k < H_; ++k) z += q(v->W2[n * H_ + k], bf16) * a1[k];
+        z += v->b2[n];
+        a2[n] = q(z > 0.0 ? z : 0.0, bf16);
+    }
+    double y = v->b4[0];
+    for (int n = 0; n < H_; ++n) {
+        double z = 0.0;
+        for (int k = 0; k < H_; ++k) z += q(v->W3[n * H_ + k], bf16) * a2[k];
+        z += v->b3[n];
+        const double a = z > 0.0 ? z : 0.0;
+        y += v->w4[n] * a;      /* the output layer reads the unrounded a3 */
+        a3[n] = q(a, bf16);
+    }
+    return y;
+}
+
+void orc_mlp_forward(const double* params, const double* theta, int B, int dof, int bf16,
+                     double* y)
+{
+    const mlp_view v = mlp_split(params);
+    double x[I_], a1[H_], a2[H_], a3[H_];
+    for (int b = 0; b < B; ++b) {
+        orc_mlp_encode(theta + b * dof, dof, x);
+        y[b] = mlp_one(&v, x, bf16, a1, a2, a3);
+    }
+}
+
+/* Mean squared error (1/B) sum (y_b - t_b)^2 and its gradient, by the chain
+ * rule written layer by layer (delta_l = (W_{l+1}^T delta_{l+1}) o [z_l > 0]). */
+double orc_mlp_loss_grad(const double* params, const double* theta, const double* target, int B,
+                         int dof, int bf16, double* grad)
+{
+    const mlp_view v = mlp_split(params);
+    const long P = orc_mlp_param_count();
+    for (long i = 0; i < P; ++i) grad[i] = 0.0;
+    double* gW1 = grad;
+    double* gW2 = gW1 + H_ * I_;
+    double* gb2 = gW2 + H_ * H_;
+    double* gW3 = gb2 + H_;
+    double* gb3 = gW3 + H_ * H_;
+    double* gw4 = gb3 + H_;
+    double* gb4 = gw4 + H_;
+    double loss = 0.0;
+    double x[I_], xq[I_], a1[H_], a2[H_], a3[H_], d3[H_], d2[H_], d1[H_];
+    for (int b = 0; b < B; ++b) {
+        orc_mlp_encode(theta + b * dof, dof, x);
+        const double y = mlp_one(&v, x, bf16, a1, a2, a3);
+        for (int i = 0; i < I_; ++i) xq[i] = q(x[i], bf16);
+        const double r = y - target[b];
+        loss += r * r / B;
+        const double dy = 2.0 * r / B;
+        gb4[0] += dy;
+        for (int n = 0; n < H_; ++n) {
+            gw4[n] += dy * a3[n];
+            d3[n] = q(a3[n] > 0.0 ? dy * v.w4[n] : 0.0, bf16);
+        }
+        for (int n = 0; n < H_; ++n) {
+            gb3[n] += d3[n];
+            for (int k = 0; k < H_; ++k) gW3[n * H_ + k] += d3[n] * a2[k];
+        }
+        for (int k = 0; k < H_; ++k) {
+            double s = 0.0;
+            for (int n = 0; n < H_; ++n) s += d3[n] * q(v.W3[n * H_ + k], bf16);
+            d2[k] = q(a2[k] > 0.0 ? s : 0.0, bf16);
+        }
+        for (int n = 0; n < H_; ++n) {
+            gb2[n] += d2[n];
+            for (int k = 0; k < H_; ++k) gW2[n * H_ + k] += d2[n] * a1[k];
+        }
+        for (int k = 0; k < H_; ++k) {
+            double s = 0.0;
+            for (int n = 0; n < H_; ++n) s += d2[n] * q(v.W2[n * H_ + k], bf16);
+            d1[k] = q(a1[k] > 0.0 ? s : 0.0, bf16);
+        }
+        for (int n = 0; n < H_; ++n)
+            for (int k = 0; k < I_; ++k) gW1[n * I_ + k] += d1[n] * xq[k];
+    }
+    return loss;
+}
+
+/* Exact label of the surrogate: the minimum signed distance over the self
+ * pairs (positive apart) for one configuration. */
+double orc_self_min_sd_theta(const orc_robot* R, const double* theta)
+{
+    double* frames = (double*)malloc(sizeof(double) * 16 * (R->dof + 1));
+    orc_fk(R, theta, frames);
+    const double sd = orc_self_min_sd(R, frames);
+    free(frames);
+    return sd;
+}
+#undef H_
+#undef I_

@@ -121,6 +121,16 @@ void orc_integrate_adjoint(int H, int d, const double* dt, const double* g_theta
 int orc_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
                   const double* state, const double* goal, const double* mu, const double* sigma,
                   const double* eps, double* grad_mu, double* J, double* dC_du);
+/* ---- self-collision surrogate network (parameters flat, see storm_oracle.c) */
+enum { ORC_MLP_IN = 16, ORC_MLP_HID = 256 };
+long orc_mlp_param_count(void);
+float orc_bf16_round(float x);
+void orc_mlp_encode(const double* theta, int dof, double* x);
+void orc_mlp_forward(const double* params, const double* theta, int B, int dof, int bf16,
+                     double* y);
+double orc_mlp_loss_grad(const double* params, const double* theta, const double* target, int B,
+                         int dof, int bf16, double* grad);
+double orc_self_min_sd_theta(const orc_robot* R, const double* theta);
 int orc_step(const orc_robot* R, const orc_world* W, const orc_params* P,
              const double* state, const double* goal, uint32_t step, double* mu,
              double* sigma, double* cmd, double* best_cost);
