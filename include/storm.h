@@ -296,6 +296,54 @@ int storm_batch_set_distribution(storm_batch* b, int i, const float* mean, const
 int storm_batch_autotune(storm_batch* b, float* best_us);
 int storm_batch_get_launch(const storm_batch* b, int* items_per_tile, int* threads);
 
+/* ---------------------------------------------------------------- learned self-collision */
+
+/* The paper replaces its exact self-collision check by a learned link-distance
+ * network (Sec. 4.2, Eq. 13).  Here the network is an MLP: 16 encoded inputs
+ * (x_j = theta_j / 3 for the joints, x_7 = 1, others 0) -> 256 -> 256 -> 256
+ * -> 1 with ReLU, predicting the minimum signed distance (positive apart)
+ * over the robot's self-collision pairs.  BF16 weights and activations, FP32
+ * accumulation, every matrix product on tcgen05 tensor cores.  Parameters are
+ * a flat FP32 vector (row-major, out x in): W1 256x16 | W2 256x256 | b2 256 |
+ * W3 256x256 | b3 256 | w4 256 | b4 1. */
+typedef struct storm_mlp storm_mlp;
+
+#define STORM_MLP_PARAMS 135937
+#define STORM_MLP_MAX_ROWS (1 << 22)
+
+/* He-uniform initial weights from the Philox stream of `seed`. */
+int storm_mlp_create(uint64_t seed, void* cuda_stream, storm_mlp** out);
+void storm_mlp_destroy(storm_mlp* m);
+const char* storm_mlp_last_error(const storm_mlp* m);
+/* Host copies of the FP32 parameters (STORM_MLP_PARAMS floats). */
+int storm_mlp_get_params(storm_mlp* m, float* params);
+int storm_mlp_set_params(storm_mlp* m, const float* params);
+/* Predicted distances for theta_dev (count x dof, dof <= 7) into out_dev
+ * (count); device buffers, waits.  count <= STORM_MLP_MAX_ROWS. */
+int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev);
+/* Mean squared error against target_dev (count) and its gradient (host,
+ * STORM_MLP_PARAMS floats, nullable); waits. */
+int storm_mlp_loss_grad(storm_mlp* m, const float* theta_dev, const float* target_dev, int count,
+                        int dof, float* loss, float* grad);
+/* Adam training over `epochs` passes of shuffled minibatches of `batch`
+ * (a multiple of 128) samples; epoch_loss (host, epochs, nullable) gets each
+ * epoch's mean minibatch loss.  Waits.  STORM_ERR_TIMEOUT if a tensor-core
+ * wait ran out (the network is then left as it was before the failing step). */
+int storm_mlp_train(storm_mlp* m, const float* theta_dev, const float* target_dev, int count,
+                    int dof, int batch, int epochs, float lr, uint64_t seed, float* epoch_loss);
+
+/* Exact self-collision label of the handle's robot: the minimum signed
+ * distance over its self pairs for each configuration of theta_dev
+ * (count x dof) into sd_dev (count).  Device buffers, enqueued. */
+int storm_self_distance(storm_handle* h, const float* theta_dev, int count, float* sd_dev);
+
+/* Use `mlp` (NULL: stop using it) in this handle's rollouts: each iteration
+ * first evaluates the network on every (particle, step) configuration, and
+ * the exact self-collision check runs only where the prediction is below
+ * `margin` metres (elsewhere the self term is 0).  The network must outlive
+ * its use and must not run concurrently with this handle's steps. */
+int storm_set_surrogate(storm_handle* h, storm_mlp* mlp, double margin);
+
 /* ---------------------------------------------------------------- checkpoint */
 
 /* Serialise mu, sigma and the step counter (the Philox key is fixed by the

@@ -5,8 +5,8 @@ CUDA library ``libstorm_b300.so`` behind the C ABI of ``include/storm.h``;
 ``binding`` is its ctypes marshalling layer and ``workloads`` draws seeded
 synthetic inputs shaped like the paper's.
 """
-from .binding import (BatchController, Controller, StormError, build, lib,  # noqa: F401
-                      status_string, storm_cost)
+from .binding import (BatchController, Controller, StormError, SurrogateMLP, build,  # noqa: F401
+                      lib, status_string, storm_cost)
 
-__all__ = ["BatchController", "Controller", "StormError", "build", "lib", "status_string",
-           "storm_cost"]
+__all__ = ["BatchController", "Controller", "StormError", "SurrogateMLP", "build", "lib",
+           "status_string", "storm_cost"]

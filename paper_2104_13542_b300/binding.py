@@ -41,7 +41,11 @@ EXPORTED = [
     "storm_batch_last_error", "storm_batch_sizes", "storm_batch_step", "storm_batch_step_resident",
     "storm_batch_device_io", "storm_batch_sync", "storm_batch_get_distribution",
     "storm_batch_set_distribution", "storm_batch_autotune", "storm_batch_get_launch",
+    "storm_mlp_create", "storm_mlp_destroy", "storm_mlp_last_error", "storm_mlp_get_params",
+    "storm_mlp_set_params", "storm_mlp_predict", "storm_mlp_loss_grad", "storm_mlp_train",
+    "storm_self_distance", "storm_set_surrogate",
 ]
+MLP_PARAMS = 135937
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -146,6 +150,19 @@ def lib():
         L.storm_batch_set_distribution.argtypes = [vp, C.c_int, _fp, _fp]
         L.storm_batch_autotune.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_batch_get_launch.argtypes = [vp, ip, ip]
+        L.storm_mlp_create.argtypes = [C.c_uint64, vp, C.POINTER(vp)]
+        L.storm_mlp_destroy.argtypes = [vp]
+        L.storm_mlp_destroy.restype = None
+        L.storm_mlp_last_error.argtypes = [vp]
+        L.storm_mlp_last_error.restype = C.c_char_p
+        L.storm_mlp_get_params.argtypes = [vp, _fp]
+        L.storm_mlp_set_params.argtypes = [vp, _fp]
+        L.storm_mlp_predict.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+        L.storm_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, C.c_int, _fp, _fp]
+        L.storm_mlp_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                                      C.c_uint64, _fp]
+        L.storm_self_distance.argtypes = [vp, vp, C.c_int, vp]
+        L.storm_set_surrogate.argtypes = [vp, vp, C.c_double]
         _lib = L
     return _lib
 
@@ -399,6 +416,20 @@ class Controller:
         self._check(lib().storm_autotune(self.h, C.byref(t)))
         return t.value
 
+    def self_distance(self, theta_dev):
+        """Exact minimum self-pair signed distance for each row of theta_dev (count x dof)."""
+        n = int(theta_dev.shape[0])
+        out = self._empty(n)
+        self._join()
+        self._check(lib().storm_self_distance(self.h, _dptr(theta_dev.contiguous()), n, _dptr(out)))
+        self.stream.synchronize()
+        return out
+
+    def set_surrogate(self, mlp, margin: float = 0.05):
+        self._check(lib().storm_set_surrogate(self.h, mlp.h if mlp is not None else None,
+                                              float(margin)))
+        self._mlp = mlp  # keep the network alive while attached
+
     def get_state(self) -> bytes:
         n = C.c_size_t(0)
         self._check(lib().storm_get_state(self.h, None, C.byref(n)))
@@ -544,3 +575,75 @@ class BatchController:
         a, b = C.c_int(), C.c_int()
         self._check(lib().storm_batch_get_launch(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+
+class SurrogateMLP:
+    """The learned self-collision distance network (storm_mlp_* C ABI)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the surrogate network needs a CUDA device")
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        rc = lib().storm_mlp_create(int(seed), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise StormError(rc, "storm_mlp_create failed (see stderr)")
+        self.h = h
+
+    def _check(self, rc):
+        if rc < 0:
+            raise StormError(rc, lib().storm_mlp_last_error(self.h).decode())
+        return rc
+
+    def _sync_in(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().storm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(lib().storm_mlp_get_params(self.h, _p(out, _fp)))
+        return out
+
+    def set_params(self, params):
+        p = _f32(params).reshape(-1)
+        assert p.size == MLP_PARAMS
+        self._check(lib().storm_mlp_set_params(self.h, _p(p, _fp)))
+
+    def predict(self, theta_dev):
+        n, dof = int(theta_dev.shape[0]), int(theta_dev.shape[1])
+        with self.torch.cuda.stream(self.stream):
+            out = self.torch.empty(n, dtype=self.torch.float32, device="cuda")
+        self._sync_in()
+        self._check(lib().storm_mlp_predict(self.h, _dptr(theta_dev.contiguous()), n, dof, _dptr(out)))
+        return out
+
+    def loss_grad(self, theta_dev, target_dev):
+        n, dof = int(theta_dev.shape[0]), int(theta_dev.shape[1])
+        loss = np.zeros(1, dtype=np.float32)
+        grad = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._sync_in()
+        self._check(lib().storm_mlp_loss_grad(self.h, _dptr(theta_dev.contiguous()),
+                                              _dptr(target_dev.contiguous()), n, dof,
+                                              _p(loss, _fp), _p(grad, _fp)))
+        return float(loss[0]), grad
+
+    def train(self, theta_dev, target_dev, batch=4096, epochs=4, lr=1e-3, seed=0):
+        n, dof = int(theta_dev.shape[0]), int(theta_dev.shape[1])
+        losses = np.zeros(epochs, dtype=np.float32)
+        self._sync_in()
+        self._check(lib().storm_mlp_train(self.h, _dptr(theta_dev.contiguous()),
+                                          _dptr(target_dev.contiguous()), n, dof, int(batch),
+                                          int(epochs), float(lr), int(seed), _p(losses, _fp)))
+        return losses

@@ -102,7 +102,8 @@ struct RolloutOut {
 __device__ __forceinline__ void rollout_particles(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state,
                                                   const float* __restrict__ goal, uint32_t step,
-                                                  int iter, int n0, int np, unsigned char* smem)
+                                                  int iter, int n0, int np, unsigned char* smem,
+                                                  int front_only = 0)
 {
     const RolloutLayout L = rollout_layout(pb);
     float4* s_frame = reinterpret_cast<float4*>(smem + L.frame);
@@ -251,6 +252,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     if (out.theta_dot)
         for (int i = tid; i < np * HD; i += nt)
             out.theta_dot[static_cast<size_t>(n0) * HD + i] = s_thd[i];
+    if (front_only) return;  // joint states only (surrogate input)
 
     // ---- per (particle, step): FK frames, Jacobian, non-collision costs
     for (int item = tid; item < I; item += nt) {
@@ -409,8 +411,10 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     // ---- self collision, Eq. 13 reading.  Pair blocks (every sphere of one
     // link against up to 8 spheres of another) keep the 8 centres in registers
     // while streaming the first link's spheres; leftover pairs one by one.
+    const float* pred = pb.self_pred ? pb.self_pred + static_cast<size_t>(n0) * H : nullptr;
     for (int idx = tid; idx < I * pb.NPB; idx += nt) {
         const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
+        if (pred && pred[item] >= pb.self_margin) continue;  // surrogate: clearly apart
         const uint4 blk = s_pblk[bk];  // a0, a1, b0, nb
         const float4* ci = s_cent + item * M;
         float4 cb[8];
@@ -435,6 +439,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         const float rs = s_sph[a].w + s_sph[b].w;
         const float rs2 = rs * rs;
         for (int item = 0; item < I; ++item) {
+            if (pred && pred[item] >= pb.self_margin) continue;
             const float4 ca = s_cent[item * M + a];
             const float4 cb = s_cent[item * M + b];
             const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
@@ -468,14 +473,14 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
 __global__ void __launch_bounds__(kMaxThreads)
 k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
           const float* __restrict__ goal, const StepState* __restrict__ st, int step_override,
-          int iter)
+          int iter, int front_only)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n0 = blockIdx.x * pb.ppc;
     const int np = min(pb.ppc, pb.N - n0);
     if (np <= 0) return;
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
-    rollout_particles(pb, out, state, goal, step, iter, n0, np, smem);
+    rollout_particles(pb, out, state, goal, step, iter, n0, np, smem, front_only);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -714,6 +719,7 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
 }
 
 #include "storm_adjoint.cuh"
+#include "storm_mlp.cuh"
 
 // Raw noise of sample_controls: one thread per Philox block (4 values).
 __global__ void k_noise(Problem pb, uint32_t step, int iter, float* __restrict__ eps)
@@ -960,6 +966,204 @@ k_update_batch(const BatchInstance* __restrict__ insts, const int2* __restrict__
     update_row(s_pb, I.C, I.u, nullptr, I.st, I.cmd, iter == I.K - 1, I.upd, r.y, s_pb.H);
 }
 
+// ============================================================================ surrogate network host side
+
+// Activations of the surrogate network for up to `cap` rows.
+struct MlpBuffers {
+    int cap = 0;
+    bool train = false;
+    __nv_bfloat16 *x = nullptr, *xT = nullptr, *a1 = nullptr, *a1T = nullptr, *a2 = nullptr,
+                  *a2T = nullptr, *a3 = nullptr, *d3 = nullptr, *d3T = nullptr, *d2 = nullptr,
+                  *d2T = nullptr, *d1T = nullptr;
+    float *y = nullptr, *dy = nullptr, *loss_part = nullptr;
+};
+
+struct storm_mlp {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
+    __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w2t = nullptr, *w3 = nullptr, *w3t = nullptr;
+    MlpBuffers buf;
+    float *th_b = nullptr, *t_b = nullptr, *loss_hist = nullptr;
+    int* idx = nullptr;
+    int cap_batch = 0, cap_idx = 0, cap_hist = 0;
+    int* err = nullptr;
+    int t = 0;
+    std::string msg = "no error";
+};
+
+void mlp_free_buffers(MlpBuffers& b)
+{
+    __nv_bfloat16* bf[] = {b.x, b.xT, b.a1, b.a1T, b.a2, b.a2T, b.a3, b.d3, b.d3T, b.d2, b.d2T, b.d1T};
+    for (auto* q : bf)
+        if (q) cudaFree(q);
+    float* fl[] = {b.y, b.dy, b.loss_part};
+    for (auto* q : fl)
+        if (q) cudaFree(q);
+    b = MlpBuffers{};
+}
+
+cudaError_t mlp_reserve(MlpBuffers& b, int rows, bool train)
+{
+    if (rows <= b.cap && (b.train || !train)) return cudaSuccess;
+    mlp_free_buffers(b);
+    const size_t R = static_cast<size_t>(rows);
+    const size_t h = sizeof(__nv_bfloat16) * R * kMlpHid;
+    cudaError_t e = cudaSuccess;
+    auto get = [&](auto** q, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(q), bytes);
+    };
+    get(&b.x, sizeof(__nv_bfloat16) * R * kMlpIn);
+    get(&b.a1, h);
+    get(&b.a2, h);
+    get(&b.y, sizeof(float) * R);
+    if (train) {
+        get(&b.xT, sizeof(__nv_bfloat16) * R * kMlpIn);
+        get(&b.a1T, h);
+        get(&b.a2T, h);
+        get(&b.a3, h);
+        get(&b.d3, h);
+        get(&b.d3T, h);
+        get(&b.d2, h);
+        get(&b.d2T, h);
+        get(&b.d1T, h);
+        get(&b.dy, sizeof(float) * R);
+        get(&b.loss_part, sizeof(float) * R);
+    }
+    if (e == cudaSuccess) {
+        b.cap = rows;
+        b.train = train;
+    }
+    return e;
+}
+
+template <int BN>
+cudaError_t gemm(const tc::GemmArgs& g, cudaStream_t s)
+{
+    static int attr_set = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_set != dev) {
+        const cudaError_t e = cudaFuncSetAttribute(tc::k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   static_cast<int>(tc::gemm_smem<BN>()));
+        if (e != cudaSuccess) return e;
+        attr_set = dev;
+    }
+    if (g.M % tc::kBM || g.N != BN || g.K % 16 || g.K <= 0) return cudaErrorInvalidValue;
+    tc::k_gemm<BN><<<g.M / tc::kBM, tc::kThreads, tc::gemm_smem<BN>(), s>>>(g);
+    return cudaGetLastError();
+}
+
+tc::GemmArgs gemm_args(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
+                       int K, int* err)
+{
+    tc::GemmArgs g{};
+    g.A = A;
+    g.lda = lda;
+    g.B = B;
+    g.ldb = ldb;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.err = err;
+    return g;
+}
+
+// Forward pass for `count` configurations (rows padded to 128); y (or the
+// buffers' own y when NULL) receives the predicted distances of the padded rows.  With `train` the activations the
+// backward pass needs are kept.
+int mlp_forward(storm_mlp* m, MlpBuffers& b, const float* theta, int count, int dof, bool train,
+                float* y, cudaStream_t s)
+{
+    const int R = (count + tc::kBM - 1) / tc::kBM * tc::kBM;
+    if (mlp_reserve(b, R, train) != cudaSuccess) return STORM_ERR_OOM;
+    if (!y) y = b.y;  // after the reserve, which may reallocate b.y
+    k_mlp_encode<<<(R + 255) / 256, 256, 0, s>>>(theta, count, dof, R, b.x, train ? b.xT : nullptr);
+    if (cudaGetLastError() != cudaSuccess) return STORM_ERR_CUDA;
+    tc::GemmArgs g = gemm_args(b.x, kMlpIn, m->w1, kMlpIn, R, kMlpHid, kMlpIn, m->err);
+    g.relu = 1;
+    g.out_bf = b.a1;
+    g.ldo = kMlpHid;
+    if (train) {
+        g.out_bfT = b.a1T;
+        g.ldoT = R;
+    }
+    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    g = gemm_args(b.a1, kMlpHid, m->w2, kMlpHid, R, kMlpHid, kMlpHid, m->err);
+    g.bias = m->p + kOffB2;
+    g.relu = 1;
+    g.out_bf = b.a2;
+    g.ldo = kMlpHid;
+    if (train) {
+        g.out_bfT = b.a2T;
+        g.ldoT = R;
+    }
+    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    g = gemm_args(b.a2, kMlpHid, m->w3, kMlpHid, R, kMlpHid, kMlpHid, m->err);
+    g.bias = m->p + kOffB3;
+    g.relu = 1;
+    g.head_w = m->p + kOffW4;
+    g.head_b = m->p + kOffB4;
+    g.head_y = y;
+    if (train) {
+        g.out_bf = b.a3;
+        g.ldo = kMlpHid;
+    }
+    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    return STORM_OK;
+}
+
+// Backward pass of the mean squared error after a training forward pass:
+// gradient into m->g, loss into *m->loss.
+int mlp_backward(storm_mlp* m, MlpBuffers& b, const float* target, int count, cudaStream_t s)
+{
+    const int R = (count + tc::kBM - 1) / tc::kBM * tc::kBM;
+    k_mlp_dhead<<<R, kMlpHid, 0, s>>>(b.y, target, count, R, b.a3, m->p, b.dy, b.d3, b.d3T, b.loss_part);
+    k_mlp_head_grad<<<kMlpHid + 2, 256, 0, s>>>(b.dy, b.a3, R, count, b.loss_part, m->g, m->loss);
+    if (cudaGetLastError() != cudaSuccess) return STORM_ERR_CUDA;
+    // dW3 = delta3^T a2, db3 = sum delta3
+    tc::GemmArgs g = gemm_args(b.d3T, R, b.a2T, R, kMlpHid, kMlpHid, R, m->err);
+    g.out_f = m->g + kOffW3;
+    g.ldf = kMlpHid;
+    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    k_mlp_rowsum<<<kMlpHid, 256, 0, s>>>(b.d3T, R, m->g + kOffB3);
+    // delta2 = (delta3 W3) o [a2 > 0]
+    g = gemm_args(b.d3, kMlpHid, m->w3t, kMlpHid, R, kMlpHid, kMlpHid, m->err);
+    g.mask = b.a2;
+    g.ldm = kMlpHid;
+    g.out_bf = b.d2;
+    g.ldo = kMlpHid;
+    g.out_bfT = b.d2T;
+    g.ldoT = R;
+    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    // dW2 = delta2^T a1, db2 = sum delta2
+    g = gemm_args(b.d2T, R, b.a1T, R, kMlpHid, kMlpHid, R, m->err);
+    g.out_f = m->g + kOffW2;
+    g.ldf = kMlpHid;
+    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    k_mlp_rowsum<<<kMlpHid, 256, 0, s>>>(b.d2T, R, m->g + kOffB2);
+    // delta1 = (delta2 W2) o [a1 > 0]
+    g = gemm_args(b.d2, kMlpHid, m->w2t, kMlpHid, R, kMlpHid, kMlpHid, m->err);
+    g.mask = b.a1;
+    g.ldm = kMlpHid;
+    g.out_bfT = b.d1T;
+    g.ldoT = R;
+    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    // dW1 = delta1^T x
+    g = gemm_args(b.d1T, R, b.xT, R, kMlpHid, kMlpIn, R, m->err);
+    g.out_f = m->g + kOffW1;
+    g.ldf = kMlpIn;
+    if (gemm<kMlpIn>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? STORM_OK : STORM_ERR_CUDA;
+}
+
+int mlp_cast(storm_mlp* m, cudaStream_t s)
+{
+    k_mlp_cast<<<(kMlpHid * kMlpHid + 255) / 256, 256, 0, s>>>(m->p, m->w1, m->w2, m->w2t, m->w3, m->w3t);
+    return cudaGetLastError() == cudaSuccess ? STORM_OK : STORM_ERR_CUDA;
+}
+
 // ============================================================================ host runtime
 
 struct storm_handle {
@@ -981,6 +1185,10 @@ struct storm_handle {
     StepState* d_st = nullptr;
     UpdateScratch* d_upd = nullptr;  // multi-CTA update: counter + H x d partials
     float* d_adj = nullptr;          // adjoint partial rows: N x (H*d + 1)
+    storm_mlp* mlp = nullptr;        // learned self-collision surrogate (not owned)
+    MlpBuffers* mlp_buf = nullptr;   // its inference activations for N x H rows
+    float* d_theta = nullptr;        // N x H x d joint states for the surrogate
+    float* d_pred = nullptr;         // N x H (padded) predicted self distances
     size_t adjoint_smem = 0;
     int grad_steps = 0;
     float grad_eta = 0.f;
@@ -1129,10 +1337,13 @@ int upload_world(storm_handle* h, const storm_world* w)
 }
 
 int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const float* state,
-                   const float* goal, int step_override, int iter)
+                   const float* goal, int step_override, int iter, bool exact_self = false,
+                   int front_only = 0)
 {
-    k_rollout<<<h->grid, h->threads, h->rollout_smem, s>>>(h->pb, out, state, goal, h->d_st,
-                                                         step_override, iter);
+    Problem pb = h->pb;
+    if (exact_self) pb.self_pred = nullptr;
+    k_rollout<<<h->grid, h->threads, h->rollout_smem, s>>>(pb, out, state, goal, h->d_st,
+                                                         step_override, iter, front_only);
     CK(cudaGetLastError());
     return STORM_OK;
 }
@@ -1171,6 +1382,14 @@ int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
     const float* goal = h->d_io + io_goal(h->pb);
     float* cmd = h->d_io + io_cmd(h->pb);
     for (int k = 0; k < h->K; ++k) {
+        if (h->mlp) {  // surrogate: joint states, network, then the rollout proper
+            RolloutOut front{h->d_u, h->d_theta, nullptr, nullptr, nullptr, nullptr, h->d_C};
+            int rc = launch_rollout(h, s, front, state, goal, -1, k, false, 1);
+            if (rc) return rc;
+            rc = mlp_forward(h->mlp, *h->mlp_buf, h->d_theta, h->pb.N * h->pb.H, h->pb.d, false,
+                             h->d_pred, s);
+            if (rc) return fail(h, rc, "surrogate forward launch failed");
+        }
         int rc = launch_rollout(h, s, out, state, goal, -1, k);
         if (rc) return rc;
         rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1 && h->grad_steps == 0);
@@ -1263,6 +1482,12 @@ void free_all(storm_handle* h)
     if (h->d_io) cudaFree(h->d_io);
     if (h->d_upd) cudaFree(h->d_upd);
     if (h->d_adj) cudaFree(h->d_adj);
+    if (h->d_theta) cudaFree(h->d_theta);
+    if (h->d_pred) cudaFree(h->d_pred);
+    if (h->mlp_buf) {
+        mlp_free_buffers(*h->mlp_buf);
+        delete h->mlp_buf;
+    }
     if (h->h_io) cudaFreeHost(h->h_io);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -1640,7 +1865,7 @@ int storm_generate_rollouts(storm_handle* h, const float* state_dev, const float
     if (iter < 0 || iter > 255 || step > 0x7fffffffu) return fail(h, STORM_ERR_INVALID_ARG, "bad iter/step");
     RolloutOut out{u_dev ? u_dev : h->d_u, theta_dev, theta_dot_dev, ee_dev, terms_dev, cost_dev,
                    Ctot_dev ? Ctot_dev : h->d_C};
-    return launch_rollout(h, h->stream, out, state_dev, goal_dev, static_cast<int>(step), iter);
+    return launch_rollout(h, h->stream, out, state_dev, goal_dev, static_cast<int>(step), iter, true);
 }
 
 int storm_cost_grad(storm_handle* h, const float* state_dev, const float* goal_dev,
@@ -2040,7 +2265,7 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
         RolloutOut out{d_u, nullptr, nullptr, nullptr, nullptr, nullptr, Ctot_dev};
         const int grid = (pb.N + pb.ppc - 1) / pb.ppc;
         k_rollout<<<grid, kThreads, L.bytes, stream>>>(pb, out, state_dev, goal_dev, nullptr,
-                                                      static_cast<int>(step), iter);
+                                                      static_cast<int>(step), iter, 0);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
@@ -2474,6 +2699,258 @@ int storm_batch_autotune(storm_batch* b, float* best_us)
     if (rc) return rc;
     if (best_us) *best_us = best;
     return batch_build_graphs(b);
+}
+
+}  // extern "C"
+
+
+// ============================================================================ surrogate C ABI
+
+namespace {
+#define MK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            (void)cudaGetLastError();                                              \
+            m->msg = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+            return e_ == cudaErrorMemoryAllocation ? STORM_ERR_OOM : STORM_ERR_CUDA; \
+        }                                                                          \
+    } while (0)
+
+void mlp_free(storm_mlp* m)
+{
+    mlp_free_buffers(m->buf);
+    float* fl[] = {m->p, m->g, m->m, m->v, m->loss, m->th_b, m->t_b, m->loss_hist};
+    for (auto* q : fl)
+        if (q) cudaFree(q);
+    __nv_bfloat16* bf[] = {m->w1, m->w2, m->w2t, m->w3, m->w3t};
+    for (auto* q : bf)
+        if (q) cudaFree(q);
+    if (m->idx) cudaFree(m->idx);
+    if (m->err) cudaFree(m->err);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+}
+
+int mlp_check_err(storm_mlp* m)
+{
+    int e = 0;
+    MK(cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MK(cudaStreamSynchronize(m->stream));
+    if (e) {
+        m->msg = "a tensor-core wait timed out";
+        MK(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream));
+        return STORM_ERR_TIMEOUT;
+    }
+    return STORM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+const char* storm_mlp_last_error(const storm_mlp* m) { return m ? m->msg.c_str() : "NULL network"; }
+
+int storm_mlp_create(uint64_t seed, void* cuda_stream, storm_mlp** out)
+{
+    if (!out) return STORM_ERR_INVALID_ARG;
+    *out = nullptr;
+    storm_mlp* m = new (std::nothrow) storm_mlp();
+    if (!m) return STORM_ERR_OOM;
+    auto fail_m = [&](int rc) {
+        fprintf(stderr, "storm_mlp_create: %s\n", m->msg.c_str());
+        mlp_free(m);
+        delete m;
+        return rc;
+    };
+    int rc = STORM_OK;
+    auto try_ = [&](cudaError_t e, const char* what) {
+        if (rc == STORM_OK && e != cudaSuccess) {
+            (void)cudaGetLastError();
+            m->msg = std::string(what) + ": " + cudaGetErrorString(e);
+            rc = e == cudaErrorMemoryAllocation ? STORM_ERR_OOM : STORM_ERR_CUDA;
+        }
+    };
+    try_(cudaGetDevice(&m->device), "cudaGetDevice");
+    if (cuda_stream) {
+        m->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        try_(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking), "stream");
+        m->own_stream = rc == STORM_OK;
+    }
+    const size_t P = sizeof(float) * kMlpParams;
+    try_(cudaMalloc(&m->p, P), "params");
+    try_(cudaMalloc(&m->g, P), "grad");
+    try_(cudaMalloc(&m->m, P), "adam m");
+    try_(cudaMalloc(&m->v, P), "adam v");
+    try_(cudaMalloc(&m->loss, sizeof(float)), "loss");
+    try_(cudaMalloc(&m->err, sizeof(int)), "err");
+    const size_t hh = sizeof(__nv_bfloat16) * kMlpHid * kMlpHid;
+    try_(cudaMalloc(&m->w1, sizeof(__nv_bfloat16) * kMlpHid * kMlpIn), "w1");
+    try_(cudaMalloc(&m->w2, hh), "w2");
+    try_(cudaMalloc(&m->w2t, hh), "w2t");
+    try_(cudaMalloc(&m->w3, hh), "w3");
+    try_(cudaMalloc(&m->w3t, hh), "w3t");
+    if (rc) return fail_m(rc);
+    try_(cudaMemsetAsync(m->m, 0, P, m->stream), "memset");
+    try_(cudaMemsetAsync(m->v, 0, P, m->stream), "memset");
+    try_(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream), "memset");
+    k_mlp_init<<<(kMlpParams + 255) / 256, 256, 0, m->stream>>>(
+        m->p, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+    try_(cudaGetLastError(), "init");
+    if (rc == STORM_OK) rc = mlp_cast(m, m->stream);
+    try_(cudaStreamSynchronize(m->stream), "sync");
+    if (rc) return fail_m(rc);
+    *out = m;
+    return STORM_OK;
+}
+
+void storm_mlp_destroy(storm_mlp* m)
+{
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    mlp_free(m);
+    delete m;
+}
+
+int storm_mlp_get_params(storm_mlp* m, float* params)
+{
+    if (!m || !params) return STORM_ERR_INVALID_ARG;
+    MK(cudaMemcpyAsync(params, m->p, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, m->stream));
+    MK(cudaStreamSynchronize(m->stream));
+    return STORM_OK;
+}
+
+int storm_mlp_set_params(storm_mlp* m, const float* params)
+{
+    if (!m || !params) return STORM_ERR_INVALID_ARG;
+    for (int i = 0; i < kMlpParams; ++i)
+        if (!std::isfinite(params[i])) return m->msg = "non-finite parameter", STORM_ERR_INVALID_ARG;
+    MK(cudaMemcpyAsync(m->p, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, m->stream));
+    const int rc = mlp_cast(m, m->stream);
+    if (rc) return rc;
+    MK(cudaStreamSynchronize(m->stream));
+    return STORM_OK;
+}
+
+int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev)
+{
+    if (!m || !theta_dev || !out_dev || count < 1 || count > STORM_MLP_MAX_ROWS || dof < 1 || dof > 7)
+        return STORM_ERR_INVALID_ARG;
+    const int rc = mlp_forward(m, m->buf, theta_dev, count, dof, false, nullptr, m->stream);
+    if (rc) return rc;
+    MK(cudaMemcpyAsync(out_dev, m->buf.y, sizeof(float) * count, cudaMemcpyDeviceToDevice, m->stream));
+    return mlp_check_err(m);
+}
+
+int storm_mlp_loss_grad(storm_mlp* m, const float* theta_dev, const float* target_dev, int count,
+                        int dof, float* loss, float* grad)
+{
+    if (!m || !theta_dev || !target_dev || count < 1 || count > STORM_MLP_MAX_ROWS || dof < 1 || dof > 7)
+        return STORM_ERR_INVALID_ARG;
+    const int R = (count + tc::kBM - 1) / tc::kBM * tc::kBM;
+    if (mlp_reserve(m->buf, R, true) != cudaSuccess) return STORM_ERR_OOM;
+    int rc = mlp_forward(m, m->buf, theta_dev, count, dof, true, nullptr, m->stream);
+    if (!rc) rc = mlp_backward(m, m->buf, target_dev, count, m->stream);
+    if (rc) return rc;
+    if (loss) MK(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    if (grad) MK(cudaMemcpyAsync(grad, m->g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, m->stream));
+    return mlp_check_err(m);
+}
+
+int storm_mlp_train(storm_mlp* m, const float* theta_dev, const float* target_dev, int count, int dof,
+                    int batch, int epochs, float lr, uint64_t seed, float* epoch_loss)
+{
+    if (!m || !theta_dev || !target_dev || count < batch || batch < 128 || batch % 128 ||
+        batch > STORM_MLP_MAX_ROWS || epochs < 1 || !(lr > 0.f) || dof < 1 || dof > 7)
+        return STORM_ERR_INVALID_ARG;
+    if (mlp_reserve(m->buf, batch, true) != cudaSuccess) return STORM_ERR_OOM;
+    const int nb = count / batch;
+    if (m->cap_batch < batch) {
+        if (m->th_b) cudaFree(m->th_b);
+        if (m->t_b) cudaFree(m->t_b);
+        m->th_b = m->t_b = nullptr;
+        MK(cudaMalloc(&m->th_b, sizeof(float) * batch * 7));
+        MK(cudaMalloc(&m->t_b, sizeof(float) * batch));
+        m->cap_batch = batch;
+    }
+    if (m->cap_idx < count) {
+        if (m->idx) cudaFree(m->idx);
+        m->idx = nullptr;
+        MK(cudaMalloc(&m->idx, sizeof(int) * count));
+        m->cap_idx = count;
+    }
+    if (m->cap_hist < nb) {
+        if (m->loss_hist) cudaFree(m->loss_hist);
+        m->loss_hist = nullptr;
+        MK(cudaMalloc(&m->loss_hist, sizeof(float) * nb));
+        m->cap_hist = nb;
+    }
+    std::vector<int> perm(count);
+    std::vector<float> hist(nb);
+    uint64_t state = seed ^ 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {  // splitmix64
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::iota(perm.begin(), perm.end(), 0);
+        for (int i = count - 1; i > 0; --i) std::swap(perm[i], perm[next() % (i + 1)]);
+        MK(cudaMemcpyAsync(m->idx, perm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, m->stream));
+        MK(cudaStreamSynchronize(m->stream));
+        for (int bi = 0; bi < nb; ++bi) {
+            k_mlp_gather<<<(batch + 255) / 256, 256, 0, m->stream>>>(theta_dev, target_dev, m->idx, bi * batch,
+                                                                   batch, dof, m->th_b, m->t_b);
+            int rc = mlp_forward(m, m->buf, m->th_b, batch, dof, true, nullptr, m->stream);
+            if (!rc) rc = mlp_backward(m, m->buf, m->t_b, batch, m->stream);
+            if (rc) return rc;
+            k_adam<<<(kMlpParams + 255) / 256, 256, 0, m->stream>>>(m->p, m->g, m->m, m->v, kMlpParams, lr,
+                                                                   0.9f, 0.999f, 1e-8f, ++m->t);
+            rc = mlp_cast(m, m->stream);
+            if (rc) return rc;
+            MK(cudaMemcpyAsync(m->loss_hist + bi, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
+        }
+        MK(cudaMemcpyAsync(hist.data(), m->loss_hist, sizeof(float) * nb, cudaMemcpyDeviceToHost, m->stream));
+        const int rc = mlp_check_err(m);
+        if (rc) return rc;
+        if (epoch_loss) {
+            double acc = 0.0;
+            for (float x : hist) acc += x;
+            epoch_loss[ep] = static_cast<float>(acc / nb);
+        }
+    }
+    return STORM_OK;
+}
+
+int storm_self_distance(storm_handle* h, const float* theta_dev, int count, float* sd_dev)
+{
+    if (!h || !theta_dev || !sd_dev || count < 0) return fail(h, STORM_ERR_INVALID_ARG, "bad argument");
+    if (count == 0) return STORM_OK;
+    const size_t smem = sizeof(float4) * 8 * std::max(h->pb.M, 1);
+    k_self_distance<<<(count + 7) / 8, 256, smem, h->stream>>>(h->pb, theta_dev, count, sd_dev);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+int storm_set_surrogate(storm_handle* h, storm_mlp* mlp, double margin)
+{
+    if (!h || std::isnan(margin)) return fail(h, STORM_ERR_INVALID_ARG, "bad argument");
+    CK(cudaStreamSynchronize(h->stream));
+    h->mlp = mlp;
+    if (mlp) {
+        const int rows = h->pb.N * h->pb.H;
+        const int R = (rows + tc::kBM - 1) / tc::kBM * tc::kBM;
+        if (!h->mlp_buf) h->mlp_buf = new MlpBuffers();
+        CK(mlp_reserve(*h->mlp_buf, R, false));
+        if (!h->d_theta) CK(cudaMalloc(&h->d_theta, sizeof(float) * size_t(rows) * h->pb.d));
+        if (!h->d_pred) CK(cudaMalloc(&h->d_pred, sizeof(float) * R));
+        h->pb.self_pred = h->d_pred;
+        h->pb.self_margin = static_cast<float>(margin);
+    } else {
+        h->pb.self_pred = nullptr;
+    }
+    return build_graphs(h);
 }
 
 }  // extern "C"

@@ -44,6 +44,8 @@ struct Problem {
     const float* halton;     // N x S x d normal noise (Halton sampler only)
     float* mu;               // H x d
     float* sigma;            // d
+    const float* self_pred;  // N x H surrogate self distances (nullable)
+    float self_margin;       // exact self check only where self_pred < self_margin
 };
 
 // Step bookkeeping kept on the device so captured graphs need no host update.

@@ -1,0 +1,455 @@
+// storm_mlp.cuh -- the self-collision surrogate network on Blackwell tensor cores.
+//
+// The paper replaces its exact self-collision check by a learned distance
+// network (Sec. 4.2, Eq. 13).  Here: 16 encoded inputs -> 256 -> 256 -> 256 -> 1
+// with ReLU, BF16 operands and FP32 accumulation.  Every GEMM runs on the 5th
+// generation tensor cores: operands staged in shared memory by cp.async in the
+// no-swizzle K-major core-matrix layout, one elected thread issues
+// tcgen05.mma with the accumulator in tensor memory (TMEM), tcgen05.commit
+// signals an mbarrier, and the epilogue reads TMEM with tcgen05.ld.  Every
+// wait is bounded in time and reports through an error flag.
+#pragma once
+
+#include <cuda_bf16.h>
+
+namespace tc {
+
+constexpr int kBM = 128;         // rows of a CTA tile = TMEM lanes
+constexpr int kKB = 64;          // K per shared-memory stage
+constexpr int kThreads = 128;    // one warpgroup: warp w owns TMEM lanes 32w..32w+31
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound on any wait
+
+struct GemmArgs {
+    const __nv_bfloat16* A;  // M x K, row-major (K contiguous)
+    const __nv_bfloat16* B;  // N x K, row-major (K contiguous)
+    int lda, ldb;
+    int M, N, K;             // M % 128 == 0, N % 16 == 0 and <= 256, K % 16 == 0
+    const float* bias;       // N (nullable)
+    int relu;
+    const __nv_bfloat16* mask;  // M x N: keep entries where mask > 0 (nullable)
+    int ldm;
+    __nv_bfloat16* out_bf;      // M x N (nullable)
+    int ldo;
+    __nv_bfloat16* out_bfT;     // N x M (nullable)
+    int ldoT;
+    float* out_f;               // M x N (nullable)
+    int ldf;
+    const float* head_w;        // N: y[m] = *head_b + sum_n head_w[n] v[m][n] (nullable)
+    const float* head_b;
+    float* head_y;              // M
+    int* err;                   // set to 1 when a wait times out
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension
+// byte offset (between core matrices along K), stride-dimension byte offset
+// (between 8-row groups), the fixed 0b001 at bits 46-48.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) |
+           (static_cast<uint64_t>((lbo & 0x3FFFFu) >> 4) << 16) |
+           (static_cast<uint64_t>((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, N, M.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+// Wait for the phase with parity `parity` to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+{
+    const unsigned long long t0 = now_ns();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (now_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Stage a rows x kb tile (row-major source, K contiguous) into the core-matrix
+// layout: element (r, k) at (r / 8) * SBO + (r % 8) * 16 + (k / 8) * 128 + (k % 8) * 2.
+__device__ __forceinline__ void stage_tile(uint32_t dst, const __nv_bfloat16* src, int ld, int rows,
+                                           int kb)
+{
+    const int chunks = kb / 8, sbo = chunks * 128;
+    for (int c = threadIdx.x; c < rows * chunks; c += blockDim.x) {
+        const int r = c / chunks, kg = c - r * chunks;
+        cp_async16(dst + (r >> 3) * sbo + (r & 7) * 16 + kg * 128, src + static_cast<size_t>(r) * ld + kg * 8);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// C = A B^T on one 128 x BN tile per CTA, FP32 accumulator in TMEM, fused
+// epilogue (bias, ReLU, mask, BF16 / FP32 stores, transposed store, dot head).
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    constexpr int kCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    constexpr int kStageA = kBM * kKB * 2, kStageB = BN * kKB * 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM;
+    unsigned char* sA[2] = {smem, smem + kStageA + kStageB};
+    unsigned char* sB[2] = {smem + kStageA, smem + 2 * kStageA + kStageB};
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    const int nk = (g.K + kKB - 1) / kKB;
+    uint32_t parity[2] = {0u, 0u};
+    bool ok = true;
+    const __nv_bfloat16* A = g.A + static_cast<size_t>(m0) * g.lda;
+    stage_tile(smem_u32(sA[0]), A, g.lda, kBM, min(kKB, g.K));
+    stage_tile(smem_u32(sB[0]), g.B, g.ldb, BN, min(kKB, g.K));
+    int last = 0;
+    for (int it = 0; it < nk && ok; ++it) {
+        const int s = it & 1, k0 = it * kKB, kb = min(kKB, g.K - k0);
+        if (it + 1 < nk) {
+            const int s2 = s ^ 1, k1 = k0 + kKB, kb1 = min(kKB, g.K - k1);
+            if (it >= 1) {  // the MMAs of iteration it-1 read stage s2
+                ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[s2]), parity[s2]));
+                parity[s2] ^= 1u;
+                if (!ok) break;  // uniform across the CTA
+            }
+            stage_tile(smem_u32(sA[s2]), A + k1, g.lda, kBM, kb1);
+            stage_tile(smem_u32(sB[s2]), g.B + k1, g.ldb, BN, kb1);
+            asm volatile("cp.async.wait_group 2;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sbo = (kb / 8) * 128;
+            const uint32_t idesc = instr_desc(kBM, BN);
+            for (int kk = 0; kk < kb / 16; ++kk) {
+                const uint64_t da = smem_desc(smem_u32(sA[s]) + kk * 256, 128, sbo);
+                const uint64_t db = smem_desc(smem_u32(sB[s]) + kk * 256, 128, sbo);
+                const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar[s]))
+                : "memory");
+        }
+        last = s;
+    }
+    // every thread waits for the final commit (it covers all earlier MMAs)
+    if (ok) ok = mbar_wait(smem_u32(&mbar[last]), parity[last]);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (g.err && lane == 0) atomicExch(g.err, 1);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        mbar_wait(smem_u32(&mbar[last]), parity[last]);  // once more, bounded
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        float yacc = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 8) {
+            uint32_t r[8];
+            const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int n = c0 + i;
+                float x = __uint_as_float(r[i]);
+                if (g.bias) x += g.bias[n];
+                if (g.relu) x = fmaxf(x, 0.f);
+                if (g.mask && !(__bfloat162float(g.mask[static_cast<size_t>(row) * g.ldm + n]) > 0.f)) x = 0.f;
+                v[i] = x;
+                if (g.head_w) yacc = fmaf(g.head_w[n], x, yacc);
+            }
+            if (g.out_f) {
+                float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
+                o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                o[1] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+            if (g.out_bf) {
+                __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[i]);
+                *reinterpret_cast<uint4*>(g.out_bf + static_cast<size_t>(row) * g.ldo + c0) =
+                    *reinterpret_cast<const uint4*>(b);
+            }
+            if (g.out_bfT) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    g.out_bfT[static_cast<size_t>(c0 + i) * g.ldoT + row] = __float2bfloat16_rn(v[i]);
+            }
+        }
+        if (g.head_w) g.head_y[row] = *g.head_b + yacc;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                     : "memory");
+}
+
+template <int BN>
+constexpr size_t gemm_smem() { return 2 * (kBM * kKB * 2 + BN * kKB * 2); }
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- MLP helpers
+
+constexpr int kMlpIn = 16, kMlpHid = 256;
+constexpr int kMlpParams = kMlpHid * kMlpIn + 2 * (kMlpHid * kMlpHid + kMlpHid) + kMlpHid + 1;
+
+// Offsets in the flat FP32 parameter vector: W1 | W2 | b2 | W3 | b3 | w4 | b4.
+constexpr int kOffW1 = 0, kOffW2 = kOffW1 + kMlpHid * kMlpIn, kOffB2 = kOffW2 + kMlpHid * kMlpHid,
+              kOffW3 = kOffB2 + kMlpHid, kOffB3 = kOffW3 + kMlpHid * kMlpHid,
+              kOffW4 = kOffB3 + kMlpHid, kOffB4 = kOffW4 + kMlpHid;
+
+// Inputs: x_j = theta_j / 3 for the joints, x_7 = 1 (first-layer bias), rest 0.
+// Rows count..rows_pad-1 are zero.  x: rows_pad x 16; xT (nullable): 16 x rows_pad.
+__global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof, int rows_pad,
+                             __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ xT)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows_pad) return;
+    float v[kMlpIn];
+#pragma unroll
+    for (int i = 0; i < kMlpIn; ++i) v[i] = 0.f;
+    if (r < count) {
+        for (int j = 0; j < dof && j < 7; ++j) v[j] = theta[static_cast<size_t>(r) * dof + j] / 3.f;
+        v[7] = 1.f;
+    }
+#pragma unroll
+    for (int i = 0; i < kMlpIn; ++i) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(v[i]);
+        x[static_cast<size_t>(r) * kMlpIn + i] = b;
+        if (xT) xT[static_cast<size_t>(i) * rows_pad + r] = b;
+    }
+}
+
+// FP32 master weights -> BF16 operands: W1, W2, W3 and the transposes W2^T, W3^T.
+__global__ void k_mlp_cast(const float* __restrict__ p, __nv_bfloat16* __restrict__ w1,
+                           __nv_bfloat16* __restrict__ w2, __nv_bfloat16* __restrict__ w2t,
+                           __nv_bfloat16* __restrict__ w3, __nv_bfloat16* __restrict__ w3t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kMlpHid * kMlpIn) w1[i] = __float2bfloat16_rn(p[kOffW1 + i]);
+    if (i < kMlpHid * kMlpHid) {
+        const int n = i / kMlpHid, k = i - n * kMlpHid;
+        const __nv_bfloat16 a = __float2bfloat16_rn(p[kOffW2 + i]);
+        const __nv_bfloat16 b = __float2bfloat16_rn(p[kOffW3 + i]);
+        w2[i] = a;
+        w3[i] = b;
+        w2t[k * kMlpHid + n] = a;
+        w3t[k * kMlpHid + n] = b;
+    }
+}
+
+// He-uniform initialisation from the Philox stream (tag 1): W ~ U(-sqrt(6/fan_in),
+// sqrt(6/fan_in)), biases 0; the first layer's bias column (input 7) starts at 0.
+__global__ void k_mlp_init(float* __restrict__ p, uint32_t seed_lo, uint32_t seed_hi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    const uint4 r = storm::philox4x32_10(make_uint4(static_cast<uint32_t>(i), 0u, 0u, 1u), seed_lo, seed_hi);
+    const float u = 2.f * storm::bits_to_unit(r.x) - 1.f;
+    float v = 0.f;
+    if (i < kOffW2) {
+        v = ((i % kMlpIn) == 7 || (i % kMlpIn) > 7) ? 0.f : u * sqrtf(6.f / 8.f);
+    } else if (i < kOffB2 || (i >= kOffW3 && i < kOffB3)) {
+        v = u * sqrtf(6.f / kMlpHid);
+    } else if (i >= kOffW4 && i < kOffB4) {
+        v = u * sqrtf(6.f / kMlpHid);
+    }
+    p[i] = v;
+}
+
+// Output layer gradient of the mean squared error: r = y - t, dy = 2 r / count,
+// delta3 = dy w4 o [a3 > 0] (BF16, row-major and transposed); rows >= count get 0.
+// loss_part[blockIdx.x] = sum of r^2 over the block's rows (fixed order).
+__global__ void __launch_bounds__(256)
+k_mlp_dhead(const float* __restrict__ y, const float* __restrict__ t, int count, int rows_pad,
+            const __nv_bfloat16* __restrict__ a3, const float* __restrict__ p,
+            float* __restrict__ dy, __nv_bfloat16* __restrict__ d3, __nv_bfloat16* __restrict__ d3T,
+            float* __restrict__ loss_part)
+{
+    const int b = blockIdx.x, n = threadIdx.x;
+    const float r = (b < count) ? y[b] - t[b] : 0.f;
+    const float g = 2.f * r / static_cast<float>(count);
+    if (n == 0) dy[b] = g;
+    const float a = __bfloat162float(a3[static_cast<size_t>(b) * kMlpHid + n]);
+    const __nv_bfloat16 v = __float2bfloat16_rn(a > 0.f ? g * p[kOffW4 + n] : 0.f);
+    d3[static_cast<size_t>(b) * kMlpHid + n] = v;
+    d3T[static_cast<size_t>(n) * rows_pad + b] = v;
+    if (n == 0) loss_part[b] = r * r;
+}
+
+// out[n] = sum_b rows[n][b] (rows: n x rows_pad, contiguous), one block per n.
+__global__ void __launch_bounds__(256)
+k_mlp_rowsum(const __nv_bfloat16* __restrict__ rows, int rows_pad, float* __restrict__ out)
+{
+    __shared__ float sh[32];
+    const int n = blockIdx.x;
+    float acc = 0.f;
+    for (int b = threadIdx.x; b < rows_pad; b += blockDim.x)
+        acc += __bfloat162float(rows[static_cast<size_t>(n) * rows_pad + b]);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[n] = acc;
+}
+
+// dw4[n] = sum_b dy_b a3[b][n]; db4 = sum_b dy_b; loss = sum_b r_b^2 / count.
+__global__ void __launch_bounds__(256)
+k_mlp_head_grad(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ a3, int rows_pad,
+                int count, const float* __restrict__ loss_part, float* __restrict__ grad,
+                float* __restrict__ loss)
+{
+    __shared__ float sh[32];
+    const int n = blockIdx.x;
+    float acc = 0.f;
+    if (n < kMlpHid) {
+        for (int b = threadIdx.x; b < rows_pad; b += blockDim.x)
+            acc = fmaf(dy[b], __bfloat162float(a3[static_cast<size_t>(b) * kMlpHid + n]), acc);
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) grad[kOffW4 + n] = acc;
+    } else if (n == kMlpHid) {
+        for (int b = threadIdx.x; b < rows_pad; b += blockDim.x) acc += dy[b];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) grad[kOffB4] = acc;
+    } else {
+        for (int b = threadIdx.x; b < rows_pad; b += blockDim.x) acc += loss_part[b];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) *loss = acc / static_cast<float>(count);
+    }
+}
+
+// Adam (Kingma & Ba, 2015) with bias correction, step t >= 1.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps, int t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.f - powf(b1, static_cast<float>(t)));
+    const float vh = vi / (1.f - powf(b2, static_cast<float>(t)));
+    w[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// Minibatch gather: theta rows and targets of idx[b0 .. b0 + B).
+__global__ void k_mlp_gather(const float* __restrict__ theta, const float* __restrict__ target,
+                             const int* __restrict__ idx, int b0, int B, int dof,
+                             float* __restrict__ th_out, float* __restrict__ t_out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int s = idx[b0 + b];
+    for (int j = 0; j < dof; ++j) th_out[static_cast<size_t>(b) * dof + j] = theta[static_cast<size_t>(s) * dof + j];
+    t_out[b] = target[s];
+}
+
+// Exact label: minimum signed distance over the self pairs (Eq. 13 reading,
+// positive apart) of each configuration; one warp per configuration.
+__global__ void __launch_bounds__(256)
+k_self_distance(storm::Problem pb, const float* __restrict__ theta, int count, float* __restrict__ sd)
+{
+    extern __shared__ __align__(16) float4 s_c[];  // 8 warps x M centres
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int idx = blockIdx.x * 8 + warp;
+    if (idx >= count) return;
+    float4* cent = s_c + warp * pb.M;
+    const float* th = theta + static_cast<size_t>(idx) * pb.d;
+    float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    float pp[3] = {0.f, 0.f, 0.f};
+    for (int f = 0; f <= pb.d; ++f) {
+        if (f > 0) {
+            const float* dh = pb.dhx + (f - 1) * 8;
+            storm::dh_step(R, pp, dh[0], dh[1], dh[2], dh[3], th[f - 1] + dh[4]);
+        }
+        for (int s = pb.link_first[f] + lane; s < pb.link_first[f + 1]; s += 32) {
+            const float4 q = pb.sph[s];
+            cent[s] = make_float4(fmaf(R[0], q.x, fmaf(R[1], q.y, fmaf(R[2], q.z, pp[0]))),
+                                  fmaf(R[3], q.x, fmaf(R[4], q.y, fmaf(R[5], q.z, pp[1]))),
+                                  fmaf(R[6], q.x, fmaf(R[7], q.y, fmaf(R[8], q.z, pp[2]))), q.w);
+        }
+    }
+    __syncwarp();
+    float best = INFINITY;
+    for (int bk = 0; bk < pb.NPB; ++bk) {
+        const uint4 blk = pb.pblk[bk];
+        const int na = blk.y - blk.x, total = na * static_cast<int>(blk.w);
+        for (int c = lane; c < total; c += 32) {
+            const float4 ca = cent[blk.x + c / blk.w], cb = cent[blk.z + c % blk.w];
+            const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+            best = fminf(best, sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) - ca.w - cb.w);
+        }
+    }
+    for (int k = lane; k < pb.P; k += 32) {
+        const uint32_t pr = pb.pairs[k];
+        const float4 ca = cent[pr & 0xffff], cb = cent[pr >> 16];
+        const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+        best = fminf(best, sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) - ca.w - cb.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) sd[idx] = best;
+}

@@ -7,7 +7,8 @@ oracle may consume its output.
 
 Recipe (all draws from ``numpy.random.default_rng(seed)``):
   * robot: d revolute joints in modified DH form; a_{i-1}, d_i ~ U[0, 0.4] m,
-    alpha_{i-1} ~ U{0, +pi/2, -pi/2}, offsets 0; limits +-2.8 rad.  Seven
+    alpha_{i-1} ~ U{0, +pi/2, -pi/2}, offsets 0, redrawn while a moving link's
+    segment to the next joint is shorter than 0.2 m; limits +-2.8 rad.  Seven
     collision spheres per moving link, evenly spaced on the segment from the
     link's frame origin to the next joint's origin (a fixed 0.1 m stub along z
     for the last link), radii ~ U[0.04, 0.10] m.  Self-collision pairs: every
@@ -105,22 +106,33 @@ class Workload:
     goal: np.ndarray   # (7,) x, y, z, qw, qx, qy, qz
 
 
-def make_robot(seed: int, dof: int = 7, spheres_per_link: int = 7) -> Robot:
+def _segment_end(dh: np.ndarray, i: int) -> np.ndarray:
+    """Origin of joint i+1 in frame i (modified DH row i), or a 0.1 m stub along z
+    after the last joint: where the spheres of link i are placed."""
+    if i < dh.shape[0]:
+        a_i, al_i, d_next = dh[i, 0], dh[i, 1], dh[i, 2]
+        return np.array([a_i, -np.sin(al_i) * d_next, np.cos(al_i) * d_next])
+    return np.array([0.0, 0.0, 0.1])
+
+
+def make_robot(seed: int, dof: int = 7, spheres_per_link: int = 7,
+               min_link: float = 0.2) -> Robot:
+    """Chains are redrawn while any moving link is shorter than `min_link`
+    (a link of near-zero length would put the spheres of its neighbours on top
+    of each other, i.e. in self-collision in every configuration)."""
     rng = np.random.default_rng([seed, 1])
-    a = rng.uniform(0.0, 0.4, dof)
-    d = rng.uniform(0.0, 0.4, dof)
-    alpha = rng.choice(np.array([0.0, np.pi / 2, -np.pi / 2]), dof)
-    dh = np.stack([a, alpha, d, np.zeros(dof)], axis=1)
+    while True:
+        a = rng.uniform(0.0, 0.4, dof)
+        d = rng.uniform(0.0, 0.4, dof)
+        alpha = rng.choice(np.array([0.0, np.pi / 2, -np.pi / 2]), dof)
+        dh = np.stack([a, alpha, d, np.zeros(dof)], axis=1)
+        if all(np.linalg.norm(_segment_end(dh, i)) >= min_link for i in range(1, dof)):
+            break
     q_min = np.full(dof, -2.8)
     q_max = np.full(dof, 2.8)
     links, centres = [], []
     for i in range(1, dof + 1):
-        # segment from frame i's origin to frame i+1's origin, in frame i
-        if i < dof:
-            a_i, al_i, d_next = dh[i, 0], dh[i, 1], dh[i, 2]
-            end = np.array([a_i, -np.sin(al_i) * d_next, np.cos(al_i) * d_next])
-        else:
-            end = np.array([0.0, 0.0, 0.1])
+        end = _segment_end(dh, i)  # segment from frame i's origin to frame i+1's origin
         for k in range(spheres_per_link):
             f = (k + 0.5) / spheres_per_link
             links.append(i)

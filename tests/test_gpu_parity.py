@@ -101,7 +101,7 @@ def test_rollout_stage_parity(name):
 def test_rollout_collision_terms_active():
     """The paper-scale workload exercises every cost term (none identically zero)."""
     wl, p = VARIANTS["paper"]
-    state = W.make_state(15, 7)  # chosen on the oracle: every term active
+    state = W.make_state(21, 7)  # chosen on the oracle: every term active
     state[0, 3], state[1, 3] = 2.2, 0.8  # joint 4 heading through its soft limit (2.24)
     orc, g, o = _rollout_pair(wl, p, seed=3, state=state)
     for t, name in enumerate(W.TERM_NAMES):
