@@ -64,6 +64,26 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+def kernel_source_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2104_13542_b300", "csrc", "*.cu")) +
+                    glob.glob(os.path.join(ROOT, "paper_2104_13542_b300", "csrc", "*.cuh"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def rollout_traffic():
+    """DRAM bytes per rollout launch from the committed ncu summary, or None when
+    the kernels changed since that capture."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_rollout"]
+    except Exception:
+        return None
+    return rec["dram_bytes_per_launch"] if rec.get("src_sha256_16") == kernel_source_hash() else None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -261,7 +281,7 @@ def run_gpu(args, rank, world_size):
                             "p99": float(np.percentile(e2e_ms, 99))},
              "closed_loop_final_pos_err_m": pos_err},
         roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                  "frac": achieved / peak, "traffic": None,
+                  "frac": achieved / peak, "traffic": rollout_traffic(),
                   "kernel": "k_rollout", "kernel_ms": rk_ms, "flops_per_launch": flops_launch,
                   "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                 f"{sm_mhz:.0f} MHz (fallback-free unit count; SM max clock)"},
@@ -271,6 +291,98 @@ def run_gpu(args, rank, world_size):
     )
     ctl.close()
     return res, wl
+
+
+def _time_steps(step_fn, stream, flush, n):
+    import torch
+    ev = []
+    for i in range(n):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step_fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def run_variants(args, seed: int):
+    """The gradient-refined, batched and surrogate forms next to the plain step,
+    same GPU, same timing rules (device time per step, L2 flushed before each)."""
+    import torch
+    from paper_2104_13542_b300 import BatchController, Controller, SurrogateMLP
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    n = max(20, min(args.steps, 200))
+    out = {}
+    # plain and gradient-refined paper-scale steps
+    for name, wl in (("plain", W.config_paper(seed)), ("refined_grad5", W.config_differentiable(seed))):
+        p = wl.params
+        with Controller(wl.robot, wl.world, p) as c:
+            st, gl = wl.state.astype(np.float32), wl.goal.astype(np.float32)
+            c.step(st, gl)
+            for _ in range(3):
+                c.step_resident()
+            ms = _time_steps(c.step_resident, c.stream, flush, n)
+            entry = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99)),
+                     "rollout_steps_per_s": p.N * p.H * p.K * len(ms) / float(ms.sum() / 1e3)}
+            if p.grad_steps:
+                mu, _ = c.get_distribution()
+                m = torch.as_tensor(mu, device="cuda")
+                s_d, g_d = torch.as_tensor(st.reshape(-1), device="cuda"), torch.as_tensor(gl, device="cuda")
+                J0, g = c.cost_grad(m, s_d, g_d, 7, 0)
+                Js = [float(J0[0])]
+                for _ in range(p.grad_steps):
+                    m = m - p.grad_eta * g
+                    J, g = c.cost_grad(m, s_d, g_d, 7, 0)
+                    Js.append(float(J[0]))
+                entry["grad_steps"] = p.grad_steps
+                entry["J_along_refinement"] = Js
+            out[name] = entry
+    # batched uneven instances
+    wls = W.config_batch(seed, 256)
+    with BatchController([w.robot for w in wls], [w.world for w in wls], [w.params for w in wls]) as b:
+        b.step([w.state.astype(np.float32) for w in wls], np.stack([w.goal for w in wls]).astype(np.float32))
+        t_tune = b.autotune()
+        for _ in range(3):
+            b.step_resident()
+        ms = _time_steps(b.step_resident, b.stream, flush, n)
+        units = sum(w.params.N * w.params.H * w.params.K for w in wls)
+        out["batched_256"] = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99)),
+                              "rollout_steps_per_s": units * len(ms) / float(ms.sum() / 1e3),
+                              "instances": len(wls), "rollout_steps_per_step": units,
+                              "tile": b.get_launch(), "autotune_rollout_us": t_tune}
+    # learned self-collision surrogate at 1000 x 30
+    wl = W.config_paper(seed, N=1000, H=30)
+    margin = 0.05
+    with Controller(wl.robot, wl.world, wl.params.replace(N=8)) as lab:
+        rng = np.random.default_rng([seed, 77])
+        th = torch.as_tensor(rng.uniform(-2.8, 2.8, (262_144, 7)).astype(np.float32), device="cuda")
+        th_te = torch.as_tensor(rng.uniform(-2.8, 2.8, (65_536, 7)).astype(np.float32), device="cuda")
+        sd, sd_te = lab.self_distance(th), lab.self_distance(th_te)
+    net = SurrogateMLP(seed=seed)
+    t0 = time.perf_counter()
+    losses = net.train(th, torch.clamp(sd, max=0.5), batch=4096, epochs=8, lr=2e-3, seed=seed)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    y, ref = net.predict(th_te).cpu().numpy(), sd_te.cpu().numpy()
+    near, coll = ref < 0.5, ref < 0.0
+    acc = {"mae_m": float(np.abs(y[near] - ref[near]).mean()),
+           "false_negative_rate": float(np.mean(y[coll] >= margin)) if coll.any() else 0.0,
+           "skip_fraction": float(np.mean(y >= margin)), "margin_m": margin,
+           "train_s": train_s, "train_samples": int(th.shape[0]), "epochs": len(losses),
+           "final_loss": float(losses[-1])}
+    for name in ("exact_1000x30", "surrogate_1000x30"):
+        with Controller(wl.robot, wl.world, wl.params) as c:
+            if name.startswith("surrogate"):
+                c.set_surrogate(net, margin)
+            c.step(wl.state.astype(np.float32), wl.goal.astype(np.float32))
+            ms = _time_steps(c.step_resident, c.stream, flush, n)
+            out[name] = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99))}
+    out["surrogate_1000x30"].update(acc)
+    net.close()
+    return out
 
 
 def cpu_baseline(wl, budget_s: float = 12.0, n_sample: int | None = None):
@@ -344,6 +456,7 @@ def main():
     ap.add_argument("--ref-particles", type=int, default=25)
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -384,6 +497,8 @@ def main():
         "latency_ms": res["latency_ms"], "e2e": res["e2e"], "roofline": res["roofline"],
         "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
     }
+    if world_size == 1 and not args.no_variants:
+        line["variants"] = run_variants(args, args.seed)
     if world_size == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget_s)
     print(json.dumps(line))
