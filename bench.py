@@ -146,10 +146,13 @@ class ClockSampler:
 
 
 def goals_for(ctl, robot, seed: int, count: int):
-    """Reachable goal poses X_g = FK(theta_g), theta_g ~ U[-2.24, 2.24]."""
+    """Reachable goal poses X_g = FK(theta_g), theta_g ~ U[-2.24, 2.24] drawn until the
+    configuration is at least 3 cm clear of self-collision (exact check of the library)."""
     import torch
     rng = np.random.default_rng([seed, 99])
-    th = rng.uniform(-2.24, 2.24, (count, robot.dof)).astype(np.float32)
+    cand = rng.uniform(-2.24, 2.24, (64 * count, robot.dof)).astype(np.float32)
+    sd = ctl.self_distance(torch.as_tensor(cand, device="cuda")).cpu().numpy()
+    th = cand[sd > 0.03][:count]
     ee = ctl.forward_kinematics(torch.as_tensor(th, device="cuda")).cpu().numpy()
     goals = []
     for T in ee:

@@ -218,12 +218,14 @@ def config_small(seed: int = 0) -> Workload:
 
 def config_paper(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
     """Paper-scale step: 500 particles x horizon 30, 7 joints, 6-knot cubic B-spline
-    noise, 3 iterations with mean + diagonal covariance update, all cost terms,
-    49 link spheres, 20 boxes + 10 spheres."""
+    noise, 3 iterations with mean + diagonal covariance update (sigma floored at
+    0.1: without a floor the near-argmin weights collapse sigma and the arm
+    stalls), 2 null particles, all cost terms, 49 link spheres, 20 boxes + 10
+    spheres."""
     robot = make_robot(seed, 7)
     world = make_world(seed, 20, 10)
     p = Params(N=N, H=H, K=3, n_knots=6, dt=np.full(H, 0.02), beta=10.0, gamma=0.99,
-               alpha_mu=1.0, alpha_sigma=0.5, sigma_init=0.5, sigma_min=0.0,
+               alpha_mu=1.0, alpha_sigma=0.5, sigma_init=0.5, sigma_min=0.1, n_null=2,
                w_pos=150.0, w_rot=20.0, w_stop=10.0, w_joint=100.0, w_manip=30.0,
                w_coll=1000.0, w_smooth=0.0, seed=2000 + seed)
     return Workload(f"storm_{N}x{H}_7dof_k3_spline6", robot, world, p, make_state(seed, 7),
@@ -254,7 +256,8 @@ def config_batch(seed: int = 0, count: int = 256) -> list:
         robot = make_robot(s, dof)
         world = make_world(s, n_boxes=(n_obs + 1) // 2, n_spheres=n_obs // 2)
         p = Params(N=N, H=H, K=1, n_knots=6, dt=np.full(H, 0.02), beta=10.0, gamma=0.99,
-                   alpha_mu=1.0, alpha_sigma=0.5, sigma_init=0.5, w_pos=150.0, w_rot=20.0,
+                   alpha_mu=1.0, alpha_sigma=0.5, sigma_init=0.5, sigma_min=0.1, n_null=2,
+                   w_pos=150.0, w_rot=20.0,
                    w_stop=10.0, w_joint=100.0, w_manip=30.0, w_coll=1000.0, w_smooth=0.0,
                    seed=3000 + seed, instance=i)
         out.append(Workload(f"batch{i}_{N}x{H}_{dof}dof_{n_obs}obs", robot, world, p,

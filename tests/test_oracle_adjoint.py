@@ -104,7 +104,7 @@ def test_cost_gradient_matches_finite_differences():
 
 def test_cost_gradient_null_particles_and_spline():
     wl = W.config_paper(7, N=3, H=10)
-    p = wl.params.replace(N=3, H=10, n_knots=5)
+    p = wl.params.replace(N=3, H=10, n_knots=5, n_null=0)
     o = oracle.Oracle(wl.robot, wl.world, p)
     mu, sig = W.make_mean(7, 10, 7), W.make_sigma(7, 7)
     eps = o.noise(0, 1)

@@ -174,7 +174,7 @@ def test_controls_null_particles_and_no_spline():
 
 def test_controls_with_spline_constant_knots():
     wl = W.config_paper(0, N=4, H=30)
-    o = oracle.Oracle(wl.robot, wl.world, wl.params)
+    o = oracle.Oracle(wl.robot, wl.world, wl.params.replace(n_null=0))
     mu = W.make_mean(2, 30, 7)
     sig = W.make_sigma(2, 7)
     eps = np.broadcast_to(np.arange(7.0)[None, None, :], (4, 6, 7)).copy()
