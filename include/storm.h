@@ -236,6 +236,20 @@ int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count,
 int storm_set_launch(storm_handle* h, int particles_per_cta, int threads_per_cta);
 int storm_get_launch(const storm_handle* h, int* particles_per_cta, int* threads_per_cta);
 
+/* Tracing: with trace_dev (device, 7 x uint64) set, thread 0 of rollout CTA 0
+ * writes %globaltimer (ns) at the phase boundaries of every rollout launch:
+ * [0] start, [1] tables + noise staged, [2] controls + integration, [3] FK,
+ * Jacobian and non-collision costs, [4] world collision, [5] self collision,
+ * [6] end.  NULL turns it off.  Re-captures the step graph. */
+int storm_set_trace(storm_handle* h, unsigned long long* trace_dev);
+
+/* Collision broad phase (on by default): each link's spheres are enclosed in
+ * one bounding sphere (fixed in the link frame, padded by 1e-4 m), and the
+ * exact sphere-obstacle and sphere-pair tests run only where two such bounds,
+ * or a bound and an obstacle, overlap.  The costs are identical either way;
+ * off runs every exact test (brute force).  Re-captures the step graph. */
+int storm_set_broadphase(storm_handle* h, int on);
+
 /* Autotuner: times this handle's rollout kernel (sample_controls +
  * generate_rollouts) with CUDA events on its stream for every candidate shape
  * -- particles per CTA 1, 2, 3, 4, 6, 8, 12, 16 (at most N and 512/H) x

@@ -43,7 +43,7 @@ EXPORTED = [
     "storm_batch_set_distribution", "storm_batch_autotune", "storm_batch_get_launch",
     "storm_mlp_create", "storm_mlp_destroy", "storm_mlp_last_error", "storm_mlp_get_params",
     "storm_mlp_set_params", "storm_mlp_predict", "storm_mlp_loss_grad", "storm_mlp_train",
-    "storm_self_distance", "storm_set_surrogate",
+    "storm_self_distance", "storm_set_surrogate", "storm_set_broadphase", "storm_set_trace",
 ]
 MLP_PARAMS = 135937
 
@@ -163,6 +163,8 @@ def lib():
                                       C.c_uint64, _fp]
         L.storm_self_distance.argtypes = [vp, vp, C.c_int, vp]
         L.storm_set_surrogate.argtypes = [vp, vp, C.c_double]
+        L.storm_set_broadphase.argtypes = [vp, C.c_int]
+        L.storm_set_trace.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -406,6 +408,14 @@ class Controller:
     def set_launch(self, particles_per_cta: int, threads: int):
         self._check(lib().storm_set_launch(self.h, int(particles_per_cta), int(threads)))
 
+    def set_trace(self, trace_dev):
+        """trace_dev: int64 CUDA tensor of 7 entries (phase stamps in ns) or None."""
+        self._check(lib().storm_set_trace(self.h, _dptr(trace_dev)))
+        self._trace = trace_dev
+
+    def set_broadphase(self, on: bool):
+        self._check(lib().storm_set_broadphase(self.h, int(bool(on))))
+
     def get_launch(self):
         a, b = C.c_int(), C.c_int()
         self._check(lib().storm_get_launch(self.h, C.byref(a), C.byref(b)))
@@ -570,6 +580,14 @@ class BatchController:
         t = C.c_float()
         self._check(lib().storm_batch_autotune(self.h, C.byref(t)))
         return t.value
+
+    def set_trace(self, trace_dev):
+        """trace_dev: int64 CUDA tensor of 7 entries (phase stamps in ns) or None."""
+        self._check(lib().storm_set_trace(self.h, _dptr(trace_dev)))
+        self._trace = trace_dev
+
+    def set_broadphase(self, on: bool):
+        self._check(lib().storm_set_broadphase(self.h, int(bool(on))))
 
     def get_launch(self):
         a, b = C.c_int(), C.c_int()

@@ -28,10 +28,9 @@ using namespace storm;
 // ============================================================================ layout
 
 struct RolloutLayout {
-    int frame, cent, sph, wsph, boxlh, pblk;                // 16-byte arrays
-    int mu, sigma, eps, u, th, thd, basis, dt, gpow, vmax;  // float arrays
-    int dhx, qlo, qhi, boxes, part, dself, dworld, goal, state;
-    int first, slink, pairs;                                // int arrays
+    int tab, frame, boxlh;                                  // 16-byte arrays
+    int mu, sigma, eps, u, th, thd, part, dself, dworld, goal, state;  // float arrays
+    int slink;                                              // int arrays
     int bytes;
 };
 
@@ -42,42 +41,38 @@ __host__ __device__ inline int take_(int& off, int bytes)
     return o;
 }
 
-// Shared-memory plan of one rollout CTA (identical on host and device).
+// Shared-memory plan of one rollout CTA (identical on host and device): a copy
+// of the per-problem tables, then the CTA's working arrays.
 __host__ __device__ inline RolloutLayout rollout_layout(const Problem& pb)
 {
     RolloutLayout L;
     int off = 0;
     const int I = pb.ppc * pb.H;
+    L.tab = take_(off, pb.table_bytes);
     L.frame = take_(off, I * (pb.d + 1) * 3 * 16);
-    L.cent = take_(off, I * pb.M * 16);
-    L.sph = take_(off, pb.M * 16);
-    L.wsph = take_(off, pb.O * 16);
     L.boxlh = take_(off, pb.B * 2 * 16);
-    L.pblk = take_(off, pb.NPB * 16);
     L.mu = take_(off, pb.H * pb.d * 4);
     L.sigma = take_(off, pb.d * 4);
     L.eps = take_(off, pb.ppc * pb.S * pb.d * 4);
     L.u = take_(off, pb.ppc * pb.H * pb.d * 4);
     L.th = take_(off, pb.ppc * pb.H * pb.d * 4);
     L.thd = take_(off, pb.ppc * pb.H * pb.d * 4);
-    L.basis = take_(off, pb.spline ? pb.H * pb.S * 4 : 0);
-    L.dt = take_(off, pb.H * 4);
-    L.gpow = take_(off, pb.H * 4);
-    L.vmax = take_(off, pb.H * 4);
-    L.dhx = take_(off, pb.d * 8 * 4);
-    L.qlo = take_(off, pb.d * 4);
-    L.qhi = take_(off, pb.d * 4);
-    L.boxes = take_(off, pb.B * 6 * 4);
     L.part = take_(off, I * 4);
     L.dself = take_(off, I * 4);
     L.dworld = take_(off, I * 4);
     L.goal = take_(off, 12 * 4);
     L.state = take_(off, 3 * pb.d * 4);
-    L.first = take_(off, (pb.d + 2) * 4);
     L.slink = take_(off, pb.M * 4);
-    L.pairs = take_(off, pb.P * 4);
     L.bytes = off;
     return L;
+}
+
+// Where table `p` of the device table block lands in the shared-memory copy.
+template <typename T>
+__device__ __forceinline__ const T* in_copy(const unsigned char* copy, const uint4* base, const T* p)
+{
+    return reinterpret_cast<const T*>(copy + (reinterpret_cast<const unsigned char*>(p) -
+                                              reinterpret_cast<const unsigned char*>(base)));
 }
 
 struct RolloutOut {
@@ -107,75 +102,36 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
 {
     const RolloutLayout L = rollout_layout(pb);
     float4* s_frame = reinterpret_cast<float4*>(smem + L.frame);
-    float4* s_cent = reinterpret_cast<float4*>(smem + L.cent);
-    float4* s_sph = reinterpret_cast<float4*>(smem + L.sph);
-    float4* s_wsph = reinterpret_cast<float4*>(smem + L.wsph);
     float4* s_boxlh = reinterpret_cast<float4*>(smem + L.boxlh);
-    uint4* s_pblk = reinterpret_cast<uint4*>(smem + L.pblk);
     float* s_mu = reinterpret_cast<float*>(smem + L.mu);
     float* s_sigma = reinterpret_cast<float*>(smem + L.sigma);
     float* s_eps = reinterpret_cast<float*>(smem + L.eps);
     float* s_u = reinterpret_cast<float*>(smem + L.u);
     float* s_th = reinterpret_cast<float*>(smem + L.th);
     float* s_thd = reinterpret_cast<float*>(smem + L.thd);
-    float* s_basis = reinterpret_cast<float*>(smem + L.basis);
-    float* s_dt = reinterpret_cast<float*>(smem + L.dt);
-    float* s_gpow = reinterpret_cast<float*>(smem + L.gpow);
-    float* s_vmax = reinterpret_cast<float*>(smem + L.vmax);
-    float* s_dhx = reinterpret_cast<float*>(smem + L.dhx);
-    float* s_qlo = reinterpret_cast<float*>(smem + L.qlo);
-    float* s_qhi = reinterpret_cast<float*>(smem + L.qhi);
-    float* s_boxes = reinterpret_cast<float*>(smem + L.boxes);
     float* s_part = reinterpret_cast<float*>(smem + L.part);
     float* s_dself = reinterpret_cast<float*>(smem + L.dself);
     float* s_dworld = reinterpret_cast<float*>(smem + L.dworld);
     float* s_goal = reinterpret_cast<float*>(smem + L.goal);
     float* s_state = reinterpret_cast<float*>(smem + L.state);
-    int* s_first = reinterpret_cast<int*>(smem + L.first);
     int* s_slink = reinterpret_cast<int*>(smem + L.slink);
-    uint32_t* s_pairs = reinterpret_cast<uint32_t*>(smem + L.pairs);
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int d = pb.d, H = pb.H, S = pb.S, M = pb.M, F = pb.d + 1;
     const int I = np * H;
     const int HD = H * d;
+    trace_stamp(pb.trace, 0);
 
-    // ---- stage per-problem tables
+    // ---- stage: the per-problem tables in one vectorised copy, then mu, sigma,
+    // the state and the goal rotation
+    {
+        const uint4* src = pb.tables;
+        uint4* dst = reinterpret_cast<uint4*>(smem + L.tab);
+        for (int i = tid; i < pb.table_bytes / 16; i += nt) dst[i] = src[i];
+    }
     for (int i = tid; i < HD; i += nt) s_mu[i] = pb.mu[i];
-    for (int i = tid; i < d; i += nt) {
-        s_sigma[i] = pb.sigma[i];
-        s_qlo[i] = pb.qlo[i];
-        s_qhi[i] = pb.qhi[i];
-    }
+    for (int i = tid; i < d; i += nt) s_sigma[i] = pb.sigma[i];
     for (int i = tid; i < 3 * d; i += nt) s_state[i] = state[i];
-    for (int i = tid; i < H; i += nt) {
-        s_dt[i] = pb.dt[i];
-        s_gpow[i] = pb.gpow[i];
-        s_vmax[i] = pb.vmax[i];
-    }
-    if (pb.spline)
-        for (int i = tid; i < H * S; i += nt) s_basis[i] = pb.basis[i];
-    for (int i = tid; i < d * 8; i += nt) s_dhx[i] = pb.dhx[i];
-    for (int i = tid; i < d + 2; i += nt) s_first[i] = pb.link_first[i];
-    for (int i = tid; i < M; i += nt) {
-        s_sph[i] = pb.sph[i];
-        int f = 0;
-        while (f < d && i >= pb.link_first[f + 1]) ++f;
-        s_slink[i] = f;
-    }
-    for (int i = tid; i < pb.P; i += nt) s_pairs[i] = pb.pairs[i];
-    for (int i = tid; i < pb.NPB; i += nt) s_pblk[i] = pb.pblk[i];
-    for (int i = tid; i < pb.B; i += nt) {
-        float b[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            b[k] = pb.boxes[i * 6 + k];
-            s_boxes[i * 6 + k] = b[k];
-        }
-        s_boxlh[2 * i] = make_float4(b[0] - b[3], b[1] - b[4], b[2] - b[5], 0.f);
-        s_boxlh[2 * i + 1] = make_float4(b[0] + b[3], b[1] + b[4], b[2] + b[5], 0.f);
-    }
-    for (int i = tid; i < pb.O; i += nt) s_wsph[i] = pb.wsph[i];
     if (tid == 0) {
         // goal rotation R_g (row-major) from the normalised quaternion, then p_g
         const float qn = rsqrtf(goal[3] * goal[3] + goal[4] * goal[4] + goal[5] * goal[5] +
@@ -193,6 +149,33 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         s_goal[9] = goal[0];
         s_goal[10] = goal[1];
         s_goal[11] = goal[2];
+    }
+    __syncthreads();
+    const unsigned char* tab = smem + L.tab;
+    const float* s_dhx = in_copy(tab, pb.tables, pb.dhx);
+    const float* s_qlo = in_copy(tab, pb.tables, pb.qlo);
+    const float* s_qhi = in_copy(tab, pb.tables, pb.qhi);
+    const float4* s_sph = in_copy(tab, pb.tables, pb.sph);
+    const int* s_first = in_copy(tab, pb.tables, pb.link_first);
+    const uint32_t* s_pairs = in_copy(tab, pb.tables, pb.pairs);
+    const uint4* s_pblk = in_copy(tab, pb.tables, pb.pblk);
+    const float4* s_lb = in_copy(tab, pb.tables, pb.lbound);
+    const float* s_boxes = in_copy(tab, pb.tables, pb.boxes);
+    const float4* s_wsph = in_copy(tab, pb.tables, pb.wsph);
+    const float* s_dt = in_copy(tab, pb.tables, pb.dt);
+    const float* s_gpow = in_copy(tab, pb.tables, pb.gpow);
+    const float* s_vmax = in_copy(tab, pb.tables, pb.vmax);
+    const float* s_basis = in_copy(tab, pb.tables, pb.basis);
+    // derived per-CTA tables (read after the next barrier)
+    for (int i = tid; i < M; i += nt) {
+        int f = 0;
+        while (f < d && i >= s_first[f + 1]) ++f;
+        s_slink[i] = f;
+    }
+    for (int i = tid; i < pb.B; i += nt) {
+        const float* b = s_boxes + i * 6;
+        s_boxlh[2 * i] = make_float4(b[0] - b[3], b[1] - b[4], b[2] - b[5], 0.f);
+        s_boxlh[2 * i + 1] = make_float4(b[0] + b[3], b[1] + b[4], b[2] + b[5], 0.f);
     }
 
     // ---- noise eps[n][s][j] for this CTA's particles
@@ -217,6 +200,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         for (int i = tid; i < np * per; i += nt) s_eps[i] = pb.halton[static_cast<size_t>(n0) * per + i];
     }
     __syncthreads();
+    trace_stamp(pb.trace, 1);
 
     // ---- controls u = mu + sigma o (B eps), null particles zero
     for (int i = tid; i < np * HD; i += nt) {
@@ -247,6 +231,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         }
     }
     __syncthreads();
+    trace_stamp(pb.trace, 2);
     if (out.theta)
         for (int i = tid; i < np * HD; i += nt) out.theta[static_cast<size_t>(n0) * HD + i] = s_th[i];
     if (out.theta_dot)
@@ -265,9 +250,6 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
 
         float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
         float pp[3] = {0.f, 0.f, 0.f};
-        const bool want_manip = pb.w_manip != 0.f || out.terms;
-        GramFactor G;
-        G.zero();
         fr[0] = make_float4(1.f, 0.f, 0.f, 0.f);
         fr[1] = make_float4(0.f, 1.f, 0.f, 0.f);
         fr[2] = make_float4(0.f, 0.f, 1.f, 0.f);
@@ -279,15 +261,6 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
                     fr[(i + 1) * 3 + r] = make_float4(R[r * 3 + 0], R[r * 3 + 1], R[r * 3 + 2], pp[r]);
-                if (want_manip) {
-                    // geometric Jacobian column (Eq. 8) about the base origin,
-                    // [o_i x z_i; z_i]: det(J J^T) does not depend on the
-                    // reference point (J(p) = [[I, -[p]x], [0, I]] J(0))
-                    const float zx = R[2], zy = R[5], zz = R[8];
-                    float x[6] = {pp[1] * zz - pp[2] * zy, pp[2] * zx - pp[0] * zz,
-                                  pp[0] * zy - pp[1] * zx, zx, zy, zz};
-                    G.add(x);
-                }
             }
         }
 
@@ -333,14 +306,9 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         }
         c_stop = sqrtf(c_stop);
         c_joint = sqrtf(c_joint);
-        // manipulability (Eq. 12)
-        float c_manip = 0.f;
-        if (want_manip) {
-            const float m = G.sqrt_det();
-            c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
-        }
+        // (manipulability, Eq. 12, is added in the collision phase)
         s_part[item] = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop +
-                       pb.w_joint * c_joint + pb.w_manip * c_manip + pb.w_smooth * c_smooth;
+                       pb.w_joint * c_joint + pb.w_smooth * c_smooth;
         s_dself[item] = 0.f;
         s_dworld[item] = 0.f;
         const size_t g = static_cast<size_t>(n0) * H + item;
@@ -360,14 +328,104 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
             t[1] = c_rot;
             t[2] = c_stop;
             t[3] = c_joint;
-            t[4] = c_manip;
             t[7] = c_smooth;
         }
     }
     __syncthreads();
+    trace_stamp(pb.trace, 3);
 
-    // ---- sphere centres and world collision over (step, sphere), Eq. 14 reading:
-    // clamp test d(c, box)^2 < r^2 first, exact signed distance only on contact
+    // ---- world collision, Eq. 14 reading.  Broad phase: per (step, link) the
+    // link's bounding sphere against every obstacle, and the exact per-sphere
+    // test (below) only for the obstacles it touches.  Brute force otherwise:
+    // per (step, sphere) against every obstacle.  Both give the same depths.
+    // Manipulability (Eq. 12) shares this phase: its long dependent chain is
+    // hidden behind the other warps' collision work.  The geometric Jacobian
+    // is taken about the base origin, columns [o_i x z_i; z_i] -- det(J J^T)
+    // does not depend on the reference point (J(p) = [[I, -[p]x], [0, I]] J(0)).
+    const bool want_manip = pb.w_manip != 0.f || out.terms;
+    const int NMU = want_manip ? I : 0;
+    // one manipulability unit per thread, taken by the last threads of the CTA
+    for (int item = nt - 1 - tid; item < NMU && item >= 0; item += nt) {
+        const float4* fr = s_frame + item * F * 3;
+        float J[6][kMaxDof];
+#pragma unroll
+        for (int i = 0; i < kMaxDof; ++i) {
+            if (i < d) {
+                const float4 r0 = fr[(i + 1) * 3], r1 = fr[(i + 1) * 3 + 1], r2 = fr[(i + 1) * 3 + 2];
+                J[0][i] = r1.w * r2.z - r2.w * r1.z;
+                J[1][i] = r2.w * r0.z - r0.w * r2.z;
+                J[2][i] = r0.w * r1.z - r1.w * r0.z;
+                J[3][i] = r0.z;
+                J[4][i] = r1.z;
+                J[5][i] = r2.z;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 6; ++r) J[r][i] = 0.f;
+            }
+        }
+        const float m = manipulability_mgs(J, d);
+        const float c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
+        s_part[item] += pb.w_manip * c_manip;  // this unit alone writes s_part here
+        if (out.terms) out.terms[(static_cast<size_t>(n0) * H + item) * STORM_NTERMS + 4] = c_manip;
+    }
+    if (pb.broadphase) {
+        for (int idx = tid; idx < I * F; idx += nt) {
+            const int item = idx / F, f = idx - item * F;
+            const int s0 = s_first[f], s1 = s_first[f + 1];
+            if (s0 == s1) continue;
+            const float4* T = s_frame + (item * F + f) * 3;
+            const float4 r0 = T[0], r1 = T[1], r2 = T[2];
+            const float4 lb = s_lb[f];
+            const float bx = fmaf(r0.x, lb.x, fmaf(r0.y, lb.y, fmaf(r0.z, lb.z, r0.w)));
+            const float by = fmaf(r1.x, lb.x, fmaf(r1.y, lb.y, fmaf(r1.z, lb.z, r1.w)));
+            const float bz = fmaf(r2.x, lb.x, fmaf(r2.y, lb.y, fmaf(r2.z, lb.z, r2.w)));
+            const float R2 = lb.w * lb.w;
+            float depth = 0.f;
+            for (int b = 0; b < pb.B; ++b) {
+                const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
+                const float ex = bx - fminf(fmaxf(bx, lo.x), hi.x);
+                const float ey = by - fminf(fmaxf(by, lo.y), hi.y);
+                const float ez = bz - fminf(fmaxf(bz, lo.z), hi.z);
+                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= R2) continue;
+                const float* box = s_boxes + b * 6;
+                for (int s = s0; s < s1; ++s) {
+                    const float4 q = s_sph[s];
+                    const float cx = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
+                    const float cy = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
+                    const float cz = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
+                    const float fx = cx - fminf(fmaxf(cx, lo.x), hi.x);
+                    const float fy = cy - fminf(fmaxf(cy, lo.y), hi.y);
+                    const float fz = cz - fminf(fmaxf(cz, lo.z), hi.z);
+                    if (fmaf(fx, fx, fmaf(fy, fy, fz * fz)) < q.w * q.w) {
+                        const float qx = fabsf(cx - box[0]) - box[3];
+                        const float qy = fabsf(cy - box[1]) - box[4];
+                        const float qz = fabsf(cz - box[2]) - box[5];
+                        const float ox = fmaxf(qx, 0.f), oy = fmaxf(qy, 0.f), oz = fmaxf(qz, 0.f);
+                        const float sd = sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) +
+                                         fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f) - q.w;
+                        depth = fmaxf(depth, -sd);
+                    }
+                }
+            }
+            for (int k = 0; k < pb.O; ++k) {
+                const float4 w = s_wsph[k];
+                const float ex = bx - w.x, ey = by - w.y, ez = bz - w.z;
+                const float rb = lb.w + w.w;
+                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rb * rb) continue;
+                for (int s = s0; s < s1; ++s) {
+                    const float4 q = s_sph[s];
+                    const float cx = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
+                    const float cy = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
+                    const float cz = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
+                    const float gx = cx - w.x, gy = cy - w.y, gz = cz - w.z;
+                    const float dist2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                    const float rs = q.w + w.w;
+                    if (dist2 < rs * rs) depth = fmaxf(depth, rs - sqrtf(dist2));
+                }
+            }
+            if (depth > 0.f) atomicMax(reinterpret_cast<int*>(s_dworld + item), __float_as_int(depth));
+        }
+    } else
     for (int idx = tid; idx < I * M; idx += nt) {
         const int item = idx / M, s = idx - item * M;
         const float4 q = s_sph[s];
@@ -378,7 +436,6 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         c.y = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
         c.z = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
         c.w = q.w;
-        s_cent[idx] = c;
         const float r2s = c.w * c.w;
         float depth = 0.f;
         for (int b = 0; b < pb.B; ++b) {
@@ -408,6 +465,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         if (depth > 0.f) atomicMax(reinterpret_cast<int*>(s_dworld + item), __float_as_int(depth));
     }
     __syncthreads();
+    trace_stamp(pb.trace, 4);
     // ---- self collision, Eq. 13 reading.  Pair blocks (every sphere of one
     // link against up to 8 spheres of another) keep the 8 centres in registers
     // while streaming the first link's spheres; leftover pairs one by one.
@@ -416,18 +474,47 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
         if (pred && pred[item] >= pb.self_margin) continue;  // surrogate: clearly apart
         const uint4 blk = s_pblk[bk];  // a0, a1, b0, nb
-        const float4* ci = s_cent + item * M;
+        const int la = s_slink[blk.x], lbk = s_slink[blk.z];
+        const float4* fa = s_frame + (item * F + la) * 3;
+        const float4* fb = s_frame + (item * F + lbk) * 3;
+        if (pb.broadphase) {  // the two links' bounding spheres apart: no sphere pair touches
+            const float4 ba = s_lb[la], bb = s_lb[lbk];
+            const float ex = (fmaf(fa[0].x, ba.x, fmaf(fa[0].y, ba.y, fmaf(fa[0].z, ba.z, fa[0].w)))) -
+                             (fmaf(fb[0].x, bb.x, fmaf(fb[0].y, bb.y, fmaf(fb[0].z, bb.z, fb[0].w))));
+            const float ey = (fmaf(fa[1].x, ba.x, fmaf(fa[1].y, ba.y, fmaf(fa[1].z, ba.z, fa[1].w)))) -
+                             (fmaf(fb[1].x, bb.x, fmaf(fb[1].y, bb.y, fmaf(fb[1].z, bb.z, fb[1].w))));
+            const float ez = (fmaf(fa[2].x, ba.x, fmaf(fa[2].y, ba.y, fmaf(fa[2].z, ba.z, fa[2].w)))) -
+                             (fmaf(fb[2].x, bb.x, fmaf(fb[2].y, bb.y, fmaf(fb[2].z, bb.z, fb[2].w))));
+            const float rr = ba.w + bb.w;
+            if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rr * rr) continue;
+        }
         float4 cb[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) cb[k] = k < static_cast<int>(blk.w) ? ci[blk.z + k] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
-        float depth = 0.f;
-        for (uint32_t a = blk.x; a < blk.y; ++a) {
-            const float4 ca = ci[a];
+        {
+            const float4 r0 = fb[0], r1 = fb[1], r2 = fb[2];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const float ex = ca.x - cb[k].x, ey = ca.y - cb[k].y, ez = ca.z - cb[k].z;
+                if (k < static_cast<int>(blk.w)) {
+                    const float4 q = s_sph[blk.z + k];
+                    cb[k] = make_float4(fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w))),
+                                        fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w))),
+                                        fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w))), q.w);
+                } else {
+                    cb[k] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                }
+            }
+        }
+        const float4 r0 = fa[0], r1 = fa[1], r2 = fa[2];
+        float depth = 0.f;
+        for (uint32_t a = blk.x; a < blk.y; ++a) {
+            const float4 q = s_sph[a];
+            const float cx = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
+            const float cy = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
+            const float cz = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float ex = cx - cb[k].x, ey = cy - cb[k].y, ez = cz - cb[k].z;
                 const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                const float rs = ca.w + cb[k].w;
+                const float rs = q.w + cb[k].w;
                 if (dist2 < rs * rs) depth = fmaxf(depth, rs - sqrtf(dist2));
             }
         }
@@ -436,13 +523,19 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     for (int k = tid; k < pb.P; k += nt) {
         const uint32_t pr = s_pairs[k];
         const int a = pr & 0xffff, b = pr >> 16;
-        const float rs = s_sph[a].w + s_sph[b].w;
+        const float4 qa = s_sph[a], qb = s_sph[b];
+        const float rs = qa.w + qb.w;
         const float rs2 = rs * rs;
         for (int item = 0; item < I; ++item) {
             if (pred && pred[item] >= pb.self_margin) continue;
-            const float4 ca = s_cent[item * M + a];
-            const float4 cb = s_cent[item * M + b];
-            const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+            const float4* fa = s_frame + (item * F + s_slink[a]) * 3;
+            const float4* fb = s_frame + (item * F + s_slink[b]) * 3;
+            const float ex = (fmaf(fa[0].x, qa.x, fmaf(fa[0].y, qa.y, fmaf(fa[0].z, qa.z, fa[0].w)))) -
+                             (fmaf(fb[0].x, qb.x, fmaf(fb[0].y, qb.y, fmaf(fb[0].z, qb.z, fb[0].w))));
+            const float ey = (fmaf(fa[1].x, qa.x, fmaf(fa[1].y, qa.y, fmaf(fa[1].z, qa.z, fa[1].w)))) -
+                             (fmaf(fb[1].x, qb.x, fmaf(fb[1].y, qb.y, fmaf(fb[1].z, qb.z, fb[1].w))));
+            const float ez = (fmaf(fa[2].x, qa.x, fmaf(fa[2].y, qa.y, fmaf(fa[2].z, qa.z, fa[2].w)))) -
+                             (fmaf(fb[2].x, qb.x, fmaf(fb[2].y, qb.y, fmaf(fb[2].z, qb.z, fb[2].w))));
             const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
             if (dist2 < rs2)
                 atomicMax(reinterpret_cast<int*>(s_dself + item), __float_as_int(rs - sqrtf(dist2)));
@@ -450,6 +543,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     }
     __syncthreads();
 
+    trace_stamp(pb.trace, 5);
     // ---- running cost (Eq. 15)
     for (int item = tid; item < I; item += nt) {
         const float c = s_part[item] + pb.w_coll * (s_dself[item] + s_dworld[item]);
@@ -468,6 +562,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         for (int h = 0; h < H; ++h) C = fmaf(s_gpow[h], s_part[p * H + h], C);
         out.Ctot[n0 + p] = C;
     }
+    trace_stamp(pb.trace, 6);
 }
 
 __global__ void __launch_bounds__(kMaxThreads)
@@ -1284,8 +1379,8 @@ int validate(const storm_robot* r, const storm_world* w, const storm_params* p, 
 
 // Tables live in one device block; offsets in bytes, 256-aligned.
 struct TablePlan {
-    size_t dhx, qlo, qhi, sph, first, pairs, pblk, boxes, wsph, dt, gpow, vmax, basis, halton, mu,
-        sigma, prime, raw, total;
+    size_t dhx, qlo, qhi, sph, first, pairs, pblk, lbound, boxes, wsph, dt, gpow, vmax, basis, halton,
+        mu, sigma, prefix, prime, raw, total;
 };
 
 TablePlan plan_tables(const Problem& pb, int cap_boxes, int cap_wsph, int raw_doubles)
@@ -1294,7 +1389,7 @@ TablePlan plan_tables(const Problem& pb, int cap_boxes, int cap_wsph, int raw_do
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
-        off += (bytes + 255) & ~size_t(255);
+        off += (bytes + 15) & ~size_t(15);
         return o;
     };
     t.dhx = take(pb.d * 8 * 4);
@@ -1304,15 +1399,17 @@ TablePlan plan_tables(const Problem& pb, int cap_boxes, int cap_wsph, int raw_do
     t.first = take((pb.d + 2) * 4);
     t.pairs = take(std::max(pb.P, 1) * 4);
     t.pblk = take(std::max(pb.NPB, 1) * 16);
+    t.lbound = take((pb.d + 1) * 16);
     t.boxes = take(std::max(cap_boxes, 1) * 6 * 4);
     t.wsph = take(std::max(cap_wsph, 1) * 16);
     t.dt = take(pb.H * 4);
     t.gpow = take(pb.H * 4);
     t.vmax = take(pb.H * 4);
     t.basis = take(pb.spline ? pb.H * pb.S * 4 : 4);
-    t.halton = take(pb.sampler == STORM_SAMPLER_HALTON ? size_t(pb.N) * pb.S * pb.d * 4 : 4);
+    t.prefix = off;  // dhx .. basis: what every rollout CTA copies to shared memory
     t.mu = take(pb.H * pb.d * 4);
     t.sigma = take(pb.d * 4);
+    t.halton = take(pb.sampler == STORM_SAMPLER_HALTON ? size_t(pb.N) * pb.S * pb.d * 4 : 4);
     t.prime = take(pb.S * pb.d * 4);
     t.raw = take(raw_doubles * 8);
     t.total = off;
@@ -1528,6 +1625,7 @@ struct HostTables {
     std::vector<int> first;
     std::vector<uint32_t> pairs;
     std::vector<uint4> blocks;
+    std::vector<float4> lbound;  // per frame: bounding sphere of its spheres (local)
     std::vector<double> raw;  // dh | q_min | q_max | dt, read by the set-up kernel
     double k_jl = 0, qdd_max = 0, gamma = 0;
 };
@@ -1597,6 +1695,24 @@ void fill_problem(const storm_robot* r, const storm_world* w, const storm_params
     pb.NPB = static_cast<int>(ht.blocks.size());
     ht.pairs.resize(std::max(pb.P, 1));
     ht.blocks.resize(std::max(pb.NPB, 1));
+    // per frame: the sphere about the centroid of its spheres' centres that
+    // encloses them all, padded by 1e-4 m against FP32 rounding in the tests
+    ht.lbound.assign(pb.d + 1, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int f = 0; f <= pb.d; ++f) {
+        const int a = ht.first[f], b = ht.first[f + 1];
+        if (a == b) continue;
+        double c[3] = {0, 0, 0};
+        for (int i = a; i < b; ++i)
+            for (int k = 0; k < 3; ++k) c[k] += ht.sph[4 * i + k] / double(b - a);
+        double R = 0.0;
+        for (int i = a; i < b; ++i) {
+            const double dx = ht.sph[4 * i] - c[0], dy = ht.sph[4 * i + 1] - c[1], dz = ht.sph[4 * i + 2] - c[2];
+            R = std::max(R, std::sqrt(dx * dx + dy * dy + dz * dz) + ht.sph[4 * i + 3]);
+        }
+        ht.lbound[f] = make_float4(static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
+                                   static_cast<float>(R + 1e-4));
+    }
+    pb.broadphase = 1;
     ht.boxes.assign(6 * std::max(pb.B, 1), 0.f);
     ht.wsph.assign(4 * std::max(pb.O, 1), 0.f);
     for (int i = 0; i < 6 * pb.B; ++i) ht.boxes[i] = static_cast<float>(w->boxes[i]);
@@ -1632,6 +1748,8 @@ cudaError_t upload_problem(Problem& pb, const HostTables& ht, char* base, const 
     pb.halton = reinterpret_cast<float*>(base + t.halton);
     pb.mu = reinterpret_cast<float*>(base + t.mu);
     pb.sigma = reinterpret_cast<float*>(base + t.sigma);
+    pb.tables = reinterpret_cast<const uint4*>(base);
+    pb.table_bytes = static_cast<int>(t.prefix);
     int* d_prime = reinterpret_cast<int*>(base + t.prime);
     double* d_raw = reinterpret_cast<double*>(base + t.raw);
     cudaError_t e = cudaSuccess;
@@ -1643,6 +1761,8 @@ cudaError_t upload_problem(Problem& pb, const HostTables& ht, char* base, const 
     put(pb.link_first, ht.first.data(), 4 * ht.first.size());
     put(pb.pairs, ht.pairs.data(), 4 * ht.pairs.size());
     put(pb.pblk, ht.blocks.data(), 16 * ht.blocks.size());
+    pb.lbound = reinterpret_cast<float4*>(base + t.lbound);
+    put(pb.lbound, ht.lbound.data(), 16 * ht.lbound.size());
     put(pb.boxes, ht.boxes.data(), 4 * ht.boxes.size());
     put(pb.wsph, ht.wsph.data(), 4 * ht.wsph.size());
     put(d_raw, ht.raw.data(), 8 * ht.raw.size());
@@ -1945,6 +2065,22 @@ int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count,
     return STORM_OK;
 }
 
+int storm_set_trace(storm_handle* h, unsigned long long* trace_dev)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    h->pb.trace = trace_dev;
+    return build_graphs(h);
+}
+
+int storm_set_broadphase(storm_handle* h, int on)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    h->pb.broadphase = on ? 1 : 0;
+    return build_graphs(h);
+}
+
 int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
 {
     if (!h) return STORM_ERR_INVALID_ARG;
@@ -2201,6 +2337,7 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
 
     // scratch plan: the model tables, then the N x H x d control batch
     const TablePlan t = plan_tables(pb, std::max(pb.B, 1), std::max(pb.O, 1), static_cast<int>(raw.size()));
+    pb.table_bytes = static_cast<int>(t.prefix);  // the shared-memory plan below depends on it
     const size_t u_off = (t.total + 255) & ~size_t(255);
     const size_t u_bytes = sizeof(float) * size_t(pb.N) * pb.H * pb.d;
     if (u_off + u_bytes > STORM_NOALLOC_SCRATCH_BYTES) {
@@ -2237,6 +2374,8 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
     pb.vmax = reinterpret_cast<float*>(base + t.vmax);
     pb.basis = reinterpret_cast<float*>(base + t.basis);
     pb.halton = reinterpret_cast<float*>(base + t.halton);
+    pb.tables = reinterpret_cast<const uint4*>(base);
+    pb.table_bytes = static_cast<int>(t.prefix);
     int* d_prime = reinterpret_cast<int*>(base + t.prime);
     double* d_raw = reinterpret_cast<double*>(base + t.raw);
     float* d_u = reinterpret_cast<float*>(base + u_off);

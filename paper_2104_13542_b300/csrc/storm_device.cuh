@@ -35,6 +35,11 @@ struct Problem {
     const uint32_t* pairs;   // P: a | b << 16 (sorted sphere indices), pairs outside blocks
     int NPB;                 // pair blocks
     const uint4* pblk;       // NPB: (a0, a1, b0, nb): spheres [a0, a1) x [b0, b0 + nb), nb <= 8
+    const float4* lbound;    // d + 1: bounding sphere of each frame's spheres (local centre, radius)
+    int broadphase;          // 1: exact sphere tests only where the link bounds overlap
+    unsigned long long* trace;  // nullable: phase-boundary %globaltimer stamps of rollout CTA 0
+    const uint4* tables;     // start of the contiguous per-problem tables (dhx .. basis)
+    int table_bytes;         // their size, a multiple of 16
     const float* boxes;      // B x 6
     const float4* wsph;      // O
     const float* dt;         // H
@@ -55,6 +60,16 @@ struct StepState {
     float best;      // min total cost of the last iteration
     float wmean;     // weighted mean total cost of the last iteration
 };
+
+// Phase stamp of the rollout trace (CTA 0, thread 0 only).
+__device__ __forceinline__ void trace_stamp(unsigned long long* trace, int phase)
+{
+    if (trace && blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        trace[phase] = t;
+    }
+}
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon et al., SC'11: ten rounds of two 32x32->64 multiplies with a Weyl key
@@ -107,6 +122,37 @@ __device__ __forceinline__ void dh_step(float (&R)[9], float (&p)[3], float a, f
     }
 }
 
+// sqrt(det(J J^T)) of a 6 x d Jacobian given as rows, by modified Gram-Schmidt
+// on the six rows: det(J J^T) is the product of the squared norms of the
+// orthogonalised rows.  Six dependent reciprocal square roots; the dot
+// products of one row against the earlier ones are independent.
+__device__ __forceinline__ float manipulability_mgs(float (&J)[6][kMaxDof], int d)
+{
+    float m = 1.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int i = 0; i < k; ++i) {
+            float dot = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kMaxDof; ++c)
+                if (c < d) dot = fmaf(J[i][c], J[k][c], dot);
+#pragma unroll
+            for (int c = 0; c < kMaxDof; ++c)
+                if (c < d) J[k][c] = fmaf(-dot, J[i][c], J[k][c]);
+        }
+        float nn = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kMaxDof; ++c)
+            if (c < d) nn = fmaf(J[k][c], J[k][c], nn);
+        const float inv = nn > 0.0f ? rsqrtf(nn) : 0.0f;
+        m *= nn * inv;  // the row's norm
+#pragma unroll
+        for (int c = 0; c < kMaxDof; ++c) J[k][c] *= inv;
+    }
+    return m;
+}
+
 // Manipulability sqrt(det(J J^T)) (Eq. 12) accumulated one Jacobian column at
 // a time.  R is the upper-triangular 6x6 factor with R^T R = sum_i J_i J_i^T
 // (21 packed entries, row-major upper triangle); adding column x is a
@@ -127,10 +173,10 @@ struct GramFactor {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const float a = r[at(k, k)], b = x[k];
-            const float h = sqrtf(fmaf(a, a, b * b));
-            const float inv = h > 0.f ? 1.f / h : 0.f;
-            const float c = h > 0.f ? a * inv : 1.f, s = b * inv;
-            r[at(k, k)] = h;
+            const float hh = fmaf(a, a, b * b);
+            const float inv = hh > 0.f ? rsqrtf(hh) : 0.f;
+            const float c = hh > 0.f ? a * inv : 1.f, s = b * inv;
+            r[at(k, k)] = hh * inv;  // sqrt(a^2 + b^2)
 #pragma unroll
             for (int j = k + 1; j < 6; ++j) {
                 const float rkj = r[at(k, j)], xj = x[j];

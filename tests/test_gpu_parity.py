@@ -343,3 +343,22 @@ def test_launch_shapes_are_bitwise_identical_and_autotune():
         g = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 1, 0).items()}
         for k in ref:
             assert np.array_equal(g[k], ref[k]), k
+
+
+@pytest.mark.parametrize("seed,world", [(0, None), (3, (64, 64)), (5, (8, 0))])
+def test_broadphase_is_bitwise_identical(seed, world):
+    wl = W.config_paper(seed)
+    if world is not None:
+        wl.world = W.make_world(seed + 40, n_boxes=world[0], n_spheres=world[1])
+    p = wl.params.replace(N=200)
+    state, goal = cuda(f32(W.make_state(seed + 60, 7))), cuda(f32(wl.goal))
+    mu, sig = f32(W.make_mean(seed, p.H, 7, 0.8)), f32(W.make_sigma(seed, 7, 0.2, 0.6))
+    outs = []
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(mu, sig)
+        for on in (True, False):
+            ctl.set_broadphase(on)
+            outs.append({k: host(v) for k, v in ctl.generate_rollouts(state, goal, 4, 1).items()})
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    assert (outs[0]["terms"][..., 5] > 0).any() or (outs[0]["terms"][..., 6] > 0).any()
