@@ -166,6 +166,22 @@ def goals_for(ctl, robot, seed: int, count: int):
     return goals
 
 
+def max_over_ranks(value: float, world_size: int, device: str = "cuda") -> float:
+    """The largest `value` over all ranks (the job's time is its slowest rank's)."""
+    if world_size <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: int, steps: int, world_size: int, max_time_s: float) -> float:
+    """Whole-job rollout-steps/s: every rank runs its own replica (weak scaling)."""
+    return units_per_step * steps * world_size / max_time_s
+
+
 def run_gpu(args, rank, world_size):
     import torch
     from paper_2104_13542_b300 import Controller
@@ -179,6 +195,10 @@ def run_gpu(args, rank, world_size):
     state0 = wl.state.copy()
     state0[1:] = 0.0
     goals = goals_for(ctl, wl.robot, args.seed + rank, 5)
+    # the library's autotuner picks the rollout launch shape for this workload
+    ctl.step(state0.astype(np.float32), goals[0])
+    tuned_us = ctl.autotune()
+    ctl.reset()
 
     # ---------------- device-resident timing (value)
     s_ptr, g_ptr, _ = ctl.device_io_ptrs()
@@ -211,35 +231,38 @@ def run_gpu(args, rank, world_size):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     ms = np.array([a.elapsed_time(b) for a, b in ev])
-    dev_time_s = float(ms.sum() / 1e3)
-    if world_size > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_time_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_time_s = float(t.item())
+    dev_time_s = max_over_ranks(float(ms.sum() / 1e3), world_size)
     clocks = clk.summary()
 
     # ---------------- rollout-kernel roofline: kernel time from the step's share
     # (the rollout kernel alone, timed with events on the controller's stream)
     from paper_2104_13542_b300.binding import lib
-    rk = []
     st_d = torch.as_tensor(st_host, device="cuda").reshape(-1)
-    for i in range(max(20, min(args.steps, 200))):
-        with torch.cuda.stream(ctl.stream):
-            flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(ctl.stream)
-        lib().storm_generate_rollouts(ctl.h, ctypes.c_void_p(st_d.data_ptr()),
-                                      ctypes.c_void_p(gl_dev.data_ptr()), 0, 0, None, None, None,
-                                      None, None, None, None)
-        b.record(ctl.stream)
-        rk.append((a, b))
-    torch.cuda.synchronize()
-    rk_ms = float(np.mean([a.elapsed_time(b) for a, b in rk]))
+
+    def rollout_ms():
+        rk = []
+        for i in range(max(20, min(args.steps, 200))):
+            with torch.cuda.stream(ctl.stream):
+                flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctl.stream)
+            lib().storm_generate_rollouts(ctl.h, ctypes.c_void_p(st_d.data_ptr()),
+                                          ctypes.c_void_p(gl_dev.data_ptr()), 0, 0, None, None, None,
+                                          None, None, None, None)
+            b.record(ctl.stream)
+            rk.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in rk]))
+
+    rk_ms = rollout_ms()
+    ctl.set_broadphase(False)  # the same kernel doing every exact collision test
+    rk_bf_ms = rollout_ms()
+    ctl.set_broadphase(True)
     flops_launch = algorithmic_flops_per_item(p, wl.robot, wl.world) * p.N * p.H
     sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
     peak = fp32_peak_tflops(sm_mhz)
     achieved = flops_launch / (rk_ms * 1e-3) / 1e12
+    achieved_bf = flops_launch / (rk_bf_ms * 1e-3) / 1e12
 
     # ---------------- end-to-end closed loop through the host API (e2e)
     ctl.reset()
@@ -265,19 +288,14 @@ def run_gpu(args, rank, world_size):
             ee = ctl.forward_kinematics(torch.as_tensor(state[0:1], device="cuda")).cpu().numpy()[0]
             pos_err.append(float(np.linalg.norm(ee[:, 3] - goal[:3])))
     e2e_ms = np.array(e2e_ms)
-    e2e_time_s = float(e2e_ms.sum() / 1e3)
-    if world_size > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_time_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_time_s = float(t.item())
+    e2e_time_s = max_over_ranks(float(e2e_ms.sum() / 1e3), world_size)
 
     res = dict(
-        value=units_per_step * args.steps * world_size / dev_time_s,
+        value=job_throughput(units_per_step, args.steps, world_size, dev_time_s),
         ms_per_step=float(ms.mean()),
         latency_ms={"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                     "max": float(ms.max())},
-        e2e={"value": units_per_step * args.steps * world_size / e2e_time_s, "unit": UNIT,
+        e2e={"value": job_throughput(units_per_step, args.steps, world_size, e2e_time_s), "unit": UNIT,
              "h2d_bytes_per_step": 4 * (3 * wl.robot.dof + 7),
              "d2h_bytes_per_step": 4 * wl.robot.dof + 16,
              "latency_ms": {"p50": float(np.percentile(e2e_ms, 50)),
@@ -286,8 +304,13 @@ def run_gpu(args, rank, world_size):
         roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                   "frac": achieved / peak, "traffic": rollout_traffic(),
                   "kernel": "k_rollout", "kernel_ms": rk_ms, "flops_per_launch": flops_launch,
+                  "flops_basis": "brute-force count of the method's work per (particle, step); "
+                                 "with the collision broad phase the kernel executes fewer",
+                  "brute_force_kernel_ms": rk_bf_ms, "brute_force_frac": achieved_bf / peak,
+                  "launch_shape": list(ctl.get_launch()), "autotune_us": tuned_us,
                   "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                                f"{sm_mhz:.0f} MHz (fallback-free unit count; SM max clock)"},
+                                f"{sm_mhz:.0f} MHz (unit count x SM max clock; MEASURED_PEAKS has "
+                                f"no FP32 figure)"},
         clocks=clocks,
         gpu_launches=(1 + 2 * p.K) * args.steps,
         wall_s=wall,

@@ -229,18 +229,38 @@ int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count,
 
 /* ---------------------------------------------------------------- launch shape */
 
-/* Rollout launch shape: particles per CTA (1..N) and threads per CTA (a
+/* Rollout work mappings.  Both compute bitwise the same results; they differ
+ * only in how the (particle, step) items are spread over threads:
+ *   STORM_MAP_CTA   a CTA takes a group of particles and runs each phase
+ *                   (noise, controls, integration, FK and costs, world and
+ *                   self collision, discounting) across all its threads,
+ *                   with a CTA barrier between phases;
+ *   STORM_MAP_WARP  a warp takes one particle (or 2 / 4 of them when H <= 16
+ *                   / 8), one lane per step (two steps per lane when H > 32),
+ *                   with warp-level synchronisation only; the default. */
+#define STORM_MAP_CTA 0
+#define STORM_MAP_WARP 1
+
+/* CTA mapping and its shape: particles per CTA (1..N) and threads per CTA (a
  * multiple of 32 in 64..512).  Re-captures the step graph.  Errors:
  * INVALID_ARG when out of range or when the shape's shared-memory plan does not
  * fit a CTA. */
 int storm_set_launch(storm_handle* h, int particles_per_cta, int threads_per_cta);
+/* Warp mapping with 1..8 warps per CTA.  Re-captures the step graph.  Errors:
+ * INVALID_ARG when out of range or when the plan does not fit a CTA. */
+int storm_set_launch_warp(storm_handle* h, int warps_per_cta);
+/* Shape of the active mapping: particles and threads per CTA. */
 int storm_get_launch(const storm_handle* h, int* particles_per_cta, int* threads_per_cta);
+/* STORM_MAP_CTA or STORM_MAP_WARP; INVALID_ARG for a NULL handle. */
+int storm_get_launch_mapping(const storm_handle* h);
 
 /* Tracing: with trace_dev (device, 7 x uint64) set, thread 0 of rollout CTA 0
  * writes %globaltimer (ns) at the phase boundaries of every rollout launch:
  * [0] start, [1] tables + noise staged, [2] controls + integration, [3] FK,
  * Jacobian and non-collision costs, [4] world collision, [5] self collision,
- * [6] end.  NULL turns it off.  Re-captures the step graph. */
+ * [6] end (under the warp mapping, the timeline of warp 0; with two steps per
+ * lane, [3]..[5] are those of the second).  NULL turns it off.  Re-captures
+ * the step graph. */
 int storm_set_trace(storm_handle* h, unsigned long long* trace_dev);
 
 /* Collision broad phase (on by default): each link's spheres are enclosed in
@@ -252,10 +272,10 @@ int storm_set_broadphase(storm_handle* h, int on);
 
 /* Autotuner: times this handle's rollout kernel (sample_controls +
  * generate_rollouts) with CUDA events on its stream for every candidate shape
- * -- particles per CTA 1, 2, 3, 4, 6, 8, 12, 16 (at most N and 512/H) x
- * threads 128, 256, 512 -- on the state and goal of the handle's input
- * buffers (call it after a first step), keeps the fastest and re-captures
- * the step graph.  best_us (nullable) receives the median time of the chosen
+ * -- CTA mapping with particles per CTA 1, 2, 3, 4, 6, 8, 12, 16 (at most N
+ * and 512/H) x threads 128, 256, 512, warp mapping with 1, 2, 4, 8 warps per
+ * CTA -- on the state and goal of the handle's input buffers (call it after a
+ * first step), keeps the fastest and re-captures the step graph.  best_us (nullable) receives the median time of the chosen
  * shape.  Waits. */
 int storm_autotune(storm_handle* h, float* best_us);
 

@@ -29,6 +29,8 @@ STORM_ERR_OOM = -3
 STORM_ERR_NONFINITE = -4
 STORM_ERR_TIMEOUT = -5
 STORM_ERR_STATE = -6
+STORM_MAP_CTA = 0
+STORM_MAP_WARP = 1
 NTERMS = 8
 
 EXPORTED = [
@@ -36,7 +38,7 @@ EXPORTED = [
     "storm_step", "storm_step_async", "storm_sync", "storm_device_io", "storm_shift",
     "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
     "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
-    "storm_set_state", "storm_rollout_costs_noalloc", "storm_set_launch", "storm_get_launch",
+    "storm_set_state", "storm_rollout_costs_noalloc", "storm_set_launch", "storm_get_launch", "storm_set_launch_warp", "storm_get_launch_mapping",
     "storm_autotune", "storm_cost_grad", "storm_batch_create", "storm_batch_destroy",
     "storm_batch_last_error", "storm_batch_sizes", "storm_batch_step", "storm_batch_step_resident",
     "storm_batch_device_io", "storm_batch_sync", "storm_batch_get_distribution",
@@ -132,6 +134,8 @@ def lib():
         L.storm_set_state.argtypes = [vp, vp, C.c_size_t]
         L.storm_set_launch.argtypes = [vp, C.c_int, C.c_int]
         L.storm_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.storm_set_launch_warp.argtypes = [vp, C.c_int]
+        L.storm_get_launch_mapping.argtypes = [vp]
         L.storm_autotune.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_cost_grad.argtypes = [vp, vp, vp, vp, C.c_uint32, C.c_int, vp, vp, vp]
         ip = C.POINTER(C.c_int)
@@ -406,7 +410,18 @@ class Controller:
         return ee
 
     def set_launch(self, particles_per_cta: int, threads: int):
+        """CTA-wide mapping with this shape."""
         self._check(lib().storm_set_launch(self.h, int(particles_per_cta), int(threads)))
+
+    def set_launch_warp(self, warps_per_cta: int):
+        """Warp mapping (one lane per (particle, step)) with this many warps per CTA."""
+        self._check(lib().storm_set_launch_warp(self.h, int(warps_per_cta)))
+
+    def launch_mapping(self) -> str:
+        m = lib().storm_get_launch_mapping(self.h)
+        if m < 0:
+            self._check(m)
+        return "warp" if m == STORM_MAP_WARP else "cta"
 
     def set_trace(self, trace_dev):
         """trace_dev: int64 CUDA tensor of 7 entries (phase stamps in ns) or None."""

@@ -578,6 +578,8 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
     rollout_particles(pb, out, state, goal, step, iter, n0, np, smem, front_only);
 }
 
+#include "storm_rollout_warp.cuh"
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -1071,6 +1073,7 @@ struct MlpBuffers {
                   *a2T = nullptr, *a3 = nullptr, *d3 = nullptr, *d3T = nullptr, *d2 = nullptr,
                   *d2T = nullptr, *d1T = nullptr;
     float *y = nullptr, *dy = nullptr, *loss_part = nullptr;
+    float* part = nullptr;  // split-K partial weight gradients, kSplitMax x 256 x 256
 };
 
 struct storm_mlp {
@@ -1093,7 +1096,7 @@ void mlp_free_buffers(MlpBuffers& b)
     __nv_bfloat16* bf[] = {b.x, b.xT, b.a1, b.a1T, b.a2, b.a2T, b.a3, b.d3, b.d3T, b.d2, b.d2T, b.d1T};
     for (auto* q : bf)
         if (q) cudaFree(q);
-    float* fl[] = {b.y, b.dy, b.loss_part};
+    float* fl[] = {b.y, b.dy, b.loss_part, b.part};
     for (auto* q : fl)
         if (q) cudaFree(q);
     b = MlpBuffers{};
@@ -1125,6 +1128,7 @@ cudaError_t mlp_reserve(MlpBuffers& b, int rows, bool train)
         get(&b.d1T, h);
         get(&b.dy, sizeof(float) * R);
         get(&b.loss_part, sizeof(float) * R);
+        get(&b.part, sizeof(float) * kSplitMax * kMlpHid * kMlpHid);
     }
     if (e == cudaSuccess) {
         b.cap = rows;
@@ -1133,8 +1137,27 @@ cudaError_t mlp_reserve(MlpBuffers& b, int rows, bool train)
     return e;
 }
 
+// Split-K count for a weight gradient over R rows: a divisor of R / 128 of at
+// most kSplitMax, so that every split covers whole 128-row blocks.
+int split_count(int R)
+{
+    int sp = std::min(kSplitMax, R / tc::kBM);
+    while (sp > 1 && (R / tc::kBM) % sp) --sp;
+    return std::max(sp, 1);
+}
+
+// out[i] = sum over s of part[s * n + i], in the order s = 0, 1, ...
+__global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int n, float* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float acc = 0.f;
+    for (int s = 0; s < splits; ++s) acc += part[static_cast<size_t>(s) * n + i];
+    out[i] = acc;
+}
+
 template <int BN>
-cudaError_t gemm(const tc::GemmArgs& g, cudaStream_t s)
+cudaError_t gemm(const tc::GemmArgs& g, cudaStream_t s, int splits = 1)
 {
     static int attr_set = -1;
     int dev = 0;
@@ -1145,8 +1168,30 @@ cudaError_t gemm(const tc::GemmArgs& g, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = dev;
     }
-    if (g.M % tc::kBM || g.N != BN || g.K % 16 || g.K <= 0) return cudaErrorInvalidValue;
-    tc::k_gemm<BN><<<g.M / tc::kBM, tc::kThreads, tc::gemm_smem<BN>(), s>>>(g);
+    if (g.M % tc::kBM || g.N != BN || g.K % 16 || g.K <= 0 || splits < 1) return cudaErrorInvalidValue;
+    tc::k_gemm<BN><<<dim3(g.M / tc::kBM, splits), tc::kThreads, tc::gemm_smem<BN>(), s>>>(g);
+    return cudaGetLastError();
+}
+
+// Forward layer with the weights resident in shared memory (N = 256, K = 16 or 256).
+cudaError_t gemm_rw(const tc::GemmArgs& g, cudaStream_t s)
+{
+    static int attr_dev = -1;
+    static int sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(tc::k_gemm_rw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(tc::gemm_rw_smem(256)));
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    if (g.M % tc::kBM || g.N != 256 || (g.K != 16 && g.K != 256)) return cudaErrorInvalidValue;
+    const int grid = std::min(g.M / tc::kBM, sms);
+    // the full-K shared-memory size for every layer keeps one CTA (and one
+    // 512-column TMEM allocation) per SM
+    tc::k_gemm_rw<<<grid, tc::kThreads, tc::gemm_rw_smem(256), s>>>(g);
     return cudaGetLastError();
 }
 
@@ -1162,6 +1207,18 @@ tc::GemmArgs gemm_args(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, 
     g.N = N;
     g.K = K;
     g.err = err;
+    return g;
+}
+
+// dW = delta^T act over R rows (both operands stored transposed, R contiguous),
+// split into `splits` K ranges whose FP32 partials go to part[split][256][N].
+tc::GemmArgs weight_grad(const __nv_bfloat16* deltaT, const __nv_bfloat16* actT, int R, int splits, int N,
+                         float* part, int* err)
+{
+    tc::GemmArgs g = gemm_args(deltaT, R, actT, R, kMlpHid, N, R / splits, err);
+    g.out_f = part;
+    g.ldf = N;
+    g.split_stride = static_cast<size_t>(kMlpHid) * N;
     return g;
 }
 
@@ -1184,7 +1241,7 @@ int mlp_forward(storm_mlp* m, MlpBuffers& b, const float* theta, int count, int 
         g.out_bfT = b.a1T;
         g.ldoT = R;
     }
-    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     g = gemm_args(b.a1, kMlpHid, m->w2, kMlpHid, R, kMlpHid, kMlpHid, m->err);
     g.bias = m->p + kOffB2;
     g.relu = 1;
@@ -1194,7 +1251,7 @@ int mlp_forward(storm_mlp* m, MlpBuffers& b, const float* theta, int count, int 
         g.out_bfT = b.a2T;
         g.ldoT = R;
     }
-    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     g = gemm_args(b.a2, kMlpHid, m->w3, kMlpHid, R, kMlpHid, kMlpHid, m->err);
     g.bias = m->p + kOffB3;
     g.relu = 1;
@@ -1205,7 +1262,7 @@ int mlp_forward(storm_mlp* m, MlpBuffers& b, const float* theta, int count, int 
         g.out_bf = b.a3;
         g.ldo = kMlpHid;
     }
-    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     return STORM_OK;
 }
 
@@ -1218,10 +1275,10 @@ int mlp_backward(storm_mlp* m, MlpBuffers& b, const float* target, int count, cu
     k_mlp_head_grad<<<kMlpHid + 2, 256, 0, s>>>(b.dy, b.a3, R, count, b.loss_part, m->g, m->loss);
     if (cudaGetLastError() != cudaSuccess) return STORM_ERR_CUDA;
     // dW3 = delta3^T a2, db3 = sum delta3
-    tc::GemmArgs g = gemm_args(b.d3T, R, b.a2T, R, kMlpHid, kMlpHid, R, m->err);
-    g.out_f = m->g + kOffW3;
-    g.ldf = kMlpHid;
-    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    const int sp = split_count(R);
+    tc::GemmArgs g = weight_grad(b.d3T, b.a2T, R, sp, kMlpHid, b.part, m->err);
+    if (gemm<kMlpHid>(g, s, sp) != cudaSuccess) return STORM_ERR_CUDA;
+    k_splitk_reduce<<<kMlpHid * kMlpHid / 256, 256, 0, s>>>(b.part, sp, kMlpHid * kMlpHid, m->g + kOffW3);
     k_mlp_rowsum<<<kMlpHid, 256, 0, s>>>(b.d3T, R, m->g + kOffB3);
     // delta2 = (delta3 W3) o [a2 > 0]
     g = gemm_args(b.d3, kMlpHid, m->w3t, kMlpHid, R, kMlpHid, kMlpHid, m->err);
@@ -1231,12 +1288,11 @@ int mlp_backward(storm_mlp* m, MlpBuffers& b, const float* target, int count, cu
     g.ldo = kMlpHid;
     g.out_bfT = b.d2T;
     g.ldoT = R;
-    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     // dW2 = delta2^T a1, db2 = sum delta2
-    g = gemm_args(b.d2T, R, b.a1T, R, kMlpHid, kMlpHid, R, m->err);
-    g.out_f = m->g + kOffW2;
-    g.ldf = kMlpHid;
-    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    g = weight_grad(b.d2T, b.a1T, R, sp, kMlpHid, b.part, m->err);
+    if (gemm<kMlpHid>(g, s, sp) != cudaSuccess) return STORM_ERR_CUDA;
+    k_splitk_reduce<<<kMlpHid * kMlpHid / 256, 256, 0, s>>>(b.part, sp, kMlpHid * kMlpHid, m->g + kOffW2);
     k_mlp_rowsum<<<kMlpHid, 256, 0, s>>>(b.d2T, R, m->g + kOffB2);
     // delta1 = (delta2 W2) o [a1 > 0]
     g = gemm_args(b.d2, kMlpHid, m->w2t, kMlpHid, R, kMlpHid, kMlpHid, m->err);
@@ -1244,12 +1300,11 @@ int mlp_backward(storm_mlp* m, MlpBuffers& b, const float* target, int count, cu
     g.ldm = kMlpHid;
     g.out_bfT = b.d1T;
     g.ldoT = R;
-    if (gemm<kMlpHid>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     // dW1 = delta1^T x
-    g = gemm_args(b.d1T, R, b.xT, R, kMlpHid, kMlpIn, R, m->err);
-    g.out_f = m->g + kOffW1;
-    g.ldf = kMlpIn;
-    if (gemm<kMlpIn>(g, s) != cudaSuccess) return STORM_ERR_CUDA;
+    g = weight_grad(b.d1T, b.xT, R, sp, kMlpIn, b.part, m->err);
+    if (gemm<kMlpIn>(g, s, sp) != cudaSuccess) return STORM_ERR_CUDA;
+    k_splitk_reduce<<<kMlpHid * kMlpIn / 256, 256, 0, s>>>(b.part, sp, kMlpHid * kMlpIn, m->g + kOffW1);
     return cudaGetLastError() == cudaSuccess ? STORM_OK : STORM_ERR_CUDA;
 }
 
@@ -1271,7 +1326,11 @@ struct storm_handle {
     int n_spheres_in = 0;
     size_t rollout_smem = 0, update_smem = 0;
     int grid = 0;
-    int threads = kThreads;  // rollout CTA size
+    int threads = kThreads;  // rollout CTA size (CTA-wide mapping)
+    int mapping = STORM_MAP_WARP;  // rollout work mapping
+    int wpc = 2;                   // warps per CTA (warp mapping)
+    size_t warp_smem = 0;          // its dynamic shared memory
+    int warp_grid = 0;
     // device allocations
     void* d_tables = nullptr;  // one block for every table
     float* d_u = nullptr;
@@ -1439,8 +1498,12 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
 {
     Problem pb = h->pb;
     if (exact_self) pb.self_pred = nullptr;
-    k_rollout<<<h->grid, h->threads, h->rollout_smem, s>>>(pb, out, state, goal, h->d_st,
-                                                         step_override, iter, front_only);
+    if (h->mapping == STORM_MAP_WARP)
+        k_rollout_warp<<<h->warp_grid, h->wpc * 32, h->warp_smem, s>>>(pb, out, state, goal, h->d_st,
+                                                                      step_override, iter, front_only);
+    else
+        k_rollout<<<h->grid, h->threads, h->rollout_smem, s>>>(pb, out, state, goal, h->d_st, step_override,
+                                                             iter, front_only);
     CK(cudaGetLastError());
     return STORM_OK;
 }
@@ -1506,8 +1569,11 @@ int allow_smem(storm_handle* h)
 {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    cudaFuncAttributes ra, ua, aa;
+    cudaFuncAttributes ra, ua, aa, wa;
     CK(cudaFuncGetAttributes(&ra, k_rollout));
+    CK(cudaFuncGetAttributes(&wa, k_rollout_warp));
+    CK(cudaFuncSetAttribute(k_rollout_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(wa.sharedSizeBytes)));
     CK(cudaFuncGetAttributes(&ua, k_update));
     CK(cudaFuncGetAttributes(&aa, k_adjoint));
     if (h->rollout_smem + ra.sharedSizeBytes > size_t(optin) ||
@@ -1693,6 +1759,22 @@ void fill_problem(const storm_robot* r, const storm_world* w, const storm_params
     build_pair_blocks(all_pairs, ht.first, pb.d, ht.blocks, ht.pairs);
     pb.P = static_cast<int>(ht.pairs.size());
     pb.NPB = static_cast<int>(ht.blocks.size());
+    {
+        // block range of every frame pair (blocks come sorted by (la, lb))
+        auto link_of = [&](int sidx) {
+            int f = 0;
+            while (f < pb.d && sidx >= ht.first[f + 1]) ++f;
+            return f;
+        };
+        int bk = 0;
+        for (int la = 0; la < kMaxDof; ++la)
+            for (int lb = la + 1; lb <= kMaxDof; ++lb) {
+                const int t = link_pair_index(la, lb);
+                pb.lp_begin[t] = static_cast<uint16_t>(bk);
+                while (bk < pb.NPB && link_of(ht.blocks[bk].x) == la && link_of(ht.blocks[bk].z) == lb) ++bk;
+            }
+        pb.lp_begin[kLinkPairs] = static_cast<uint16_t>(bk);
+    }
     ht.pairs.resize(std::max(pb.P, 1));
     ht.blocks.resize(std::max(pb.NPB, 1));
     // per frame: the sphere about the centroid of its spheres' centres that
@@ -1802,6 +1884,11 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     h->cap_boxes = STORM_MAX_OBSTACLES;
     h->cap_wsph = STORM_MAX_OBSTACLES;
     h->grid = (pb.N + pb.ppc - 1) / pb.ppc;
+    {
+        const WarpPlan wp = warp_plan(pb);
+        h->warp_smem = sizeof(float) * size_t(wp.floats) * h->wpc;
+        h->warp_grid = (pb.N + wp.PW * h->wpc - 1) / (wp.PW * h->wpc);
+    }
 
     const TablePlan t = plan_tables(pb, h->cap_boxes, h->cap_wsph, static_cast<int>(ht.raw.size()));
     CK(cudaMalloc(&h->d_tables, t.total));
@@ -2084,9 +2171,38 @@ int storm_set_broadphase(storm_handle* h, int on)
 int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
 {
     if (!h) return STORM_ERR_INVALID_ARG;
-    if (ppc) *ppc = h->pb.ppc;
-    if (threads) *threads = h->threads;
+    if (h->mapping == STORM_MAP_WARP) {
+        if (ppc) *ppc = h->wpc * warp_plan(h->pb).PW;
+        if (threads) *threads = h->wpc * 32;
+    } else {
+        if (ppc) *ppc = h->pb.ppc;
+        if (threads) *threads = h->threads;
+    }
     return STORM_OK;
+}
+
+int storm_get_launch_mapping(const storm_handle* h) { return h ? h->mapping : STORM_ERR_INVALID_ARG; }
+
+static int set_launch_warp_impl(storm_handle* h, int wpc, bool rebuild)
+{
+    if (wpc < 1 || wpc > kWarpMaxWarps) return fail(h, STORM_ERR_INVALID_ARG, "warps per CTA out of range");
+    const WarpPlan wp = warp_plan(h->pb);
+    const size_t bytes = sizeof(float) * size_t(wp.floats) * wpc;
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (bytes > size_t(optin)) return fail(h, STORM_ERR_INVALID_ARG, "launch shape needs too much shared memory");
+    h->mapping = STORM_MAP_WARP;
+    h->wpc = wpc;
+    h->warp_smem = bytes;
+    h->warp_grid = (h->pb.N + wp.PW * wpc - 1) / (wp.PW * wpc);
+    return rebuild ? build_graphs(h) : STORM_OK;
+}
+
+int storm_set_launch_warp(storm_handle* h, int warps_per_cta)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    return set_launch_warp_impl(h, warps_per_cta, true);
 }
 
 static int set_launch_impl(storm_handle* h, int ppc, int threads, bool rebuild)
@@ -2103,6 +2219,7 @@ static int set_launch_impl(storm_handle* h, int ppc, int threads, bool rebuild)
     h->threads = threads;
     h->grid = (h->pb.N + ppc - 1) / ppc;
     h->rollout_smem = L.bytes;
+    h->mapping = STORM_MAP_CTA;
     return rebuild ? build_graphs(h) : STORM_OK;
 }
 
@@ -2119,9 +2236,10 @@ int storm_autotune(storm_handle* h, float* best_us)
     CK(cudaStreamSynchronize(h->stream));
     const int ppcs[] = {1, 2, 3, 4, 6, 8, 12, 16};
     const int ths[] = {128, 256, 512};
-    const int old_ppc = h->pb.ppc, old_threads = h->threads;
+    const int wpcs[] = {1, 2, 4, 8};
+    const int old_map = h->mapping, old_ppc = h->pb.ppc, old_threads = h->threads, old_wpc = h->wpc;
     float best = INFINITY;
-    int best_ppc = old_ppc, best_threads = old_threads;
+    int best_map = old_map, best_ppc = old_ppc, best_threads = old_threads, best_wpc = old_wpc;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -2129,38 +2247,66 @@ int storm_autotune(storm_handle* h, float* best_us)
     const float* state = h->d_io + io_state(h->pb);
     const float* goal = h->d_io + io_goal(h->pb);
     int rc = STORM_OK;
+    auto measure = [&]() {  // median of 10 timed launches after 3 warm-up launches
+        std::vector<float> t;
+        for (int it = 0; it < 13 && rc == STORM_OK; ++it) {
+            cudaEventRecord(e0, h->stream);
+            rc = launch_rollout(h, h->stream, out, state, goal, 0, 0);
+            cudaEventRecord(e1, h->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = STORM_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (it >= 3) t.push_back(ms * 1e3f);
+        }
+        if (rc) return INFINITY;
+        std::sort(t.begin(), t.end());
+        return t[t.size() / 2];
+    };
     for (int ppc : ppcs) {
         if (ppc > h->pb.N || ppc * h->pb.H > kMaxThreads) continue;
         for (int th : ths) {
             if (set_launch_impl(h, ppc, th, false) != STORM_OK) continue;
-            std::vector<float> t;
-            for (int it = 0; it < 13 && rc == STORM_OK; ++it) {
-                cudaEventRecord(e0, h->stream);
-                rc = launch_rollout(h, h->stream, out, state, goal, 0, 0);
-                cudaEventRecord(e1, h->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = STORM_ERR_CUDA;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (it >= 3) t.push_back(ms * 1e3f);
-            }
+            const float med = measure();
             if (rc) break;
-            std::sort(t.begin(), t.end());
-            const float med = t[t.size() / 2];
             if (med < best) {
                 best = med;
+                best_map = STORM_MAP_CTA;
                 best_ppc = ppc;
                 best_threads = th;
             }
         }
         if (rc) break;
     }
+    for (int w : wpcs) {
+        if (rc) break;
+        if (set_launch_warp_impl(h, w, false) != STORM_OK) continue;
+        const float med = measure();
+        if (rc) break;
+        if (med < best) {
+            best = med;
+            best_map = STORM_MAP_WARP;
+            best_wpc = w;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    h->err = "no error";  // shapes that did not fit are not errors of the handle
     if (rc) {
-        set_launch_impl(h, old_ppc, old_threads, true);
+        if (old_map == STORM_MAP_WARP) {
+            set_launch_impl(h, old_ppc, old_threads, false);
+            set_launch_warp_impl(h, old_wpc, true);
+        } else {
+            set_launch_warp_impl(h, old_wpc, false);
+            set_launch_impl(h, old_ppc, old_threads, true);
+        }
         return rc;
     }
     if (best_us) *best_us = best;
+    if (best_map == STORM_MAP_WARP) {
+        set_launch_impl(h, best_ppc, best_threads, false);  // keep the CTA-mapping shape consistent
+        return set_launch_warp_impl(h, best_wpc, true);
+    }
+    set_launch_warp_impl(h, best_wpc, false);
     return set_launch_impl(h, best_ppc, best_threads, true);
 }
 

@@ -14,6 +14,13 @@ constexpr int kMaxDof = 7;
 constexpr int kThreads = 256;        // default rollout CTA size
 constexpr int kMaxThreads = 512;     // largest rollout CTA size the tuner may pick
 constexpr int kUpdateThreads = 256;  // distribution-update CTA size (one CTA per horizon step)
+constexpr int kLinkPairs = (kMaxDof + 1) * kMaxDof / 2;  // frame pairs (la < lb) of a chain
+
+// Position of frame pair (la, lb), la < lb <= kMaxDof, in lexicographic order.
+__host__ __device__ constexpr int link_pair_index(int la, int lb)
+{
+    return la * kMaxDof - la * (la - 1) / 2 + (lb - la - 1);
+}
 
 // Per-problem constants and device table pointers (kernel parameter, by value).
 struct Problem {
@@ -51,6 +58,9 @@ struct Problem {
     float* sigma;            // d
     const float* self_pred;  // N x H surrogate self distances (nullable)
     float self_margin;       // exact self check only where self_pred < self_margin
+    // pair blocks of frames (la, lb), la < lb, are [lp_begin[t], lp_begin[t + 1]) with
+    // t = link_pair_index(la, lb); the blocks are sorted by (la, lb)
+    uint16_t lp_begin[kLinkPairs + 1];
 };
 
 // Step bookkeeping kept on the device so captured graphs need no host update.

@@ -38,6 +38,8 @@ struct GemmArgs {
     const float* head_b;
     float* head_y;              // M
     int* err;                   // set to 1 when a wait times out
+    size_t split_stride;        // split-K: CTA row blockIdx.y takes K range [y K, (y+1) K) of A and B
+                                // and writes out_f + y split_stride (0: no split)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -144,9 +146,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g)
     const int nk = (g.K + kKB - 1) / kKB;
     uint32_t parity[2] = {0u, 0u};
     bool ok = true;
-    const __nv_bfloat16* A = g.A + static_cast<size_t>(m0) * g.lda;
+    const size_t k_base = static_cast<size_t>(blockIdx.y) * g.K;
+    const __nv_bfloat16* A = g.A + static_cast<size_t>(m0) * g.lda + k_base;
+    const __nv_bfloat16* B = g.B + k_base;
+    float* out_f = g.out_f ? g.out_f + blockIdx.y * g.split_stride : nullptr;
     stage_tile(smem_u32(sA[0]), A, g.lda, kBM, min(kKB, g.K));
-    stage_tile(smem_u32(sB[0]), g.B, g.ldb, BN, min(kKB, g.K));
+    stage_tile(smem_u32(sB[0]), B, g.ldb, BN, min(kKB, g.K));
     int last = 0;
     for (int it = 0; it < nk && ok; ++it) {
         const int s = it & 1, k0 = it * kKB, kb = min(kKB, g.K - k0);
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g)
                 if (!ok) break;  // uniform across the CTA
             }
             stage_tile(smem_u32(sA[s2]), A + k1, g.lda, kBM, kb1);
-            stage_tile(smem_u32(sB[s2]), g.B + k1, g.ldb, BN, kb1);
+            stage_tile(smem_u32(sB[s2]), B + k1, g.ldb, BN, kb1);
             asm volatile("cp.async.wait_group 2;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -220,8 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g)
                 v[i] = x;
                 if (g.head_w) yacc = fmaf(g.head_w[n], x, yacc);
             }
-            if (g.out_f) {
-                float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
+            if (out_f) {
+                float4* o = reinterpret_cast<float4*>(out_f + static_cast<size_t>(row) * g.ldf + c0);
                 o[0] = make_float4(v[0], v[1], v[2], v[3]);
                 o[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
@@ -250,11 +255,194 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g)
 template <int BN>
 constexpr size_t gemm_smem() { return 2 * (kBM * kKB * 2 + BN * kKB * 2); }
 
+// Forward layers (N = 256): the whole weight matrix B (256 x K, K <= 256) stays
+// resident in shared memory, one persistent CTA per SM walks the 128-row tiles
+// of A through a kStagesRW-deep cp.async pipeline, and one elected thread
+// issues the tcgen05.mma of each K block.  The accumulator is double-buffered
+// in TMEM (2 x 256 columns), so the epilogue of tile t runs while the tensor
+// core works on tile t+1; a K block's stage is refilled as soon as the commit
+// of its MMAs arrives.  Same epilogue as k_gemm.
+constexpr int kStagesRW = 4;
+
+__host__ __device__ constexpr size_t gemm_rw_smem(int K)
+{
+    return static_cast<size_t>(256) * K * 2 + static_cast<size_t>(kStagesRW) * kBM * (K < kKB ? K : kKB) * 2;
+}
+
+__device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, int row, int warp)
+{
+    float yacc = 0.f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < 256; c0 += 8) {
+        uint32_t r[8];
+        const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int n = c0 + i;
+            float x = __uint_as_float(r[i]);
+            if (g.bias) x += g.bias[n];
+            if (g.relu) x = fmaxf(x, 0.f);
+            if (g.mask && !(__bfloat162float(g.mask[static_cast<size_t>(row) * g.ldm + n]) > 0.f)) x = 0.f;
+            v[i] = x;
+            if (g.head_w) yacc = fmaf(g.head_w[n], x, yacc);
+        }
+        if (g.out_f) {
+            float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+        if (g.out_bf) {
+            __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[i]);
+            *reinterpret_cast<uint4*>(g.out_bf + static_cast<size_t>(row) * g.ldo + c0) =
+                *reinterpret_cast<const uint4*>(b);
+        }
+        if (g.out_bfT) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                g.out_bfT[static_cast<size_t>(c0 + i) * g.ldoT + row] = __float2bfloat16_rn(v[i]);
+        }
+    }
+    if (g.head_w) g.head_y[row] = *g.head_b + yacc;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[kStagesRW];
+    __shared__ uint32_t tmem_slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = g.K, kb = K < kKB ? K : kKB, nk = K / kb;
+    unsigned char* sW = smem;                                     // nk blocks of 256 x kb
+    unsigned char* sA = smem + static_cast<size_t>(256) * K * 2;  // kStagesRW stages of 128 x kb
+    const int stageA = kBM * kb * 2, blockW = 256 * kb * 2;
+    const uint32_t sbo = (kb / 8) * 128;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStagesRW; ++i) mbar_init(smem_u32(&mbar[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // the weights, once (first cp.async group): block j holds B[:, j*kb .. (j+1)*kb)
+    {
+        const int chunks = kb / 8;
+        for (int c = threadIdx.x; c < nk * 256 * chunks; c += blockDim.x) {
+            const int j = c / (256 * chunks), rem = c - j * 256 * chunks;
+            const int r = rem / chunks, kg = rem - r * chunks;
+            cp_async16(smem_u32(sW + j * blockW) + (r >> 3) * sbo + (r & 7) * 16 + kg * 128,
+                       g.B + static_cast<size_t>(r) * g.ldb + j * kb + kg * 8);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+
+    // item i = (local tile i / nk, K block i % nk); tile t_local -> global tile
+    const int tiles = g.M / kBM;
+    const int bx = blockIdx.x, gx = gridDim.x;
+    const int my_tiles = tiles > bx ? (tiles - 1 - bx) / gx + 1 : 0;
+    const int total = my_tiles * nk;
+    auto issue = [&](int item) {  // one cp.async group per item
+        const int t = bx + (item / nk) * gx, j = item % nk;
+        stage_tile(smem_u32(sA + (item % kStagesRW) * stageA),
+                   g.A + static_cast<size_t>(t) * kBM * g.lda + j * kb, g.lda, kBM, kb);
+    };
+    auto epilogue = [&](int item) {  // item is the last K block of its tile
+        const int tl = item / nk;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        gemm_epilogue(g, tmem + (tl & 1) * 256, (bx + tl * gx) * kBM + warp * 32 + lane, warp);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+    int issued = 0;
+    for (; issued < total && issued < kStagesRW; ++issued) issue(issued);
+    bool ok = true;
+    int waited = -1;  // every item <= waited has completed its MMAs
+    for (int c = 0; c < total; ++c) {
+        const int newer = issued - c - 1;  // groups committed after item c's
+        if (newer >= 3)
+            asm volatile("cp.async.wait_group 3;" ::: "memory");
+        else if (newer == 2)
+            asm volatile("cp.async.wait_group 2;" ::: "memory");
+        else if (newer == 1)
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();  // also orders the previous epilogue's TMEM reads before these MMAs
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int j = c % nk;
+            const uint32_t idesc = instr_desc(kBM, 256);
+            const uint32_t d = tmem + ((c / nk) & 1) * 256;
+            const uint32_t a0 = smem_u32(sA + (c % kStagesRW) * stageA), b0 = smem_u32(sW + j * blockW);
+            for (int kk = 0; kk < kb / 16; ++kk) {
+                const uint64_t da = smem_desc(a0 + kk * 256, 128, sbo);
+                const uint64_t db = smem_desc(b0 + kk * 256, 128, sbo);
+                const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar[c % kStagesRW]))
+                : "memory");
+        }
+        if (c >= 1) {  // item c-1: its stage is free and, at a tile end, its accumulator final
+            const int p = c - 1;
+            ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[p % kStagesRW]), (p / kStagesRW) & 1));
+            if (!ok) break;
+            waited = p;
+            if (issued < total) issue(issued++);
+            if (p % nk == nk - 1) epilogue(p);
+        }
+    }
+    if (ok && total > 0) {
+        const int p = total - 1;
+        ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[p % kStagesRW]), (p / kStagesRW) & 1));
+        if (ok) {
+            waited = p;
+            epilogue(p);
+        }
+    }
+    if (!ok && g.err && lane == 0) atomicExch(g.err, 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok) {  // at most two committed items are unfinished; wait for them, bounded
+        for (int p = waited + 1; p < total && p <= waited + 2; ++p)
+            mbar_wait(smem_u32(&mbar[p % kStagesRW]), (p / kStagesRW) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                     : "memory");
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- MLP helpers
 
 constexpr int kMlpIn = 16, kMlpHid = 256;
+constexpr int kSplitMax = 74;  // split-K of a weight gradient: 2 x 74 CTAs cover the 148 SMs
 constexpr int kMlpParams = kMlpHid * kMlpIn + 2 * (kMlpHid * kMlpHid + kMlpHid) + kMlpHid + 1;
 
 // Offsets in the flat FP32 parameter vector: W1 | W2 | b2 | W3 | b3 | w4 | b4.

@@ -1,0 +1,609 @@
+// storm_rollout_warp.cuh -- sample_controls + generate_rollouts with one lane
+// per (particle, step) item.
+//
+// A particle's horizon lies along one segment of Lp = 8, 16 or 32 lanes of a
+// warp (Lp >= H, or Lp = 32 with ceil(H / 32) items per lane), so each phase
+// runs on all the particle's items at once and the only synchronisation is the
+// warp's own.  Per-item results are bitwise those of the CTA-wide mapping in
+// k_rollout: the same noise, the same sequential integration (one lane per
+// (particle, joint)), the same FK / Jacobian / cost expressions, exact sphere
+// tests with the same formulas, and the same sequential discounted sum.  What
+// changes is the work schedule: no CTA barriers, Jacobian and bounding-sphere
+// centres in registers, and world obstacles culled once per warp against the
+// axis-aligned box enclosing every link bound of the warp's items.
+#pragma once
+
+// Per-warp shared-memory plan (float offsets).
+struct WarpPlan {
+    int Lp, PW, SL;  // lanes per particle, particles per warp, items per lane
+    int frame;       // F x 12 x 32: link frames, row-major [R | p] rows, lane-minor
+    int cb;          // F x 3 x 32: link bounding-sphere centres, lane-minor
+    int eps;         // PW x S x d noise
+    int u, th, thd;  // PW x H x d controls and joint states
+    int c;           // PW x H running costs
+    int floats;      // size of one warp's region
+};
+
+__host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
+{
+    WarpPlan w;
+    w.Lp = pb.H > 16 ? 32 : (pb.H > 8 ? 16 : 8);
+    w.PW = 32 / w.Lp;
+    w.SL = (pb.H + w.Lp - 1) / w.Lp;
+    const int F = pb.d + 1;
+    int off = 0;
+    auto take = [&](int n) {
+        const int o = off;
+        off += (n + 3) & ~3;
+        return o;
+    };
+    w.frame = take(F * 12 * 32);
+    w.cb = take(F * 3 * 32);
+    w.eps = take(w.PW * pb.S * pb.d);
+    w.u = take(w.PW * pb.H * pb.d);
+    w.th = take(w.PW * pb.H * pb.d);
+    w.thd = take(w.PW * pb.H * pb.d);
+    w.c = take(w.PW * pb.H);
+    w.floats = off;
+    return w;
+}
+
+constexpr int kWarpMaxWarps = 8;  // largest CTA of the warp mapping (warps)
+
+// Exact depth of the spheres [s0, s1) of one frame against box b (centre,
+// half extents) -- the per-sphere formula of k_rollout.
+__device__ __forceinline__ float box_depth(const float* __restrict__ fr, int lane, const float4* __restrict__ sph,
+                                           int s0, int s1, const float* __restrict__ box, float depth)
+{
+    const float r0x = fr[0 * 32 + lane], r0y = fr[1 * 32 + lane], r0z = fr[2 * 32 + lane], r0w = fr[3 * 32 + lane];
+    const float r1x = fr[4 * 32 + lane], r1y = fr[5 * 32 + lane], r1z = fr[6 * 32 + lane], r1w = fr[7 * 32 + lane];
+    const float r2x = fr[8 * 32 + lane], r2y = fr[9 * 32 + lane], r2z = fr[10 * 32 + lane], r2w = fr[11 * 32 + lane];
+    const float lox = box[0] - box[3], loy = box[1] - box[4], loz = box[2] - box[5];
+    const float hix = box[0] + box[3], hiy = box[1] + box[4], hiz = box[2] + box[5];
+    for (int s = s0; s < s1; ++s) {
+        const float4 q = sph[s];
+        const float cx = fmaf(r0x, q.x, fmaf(r0y, q.y, fmaf(r0z, q.z, r0w)));
+        const float cy = fmaf(r1x, q.x, fmaf(r1y, q.y, fmaf(r1z, q.z, r1w)));
+        const float cz = fmaf(r2x, q.x, fmaf(r2y, q.y, fmaf(r2z, q.z, r2w)));
+        const float fx = cx - fminf(fmaxf(cx, lox), hix);
+        const float fy = cy - fminf(fmaxf(cy, loy), hiy);
+        const float fz = cz - fminf(fmaxf(cz, loz), hiz);
+        if (fmaf(fx, fx, fmaf(fy, fy, fz * fz)) < q.w * q.w) {
+            const float qx = fabsf(cx - box[0]) - box[3];
+            const float qy = fabsf(cy - box[1]) - box[4];
+            const float qz = fabsf(cz - box[2]) - box[5];
+            const float ox = fmaxf(qx, 0.f), oy = fmaxf(qy, 0.f), oz = fmaxf(qz, 0.f);
+            const float sd = sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f) - q.w;
+            depth = fmaxf(depth, -sd);
+        }
+    }
+    return depth;
+}
+
+// Exact depth of the spheres [s0, s1) of one frame against obstacle sphere w.
+__device__ __forceinline__ float ball_depth(const float* __restrict__ fr, int lane, const float4* __restrict__ sph,
+                                            int s0, int s1, float4 w, float depth)
+{
+    const float r0x = fr[0 * 32 + lane], r0y = fr[1 * 32 + lane], r0z = fr[2 * 32 + lane], r0w = fr[3 * 32 + lane];
+    const float r1x = fr[4 * 32 + lane], r1y = fr[5 * 32 + lane], r1z = fr[6 * 32 + lane], r1w = fr[7 * 32 + lane];
+    const float r2x = fr[8 * 32 + lane], r2y = fr[9 * 32 + lane], r2z = fr[10 * 32 + lane], r2w = fr[11 * 32 + lane];
+    for (int s = s0; s < s1; ++s) {
+        const float4 q = sph[s];
+        const float cx = fmaf(r0x, q.x, fmaf(r0y, q.y, fmaf(r0z, q.z, r0w)));
+        const float cy = fmaf(r1x, q.x, fmaf(r1y, q.y, fmaf(r1z, q.z, r1w)));
+        const float cz = fmaf(r2x, q.x, fmaf(r2y, q.y, fmaf(r2z, q.z, r2w)));
+        const float gx = cx - w.x, gy = cy - w.y, gz = cz - w.z;
+        const float dist2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+        const float rs = q.w + w.w;
+        if (dist2 < rs * rs) depth = fmaxf(depth, rs - sqrtf(dist2));
+    }
+    return depth;
+}
+
+// Centre of sphere q in frame fr (the k_rollout expression).
+__device__ __forceinline__ float3 frame_point(const float* __restrict__ fr, int lane, float4 q)
+{
+    return make_float3(fmaf(fr[0 * 32 + lane], q.x, fmaf(fr[1 * 32 + lane], q.y, fmaf(fr[2 * 32 + lane], q.z, fr[3 * 32 + lane]))),
+                       fmaf(fr[4 * 32 + lane], q.x, fmaf(fr[5 * 32 + lane], q.y, fmaf(fr[6 * 32 + lane], q.z, fr[7 * 32 + lane]))),
+                       fmaf(fr[8 * 32 + lane], q.x, fmaf(fr[9 * 32 + lane], q.y, fmaf(fr[10 * 32 + lane], q.z, fr[11 * 32 + lane]))));
+}
+
+__global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
+k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
+               const StepState* __restrict__ st, int step_override, int iter, int front_only)
+{
+    extern __shared__ __align__(16) float wsm[];
+    const WarpPlan W = warp_plan(pb);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wg = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nw0 = wg * W.PW;  // first particle of this warp
+    if (nw0 >= pb.N) return;    // warp-uniform
+    float* ws = wsm + warp * W.floats;
+    float* s_fr = ws + W.frame;
+    float* s_cb = ws + W.cb;
+    float* s_eps = ws + W.eps;
+    float* s_u = ws + W.u;
+    float* s_th = ws + W.th;
+    float* s_thd = ws + W.thd;
+    float* s_c = ws + W.c;
+    const int d = pb.d, H = pb.H, S = pb.S, F = d + 1, Lp = W.Lp, HD = H * d;
+    const int seg = lane / Lp, hl = lane - seg * Lp;
+    const int np_w = min(W.PW, pb.N - nw0);
+    const int n = nw0 + seg;
+    const bool pvalid = seg < np_w;
+    const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
+    trace_stamp(pb.trace, 0);
+    {
+        // The grid is a single wave, so every warp meets this SM's L1 cold: pull
+        // the read-only tables (and the mean and sigma) into it now, while the
+        // noise is drawn, rather than one dependent miss at a time later.
+        const char* tb = reinterpret_cast<const char*>(pb.tables);
+        for (int o = lane * 128; o < pb.table_bytes; o += 32 * 128)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(tb + o));
+        const char* mb = reinterpret_cast<const char*>(pb.mu);
+        for (int o = lane * 128; o < H * d * 4; o += 32 * 128)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(mb + o));
+        if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(pb.sigma));
+    }
+
+    // ---- noise eps[n][s][j] of the warp's particles
+    const int per = S * d;
+    if (pb.sampler == STORM_SAMPLER_PHILOX) {
+        const uint32_t e0 = static_cast<uint32_t>(nw0) * per;
+        const uint32_t e1 = static_cast<uint32_t>(nw0 + np_w) * per;
+        const uint32_t b0 = e0 >> 2, b1 = (e1 + 3) >> 2;
+        const uint32_t c2 = (pb.instance << 8) | static_cast<uint32_t>(iter);
+        for (uint32_t b = b0 + lane; b < b1; b += 32) {
+            const uint4 x = philox4x32_10(make_uint4(b, step, c2, 0u), pb.seed_lo, pb.seed_hi);
+            const float2 z01 = gauss_pair(x.x, x.y);
+            const float2 z23 = gauss_pair(x.z, x.w);
+            const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const uint32_t e = 4 * b + l;
+                if (e >= e0 && e < e1) s_eps[e - e0] = z[l];
+            }
+        }
+    } else {
+        for (int i = lane; i < np_w * per; i += 32) s_eps[i] = pb.halton[static_cast<size_t>(nw0) * per + i];
+    }
+    __syncwarp();
+    trace_stamp(pb.trace, 1);
+
+    // ---- controls u = mu + sigma o (B eps) of the lane's own steps, null particles zero
+    for (int slot = 0; slot < W.SL; ++slot) {
+        const int h = slot * Lp + hl;
+        if (!pvalid || h >= H) continue;
+        float e[kMaxDof];
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) e[j] = 0.f;
+        if (pb.spline) {
+            const float* eps = s_eps + seg * S * d;
+#pragma unroll 2
+            for (int s = 0; s < S; ++s) {
+                const float b = pb.basis[h * S + s];
+#pragma unroll
+                for (int j = 0; j < kMaxDof; ++j)
+                    if (j < d) e[j] = fmaf(b, eps[s * d + j], e[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j)
+                if (j < d) e[j] = s_eps[(seg * H + h) * d + j];
+        }
+        const bool null = n < pb.n_null;
+        float* su = s_u + (seg * H + h) * d;
+        float* gu = out.u + (static_cast<size_t>(n) * H + h) * d;
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) {
+            if (j < d) {
+                const float uu = null ? 0.f : fmaf(pb.sigma[j], e[j], pb.mu[h * d + j]);
+                su[j] = uu;
+                gu[j] = uu;
+            }
+        }
+    }
+    __syncwarp();
+    // ---- integration per (particle, joint), Eq. 7: the k_rollout recurrence
+    if (lane < np_w * d) {
+        const int p = lane / d, j = lane - p * d;
+        float v = state[d + j], q = state[j];
+#pragma unroll 6
+        for (int h = 0; h < H; ++h) {
+            const int idx = (p * H + h) * d + j;
+            v = fmaf(pb.dt[h], s_u[idx], v);
+            q = fmaf(pb.dt[h], v, q);
+            s_thd[idx] = v;
+            s_th[idx] = q;
+        }
+    }
+    __syncwarp();
+    trace_stamp(pb.trace, 2);
+    if (out.theta)
+        for (int i = lane; i < np_w * HD; i += 32) out.theta[static_cast<size_t>(nw0) * HD + i] = s_th[i];
+    if (out.theta_dot)
+        for (int i = lane; i < np_w * HD; i += 32) out.theta_dot[static_cast<size_t>(nw0) * HD + i] = s_thd[i];
+    if (front_only) return;
+
+    // ---- per-problem constants in registers
+    int first[kMaxDof + 2];
+#pragma unroll
+    for (int f = 0; f < kMaxDof + 2; ++f) first[f] = f <= F ? pb.link_first[f] : pb.M;
+    float4 lbf[kMaxDof + 1];
+#pragma unroll
+    for (int f = 0; f <= kMaxDof; ++f) lbf[f] = f < F ? pb.lbound[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float g[12];  // goal rotation (row-major), then position
+    {
+        const float qn = rsqrtf(goal[3] * goal[3] + goal[4] * goal[4] + goal[5] * goal[5] + goal[6] * goal[6]);
+        const float w = goal[3] * qn, x = goal[4] * qn, y = goal[5] * qn, z = goal[6] * qn;
+        g[0] = 1.f - 2.f * (y * y + z * z);
+        g[1] = 2.f * (x * y - w * z);
+        g[2] = 2.f * (x * z + w * y);
+        g[3] = 2.f * (x * y + w * z);
+        g[4] = 1.f - 2.f * (x * x + z * z);
+        g[5] = 2.f * (y * z - w * x);
+        g[6] = 2.f * (x * z - w * y);
+        g[7] = 2.f * (y * z + w * x);
+        g[8] = 1.f - 2.f * (x * x + y * y);
+        g[9] = goal[0];
+        g[10] = goal[1];
+        g[11] = goal[2];
+    }
+    const bool want_manip = pb.w_manip != 0.f || out.terms;
+    const float* pred = pb.self_pred;
+    const int NO = pb.B + pb.O;
+
+    for (int slot = 0; slot < W.SL; ++slot) {
+        const int h = slot * Lp + hl;
+        const bool valid = pvalid && h < H;
+        const int hc = valid ? h : 0;
+        const int pl = pvalid ? seg : 0;
+        const float* th = s_th + (pl * H + hc) * d;
+        const float* thd = s_thd + (pl * H + hc) * d;
+        const float* uh = s_u + (pl * H + hc) * d;
+        const float* up = (hc == 0) ? state + 2 * d : uh - d;
+        const size_t gi = static_cast<size_t>(n) * H + hc;  // global item (valid lanes)
+
+        // ---- FK frames, Jacobian columns, bounding centres
+        float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+        float pp[3] = {0.f, 0.f, 0.f};
+        float J[6][kMaxDof];
+        float cbx[kMaxDof + 1], cby[kMaxDof + 1], cbz[kMaxDof + 1];
+        {
+            const float fr0[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 12; ++k) s_fr[k * 32 + lane] = fr0[k];
+            cbx[0] = fmaf(1.f, lbf[0].x, fmaf(0.f, lbf[0].y, fmaf(0.f, lbf[0].z, 0.f)));
+            cby[0] = fmaf(0.f, lbf[0].x, fmaf(1.f, lbf[0].y, fmaf(0.f, lbf[0].z, 0.f)));
+            cbz[0] = fmaf(0.f, lbf[0].x, fmaf(0.f, lbf[0].y, fmaf(1.f, lbf[0].z, 0.f)));
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxDof; ++i) {
+            if (i < d) {
+                const float* dh = pb.dhx + i * 8;
+                dh_step(R, pp, dh[0], dh[1], dh[2], dh[3], th[i] + dh[4]);
+                float* fr = s_fr + (i + 1) * 12 * 32 + lane;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    fr[(r * 4 + 0) * 32] = R[r * 3 + 0];
+                    fr[(r * 4 + 1) * 32] = R[r * 3 + 1];
+                    fr[(r * 4 + 2) * 32] = R[r * 3 + 2];
+                    fr[(r * 4 + 3) * 32] = pp[r];
+                }
+                J[0][i] = pp[1] * R[8] - pp[2] * R[5];
+                J[1][i] = pp[2] * R[2] - pp[0] * R[8];
+                J[2][i] = pp[0] * R[5] - pp[1] * R[2];
+                J[3][i] = R[2];
+                J[4][i] = R[5];
+                J[5][i] = R[8];
+                const float4 lb = lbf[i + 1];
+                cbx[i + 1] = fmaf(R[0], lb.x, fmaf(R[1], lb.y, fmaf(R[2], lb.z, pp[0])));
+                cby[i + 1] = fmaf(R[3], lb.x, fmaf(R[4], lb.y, fmaf(R[5], lb.z, pp[1])));
+                cbz[i + 1] = fmaf(R[6], lb.x, fmaf(R[7], lb.y, fmaf(R[8], lb.z, pp[2])));
+            } else {
+#pragma unroll
+                for (int r = 0; r < 6; ++r) J[r][i] = 0.f;
+                cbx[i + 1] = cby[i + 1] = cbz[i + 1] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int f = 0; f <= kMaxDof; ++f) {
+            if (f < F) {
+                s_cb[(f * 3 + 0) * 32 + lane] = cbx[f];
+                s_cb[(f * 3 + 1) * 32 + lane] = cby[f];
+                s_cb[(f * 3 + 2) * 32 + lane] = cbz[f];
+            }
+        }
+
+        // pose (Eq. 9), rotation, stop (Eq. 10), joint limits (Eq. 11), smoothness
+        const float dx = pp[0] - g[9], dy = pp[1] - g[10], dz = pp[2] - g[11];
+        float c_pos = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float e = pb.pos_w[a] * fmaf(g[a], dx, fmaf(g[3 + a], dy, g[6 + a] * dz));
+            c_pos = fmaf(e, e, c_pos);
+        }
+        c_pos = sqrtf(c_pos);
+        float c_rot = 0.f;
+        if (pb.rot_mode == STORM_ROT_QUAT) {
+            float tr = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) tr = fmaf(g[k], R[k], tr);
+            c_rot = 1.f - 0.5f * sqrtf(fmaxf(0.f, 1.f + tr));
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float rtr = fmaf(g[r], R[c], fmaf(g[3 + r], R[3 + c], g[6 + r] * R[6 + c]));
+                    const float e = ((r == c) ? 1.f : 0.f) - rtr;
+                    const float we = e * pb.rot_w[c];
+                    c_rot = fmaf(we, we, c_rot);
+                }
+            c_rot = sqrtf(c_rot);
+        }
+        float c_stop = 0.f, c_joint = 0.f, c_smooth = 0.f;
+        const float vlim = pb.vmax[hc];
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) {
+            if (j < d) {
+                const float vs = fmaxf(0.f, fabsf(thd[j]) - vlim);
+                c_stop = fmaf(vs, vs, c_stop);
+                const float vj = fmaxf(0.f, pb.qlo[j] - th[j]) + fmaxf(0.f, th[j] - pb.qhi[j]);
+                c_joint = fmaf(vj, vj, c_joint);
+                const float du = uh[j] - up[j];
+                c_smooth = fmaf(du, du, c_smooth);
+            }
+        }
+        c_stop = sqrtf(c_stop);
+        c_joint = sqrtf(c_joint);
+        float part = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop + pb.w_joint * c_joint +
+                     pb.w_smooth * c_smooth;
+        if (valid && out.ee) {
+            float* e = out.ee + gi * 12;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                e[r * 4 + 0] = R[r * 3 + 0];
+                e[r * 4 + 1] = R[r * 3 + 1];
+                e[r * 4 + 2] = R[r * 3 + 2];
+                e[r * 4 + 3] = pp[r];
+            }
+        }
+        if (valid && out.terms) {
+            float* t = out.terms + gi * STORM_NTERMS;
+            t[0] = c_pos;
+            t[1] = c_rot;
+            t[2] = c_stop;
+            t[3] = c_joint;
+            t[7] = c_smooth;
+        }
+        // manipulability (Eq. 12)
+        if (want_manip) {
+            const float m = manipulability_mgs(J, d);
+            const float c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
+            part += pb.w_manip * c_manip;
+            if (valid && out.terms) out.terms[gi * STORM_NTERMS + 4] = c_manip;
+        }
+        __syncwarp();
+        trace_stamp(pb.trace, 3);
+
+        // ---- world collision, Eq. 14 reading
+        float dworld = 0.f;
+        if (NO > 0 && pb.M > 0) {
+            if (pb.broadphase) {
+                // box enclosing every link bound of the warp's items, padded 1 mm
+                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+                for (int f = 0; f <= kMaxDof; ++f) {
+                    if (f < F && valid && first[f] < first[f + 1]) {
+                        const float r = lbf[f].w + 1e-3f;
+                        lo[0] = fminf(lo[0], cbx[f] - r);
+                        lo[1] = fminf(lo[1], cby[f] - r);
+                        lo[2] = fminf(lo[2], cbz[f] - r);
+                        hi[0] = fmaxf(hi[0], cbx[f] + r);
+                        hi[1] = fmaxf(hi[1], cby[f] + r);
+                        hi[2] = fmaxf(hi[2], cbz[f] + r);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        lo[a] = fminf(lo[a], __shfl_xor_sync(FULL, lo[a], o));
+                        hi[a] = fmaxf(hi[a], __shfl_xor_sync(FULL, hi[a], o));
+                    }
+                }
+                for (int k0 = 0; k0 < NO; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool near = false;
+                    if (k < pb.B) {
+                        const float* b = pb.boxes + k * 6;
+                        near = b[0] - b[3] <= hi[0] && b[0] + b[3] >= lo[0] && b[1] - b[4] <= hi[1] &&
+                               b[1] + b[4] >= lo[1] && b[2] - b[5] <= hi[2] && b[2] + b[5] >= lo[2];
+                    } else if (k < NO) {
+                        const float4 w = pb.wsph[k - pb.B];
+                        const float ex = w.x - fminf(fmaxf(w.x, lo[0]), hi[0]);
+                        const float ey = w.y - fminf(fmaxf(w.y, lo[1]), hi[1]);
+                        const float ez = w.z - fminf(fmaxf(w.z, lo[2]), hi[2]);
+                        near = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= w.w * w.w;
+                    }
+                    unsigned mask = __ballot_sync(FULL, near);
+                    while (mask) {
+                        const int kk = k0 + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        if (!valid) continue;
+                        if (kk < pb.B) {
+                            const float* box = pb.boxes + kk * 6;
+                            const float lox = box[0] - box[3], loy = box[1] - box[4], loz = box[2] - box[5];
+                            const float hix = box[0] + box[3], hiy = box[1] + box[4], hiz = box[2] + box[5];
+#pragma unroll
+                            for (int f = 0; f <= kMaxDof; ++f) {
+                                if (f < F && first[f] < first[f + 1]) {
+                                    const float ex = cbx[f] - fminf(fmaxf(cbx[f], lox), hix);
+                                    const float ey = cby[f] - fminf(fmaxf(cby[f], loy), hiy);
+                                    const float ez = cbz[f] - fminf(fmaxf(cbz[f], loz), hiz);
+                                    if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < lbf[f].w * lbf[f].w)
+                                        dworld = box_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
+                                                           box, dworld);
+                                }
+                            }
+                        } else {
+                            const float4 w = pb.wsph[kk - pb.B];
+#pragma unroll
+                            for (int f = 0; f <= kMaxDof; ++f) {
+                                if (f < F && first[f] < first[f + 1]) {
+                                    const float ex = cbx[f] - w.x, ey = cby[f] - w.y, ez = cbz[f] - w.z;
+                                    const float rb = lbf[f].w + w.w;
+                                    if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rb * rb)
+                                        dworld = ball_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
+                                                            w, dworld);
+                                }
+                            }
+                        }
+                    }
+                }
+            } else if (valid) {
+                // brute force: every sphere against every obstacle
+#pragma unroll
+                for (int f = 0; f <= kMaxDof; ++f) {
+                    if (f < F && first[f] < first[f + 1]) {
+                        for (int b = 0; b < pb.B; ++b)
+                            dworld = box_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
+                                               pb.boxes + b * 6, dworld);
+                        for (int k = 0; k < pb.O; ++k)
+                            dworld = ball_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
+                                                pb.wsph[k], dworld);
+                    }
+                }
+            }
+        }
+        trace_stamp(pb.trace, 4);
+
+        // ---- self collision, Eq. 13 reading: frame pairs whose bounds overlap
+        // (register tests over the compile-time list of pairs), then their
+        // pair blocks exactly; then the leftover pairs
+        float dself = 0.f;
+        const bool do_self = valid && !(pred && pred[gi] >= pb.self_margin);
+        uint32_t lp_hit = 0u;  // bit t: frame pair t has blocks and its bounds overlap
+        if (do_self) {
+#pragma unroll
+            for (int la = 0; la < kMaxDof; ++la) {
+#pragma unroll
+                for (int lb = la + 1; lb <= kMaxDof; ++lb) {
+                    const int t = link_pair_index(la, lb);
+                    if (lb < F && pb.lp_begin[t] < pb.lp_begin[t + 1]) {
+                        bool pass = true;
+                        if (pb.broadphase) {
+                            const float ex = cbx[la] - cbx[lb], ey = cby[la] - cby[lb], ez = cbz[la] - cbz[lb];
+                            const float rr = lbf[la].w + lbf[lb].w;
+                            pass = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rr * rr;
+                        }
+                        if (pass) lp_hit |= 1u << t;
+                    }
+                }
+            }
+        }
+        while (lp_hit) {
+            const int t = __ffs(lp_hit) - 1;
+            lp_hit &= lp_hit - 1;
+            int bk0 = 0, bk1 = 0;  // the pair's block range, read with constant indices only
+#pragma unroll
+            for (int u = 0; u < kLinkPairs; ++u) {
+                if (u == t) {
+                    bk0 = pb.lp_begin[u];
+                    bk1 = pb.lp_begin[u + 1];
+                }
+            }
+            for (int bk = bk0; bk < bk1; ++bk) {
+                const uint4 blk = pb.pblk[bk];  // a0, a1, b0, nb
+                int la = 0, lk = 0;
+#pragma unroll
+                for (int f = 1; f <= kMaxDof; ++f) {
+                    if (f <= d) {
+                        la += static_cast<int>(blk.x) >= first[f];
+                        lk += static_cast<int>(blk.z) >= first[f];
+                    }
+                }
+                const float4 bb = pb.lbound[lk];
+                const float ckx = s_cb[(lk * 3 + 0) * 32 + lane], cky = s_cb[(lk * 3 + 1) * 32 + lane],
+                            ckz = s_cb[(lk * 3 + 2) * 32 + lane];
+                const float* fa = s_fr + la * 12 * 32;
+                const float* fb = s_fr + lk * 12 * 32;
+                float4 cbk[8];
+                bool have_b = false;  // second-frame centres, computed on first need
+                for (uint32_t a = blk.x; a < blk.y; ++a) {
+                    const float4 q = pb.sph[a];
+                    const float3 c = frame_point(fa, lane, q);
+                    if (pb.broadphase) {  // sphere a apart from the second frame's bound: no pair touches
+                        const float ex = c.x - ckx, ey = c.y - cky, ez = c.z - ckz;
+                        const float rr = q.w + bb.w;
+                        if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rr * rr) continue;
+                    }
+                    if (!have_b) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (k < static_cast<int>(blk.w)) {
+                                const float4 qb = pb.sph[blk.z + k];
+                                const float3 cb = frame_point(fb, lane, qb);
+                                cbk[k] = make_float4(cb.x, cb.y, cb.z, qb.w);
+                            } else {
+                                cbk[k] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                            }
+                        }
+                        have_b = true;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float ex = c.x - cbk[k].x, ey = c.y - cbk[k].y, ez = c.z - cbk[k].z;
+                        const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        const float rs = q.w + cbk[k].w;
+                        if (dist2 < rs * rs) dself = fmaxf(dself, rs - sqrtf(dist2));
+                    }
+                }
+            }
+        }
+        if (do_self) {
+            for (int k = 0; k < pb.P; ++k) {
+                const uint32_t pr = pb.pairs[k];
+                const int a = pr & 0xffff, b = pr >> 16;
+                int la = 0, lk = 0;
+#pragma unroll
+                for (int f = 1; f <= kMaxDof; ++f) {
+                    if (f <= d) {
+                        la += a >= first[f];
+                        lk += b >= first[f];
+                    }
+                }
+                const float4 qa = pb.sph[a], qb = pb.sph[b];
+                const float rs = qa.w + qb.w;
+                const float3 ca = frame_point(s_fr + la * 12 * 32, lane, qa);
+                const float3 cb = frame_point(s_fr + lk * 12 * 32, lane, qb);
+                const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
+                const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                if (dist2 < rs * rs) dself = fmaxf(dself, rs - sqrtf(dist2));
+            }
+        }
+        trace_stamp(pb.trace, 5);
+
+        // ---- running cost (Eq. 15)
+        const float c = part + pb.w_coll * (dself + dworld);
+        if (valid) {
+            s_c[pl * H + h] = c;
+            if (out.cost) out.cost[gi] = c;
+            if (out.terms) {
+                out.terms[gi * STORM_NTERMS + 5] = dself;
+                out.terms[gi * STORM_NTERMS + 6] = dworld;
+            }
+        }
+        __syncwarp();  // the next slot rewrites the frames
+    }
+    // ---- discounted total (Eq. 2), the k_rollout order
+    if (lane < np_w) {
+        float C = 0.f;
+#pragma unroll 6
+        for (int h = 0; h < H; ++h) C = fmaf(pb.gpow[h], s_c[lane * H + h], C);
+        out.Ctot[nw0 + lane] = C;
+    }
+    trace_stamp(pb.trace, 6);
+}

@@ -345,6 +345,62 @@ def test_launch_shapes_are_bitwise_identical_and_autotune():
             assert np.array_equal(g[k], ref[k]), k
 
 
+def _mapping_cases():
+    paper = W.config_paper(0)
+    dense = W.config_paper(3)
+    dense.world = W.make_world(43, n_boxes=64, n_spheres=64)
+    return {
+        # every cost term active (state chosen on the oracle, see the collision test)
+        "paper_terms": (paper, paper.params.replace(N=61), 21),
+        "dense_world": (dense, dense.params.replace(N=40, w_smooth=0.3), 63),
+        "H5_N37_white": (paper, paper.params.replace(N=37, H=5, n_knots=0, n_null=3), 1),
+        "H12_N37_halton": (paper, paper.params.replace(N=37, H=12, sampler=W.SAMPLER_HALTON), 2),
+        "H16_N9_frob": (paper, paper.params.replace(N=9, H=16, rot_mode=W.ROT_FROBENIUS,
+                                                    rot_axis_w=(0.5, 1.0, 2.0)), 4),
+        "H50_N23": (paper, paper.params.replace(N=23, H=50, n_knots=10), 5),
+        "H64_N3": (paper, paper.params.replace(N=3, H=64, n_knots=0), 6),
+    }
+
+
+@pytest.mark.parametrize("name", list(_mapping_cases()))
+def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
+    """Both work mappings, every warp count and both collision modes give the
+    same bits in every output (controls, joint states, EE poses, cost terms,
+    running and total costs)."""
+    wl, p, sseed = _mapping_cases()[name]
+    state = W.make_state(sseed, 7)
+    if sseed == 21:
+        state[0, 3], state[1, 3] = 2.2, 0.8
+    state, goal = cuda(f32(state)), cuda(f32(wl.goal))
+    mu, sig = f32(W.make_mean(sseed, p.H, 7, 0.8)), f32(W.make_sigma(sseed, 7, 0.2, 0.6))
+    with _ctl(wl, p) as ctl:
+        assert ctl.launch_mapping() == "warp"
+        ctl.set_distribution(mu, sig)
+        ctl.set_launch(2, 256)
+        assert ctl.launch_mapping() == "cta"
+        ref = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 3, 1).items()}
+        for bp in (True, False):
+            ctl.set_broadphase(bp)
+            for wpc in (1, 3, 8):
+                ctl.set_launch_warp(wpc)
+                assert ctl.launch_mapping() == "warp"
+                ppc, threads = ctl.get_launch()
+                assert threads == 32 * wpc
+                g = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 3, 1).items()}
+                for k in ref:
+                    assert np.array_equal(g[k], ref[k]), (bp, wpc, k)
+        with pytest.raises(StormError):
+            ctl.set_launch_warp(0)
+        with pytest.raises(StormError):
+            ctl.set_launch_warp(9)
+    active = {nm for t, nm in enumerate(W.TERM_NAMES) if (ref["terms"][..., t] > 0).any()}
+    assert {"pos", "rot", "manip"} <= active
+    if name == "paper_terms":  # both collision phases exercised (checked on the oracle)
+        assert {"self", "world"} <= active, active
+    if name == "dense_world":
+        assert "world" in active, active
+
+
 @pytest.mark.parametrize("seed,world", [(0, None), (3, (64, 64)), (5, (8, 0))])
 def test_broadphase_is_bitwise_identical(seed, world):
     wl = W.config_paper(seed)
