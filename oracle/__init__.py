@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "storm_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "libstorm_oracle.so")
-NTERMS = 8
+NTERMS = 11
 
 
 def build(force: bool = False) -> str:
@@ -72,7 +72,11 @@ class _Params(C.Structure):
                 ("w_smooth", C.c_double), ("pos_axis_w", C.c_double * 3),
                 ("rot_axis_w", C.c_double * 3), ("rot_mode", C.c_int), ("k_jl", C.c_double),
                 ("k_m", C.c_double), ("qdd_max", C.c_double), ("seed", C.c_uint64),
-                ("instance", C.c_uint32), ("grad_steps", C.c_int), ("grad_eta", C.c_double)]
+                ("instance", C.c_uint32), ("grad_steps", C.c_int), ("grad_eta", C.c_double),
+                ("filter", C.c_int), ("comb", C.c_double * 3), ("mix_bspline", C.c_double),
+                ("w_ee_vel", C.c_double), ("w_ee_acc", C.c_double), ("ee_vel_max", C.c_double),
+                ("ee_acc_max", C.c_double), ("w_ball", C.c_double), ("gravity", C.c_double * 3),
+                ("tray_center", C.c_double * 3), ("ball", _dp)]
 
 
 def _declare(L):
@@ -131,6 +135,10 @@ def _declare(L):
     L.orc_mlp_loss_grad.restype = C.c_double
     L.orc_self_min_sd_theta.argtypes = [C.POINTER(_Robot), _dp]
     L.orc_self_min_sd_theta.restype = C.c_double
+    L.orc_comb_filter.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
+    L.orc_ee_twist.argtypes = [C.POINTER(_Robot), _dp, _dp, _dp, _dp, _dp]
+    L.orc_ball_states.argtypes = [C.POINTER(_Robot), C.POINTER(_Params), _dp, _dp, _dp, _dp]
+    L.orc_ball_states.restype = C.c_int
 
 
 def _f64(a):
@@ -189,6 +197,15 @@ def norm_ppf(p: float) -> float:
 def noise_halton(N, S, d) -> np.ndarray:
     out = np.zeros((N, S, d))
     lib().orc_noise_halton(N, S, d, _ptr(out))
+    return out
+
+
+def comb_filter(c, eps) -> np.ndarray:
+    """Comb filter of eps (H x d) along the horizon with coefficients c (3,)."""
+    e = _f64(eps)
+    H, d = e.shape
+    out = np.zeros((H, d))
+    lib().orc_comb_filter(H, d, _ptr(_f64(c)), _ptr(e), _ptr(out))
     return out
 
 
@@ -317,12 +334,26 @@ class Oracle:
         s.rot_mode, s.k_jl, s.k_m, s.qdd_max = p.rot_mode, p.k_jl, p.k_m, p.qdd_max
         s.seed, s.instance = int(p.seed), int(p.instance)
         s.grad_steps, s.grad_eta = int(p.grad_steps), float(p.grad_eta)
+        s.filter, s.mix_bspline = int(p.filter), float(p.mix_bspline)
+        s.comb[:] = [float(c) for c in p.comb]
+        s.w_ee_vel, s.w_ee_acc = float(p.w_ee_vel), float(p.w_ee_acc)
+        s.ee_vel_max, s.ee_acc_max = float(p.ee_vel_max), float(p.ee_acc_max)
+        s.w_ball = float(p.w_ball)
+        s.gravity[:] = [float(g) for g in p.gravity]
+        s.tray_center[:] = [float(c) for c in p.tray_center]
+        s.ball = None
         return s
+
+    def set_ball(self, pos, vel):
+        """Ball position and velocity (world frame) at the current robot state."""
+        self._ball = _f64(np.concatenate([np.asarray(pos, float).ravel(), np.asarray(vel, float).ravel()]))
+        assert self._ball.shape == (6,)
+        self.P.ball = _ptr(self._ball)
 
     @property
     def n_noise(self):
         p = self.params
-        return p.n_knots if p.n_knots > 0 else p.H
+        return p.n_knots if (p.filter == 0 and p.n_knots > 0) else p.H
 
     # -- stages
     def noise(self, step: int, it: int) -> np.ndarray:
@@ -337,6 +368,24 @@ class Oracle:
         frames = np.zeros((self.d + 1, 4, 4))
         lib().orc_fk(C.byref(self.R), _ptr(th), _ptr(frames))
         return frames
+
+    def ee_twist(self, theta, theta_dot, theta_ddot):
+        """(X_dot, X_ddot) of Eq. 8, each [linear; angular] (6,)."""
+        frames = self.fk(theta)
+        xd, xdd = np.zeros(6), np.zeros(6)
+        lib().orc_ee_twist(C.byref(self.R), _ptr(frames), _ptr(_f64(theta_dot)),
+                           _ptr(_f64(theta_ddot)), _ptr(xd), _ptr(xdd))
+        return xd, xdd
+
+    def ball_states(self, state, theta):
+        """Ball position and velocity in the end-effector frame along one rollout (H x 3 each)."""
+        H = self.params.H
+        xb, vb = np.zeros((H, 3)), np.zeros((H, 3))
+        rc = lib().orc_ball_states(C.byref(self.R), C.byref(self.P), _ptr(_f64(state)),
+                                   _ptr(_f64(theta)), _ptr(xb), _ptr(vb))
+        if rc != 0:
+            raise ValueError("no ball state set")
+        return xb, vb
 
     def jacobian(self, theta) -> np.ndarray:
         frames = self.fk(theta)

@@ -186,29 +186,68 @@ void orc_bspline_basis(int H, int S, double* B)
 }
 
 /* u_{n,h} = mu_h + sigma o (B eps_n)_h ; null particles get u = 0 (Sec. 4.3). */
+/* Samples per particle and joint drawn for one iteration: the knots of the
+ * B-spline, or one per horizon step (no smoothing, comb and mixed filters). */
+static int noise_samples(const orc_params* P)
+{
+    if (P->filter == ORC_FILTER_DEFAULT && P->n_knots > 0) return P->n_knots;
+    return P->H;
+}
+
+/* Comb filter along the horizon (Sec. 4.3): out_h = c1 eps_h + c2 out_{h-1} +
+ * c3 out_{h-2}.  Readings: the printed third term repeats index h-1 and is read
+ * as h-2; the recursion runs over the already filtered values (the in-place
+ * update the formula describes); values before h = 0 are zero.  eps, out: H x d. */
+void orc_comb_filter(int H, int d, const double* c, const double* eps, double* out)
+{
+    for (int j = 0; j < d; ++j)
+        for (int h = 0; h < H; ++h) {
+            const double y1 = h >= 1 ? out[(h - 1) * d + j] : 0.0;
+            const double y2 = h >= 2 ? out[(h - 2) * d + j] : 0.0;
+            out[h * d + j] = c[0] * eps[h * d + j] + c[1] * y1 + c[2] * y2;
+        }
+}
+
+/* sample_controls (Algorithm 1, Sec. 4.3): u = mu + sigma o smooth(eps), with
+ * the filter of P->filter; particles 0..n_null-1 are the zero-acceleration
+ * ("null") particles.  eps: N x S x d with S = noise_samples(P). */
 void orc_smooth_controls(const orc_params* P, int d, const double* mu, const double* sigma,
                          const double* eps, double* u)
 {
-    const int N = P->N, H = P->H, S = P->n_knots > 0 ? P->n_knots : P->H;
+    const int N = P->N, H = P->H, S = noise_samples(P), K = P->n_knots;
     double* B = NULL;
-    if (P->n_knots > 0) {
-        B = (double*)malloc(sizeof(double) * H * S);
-        orc_bspline_basis(H, S, B);
+    if (K > 0 && P->filter != ORC_FILTER_COMB) {
+        B = (double*)malloc(sizeof(double) * H * K);
+        orc_bspline_basis(H, K, B);
     }
-    for (int n = 0; n < N; ++n)
+    const int n_bs = P->filter == ORC_FILTER_MIXED ? (int)floor(P->mix_bspline * (N - P->n_null) + 0.5) : 0;
+    double* filt = (double*)malloc(sizeof(double) * H * d);
+    for (int n = 0; n < N; ++n) {
+        const double* en = eps + (long long)n * S * d;
+        int use_bs = 0, use_comb = 0;
+        if (P->filter == ORC_FILTER_DEFAULT) use_bs = K > 0;
+        else if (P->filter == ORC_FILTER_COMB) use_comb = 1;
+        else {
+            use_bs = n >= P->n_null && n < P->n_null + n_bs;
+            use_comb = !use_bs;
+        }
+        if (use_comb) orc_comb_filter(H, d, P->comb, en, filt);
         for (int h = 0; h < H; ++h)
             for (int j = 0; j < d; ++j) {
                 double e;
-                if (B) {
+                if (use_bs) {
                     e = 0.0;
-                    for (int s = 0; s < S; ++s)
-                        e += B[h * S + s] * eps[((long long)n * S + s) * d + j];
+                    for (int s = 0; s < K; ++s) e += B[h * K + s] * en[s * d + j];
+                } else if (use_comb) {
+                    e = filt[h * d + j];
                 } else {
-                    e = eps[((long long)n * H + h) * d + j];
+                    e = en[h * d + j];
                 }
                 const long long idx = ((long long)n * H + h) * d + j;
                 u[idx] = (n < P->n_null) ? 0.0 : mu[h * d + j] + sigma[j] * e;
             }
+    }
+    free(filt);
     free(B);
 }
 
@@ -332,6 +371,104 @@ void orc_jacobian(const orc_robot* R, const double* frames, double* J)
         J[4 * d + c] = z[1];
         J[5 * d + c] = z[2];
     }
+}
+
+/* End-effector velocity and acceleration, Eq. 8: X_dot = J theta_dot and
+ * X_ddot = J_dot theta_dot + J theta_ddot, both as [linear; angular] about the
+ * end-effector point.  J_dot by columns: with z_i, o_i the axis and origin of
+ * joint i, w_{i-1} = sum_{k<i} theta_dot_k z_k the angular velocity of the link
+ * before it, z_i_dot = w_{i-1} x z_i, o_i_dot = sum_{k<i} theta_dot_k z_k x
+ * (o_i - o_k) and p_dot the linear part of X_dot, column i of J_dot is
+ * [z_i_dot x (p - o_i) + z_i x (p_dot - o_i_dot); z_i_dot]. */
+void orc_ee_twist(const orc_robot* R, const double* frames, const double* theta_dot,
+                  const double* theta_ddot, double* xd, double* xdd)
+{
+    const int d = R->dof;
+    double J[6 * 8];
+    orc_jacobian(R, frames, J);
+    for (int r = 0; r < 6; ++r) {
+        xd[r] = 0.0;
+        for (int c = 0; c < d; ++c) xd[r] += J[r * d + c] * theta_dot[c];
+    }
+    const double* Te = frames + d * 16;
+    const double p[3] = {Te[3], Te[7], Te[11]};
+    double w[3] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < 6; ++r) xdd[r] = 0.0;
+    for (int c = 0; c < d; ++c) {
+        const double* T = frames + (c + 1) * 16;
+        const double z[3] = {T[2], T[6], T[10]}, o[3] = {T[3], T[7], T[11]};
+        const double zd[3] = {w[1] * z[2] - w[2] * z[1], w[2] * z[0] - w[0] * z[2], w[0] * z[1] - w[1] * z[0]};
+        double od[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < c; ++k) {
+            const double* Tk = frames + (k + 1) * 16;
+            const double zk[3] = {Tk[2], Tk[6], Tk[10]};
+            const double r[3] = {o[0] - Tk[3], o[1] - Tk[7], o[2] - Tk[11]};
+            od[0] += theta_dot[k] * (zk[1] * r[2] - zk[2] * r[1]);
+            od[1] += theta_dot[k] * (zk[2] * r[0] - zk[0] * r[2]);
+            od[2] += theta_dot[k] * (zk[0] * r[1] - zk[1] * r[0]);
+        }
+        const double r[3] = {p[0] - o[0], p[1] - o[1], p[2] - o[2]};
+        const double q[3] = {xd[0] - od[0], xd[1] - od[1], xd[2] - od[2]};
+        const double jd[3] = {zd[1] * r[2] - zd[2] * r[1] + z[1] * q[2] - z[2] * q[1],
+                              zd[2] * r[0] - zd[0] * r[2] + z[2] * q[0] - z[0] * q[2],
+                              zd[0] * r[1] - zd[1] * r[0] + z[0] * q[1] - z[1] * q[0]};
+        for (int a = 0; a < 3; ++a) {
+            xdd[a] += jd[a] * theta_dot[c] + J[a * d + c] * theta_ddot[c];
+            xdd[3 + a] += zd[a] * theta_dot[c] + z[a] * theta_ddot[c];
+        }
+        for (int a = 0; a < 3; ++a) w[a] += theta_dot[c] * z[a];
+    }
+}
+
+/* Ball on the tray (appendix, ball balancing): the ball's state in the
+ * end-effector frame at the current robot state, x0 = T_ee^-1 x_w and
+ * v0 = R_ee^T v_w with its normal component zeroed, then per horizon step the
+ * in-plane gravity a_h = [g_ee,x, g_ee,y, 0], g_ee = R_ee,h^T g_w, integrated by
+ * the same tensorised model as the joints (Eq. 7): v_h = v0 + sum_{k<=h} dt_k a_k,
+ * x_h = x0 + sum_{k<=h} dt_k v_k.  theta: H x d; outputs H x 3.  -1 without a ball. */
+int orc_ball_states(const orc_robot* R, const orc_params* P, const double* state,
+                    const double* theta, double* x_ball, double* v_ball)
+{
+    if (!P->ball) return -1;
+    const int d = R->dof, H = P->H;
+    double* frames = (double*)malloc(sizeof(double) * 16 * (d + 1));
+    double* a = (double*)malloc(sizeof(double) * 3 * H);
+    orc_fk(R, state, frames);
+    const double* T0 = frames + d * 16;
+    double x0[3], v0[3];
+    for (int i = 0; i < 3; ++i) {
+        x0[i] = 0.0;
+        v0[i] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            x0[i] += T0[k * 4 + i] * (P->ball[k] - T0[k * 4 + 3]);
+            v0[i] += T0[k * 4 + i] * P->ball[3 + k];
+        }
+    }
+    v0[2] = 0.0;
+    for (int h = 0; h < H; ++h) {
+        orc_fk(R, theta + (size_t)h * d, frames);
+        const double* T = frames + d * 16;
+        for (int i = 0; i < 2; ++i) {
+            a[h * 3 + i] = 0.0;
+            for (int k = 0; k < 3; ++k) a[h * 3 + i] += T[k * 4 + i] * P->gravity[k];
+        }
+        a[h * 3 + 2] = 0.0;
+    }
+    for (int h = 0; h < H; ++h)
+        for (int i = 0; i < 3; ++i) {
+            double v = v0[i];
+            for (int k = 0; k <= h; ++k) v += P->dt[k] * a[k * 3 + i];
+            v_ball[h * 3 + i] = v;
+        }
+    for (int h = 0; h < H; ++h)
+        for (int i = 0; i < 3; ++i) {
+            double x = x0[i];
+            for (int k = 0; k <= h; ++k) x += P->dt[k] * v_ball[k * 3 + i];
+            x_ball[h * 3 + i] = x;
+        }
+    free(a);
+    free(frames);
+    return 0;
 }
 
 /* Determinant by LU with partial pivoting. */
@@ -578,6 +715,14 @@ void orc_running_cost(const orc_robot* R, const orc_world* W, const orc_params* 
     const double c_self = sd_self < 0.0 ? -sd_self : 0.0;
     const double c_world = sd_world < 0.0 ? -sd_world : 0.0;
 
+    /* task-space speed and acceleration limits on Eq. 8's X_dot, X_ddot (theta_ddot = u) */
+    double xd[6], xdd[6];
+    orc_ee_twist(R, frames, theta_dot_h, u_h, xd, xdd);
+    const double speed = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+    const double accel = sqrt(xdd[0] * xdd[0] + xdd[1] * xdd[1] + xdd[2] * xdd[2]);
+    const double c_eev = speed > P->ee_vel_max ? speed - P->ee_vel_max : 0.0;
+    const double c_eea = accel > P->ee_acc_max ? accel - P->ee_acc_max : 0.0;
+
     terms[0] = c_pos;
     terms[1] = c_rot;
     terms[2] = c_stop;
@@ -586,8 +731,12 @@ void orc_running_cost(const orc_robot* R, const orc_world* W, const orc_params* 
     terms[5] = c_self;
     terms[6] = c_world;
     terms[7] = c_smooth;
+    terms[8] = c_eev;
+    terms[9] = c_eea;
+    terms[10] = 0.0;  /* the ball term needs the whole rollout: orc_rollout */
     *total = P->w_pos * c_pos + P->w_rot * c_rot + P->w_stop * c_stop + P->w_joint * c_joint +
-             P->w_manip * c_manip + P->w_coll * (c_self + c_world) + P->w_smooth * c_smooth;
+             P->w_manip * c_manip + P->w_coll * (c_self + c_world) + P->w_smooth * c_smooth +
+             P->w_ee_vel * c_eev + P->w_ee_acc * c_eea;
     free(frames);
 }
 
@@ -610,16 +759,25 @@ int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
     double* th = (double*)malloc(sizeof(double) * (size_t)H * d);
     double* thd = (double*)malloc(sizeof(double) * (size_t)H * d);
     double* frames = (double*)malloc(sizeof(double) * 16 * (d + 1));
+    double* xb = (double*)malloc(sizeof(double) * 3 * H);
+    double* vb = (double*)malloc(sizeof(double) * 3 * H);
     orc_smooth_controls(P, d, mu, sigma, eps, u);
     for (int n = 0; n < N; ++n) {
         const double* un = u + (size_t)n * H * d;
         orc_integrate(H, d, P->dt, state, un, th, thd);
+        const int with_ball = P->w_ball != 0.0 && P->ball;
+        if (with_ball) orc_ball_states(R, P, state, th, xb, vb);
         double C = 0.0;
         for (int h = 0; h < H; ++h) {
             double terms[ORC_NTERMS], c;
             const double* uprev = (h == 0) ? state + 2 * d : un + (h - 1) * d;
             orc_running_cost(R, W, P, goal, h, th + h * d, thd + h * d, un + h * d, uprev, terms,
                              &c);
+            if (with_ball) {  /* distance of the ball from the tray centre, in the tray plane */
+                const double ex = xb[h * 3] - P->tray_center[0], ey = xb[h * 3 + 1] - P->tray_center[1];
+                terms[10] = sqrt(ex * ex + ey * ey);
+                c += P->w_ball * terms[10];
+            }
             C += pow(P->gamma, (double)h) * c;
             const size_t nh = (size_t)n * H + h;
             if (terms_out) memcpy(terms_out + nh * ORC_NTERMS, terms, sizeof(terms));
@@ -639,6 +797,8 @@ int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
     free(th);
     free(thd);
     free(frames);
+    free(xb);
+    free(vb);
     return 0;
 }
 
@@ -719,7 +879,7 @@ int orc_step(const orc_robot* R, const orc_world* W, const orc_params* P,
              double* sigma, double* cmd, double* best_cost)
 {
     const int N = P->N, H = P->H, d = R->dof;
-    const int S = P->n_knots > 0 ? P->n_knots : H;
+    const int S = noise_samples(P);
     const long long count = (long long)N * S * d;
     double* eps = (double*)malloc(sizeof(double) * (size_t)count);
     double* u = (double*)malloc(sizeof(double) * (size_t)N * H * d);
@@ -1109,6 +1269,9 @@ int orc_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
 {
     const int N = P->N, H = P->H, d = R->dof;
     if (N <= 0 || H <= 0 || d <= 0 || d > 8) return -1;
+    /* the adjoint covers the paper's cost terms and the default smoothing */
+    if (P->filter != ORC_FILTER_DEFAULT || P->w_ee_vel != 0.0 || P->w_ee_acc != 0.0 || P->w_ball != 0.0)
+        return -2;
     double* u = (double*)malloc(sizeof(double) * (size_t)N * H * d);
     double* th = (double*)malloc(sizeof(double) * H * d);
     double* thd = (double*)malloc(sizeof(double) * H * d);

@@ -36,7 +36,9 @@ extern "C" {
 
 enum { ORC_SAMPLER_PHILOX = 0, ORC_SAMPLER_HALTON = 1 };
 enum { ORC_ROT_QUAT = 0, ORC_ROT_FROBENIUS = 1 };
-enum { ORC_NTERMS = 8 };  /* pos, rot, stop, joint, manip, self, world, smooth */
+enum { ORC_FILTER_DEFAULT = 0, ORC_FILTER_COMB = 1, ORC_FILTER_MIXED = 2 };
+/* pos, rot, stop, joint, manip, self, world, smooth, ee speed, ee acceleration, ball */
+enum { ORC_NTERMS = 11 };
 
 typedef struct {
     int dof;
@@ -73,6 +75,23 @@ typedef struct {
     uint32_t instance;
     int grad_steps;         /* gradient refinement steps after the K iterations */
     double grad_eta;        /* mu <- mu - grad_eta dJ/dmu */
+    /* smoothing of the sampled noise along the horizon (Sec. 4.3):
+     *   DEFAULT  B-spline through n_knots samples when n_knots > 0, else none;
+     *   COMB     comb filter with coefficients comb[0..2] on H samples;
+     *   MIXED    H samples per particle; the first round(mix_bspline (N - n_null))
+     *            non-null particles take the B-spline through their first n_knots
+     *            samples, the others the comb filter */
+    int filter;
+    double comb[3];
+    double mix_bspline;
+    /* task-space limits on the end-effector linear speed |v| and acceleration |a|
+     * of Eq. 8's X_dot and X_ddot (terms added to the paper's list) */
+    double w_ee_vel, w_ee_acc, ee_vel_max, ee_acc_max;
+    /* ball on a tray held by the end effector (appendix, ball balancing) */
+    double w_ball;
+    double gravity[3];      /* g in the world frame */
+    double tray_center[3];  /* tray centre in the end-effector frame */
+    const double* ball;     /* 6: ball position, velocity (world) at the current state; NULL: none */
 } orc_params;
 
 /* ---- noise ---- */
@@ -101,6 +120,11 @@ void orc_rot_from_quat(const double* q, double* Rm);
 double orc_box_sdf(const double* p, const double* box);
 double orc_self_min_sd(const orc_robot* R, const double* frames);
 double orc_world_min_sd(const orc_robot* R, const orc_world* W, const double* frames);
+void orc_comb_filter(int H, int d, const double* c, const double* eps, double* out);
+void orc_ee_twist(const orc_robot* R, const double* frames, const double* theta_dot,
+                  const double* theta_ddot, double* xd, double* xdd);
+int orc_ball_states(const orc_robot* R, const orc_params* P, const double* state,
+                    const double* theta, double* x_ball, double* v_ball);
 void orc_running_cost(const orc_robot* R, const orc_world* W, const orc_params* P,
                       const double* goal, int h, const double* theta_h,
                       const double* theta_dot_h, const double* u_h, const double* u_prev,

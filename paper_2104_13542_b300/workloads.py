@@ -33,7 +33,10 @@ SAMPLER_HALTON = 1
 ROT_QUAT = 0
 ROT_FROBENIUS = 1
 N_TERMS = 8
-TERM_NAMES = ("pos", "rot", "stop", "joint", "manip", "self", "world", "smooth")
+TERM_NAMES = ("pos", "rot", "stop", "joint", "manip", "self", "world", "smooth", "ee_vel", "ee_acc",
+              "ball")
+NTERMS = len(TERM_NAMES)
+FILTER_DEFAULT, FILTER_COMB, FILTER_MIXED = 0, 1, 2
 
 
 @dataclass
@@ -88,6 +91,21 @@ class Params:
     instance: int = 0
     grad_steps: int = 0
     grad_eta: float = 0.0
+    # noise smoothing along the horizon: FILTER_DEFAULT (B-spline when n_knots > 0),
+    # FILTER_COMB (comb coefficients), FILTER_MIXED (mix_bspline of the particles
+    # B-spline, the rest comb)
+    filter: int = 0
+    comb: tuple = (0.5, 0.3, 0.2)
+    mix_bspline: float = 0.6
+    # task-space limits on the end-effector speed / acceleration (m/s, m/s^2)
+    w_ee_vel: float = 0.0
+    w_ee_acc: float = 0.0
+    ee_vel_max: float = 1.0
+    ee_acc_max: float = 10.0
+    # ball on a tray held by the end effector
+    w_ball: float = 0.0
+    gravity: tuple = (0.0, 0.0, -9.81)
+    tray_center: tuple = (0.0, 0.0, 0.0)
 
     def replace(self, **kw) -> "Params":
         p = dataclasses.replace(self, **kw)
@@ -104,6 +122,7 @@ class Workload:
     params: Params
     state: np.ndarray  # (3, d) theta, theta_dot, theta_ddot
     goal: np.ndarray   # (7,) x, y, z, qw, qx, qy, qz
+    ball: np.ndarray = None  # (6,) ball position and velocity, world frame (ball-on-tray only)
 
 
 def _segment_end(dh: np.ndarray, i: int) -> np.ndarray:
@@ -239,6 +258,45 @@ def config_differentiable(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
     wl.params = wl.params.replace(grad_steps=5, grad_eta=0.01)
     wl.name = f"storm_{N}x{H}_7dof_k3_spline6_grad5"
     return wl
+
+
+def config_variable_dt(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
+    """Paper-scale step on a variable time-step schedule (Sec. 4.1: small steps near
+    the current state, growing along the horizon): dt_h = 0.01 * 1.08^h (0.01 s to
+    0.093 s, 1.13 s in all), with end-effector speed (0.5 m/s) and acceleration
+    (4 m/s^2) limits weighted into the cost."""
+    wl = config_paper(seed, N, H)
+    wl.params = wl.params.replace(dt=0.01 * 1.08 ** np.arange(H), w_ee_vel=50.0, w_ee_acc=5.0,
+                                  ee_vel_max=0.5, ee_acc_max=4.0)
+    wl.name = f"storm_{N}x{H}_7dof_k3_spline6_vardt_eelimits"
+    return wl
+
+
+def config_mixed(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
+    """Paper-scale step with the mixed sampler: 0.6 of the particles B-spline
+    smoothed (6 knots), 0.4 comb filtered (coefficients 0.5, 0.3, 0.2)."""
+    wl = config_paper(seed, N, H)
+    wl.params = wl.params.replace(filter=FILTER_MIXED, mix_bspline=0.6, comb=(0.5, 0.3, 0.2))
+    wl.name = f"storm_{N}x{H}_7dof_k3_mixed"
+    return wl
+
+
+def config_ball(seed: int = 0, N: int = 500, H: int = 30) -> Workload:
+    """Ball on a tray held by the end effector: the paper-scale sampler and
+    update, no obstacles, the ball-centring cost with a weak position hold of
+    the end effector and no orientation term (the tray must tilt).  The ball
+    state (world frame) is a seeded point with a small velocity."""
+    rng = np.random.default_rng([seed, 17])
+    robot = make_robot(seed, 7)
+    world = make_world(seed, 0, 0)
+    p = Params(N=N, H=H, K=3, n_knots=6, dt=np.full(H, 0.02), beta=10.0, gamma=0.99,
+               alpha_mu=1.0, alpha_sigma=0.5, sigma_init=0.5, sigma_min=0.1, n_null=2,
+               w_pos=20.0, w_rot=0.0, w_stop=10.0, w_joint=100.0, w_manip=0.0,
+               w_coll=1000.0, w_smooth=0.0, w_ball=200.0, gravity=(0.0, 0.0, -9.81),
+               tray_center=(0.0, 0.0, 0.0), seed=4000 + seed)
+    ball = np.concatenate([rng.uniform([-0.5, -0.5, 0.2], [0.5, 0.5, 0.8]), rng.uniform(-0.1, 0.1, 3)])
+    return Workload(f"storm_ball_{N}x{H}_7dof", robot, world, p, make_state(seed, 7), make_goal(seed),
+                    ball)
 
 
 def config_batch(seed: int = 0, count: int = 256) -> list:

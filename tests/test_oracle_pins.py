@@ -533,7 +533,8 @@ def test_rollout_stage_consistency():
         for h in (0, 17, 29):
             assert np.allclose(out["ee"][n, h], o.fk(th[h])[-1][:3])
     w = np.array([wl.params.w_pos, wl.params.w_rot, wl.params.w_stop, wl.params.w_joint,
-                  wl.params.w_manip, wl.params.w_coll, wl.params.w_coll, wl.params.w_smooth])
+                  wl.params.w_manip, wl.params.w_coll, wl.params.w_coll, wl.params.w_smooth,
+                  wl.params.w_ee_vel, wl.params.w_ee_acc, wl.params.w_ball])
     assert np.allclose(out["terms"] @ w, out["cost"], rtol=1e-13)
 
 
