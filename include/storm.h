@@ -49,7 +49,9 @@ extern "C" {
 #define STORM_MAX_PAIRS 2048
 #define STORM_MAX_OBSTACLES 64 /* per kind: boxes, spheres */
 #define STORM_MAX_N 16384
-#define STORM_NTERMS 8
+/* Cost terms reported per (particle, step): pos, rot, stop, joint, manip, self,
+ * world, smooth, ee speed, ee acceleration, ball. */
+#define STORM_NTERMS 11
 
 typedef struct storm_handle storm_handle;
 
@@ -66,6 +68,7 @@ enum storm_status {
 
 enum storm_sampler { STORM_SAMPLER_PHILOX = 0, STORM_SAMPLER_HALTON = 1 };
 enum storm_rot_mode { STORM_ROT_QUAT = 0, STORM_ROT_FROBENIUS = 1 };
+enum storm_filter { STORM_FILTER_DEFAULT = 0, STORM_FILTER_COMB = 1, STORM_FILTER_MIXED = 2 };
 
 /* Serial revolute chain in modified Denavit-Hartenberg form (Craig), with link
  * spheres for collision (Sec. 3.1 kinematic model, Eq. 8; Eqs. 13-14 with the
@@ -113,8 +116,30 @@ typedef struct {
     double qdd_max;           /* max acceleration of the stop cost (Eq. 10) */
     uint64_t seed;            /* Philox key */
     uint32_t instance;        /* Philox stream id (< 2^24) */
-    int grad_steps;           /* gradient refinement steps after the K iterations (0..64) */
+    int grad_steps;           /* gradient refinement steps after the K iterations (0..64);
+                                 requires the default filter and w_ee_vel = w_ee_acc = w_ball = 0 */
     double grad_eta;          /* their step size: mu <- mu - grad_eta * dJ/dmu */
+    /* Noise smoothing along the horizon (Sec. 4.3), storm_filter:
+     *   STORM_FILTER_DEFAULT  cubic B-spline through n_knots samples when n_knots > 0, else
+     *                         one raw sample per step;
+     *   STORM_FILTER_COMB     one sample per step through the comb filter
+     *                         y_h = comb[0] e_h + comb[1] y_{h-1} + comb[2] y_{h-2} (y_{<0} = 0);
+     *   STORM_FILTER_MIXED    one sample per step; the first round(mix_bspline (N - n_null))
+     *                         non-null particles take the B-spline through their first
+     *                         n_knots samples (n_knots >= 4 required), the rest the comb. */
+    int filter;
+    double comb[3];
+    double mix_bspline;       /* in [0, 1] */
+    /* Task-space limits on Eq. 8's end-effector linear speed |X_dot| and acceleration
+     * |X_ddot| (theta_ddot = u): terms max(0, |.| - max), weights >= 0.  Added terms. */
+    double w_ee_vel, w_ee_acc, ee_vel_max, ee_acc_max;
+    /* Ball on a tray held by the end effector (appendix, ball balancing): the ball's
+     * in-plane distance from tray_center (end-effector frame) along the horizon, the
+     * ball rolling under the in-plane part of gravity (world frame).  The ball state
+     * is an input of each step (storm_set_ball); batches take w_ball = 0. */
+    double w_ball;
+    double gravity[3];
+    double tray_center[3];
 } storm_params;
 
 typedef struct {
@@ -226,6 +251,19 @@ int storm_set_world(storm_handle* h, const storm_world* world);
 /* Batched forward kinematics (Eq. 8) on device buffers: theta_dev (count x dof)
  * -> ee_dev (count x 12, row-major [R | p]).  Enqueued (no wait). */
 int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count, float* ee_dev);
+
+/* Batched end-effector velocity and acceleration (Eq. 8) on device buffers:
+ * theta, theta_dot, theta_ddot (count x dof each) -> xd_dev, xdd_dev (count x 6,
+ * [linear; angular] at the end-effector point, world frame).  Enqueued (no
+ * wait). */
+int storm_ee_twist(storm_handle* h, const float* theta_dev, const float* theta_dot_dev,
+                   const float* theta_ddot_dev, int count, float* xd_dev, float* xdd_dev);
+
+/* Ball state for the next steps (ball-on-tray cost): position and velocity in
+ * the world frame (host, 6 floats), as measured at the current robot state.
+ * Copied on the handle's stream, ordered with the steps.  Errors: INVALID_ARG
+ * for NULL or non-finite values. */
+int storm_set_ball(storm_handle* h, const float* ball_pos_vel);
 
 /* ---------------------------------------------------------------- launch shape */
 

@@ -15,8 +15,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libstorm_b300.so")
-_SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("storm.cu", "storm_device.cuh")] + \
-    [os.path.join(_ROOT, "include", "storm.h")]
+_SOURCES = [os.path.join(_HERE, "csrc", f) for f in sorted(os.listdir(os.path.join(_HERE, "csrc")))
+            if f.endswith((".cu", ".cuh"))] + [os.path.join(_ROOT, "include", "storm.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
@@ -31,7 +31,7 @@ STORM_ERR_TIMEOUT = -5
 STORM_ERR_STATE = -6
 STORM_MAP_CTA = 0
 STORM_MAP_WARP = 1
-NTERMS = 8
+NTERMS = 11
 
 EXPORTED = [
     "storm_create", "storm_destroy", "storm_status_string", "storm_last_error", "storm_reset",
@@ -39,6 +39,7 @@ EXPORTED = [
     "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
     "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
     "storm_set_state", "storm_rollout_costs_noalloc", "storm_set_launch", "storm_get_launch", "storm_set_launch_warp", "storm_get_launch_mapping",
+    "storm_ee_twist", "storm_set_ball",
     "storm_autotune", "storm_cost_grad", "storm_batch_create", "storm_batch_destroy",
     "storm_batch_last_error", "storm_batch_sizes", "storm_batch_step", "storm_batch_step_resident",
     "storm_batch_device_io", "storm_batch_sync", "storm_batch_get_distribution",
@@ -89,7 +90,10 @@ class storm_params(C.Structure):
                 ("pos_axis_w", C.c_double * 3), ("rot_axis_w", C.c_double * 3),
                 ("rot_mode", C.c_int), ("k_jl", C.c_double), ("k_m", C.c_double),
                 ("qdd_max", C.c_double), ("seed", C.c_uint64), ("instance", C.c_uint32),
-                ("grad_steps", C.c_int), ("grad_eta", C.c_double)]
+                ("grad_steps", C.c_int), ("grad_eta", C.c_double), ("filter", C.c_int),
+                ("comb", C.c_double * 3), ("mix_bspline", C.c_double), ("w_ee_vel", C.c_double),
+                ("w_ee_acc", C.c_double), ("ee_vel_max", C.c_double), ("ee_acc_max", C.c_double),
+                ("w_ball", C.c_double), ("gravity", C.c_double * 3), ("tray_center", C.c_double * 3)]
 
 
 class storm_step_info(C.Structure):
@@ -135,6 +139,8 @@ def lib():
         L.storm_set_launch.argtypes = [vp, C.c_int, C.c_int]
         L.storm_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.storm_set_launch_warp.argtypes = [vp, C.c_int]
+        L.storm_ee_twist.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp]
+        L.storm_set_ball.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_get_launch_mapping.argtypes = [vp]
         L.storm_autotune.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_cost_grad.argtypes = [vp, vp, vp, vp, C.c_uint32, C.c_int, vp, vp, vp]
@@ -242,6 +248,13 @@ class _Marshal:
         s.rot_mode, s.k_jl, s.k_m, s.qdd_max = p.rot_mode, p.k_jl, p.k_m, p.qdd_max
         s.seed, s.instance = int(p.seed), int(p.instance)
         s.grad_steps, s.grad_eta = int(p.grad_steps), float(p.grad_eta)
+        s.filter, s.mix_bspline = int(p.filter), float(p.mix_bspline)
+        s.comb[:] = [float(c) for c in p.comb]
+        s.w_ee_vel, s.w_ee_acc = float(p.w_ee_vel), float(p.w_ee_acc)
+        s.ee_vel_max, s.ee_acc_max = float(p.ee_vel_max), float(p.ee_acc_max)
+        s.w_ball = float(p.w_ball)
+        s.gravity[:] = [float(g) for g in p.gravity]
+        s.tray_center[:] = [float(c) for c in p.tray_center]
         return s
 
 
@@ -423,6 +436,22 @@ class Controller:
             self._check(m)
         return "warp" if m == STORM_MAP_WARP else "cta"
 
+    def ee_twist(self, theta_dev, theta_dot_dev, theta_ddot_dev):
+        """(X_dot, X_ddot) of Eq. 8 for count configurations: two count x 6 tensors."""
+        n = theta_dev.shape[0]
+        xd, xdd = self._empty(n, 6), self._empty(n, 6)
+        self._join()
+        self._check(lib().storm_ee_twist(self.h, _dptr(theta_dev.contiguous()), _dptr(theta_dot_dev.contiguous()),
+                                         _dptr(theta_ddot_dev.contiguous()), int(n), _dptr(xd), _dptr(xdd)))
+        self.stream.synchronize()
+        return xd, xdd
+
+    def set_ball(self, pos, vel):
+        """Ball position and velocity (world frame) for the next steps."""
+        b = np.ascontiguousarray(np.concatenate([np.ravel(pos), np.ravel(vel)]), dtype=np.float32)
+        assert b.shape == (6,)
+        self._check(lib().storm_set_ball(self.h, b.ctypes.data_as(C.POINTER(C.c_float))))
+
     def set_trace(self, trace_dev):
         """trace_dev: int64 CUDA tensor of 7 entries (phase stamps in ns) or None."""
         self._check(lib().storm_set_trace(self.h, _dptr(trace_dev)))
@@ -595,14 +624,6 @@ class BatchController:
         t = C.c_float()
         self._check(lib().storm_batch_autotune(self.h, C.byref(t)))
         return t.value
-
-    def set_trace(self, trace_dev):
-        """trace_dev: int64 CUDA tensor of 7 entries (phase stamps in ns) or None."""
-        self._check(lib().storm_set_trace(self.h, _dptr(trace_dev)))
-        self._trace = trace_dev
-
-    def set_broadphase(self, on: bool):
-        self._check(lib().storm_set_broadphase(self.h, int(bool(on))))
 
     def get_launch(self):
         a, b = C.c_int(), C.c_int()

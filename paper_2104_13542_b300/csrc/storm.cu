@@ -29,7 +29,7 @@ using namespace storm;
 
 struct RolloutLayout {
     int tab, frame, boxlh;                                  // 16-byte arrays
-    int mu, sigma, eps, u, th, thd, part, dself, dworld, goal, state;  // float arrays
+    int mu, sigma, eps, u, th, thd, part, dself, dworld, goal, state, ba, ball0;  // float arrays
     int slink;                                              // int arrays
     int bytes;
 };
@@ -62,6 +62,8 @@ __host__ __device__ inline RolloutLayout rollout_layout(const Problem& pb)
     L.dworld = take_(off, I * 4);
     L.goal = take_(off, 12 * 4);
     L.state = take_(off, 3 * pb.d * 4);
+    L.ba = take_(off, I * 2 * 4);   // ball: in-plane gravity per item
+    L.ball0 = take_(off, 4 * 4);    // ball: initial in-plane state
     L.slink = take_(off, pb.M * 4);
     L.bytes = off;
     return L;
@@ -200,17 +202,24 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         for (int i = tid; i < np * per; i += nt) s_eps[i] = pb.halton[static_cast<size_t>(n0) * per + i];
     }
     __syncthreads();
+    if (pb.filter != STORM_FILTER_DEFAULT) {  // comb-filtered particles, one sample per step (S = H)
+        for (int t = tid; t < np * d; t += nt) {
+            const int p = t / d, j = t - p * d;
+            if (smoothing_of(pb, n0 + p) == 2) comb_column(s_eps + p * S * d + j, H, d, pb.comb);
+        }
+        __syncthreads();
+    }
     trace_stamp(pb.trace, 1);
 
     // ---- controls u = mu + sigma o (B eps), null particles zero
     for (int i = tid; i < np * HD; i += nt) {
         const int p = i / HD, r = i - p * HD, h = r / d, j = r - h * d;
         float e;
-        if (pb.spline) {
+        if (smoothing_of(pb, n0 + p) == 1) {
             e = 0.f;
-            for (int s = 0; s < S; ++s) e = fmaf(s_basis[h * S + s], s_eps[(p * S + s) * d + j], e);
+            for (int s = 0; s < pb.nk; ++s) e = fmaf(s_basis[h * pb.nk + s], s_eps[(p * S + s) * d + j], e);
         } else {
-            e = s_eps[(p * H + h) * d + j];
+            e = s_eps[(p * S + h) * d + j];
         }
         const float uu = (n0 + p < pb.n_null) ? 0.f : fmaf(s_sigma[j], e, s_mu[h * d + j]);
         s_u[i] = uu;
@@ -240,6 +249,11 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     if (front_only) return;  // joint states only (surrogate input)
 
     // ---- per (particle, step): FK frames, Jacobian, non-collision costs
+    const bool want_ee = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms;
+    const bool ball_on = pb.ball && pb.w_ball != 0.f;
+    float* s_ba = reinterpret_cast<float*>(smem + L.ba);
+    float4* s_ball0 = reinterpret_cast<float4*>(smem + L.ball0);
+    if (ball_on && tid == 0) *s_ball0 = ball_initial(s_dhx, d, s_state, pb.ball);
     for (int item = tid; item < I; item += nt) {
         const int p = item / H, h = item - p * H;
         const float* th = s_th + (p * H + h) * d;
@@ -307,8 +321,36 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         c_stop = sqrtf(c_stop);
         c_joint = sqrtf(c_joint);
         // (manipulability, Eq. 12, is added in the collision phase)
-        s_part[item] = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop +
-                       pb.w_joint * c_joint + pb.w_smooth * c_smooth;
+        float part = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop + pb.w_joint * c_joint +
+                     pb.w_smooth * c_smooth;
+        float2 c_ee = make_float2(0.f, 0.f);
+        if (want_ee) {  // task-space limits on X_dot, X_ddot (Eq. 8), theta_ddot = u
+            float zc[kMaxDof][3], oc[kMaxDof][3];  // joint axes and origins, from the frames
+#pragma unroll
+            for (int i = 0; i < kMaxDof; ++i) {
+                if (i < d) {
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        const float4 row = fr[(i + 1) * 3 + r];
+                        zc[i][r] = row.z;
+                        oc[i][r] = row.w;
+                    }
+                } else {
+                    zc[i][0] = zc[i][1] = zc[i][2] = oc[i][0] = oc[i][1] = oc[i][2] = 0.f;
+                }
+            }
+            float xd[6], xdd[6];
+            ee_twist(zc, oc, pp, thd, uh, d, xd, xdd);
+            c_ee = ee_limit_terms(pb, xd, xdd);
+            if (pb.w_ee_vel != 0.f) part = fmaf(pb.w_ee_vel, c_ee.x, part);
+            if (pb.w_ee_acc != 0.f) part = fmaf(pb.w_ee_acc, c_ee.y, part);
+        }
+        if (ball_on) {
+            const float2 a = ball_accel(R, pb.grav);
+            s_ba[2 * item] = a.x;
+            s_ba[2 * item + 1] = a.y;
+        }
+        s_part[item] = part;
         s_dself[item] = 0.f;
         s_dworld[item] = 0.f;
         const size_t g = static_cast<size_t>(n0) * H + item;
@@ -329,6 +371,9 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
             t[2] = c_stop;
             t[3] = c_joint;
             t[7] = c_smooth;
+            t[8] = c_ee.x;
+            t[9] = c_ee.y;
+            t[10] = 0.f;
         }
     }
     __syncthreads();
@@ -549,13 +594,21 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         const float c = s_part[item] + pb.w_coll * (s_dself[item] + s_dworld[item]);
         s_part[item] = c;
         const size_t g = static_cast<size_t>(n0) * H + item;
-        if (out.cost) out.cost[g] = c;
         if (out.terms) {
             out.terms[g * STORM_NTERMS + 5] = s_dself[item];
             out.terms[g * STORM_NTERMS + 6] = s_dworld[item];
         }
     }
     __syncthreads();
+    if (ball_on) {  // the ball along each particle's horizon
+        for (int p = tid; p < np; p += nt)
+            ball_scan(pb, *s_ball0, s_ba + 2 * p * H, s_dt, s_part + p * H,
+                      out.terms ? out.terms + (static_cast<size_t>(n0 + p) * H) * STORM_NTERMS + 10 : nullptr,
+                      STORM_NTERMS);
+        __syncthreads();
+    }
+    if (out.cost)
+        for (int item = tid; item < I; item += nt) out.cost[static_cast<size_t>(n0) * H + item] = s_part[item];
     // ---- discounted total (Eq. 2)
     for (int p = tid; p < np; p += nt) {
         float C = 0.f;
@@ -883,6 +936,40 @@ __global__ void k_fk(Problem pb, const float* __restrict__ theta, int count, flo
     }
 }
 
+// End-effector velocity and acceleration (Eq. 8) of count configurations.
+__global__ void k_ee_twist(Problem pb, const float* __restrict__ theta, const float* __restrict__ theta_dot,
+                           const float* __restrict__ theta_ddot, int count, float* __restrict__ xd_out,
+                           float* __restrict__ xdd_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int d = pb.d;
+    const size_t o = static_cast<size_t>(i) * d;
+    float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    float p[3] = {0.f, 0.f, 0.f};
+    float zc[kMaxDof][3], oc[kMaxDof][3], thd[kMaxDof], thdd[kMaxDof];
+#pragma unroll
+    for (int j = 0; j < kMaxDof; ++j) {
+        if (j < d) {
+            const float* dh = pb.dhx + j * 8;
+            dh_step(R, p, dh[0], dh[1], dh[2], dh[3], theta[o + j] + dh[4]);
+            zc[j][0] = R[2], zc[j][1] = R[5], zc[j][2] = R[8];
+            oc[j][0] = p[0], oc[j][1] = p[1], oc[j][2] = p[2];
+            thd[j] = theta_dot[o + j];
+            thdd[j] = theta_ddot[o + j];
+        } else {
+            zc[j][0] = zc[j][1] = zc[j][2] = oc[j][0] = oc[j][1] = oc[j][2] = thd[j] = thdd[j] = 0.f;
+        }
+    }
+    float xd[6], xdd[6];
+    ee_twist(zc, oc, p, thd, thdd, d, xd, xdd);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        xd_out[static_cast<size_t>(i) * 6 + k] = xd[k];
+        xdd_out[static_cast<size_t>(i) * 6 + k] = xdd[k];
+    }
+}
+
 // ---------------------------------------------------------------- set-up tables
 
 __device__ double clamped_knot(int i, int S)
@@ -949,9 +1036,9 @@ __global__ void k_init_tables(Problem pb, InitArgs a)
         double rest = 0.0;  // (S_u(1) qdd_max dt)_h
         for (int k = pb.H - 1; k >= h; --k) rest += a.dt[k];
         const_cast<float*>(pb.vmax)[h] = static_cast<float>(a.qdd_max * rest);
-        if (pb.spline) {
+        if (pb.nk > 0) {
             const double x = pb.H > 1 ? static_cast<double>(h) / (pb.H - 1) : 0.0;
-            bspline_row(pb.S, x, const_cast<float*>(pb.basis) + h * pb.S);
+            bspline_row(pb.nk, x, const_cast<float*>(pb.basis) + h * pb.nk);
         }
     }
 }
@@ -1343,6 +1430,8 @@ struct storm_handle {
     MlpBuffers* mlp_buf = nullptr;   // its inference activations for N x H rows
     float* d_theta = nullptr;        // N x H x d joint states for the surrogate
     float* d_pred = nullptr;         // N x H (padded) predicted self distances
+    float* d_ball = nullptr;         // 8: ball position, velocity (world frame), padding
+    float h_ball[8] = {};
     size_t adjoint_smem = 0;
     int grad_steps = 0;
     float grad_eta = 0.f;
@@ -1384,6 +1473,29 @@ bool finite_all(const double* p, int n)
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return false;
     return true;
+}
+
+// Sampler, end-effector-limit and ball fields of the problem block.
+void fill_sampling(const storm_params* p, Problem& pb)
+{
+    pb.filter = p->filter;
+    pb.nk = (p->filter != STORM_FILTER_COMB && p->n_knots > 0) ? p->n_knots : 0;
+    pb.spline = pb.nk > 0;  // a basis table exists
+    pb.S = (p->filter == STORM_FILTER_DEFAULT && pb.nk > 0) ? pb.nk : p->H;
+    pb.n_bs = p->filter == STORM_FILTER_MIXED
+                  ? static_cast<int>(std::floor(p->mix_bspline * (p->N - p->n_null) + 0.5))
+                  : 0;
+    for (int i = 0; i < 3; ++i) {
+        pb.comb[i] = static_cast<float>(p->comb[i]);
+        pb.grav[i] = static_cast<float>(p->gravity[i]);
+        pb.tray[i] = static_cast<float>(p->tray_center[i]);
+    }
+    pb.w_ee_vel = static_cast<float>(p->w_ee_vel);
+    pb.w_ee_acc = static_cast<float>(p->w_ee_acc);
+    pb.ee_vel_max = static_cast<float>(p->ee_vel_max);
+    pb.ee_acc_max = static_cast<float>(p->ee_acc_max);
+    pb.w_ball = static_cast<float>(p->w_ball);
+    pb.ball = nullptr;
 }
 
 int validate(const storm_robot* r, const storm_world* w, const storm_params* p, std::string& msg)
@@ -1433,6 +1545,21 @@ int validate(const storm_robot* r, const storm_world* w, const storm_params* p, 
     if (p->grad_steps < 0 || p->grad_steps > 64 || p->K + p->grad_steps > 256 ||
         !std::isfinite(p->grad_eta))
         return msg = "bad grad_steps / grad_eta", STORM_ERR_INVALID_ARG;
+    if (p->filter != STORM_FILTER_DEFAULT && p->filter != STORM_FILTER_COMB && p->filter != STORM_FILTER_MIXED)
+        return msg = "bad filter", STORM_ERR_INVALID_ARG;
+    if (p->filter == STORM_FILTER_MIXED && p->n_knots < 4)
+        return msg = "the mixed filter needs n_knots >= 4", STORM_ERR_INVALID_ARG;
+    if (!finite_all(p->comb, 3) || !(p->mix_bspline >= 0.0 && p->mix_bspline <= 1.0))
+        return msg = "bad comb coefficients / mix_bspline", STORM_ERR_INVALID_ARG;
+    if (!(p->w_ee_vel >= 0) || !(p->w_ee_acc >= 0) || !(p->ee_vel_max >= 0) || !(p->ee_acc_max >= 0) ||
+        !std::isfinite(p->w_ee_vel + p->w_ee_acc + p->ee_vel_max + p->ee_acc_max))
+        return msg = "bad end-effector limits", STORM_ERR_INVALID_ARG;
+    if (!std::isfinite(p->w_ball) || !finite_all(p->gravity, 3) || !finite_all(p->tray_center, 3))
+        return msg = "bad ball parameters", STORM_ERR_INVALID_ARG;
+    if (p->grad_steps > 0 &&
+        (p->filter != STORM_FILTER_DEFAULT || p->w_ee_vel != 0 || p->w_ee_acc != 0 || p->w_ball != 0))
+        return msg = "gradient refinement needs the default filter and no ee / ball terms",
+               STORM_ERR_INVALID_ARG;
     return STORM_OK;
 }
 
@@ -1464,7 +1591,7 @@ TablePlan plan_tables(const Problem& pb, int cap_boxes, int cap_wsph, int raw_do
     t.dt = take(pb.H * 4);
     t.gpow = take(pb.H * 4);
     t.vmax = take(pb.H * 4);
-    t.basis = take(pb.spline ? pb.H * pb.S * 4 : 4);
+    t.basis = take(pb.nk > 0 ? pb.H * pb.nk * 4 : 4);
     t.prefix = off;  // dhx .. basis: what every rollout CTA copies to shared memory
     t.mu = take(pb.H * pb.d * 4);
     t.sigma = take(pb.d * 4);
@@ -1647,6 +1774,7 @@ void free_all(storm_handle* h)
     if (h->d_adj) cudaFree(h->d_adj);
     if (h->d_theta) cudaFree(h->d_theta);
     if (h->d_pred) cudaFree(h->d_pred);
+    if (h->d_ball) cudaFree(h->d_ball);
     if (h->mlp_buf) {
         mlp_free_buffers(*h->mlp_buf);
         delete h->mlp_buf;
@@ -1705,8 +1833,7 @@ void fill_problem(const storm_robot* r, const storm_world* w, const storm_params
     pb.N = p->N;
     pb.H = p->H;
     pb.d = r->dof;
-    pb.spline = p->n_knots > 0;
-    pb.S = pb.spline ? p->n_knots : p->H;
+    fill_sampling(p, pb);
     pb.sampler = p->sampler;
     pb.n_null = p->n_null;
     pb.rot_mode = p->rot_mode;
@@ -1894,6 +2021,9 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     CK(cudaMalloc(&h->d_tables, t.total));
     CK(cudaMalloc(&h->d_u, sizeof(float) * size_t(pb.N) * pb.H * pb.d));
     CK(cudaMalloc(&h->d_C, sizeof(float) * pb.N));
+    CK(cudaMalloc(&h->d_ball, sizeof(float) * 8));
+    CK(cudaMemsetAsync(h->d_ball, 0, sizeof(float) * 8, h->stream));
+    pb.ball = h->d_ball;  // the ball state of storm_set_ball (zero until set)
     CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
     CK(cudaMallocHost(&h->h_io, sizeof(float) * io_floats(pb)));
     CK(cudaMalloc(&h->d_upd, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d));
@@ -2082,6 +2212,9 @@ int storm_cost_grad(storm_handle* h, const float* state_dev, const float* goal_d
     if (!h || !state_dev || !goal_dev || !mean_dev || !grad_dev || !J_dev)
         return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
     if (iter < 0 || iter > 255 || step > 0x7fffffffu) return fail(h, STORM_ERR_INVALID_ARG, "bad iter/step");
+    if (h->pb.filter != STORM_FILTER_DEFAULT || h->pb.w_ee_vel != 0.f || h->pb.w_ee_acc != 0.f ||
+        h->pb.w_ball != 0.f)
+        return fail(h, STORM_ERR_INVALID_ARG, "the adjoint needs the default filter and no ee / ball terms");
     return launch_adjoint(h, h->stream, state_dev, goal_dev, mean_dev, static_cast<int>(step), iter,
                           grad_dev, J_dev, Ctot_dev, 0.f, nullptr, 0);
 }
@@ -2149,6 +2282,30 @@ int storm_forward_kinematics(storm_handle* h, const float* theta_dev, int count,
     if (count == 0) return STORM_OK;
     k_fk<<<(count + 127) / 128, 128, 0, h->stream>>>(h->pb, theta_dev, count, ee_dev);
     CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+int storm_ee_twist(storm_handle* h, const float* theta_dev, const float* theta_dot_dev,
+                   const float* theta_ddot_dev, int count, float* xd_dev, float* xdd_dev)
+{
+    if (!h || count < 0 ||
+        (count > 0 && (!theta_dev || !theta_dot_dev || !theta_ddot_dev || !xd_dev || !xdd_dev)))
+        return fail(h, STORM_ERR_INVALID_ARG, "bad argument");
+    if (count == 0) return STORM_OK;
+    k_ee_twist<<<(count + 127) / 128, 128, 0, h->stream>>>(h->pb, theta_dev, theta_dot_dev, theta_ddot_dev, count,
+                                                          xd_dev, xdd_dev);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
+int storm_set_ball(storm_handle* h, const float* ball)
+{
+    if (!h || !ball) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(ball[i])) return fail(h, STORM_ERR_INVALID_ARG, "non-finite ball state");
+    std::memcpy(h->h_ball, ball, sizeof(float) * 6);
+    CK(cudaMemcpyAsync(h->d_ball, h->h_ball, sizeof(float) * 6, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return STORM_OK;
 }
 
@@ -2423,8 +2580,7 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
     pb.N = p->N;
     pb.H = p->H;
     pb.d = r->dof;
-    pb.spline = p->n_knots > 0;
-    pb.S = pb.spline ? p->n_knots : p->H;
+    fill_sampling(p, pb);
     pb.sampler = p->sampler;
     pb.n_null = p->n_null;
     pb.rot_mode = p->rot_mode;
@@ -2831,7 +2987,11 @@ int storm_batch_create(int count, const storm_robot* robots, const storm_world* 
         return STORM_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i) {
         std::string msg;
-        const int v = validate(robots + i, worlds + i, params + i, msg);
+        int v = validate(robots + i, worlds + i, params + i, msg);
+        if (!v && params[i].w_ball != 0.0) {
+            msg = "batched instances take no ball term (w_ball = 0)";
+            v = STORM_ERR_INVALID_ARG;
+        }
         if (v) {
             fprintf(stderr, "storm_batch_create: instance %d: %s\n", i, msg.c_str());
             return v;

@@ -8,6 +8,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "storm.h"
+
 namespace storm {
 
 constexpr int kMaxDof = 7;
@@ -61,6 +63,16 @@ struct Problem {
     // pair blocks of frames (la, lb), la < lb, are [lp_begin[t], lp_begin[t + 1]) with
     // t = link_pair_index(la, lb); the blocks are sorted by (la, lb)
     uint16_t lp_begin[kLinkPairs + 1];
+    // noise smoothing (Sec. 4.3)
+    int filter;              // STORM_FILTER_*
+    int nk;                  // B-spline knots (basis columns); the basis is H x nk
+    int n_bs;                // mixed filter: particles [n_null, n_null + n_bs) take the B-spline
+    float comb[3];           // comb-filter coefficients
+    // task-space limits on the end-effector speed and acceleration (Eq. 8)
+    float w_ee_vel, w_ee_acc, ee_vel_max, ee_acc_max;
+    // ball on a tray
+    float w_ball, grav[3], tray[3];
+    const float* ball;       // 6: ball position, velocity (world frame); nullable: no ball
 };
 
 // Step bookkeeping kept on the device so captured graphs need no host update.
@@ -203,5 +215,139 @@ struct GramFactor {
         return fabsf(m);
     }
 };
+
+// ---------------------------------------------------------------- samplers (Sec. 4.3)
+// Smoothing of particle n's noise: 0 raw samples, 1 cubic B-spline, 2 comb filter.
+__device__ __forceinline__ int smoothing_of(const Problem& pb, int n)
+{
+    if (pb.filter == STORM_FILTER_COMB) return 2;
+    if (pb.filter == STORM_FILTER_MIXED) return (n >= pb.n_null && n < pb.n_null + pb.n_bs) ? 1 : 2;
+    return pb.nk > 0 ? 1 : 0;
+}
+
+// Comb filter of one (particle, joint) noise column in place, e[h * stride],
+// h = 0..H-1: y_h = c0 e_h + c1 y_{h-1} + c2 y_{h-2}, zero before h = 0.
+__device__ __forceinline__ void comb_column(float* e, int H, int stride, const float (&c)[3])
+{
+    float y1 = 0.f, y2 = 0.f;
+    for (int h = 0; h < H; ++h) {
+        const float y = fmaf(c[0], e[h * stride], fmaf(c[1], y1, c[2] * y2));
+        e[h * stride] = y;
+        y2 = y1;
+        y1 = y;
+    }
+}
+
+// ---------------------------------------------------------------- Eq. 8 twist
+__device__ __forceinline__ void cross3(const float* a, const float* b, float* c)
+{
+    c[0] = fmaf(a[1], b[2], -a[2] * b[1]);
+    c[1] = fmaf(a[2], b[0], -a[0] * b[2]);
+    c[2] = fmaf(a[0], b[1], -a[1] * b[0]);
+}
+
+// End-effector velocity and acceleration, [linear; angular] at the end-effector
+// point p, from the joint axes z[c] and origins o[c] (world frame):
+// X_dot = sum_c theta_dot_c [z_c x (p - o_c); z_c] and X_ddot = J_dot theta_dot +
+// J theta_ddot.  Joint by joint, w is the angular velocity of the link before
+// joint c and v_o the velocity of o_c (v_o += w x (o_c - o_{c-1})); then
+// z_c_dot = w x z_c and column c of J_dot is [z_c_dot x (p - o_c) + z_c x
+// (p_dot - v_o); z_c_dot].
+__device__ __forceinline__ void ee_twist(const float (&z)[kMaxDof][3], const float (&o)[kMaxDof][3],
+                                         const float (&p)[3], const float* thd, const float* thdd, int d,
+                                         float (&xd)[6], float (&xdd)[6])
+{
+    float zr[kMaxDof][3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xd[k] = xdd[k] = 0.f;
+#pragma unroll
+    for (int c = 0; c < kMaxDof; ++c) {
+        if (c < d) {
+            const float r[3] = {p[0] - o[c][0], p[1] - o[c][1], p[2] - o[c][2]};
+            cross3(z[c], r, zr[c]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xd[a] = fmaf(thd[c], zr[c][a], xd[a]);
+                xd[3 + a] = fmaf(thd[c], z[c][a], xd[3 + a]);
+            }
+        }
+    }
+    float w[3] = {0.f, 0.f, 0.f}, vo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < kMaxDof; ++c) {
+        if (c < d) {
+            if (c > 0) {
+                const float dd[3] = {o[c][0] - o[c - 1][0], o[c][1] - o[c - 1][1], o[c][2] - o[c - 1][2]};
+                float t[3];
+                cross3(w, dd, t);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) vo[a] += t[a];
+            }
+            float zd[3], t1[3], t2[3];
+            cross3(w, z[c], zd);
+            const float r[3] = {p[0] - o[c][0], p[1] - o[c][1], p[2] - o[c][2]};
+            const float q[3] = {xd[0] - vo[0], xd[1] - vo[1], xd[2] - vo[2]};
+            cross3(zd, r, t1);
+            cross3(z[c], q, t2);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xdd[a] = fmaf(thd[c], t1[a] + t2[a], fmaf(thdd[c], zr[c][a], xdd[a]));
+                xdd[3 + a] = fmaf(thd[c], zd[a], fmaf(thdd[c], z[c][a], xdd[3 + a]));
+                w[a] = fmaf(thd[c], z[c][a], w[a]);
+            }
+        }
+    }
+}
+
+// The two task-space limit terms: max(0, |v| - v_max), max(0, |a| - a_max).
+__device__ __forceinline__ float2 ee_limit_terms(const Problem& pb, const float (&xd)[6], const float (&xdd)[6])
+{
+    const float sp = sqrtf(fmaf(xd[0], xd[0], fmaf(xd[1], xd[1], xd[2] * xd[2])));
+    const float ac = sqrtf(fmaf(xdd[0], xdd[0], fmaf(xdd[1], xdd[1], xdd[2] * xdd[2])));
+    return make_float2(fmaxf(0.f, sp - pb.ee_vel_max), fmaxf(0.f, ac - pb.ee_acc_max));
+}
+
+// ---------------------------------------------------------------- ball on a tray
+// The ball's in-plane state in the end-effector frame at the current robot
+// state theta: x0 = R^T (b - p), v0 = R^T v_b -> (x0.x, x0.y, v0.x, v0.y).
+__device__ __forceinline__ float4 ball_initial(const float* dhx, int d, const float* theta, const float* ball)
+{
+    float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    float p[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < kMaxDof; ++i)
+        if (i < d) dh_step(R, p, dhx[i * 8], dhx[i * 8 + 1], dhx[i * 8 + 2], dhx[i * 8 + 3], theta[i] + dhx[i * 8 + 4]);
+    const float e[3] = {ball[0] - p[0], ball[1] - p[1], ball[2] - p[2]};
+    return make_float4(fmaf(R[0], e[0], fmaf(R[3], e[1], R[6] * e[2])),
+                       fmaf(R[1], e[0], fmaf(R[4], e[1], R[7] * e[2])),
+                       fmaf(R[0], ball[3], fmaf(R[3], ball[4], R[6] * ball[5])),
+                       fmaf(R[1], ball[3], fmaf(R[4], ball[4], R[7] * ball[5])));
+}
+
+// In-plane gravity in the end-effector frame of rotation R (row-major): (R^T g).xy.
+__device__ __forceinline__ float2 ball_accel(const float (&R)[9], const float (&g)[3])
+{
+    return make_float2(fmaf(R[0], g[0], fmaf(R[3], g[1], R[6] * g[2])),
+                       fmaf(R[1], g[0], fmaf(R[4], g[1], R[7] * g[2])));
+}
+
+// One particle's ball along the horizon (Eq. 7's semi-implicit recurrence on the
+// in-plane accelerations a[h * 2 .. +1]); c[h] += w_ball * |x_h - tray|, and the
+// unweighted term to term[h * term_stride] when term is not null.
+__device__ __forceinline__ void ball_scan(const Problem& pb, float4 s0, const float* a, const float* dt, float* c,
+                                          float* term, int term_stride)
+{
+    float vx = s0.z, vy = s0.w, x = s0.x, y = s0.y;
+    for (int h = 0; h < pb.H; ++h) {
+        vx = fmaf(dt[h], a[2 * h], vx);
+        vy = fmaf(dt[h], a[2 * h + 1], vy);
+        x = fmaf(dt[h], vx, x);
+        y = fmaf(dt[h], vy, y);
+        const float ex = x - pb.tray[0], ey = y - pb.tray[1];
+        const float cb = sqrtf(fmaf(ex, ex, ey * ey));
+        c[h] = fmaf(pb.w_ball, cb, c[h]);
+        if (term) term[static_cast<size_t>(h) * term_stride] = cb;
+    }
+}
 
 }  // namespace storm

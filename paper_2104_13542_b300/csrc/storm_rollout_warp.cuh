@@ -21,6 +21,7 @@ struct WarpPlan {
     int eps;         // PW x S x d noise
     int u, th, thd;  // PW x H x d controls and joint states
     int c;           // PW x H running costs
+    int ba;          // PW x H x 2 ball in-plane gravity
     int floats;      // size of one warp's region
 };
 
@@ -44,6 +45,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
     w.th = take(w.PW * pb.H * pb.d);
     w.thd = take(w.PW * pb.H * pb.d);
     w.c = take(w.PW * pb.H);
+    w.ba = take(w.PW * pb.H * 2);
     w.floats = off;
     return w;
 }
@@ -169,6 +171,13 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         for (int i = lane; i < np_w * per; i += 32) s_eps[i] = pb.halton[static_cast<size_t>(nw0) * per + i];
     }
     __syncwarp();
+    if (pb.filter != STORM_FILTER_DEFAULT) {  // comb-filtered particles, one sample per step (S = H)
+        if (lane < np_w * d) {
+            const int p = lane / d, j = lane - p * d;
+            if (smoothing_of(pb, nw0 + p) == 2) comb_column(s_eps + p * S * d + j, H, d, pb.comb);
+        }
+        __syncwarp();
+    }
     trace_stamp(pb.trace, 1);
 
     // ---- controls u = mu + sigma o (B eps) of the lane's own steps, null particles zero
@@ -178,11 +187,12 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         float e[kMaxDof];
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) e[j] = 0.f;
-        if (pb.spline) {
+        if (smoothing_of(pb, n) == 1) {
             const float* eps = s_eps + seg * S * d;
+            const int nk = pb.nk;
 #pragma unroll 2
-            for (int s = 0; s < S; ++s) {
-                const float b = pb.basis[h * S + s];
+            for (int s = 0; s < nk; ++s) {
+                const float b = pb.basis[h * nk + s];
 #pragma unroll
                 for (int j = 0; j < kMaxDof; ++j)
                     if (j < d) e[j] = fmaf(b, eps[s * d + j], e[j]);
@@ -190,7 +200,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         } else {
 #pragma unroll
             for (int j = 0; j < kMaxDof; ++j)
-                if (j < d) e[j] = s_eps[(seg * H + h) * d + j];
+                if (j < d) e[j] = s_eps[(seg * S + h) * d + j];
         }
         const bool null = n < pb.n_null;
         float* su = s_u + (seg * H + h) * d;
@@ -251,6 +261,9 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         g[11] = goal[2];
     }
     const bool want_manip = pb.w_manip != 0.f || out.terms;
+    const bool want_ee = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms;
+    const bool ball_on = pb.ball && pb.w_ball != 0.f;
+    float* s_ba = ws + W.ba;
     const float* pred = pb.self_pred;
     const int NO = pb.B + pb.O;
 
@@ -269,6 +282,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
         float pp[3] = {0.f, 0.f, 0.f};
         float J[6][kMaxDof];
+        float oc[kMaxDof][3];  // joint origins (Eq. 8; the axes are J's angular rows)
         float cbx[kMaxDof + 1], cby[kMaxDof + 1], cbz[kMaxDof + 1];
         {
             const float fr0[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
@@ -297,6 +311,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
                 J[3][i] = R[2];
                 J[4][i] = R[5];
                 J[5][i] = R[8];
+                oc[i][0] = pp[0], oc[i][1] = pp[1], oc[i][2] = pp[2];
                 const float4 lb = lbf[i + 1];
                 cbx[i + 1] = fmaf(R[0], lb.x, fmaf(R[1], lb.y, fmaf(R[2], lb.z, pp[0])));
                 cby[i + 1] = fmaf(R[3], lb.x, fmaf(R[4], lb.y, fmaf(R[5], lb.z, pp[1])));
@@ -304,6 +319,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
             } else {
 #pragma unroll
                 for (int r = 0; r < 6; ++r) J[r][i] = 0.f;
+                oc[i][0] = oc[i][1] = oc[i][2] = 0.f;
                 cbx[i + 1] = cby[i + 1] = cbz[i + 1] = 0.f;
             }
         }
@@ -360,6 +376,22 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         c_joint = sqrtf(c_joint);
         float part = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop + pb.w_joint * c_joint +
                      pb.w_smooth * c_smooth;
+        float2 c_ee = make_float2(0.f, 0.f);
+        if (want_ee) {  // task-space limits on X_dot, X_ddot (Eq. 8), theta_ddot = u
+            float zc[kMaxDof][3];
+#pragma unroll
+            for (int i = 0; i < kMaxDof; ++i) zc[i][0] = J[3][i], zc[i][1] = J[4][i], zc[i][2] = J[5][i];
+            float xd[6], xdd[6];
+            ee_twist(zc, oc, pp, thd, uh, d, xd, xdd);
+            c_ee = ee_limit_terms(pb, xd, xdd);
+            if (pb.w_ee_vel != 0.f) part = fmaf(pb.w_ee_vel, c_ee.x, part);
+            if (pb.w_ee_acc != 0.f) part = fmaf(pb.w_ee_acc, c_ee.y, part);
+        }
+        if (ball_on && valid) {
+            const float2 a = ball_accel(R, pb.grav);
+            s_ba[(pl * H + h) * 2] = a.x;
+            s_ba[(pl * H + h) * 2 + 1] = a.y;
+        }
         if (valid && out.ee) {
             float* e = out.ee + gi * 12;
 #pragma unroll
@@ -377,6 +409,9 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
             t[2] = c_stop;
             t[3] = c_joint;
             t[7] = c_smooth;
+            t[8] = c_ee.x;
+            t[9] = c_ee.y;
+            t[10] = 0.f;
         }
         // manipulability (Eq. 12)
         if (want_manip) {
@@ -590,7 +625,6 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         const float c = part + pb.w_coll * (dself + dworld);
         if (valid) {
             s_c[pl * H + h] = c;
-            if (out.cost) out.cost[gi] = c;
             if (out.terms) {
                 out.terms[gi * STORM_NTERMS + 5] = dself;
                 out.terms[gi * STORM_NTERMS + 6] = dworld;
@@ -598,6 +632,20 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         }
         __syncwarp();  // the next slot rewrites the frames
     }
+    if (ball_on) {  // the ball along each particle's horizon
+        if (lane < np_w) {
+            const float4 s0 = ball_initial(pb.dhx, d, state, pb.ball);
+            ball_scan(pb, s0, s_ba + lane * H * 2, pb.dt, s_c + lane * H,
+                      out.terms ? out.terms + (static_cast<size_t>(nw0 + lane) * H) * STORM_NTERMS + 10 : nullptr,
+                      STORM_NTERMS);
+        }
+        __syncwarp();
+    }
+    if (out.cost)
+        for (int slot = 0; slot < W.SL; ++slot) {
+            const int h = slot * Lp + hl;
+            if (pvalid && h < H) out.cost[static_cast<size_t>(n) * H + h] = s_c[seg * H + h];
+        }
     // ---- discounted total (Eq. 2), the k_rollout order
     if (lane < np_w) {
         float C = 0.f;

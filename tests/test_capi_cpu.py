@@ -65,6 +65,14 @@ def _structs(wl):
     lambda r, w, p: setattr(r, "n_pairs", 2049),
     lambda r, w, p: setattr(w, "n_boxes", 65),
     lambda r, w, p: setattr(p, "dt", None),
+    lambda r, w, p: setattr(p, "filter", 7),
+    lambda r, w, p: (setattr(p, "filter", 2), setattr(p, "n_knots", 0)),
+    lambda r, w, p: setattr(p, "mix_bspline", 1.5),
+    lambda r, w, p: setattr(p, "w_ee_vel", -1.0),
+    lambda r, w, p: setattr(p, "ee_acc_max", float("nan")),
+    lambda r, w, p: setattr(p, "w_ball", float("inf")),
+    lambda r, w, p: (setattr(p, "grad_steps", 2), setattr(p, "filter", 1)),
+    lambda r, w, p: (setattr(p, "grad_steps", 2), setattr(p, "w_ball", 1.0)),
 ])
 def test_create_rejects_bad_arguments(L, mutate):
     wl = W.config_paper(0, N=8, H=10)
@@ -116,6 +124,20 @@ def test_oracle_and_library_share_nothing():
     for py in ("binding.py", "__init__.py", "workloads.py"):
         src = open(os.path.join(ROOT, "paper_2104_13542_b300", py)).read()
         assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_batch_rejects_ball_term(L):
+    wls = [W.config_paper(0, N=8, H=10), W.config_ball(1, N=8, H=10)]
+    m = binding._Marshal()
+    R = (binding.storm_robot * 2)(*[m.robot(w.robot) for w in wls])
+    Wd = (binding.storm_world * 2)(*[m.world(w.world) for w in wls])
+    P = (binding.storm_params * 2)(*[m.params(w.params) for w in wls])
+    h = C.c_void_p()
+    L.storm_batch_create.argtypes = [C.c_int, C.POINTER(binding.storm_robot),
+                                     C.POINTER(binding.storm_world), C.POINTER(binding.storm_params),
+                                     C.c_void_p, C.POINTER(C.c_void_p)]
+    assert L.storm_batch_create(2, R, Wd, P, None, C.byref(h)) == binding.STORM_ERR_INVALID_ARG
+    assert h.value is None
 
 
 def test_batch_create_rejects_bad_instance(L):
