@@ -145,7 +145,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def goals_for(ctl, robot, seed: int, count: int):
+def goals_for(ctl, robot, seed: int, count: int, with_theta: bool = False):
     """Reachable goal poses X_g = FK(theta_g), theta_g ~ U[-2.24, 2.24] drawn until the
     configuration is at least 3 cm clear of self-collision (exact check of the library)."""
     import torch
@@ -163,7 +163,7 @@ def goals_for(ctl, robot, seed: int, count: int):
         y = math.copysign(math.sqrt(max(0.0, 1 - Rm[0, 0] + Rm[1, 1] - Rm[2, 2])) / 2, Rm[0, 2] - Rm[2, 0])
         z = math.copysign(math.sqrt(max(0.0, 1 - Rm[0, 0] - Rm[1, 1] + Rm[2, 2])) / 2, Rm[1, 0] - Rm[0, 1])
         goals.append(np.array([p[0], p[1], p[2], w, x, y, z], dtype=np.float32))
-    return goals
+    return (goals, th) if with_theta else goals
 
 
 def max_over_ranks(value: float, world_size: int, device: str = "cuda") -> float:
@@ -366,6 +366,19 @@ def run_variants(args, seed: int):
                 entry["grad_steps"] = p.grad_steps
                 entry["J_along_refinement"] = Js
             out[name] = entry
+    # the widened rows: variable-dt schedule with end-effector limits, mixed sampler, ball on a tray
+    for name, wl in (("vardt_ee_limits", W.config_variable_dt(seed)), ("mixed_sampler", W.config_mixed(seed)),
+                     ("ball_on_tray", W.config_ball(seed))):
+        p = wl.params
+        with Controller(wl.robot, wl.world, p) as c:
+            if wl.ball is not None:
+                c.set_ball(wl.ball[:3], wl.ball[3:])
+            c.step(wl.state.astype(np.float32), wl.goal.astype(np.float32))
+            for _ in range(3):
+                c.step_resident()
+            ms = _time_steps(c.step_resident, c.stream, flush, n)
+            out[name] = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99)),
+                         "rollout_steps_per_s": p.N * p.H * p.K * len(ms) / float(ms.sum() / 1e3)}
     # batched uneven instances
     wls = W.config_batch(seed, 256)
     with BatchController([w.robot for w in wls], [w.world for w in wls], [w.params for w in wls]) as b:
@@ -409,6 +422,90 @@ def run_variants(args, seed: int):
     out["surrogate_1000x30"].update(acc)
     net.close()
     return out
+
+
+def run_ablation(args):
+    """Closed-loop sampling ablation (the paper's pseudo-random vs Halton and comb
+    vs B-spline vs mixed studies, on the synthetic paper-scale workload): every
+    sampler x filter x particle count reaches the same goals from the same start
+    through the ideal double-integrator plant; reported per variant: position
+    and quaternion error (1 - |q . q_g|) averaged over the last 50 steps of each
+    goal, and the mean absolute joint jerk (smoothness)."""
+    import torch
+    from paper_2104_13542_b300 import Controller
+    base = W.config_paper(args.seed)
+    # pose reaching in free space with the paper's orientation-constrained weights
+    base.world = W.World(np.zeros((0, 6)), np.zeros((0, 4)))
+    base.params = base.params.replace(w_pos=100.0, w_rot=100.0)
+    goals = None
+    steps_per_goal = 400
+    out = {}
+    for N in (100, 500):
+        for sampler, sname in ((W.SAMPLER_PHILOX, "pseudo_random"), (W.SAMPLER_HALTON, "halton")):
+            for filt, fname in ((W.FILTER_COMB, "comb"), (W.FILTER_DEFAULT, "bspline"),
+                                (W.FILTER_MIXED, "mixed")):
+                p = base.params.replace(N=N, sampler=sampler, filter=filt, n_null=2)
+                with Controller(base.robot, base.world, p) as ctl:
+                    if goals is None:
+                        _, th = goals_for(ctl, base.robot, args.seed, 1, with_theta=True)
+                        start = th[0]  # a configuration clear of self-collision, at rest
+                        goals = _local_goals(ctl, start, args.seed, 3)
+                    state = np.zeros((3, base.robot.dof), np.float32)
+                    state[0] = start
+                    dt = float(p.dt[0])
+                    pos_e, rot_e, jerk, prev = [], [], [], None
+                    for goal in goals:
+                        for i in range(steps_per_goal):
+                            cmd, info, rc = ctl.step(state, goal)
+                            if prev is not None:
+                                jerk.append(float(np.abs(cmd - prev).mean() / dt))
+                            prev = cmd.copy()
+                            state[2] = cmd
+                            state[1] = state[1] + dt * cmd
+                            state[0] = state[0] + dt * state[1]
+                            if i >= steps_per_goal - 50:
+                                T = ctl.forward_kinematics(torch.as_tensor(state[0:1], device="cuda")).cpu().numpy()[0]
+                                pos_e.append(float(np.linalg.norm(T[:, 3] - goal[:3])))
+                                R = T[:, :3].astype(np.float64)
+                                tr = float(np.trace(_rot_from_quat(goal[3:]).T @ R))
+                                rot_e.append(1.0 - 0.5 * np.sqrt(max(0.0, 1.0 + tr)))
+                out[f"N{N}_{sname}_{fname}"] = {"pos_err_m": float(np.mean(pos_e)),
+                                                "quat_err": float(np.mean(rot_e)),
+                                                "mean_abs_jerk": float(np.mean(jerk))}
+    return {"ablation": out, "workload": base.name, "goals": len(goals), "steps_per_goal": steps_per_goal,
+            "data": "synthetic"}
+
+
+def _local_goals(ctl, theta0, seed: int, count: int):
+    """Goal poses FK(theta_g) with theta_g = theta0 + U[-0.6, 0.6] rad per joint, within
+    [-2.2, 2.2] and 3 cm clear of self-collision: reaching moves that a local
+    optimiser can complete, so the samplers are compared on accuracy and smoothness."""
+    import torch
+    rng = np.random.default_rng([seed, 123])
+    cand = np.clip(theta0 + rng.uniform(-0.6, 0.6, (64 * count, theta0.shape[0])), -2.2, 2.2).astype(np.float32)
+    sd = ctl.self_distance(torch.as_tensor(cand, device="cuda")).cpu().numpy()
+    th = cand[sd > 0.03][:count]
+    ee = ctl.forward_kinematics(torch.as_tensor(th, device="cuda")).cpu().numpy()
+    goals = []
+    for T in ee:
+        q = _quat_from_rot(T[:, :3].astype(np.float64))
+        goals.append(np.concatenate([T[:, 3], q]).astype(np.float32))
+    return goals
+
+
+def _quat_from_rot(Rm):
+    w = math.sqrt(max(0.0, 1 + Rm[0, 0] + Rm[1, 1] + Rm[2, 2])) / 2
+    x = math.copysign(math.sqrt(max(0.0, 1 + Rm[0, 0] - Rm[1, 1] - Rm[2, 2])) / 2, Rm[2, 1] - Rm[1, 2])
+    y = math.copysign(math.sqrt(max(0.0, 1 - Rm[0, 0] + Rm[1, 1] - Rm[2, 2])) / 2, Rm[0, 2] - Rm[2, 0])
+    z = math.copysign(math.sqrt(max(0.0, 1 - Rm[0, 0] - Rm[1, 1] + Rm[2, 2])) / 2, Rm[1, 0] - Rm[0, 1])
+    return np.array([w, x, y, z])
+
+
+def _rot_from_quat(q):
+    w, x, y, z = np.asarray(q, np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
 
 
 def cpu_baseline(wl, budget_s: float = 12.0, n_sample: int | None = None):
@@ -483,6 +580,8 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--ablation", action="store_true",
+                    help="run the closed-loop sampling ablation instead of the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -493,6 +592,10 @@ def main():
         if rank != 0:
             return
         print(json.dumps(run_reference(args)))
+        return
+    if args.ablation:
+        if rank == 0:
+            print(json.dumps(run_ablation(args)))
         return
 
     if world_size > 1:
