@@ -62,6 +62,15 @@ class _World(C.Structure):
                 ("spheres", _dp)]
 
 
+class _Arch(C.Structure):
+    _fields_ = [("enc", C.c_int), ("h1", C.c_int), ("h2", C.c_int), ("h3", C.c_int)]
+
+
+# surrogate architectures: (encoding, h1, h2, h3)
+ARCH_DISTANCE = (0, 256, 256, 256)   # theta / 3 encoding, three 256-wide layers
+ARCH_JOINTNERF = (1, 256, 128, 64)   # [sin theta, cos theta] encoding, [256, 128, 64] (Sec. 4.2)
+
+
 class _Params(C.Structure):
     _fields_ = [("N", C.c_int), ("H", C.c_int), ("K", C.c_int), ("n_knots", C.c_int),
                 ("sampler", C.c_int), ("n_null", C.c_int), ("dt", _dp),
@@ -128,6 +137,12 @@ def _declare(L):
                                 _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_cost_grad.restype = C.c_int
     L.orc_mlp_param_count.restype = C.c_long
+    L.orc_mlp_arch_param_count.argtypes = [C.POINTER(_Arch)]
+    L.orc_mlp_arch_param_count.restype = C.c_long
+    L.orc_mlp_arch_encode.argtypes = [C.POINTER(_Arch), _dp, C.c_int, _dp]
+    L.orc_mlp_arch_forward.argtypes = [C.POINTER(_Arch), _dp, _dp, C.c_int, C.c_int, C.c_int, _dp]
+    L.orc_mlp_arch_loss_grad.argtypes = [C.POINTER(_Arch), _dp, _dp, _dp, C.c_int, C.c_int, C.c_int, _dp]
+    L.orc_mlp_arch_loss_grad.restype = C.c_double
     L.orc_bf16_round.argtypes = [C.c_float]
     L.orc_bf16_round.restype = C.c_float
     L.orc_mlp_forward.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, _dp]
@@ -229,6 +244,34 @@ def mlp_forward(params, theta, bf16=True) -> np.ndarray:
     y = np.zeros(B)
     lib().orc_mlp_forward(_ptr(params), _ptr(theta), B, dof, int(bf16), _ptr(y))
     return y
+
+
+def mlp_arch_param_count(arch) -> int:
+    return int(lib().orc_mlp_arch_param_count(C.byref(_Arch(*arch))))
+
+
+def mlp_arch_encode(arch, theta) -> np.ndarray:
+    th = _f64(theta)
+    x = np.zeros(16)
+    lib().orc_mlp_arch_encode(C.byref(_Arch(*arch)), _ptr(th), th.shape[0], _ptr(x))
+    return x
+
+
+def mlp_arch_forward(arch, params, theta, bf16=True) -> np.ndarray:
+    params, theta = _f64(params), _f64(theta)
+    B, dof = theta.shape
+    y = np.zeros(B)
+    lib().orc_mlp_arch_forward(C.byref(_Arch(*arch)), _ptr(params), _ptr(theta), B, dof, int(bf16), _ptr(y))
+    return y
+
+
+def mlp_arch_loss_grad(arch, params, theta, target, bf16=True):
+    params, theta, target = _f64(params), _f64(theta), _f64(target)
+    B, dof = theta.shape
+    g = np.zeros(mlp_arch_param_count(arch))
+    loss = lib().orc_mlp_arch_loss_grad(C.byref(_Arch(*arch)), _ptr(params), _ptr(theta), _ptr(target), B, dof,
+                                        int(bf16), _ptr(g))
+    return loss, g
 
 
 def mlp_loss_grad(params, theta, target, bf16=True):

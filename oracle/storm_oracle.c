@@ -1337,7 +1337,21 @@ int orc_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
 #define H_ ORC_MLP_HID
 #define I_ ORC_MLP_IN
 
-long orc_mlp_param_count(void) { return (long)H_ * I_ + 2L * (H_ * H_ + H_) + H_ + 1; }
+/* Surrogate networks for the self-collision term (Sec. 4.2, Eq. 13).  Layers:
+ * x (16) -> h1 -> h2 -> h3 -> 1, ReLU on the hidden layers, no bias on the
+ * first (the encoding carries a constant-one feature), a linear output.
+ * Parameters flat: W1 (h1 x 16) | W2 (h2 x h1) | b2 | W3 (h3 x h2) | b3 |
+ * w4 (h3) | b4.  Encodings: SCALED x_j = theta_j / 3, x_7 = 1 (the 256-256-256
+ * distance network); SINCOS x_j = sin theta_j, x_{7+j} = cos theta_j, x_14 = 1
+ * (jointNERF's positional encoding, hidden [256, 128, 64]). */
+static const orc_mlp_arch k_arch_default = {ORC_ENC_SCALED, 256, 256, 256};
+
+long orc_mlp_arch_param_count(const orc_mlp_arch* A)
+{
+    return (long)A->h1 * I_ + (long)A->h2 * A->h1 + A->h2 + (long)A->h3 * A->h2 + A->h3 + A->h3 + 1;
+}
+
+long orc_mlp_param_count(void) { return orc_mlp_arch_param_count(&k_arch_default); }
 
 /* Round to the nearest bfloat16 (ties to even) through binary32. */
 float orc_bf16_round(float x)
@@ -1354,121 +1368,147 @@ float orc_bf16_round(float x)
 
 static double q(double v, int bf16) { return bf16 ? (double)orc_bf16_round((float)v) : v; }
 
-void orc_mlp_encode(const double* theta, int dof, double* x)
+void orc_mlp_arch_encode(const orc_mlp_arch* A, const double* theta, int dof, double* x)
 {
     for (int i = 0; i < I_; ++i) x[i] = 0.0;
-    for (int j = 0; j < dof && j < 7; ++j) x[j] = theta[j] / 3.0;
-    x[7] = 1.0;
+    if (A->enc == ORC_ENC_SINCOS) {
+        for (int j = 0; j < dof && j < 7; ++j) {
+            x[j] = sin(theta[j]);
+            x[7 + j] = cos(theta[j]);
+        }
+        x[14] = 1.0;
+    } else {
+        for (int j = 0; j < dof && j < 7; ++j) x[j] = theta[j] / 3.0;
+        x[7] = 1.0;
+    }
 }
+
+void orc_mlp_encode(const double* theta, int dof, double* x) { orc_mlp_arch_encode(&k_arch_default, theta, dof, x); }
 
 typedef struct {
     const double *W1, *W2, *b2, *W3, *b3, *w4, *b4;
 } mlp_view;
 
-static mlp_view mlp_split(const double* p)
+static mlp_view mlp_split(const orc_mlp_arch* A, const double* p)
 {
     mlp_view v;
     v.W1 = p;
-    v.W2 = v.W1 + H_ * I_;
-    v.b2 = v.W2 + H_ * H_;
-    v.W3 = v.b2 + H_;
-    v.b3 = v.W3 + H_ * H_;
-    v.w4 = v.b3 + H_;
-    v.b4 = v.w4 + H_;
+    v.W2 = v.W1 + A->h1 * I_;
+    v.b2 = v.W2 + A->h2 * A->h1;
+    v.W3 = v.b2 + A->h2;
+    v.b3 = v.W3 + A->h3 * A->h2;
+    v.w4 = v.b3 + A->h3;
+    v.b4 = v.w4 + A->h3;
     return v;
 }
 
-/* one sample: activations a1, a2, a3 (H_ each) and output */
-static double mlp_one(const mlp_view* v, const double* x_in, int bf16, double* a1, double* a2,
-                      double* a3)
+/* one sample: activations a1 (h1), a2 (h2), a3 (h3) and output; with bf16 the
+ * operands of the three GEMM layers are rounded as the tensor-core path rounds
+ * them (inputs, weights, a1, a2), the output layer reads the unrounded a3 */
+static double mlp_one(const orc_mlp_arch* A, const mlp_view* v, const double* x_in, int bf16, double* a1,
+                      double* a2, double* a3)
 {
     double x[I_];
     for (int i = 0; i < I_; ++i) x[i] = q(x_in[i], bf16);
-    for (int n = 0; n < H_; ++n) {
+    for (int n = 0; n < A->h1; ++n) {
         double z = 0.0;
         for (int k = 0; k < I_; ++k) z += q(v->W1[n * I_ + k], bf16) * x[k];
         a1[n] = q(z > 0.0 ? z : 0.0, bf16);
     }
-    for (int n = 0; n < H_; ++n) {
+    for (int n = 0; n < A->h2; ++n) {
         double z = 0.0;
-        for (int k = 0; k < H_; ++k) z += q(v->W2[n * H_ + k], bf16) * a1[k];
+        for (int k = 0; k < A->h1; ++k) z += q(v->W2[n * A->h1 + k], bf16) * a1[k];
         z += v->b2[n];
         a2[n] = q(z > 0.0 ? z : 0.0, bf16);
     }
     double y = v->b4[0];
-    for (int n = 0; n < H_; ++n) {
+    for (int n = 0; n < A->h3; ++n) {
         double z = 0.0;
-        for (int k = 0; k < H_; ++k) z += q(v->W3[n * H_ + k], bf16) * a2[k];
+        for (int k = 0; k < A->h2; ++k) z += q(v->W3[n * A->h2 + k], bf16) * a2[k];
         z += v->b3[n];
         const double a = z > 0.0 ? z : 0.0;
-        y += v->w4[n] * a;      /* the output layer reads the unrounded a3 */
+        y += v->w4[n] * a;
         a3[n] = q(a, bf16);
     }
     return y;
 }
 
-void orc_mlp_forward(const double* params, const double* theta, int B, int dof, int bf16,
-                     double* y)
+enum { MAXH_ = 256 };
+
+void orc_mlp_arch_forward(const orc_mlp_arch* A, const double* params, const double* theta, int B, int dof,
+                          int bf16, double* y)
 {
-    const mlp_view v = mlp_split(params);
-    double x[I_], a1[H_], a2[H_], a3[H_];
+    const mlp_view v = mlp_split(A, params);
+    double x[I_], a1[MAXH_], a2[MAXH_], a3[MAXH_];
     for (int b = 0; b < B; ++b) {
-        orc_mlp_encode(theta + b * dof, dof, x);
-        y[b] = mlp_one(&v, x, bf16, a1, a2, a3);
+        orc_mlp_arch_encode(A, theta + b * dof, dof, x);
+        y[b] = mlp_one(A, &v, x, bf16, a1, a2, a3);
     }
+}
+
+void orc_mlp_forward(const double* params, const double* theta, int B, int dof, int bf16, double* y)
+{
+    orc_mlp_arch_forward(&k_arch_default, params, theta, B, dof, bf16, y);
 }
 
 /* Mean squared error (1/B) sum (y_b - t_b)^2 and its gradient, by the chain
  * rule written layer by layer (delta_l = (W_{l+1}^T delta_{l+1}) o [z_l > 0]). */
-double orc_mlp_loss_grad(const double* params, const double* theta, const double* target, int B,
-                         int dof, int bf16, double* grad)
+double orc_mlp_arch_loss_grad(const orc_mlp_arch* A, const double* params, const double* theta,
+                              const double* target, int B, int dof, int bf16, double* grad)
 {
-    const mlp_view v = mlp_split(params);
-    const long P = orc_mlp_param_count();
+    const int h1 = A->h1, h2 = A->h2, h3 = A->h3;
+    const mlp_view v = mlp_split(A, params);
+    const long P = orc_mlp_arch_param_count(A);
     for (long i = 0; i < P; ++i) grad[i] = 0.0;
     double* gW1 = grad;
-    double* gW2 = gW1 + H_ * I_;
-    double* gb2 = gW2 + H_ * H_;
-    double* gW3 = gb2 + H_;
-    double* gb3 = gW3 + H_ * H_;
-    double* gw4 = gb3 + H_;
-    double* gb4 = gw4 + H_;
+    double* gW2 = gW1 + h1 * I_;
+    double* gb2 = gW2 + h2 * h1;
+    double* gW3 = gb2 + h2;
+    double* gb3 = gW3 + h3 * h2;
+    double* gw4 = gb3 + h3;
+    double* gb4 = gw4 + h3;
     double loss = 0.0;
-    double x[I_], xq[I_], a1[H_], a2[H_], a3[H_], d3[H_], d2[H_], d1[H_];
+    double x[I_], xq[I_], a1[MAXH_], a2[MAXH_], a3[MAXH_], d3[MAXH_], d2[MAXH_], d1[MAXH_];
     for (int b = 0; b < B; ++b) {
-        orc_mlp_encode(theta + b * dof, dof, x);
-        const double y = mlp_one(&v, x, bf16, a1, a2, a3);
+        orc_mlp_arch_encode(A, theta + b * dof, dof, x);
+        const double y = mlp_one(A, &v, x, bf16, a1, a2, a3);
         for (int i = 0; i < I_; ++i) xq[i] = q(x[i], bf16);
         const double r = y - target[b];
         loss += r * r / B;
         const double dy = 2.0 * r / B;
         gb4[0] += dy;
-        for (int n = 0; n < H_; ++n) {
+        for (int n = 0; n < h3; ++n) {
             gw4[n] += dy * a3[n];
             d3[n] = q(a3[n] > 0.0 ? dy * v.w4[n] : 0.0, bf16);
         }
-        for (int n = 0; n < H_; ++n) {
+        for (int n = 0; n < h3; ++n) {
             gb3[n] += d3[n];
-            for (int k = 0; k < H_; ++k) gW3[n * H_ + k] += d3[n] * a2[k];
+            for (int k = 0; k < h2; ++k) gW3[n * h2 + k] += d3[n] * a2[k];
         }
-        for (int k = 0; k < H_; ++k) {
+        for (int k = 0; k < h2; ++k) {
             double s = 0.0;
-            for (int n = 0; n < H_; ++n) s += d3[n] * q(v.W3[n * H_ + k], bf16);
+            for (int n = 0; n < h3; ++n) s += d3[n] * q(v.W3[n * h2 + k], bf16);
             d2[k] = q(a2[k] > 0.0 ? s : 0.0, bf16);
         }
-        for (int n = 0; n < H_; ++n) {
+        for (int n = 0; n < h2; ++n) {
             gb2[n] += d2[n];
-            for (int k = 0; k < H_; ++k) gW2[n * H_ + k] += d2[n] * a1[k];
+            for (int k = 0; k < h1; ++k) gW2[n * h1 + k] += d2[n] * a1[k];
         }
-        for (int k = 0; k < H_; ++k) {
+        for (int k = 0; k < h1; ++k) {
             double s = 0.0;
-            for (int n = 0; n < H_; ++n) s += d2[n] * q(v.W2[n * H_ + k], bf16);
+            for (int n = 0; n < h2; ++n) s += d2[n] * q(v.W2[n * h1 + k], bf16);
             d1[k] = q(a1[k] > 0.0 ? s : 0.0, bf16);
         }
-        for (int n = 0; n < H_; ++n)
+        for (int n = 0; n < h1; ++n)
             for (int k = 0; k < I_; ++k) gW1[n * I_ + k] += d1[n] * xq[k];
     }
     return loss;
+}
+
+double orc_mlp_loss_grad(const double* params, const double* theta, const double* target, int B, int dof,
+                         int bf16, double* grad)
+{
+    return orc_mlp_arch_loss_grad(&k_arch_default, params, theta, target, B, dof, bf16, grad);
 }
 
 /* Exact label of the surrogate: the minimum signed distance over the self

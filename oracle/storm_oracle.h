@@ -147,6 +147,17 @@ int orc_cost_grad(const orc_robot* R, const orc_world* W, const orc_params* P,
                   const double* eps, double* grad_mu, double* J, double* dC_du);
 /* ---- self-collision surrogate network (parameters flat, see storm_oracle.c) */
 enum { ORC_MLP_IN = 16, ORC_MLP_HID = 256 };
+enum { ORC_ENC_SCALED = 0, ORC_ENC_SINCOS = 1 };
+typedef struct {
+    int enc;           /* ORC_ENC_* */
+    int h1, h2, h3;    /* hidden widths (each <= 256) */
+} orc_mlp_arch;
+long orc_mlp_arch_param_count(const orc_mlp_arch* A);
+void orc_mlp_arch_encode(const orc_mlp_arch* A, const double* theta, int dof, double* x);
+void orc_mlp_arch_forward(const orc_mlp_arch* A, const double* params, const double* theta, int B, int dof,
+                          int bf16, double* y);
+double orc_mlp_arch_loss_grad(const orc_mlp_arch* A, const double* params, const double* theta,
+                              const double* target, int B, int dof, int bf16, double* grad);
 long orc_mlp_param_count(void);
 float orc_bf16_round(float x);
 void orc_mlp_encode(const double* theta, int dof, double* x);

@@ -79,3 +79,78 @@ def test_bf16_mode_close_to_fp64():
     y16 = oracle.mlp_forward(p, th, bf16=True)
     assert np.max(np.abs(y64 - y16)) < 0.05 * max(1.0, np.max(np.abs(y64)))
     assert not np.array_equal(y64, y16)
+
+
+# ----------------------------------------------------------------------------- jointNERF (Sec. 4.2)
+
+NERF = oracle.ARCH_JOINTNERF
+PN = 256 * 16 + 128 * 256 + 128 + 64 * 128 + 64 + 64 + 1
+
+
+def _split_nerf(p):
+    o, parts = 0, {}
+    for name, n in [("W1", 256 * 16), ("W2", 128 * 256), ("b2", 128), ("W3", 64 * 128), ("b3", 64),
+                    ("w4", 64), ("b4", 1)]:
+        parts[name] = p[o:o + n]
+        o += n
+    return parts
+
+
+def test_jointnerf_shape_and_encoding():
+    assert oracle.mlp_arch_param_count(NERF) == PN == 45313
+    assert oracle.mlp_arch_param_count(oracle.ARCH_DISTANCE) == P
+    th = np.array([0.3, -1.2, 2.0, 0.0, -2.7, 1.1, 0.5])
+    x = oracle.mlp_arch_encode(NERF, th)
+    assert np.allclose(x[:7], np.sin(th)) and np.allclose(x[7:14], np.cos(th))
+    assert x[14] == 1.0 and x[15] == 0.0
+
+
+def test_jointnerf_routes_by_hand():
+    """Single paths through the three layers, at asymmetric indices: y = relu(sin th_0)
+    through units (5, 3, 2), plus 0.5 relu(cos th_1 - 0.2) through (9, 100, 40)."""
+    p = np.zeros(PN)
+    d = _split_nerf(p)
+    d["W1"][5 * 16 + 0] = 1.0        # a1_5 = relu(sin th0)
+    d["W2"][3 * 256 + 5] = 1.0       # a2_3 = a1_5
+    d["W3"][2 * 128 + 3] = 1.0       # a3_2 = a2_3
+    d["w4"][2] = 1.0
+    d["W1"][9 * 16 + 8] = 1.0        # a1_9 = relu(cos th1 - 0.2)  (x_8 = cos th1, x_14 = 1)
+    d["W1"][9 * 16 + 14] = -0.2
+    d["W2"][100 * 256 + 9] = 2.0     # a2_100 = 2 a1_9
+    d["W3"][40 * 128 + 100] = 0.25   # a3_40 = 0.5 a1_9
+    d["w4"][40] = 1.0
+    d["b4"][0] = -0.05
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-3, 3, (20, 7))
+    y = oracle.mlp_arch_forward(NERF, p, th, bf16=False)
+    ref = np.maximum(0, np.sin(th[:, 0])) + 0.5 * np.maximum(0, np.cos(th[:, 1]) - 0.2) - 0.05
+    assert np.allclose(y, ref, atol=1e-14)
+
+
+def test_jointnerf_loss_gradient_finite_differences():
+    rng = np.random.default_rng(1)
+    p = rng.normal(0, 0.15, PN)
+    th = rng.uniform(-2.8, 2.8, (4, 7))
+    t = rng.uniform(-0.1, 0.4, 4)
+    loss, g = oracle.mlp_arch_loss_grad(NERF, p, th, t, bf16=False)
+    y = oracle.mlp_arch_forward(NERF, p, th, bf16=False)
+    assert loss == pytest.approx(np.mean((y - t) ** 2), rel=1e-12)
+    idx = np.concatenate([rng.choice(PN, 60, replace=False), [PN - 1, PN - 2, 4096 + 32768 + 5]])
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (oracle.mlp_arch_loss_grad(NERF, pp, th, t, bf16=False)[0] -
+              oracle.mlp_arch_loss_grad(NERF, pm, th, t, bf16=False)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, abs=1e-7 + 1e-5 * abs(fd)), i
+
+
+def test_jointnerf_bf16_mode_close_to_fp64():
+    rng = np.random.default_rng(2)
+    p = rng.normal(0, 0.1, PN)
+    th = rng.uniform(-2.8, 2.8, (50, 7))
+    y64 = oracle.mlp_arch_forward(NERF, p, th, bf16=False)
+    y16 = oracle.mlp_arch_forward(NERF, p, th, bf16=True)
+    assert np.abs(y16 - y64).max() < 0.03 * max(1.0, np.abs(y64).max())
+    assert not np.array_equal(y16, y64)
