@@ -383,18 +383,28 @@ typedef struct storm_mlp storm_mlp;
 #define STORM_MLP_PARAMS 135937
 #define STORM_MLP_MAX_ROWS (1 << 22)
 
+/* Architectures: STORM_MLP_DISTANCE is the network above; STORM_MLP_JOINTNERF
+ * is the paper's jointNERF (Sec. 4.2): positional encoding x_j = sin theta_j,
+ * x_{7+j} = cos theta_j, x_14 = 1, then 256 -> 128 -> 64 -> 1 with ReLU, the
+ * same flat layout with those widths (45313 parameters). */
+#define STORM_MLP_DISTANCE 0
+#define STORM_MLP_JOINTNERF 1
+
 /* He-uniform initial weights from the Philox stream of `seed`. */
-int storm_mlp_create(uint64_t seed, void* cuda_stream, storm_mlp** out);
+int storm_mlp_create(uint64_t seed, void* cuda_stream, storm_mlp** out); /* STORM_MLP_DISTANCE */
+int storm_mlp_create_arch(uint64_t seed, int arch, void* cuda_stream, storm_mlp** out);
+/* Number of FP32 parameters of the network (INVALID_ARG for NULL). */
+int storm_mlp_param_count(const storm_mlp* m);
 void storm_mlp_destroy(storm_mlp* m);
 const char* storm_mlp_last_error(const storm_mlp* m);
-/* Host copies of the FP32 parameters (STORM_MLP_PARAMS floats). */
+/* Host copies of the FP32 parameters (storm_mlp_param_count floats). */
 int storm_mlp_get_params(storm_mlp* m, float* params);
 int storm_mlp_set_params(storm_mlp* m, const float* params);
 /* Predicted distances for theta_dev (count x dof, dof <= 7) into out_dev
  * (count); device buffers, waits.  count <= STORM_MLP_MAX_ROWS. */
 int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev);
 /* Mean squared error against target_dev (count) and its gradient (host,
- * STORM_MLP_PARAMS floats, nullable); waits. */
+ * storm_mlp_param_count floats, nullable); waits. */
 int storm_mlp_loss_grad(storm_mlp* m, const float* theta_dev, const float* target_dev, int count,
                         int dof, float* loss, float* grad);
 /* Adam training over `epochs` passes of shuffled minibatches of `batch`
@@ -415,6 +425,12 @@ int storm_self_distance(storm_handle* h, const float* theta_dev, int count, floa
  * `margin` metres (elsewhere the self term is 0).  The network must outlive
  * its use and must not run concurrently with this handle's steps. */
 int storm_set_surrogate(storm_handle* h, storm_mlp* mlp, double margin);
+
+/* The paper's own use of the network (Eq. 13): the self-collision term of each
+ * (particle, step) is max(0, mlp(theta)) with the network predicting the
+ * penetration depth (positive when colliding), and no exact self check runs.
+ * NULL stops it.  Same lifetime rules as storm_set_surrogate. */
+int storm_set_surrogate_cost(storm_handle* h, storm_mlp* mlp);
 
 /* ---------------------------------------------------------------- checkpoint */
 

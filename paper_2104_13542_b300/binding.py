@@ -47,6 +47,7 @@ EXPORTED = [
     "storm_mlp_create", "storm_mlp_destroy", "storm_mlp_last_error", "storm_mlp_get_params",
     "storm_mlp_set_params", "storm_mlp_predict", "storm_mlp_loss_grad", "storm_mlp_train",
     "storm_self_distance", "storm_set_surrogate", "storm_set_broadphase", "storm_set_trace",
+    "storm_mlp_create_arch", "storm_mlp_param_count", "storm_set_surrogate_cost",
 ]
 MLP_PARAMS = 135937
 
@@ -161,6 +162,9 @@ def lib():
         L.storm_batch_autotune.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_batch_get_launch.argtypes = [vp, ip, ip]
         L.storm_mlp_create.argtypes = [C.c_uint64, vp, C.POINTER(vp)]
+        L.storm_mlp_create_arch.argtypes = [C.c_uint64, C.c_int, vp, C.POINTER(vp)]
+        L.storm_mlp_param_count.argtypes = [vp]
+        L.storm_set_surrogate_cost.argtypes = [vp, vp]
         L.storm_mlp_destroy.argtypes = [vp]
         L.storm_mlp_destroy.restype = None
         L.storm_mlp_last_error.argtypes = [vp]
@@ -479,6 +483,11 @@ class Controller:
         self.stream.synchronize()
         return out
 
+    def set_surrogate_cost(self, mlp):
+        """Self term = max(0, mlp(theta)) (Eq. 13), mlp predicting penetration depth; None stops it."""
+        self._check(lib().storm_set_surrogate_cost(self.h, mlp.h if mlp is not None else None))
+        self._mlp = mlp
+
     def set_surrogate(self, mlp, margin: float = 0.05):
         self._check(lib().storm_set_surrogate(self.h, mlp.h if mlp is not None else None,
                                               float(margin)))
@@ -631,20 +640,28 @@ class BatchController:
         return a.value, b.value
 
 
-class SurrogateMLP:
-    """The learned self-collision distance network (storm_mlp_* C ABI)."""
+MLP_ARCHS = {"distance": 0, "jointnerf": 1}
 
-    def __init__(self, seed: int = 0, stream=None):
+
+class SurrogateMLP:
+    """A learned self-collision network (storm_mlp_* C ABI): arch "distance"
+    (theta / 3 encoding, 256-256-256) or "jointnerf" (the paper's [sin, cos]
+    encoding, 256-128-64)."""
+
+    def __init__(self, seed: int = 0, stream=None, arch: str = "distance"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the surrogate network needs a CUDA device")
         self.torch = torch
+        self.arch = arch
         self.stream = stream if stream is not None else torch.cuda.Stream()
         h = C.c_void_p()
-        rc = lib().storm_mlp_create(int(seed), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        rc = lib().storm_mlp_create_arch(int(seed), MLP_ARCHS[arch], C.c_void_p(self.stream.cuda_stream),
+                                         C.byref(h))
         if rc != 0:
             raise StormError(rc, "storm_mlp_create failed (see stderr)")
         self.h = h
+        self.n_params = int(lib().storm_mlp_param_count(self.h))
 
     def _check(self, rc):
         if rc < 0:
@@ -666,13 +683,13 @@ class SurrogateMLP:
             pass
 
     def get_params(self) -> np.ndarray:
-        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        out = np.zeros(self.n_params, dtype=np.float32)
         self._check(lib().storm_mlp_get_params(self.h, _p(out, _fp)))
         return out
 
     def set_params(self, params):
         p = _f32(params).reshape(-1)
-        assert p.size == MLP_PARAMS
+        assert p.size == self.n_params
         self._check(lib().storm_mlp_set_params(self.h, _p(p, _fp)))
 
     def predict(self, theta_dev):
@@ -686,7 +703,7 @@ class SurrogateMLP:
     def loss_grad(self, theta_dev, target_dev):
         n, dof = int(theta_dev.shape[0]), int(theta_dev.shape[1])
         loss = np.zeros(1, dtype=np.float32)
-        grad = np.zeros(MLP_PARAMS, dtype=np.float32)
+        grad = np.zeros(self.n_params, dtype=np.float32)
         self._sync_in()
         self._check(lib().storm_mlp_loss_grad(self.h, _dptr(theta_dev.contiguous()),
                                               _dptr(target_dev.contiguous()), n, dof,

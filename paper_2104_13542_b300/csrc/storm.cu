@@ -351,7 +351,9 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
             s_ba[2 * item + 1] = a.y;
         }
         s_part[item] = part;
-        s_dself[item] = 0.f;
+        // the learned term of Eq. 13 replaces the exact self check
+        s_dself[item] = (pb.self_pred && pb.self_direct)
+                            ? fmaxf(0.f, pb.self_pred[static_cast<size_t>(n0) * H + item]) : 0.f;
         s_dworld[item] = 0.f;
         const size_t g = static_cast<size_t>(n0) * H + item;
         if (out.ee) {
@@ -517,7 +519,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     const float* pred = pb.self_pred ? pb.self_pred + static_cast<size_t>(n0) * H : nullptr;
     for (int idx = tid; idx < I * pb.NPB; idx += nt) {
         const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
-        if (pred && pred[item] >= pb.self_margin) continue;  // surrogate: clearly apart
+        if (pred && (pb.self_direct || pred[item] >= pb.self_margin)) continue;  // surrogate
         const uint4 blk = s_pblk[bk];  // a0, a1, b0, nb
         const int la = s_slink[blk.x], lbk = s_slink[blk.z];
         const float4* fa = s_frame + (item * F + la) * 3;
@@ -572,7 +574,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         const float rs = qa.w + qb.w;
         const float rs2 = rs * rs;
         for (int item = 0; item < I; ++item) {
-            if (pred && pred[item] >= pb.self_margin) continue;
+            if (pred && (pb.self_direct || pred[item] >= pb.self_margin)) continue;
             const float4* fa = s_frame + (item * F + s_slink[a]) * 3;
             const float4* fb = s_frame + (item * F + s_slink[b]) * 3;
             const float ex = (fmaf(fa[0].x, qa.x, fmaf(fa[0].y, qa.y, fmaf(fa[0].z, qa.z, fa[0].w)))) -
@@ -1164,6 +1166,7 @@ struct MlpBuffers {
 };
 
 struct storm_mlp {
+    MlpArch a = mlp_arch(0, kMlpHid, kMlpHid, kMlpHid);
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -1233,13 +1236,17 @@ int split_count(int R)
     return std::max(sp, 1);
 }
 
-// out[i] = sum over s of part[s * n + i], in the order s = 0, 1, ...
-__global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int n, float* __restrict__ out)
+// out[i] = sum over s of part[s * n + i], in the order s = 0, 1, ...; with
+// tr_rows > 0 the partials are the transpose (tr_cols x tr_rows) of out
+// (tr_rows x tr_cols): out[r * tr_cols + c] = sum_s part[s][c * tr_rows + r].
+__global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int n, int tr_rows, int tr_cols,
+                                float* __restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int src = tr_rows > 0 ? (i % tr_cols) * tr_rows + i / tr_cols : i;
     float acc = 0.f;
-    for (int s = 0; s < splits; ++s) acc += part[static_cast<size_t>(s) * n + i];
+    for (int s = 0; s < splits; ++s) acc += part[static_cast<size_t>(s) * n + src];
     out[i] = acc;
 }
 
@@ -1260,26 +1267,38 @@ cudaError_t gemm(const tc::GemmArgs& g, cudaStream_t s, int splits = 1)
     return cudaGetLastError();
 }
 
-// Forward layer with the weights resident in shared memory (N = 256, K = 16 or 256).
-cudaError_t gemm_rw(const tc::GemmArgs& g, cudaStream_t s)
+// Layer with the weights resident in shared memory: N = 64, 128 or 256 and
+// K = 16, 64, 128 or 256.
+template <int BN>
+cudaError_t gemm_rw_bn(const tc::GemmArgs& g, cudaStream_t s)
 {
     static int attr_dev = -1;
     static int sms = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(tc::k_gemm_rw, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(tc::gemm_rw_smem(256)));
+        cudaError_t e = cudaFuncSetAttribute(tc::k_gemm_rw<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(tc::gemm_rw_smem(256, 256)));
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    if (g.M % tc::kBM || g.N != 256 || (g.K != 16 && g.K != 256)) return cudaErrorInvalidValue;
     const int grid = std::min(g.M / tc::kBM, sms);
-    // the full-K shared-memory size for every layer keeps one CTA (and one
-    // 512-column TMEM allocation) per SM
-    tc::k_gemm_rw<<<grid, tc::kThreads, tc::gemm_rw_smem(256), s>>>(g);
+    // the largest plan's shared-memory size for every layer keeps one CTA (and
+    // one TMEM allocation) per SM
+    tc::k_gemm_rw<BN><<<grid, tc::kThreads, tc::gemm_rw_smem(256, 256), s>>>(g);
     return cudaGetLastError();
+}
+
+cudaError_t gemm_rw(const tc::GemmArgs& g, cudaStream_t s)
+{
+    if (g.M % tc::kBM || (g.K != 16 && g.K != 64 && g.K != 128 && g.K != 256)) return cudaErrorInvalidValue;
+    switch (g.N) {
+    case 64: return gemm_rw_bn<64>(g, s);
+    case 128: return gemm_rw_bn<128>(g, s);
+    case 256: return gemm_rw_bn<256>(g, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 tc::GemmArgs gemm_args(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
@@ -1297,16 +1316,45 @@ tc::GemmArgs gemm_args(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, 
     return g;
 }
 
-// dW = delta^T act over R rows (both operands stored transposed, R contiguous),
-// split into `splits` K ranges whose FP32 partials go to part[split][256][N].
-tc::GemmArgs weight_grad(const __nv_bfloat16* deltaT, const __nv_bfloat16* actT, int R, int splits, int N,
+// C = P^T Q over R rows (both operands stored transposed, R contiguous: P is
+// M x R, Q is N x R), split into `splits` K ranges whose FP32 partials go to
+// part[split][M][N].
+tc::GemmArgs weight_grad(const __nv_bfloat16* PT, const __nv_bfloat16* QT, int R, int splits, int M, int N,
                          float* part, int* err)
 {
-    tc::GemmArgs g = gemm_args(deltaT, R, actT, R, kMlpHid, N, R / splits, err);
+    tc::GemmArgs g = gemm_args(PT, R, QT, R, M, N, R / splits, err);
     g.out_f = part;
     g.ldf = N;
-    g.split_stride = static_cast<size_t>(kMlpHid) * N;
+    g.split_stride = static_cast<size_t>(M) * N;
     return g;
+}
+
+cudaError_t gemm_split(const tc::GemmArgs& g, cudaStream_t s, int splits)
+{
+    switch (g.N) {
+    case 16: return gemm<16>(g, s, splits);
+    case 64: return gemm<64>(g, s, splits);
+    case 128: return gemm<128>(g, s, splits);
+    case 256: return gemm<256>(g, s, splits);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Weight gradient dW (rows x cols) = delta^T act over R rows into out (FP32,
+// row-major): split-K GEMM and fixed-order reduction; when rows is not a
+// multiple of 128 the product is formed transposed (act^T delta) and the
+// reduction writes it back transposed.
+int weight_grad_into(const __nv_bfloat16* deltaT, const __nv_bfloat16* actT, int R, int rows, int cols,
+                     float* part, float* out, int* err, cudaStream_t s)
+{
+    const int sp = split_count(R);
+    const bool tr = rows % tc::kBM != 0;
+    const tc::GemmArgs g = tr ? weight_grad(actT, deltaT, R, sp, cols, rows, part, err)
+                              : weight_grad(deltaT, actT, R, sp, rows, cols, part, err);
+    if (gemm_split(g, s, sp) != cudaSuccess) return STORM_ERR_CUDA;
+    const int n = rows * cols;
+    k_splitk_reduce<<<(n + 255) / 256, 256, 0, s>>>(part, sp, n, tr ? rows : 0, tr ? cols : 0, out);
+    return cudaGetLastError() == cudaSuccess ? STORM_OK : STORM_ERR_CUDA;
 }
 
 // Forward pass for `count` configurations (rows padded to 128); y (or the
@@ -1315,39 +1363,40 @@ tc::GemmArgs weight_grad(const __nv_bfloat16* deltaT, const __nv_bfloat16* actT,
 int mlp_forward(storm_mlp* m, MlpBuffers& b, const float* theta, int count, int dof, bool train,
                 float* y, cudaStream_t s)
 {
+    const MlpArch& A = m->a;
     const int R = (count + tc::kBM - 1) / tc::kBM * tc::kBM;
     if (mlp_reserve(b, R, train) != cudaSuccess) return STORM_ERR_OOM;
     if (!y) y = b.y;  // after the reserve, which may reallocate b.y
-    k_mlp_encode<<<(R + 255) / 256, 256, 0, s>>>(theta, count, dof, R, b.x, train ? b.xT : nullptr);
+    k_mlp_encode<<<(R + 255) / 256, 256, 0, s>>>(theta, count, dof, R, A.enc, b.x, train ? b.xT : nullptr);
     if (cudaGetLastError() != cudaSuccess) return STORM_ERR_CUDA;
-    tc::GemmArgs g = gemm_args(b.x, kMlpIn, m->w1, kMlpIn, R, kMlpHid, kMlpIn, m->err);
+    tc::GemmArgs g = gemm_args(b.x, kMlpIn, m->w1, kMlpIn, R, A.h1, kMlpIn, m->err);
     g.relu = 1;
     g.out_bf = b.a1;
-    g.ldo = kMlpHid;
+    g.ldo = A.h1;
     if (train) {
         g.out_bfT = b.a1T;
         g.ldoT = R;
     }
     if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
-    g = gemm_args(b.a1, kMlpHid, m->w2, kMlpHid, R, kMlpHid, kMlpHid, m->err);
-    g.bias = m->p + kOffB2;
+    g = gemm_args(b.a1, A.h1, m->w2, A.h1, R, A.h2, A.h1, m->err);
+    g.bias = m->p + A.ob2;
     g.relu = 1;
     g.out_bf = b.a2;
-    g.ldo = kMlpHid;
+    g.ldo = A.h2;
     if (train) {
         g.out_bfT = b.a2T;
         g.ldoT = R;
     }
     if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
-    g = gemm_args(b.a2, kMlpHid, m->w3, kMlpHid, R, kMlpHid, kMlpHid, m->err);
-    g.bias = m->p + kOffB3;
+    g = gemm_args(b.a2, A.h2, m->w3, A.h2, R, A.h3, A.h2, m->err);
+    g.bias = m->p + A.ob3;
     g.relu = 1;
-    g.head_w = m->p + kOffW4;
-    g.head_b = m->p + kOffB4;
+    g.head_w = m->p + A.ow4;
+    g.head_b = m->p + A.ob4;
     g.head_y = y;
     if (train) {
         g.out_bf = b.a3;
-        g.ldo = kMlpHid;
+        g.ldo = A.h3;
     }
     if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     return STORM_OK;
@@ -1357,47 +1406,46 @@ int mlp_forward(storm_mlp* m, MlpBuffers& b, const float* theta, int count, int 
 // gradient into m->g, loss into *m->loss.
 int mlp_backward(storm_mlp* m, MlpBuffers& b, const float* target, int count, cudaStream_t s)
 {
+    const MlpArch& A = m->a;
     const int R = (count + tc::kBM - 1) / tc::kBM * tc::kBM;
-    k_mlp_dhead<<<R, kMlpHid, 0, s>>>(b.y, target, count, R, b.a3, m->p, b.dy, b.d3, b.d3T, b.loss_part);
-    k_mlp_head_grad<<<kMlpHid + 2, 256, 0, s>>>(b.dy, b.a3, R, count, b.loss_part, m->g, m->loss);
+    k_mlp_dhead<<<R, A.h3, 0, s>>>(b.y, target, count, R, A, b.a3, m->p, b.dy, b.d3, b.d3T, b.loss_part);
+    k_mlp_head_grad<<<A.h3 + 2, 256, 0, s>>>(b.dy, b.a3, R, count, A, b.loss_part, m->g, m->loss);
     if (cudaGetLastError() != cudaSuccess) return STORM_ERR_CUDA;
     // dW3 = delta3^T a2, db3 = sum delta3
-    const int sp = split_count(R);
-    tc::GemmArgs g = weight_grad(b.d3T, b.a2T, R, sp, kMlpHid, b.part, m->err);
-    if (gemm<kMlpHid>(g, s, sp) != cudaSuccess) return STORM_ERR_CUDA;
-    k_splitk_reduce<<<kMlpHid * kMlpHid / 256, 256, 0, s>>>(b.part, sp, kMlpHid * kMlpHid, m->g + kOffW3);
-    k_mlp_rowsum<<<kMlpHid, 256, 0, s>>>(b.d3T, R, m->g + kOffB3);
+    int rc = weight_grad_into(b.d3T, b.a2T, R, A.h3, A.h2, b.part, m->g + A.oW3, m->err, s);
+    if (rc) return rc;
+    k_mlp_rowsum<<<A.h3, 256, 0, s>>>(b.d3T, R, m->g + A.ob3);
     // delta2 = (delta3 W3) o [a2 > 0]
-    g = gemm_args(b.d3, kMlpHid, m->w3t, kMlpHid, R, kMlpHid, kMlpHid, m->err);
+    tc::GemmArgs g = gemm_args(b.d3, A.h3, m->w3t, A.h3, R, A.h2, A.h3, m->err);
     g.mask = b.a2;
-    g.ldm = kMlpHid;
+    g.ldm = A.h2;
     g.out_bf = b.d2;
-    g.ldo = kMlpHid;
+    g.ldo = A.h2;
     g.out_bfT = b.d2T;
     g.ldoT = R;
     if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     // dW2 = delta2^T a1, db2 = sum delta2
-    g = weight_grad(b.d2T, b.a1T, R, sp, kMlpHid, b.part, m->err);
-    if (gemm<kMlpHid>(g, s, sp) != cudaSuccess) return STORM_ERR_CUDA;
-    k_splitk_reduce<<<kMlpHid * kMlpHid / 256, 256, 0, s>>>(b.part, sp, kMlpHid * kMlpHid, m->g + kOffW2);
-    k_mlp_rowsum<<<kMlpHid, 256, 0, s>>>(b.d2T, R, m->g + kOffB2);
+    rc = weight_grad_into(b.d2T, b.a1T, R, A.h2, A.h1, b.part, m->g + A.oW2, m->err, s);
+    if (rc) return rc;
+    k_mlp_rowsum<<<A.h2, 256, 0, s>>>(b.d2T, R, m->g + A.ob2);
     // delta1 = (delta2 W2) o [a1 > 0]
-    g = gemm_args(b.d2, kMlpHid, m->w2t, kMlpHid, R, kMlpHid, kMlpHid, m->err);
+    g = gemm_args(b.d2, A.h2, m->w2t, A.h2, R, A.h1, A.h2, m->err);
     g.mask = b.a1;
-    g.ldm = kMlpHid;
+    g.ldm = A.h1;
     g.out_bfT = b.d1T;
     g.ldoT = R;
     if (gemm_rw(g, s) != cudaSuccess) return STORM_ERR_CUDA;
     // dW1 = delta1^T x
-    g = weight_grad(b.d1T, b.xT, R, sp, kMlpIn, b.part, m->err);
-    if (gemm<kMlpIn>(g, s, sp) != cudaSuccess) return STORM_ERR_CUDA;
-    k_splitk_reduce<<<kMlpHid * kMlpIn / 256, 256, 0, s>>>(b.part, sp, kMlpHid * kMlpIn, m->g + kOffW1);
+    rc = weight_grad_into(b.d1T, b.xT, R, A.h1, kMlpIn, b.part, m->g + A.oW1, m->err, s);
+    if (rc) return rc;
     return cudaGetLastError() == cudaSuccess ? STORM_OK : STORM_ERR_CUDA;
 }
 
 int mlp_cast(storm_mlp* m, cudaStream_t s)
 {
-    k_mlp_cast<<<(kMlpHid * kMlpHid + 255) / 256, 256, 0, s>>>(m->p, m->w1, m->w2, m->w2t, m->w3, m->w3t);
+    const MlpArch& A = m->a;
+    const int n = std::max(A.h1 * kMlpIn, std::max(A.h2 * A.h1, A.h3 * A.h2));
+    k_mlp_cast<<<(n + 255) / 256, 256, 0, s>>>(m->p, A, m->w1, m->w2, m->w2t, m->w3, m->w3t);
     return cudaGetLastError() == cudaSuccess ? STORM_OK : STORM_ERR_CUDA;
 }
 
@@ -3196,10 +3244,19 @@ const char* storm_mlp_last_error(const storm_mlp* m) { return m ? m->msg.c_str()
 
 int storm_mlp_create(uint64_t seed, void* cuda_stream, storm_mlp** out)
 {
+    return storm_mlp_create_arch(seed, STORM_MLP_DISTANCE, cuda_stream, out);
+}
+
+int storm_mlp_param_count(const storm_mlp* m) { return m ? m->a.count : STORM_ERR_INVALID_ARG; }
+
+int storm_mlp_create_arch(uint64_t seed, int arch, void* cuda_stream, storm_mlp** out)
+{
     if (!out) return STORM_ERR_INVALID_ARG;
     *out = nullptr;
+    if (arch != STORM_MLP_DISTANCE && arch != STORM_MLP_JOINTNERF) return STORM_ERR_INVALID_ARG;
     storm_mlp* m = new (std::nothrow) storm_mlp();
     if (!m) return STORM_ERR_OOM;
+    if (arch == STORM_MLP_JOINTNERF) m->a = mlp_arch(1, 256, 128, 64);
     auto fail_m = [&](int rc) {
         fprintf(stderr, "storm_mlp_create: %s\n", m->msg.c_str());
         mlp_free(m);
@@ -3221,7 +3278,7 @@ int storm_mlp_create(uint64_t seed, void* cuda_stream, storm_mlp** out)
         try_(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking), "stream");
         m->own_stream = rc == STORM_OK;
     }
-    const size_t P = sizeof(float) * kMlpParams;
+    const size_t P = sizeof(float) * m->a.count;
     try_(cudaMalloc(&m->p, P), "params");
     try_(cudaMalloc(&m->g, P), "grad");
     try_(cudaMalloc(&m->m, P), "adam m");
@@ -3238,8 +3295,8 @@ int storm_mlp_create(uint64_t seed, void* cuda_stream, storm_mlp** out)
     try_(cudaMemsetAsync(m->m, 0, P, m->stream), "memset");
     try_(cudaMemsetAsync(m->v, 0, P, m->stream), "memset");
     try_(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream), "memset");
-    k_mlp_init<<<(kMlpParams + 255) / 256, 256, 0, m->stream>>>(
-        m->p, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+    k_mlp_init<<<(m->a.count + 255) / 256, 256, 0, m->stream>>>(
+        m->p, m->a, static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
     try_(cudaGetLastError(), "init");
     if (rc == STORM_OK) rc = mlp_cast(m, m->stream);
     try_(cudaStreamSynchronize(m->stream), "sync");
@@ -3259,7 +3316,7 @@ void storm_mlp_destroy(storm_mlp* m)
 int storm_mlp_get_params(storm_mlp* m, float* params)
 {
     if (!m || !params) return STORM_ERR_INVALID_ARG;
-    MK(cudaMemcpyAsync(params, m->p, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, m->stream));
+    MK(cudaMemcpyAsync(params, m->p, sizeof(float) * m->a.count, cudaMemcpyDeviceToHost, m->stream));
     MK(cudaStreamSynchronize(m->stream));
     return STORM_OK;
 }
@@ -3267,9 +3324,9 @@ int storm_mlp_get_params(storm_mlp* m, float* params)
 int storm_mlp_set_params(storm_mlp* m, const float* params)
 {
     if (!m || !params) return STORM_ERR_INVALID_ARG;
-    for (int i = 0; i < kMlpParams; ++i)
+    for (int i = 0; i < m->a.count; ++i)
         if (!std::isfinite(params[i])) return m->msg = "non-finite parameter", STORM_ERR_INVALID_ARG;
-    MK(cudaMemcpyAsync(m->p, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, m->stream));
+    MK(cudaMemcpyAsync(m->p, params, sizeof(float) * m->a.count, cudaMemcpyHostToDevice, m->stream));
     const int rc = mlp_cast(m, m->stream);
     if (rc) return rc;
     MK(cudaStreamSynchronize(m->stream));
@@ -3297,7 +3354,7 @@ int storm_mlp_loss_grad(storm_mlp* m, const float* theta_dev, const float* targe
     if (!rc) rc = mlp_backward(m, m->buf, target_dev, count, m->stream);
     if (rc) return rc;
     if (loss) MK(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
-    if (grad) MK(cudaMemcpyAsync(grad, m->g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, m->stream));
+    if (grad) MK(cudaMemcpyAsync(grad, m->g, sizeof(float) * m->a.count, cudaMemcpyDeviceToHost, m->stream));
     return mlp_check_err(m);
 }
 
@@ -3350,7 +3407,7 @@ int storm_mlp_train(storm_mlp* m, const float* theta_dev, const float* target_de
             int rc = mlp_forward(m, m->buf, m->th_b, batch, dof, true, nullptr, m->stream);
             if (!rc) rc = mlp_backward(m, m->buf, m->t_b, batch, m->stream);
             if (rc) return rc;
-            k_adam<<<(kMlpParams + 255) / 256, 256, 0, m->stream>>>(m->p, m->g, m->m, m->v, kMlpParams, lr,
+            k_adam<<<(m->a.count + 255) / 256, 256, 0, m->stream>>>(m->p, m->g, m->m, m->v, m->a.count, lr,
                                                                    0.9f, 0.999f, 1e-8f, ++m->t);
             rc = mlp_cast(m, m->stream);
             if (rc) return rc;
@@ -3378,11 +3435,20 @@ int storm_self_distance(storm_handle* h, const float* theta_dev, int count, floa
     return STORM_OK;
 }
 
+int storm_set_surrogate_cost(storm_handle* h, storm_mlp* mlp)
+{
+    const int rc = storm_set_surrogate(h, mlp, 0.0);
+    if (rc) return rc;
+    h->pb.self_direct = mlp ? 1 : 0;
+    return build_graphs(h);
+}
+
 int storm_set_surrogate(storm_handle* h, storm_mlp* mlp, double margin)
 {
     if (!h || std::isnan(margin)) return fail(h, STORM_ERR_INVALID_ARG, "bad argument");
     CK(cudaStreamSynchronize(h->stream));
     h->mlp = mlp;
+    h->pb.self_direct = 0;
     if (mlp) {
         const int rows = h->pb.N * h->pb.H;
         const int R = (rows + tc::kBM - 1) / tc::kBM * tc::kBM;

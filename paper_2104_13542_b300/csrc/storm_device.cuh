@@ -58,8 +58,9 @@ struct Problem {
     const float* halton;     // N x S x d normal noise (Halton sampler only)
     float* mu;               // H x d
     float* sigma;            // d
-    const float* self_pred;  // N x H surrogate self distances (nullable)
+    const float* self_pred;  // N x H surrogate outputs (nullable)
     float self_margin;       // exact self check only where self_pred < self_margin
+    int self_direct;         // 1: self term = max(0, self_pred) (Eq. 13), no exact check
     // pair blocks of frames (la, lb), la < lb, are [lp_begin[t], lp_begin[t + 1]) with
     // t = link_pair_index(la, lb); the blocks are sorted by (la, lb)
     uint16_t lp_begin[kLinkPairs + 1];

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g)
 template <int BN>
 constexpr size_t gemm_smem() { return 2 * (kBM * kKB * 2 + BN * kKB * 2); }
 
-// Forward layers (N = 256): the whole weight matrix B (256 x K, K <= 256) stays
+// Layers with N = BN (64, 128 or 256): the whole weight matrix B (BN x K, K <= 256) stays
 // resident in shared memory, one persistent CTA per SM walks the 128-row tiles
 // of A through a kStagesRW-deep cp.async pipeline, and one elected thread
 // issues the tcgen05.mma of each K block.  The accumulator is double-buffered
@@ -264,16 +264,17 @@ constexpr size_t gemm_smem() { return 2 * (kBM * kKB * 2 + BN * kKB * 2); }
 // of its MMAs arrives.  Same epilogue as k_gemm.
 constexpr int kStagesRW = 4;
 
-__host__ __device__ constexpr size_t gemm_rw_smem(int K)
+__host__ __device__ constexpr size_t gemm_rw_smem(int BN, int K)
 {
-    return static_cast<size_t>(256) * K * 2 + static_cast<size_t>(kStagesRW) * kBM * (K < kKB ? K : kKB) * 2;
+    return static_cast<size_t>(BN) * K * 2 + static_cast<size_t>(kStagesRW) * kBM * (K < kKB ? K : kKB) * 2;
 }
 
+template <int BN>
 __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, int row, int warp)
 {
     float yacc = 0.f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < 256; c0 += 8) {
+    for (int c0 = 0; c0 < BN; c0 += 8) {
         uint32_t r[8];
         const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
         asm volatile(
@@ -314,22 +315,24 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, 
     if (g.head_w) g.head_y[row] = *g.head_b + yacc;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
 {
+    constexpr uint32_t kCols = 2 * BN;  // two accumulators of BN columns
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[kStagesRW];
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = g.K, kb = K < kKB ? K : kKB, nk = K / kb;
-    unsigned char* sW = smem;                                     // nk blocks of 256 x kb
-    unsigned char* sA = smem + static_cast<size_t>(256) * K * 2;  // kStagesRW stages of 128 x kb
-    const int stageA = kBM * kb * 2, blockW = 256 * kb * 2;
+    unsigned char* sW = smem;                                    // nk blocks of BN x kb
+    unsigned char* sA = smem + static_cast<size_t>(BN) * K * 2;  // kStagesRW stages of 128 x kb
+    const int stageA = kBM * kb * 2, blockW = BN * kb * 2;
     const uint32_t sbo = (kb / 8) * 128;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(512)
+                     "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -345,8 +348,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
     // the weights, once (first cp.async group): block j holds B[:, j*kb .. (j+1)*kb)
     {
         const int chunks = kb / 8;
-        for (int c = threadIdx.x; c < nk * 256 * chunks; c += blockDim.x) {
-            const int j = c / (256 * chunks), rem = c - j * 256 * chunks;
+        for (int c = threadIdx.x; c < nk * BN * chunks; c += blockDim.x) {
+            const int j = c / (BN * chunks), rem = c - j * BN * chunks;
             const int r = rem / chunks, kg = rem - r * chunks;
             cp_async16(smem_u32(sW + j * blockW) + (r >> 3) * sbo + (r & 7) * 16 + kg * 128,
                        g.B + static_cast<size_t>(r) * g.ldb + j * kb + kg * 8);
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
     auto epilogue = [&](int item) {  // item is the last K block of its tile
         const int tl = item / nk;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        gemm_epilogue(g, tmem + (tl & 1) * 256, (bx + tl * gx) * kBM + warp * 32 + lane, warp);
+        gemm_epilogue<BN>(g, tmem + (tl & 1) * BN, (bx + tl * gx) * kBM + warp * 32 + lane, warp);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     };
     int issued = 0;
@@ -389,8 +392,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int j = c % nk;
-            const uint32_t idesc = instr_desc(kBM, 256);
-            const uint32_t d = tmem + ((c / nk) & 1) * 256;
+            const uint32_t idesc = instr_desc(kBM, BN);
+            const uint32_t d = tmem + ((c / nk) & 1) * BN;
             const uint32_t a0 = smem_u32(sA + (c % kStagesRW) * stageA), b0 = smem_u32(sW + j * blockW);
             for (int kk = 0; kk < kb / 16; ++kk) {
                 const uint64_t da = smem_desc(a0 + kk * 256, 128, sbo);
@@ -433,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
                      : "memory");
 }
 
@@ -441,18 +444,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
 
 // ---------------------------------------------------------------- MLP helpers
 
-constexpr int kMlpIn = 16, kMlpHid = 256;
+constexpr int kMlpIn = 16, kMlpHid = 256;  // input width; widest hidden layer
 constexpr int kSplitMax = 74;  // split-K of a weight gradient: 2 x 74 CTAs cover the 148 SMs
 constexpr int kMlpParams = kMlpHid * kMlpIn + 2 * (kMlpHid * kMlpHid + kMlpHid) + kMlpHid + 1;
 
-// Offsets in the flat FP32 parameter vector: W1 | W2 | b2 | W3 | b3 | w4 | b4.
-constexpr int kOffW1 = 0, kOffW2 = kOffW1 + kMlpHid * kMlpIn, kOffB2 = kOffW2 + kMlpHid * kMlpHid,
-              kOffW3 = kOffB2 + kMlpHid, kOffB3 = kOffW3 + kMlpHid * kMlpHid,
-              kOffW4 = kOffB3 + kMlpHid, kOffB4 = kOffW4 + kMlpHid;
+// Surrogate network x (16) -> h1 -> h2 -> h3 -> 1 (ReLU hidden, linear output,
+// no first-layer bias: the encoding carries a constant one).  Flat FP32
+// parameters W1 (h1 x 16) | W2 (h2 x h1) | b2 | W3 (h3 x h2) | b3 | w4 | b4.
+// Encodings: 0 x_j = theta_j / 3, x_7 = 1; 1 (jointNERF, Sec. 4.2)
+// x_j = sin theta_j, x_{7+j} = cos theta_j, x_14 = 1.
+struct MlpArch {
+    int enc, h1, h2, h3;
+    int oW1, oW2, ob2, oW3, ob3, ow4, ob4, count;
+};
 
-// Inputs: x_j = theta_j / 3 for the joints, x_7 = 1 (first-layer bias), rest 0.
-// Rows count..rows_pad-1 are zero.  x: rows_pad x 16; xT (nullable): 16 x rows_pad.
-__global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof, int rows_pad,
+__host__ __device__ inline MlpArch mlp_arch(int enc, int h1, int h2, int h3)
+{
+    MlpArch a{enc, h1, h2, h3, 0, 0, 0, 0, 0, 0, 0, 0};
+    a.oW1 = 0;
+    a.oW2 = a.oW1 + h1 * kMlpIn;
+    a.ob2 = a.oW2 + h2 * h1;
+    a.oW3 = a.ob2 + h2;
+    a.ob3 = a.oW3 + h3 * h2;
+    a.ow4 = a.ob3 + h3;
+    a.ob4 = a.ow4 + h3;
+    a.count = a.ob4 + 1;
+    return a;
+}
+
+// Inputs of the encoding; rows count..rows_pad-1 are zero.
+// x: rows_pad x 16; xT (nullable): 16 x rows_pad.
+__global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof, int rows_pad, int enc,
                              __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ xT)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -461,8 +483,18 @@ __global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof
 #pragma unroll
     for (int i = 0; i < kMlpIn; ++i) v[i] = 0.f;
     if (r < count) {
-        for (int j = 0; j < dof && j < 7; ++j) v[j] = theta[static_cast<size_t>(r) * dof + j] / 3.f;
-        v[7] = 1.f;
+        if (enc == 1) {
+            for (int j = 0; j < dof && j < 7; ++j) {
+                float sj, cj;
+                sincosf(theta[static_cast<size_t>(r) * dof + j], &sj, &cj);
+                v[j] = sj;
+                v[7 + j] = cj;
+            }
+            v[14] = 1.f;
+        } else {
+            for (int j = 0; j < dof && j < 7; ++j) v[j] = theta[static_cast<size_t>(r) * dof + j] / 3.f;
+            v[7] = 1.f;
+        }
     }
 #pragma unroll
     for (int i = 0; i < kMlpIn; ++i) {
@@ -472,48 +504,55 @@ __global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof
     }
 }
 
-// FP32 master weights -> BF16 operands: W1, W2, W3 and the transposes W2^T, W3^T.
-__global__ void k_mlp_cast(const float* __restrict__ p, __nv_bfloat16* __restrict__ w1,
+// FP32 master weights -> BF16 operands: W1, W2, W3 and the transposes W2^T (h1 x h2), W3^T (h2 x h3).
+__global__ void k_mlp_cast(const float* __restrict__ p, MlpArch A, __nv_bfloat16* __restrict__ w1,
                            __nv_bfloat16* __restrict__ w2, __nv_bfloat16* __restrict__ w2t,
                            __nv_bfloat16* __restrict__ w3, __nv_bfloat16* __restrict__ w3t)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kMlpHid * kMlpIn) w1[i] = __float2bfloat16_rn(p[kOffW1 + i]);
-    if (i < kMlpHid * kMlpHid) {
-        const int n = i / kMlpHid, k = i - n * kMlpHid;
-        const __nv_bfloat16 a = __float2bfloat16_rn(p[kOffW2 + i]);
-        const __nv_bfloat16 b = __float2bfloat16_rn(p[kOffW3 + i]);
+    if (i < A.h1 * kMlpIn) w1[i] = __float2bfloat16_rn(p[A.oW1 + i]);
+    if (i < A.h2 * A.h1) {
+        const int n = i / A.h1, k = i - n * A.h1;
+        const __nv_bfloat16 a = __float2bfloat16_rn(p[A.oW2 + i]);
         w2[i] = a;
+        w2t[k * A.h2 + n] = a;
+    }
+    if (i < A.h3 * A.h2) {
+        const int n = i / A.h2, k = i - n * A.h2;
+        const __nv_bfloat16 b = __float2bfloat16_rn(p[A.oW3 + i]);
         w3[i] = b;
-        w2t[k * kMlpHid + n] = a;
-        w3t[k * kMlpHid + n] = b;
+        w3t[k * A.h3 + n] = b;
     }
 }
 
 // He-uniform initialisation from the Philox stream (tag 1): W ~ U(-sqrt(6/fan_in),
-// sqrt(6/fan_in)), biases 0; the first layer's bias column (input 7) starts at 0.
-__global__ void k_mlp_init(float* __restrict__ p, uint32_t seed_lo, uint32_t seed_hi)
+// sqrt(6/fan_in)) with fan_in the number of encoded features + 1 for the first
+// layer (whose bias column and padding start at 0), biases 0.
+__global__ void k_mlp_init(float* __restrict__ p, MlpArch A, uint32_t seed_lo, uint32_t seed_hi)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kMlpParams) return;
+    if (i >= A.count) return;
     const uint4 r = storm::philox4x32_10(make_uint4(static_cast<uint32_t>(i), 0u, 0u, 1u), seed_lo, seed_hi);
     const float u = 2.f * storm::bits_to_unit(r.x) - 1.f;
+    const int feats = A.enc == 1 ? 14 : 7;
     float v = 0.f;
-    if (i < kOffW2) {
-        v = ((i % kMlpIn) == 7 || (i % kMlpIn) > 7) ? 0.f : u * sqrtf(6.f / 8.f);
-    } else if (i < kOffB2 || (i >= kOffW3 && i < kOffB3)) {
-        v = u * sqrtf(6.f / kMlpHid);
-    } else if (i >= kOffW4 && i < kOffB4) {
-        v = u * sqrtf(6.f / kMlpHid);
+    if (i < A.oW2) {
+        v = (i % kMlpIn) < feats ? u * sqrtf(6.f / static_cast<float>(feats + 1)) : 0.f;
+    } else if (i < A.ob2) {
+        v = u * sqrtf(6.f / static_cast<float>(A.h1));
+    } else if (i >= A.oW3 && i < A.ob3) {
+        v = u * sqrtf(6.f / static_cast<float>(A.h2));
+    } else if (i >= A.ow4 && i < A.ob4) {
+        v = u * sqrtf(6.f / static_cast<float>(A.h3));
     }
     p[i] = v;
 }
 
 // Output layer gradient of the mean squared error: r = y - t, dy = 2 r / count,
 // delta3 = dy w4 o [a3 > 0] (BF16, row-major and transposed); rows >= count get 0.
-// loss_part[blockIdx.x] = sum of r^2 over the block's rows (fixed order).
+// One block of h3 threads per row; loss_part[row] = r^2.
 __global__ void __launch_bounds__(256)
-k_mlp_dhead(const float* __restrict__ y, const float* __restrict__ t, int count, int rows_pad,
+k_mlp_dhead(const float* __restrict__ y, const float* __restrict__ t, int count, int rows_pad, MlpArch A,
             const __nv_bfloat16* __restrict__ a3, const float* __restrict__ p,
             float* __restrict__ dy, __nv_bfloat16* __restrict__ d3, __nv_bfloat16* __restrict__ d3T,
             float* __restrict__ loss_part)
@@ -522,9 +561,9 @@ k_mlp_dhead(const float* __restrict__ y, const float* __restrict__ t, int count,
     const float r = (b < count) ? y[b] - t[b] : 0.f;
     const float g = 2.f * r / static_cast<float>(count);
     if (n == 0) dy[b] = g;
-    const float a = __bfloat162float(a3[static_cast<size_t>(b) * kMlpHid + n]);
-    const __nv_bfloat16 v = __float2bfloat16_rn(a > 0.f ? g * p[kOffW4 + n] : 0.f);
-    d3[static_cast<size_t>(b) * kMlpHid + n] = v;
+    const float a = __bfloat162float(a3[static_cast<size_t>(b) * A.h3 + n]);
+    const __nv_bfloat16 v = __float2bfloat16_rn(a > 0.f ? g * p[A.ow4 + n] : 0.f);
+    d3[static_cast<size_t>(b) * A.h3 + n] = v;
     d3T[static_cast<size_t>(n) * rows_pad + b] = v;
     if (n == 0) loss_part[b] = r * r;
 }
@@ -543,23 +582,23 @@ k_mlp_rowsum(const __nv_bfloat16* __restrict__ rows, int rows_pad, float* __rest
 }
 
 // dw4[n] = sum_b dy_b a3[b][n]; db4 = sum_b dy_b; loss = sum_b r_b^2 / count.
+// Grid h3 + 2.
 __global__ void __launch_bounds__(256)
-k_mlp_head_grad(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ a3, int rows_pad,
-                int count, const float* __restrict__ loss_part, float* __restrict__ grad,
-                float* __restrict__ loss)
+k_mlp_head_grad(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ a3, int rows_pad, int count,
+                MlpArch A, const float* __restrict__ loss_part, float* __restrict__ grad, float* __restrict__ loss)
 {
     __shared__ float sh[32];
     const int n = blockIdx.x;
     float acc = 0.f;
-    if (n < kMlpHid) {
+    if (n < A.h3) {
         for (int b = threadIdx.x; b < rows_pad; b += blockDim.x)
-            acc = fmaf(dy[b], __bfloat162float(a3[static_cast<size_t>(b) * kMlpHid + n]), acc);
+            acc = fmaf(dy[b], __bfloat162float(a3[static_cast<size_t>(b) * A.h3 + n]), acc);
         acc = block_sum(acc, sh);
-        if (threadIdx.x == 0) grad[kOffW4 + n] = acc;
-    } else if (n == kMlpHid) {
+        if (threadIdx.x == 0) grad[A.ow4 + n] = acc;
+    } else if (n == A.h3) {
         for (int b = threadIdx.x; b < rows_pad; b += blockDim.x) acc += dy[b];
         acc = block_sum(acc, sh);
-        if (threadIdx.x == 0) grad[kOffB4] = acc;
+        if (threadIdx.x == 0) grad[A.ob4] = acc;
     } else {
         for (int b = threadIdx.x; b < rows_pad; b += blockDim.x) acc += loss_part[b];
         acc = block_sum(acc, sh);

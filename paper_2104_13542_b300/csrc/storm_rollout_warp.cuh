@@ -519,7 +519,8 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         // (register tests over the compile-time list of pairs), then their
         // pair blocks exactly; then the leftover pairs
         float dself = 0.f;
-        const bool do_self = valid && !(pred && pred[gi] >= pb.self_margin);
+        const bool do_self = valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
+        if (valid && pred && pb.self_direct) dself = fmaxf(0.f, pred[gi]);  // Eq. 13's learned term
         uint32_t lp_hit = 0u;  // bit t: frame pair t has blocks and its bounds overlap
         if (do_self) {
 #pragma unroll
