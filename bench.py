@@ -197,7 +197,16 @@ def run_gpu(args, rank, world_size):
     goals = goals_for(ctl, wl.robot, args.seed + rank, 5)
     # the library's autotuner picks the rollout launch shape for this workload
     ctl.step(state0.astype(np.float32), goals[0])
-    tuned_us = ctl.autotune()
+    if args.launch == "auto":
+        tuned_us = ctl.autotune()
+    else:  # a fixed rollout shape (profiling runs: the tuner's timings are not meaningful under a profiler)
+        kind, _, shape = args.launch.partition(":")
+        if kind == "warp":
+            ctl.set_launch_warp(int(shape))
+        else:
+            ppc, threads = (int(x) for x in shape.split(","))
+            ctl.set_launch(ppc, threads)
+        tuned_us = None
     ctl.reset()
 
     # ---------------- device-resident timing (value)
@@ -580,6 +589,8 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--launch", default="auto",
+                    help="rollout launch shape: auto (autotuned), warp:W (W warps per CTA) or cta:P,T")
     ap.add_argument("--ablation", action="store_true",
                     help="run the closed-loop sampling ablation instead of the benchmark")
     args = ap.parse_args()

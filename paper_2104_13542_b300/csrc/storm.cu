@@ -708,13 +708,37 @@ __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
     bi = shi[0];
 }
 
+// Block-wide sums of two values (fixed order: butterfly per warp, then warp 0
+// over the warps); results in every thread.
+__device__ __forceinline__ float2 block_sum2(float a, float b, float2* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    __syncthreads();
+    if (lane == 0) sh[wid] = make_float2(a, b);
+    __syncthreads();
+    if (wid == 0) {
+        float2 x = lane < nw ? sh[lane] : make_float2(0.f, 0.f);
+        x.x = warp_sum(x.x);
+        x.y = warp_sum(x.y);
+        if (lane == 0) sh[32] = x;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
 // update_distribution (Eqs. 4-6), one CTA per horizon step h.  Every CTA
-// forms the min-shifted exponential weights of all N particles (Eq. 6) in
-// shared memory, then the weighted mean of row h (Eq. 4) and row h's weighted
-// squared deviations about the new mean.  The last CTA to finish sums those
-// over h in fixed order into the per-joint sigma (Eq. 5) and, at the last
-// iteration of a step, writes next_command and advances the step counter.
-// All reductions run in a fixed order: results are bitwise reproducible.
+// forms the min-shifted exponential weights of all N particles (Eq. 6), then
+// the weighted mean of row h (Eq. 4) and row h's weighted squared deviations
+// about the new mean.  Each thread loads its particles' costs and row-h
+// controls once, up front (kUpdKeep particles in registers; any beyond are
+// re-read), so the L2 round trips overlap.  The last CTA to finish sums the
+// deviations over h in fixed order into the per-joint sigma (Eq. 5) and, at
+// the last iteration of a step, writes next_command and advances the step
+// counter.  All reductions run in a fixed order: bitwise reproducible.
+constexpr int kUpdKeep = 2;
+
 __device__ __forceinline__ void update_row(const Problem& pb, const float* __restrict__ C,
                                            const float* __restrict__ u, float* __restrict__ weights_out,
                                            StepState* st, float* __restrict__ cmd_out, int finalize,
@@ -723,16 +747,37 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
     extern __shared__ __align__(16) float s_w[];  // N weights
     __shared__ float s_redf[32];
     __shared__ int s_redi[32];
+    __shared__ float2 s_red2[33];
     __shared__ float s_acc[kMaxDof][33];
     __shared__ float s_mu[kMaxDof];
     __shared__ int s_last;
     const int N = pb.N, d = pb.d, O = pb.H * pb.d;
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
 
+    // ---- this thread's costs and row-h controls (and the old mean of row h), loaded together
+    const float mu_old = tid < d ? pb.mu[h * d + tid] : 0.f;
+    float cv[kUpdKeep], uv[kUpdKeep][kMaxDof];
+#pragma unroll
+    for (int k = 0; k < kUpdKeep; ++k) {
+        const int n = tid + k * T;
+        cv[k] = n < N ? C[n] : INFINITY;
+        const float* un = u + static_cast<size_t>(n < N ? n : 0) * O + h * d;
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) uv[k][j] = (n < N && j < d) ? un[j] : 0.f;
+    }
+
     // ---- min finite cost and its lowest index
     float bv = INFINITY;
     int bi = INT_MAX;
-    for (int n = tid; n < N; n += T) {
+#pragma unroll
+    for (int k = 0; k < kUpdKeep; ++k) {
+        const int n = tid + k * T;
+        if (n < N && isfinite(cv[k]) && cv[k] < bv) {
+            bv = cv[k];
+            bi = n;
+        }
+    }
+    for (int n = tid + kUpdKeep * T; n < N; n += T) {
         const float c = C[n];
         if (isfinite(c) && c < bv) {
             bv = c;
@@ -747,22 +792,31 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
     float s = 1.f, sc = 0.f;
     if (!degenerate) {
         // ---- weights, Eq. 6
-        float ls = 0.f, lsc = 0.f;
-        for (int n = tid; n < N; n += T) {
+        auto weight = [&](int n, float c) {
+            if (!isfinite(c)) return 0.f;
+            if (pb.beta > 0.f) return expf(-(c - m) / pb.beta);
+            return (n == arg) ? 1.f : 0.f;
+        };
+        float ls = 0.f, lsc = 0.f, wk[kUpdKeep];
+#pragma unroll
+        for (int k = 0; k < kUpdKeep; ++k) {
+            const int n = tid + k * T;
+            const float w = n < N ? weight(n, cv[k]) : 0.f;
+            wk[k] = w;
+            if (n < N) s_w[n] = w;
+            ls += w;
+            if (w > 0.f) lsc = fmaf(w, cv[k], lsc);
+        }
+        for (int n = tid + kUpdKeep * T; n < N; n += T) {
             const float c = C[n];
-            float w;
-            if (!isfinite(c))
-                w = 0.f;
-            else if (pb.beta > 0.f)
-                w = expf(-(c - m) / pb.beta);
-            else
-                w = (n == arg) ? 1.f : 0.f;
+            const float w = weight(n, c);
             s_w[n] = w;
             ls += w;
             if (w > 0.f) lsc = fmaf(w, c, lsc);
         }
-        s = block_sum(ls, s_redf);
-        sc = block_sum(lsc, s_redf);
+        const float2 tot = block_sum2(ls, lsc, s_red2);
+        s = tot.x;
+        sc = tot.y;
         const float inv_s = 1.f / s;
         if (weights_out && h == 0)
             for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * inv_s;
@@ -771,7 +825,12 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
         float acc[kMaxDof];
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) acc[j] = 0.f;
-        for (int n = tid; n < N; n += T) {
+#pragma unroll
+        for (int k = 0; k < kUpdKeep; ++k)
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j)
+                if (j < d) acc[j] = fmaf(wk[k], uv[k][j], acc[j]);
+        for (int n = tid + kUpdKeep * T; n < N; n += T) {
             const float w = s_w[n];
             const float* un = u + static_cast<size_t>(n) * O + h * d;
 #pragma unroll
@@ -789,7 +848,7 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
         if (tid < d) {
             float a = 0.f;
             for (int k = 0; k < (T >> 5); ++k) a += s_acc[tid][k];
-            const float mnew = (1.f - pb.alpha_mu) * pb.mu[h * d + tid] + pb.alpha_mu * (a * inv_s);
+            const float mnew = (1.f - pb.alpha_mu) * mu_old + pb.alpha_mu * (a * inv_s);
             s_mu[tid] = mnew;
             pb.mu[h * d + tid] = mnew;  // row h belongs to this CTA alone
         }
@@ -798,7 +857,15 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
         // ---- weighted squared deviation of row h about the new mean, Eq. 5
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) acc[j] = 0.f;
-        for (int n = tid; n < N; n += T) {
+#pragma unroll
+        for (int k = 0; k < kUpdKeep; ++k)
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j)
+                if (j < d) {
+                    const float e = uv[k][j] - s_mu[j];
+                    acc[j] = fmaf(wk[k] * e, e, acc[j]);
+                }
+        for (int n = tid + kUpdKeep * T; n < N; n += T) {
             const float w = s_w[n];
             const float* un = u + static_cast<size_t>(n) * O + h * d;
 #pragma unroll
@@ -840,10 +907,14 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
         if (weights_out)
             for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
     } else {
+        // the rows' deviations in one parallel round of loads, then summed in fixed order
+        __shared__ float s_var[STORM_MAX_H * kMaxDof];
+        for (int i = tid; i < pb.H * d; i += T) s_var[i] = __ldcg(scr->var + i);
+        __syncthreads();
         if (tid < d) {
             const int j = tid;
             float v = 0.f;
-            for (int hh = 0; hh < pb.H; ++hh) v += __ldcg(scr->var + hh * d + j);
+            for (int hh = 0; hh < pb.H; ++hh) v += s_var[hh * d + j];
             v = v / s / static_cast<float>(pb.H);
             const float sg = pb.sigma[j];
             float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;

@@ -15,7 +15,7 @@ namespace storm {
 constexpr int kMaxDof = 7;
 constexpr int kThreads = 256;        // default rollout CTA size
 constexpr int kMaxThreads = 512;     // largest rollout CTA size the tuner may pick
-constexpr int kUpdateThreads = 256;  // distribution-update CTA size (one CTA per horizon step)
+constexpr int kUpdateThreads = 512;  // distribution-update CTA size (one CTA per horizon step)
 constexpr int kLinkPairs = (kMaxDof + 1) * kMaxDof / 2;  // frame pairs (la < lb) of a chain
 
 // Position of frame pair (la, lb), la < lb <= kMaxDof, in lexicographic order.
