@@ -203,6 +203,8 @@ def run_gpu(args, rank, world_size):
         kind, _, shape = args.launch.partition(":")
         if kind == "warp":
             ctl.set_launch_warp(int(shape))
+        elif kind == "pair":
+            ctl.set_launch_warp_pair(int(shape))
         else:
             ppc, threads = (int(x) for x in shape.split(","))
             ctl.set_launch(ppc, threads)
@@ -590,7 +592,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--launch", default="auto",
-                    help="rollout launch shape: auto (autotuned), warp:W (W warps per CTA) or cta:P,T")
+                    help="rollout launch shape: auto (autotuned), warp:W (W warps per CTA), pair:W (W warp "
+                         "pairs per CTA) or cta:P,T")
     ap.add_argument("--ablation", action="store_true",
                     help="run the closed-loop sampling ablation instead of the benchmark")
     args = ap.parse_args()

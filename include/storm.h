@@ -275,9 +275,13 @@ int storm_set_ball(storm_handle* h, const float* ball_pos_vel);
  *                   with a CTA barrier between phases;
  *   STORM_MAP_WARP  a warp takes one particle (or 2 / 4 of them when H <= 16
  *                   / 8), one lane per step (two steps per lane when H > 32),
- *                   with warp-level synchronisation only; the default. */
+ *                   with warp-level synchronisation only; the default;
+ *   STORM_MAP_WARP_PAIR  the same with two warps per particle group: one for
+ *                   the controls and the non-collision costs, one for world
+ *                   and self collision, meeting once per step slot. */
 #define STORM_MAP_CTA 0
 #define STORM_MAP_WARP 1
+#define STORM_MAP_WARP_PAIR 2
 
 /* CTA mapping and its shape: particles per CTA (1..N) and threads per CTA (a
  * multiple of 32 in 64..512).  Re-captures the step graph.  Errors:
@@ -287,9 +291,11 @@ int storm_set_launch(storm_handle* h, int particles_per_cta, int threads_per_cta
 /* Warp mapping with 1..8 warps per CTA.  Re-captures the step graph.  Errors:
  * INVALID_ARG when out of range or when the plan does not fit a CTA. */
 int storm_set_launch_warp(storm_handle* h, int warps_per_cta);
+/* Warp-pair mapping with 1..4 pairs per CTA.  Errors as storm_set_launch_warp. */
+int storm_set_launch_warp_pair(storm_handle* h, int pairs_per_cta);
 /* Shape of the active mapping: particles and threads per CTA. */
 int storm_get_launch(const storm_handle* h, int* particles_per_cta, int* threads_per_cta);
-/* STORM_MAP_CTA or STORM_MAP_WARP; INVALID_ARG for a NULL handle. */
+/* STORM_MAP_CTA, STORM_MAP_WARP or STORM_MAP_WARP_PAIR; INVALID_ARG for a NULL handle. */
 int storm_get_launch_mapping(const storm_handle* h);
 
 /* Tracing: with trace_dev (device, 7 x uint64) set, thread 0 of rollout CTA 0
@@ -312,7 +318,7 @@ int storm_set_broadphase(storm_handle* h, int on);
  * generate_rollouts) with CUDA events on its stream for every candidate shape
  * -- CTA mapping with particles per CTA 1, 2, 3, 4, 6, 8, 12, 16 (at most N
  * and 512/H) x threads 128, 256, 512, warp mapping with 1, 2, 4, 8 warps per
- * CTA -- on the state and goal of the handle's input buffers (call it after a
+ * CTA, pair mapping with 1, 2, 4 pairs per CTA -- on the state and goal of the handle's input buffers (call it after a
  * first step), keeps the fastest and re-captures the step graph.  best_us (nullable) receives the median time of the chosen
  * shape.  Waits. */
 int storm_autotune(storm_handle* h, float* best_us);

@@ -1534,7 +1534,7 @@ struct storm_handle {
     int grid = 0;
     int threads = kThreads;  // rollout CTA size (CTA-wide mapping)
     int mapping = STORM_MAP_WARP;  // rollout work mapping
-    int wpc = 2;                   // warps per CTA (warp mapping)
+    int wpc = 2;                   // warps (warp mapping) or warp pairs (pair mapping) per CTA
     size_t warp_smem = 0;          // its dynamic shared memory
     int warp_grid = 0;
     // device allocations
@@ -1745,8 +1745,11 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
     Problem pb = h->pb;
     if (exact_self) pb.self_pred = nullptr;
     if (h->mapping == STORM_MAP_WARP)
-        k_rollout_warp<<<h->warp_grid, h->wpc * 32, h->warp_smem, s>>>(pb, out, state, goal, h->d_st,
-                                                                      step_override, iter, front_only);
+        k_rollout_warp<false><<<h->warp_grid, h->wpc * 32, h->warp_smem, s>>>(pb, out, state, goal, h->d_st,
+                                                                             step_override, iter, front_only);
+    else if (h->mapping == STORM_MAP_WARP_PAIR)
+        k_rollout_warp<true><<<h->warp_grid, h->wpc * 64, h->warp_smem, s>>>(pb, out, state, goal, h->d_st,
+                                                                            step_override, iter, front_only);
     else
         k_rollout<<<h->grid, h->threads, h->rollout_smem, s>>>(pb, out, state, goal, h->d_st, step_override,
                                                              iter, front_only);
@@ -1817,8 +1820,11 @@ int allow_smem(storm_handle* h)
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     cudaFuncAttributes ra, ua, aa, wa;
     CK(cudaFuncGetAttributes(&ra, k_rollout));
-    CK(cudaFuncGetAttributes(&wa, k_rollout_warp));
-    CK(cudaFuncSetAttribute(k_rollout_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<false>));
+    CK(cudaFuncSetAttribute(k_rollout_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(wa.sharedSizeBytes)));
+    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<true>));
+    CK(cudaFuncSetAttribute(k_rollout_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             optin - static_cast<int>(wa.sharedSizeBytes)));
     CK(cudaFuncGetAttributes(&ua, k_update));
     CK(cudaFuncGetAttributes(&aa, k_adjoint));
@@ -2447,9 +2453,9 @@ int storm_set_broadphase(storm_handle* h, int on)
 int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
 {
     if (!h) return STORM_ERR_INVALID_ARG;
-    if (h->mapping == STORM_MAP_WARP) {
+    if (h->mapping == STORM_MAP_WARP || h->mapping == STORM_MAP_WARP_PAIR) {
         if (ppc) *ppc = h->wpc * warp_plan(h->pb).PW;
-        if (threads) *threads = h->wpc * 32;
+        if (threads) *threads = h->wpc * (h->mapping == STORM_MAP_WARP_PAIR ? 64 : 32);
     } else {
         if (ppc) *ppc = h->pb.ppc;
         if (threads) *threads = h->threads;
@@ -2459,15 +2465,16 @@ int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
 
 int storm_get_launch_mapping(const storm_handle* h) { return h ? h->mapping : STORM_ERR_INVALID_ARG; }
 
-static int set_launch_warp_impl(storm_handle* h, int wpc, bool rebuild)
+static int set_launch_warp_impl(storm_handle* h, int wpc, bool rebuild, bool pair = false)
 {
-    if (wpc < 1 || wpc > kWarpMaxWarps) return fail(h, STORM_ERR_INVALID_ARG, "warps per CTA out of range");
+    if (wpc < 1 || wpc > (pair ? kWarpMaxWarps / 2 : kWarpMaxWarps))
+        return fail(h, STORM_ERR_INVALID_ARG, "warps per CTA out of range");
     const WarpPlan wp = warp_plan(h->pb);
     const size_t bytes = sizeof(float) * size_t(wp.floats) * wpc;
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (bytes > size_t(optin)) return fail(h, STORM_ERR_INVALID_ARG, "launch shape needs too much shared memory");
-    h->mapping = STORM_MAP_WARP;
+    h->mapping = pair ? STORM_MAP_WARP_PAIR : STORM_MAP_WARP;
     h->wpc = wpc;
     h->warp_smem = bytes;
     h->warp_grid = (h->pb.N + wp.PW * wpc - 1) / (wp.PW * wpc);
@@ -2479,6 +2486,13 @@ int storm_set_launch_warp(storm_handle* h, int warps_per_cta)
     if (!h) return STORM_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(h->stream));
     return set_launch_warp_impl(h, warps_per_cta, true);
+}
+
+int storm_set_launch_warp_pair(storm_handle* h, int pairs_per_cta)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    return set_launch_warp_impl(h, pairs_per_cta, true, true);
 }
 
 static int set_launch_impl(storm_handle* h, int ppc, int threads, bool rebuild)
@@ -2513,6 +2527,7 @@ int storm_autotune(storm_handle* h, float* best_us)
     const int ppcs[] = {1, 2, 3, 4, 6, 8, 12, 16};
     const int ths[] = {128, 256, 512};
     const int wpcs[] = {1, 2, 4, 8};
+    const int pairs[] = {1, 2, 4};
     const int old_map = h->mapping, old_ppc = h->pb.ppc, old_threads = h->threads, old_wpc = h->wpc;
     float best = INFINITY;
     int best_map = old_map, best_ppc = old_ppc, best_threads = old_threads, best_wpc = old_wpc;
@@ -2564,13 +2579,24 @@ int storm_autotune(storm_handle* h, float* best_us)
             best_wpc = w;
         }
     }
+    for (int w : pairs) {
+        if (rc) break;
+        if (set_launch_warp_impl(h, w, false, true) != STORM_OK) continue;
+        const float med = measure();
+        if (rc) break;
+        if (med < best) {
+            best = med;
+            best_map = STORM_MAP_WARP_PAIR;
+            best_wpc = w;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->err = "no error";  // shapes that did not fit are not errors of the handle
     if (rc) {
-        if (old_map == STORM_MAP_WARP) {
+        if (old_map != STORM_MAP_CTA) {
             set_launch_impl(h, old_ppc, old_threads, false);
-            set_launch_warp_impl(h, old_wpc, true);
+            set_launch_warp_impl(h, old_wpc, true, old_map == STORM_MAP_WARP_PAIR);
         } else {
             set_launch_warp_impl(h, old_wpc, false);
             set_launch_impl(h, old_ppc, old_threads, true);
@@ -2578,9 +2604,9 @@ int storm_autotune(storm_handle* h, float* best_us)
         return rc;
     }
     if (best_us) *best_us = best;
-    if (best_map == STORM_MAP_WARP) {
+    if (best_map != STORM_MAP_CTA) {
         set_launch_impl(h, best_ppc, best_threads, false);  // keep the CTA-mapping shape consistent
-        return set_launch_warp_impl(h, best_wpc, true);
+        return set_launch_warp_impl(h, best_wpc, true, best_map == STORM_MAP_WARP_PAIR);
     }
     set_launch_warp_impl(h, best_wpc, false);
     return set_launch_impl(h, best_ppc, best_threads, true);

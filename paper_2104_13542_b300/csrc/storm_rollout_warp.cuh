@@ -11,6 +11,12 @@
 // changes is the work schedule: no CTA barriers, Jacobian and bounding-sphere
 // centres in registers, and world obstacles culled once per warp against the
 // axis-aligned box enclosing every link bound of the warp's items.
+//
+// The pair variant (kPair) gives each particle group two warps: warp A draws
+// the controls and integrates them, then both run FK; A takes the pose,
+// joint, end-effector and manipulability terms while B takes world and self
+// collision, and the two meet at one named barrier per step slot.  The
+// critical path is then the longer branch, not their sum.
 #pragma once
 
 // Per-warp shared-memory plan (float offsets).
@@ -22,7 +28,8 @@ struct WarpPlan {
     int u, th, thd;  // PW x H x d controls and joint states
     int c;           // PW x H running costs
     int ba;          // PW x H x 2 ball in-plane gravity
-    int floats;      // size of one warp's region
+    int ds, dw;      // PW x H self / world depths handed from warp B to A (pair variant)
+    int floats;      // size of one warp's (pair's) region
 };
 
 __host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
@@ -46,6 +53,8 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
     w.thd = take(w.PW * pb.H * pb.d);
     w.c = take(w.PW * pb.H);
     w.ba = take(w.PW * pb.H * 2);
+    w.ds = take(w.PW * pb.H);
+    w.dw = take(w.PW * pb.H);
     w.floats = off;
     return w;
 }
@@ -110,6 +119,13 @@ __device__ __forceinline__ float3 frame_point(const float* __restrict__ fr, int 
                        fmaf(fr[8 * 32 + lane], q.x, fmaf(fr[9 * 32 + lane], q.y, fmaf(fr[10 * 32 + lane], q.z, fr[11 * 32 + lane]))));
 }
 
+// The two warps of pair `unit` meet (named barrier 1 + unit, 64 threads).
+__device__ __forceinline__ void pair_sync(int unit)
+{
+    asm volatile("barrier.sync %0, 64;" ::"r"(unit + 1) : "memory");
+}
+
+template <bool kPair>
 __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
 k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
                const StepState* __restrict__ st, int step_override, int iter, int front_only)
@@ -118,10 +134,14 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
     const WarpPlan W = warp_plan(pb);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wg = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int nw0 = wg * W.PW;  // first particle of this warp
-    if (nw0 >= pb.N) return;    // warp-uniform
-    float* ws = wsm + warp * W.floats;
+    const int unit = kPair ? warp >> 1 : warp;  // the warp, or warp pair, of a particle group
+    const bool do_costs = !kPair || (warp & 1) == 0;  // A: controls, integration, non-collision costs
+    const bool do_coll = !kPair || (warp & 1) == 1;   // B: world and self collision
+    const int units = kPair ? (blockDim.x >> 6) : (blockDim.x >> 5);
+    const int wg = blockIdx.x * units + unit;
+    const int nw0 = wg * W.PW;  // first particle of this unit
+    if (nw0 >= pb.N) return;    // uniform over the unit (both warps of a pair)
+    float* ws = wsm + unit * W.floats;
     float* s_fr = ws + W.frame;
     float* s_cb = ws + W.cb;
     float* s_eps = ws + W.eps;
@@ -136,6 +156,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
     const bool pvalid = seg < np_w;
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
     trace_stamp(pb.trace, 0);
+    if (do_costs) {
     {
         // The grid is a single wave, so every warp meets this SM's L1 cold: pull
         // the read-only tables (and the mean and sigma) into it now, while the
@@ -234,6 +255,8 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         for (int i = lane; i < np_w * HD; i += 32) out.theta[static_cast<size_t>(nw0) * HD + i] = s_th[i];
     if (out.theta_dot)
         for (int i = lane; i < np_w * HD; i += 32) out.theta_dot[static_cast<size_t>(nw0) * HD + i] = s_thd[i];
+    }
+    if (kPair) pair_sync(unit);  // B reads the controls and joint states
     if (front_only) return;
 
     // ---- per-problem constants in registers
@@ -286,8 +309,9 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         float cbx[kMaxDof + 1], cby[kMaxDof + 1], cbz[kMaxDof + 1];
         {
             const float fr0[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
+            if (do_coll)
 #pragma unroll
-            for (int k = 0; k < 12; ++k) s_fr[k * 32 + lane] = fr0[k];
+                for (int k = 0; k < 12; ++k) s_fr[k * 32 + lane] = fr0[k];
             cbx[0] = fmaf(1.f, lbf[0].x, fmaf(0.f, lbf[0].y, fmaf(0.f, lbf[0].z, 0.f)));
             cby[0] = fmaf(0.f, lbf[0].x, fmaf(1.f, lbf[0].y, fmaf(0.f, lbf[0].z, 0.f)));
             cbz[0] = fmaf(0.f, lbf[0].x, fmaf(0.f, lbf[0].y, fmaf(1.f, lbf[0].z, 0.f)));
@@ -297,13 +321,15 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
             if (i < d) {
                 const float* dh = pb.dhx + i * 8;
                 dh_step(R, pp, dh[0], dh[1], dh[2], dh[3], th[i] + dh[4]);
-                float* fr = s_fr + (i + 1) * 12 * 32 + lane;
+                if (do_coll) {
+                    float* fr = s_fr + (i + 1) * 12 * 32 + lane;
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    fr[(r * 4 + 0) * 32] = R[r * 3 + 0];
-                    fr[(r * 4 + 1) * 32] = R[r * 3 + 1];
-                    fr[(r * 4 + 2) * 32] = R[r * 3 + 2];
-                    fr[(r * 4 + 3) * 32] = pp[r];
+                    for (int r = 0; r < 3; ++r) {
+                        fr[(r * 4 + 0) * 32] = R[r * 3 + 0];
+                        fr[(r * 4 + 1) * 32] = R[r * 3 + 1];
+                        fr[(r * 4 + 2) * 32] = R[r * 3 + 2];
+                        fr[(r * 4 + 3) * 32] = pp[r];
+                    }
                 }
                 J[0][i] = pp[1] * R[8] - pp[2] * R[5];
                 J[1][i] = pp[2] * R[2] - pp[0] * R[8];
@@ -325,13 +351,15 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         }
 #pragma unroll
         for (int f = 0; f <= kMaxDof; ++f) {
-            if (f < F) {
+            if (f < F && do_coll) {
                 s_cb[(f * 3 + 0) * 32 + lane] = cbx[f];
                 s_cb[(f * 3 + 1) * 32 + lane] = cby[f];
                 s_cb[(f * 3 + 2) * 32 + lane] = cbz[f];
             }
         }
 
+        float part = 0.f;
+        if (do_costs) {
         // pose (Eq. 9), rotation, stop (Eq. 10), joint limits (Eq. 11), smoothness
         const float dx = pp[0] - g[9], dy = pp[1] - g[10], dz = pp[2] - g[11];
         float c_pos = 0.f;
@@ -374,8 +402,8 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         }
         c_stop = sqrtf(c_stop);
         c_joint = sqrtf(c_joint);
-        float part = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop + pb.w_joint * c_joint +
-                     pb.w_smooth * c_smooth;
+        part = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop + pb.w_joint * c_joint +
+               pb.w_smooth * c_smooth;
         float2 c_ee = make_float2(0.f, 0.f);
         if (want_ee) {  // task-space limits on X_dot, X_ddot (Eq. 8), theta_ddot = u
             float zc[kMaxDof][3];
@@ -420,12 +448,13 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
             part += pb.w_manip * c_manip;
             if (valid && out.terms) out.terms[gi * STORM_NTERMS + 4] = c_manip;
         }
+        }  // do_costs
         __syncwarp();
         trace_stamp(pb.trace, 3);
 
         // ---- world collision, Eq. 14 reading
         float dworld = 0.f;
-        if (NO > 0 && pb.M > 0) {
+        if (do_coll && NO > 0 && pb.M > 0) {
             if (pb.broadphase) {
                 // box enclosing every link bound of the warp's items, padded 1 mm
                 float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -519,7 +548,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         // (register tests over the compile-time list of pairs), then their
         // pair blocks exactly; then the leftover pairs
         float dself = 0.f;
-        const bool do_self = valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
+        const bool do_self = do_coll && valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
         if (valid && pred && pb.self_direct) dself = fmaxf(0.f, pred[gi]);  // Eq. 13's learned term
         uint32_t lp_hit = 0u;  // bit t: frame pair t has blocks and its bounds overlap
         if (do_self) {
@@ -623,16 +652,30 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         trace_stamp(pb.trace, 5);
 
         // ---- running cost (Eq. 15)
-        const float c = part + pb.w_coll * (dself + dworld);
-        if (valid) {
-            s_c[pl * H + h] = c;
-            if (out.terms) {
-                out.terms[gi * STORM_NTERMS + 5] = dself;
-                out.terms[gi * STORM_NTERMS + 6] = dworld;
+        if (kPair) {  // B hands its depths to A
+            if (do_coll && valid) {
+                ws[W.ds + pl * H + h] = dself;
+                ws[W.dw + pl * H + h] = dworld;
+            }
+            pair_sync(unit);
+            if (do_costs && valid) {
+                dself = ws[W.ds + pl * H + h];
+                dworld = ws[W.dw + pl * H + h];
+            }
+        }
+        if (do_costs) {
+            const float c = part + pb.w_coll * (dself + dworld);
+            if (valid) {
+                s_c[pl * H + h] = c;
+                if (out.terms) {
+                    out.terms[gi * STORM_NTERMS + 5] = dself;
+                    out.terms[gi * STORM_NTERMS + 6] = dworld;
+                }
             }
         }
         __syncwarp();  // the next slot rewrites the frames
     }
+    if (!do_costs) return;  // B is done
     if (ball_on) {  // the ball along each particle's horizon
         if (lane < np_w) {
             const float4 s0 = ball_initial(pb.dhx, d, state, pb.ball);

@@ -94,11 +94,14 @@ def test_mappings_bitwise_identical(name):
         ctl.set_distribution(mu, sig)
         ctl.set_launch(2, 256)
         ref = {k: host(v) for k, v in ctl.generate_rollouts(cuda(state), cuda(goal), 3, 0).items()}
-        for wpc in (1, 3):
-            ctl.set_launch_warp(wpc)
+        for mapping, count in (("warp", 1), ("warp", 3), ("pair", 1), ("pair", 2)):
+            if mapping == "warp":
+                ctl.set_launch_warp(count)
+            else:
+                ctl.set_launch_warp_pair(count)
             g = {k: host(v) for k, v in ctl.generate_rollouts(cuda(state), cuda(goal), 3, 0).items()}
             for k in ref:
-                assert np.array_equal(g[k], ref[k]), (wpc, k)
+                assert np.array_equal(g[k], ref[k]), (mapping, count, k)
 
 
 @pytest.mark.parametrize("name", ["vardt_ee", "mixed", "ball"])

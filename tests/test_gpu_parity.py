@@ -381,18 +381,23 @@ def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
         ref = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 3, 1).items()}
         for bp in (True, False):
             ctl.set_broadphase(bp)
-            for wpc in (1, 3, 8):
-                ctl.set_launch_warp(wpc)
-                assert ctl.launch_mapping() == "warp"
+            for mapping, count in (("warp", 1), ("warp", 3), ("warp", 8), ("pair", 1), ("pair", 3)):
+                if mapping == "warp":
+                    ctl.set_launch_warp(count)
+                else:
+                    ctl.set_launch_warp_pair(count)
+                assert ctl.launch_mapping() == mapping
                 ppc, threads = ctl.get_launch()
-                assert threads == 32 * wpc
+                assert threads == (32 if mapping == "warp" else 64) * count
                 g = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 3, 1).items()}
                 for k in ref:
-                    assert np.array_equal(g[k], ref[k]), (bp, wpc, k)
+                    assert np.array_equal(g[k], ref[k]), (bp, mapping, count, k)
         with pytest.raises(StormError):
             ctl.set_launch_warp(0)
         with pytest.raises(StormError):
             ctl.set_launch_warp(9)
+        with pytest.raises(StormError):
+            ctl.set_launch_warp_pair(5)
     active = {nm for t, nm in enumerate(W.TERM_NAMES) if (ref["terms"][..., t] > 0).any()}
     assert {"pos", "rot", "manip"} <= active
     if name == "paper_terms":  # both collision phases exercised (checked on the oracle)
