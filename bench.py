@@ -487,6 +487,36 @@ def run_ablation(args):
             "data": "synthetic"}
 
 
+def run_mlp_forward(args):
+    """Forward passes of both surrogate networks on `--mlp-forward` random
+    configurations (device time per pass, CUDA events, 3 warm-up passes), with
+    the tensor-core throughput of the three GEMM layers."""
+    import torch
+    from paper_2104_13542_b300 import SurrogateMLP
+    rows = args.mlp_forward
+    th = torch.as_tensor(np.random.default_rng(args.seed).uniform(-2.8, 2.8, (rows, 7)).astype(np.float32),
+                         device="cuda")
+    R = (rows + 127) // 128 * 128
+    out = {}
+    for arch, widths in (("distance", (256, 256, 256)), ("jointnerf", (256, 128, 64))):
+        net = SurrogateMLP(seed=args.seed, arch=arch)
+        for _ in range(3):
+            net.predict(th)
+        ev = []
+        for _ in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(net.stream)
+            net.predict(th)
+            b.record(net.stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        flops = 2.0 * R * (16 * widths[0] + widths[0] * widths[1] + widths[1] * widths[2])
+        out[arch] = {"ms": ms, "gemm_tflops": flops / (ms * 1e-3) / 1e12, "rows": rows}
+        net.close()
+    return {"mlp_forward": out, "note": "per predict call, including encode and the output copy"}
+
+
 def _local_goals(ctl, theta0, seed: int, count: int):
     """Goal poses FK(theta_g) with theta_g = theta0 + U[-0.6, 0.6] rad per joint, within
     [-2.2, 2.2] and 3 cm clear of self-collision: reaching moves that a local
@@ -594,6 +624,8 @@ def main():
     ap.add_argument("--launch", default="auto",
                     help="rollout launch shape: auto (autotuned), warp:W (W warps per CTA), pair:W (W warp "
                          "pairs per CTA) or cta:P,T")
+    ap.add_argument("--mlp-forward", type=int, default=0, metavar="ROWS",
+                    help="time the surrogate networks' forward pass on ROWS configurations instead")
     ap.add_argument("--ablation", action="store_true",
                     help="run the closed-loop sampling ablation instead of the benchmark")
     args = ap.parse_args()
@@ -610,6 +642,10 @@ def main():
     if args.ablation:
         if rank == 0:
             print(json.dumps(run_ablation(args)))
+        return
+    if args.mlp_forward:
+        if rank == 0:
+            print(json.dumps(run_mlp_forward(args)))
         return
 
     if world_size > 1:

@@ -1348,16 +1348,19 @@ cudaError_t gemm_rw_bn(const tc::GemmArgs& g, cudaStream_t s)
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(tc::k_gemm_rw<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(tc::gemm_rw_smem(256, 256)));
+        cudaError_t e = cudaFuncSetAttribute(tc::k_gemm_ws<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(tc::gemm_ws_smem(256, 256)));
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
     const int grid = std::min(g.M / tc::kBM, sms);
-    // the largest plan's shared-memory size for every layer keeps one CTA (and
-    // one TMEM allocation) per SM
-    tc::k_gemm_rw<BN><<<grid, tc::kThreads, tc::gemm_rw_smem(256, 256), s>>>(g);
+    // persistent: one CTA per SM walks the 128-row tiles.  Each CTA holds 2 x BN
+    // TMEM columns; the shared-memory request keeps at most 512 / (2 BN) CTAs
+    // on an SM, so no allocation ever waits for a co-resident CTA.
+    const size_t floor_smem = BN == 256 ? 116u * 1024 : (BN == 128 ? 80u * 1024 : 48u * 1024);
+    const size_t smem = std::max(tc::gemm_ws_smem(BN, g.K), floor_smem);
+    tc::k_gemm_ws<BN><<<grid, tc::kThreadsWS, smem, s>>>(g);
     return cudaGetLastError();
 }
 

@@ -269,50 +269,78 @@ __host__ __device__ constexpr size_t gemm_rw_smem(int BN, int K)
     return static_cast<size_t>(BN) * K * 2 + static_cast<size_t>(kStagesRW) * kBM * (K < kKB ? K : kKB) * 2;
 }
 
+// TMEM -> registers, 32 consecutive FP32 columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Epilogue of one 128-row tile (this thread: row `row`, TMEM lanes of `warp`):
+// bias, ReLU, mask, BF16 / FP32 / transposed stores and the dot head, 32
+// columns per TMEM load.
 template <int BN>
-__device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, int row, int warp)
+__device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, int row, int warp,
+                                              const float* bias, const float* head_w)
 {
     float yacc = 0.f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 8) {
-        uint32_t r[8];
-        const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-              "=r"(r[7])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        float v[8];
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, r);
+        float v[32];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 32; ++i) {
             const int n = c0 + i;
             float x = __uint_as_float(r[i]);
-            if (g.bias) x += g.bias[n];
+            if (bias) x += bias[n];
             if (g.relu) x = fmaxf(x, 0.f);
-            if (g.mask && !(__bfloat162float(g.mask[static_cast<size_t>(row) * g.ldm + n]) > 0.f)) x = 0.f;
             v[i] = x;
-            if (g.head_w) yacc = fmaf(g.head_w[n], x, yacc);
         }
+        if (g.mask) {
+            const uint4* mk = reinterpret_cast<const uint4*>(g.mask + static_cast<size_t>(row) * g.ldm + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 w = mk[q];
+                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&w);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (!(__bfloat162float(mb[i]) > 0.f)) v[q * 8 + i] = 0.f;
+            }
+        }
+        if (head_w)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) yacc = fmaf(head_w[c0 + i], v[i], yacc);
         if (g.out_f) {
             float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
-            o[0] = make_float4(v[0], v[1], v[2], v[3]);
-            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
         if (g.out_bf) {
-            __align__(16) __nv_bfloat16 b[8];
+            uint4* o = reinterpret_cast<uint4*>(g.out_bf + static_cast<size_t>(row) * g.ldo + c0);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[i]);
-            *reinterpret_cast<uint4*>(g.out_bf + static_cast<size_t>(row) * g.ldo + c0) =
-                *reinterpret_cast<const uint4*>(b);
+            for (int q = 0; q < 4; ++q) {
+                __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[q * 8 + i]);
+                o[q] = *reinterpret_cast<const uint4*>(b);
+            }
         }
         if (g.out_bfT) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 32; ++i)
                 g.out_bfT[static_cast<size_t>(c0 + i) * g.ldoT + row] = __float2bfloat16_rn(v[i]);
         }
     }
-    if (g.head_w) g.head_y[row] = *g.head_b + yacc;
+    if (head_w) g.head_y[row] = *g.head_b + yacc;
 }
 
 template <int BN>
@@ -370,7 +398,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
     auto epilogue = [&](int item) {  // item is the last K block of its tile
         const int tl = item / nk;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        gemm_epilogue<BN>(g, tmem + (tl & 1) * BN, (bx + tl * gx) * kBM + warp * 32 + lane, warp);
+        gemm_epilogue<BN>(g, tmem + (tl & 1) * BN, (bx + tl * gx) * kBM + warp * 32 + lane, warp, g.bias,
+                          g.head_w);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     };
     int issued = 0;
@@ -433,6 +462,187 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
         for (int p = waited + 1; p < total && p <= waited + 2; ++p)
             mbar_wait(smem_u32(&mbar[p % kStagesRW]), (p / kStagesRW) & 1);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------- warp-specialised layer
+// The same layer as k_gemm_rw (weights resident, N = BN) with the roles split
+// across warps so that loading, multiplying and draining overlap:
+//   warp 0     producer: the weights once, then the A tiles through kStagesWS
+//              shared-memory stages with cp.async; it waits for its own copies
+//              kLagWS groups behind, fences them into the async proxy and
+//              signals full[stage];
+//   warp 1     one thread issues the tcgen05.mma of each K block once
+//              full[stage] completes, commits to empty[stage] (the stage is
+//              free again when those MMAs finish) and, at a tile's end, to
+//              tfull[buf] (accumulator buffer buf = tile parity, 2 x BN TMEM
+//              columns);
+//   warps 2-5  the epilogue: warp w drains TMEM lanes 32 (w % 4) .. +31 of
+//              buffer buf, then arrives on tempty[buf].
+// Every wait is bounded (1 s): on a timeout the role sets *err and leaves its
+// loop; the others time out in turn, and the CTA still meets at the final
+// barrier before the TMEM is freed.
+constexpr int kStagesWS = 6, kLagWS = 3;
+constexpr int kThreadsWS = 192;
+
+__host__ __device__ constexpr size_t gemm_ws_smem(int BN, int K)
+{
+    return static_cast<size_t>(BN) * K * 2 + static_cast<size_t>(kStagesWS) * kBM * (K < kKB ? K : kKB) * 2;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
+{
+    constexpr uint32_t kCols = 2 * BN;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kStagesWS], empty[kStagesWS], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ float s_bias[BN], s_headw[BN];  // the epilogue's per-column vectors, read by every row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = g.K, kb = K < kKB ? K : kKB, nk = K / kb;
+    unsigned char* sW = smem;
+    unsigned char* sA = smem + static_cast<size_t>(BN) * K * 2;
+    const int stageA = kBM * kb * 2, blockW = BN * kb * 2;
+    const uint32_t sbo = (kb / 8) * 128;
+    const int tiles = g.M / kBM, bx = blockIdx.x, gx = gridDim.x;
+    const int my_tiles = tiles > bx ? (tiles - 1 - bx) / gx + 1 : 0;
+    const int total = my_tiles * nk;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int n = threadIdx.x; n < BN; n += blockDim.x) {
+        s_bias[n] = g.bias ? g.bias[n] : 0.f;
+        s_headw[n] = g.head_w ? g.head_w[n] : 0.f;
+    }
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < kStagesWS; ++i) {
+            mbar_init(smem_u32(&full[i]), 1);
+            mbar_init(smem_u32(&empty[i]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---- producer
+        {
+            const int chunks = kb / 8;
+            for (int c = lane; c < nk * BN * chunks; c += 32) {
+                const int j = c / (BN * chunks), rem = c - j * BN * chunks;
+                const int r = rem / chunks, kg = rem - r * chunks;
+                cp_async16(smem_u32(sW + j * blockW) + (r >> 3) * sbo + (r & 7) * 16 + kg * 128,
+                           g.B + static_cast<size_t>(r) * g.ldb + j * kb + kg * 8);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        auto signal = [&](int item) {  // item's copies (and all older ones) are complete
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&full[item % kStagesWS]));
+        };
+        for (int i = 0; i < total && ok; ++i) {
+            const int stage = i % kStagesWS;
+            if (i >= kStagesWS)  // the MMAs of item i - kStagesWS released the stage
+                ok = mbar_wait(smem_u32(&empty[stage]), ((i / kStagesWS) - 1) & 1);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            const int t = bx + (i / nk) * gx, j = i % nk;
+            const __nv_bfloat16* src = g.A + static_cast<size_t>(t) * kBM * g.lda + j * kb;
+            const uint32_t dst = smem_u32(sA + stage * stageA);
+            const int chunks = kb / 8;
+            for (int c = lane; c < kBM * chunks; c += 32) {
+                const int r = c / chunks, kg = c - r * chunks;
+                cp_async16(dst + (r >> 3) * sbo + (r & 7) * 16 + kg * 128, src + static_cast<size_t>(r) * g.lda + kg * 8);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (i >= kLagWS) {
+                asm volatile("cp.async.wait_group %0;" ::"n"(kLagWS) : "memory");
+                signal(i - kLagWS);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (ok)
+            for (int i = total > kLagWS ? total - kLagWS : 0; i < total; ++i) signal(i);
+    } else if (warp == 1) {
+        // ---- MMA issue (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(kBM, BN);
+            for (int tl = 0; tl < my_tiles && ok; ++tl) {
+                const int buf = tl & 1;
+                if (tl >= 2) ok = mbar_wait(smem_u32(&tempty[buf]), ((tl >> 1) - 1) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + buf * BN;
+                for (int j = 0; j < nk && ok; ++j) {
+                    const int i = tl * nk + j, stage = i % kStagesWS;
+                    ok = mbar_wait(smem_u32(&full[stage]), (i / kStagesWS) & 1);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sA + stage * stageA), b0 = smem_u32(sW + j * blockW);
+                    for (int kk = 0; kk < kb / 16; ++kk) {
+                        const uint64_t da = smem_desc(a0 + kk * 256, 128, sbo);
+                        const uint64_t db = smem_desc(b0 + kk * 256, 128, sbo);
+                        const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            smem_u32(&empty[stage]))
+                        : "memory");
+                }
+                if (!ok) break;
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&tfull[buf]))
+                    : "memory");
+            }
+            if (ok && my_tiles > 0)  // the last accumulator is complete before the CTA may free TMEM
+                ok = mbar_wait(smem_u32(&tfull[(my_tiles - 1) & 1]), ((my_tiles - 1) >> 1) & 1);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue warps 2..5: TMEM lanes 32 (warp % 4) + lane
+        const int q = warp & 3;
+        for (int tl = 0; tl < my_tiles && ok; ++tl) {
+            const int buf = tl & 1;
+            ok = mbar_wait(smem_u32(&tfull[buf]), (tl >> 1) & 1);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            gemm_epilogue<BN>(g, tmem + buf * BN, (bx + tl * gx) * kBM + q * 32 + lane, q,
+                              g.bias ? s_bias : nullptr, g.head_w ? s_headw : nullptr);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+        }
+    }
+    if (!ok && g.err && lane == 0) atomicExch(g.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
