@@ -85,7 +85,7 @@ class _Params(C.Structure):
                 ("filter", C.c_int), ("comb", C.c_double * 3), ("mix_bspline", C.c_double),
                 ("w_ee_vel", C.c_double), ("w_ee_acc", C.c_double), ("ee_vel_max", C.c_double),
                 ("ee_acc_max", C.c_double), ("w_ball", C.c_double), ("gravity", C.c_double * 3),
-                ("tray_center", C.c_double * 3), ("ball", _dp)]
+                ("tray_center", C.c_double * 3), ("ball", _dp), ("halton_scramble", C.c_int)]
 
 
 def _declare(L):
@@ -102,6 +102,11 @@ def _declare(L):
     L.orc_norm_ppf.argtypes = [C.c_double]
     L.orc_norm_ppf.restype = C.c_double
     L.orc_noise_halton.argtypes = [C.c_int, C.c_int, C.c_int, _dp]
+    L.orc_noise_halton_ex.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp]
+    L.orc_radical_inverse_scrambled.argtypes = [C.c_uint64, C.c_int, C.c_int]
+    L.orc_radical_inverse_scrambled.restype = C.c_double
+    L.orc_halton_multiplier.argtypes = [C.c_uint64, C.c_int, C.c_int]
+    L.orc_halton_multiplier.restype = C.c_int
     L.orc_bspline_basis.argtypes = [C.c_int, C.c_int, _dp]
     L.orc_smooth_controls.argtypes = [C.POINTER(_Params), C.c_int, _dp, _dp, _dp, _dp]
     L.orc_integrate.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
@@ -209,10 +214,18 @@ def norm_ppf(p: float) -> float:
     return lib().orc_norm_ppf(float(p))
 
 
-def noise_halton(N, S, d) -> np.ndarray:
+def noise_halton(N, S, d, scramble=False, seed=0) -> np.ndarray:
     out = np.zeros((N, S, d))
-    lib().orc_noise_halton(N, S, d, _ptr(out))
+    lib().orc_noise_halton_ex(N, S, d, int(bool(scramble)), int(seed), _ptr(out))
     return out
+
+
+def radical_inverse_scrambled(i: int, base: int, mult: int) -> float:
+    return lib().orc_radical_inverse_scrambled(int(i), int(base), int(mult))
+
+
+def halton_multiplier(seed: int, dim: int, base: int) -> int:
+    return int(lib().orc_halton_multiplier(int(seed), int(dim), int(base)))
 
 
 def comb_filter(c, eps) -> np.ndarray:
@@ -385,6 +398,7 @@ class Oracle:
         s.gravity[:] = [float(g) for g in p.gravity]
         s.tray_center[:] = [float(c) for c in p.tray_center]
         s.ball = None
+        s.halton_scramble = int(p.halton_scramble)
         return s
 
     def set_ball(self, pos, vel):
@@ -402,7 +416,7 @@ class Oracle:
     def noise(self, step: int, it: int) -> np.ndarray:
         p = self.params
         if p.sampler == 1:
-            return noise_halton(p.N, self.n_noise, self.d)
+            return noise_halton(p.N, self.n_noise, self.d, p.halton_scramble, p.seed)
         return noise_philox(p.seed, step, p.instance, it, 0,
                             p.N * self.n_noise * self.d).reshape(p.N, self.n_noise, self.d)
 

@@ -137,13 +137,47 @@ double orc_norm_ppf(double p)
     return 0.5 * (lo + hi);
 }
 
-void orc_noise_halton(int N, int S, int d, double* eps)
+void orc_noise_halton(int N, int S, int d, double* eps) { orc_noise_halton_ex(N, S, d, 0, 0, eps); }
+
+/* Radical inverse with linearly scrambled digits: digit a of i in base b
+ * contributes ((mult * a) mod b) b^-(position).  mult = 1 is the plain
+ * radical inverse; for prime b and 0 < mult < b the map is a permutation of
+ * the digits that fixes 0 (generalised Halton sequences, Faure and Lemieux). */
+double orc_radical_inverse_scrambled(uint64_t i, int base, int mult)
+{
+    double f = 1.0 / base, r = 0.0;
+    while (i > 0) {
+        r += (double)(((uint64_t)mult * (i % (uint64_t)base)) % (uint64_t)base) * f;
+        i /= (uint64_t)base;
+        f /= base;
+    }
+    return r;
+}
+
+/* Multiplier of dimension dim (base b) drawn from the Philox stream of the
+ * seed: 1 + (Philox4x32-10 of counter (dim, 0, 0, 3), first word) mod (b - 1). */
+int orc_halton_multiplier(uint64_t seed, int dim, int base)
+{
+    const uint32_t ctr[4] = {(uint32_t)dim, 0u, 0u, 3u};
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return base > 2 ? 1 + (int)(out[0] % (uint32_t)(base - 1)) : 1;
+}
+
+/* Halton noise (Sec. 4.3): point n + 1 of the sequence in the first S*d primes,
+ * mapped to normal by the inverse CDF; scramble selects the linearly scrambled
+ * digits (an added option: unscrambled, the first points of the large-prime
+ * dimensions are i / p, the same for every such dimension). */
+void orc_noise_halton_ex(int N, int S, int d, int scramble, uint64_t seed, double* eps)
 {
     for (int n = 0; n < N; ++n)
         for (int s = 0; s < S; ++s)
             for (int j = 0; j < d; ++j) {
                 const int dim = s * d + j;
-                const double w = orc_radical_inverse((uint64_t)n + 1, orc_nth_prime(dim));
+                const int b = orc_nth_prime(dim);
+                const int f = scramble ? orc_halton_multiplier(seed, dim, b) : 1;
+                const double w = orc_radical_inverse_scrambled((uint64_t)n + 1, b, f);
                 eps[((long long)n * S + s) * d + j] = orc_norm_ppf(w);
             }
 }
@@ -886,7 +920,7 @@ int orc_step(const orc_robot* R, const orc_world* W, const orc_params* P,
     double* C = (double*)malloc(sizeof(double) * N);
     int status = 0;
     if (step > 0) orc_shift(H, d, mu);
-    if (P->sampler == ORC_SAMPLER_HALTON) orc_noise_halton(N, S, d, eps);
+    if (P->sampler == ORC_SAMPLER_HALTON) orc_noise_halton_ex(N, S, d, P->halton_scramble, P->seed, eps);
     for (int k = 0; k < P->K; ++k) {
         if (P->sampler == ORC_SAMPLER_PHILOX)
             orc_noise_philox(P->seed, step, P->instance, (uint32_t)k, 0u, count, eps);

@@ -92,6 +92,7 @@ typedef struct {
     double gravity[3];      /* g in the world frame */
     double tray_center[3];  /* tray centre in the end-effector frame */
     const double* ball;     /* 6: ball position, velocity (world) at the current state; NULL: none */
+    int halton_scramble;    /* Halton sampler: linearly scrambled digits (multipliers from the seed) */
 } orc_params;
 
 /* ---- noise ---- */
@@ -104,6 +105,9 @@ double orc_radical_inverse(uint64_t i, int base);
 int orc_nth_prime(int n);
 double orc_norm_ppf(double p);
 void orc_noise_halton(int N, int S, int d, double* eps);
+double orc_radical_inverse_scrambled(uint64_t i, int base, int mult);
+int orc_halton_multiplier(uint64_t seed, int dim, int base);
+void orc_noise_halton_ex(int N, int S, int d, int scramble, uint64_t seed, double* eps);
 void orc_bspline_basis(int H, int S, double* B);
 
 /* ---- rollout stages ---- */

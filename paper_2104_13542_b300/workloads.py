@@ -106,6 +106,8 @@ class Params:
     w_ball: float = 0.0
     gravity: tuple = (0.0, 0.0, -9.81)
     tray_center: tuple = (0.0, 0.0, 0.0)
+    # Halton sampler: linearly scrambled digits (per-dimension multipliers from the seed)
+    halton_scramble: int = 0
 
     def replace(self, **kw) -> "Params":
         p = dataclasses.replace(self, **kw)

@@ -640,3 +640,41 @@ def test_shift_and_step_semantics():
     m3, s3, _, _ = o.update(out["C"], out["u"], m2, s2)
     cmd1, mu1, sig1, _, _ = o.step(wl.state, wl.goal, 1, mu, sig)
     assert np.allclose(mu1, m3) and np.allclose(sig1, s3) and np.allclose(cmd1, m3[0])
+
+
+# ----------------------------------------------------------------------------- scrambled Halton
+
+def test_scrambled_radical_inverse_by_hand():
+    # 5 = (12)_3 with digits 2, 1 (least significant first)
+    assert oracle.radical_inverse_scrambled(5, 3, 1) == pytest.approx(2 / 3 + 1 / 9, abs=1e-15)
+    assert oracle.radical_inverse_scrambled(5, 3, 2) == pytest.approx(1 / 3 + 2 / 9, abs=1e-15)
+    # 10 = (1010)_2: multiplier 1 is the only one in base 2
+    assert oracle.radical_inverse_scrambled(10, 2, 1) == pytest.approx(0.5 ** 2 + 0.5 ** 4, abs=1e-15)
+    # 23 = (43)_5, mult 3: digits 3, 4 -> 9 mod 5 = 4, 12 mod 5 = 2
+    assert oracle.radical_inverse_scrambled(23, 5, 3) == pytest.approx(4 / 5 + 2 / 25, abs=1e-15)
+
+
+@pytest.mark.parametrize("base,mult", [(7, 3), (11, 5), (13, 12)])
+def test_scrambled_sequence_keeps_the_stratification(base, mult):
+    """b^k consecutive points (from 0) still hit every cell j / b^k once: the
+    digit map is a permutation of each digit position."""
+    k = 2
+    pts = sorted(oracle.radical_inverse_scrambled(i, base, mult) for i in range(base ** k))
+    assert np.allclose(pts, np.arange(base ** k) / base ** k, atol=1e-12)
+
+
+def test_halton_multipliers_and_decorrelation():
+    seed = 2000
+    primes = [oracle.nth_prime(k) for k in range(42)]
+    mults = [oracle.halton_multiplier(seed, k, b) for k, b in enumerate(primes)]
+    assert mults[0] == 1 and all(1 <= m < b for m, b in zip(mults, primes))
+    assert len(set(mults[10:])) > 20  # drawn, not constant
+    # the unscrambled leading points of two large-prime dimensions are i / p: collinear
+    plain = oracle.noise_halton(100, 6, 7)
+    scr = oracle.noise_halton(100, 6, 7, scramble=True, seed=seed)
+    a, b = 40, 41
+    r_plain = np.corrcoef(plain[:, a // 7, a % 7], plain[:, b // 7, b % 7])[0, 1]
+    r_scr = np.corrcoef(scr[:, a // 7, a % 7], scr[:, b // 7, b % 7])[0, 1]
+    assert r_plain > 0.95 and abs(r_scr) < 0.5, (r_plain, r_scr)
+    # marginals stay standard normal-like
+    assert abs(scr.mean()) < 0.05 and abs(scr.std() - 1.0) < 0.1
