@@ -452,10 +452,11 @@ def run_ablation(args):
     steps_per_goal = 400
     out = {}
     for N in (100, 500):
-        for sampler, sname in ((W.SAMPLER_PHILOX, "pseudo_random"), (W.SAMPLER_HALTON, "halton")):
+        for sampler, scr, sname in ((W.SAMPLER_PHILOX, 0, "pseudo_random"), (W.SAMPLER_HALTON, 0, "halton"),
+                                    (W.SAMPLER_HALTON, 1, "halton_scrambled")):
             for filt, fname in ((W.FILTER_COMB, "comb"), (W.FILTER_DEFAULT, "bspline"),
                                 (W.FILTER_MIXED, "mixed")):
-                p = base.params.replace(N=N, sampler=sampler, filter=filt, n_null=2)
+                p = base.params.replace(N=N, sampler=sampler, halton_scramble=scr, filter=filt, n_null=2)
                 with Controller(base.robot, base.world, p) as ctl:
                     if goals is None:
                         _, th = goals_for(ctl, base.robot, args.seed, 1, with_theta=True)

@@ -140,6 +140,11 @@ typedef struct {
     double w_ball;
     double gravity[3];
     double tray_center[3];
+    /* STORM_SAMPLER_HALTON only: 1 scrambles the digits linearly, dimension k (base p_k)
+     * mapping digit a to (f_k a) mod p_k with f_k = 1 + (Philox4x32-10 of counter
+     * (k, 0, 0, 3) under the seed's key, first word) mod (p_k - 1) (generalised Halton;
+     * plain Halton points in many prime dimensions are strongly correlated); 0 plain. */
+    int halton_scramble;
 } storm_params;
 
 typedef struct {

@@ -95,7 +95,8 @@ class storm_params(C.Structure):
                 ("grad_steps", C.c_int), ("grad_eta", C.c_double), ("filter", C.c_int),
                 ("comb", C.c_double * 3), ("mix_bspline", C.c_double), ("w_ee_vel", C.c_double),
                 ("w_ee_acc", C.c_double), ("ee_vel_max", C.c_double), ("ee_acc_max", C.c_double),
-                ("w_ball", C.c_double), ("gravity", C.c_double * 3), ("tray_center", C.c_double * 3)]
+                ("w_ball", C.c_double), ("gravity", C.c_double * 3), ("tray_center", C.c_double * 3),
+                ("halton_scramble", C.c_int)]
 
 
 class storm_step_info(C.Structure):
@@ -261,6 +262,7 @@ class _Marshal:
         s.w_ball = float(p.w_ball)
         s.gravity[:] = [float(g) for g in p.gravity]
         s.tray_center[:] = [float(c) for c in p.tray_center]
+        s.halton_scramble = int(p.halton_scramble)
         return s
 
 

@@ -1139,7 +1139,12 @@ __global__ void k_primes(int D, int* prime)
 // Halton noise: point n+1, dimension s*d+j, radical inverse as the exact
 // fraction (digit-reversed numerator) / base^digits, mapped through the
 // standard normal quantile.
-__global__ void k_halton(int N, int S, int d, const int* prime, float* out)
+// Halton table (Sec. 4.3): point n + 1 in the first S*d prime bases, through
+// the inverse normal CDF.  With `scramble` each digit a of dimension dim (base
+// b) becomes (f a) mod b, f = 1 + (Philox4x32-10 of counter (dim, 0, 0, 3),
+// first word) mod (b - 1): linearly scrambled (generalised) Halton points.
+__global__ void k_halton(int N, int S, int d, const int* prime, int scramble, uint32_t seed_lo, uint32_t seed_hi,
+                         float* out)
 {
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const size_t total = static_cast<size_t>(N) * S * d;
@@ -1147,9 +1152,12 @@ __global__ void k_halton(int N, int S, int d, const int* prime, float* out)
     const int dim = static_cast<int>(i % (static_cast<size_t>(S) * d));
     const uint64_t n = i / (static_cast<size_t>(S) * d) + 1;
     const uint64_t b = static_cast<uint64_t>(prime[dim]);
+    uint64_t f = 1;
+    if (scramble && b > 2)
+        f = 1 + philox4x32_10(make_uint4(static_cast<uint32_t>(dim), 0u, 0u, 3u), seed_lo, seed_hi).x % (b - 1);
     uint64_t num = 0, den = 1, k = n;
     while (k > 0) {
-        num = num * b + k % b;
+        num = num * b + (f * (k % b)) % b;
         den *= b;
         k /= b;
     }
@@ -1667,6 +1675,7 @@ int validate(const storm_robot* r, const storm_world* w, const storm_params* p, 
     if (p->grad_steps < 0 || p->grad_steps > 64 || p->K + p->grad_steps > 256 ||
         !std::isfinite(p->grad_eta))
         return msg = "bad grad_steps / grad_eta", STORM_ERR_INVALID_ARG;
+    if (p->halton_scramble != 0 && p->halton_scramble != 1) return msg = "bad halton_scramble", STORM_ERR_INVALID_ARG;
     if (p->filter != STORM_FILTER_DEFAULT && p->filter != STORM_FILTER_COMB && p->filter != STORM_FILTER_MIXED)
         return msg = "bad filter", STORM_ERR_INVALID_ARG;
     if (p->filter == STORM_FILTER_MIXED && p->n_knots < 4)
@@ -1950,6 +1959,7 @@ struct HostTables {
     std::vector<float4> lbound;  // per frame: bounding sphere of its spheres (local)
     std::vector<double> raw;  // dh | q_min | q_max | dt, read by the set-up kernel
     double k_jl = 0, qdd_max = 0, gamma = 0;
+    int halton_scramble = 0;
 };
 
 // Scalars of the problem and its host tables: spheres sorted by link (stable),
@@ -2060,6 +2070,7 @@ void fill_problem(const storm_robot* r, const storm_world* w, const storm_params
     ht.raw.insert(ht.raw.end(), r->q_max, r->q_max + pb.d);
     ht.raw.insert(ht.raw.end(), p->dt, p->dt + pb.H);
     ht.k_jl = p->k_jl;
+    ht.halton_scramble = p->halton_scramble;
     ht.qdd_max = p->qdd_max;
     ht.gamma = p->gamma;
 }
@@ -2112,7 +2123,7 @@ cudaError_t upload_problem(Problem& pb, const HostTables& ht, char* base, const 
         k_primes<<<(D + 127) / 128, 128, 0, s>>>(D, d_prime);
         const size_t total = size_t(pb.N) * pb.S * pb.d;
         k_halton<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
-            pb.N, pb.S, pb.d, d_prime, const_cast<float*>(pb.halton));
+            pb.N, pb.S, pb.d, d_prime, ht.halton_scramble, pb.seed_lo, pb.seed_hi, const_cast<float*>(pb.halton));
     }
     return cudaGetLastError();
 }
@@ -2849,7 +2860,8 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
             k_primes<<<(D + 127) / 128, 128, 0, stream>>>(D, d_prime);
             const size_t total = size_t(pb.N) * pb.S * pb.d;
             k_halton<<<static_cast<unsigned>((total + 255) / 256), 256, 0, stream>>>(
-                pb.N, pb.S, pb.d, d_prime, const_cast<float*>(pb.halton));
+                pb.N, pb.S, pb.d, d_prime, p->halton_scramble, pb.seed_lo, pb.seed_hi,
+                const_cast<float*>(pb.halton));
         }
         RolloutOut out{d_u, nullptr, nullptr, nullptr, nullptr, nullptr, Ctot_dev};
         const int grid = (pb.N + pb.ppc - 1) / pb.ppc;

@@ -30,6 +30,7 @@ def _variants():
         "paper": (paper, paper.params),
         "paper_ragged_N37": (paper, paper.params.replace(N=37)),
         "paper_halton": (paper, paper.params.replace(N=96, sampler=W.SAMPLER_HALTON)),
+        "paper_halton_scrambled": (paper, paper.params.replace(N=96, sampler=W.SAMPLER_HALTON, halton_scramble=1)),
         "paper_null_frob": (paper, paper.params.replace(N=64, n_null=5,
                                                         rot_mode=W.ROT_FROBENIUS,
                                                         rot_axis_w=(0.5, 1.0, 2.0),
@@ -45,7 +46,7 @@ VARIANTS = _variants()
 
 # ----------------------------------------------------------------------------- noise
 
-@pytest.mark.parametrize("name", ["small", "paper", "paper_ragged_N37", "paper_halton"])
+@pytest.mark.parametrize("name", ["small", "paper", "paper_ragged_N37", "paper_halton", "paper_halton_scrambled"])
 def test_noise_matches_oracle(name):
     wl, p = VARIANTS[name]
     orc = oracle.Oracle(wl.robot, wl.world, p)
@@ -185,7 +186,7 @@ def _step_pair(wl, p, n_steps=1, state_seed=0):
     return res
 
 
-@pytest.mark.parametrize("name", ["small", "paper", "paper_ragged_N37", "paper_halton",
+@pytest.mark.parametrize("name", ["small", "paper", "paper_ragged_N37", "paper_halton", "paper_halton_scrambled",
                                   "paper_null_frob", "small_N1"])
 def test_step_parity(name):
     wl, p = VARIANTS[name]
