@@ -74,11 +74,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def rollout_traffic():
-    """DRAM bytes per rollout launch from the committed ncu summary, or None when
-    the kernels changed since that capture."""
+ROLLOUT_KERNELS = {"cta": "k_rollout", "warp": "k_rollout_warp<false>", "pair": "k_rollout_warp<true>"}
+
+
+def rollout_traffic(kernel: str):
+    """DRAM bytes per launch of this rollout kernel from the committed ncu summary,
+    or None when there is none for it or the kernels changed since the capture."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_rollout"]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
     except Exception:
         return None
     return rec["dram_bytes_per_launch"] if rec.get("src_sha256_16") == kernel_source_hash() else None
@@ -313,8 +316,9 @@ def run_gpu(args, rank, world_size):
                             "p99": float(np.percentile(e2e_ms, 99))},
              "closed_loop_final_pos_err_m": pos_err},
         roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                  "frac": achieved / peak, "traffic": rollout_traffic(),
-                  "kernel": "k_rollout", "kernel_ms": rk_ms, "flops_per_launch": flops_launch,
+                  "frac": achieved / peak, "traffic": rollout_traffic(ROLLOUT_KERNELS[ctl.launch_mapping()]),
+                  "kernel": ROLLOUT_KERNELS[ctl.launch_mapping()], "kernel_ms": rk_ms,
+                  "flops_per_launch": flops_launch,
                   "flops_basis": "brute-force count of the method's work per (particle, step); "
                                  "with the collision broad phase the kernel executes fewer",
                   "brute_force_kernel_ms": rk_bf_ms, "brute_force_frac": achieved_bf / peak,
