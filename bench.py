@@ -406,7 +406,8 @@ def run_variants(args, seed: int):
         out["batched_256"] = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99)),
                               "rollout_steps_per_s": units * len(ms) / float(ms.sum() / 1e3),
                               "instances": len(wls), "rollout_steps_per_step": units,
-                              "tile": b.get_launch(), "autotune_rollout_us": t_tune}
+                              "mapping": b.launch_mapping, "tile": b.get_launch(),
+                              "autotune_rollout_us": t_tune}
     # learned self-collision surrogate at 1000 x 30
     wl = W.config_paper(seed, N=1000, H=30)
     margin = 0.05

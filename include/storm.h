@@ -372,12 +372,31 @@ int storm_batch_sync(storm_batch* b);
 int storm_batch_get_distribution(storm_batch* b, int i, float* mean, float* sigma);
 int storm_batch_set_distribution(storm_batch* b, int i, const float* mean, const float* sigma);
 
-/* Autotuner of the batched rollout: for (particle, step) items per tile of 32,
- * 48, 64, 96, 128 and 128 / 256 / 512 threads per CTA, rebuilds the tile list
- * and times the batched rollout kernel with CUDA events on the batch's inputs,
- * keeps the fastest and re-captures the step graph.  Waits. */
+/* Work mapping of the batched rollout, as for a single handle: the CTA-wide
+ * mapping deals tiles of (particle, step) items to persistent CTAs; the warp
+ * mapping (the default, 4 warps per CTA) deals (instance, particle group)
+ * tasks to warps, each running the single-handle warp rollout on its
+ * instance.  Both give every instance's results bitwise.
+ *
+ * storm_batch_set_launch: CTA mapping, items_per_tile >= 1 (rounded down to
+ * whole particles, at least one), threads in 32..512, a multiple of 32.
+ * storm_batch_set_launch_warp: warp mapping, warps_per_cta in 1..8.  Both
+ * rebuild the task list and re-capture the step graph; wait.  Errors:
+ * INVALID_ARG (also when the shape does not fit in shared memory), CUDA.
+ *
+ * Autotuner: every CTA shape of 32, 48, 64, 96, 128 items per tile x 128 /
+ * 256 / 512 threads and every warp shape of 1, 2, 4, 8 warps per CTA, each
+ * timed with CUDA events on the batch's inputs; keeps the fastest and
+ * re-captures the step graph.  Waits.
+ *
+ * storm_batch_get_launch: items per tile and threads of the CTA mapping, or
+ * 32 x warps per CTA for both on the warp mapping.
+ * storm_batch_get_launch_mapping: STORM_MAP_CTA or STORM_MAP_WARP. */
+int storm_batch_set_launch(storm_batch* b, int items_per_tile, int threads);
+int storm_batch_set_launch_warp(storm_batch* b, int warps_per_cta);
 int storm_batch_autotune(storm_batch* b, float* best_us);
 int storm_batch_get_launch(const storm_batch* b, int* items_per_tile, int* threads);
+int storm_batch_get_launch_mapping(const storm_batch* b);
 
 /* ---------------------------------------------------------------- learned self-collision */
 

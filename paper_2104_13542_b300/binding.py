@@ -45,6 +45,7 @@ EXPORTED = [
     "storm_batch_last_error", "storm_batch_sizes", "storm_batch_step", "storm_batch_step_resident",
     "storm_batch_device_io", "storm_batch_sync", "storm_batch_get_distribution",
     "storm_batch_set_distribution", "storm_batch_autotune", "storm_batch_get_launch",
+    "storm_batch_set_launch", "storm_batch_set_launch_warp", "storm_batch_get_launch_mapping",
     "storm_mlp_create", "storm_mlp_destroy", "storm_mlp_last_error", "storm_mlp_get_params",
     "storm_mlp_set_params", "storm_mlp_predict", "storm_mlp_loss_grad", "storm_mlp_train",
     "storm_self_distance", "storm_set_surrogate", "storm_set_broadphase", "storm_set_trace",
@@ -164,6 +165,9 @@ def lib():
         L.storm_batch_set_distribution.argtypes = [vp, C.c_int, _fp, _fp]
         L.storm_batch_autotune.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_batch_get_launch.argtypes = [vp, ip, ip]
+        L.storm_batch_set_launch.argtypes = [vp, C.c_int, C.c_int]
+        L.storm_batch_set_launch_warp.argtypes = [vp, C.c_int]
+        L.storm_batch_get_launch_mapping.argtypes = [vp]
         L.storm_mlp_create.argtypes = [C.c_uint64, vp, C.POINTER(vp)]
         L.storm_mlp_create_arch.argtypes = [C.c_uint64, C.c_int, vp, C.POINTER(vp)]
         L.storm_mlp_param_count.argtypes = [vp]
@@ -646,6 +650,19 @@ class BatchController:
         a, b = C.c_int(), C.c_int()
         self._check(lib().storm_batch_get_launch(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def set_launch(self, items_per_tile: int, threads: int):
+        """CTA-wide mapping of the batched rollout."""
+        self._check(lib().storm_batch_set_launch(self.h, int(items_per_tile), int(threads)))
+
+    def set_launch_warp(self, warps_per_cta: int):
+        """Warp mapping of the batched rollout (the default)."""
+        self._check(lib().storm_batch_set_launch_warp(self.h, int(warps_per_cta)))
+
+    @property
+    def launch_mapping(self) -> str:
+        return {STORM_MAP_CTA: "cta", STORM_MAP_WARP: "warp"}[
+            self._check(lib().storm_batch_get_launch_mapping(self.h))]
 
 
 MLP_ARCHS = {"distance": 0, "jointnerf": 1}

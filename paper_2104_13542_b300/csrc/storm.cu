@@ -1219,6 +1219,38 @@ k_rollout_batch(const BatchInstance* __restrict__ insts, const BatchTile* __rest
     }
 }
 
+// Rollout of every instance on the warp mapping: each warp takes (instance,
+// particle group) tasks from the list (sorted by decreasing work), copies the
+// instance's Problem into its own shared slot and runs the single-handle warp
+// body, so each instance's results are bitwise those of its own handle.
+__global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
+k_rollout_warp_batch(const BatchInstance* __restrict__ insts, const int2* __restrict__ tasks, int n_tasks,
+                     int iter, int warp_floats)
+{
+    extern __shared__ __align__(16) float wsm[];
+    __shared__ Problem s_pb[kWarpMaxWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    Problem& pb = s_pb[warp];
+    int* dst = reinterpret_cast<int*>(&pb);
+    int loaded = -1;
+    for (int t = blockIdx.x * wpc + warp; t < n_tasks; t += gridDim.x * wpc) {
+        const int2 task = tasks[t];
+        const BatchInstance& I = insts[task.x];
+        if (iter >= I.K) continue;
+        if (task.x != loaded) {
+            __syncwarp();
+            const int* src = reinterpret_cast<const int*>(&I.pb);
+            for (int k = lane; k < static_cast<int>(sizeof(Problem) / 4); k += 32) dst[k] = src[k];
+            __syncwarp();
+            loaded = task.x;
+        }
+        const RolloutOut out{I.u, nullptr, nullptr, nullptr, nullptr, nullptr, I.C};
+        rollout_warp_body<false>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
+                                 wsm + size_t(warp) * warp_floats);
+        __syncwarp();
+    }
+}
+
 // Distribution update of every instance: one CTA per (instance, horizon step).
 __global__ void __launch_bounds__(kUpdateThreads)
 k_update_batch(const BatchInstance* __restrict__ insts, const int2* __restrict__ rows, int iter)
@@ -2885,6 +2917,8 @@ struct storm_batch {
     bool own_stream = false;
     int n = 0, Kmax = 1;
     int threads = kThreads, items = 64;
+    int mapping = STORM_MAP_WARP;  // rollout work mapping (CTA tiles or warp tasks)
+    int wpc = 4;                   // warps per CTA of the warp mapping
     std::vector<BatchInstance> inst;  // host mirror of d_inst
     std::vector<int> dof, state_off, cmd_off;
     std::vector<double> sigma_init;
@@ -2892,6 +2926,8 @@ struct storm_batch {
     void* arena = nullptr;
     BatchInstance* d_inst = nullptr;
     BatchTile* d_tiles = nullptr;
+    int2* d_tasks = nullptr;  // (instance, particle group) of the warp mapping
+    int n_tasks = 0, warp_floats = 0;
     int2* d_rows = nullptr;
     int n_tiles = 0, n_rows = 0, grid = 0;
     float* d_in = nullptr;   // states | goals
@@ -2976,7 +3012,74 @@ int batch_apply_launch(storm_batch* b, int items, int threads)
     b->rollout_smem = smem;
     b->items = items;
     b->threads = threads;
+    b->mapping = STORM_MAP_CTA;
     return STORM_OK;
+}
+
+// Warp mapping: one task per (instance, group of PW particles), largest first;
+// every warp's shared region is sized for the largest instance.
+int batch_apply_launch_warp(storm_batch* b, int wpc)
+{
+    if (wpc < 1 || wpc > kWarpMaxWarps) {
+        b->err = "warps per CTA must be in 1..8";
+        return STORM_ERR_INVALID_ARG;
+    }
+    std::vector<std::pair<double, int2>> w;
+    int floats = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const Problem& pb = b->inst[i].pb;
+        const WarpPlan wp = warp_plan(pb);
+        floats = std::max(floats, wp.floats);
+        const double per_item = 100.0 + pb.M * (pb.B + pb.O) + 49.0 * pb.NPB + pb.P;
+        for (int g = 0; g * wp.PW < pb.N; ++g)
+            w.push_back({std::min(wp.PW, pb.N - g * wp.PW) * pb.H * per_item, make_int2(i, g)});
+    }
+    std::stable_sort(w.begin(), w.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<int2> tasks;
+    for (auto& e : w) tasks.push_back(e.second);
+    const size_t smem = sizeof(float) * size_t(floats) * wpc;
+    int optin = 0, sms = 0;
+    BK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    cudaFuncAttributes fa;
+    BK(cudaFuncGetAttributes(&fa, k_rollout_warp_batch));
+    if (smem + fa.sharedSizeBytes > size_t(optin)) {
+        b->err = "warp shape needs too much shared memory";
+        return STORM_ERR_INVALID_ARG;
+    }
+    BK(cudaFuncSetAttribute(k_rollout_warp_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(fa.sharedSizeBytes)));
+    int per_sm = 0;
+    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rollout_warp_batch, wpc * 32, smem));
+    if (per_sm < 1) {
+        b->err = "warp shape does not fit an SM";
+        return STORM_ERR_INVALID_ARG;
+    }
+    if (b->d_tasks) cudaFree(b->d_tasks);
+    b->d_tasks = nullptr;
+    BK(cudaMalloc(&b->d_tasks, sizeof(int2) * tasks.size()));
+    BK(cudaMemcpyAsync(b->d_tasks, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice,
+                       b->stream));
+    BK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInstance) * b->n,
+                       cudaMemcpyHostToDevice, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    b->n_tasks = static_cast<int>(tasks.size());
+    b->grid = std::min((b->n_tasks + wpc - 1) / wpc, per_sm * sms);
+    b->rollout_smem = smem;
+    b->warp_floats = floats;
+    b->wpc = wpc;
+    b->mapping = STORM_MAP_WARP;
+    return STORM_OK;
+}
+
+cudaError_t batch_launch_rollout(storm_batch* b, cudaStream_t s, int iter)
+{
+    if (b->mapping == STORM_MAP_WARP)
+        k_rollout_warp_batch<<<b->grid, b->wpc * 32, b->rollout_smem, s>>>(b->d_inst, b->d_tasks, b->n_tasks,
+                                                                           iter, b->warp_floats);
+    else
+        k_rollout_batch<<<b->grid, b->threads, b->rollout_smem, s>>>(b->d_inst, b->d_tiles, b->n_tiles, iter);
+    return cudaGetLastError();
 }
 
 int batch_enqueue(storm_batch* b, cudaStream_t s)
@@ -2984,9 +3087,7 @@ int batch_enqueue(storm_batch* b, cudaStream_t s)
     k_shift_batch<<<b->n, 128, 0, s>>>(b->d_inst);
     BK(cudaGetLastError());
     for (int k = 0; k < b->Kmax; ++k) {
-        k_rollout_batch<<<b->grid, b->threads, b->rollout_smem, s>>>(b->d_inst, b->d_tiles,
-                                                                    b->n_tiles, k);
-        BK(cudaGetLastError());
+        BK(batch_launch_rollout(b, s, k));
         k_update_batch<<<b->n_rows, kUpdateThreads, b->update_smem, s>>>(b->d_inst, b->d_rows, k);
         BK(cudaGetLastError());
     }
@@ -3036,6 +3137,7 @@ void batch_free(storm_batch* b)
     if (b->arena) cudaFree(b->arena);
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_tasks) cudaFree(b->d_tasks);
     if (b->d_rows) cudaFree(b->d_rows);
     if (b->d_in) cudaFree(b->d_in);
     if (b->d_out) cudaFree(b->d_out);
@@ -3127,7 +3229,7 @@ int batch_create_impl(storm_batch* b, int n, const storm_robot* r, const storm_w
     }
     BK(cudaFuncSetAttribute(k_update_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             optin - static_cast<int>(ua.sharedSizeBytes)));
-    const int rc = batch_apply_launch(b, 64, kThreads);
+    const int rc = batch_apply_launch_warp(b, 4);
     if (rc) return rc;
     return batch_build_graphs(b);
 }
@@ -3255,9 +3357,31 @@ int storm_batch_set_distribution(storm_batch* b, int i, const float* mean, const
 int storm_batch_get_launch(const storm_batch* b, int* items, int* threads)
 {
     if (!b) return STORM_ERR_INVALID_ARG;
-    if (items) *items = b->items;
-    if (threads) *threads = b->threads;
+    const bool warp = b->mapping == STORM_MAP_WARP;
+    if (items) *items = warp ? 32 * b->wpc : b->items;
+    if (threads) *threads = warp ? 32 * b->wpc : b->threads;
     return STORM_OK;
+}
+
+int storm_batch_get_launch_mapping(const storm_batch* b) { return b ? b->mapping : STORM_ERR_INVALID_ARG; }
+
+int storm_batch_set_launch(storm_batch* b, int items_per_tile, int threads)
+{
+    if (!b || threads < 32 || threads > kMaxThreads || threads % 32 || items_per_tile < 1)
+        return STORM_ERR_INVALID_ARG;
+    BK(cudaStreamSynchronize(b->stream));
+    const int rc = batch_apply_launch(b, items_per_tile, threads);
+    if (rc) return rc;
+    return batch_build_graphs(b);
+}
+
+int storm_batch_set_launch_warp(storm_batch* b, int warps_per_cta)
+{
+    if (!b || warps_per_cta < 1 || warps_per_cta > kWarpMaxWarps) return STORM_ERR_INVALID_ARG;
+    BK(cudaStreamSynchronize(b->stream));
+    const int rc = batch_apply_launch_warp(b, warps_per_cta);
+    if (rc) return rc;
+    return batch_build_graphs(b);
 }
 
 int storm_batch_autotune(storm_batch* b, float* best_us)
@@ -3266,41 +3390,50 @@ int storm_batch_autotune(storm_batch* b, float* best_us)
     BK(cudaStreamSynchronize(b->stream));
     const int items_c[] = {32, 48, 64, 96, 128};
     const int threads_c[] = {128, 256, 512};
-    const int old_items = b->items, old_threads = b->threads;
+    const int wpcs[] = {1, 2, 4, 8};
     float best = INFINITY;
-    int bi = old_items, bt = old_threads;
+    int bm = b->mapping, bi = b->items, bt = b->threads, bw = b->wpc;
     cudaEvent_t e0, e1;
     BK(cudaEventCreate(&e0));
     BK(cudaEventCreate(&e1));
+    std::vector<int3> shapes;  // (mapping, items or warps, threads)
     for (int it : items_c)
-        for (int th : threads_c) {
-            if (batch_apply_launch(b, it, th) != STORM_OK) continue;
-            std::vector<float> t;
-            for (int r = 0; r < 8; ++r) {
-                cudaEventRecord(e0, b->stream);
-                k_rollout_batch<<<b->grid, b->threads, b->rollout_smem, b->stream>>>(
-                    b->d_inst, b->d_tiles, b->n_tiles, 0);
-                cudaEventRecord(e1, b->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    b->err = "autotune launch failed";
-                    return STORM_ERR_CUDA;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (r >= 2) t.push_back(ms * 1e3f);
+        for (int th : threads_c) shapes.push_back(make_int3(STORM_MAP_CTA, it, th));
+    for (int w : wpcs) shapes.push_back(make_int3(STORM_MAP_WARP, w, 32 * w));
+    for (const int3 sh : shapes) {
+        const int rc = sh.x == STORM_MAP_WARP ? batch_apply_launch_warp(b, sh.y)
+                                              : batch_apply_launch(b, sh.y, sh.z);
+        if (rc != STORM_OK) continue;
+        std::vector<float> t;
+        for (int r = 0; r < 8; ++r) {
+            cudaEventRecord(e0, b->stream);
+            const cudaError_t le = batch_launch_rollout(b, b->stream, 0);
+            cudaEventRecord(e1, b->stream);
+            if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                b->err = "autotune launch failed";
+                return STORM_ERR_CUDA;
             }
-            std::sort(t.begin(), t.end());
-            if (t[t.size() / 2] < best) {
-                best = t[t.size() / 2];
-                bi = it;
-                bt = th;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r >= 2) t.push_back(ms * 1e3f);
+        }
+        std::sort(t.begin(), t.end());
+        if (t[t.size() / 2] < best) {
+            best = t[t.size() / 2];
+            bm = sh.x;
+            if (sh.x == STORM_MAP_WARP) {
+                bw = sh.y;
+            } else {
+                bi = sh.y;
+                bt = sh.z;
             }
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const int rc = batch_apply_launch(b, bi, bt);
+    const int rc = bm == STORM_MAP_WARP ? batch_apply_launch_warp(b, bw) : batch_apply_launch(b, bi, bt);
     if (rc) return rc;
     if (best_us) *best_us = best;
     return batch_build_graphs(b);

@@ -125,23 +125,20 @@ __device__ __forceinline__ void pair_sync(int unit)
     asm volatile("barrier.sync %0, 64;" ::"r"(unit + 1) : "memory");
 }
 
+// The rollout of particle group `wg` (particles wg*PW ..) of problem pb by
+// this warp (or warp pair `unit`), in the warp's shared-memory region ws.
 template <bool kPair>
-__global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
-k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
-               const StepState* __restrict__ st, int step_override, int iter, int front_only)
+__device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
+                                                  const float* __restrict__ state, const float* __restrict__ goal,
+                                                  uint32_t step, int iter, int front_only, int wg, int unit, float* ws)
 {
-    extern __shared__ __align__(16) float wsm[];
     const WarpPlan W = warp_plan(pb);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int unit = kPair ? warp >> 1 : warp;  // the warp, or warp pair, of a particle group
     const bool do_costs = !kPair || (warp & 1) == 0;  // A: controls, integration, non-collision costs
     const bool do_coll = !kPair || (warp & 1) == 1;   // B: world and self collision
-    const int units = kPair ? (blockDim.x >> 6) : (blockDim.x >> 5);
-    const int wg = blockIdx.x * units + unit;
     const int nw0 = wg * W.PW;  // first particle of this unit
     if (nw0 >= pb.N) return;    // uniform over the unit (both warps of a pair)
-    float* ws = wsm + unit * W.floats;
     float* s_fr = ws + W.frame;
     float* s_cb = ws + W.cb;
     float* s_eps = ws + W.eps;
@@ -154,7 +151,6 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
     const int np_w = min(W.PW, pb.N - nw0);
     const int n = nw0 + seg;
     const bool pvalid = seg < np_w;
-    const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
     trace_stamp(pb.trace, 0);
     if (do_costs) {
     {
@@ -698,4 +694,19 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
         out.Ctot[nw0 + lane] = C;
     }
     trace_stamp(pb.trace, 6);
+}
+
+template <bool kPair>
+__global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
+k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
+               const StepState* __restrict__ st, int step_override, int iter, int front_only)
+{
+    extern __shared__ __align__(16) float wsm[];
+    const WarpPlan W = warp_plan(pb);
+    const int warp = threadIdx.x >> 5;
+    const int unit = kPair ? warp >> 1 : warp;  // the warp, or warp pair, of a particle group
+    const int units = kPair ? (blockDim.x >> 6) : (blockDim.x >> 5);
+    const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
+    rollout_warp_body<kPair>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
+                             wsm + unit * W.floats);
 }

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2104_13542_b300 import BatchController, Controller
+from paper_2104_13542_b300 import BatchController, Controller, StormError
 from paper_2104_13542_b300 import workloads as W
 
 from gpu_helpers import f32, max_rel, mu_tolerance
@@ -70,10 +70,55 @@ def test_batch_autotune_keeps_results():
         t = b.autotune()
         assert 0 < t < 1e5
         items, threads = b.get_launch()
-        assert items in (32, 48, 64, 96, 128) and threads in (128, 256, 512)
+        if b.launch_mapping == "cta":
+            assert items in (32, 48, 64, 96, 128) and threads in (128, 256, 512)
+        else:
+            assert items == threads and threads in (32, 64, 128, 256)
         got, _ = b.step(states, goals)
     for x, y in zip(ref, got):
         assert np.array_equal(x, y)
+
+
+def test_batch_mappings_bitwise_identical():
+    """The CTA-tile and warp-task mappings of the batched rollout, at several
+    shapes, give the same commands and distributions bit for bit."""
+    wls = _batch(9, seed=4)
+    # short horizons too, so that the warp mapping packs 2 and 4 particles per warp
+    for i, h in ((0, 6), (1, 8), (2, 12)):
+        p = wls[i].params
+        wls[i].params = p.replace(H=h, dt=np.full(h, 0.02))
+    states = [f32(wl.state) for wl in wls]
+    goals = np.stack([f32(wl.goal) for wl in wls])
+    args = ([w.robot for w in wls], [w.world for w in wls], [w.params for w in wls])
+    runs = []
+    for shape in (("warp", 4), ("cta", 64, 256), ("warp", 1), ("warp", 8), ("cta", 32, 128)):
+        with BatchController(*args) as b:
+            assert b.launch_mapping == "warp"
+            if shape[0] == "warp":
+                b.set_launch_warp(shape[1])
+            else:
+                b.set_launch(shape[1], shape[2])
+            assert b.launch_mapping == shape[0]
+            cmds = [b.step(states, goals)[0] for _ in range(2)]
+            runs.append((cmds, [b.get_distribution(i) for i in range(len(wls))]))
+    for cmds, dists in runs[1:]:
+        for t in range(2):
+            for x, y in zip(cmds[t], runs[0][0][t]):
+                assert np.array_equal(x, y)
+        for (m, s), (m0, s0) in zip(dists, runs[0][1]):
+            assert np.array_equal(m, m0) and np.array_equal(s, s0)
+
+
+def test_batch_launch_shapes_are_validated():
+    wls = _batch(2, seed=5)
+    with BatchController([w.robot for w in wls], [w.world for w in wls], [w.params for w in wls]) as b:
+        for bad in (0, 9):
+            with pytest.raises(StormError):
+                b.set_launch_warp(bad)
+        for items, threads in ((0, 128), (64, 48), (64, 1024)):
+            with pytest.raises(StormError):
+                b.set_launch(items, threads)
+        assert b.launch_mapping == "warp"
 
 
 def test_full_size_batch_runs():
