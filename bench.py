@@ -212,6 +212,8 @@ def run_gpu(args, rank, world_size):
             ppc, threads = (int(x) for x in shape.split(","))
             ctl.set_launch(ppc, threads)
         tuned_us = None
+    if args.dep_launch:
+        ctl.set_dependent_launch(True)
     ctl.reset()
 
     # ---------------- device-resident timing (value)
@@ -323,6 +325,7 @@ def run_gpu(args, rank, world_size):
                                  "with the collision broad phase the kernel executes fewer",
                   "brute_force_kernel_ms": rk_bf_ms, "brute_force_frac": achieved_bf / peak,
                   "launch_shape": list(ctl.get_launch()), "autotune_us": tuned_us,
+                  "dependent_launch": ctl.dependent_launch(),
                   "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                 f"{sm_mhz:.0f} MHz (unit count x SM max clock; MEASURED_PEAKS has "
                                 f"no FP32 figure)"},
@@ -406,7 +409,7 @@ def run_variants(args, seed: int):
         out["batched_256"] = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99)),
                               "rollout_steps_per_s": units * len(ms) / float(ms.sum() / 1e3),
                               "instances": len(wls), "rollout_steps_per_step": units,
-                              "mapping": b.launch_mapping, "tile": b.get_launch(),
+                              "mapping": b.launch_mapping(), "tile": b.get_launch(),
                               "autotune_rollout_us": t_tune}
     # learned self-collision surrogate at 1000 x 30
     wl = W.config_paper(seed, N=1000, H=30)
@@ -630,6 +633,8 @@ def main():
     ap.add_argument("--launch", default="auto",
                     help="rollout launch shape: auto (autotuned), warp:W (W warps per CTA), pair:W (W warp "
                          "pairs per CTA) or cta:P,T")
+    ap.add_argument("--dep-launch", action="store_true",
+                    help="launch the step graph's rollouts and updates as programmatic dependents")
     ap.add_argument("--mlp-forward", type=int, default=0, metavar="ROWS",
                     help="time the surrogate networks' forward pass on ROWS configurations instead")
     ap.add_argument("--ablation", action="store_true",

@@ -303,6 +303,19 @@ int storm_get_launch(const storm_handle* h, int* particles_per_cta, int* threads
 /* STORM_MAP_CTA, STORM_MAP_WARP or STORM_MAP_WARP_PAIR; INVALID_ARG for a NULL handle. */
 int storm_get_launch_mapping(const storm_handle* h);
 
+/* Dependent launch in the step graph (on = 1; off = 0, the default): every
+ * rollout and distribution update is launched as a programmatic dependent of
+ * the kernel before it, so its CTAs start while that kernel finishes and the
+ * rollout draws its noise (a function of seed, step and iteration only) before
+ * waiting for the previous update's mu and sigma.  Results are bitwise the same
+ * either way; only the step graph uses it (the single-stage calls launch
+ * ordinarily).  Off by default: on the 500 x 30 workload the early CTAs cost
+ * more (the rollout's phases after the wait run slower) than the overlap
+ * saves.  Re-captures the step graph; waits.  Errors: INVALID_ARG for a NULL
+ * handle or on not 0 / 1.  storm_get_dependent_launch: 1, 0 or INVALID_ARG. */
+int storm_set_dependent_launch(storm_handle* h, int on);
+int storm_get_dependent_launch(const storm_handle* h);
+
 /* Tracing: with trace_dev (device, 7 x uint64) set, thread 0 of rollout CTA 0
  * writes %globaltimer (ns) at the phase boundaries of every rollout launch:
  * [0] start, [1] tables + noise staged, [2] controls + integration, [3] FK,

@@ -46,6 +46,7 @@ EXPORTED = [
     "storm_batch_device_io", "storm_batch_sync", "storm_batch_get_distribution",
     "storm_batch_set_distribution", "storm_batch_autotune", "storm_batch_get_launch",
     "storm_batch_set_launch", "storm_batch_set_launch_warp", "storm_batch_get_launch_mapping",
+    "storm_set_dependent_launch", "storm_get_dependent_launch",
     "storm_mlp_create", "storm_mlp_destroy", "storm_mlp_last_error", "storm_mlp_get_params",
     "storm_mlp_set_params", "storm_mlp_predict", "storm_mlp_loss_grad", "storm_mlp_train",
     "storm_self_distance", "storm_set_surrogate", "storm_set_broadphase", "storm_set_trace",
@@ -168,6 +169,8 @@ def lib():
         L.storm_batch_set_launch.argtypes = [vp, C.c_int, C.c_int]
         L.storm_batch_set_launch_warp.argtypes = [vp, C.c_int]
         L.storm_batch_get_launch_mapping.argtypes = [vp]
+        L.storm_set_dependent_launch.argtypes = [vp, C.c_int]
+        L.storm_get_dependent_launch.argtypes = [vp]
         L.storm_mlp_create.argtypes = [C.c_uint64, vp, C.POINTER(vp)]
         L.storm_mlp_create_arch.argtypes = [C.c_uint64, C.c_int, vp, C.POINTER(vp)]
         L.storm_mlp_param_count.argtypes = [vp]
@@ -452,6 +455,13 @@ class Controller:
             self._check(m)
         return {STORM_MAP_WARP: "warp", STORM_MAP_WARP_PAIR: "pair"}.get(m, "cta")
 
+    def set_dependent_launch(self, on: bool):
+        """Programmatic dependent launch of the step graph's rollouts and updates."""
+        self._check(lib().storm_set_dependent_launch(self.h, 1 if on else 0))
+
+    def dependent_launch(self) -> bool:
+        return bool(self._check(lib().storm_get_dependent_launch(self.h)))
+
     def ee_twist(self, theta_dev, theta_dot_dev, theta_ddot_dev):
         """(X_dot, X_ddot) of Eq. 8 for count configurations: two count x 6 tensors."""
         n = theta_dev.shape[0]
@@ -659,7 +669,6 @@ class BatchController:
         """Warp mapping of the batched rollout (the default)."""
         self._check(lib().storm_batch_set_launch_warp(self.h, int(warps_per_cta)))
 
-    @property
     def launch_mapping(self) -> str:
         return {STORM_MAP_CTA: "cta", STORM_MAP_WARP: "warp"}[
             self._check(lib().storm_batch_get_launch_mapping(self.h))]

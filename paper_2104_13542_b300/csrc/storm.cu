@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <map>
+#include <utility>
 #include <mutex>
 #include <set>
 #include <cmath>
@@ -131,8 +132,8 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         uint4* dst = reinterpret_cast<uint4*>(smem + L.tab);
         for (int i = tid; i < pb.table_bytes / 16; i += nt) dst[i] = src[i];
     }
-    for (int i = tid; i < HD; i += nt) s_mu[i] = pb.mu[i];
-    for (int i = tid; i < d; i += nt) s_sigma[i] = pb.sigma[i];
+    for (int i = tid; i < HD; i += nt) s_mu[i] = __ldcg(pb.mu + i);
+    for (int i = tid; i < d; i += nt) s_sigma[i] = __ldcg(pb.sigma + i);
     for (int i = tid; i < 3 * d; i += nt) s_state[i] = state[i];
     if (tid == 0) {
         // goal rotation R_g (row-major) from the normalised quaternion, then p_g
@@ -628,6 +629,8 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
     extern __shared__ __align__(16) unsigned char smem[];
     const int n0 = blockIdx.x * pb.ppc;
     const int np = min(pb.ppc, pb.N - n0);
+    pdl_trigger();
+    pdl_wait();
     if (np <= 0) return;
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
     rollout_particles(pb, out, state, goal, step, iter, n0, np, smem, front_only);
@@ -755,15 +758,17 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
 
     // ---- this thread's costs and row-h controls (and the old mean of row h), loaded together
-    const float mu_old = tid < d ? pb.mu[h * d + tid] : 0.f;
+    // (all through L2: under a dependent launch this CTA may have started
+    // before the rollout that wrote them finished)
+    const float mu_old = tid < d ? __ldcg(pb.mu + h * d + tid) : 0.f;
     float cv[kUpdKeep], uv[kUpdKeep][kMaxDof];
 #pragma unroll
     for (int k = 0; k < kUpdKeep; ++k) {
         const int n = tid + k * T;
-        cv[k] = n < N ? C[n] : INFINITY;
+        cv[k] = n < N ? __ldcg(C + n) : INFINITY;
         const float* un = u + static_cast<size_t>(n < N ? n : 0) * O + h * d;
 #pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) uv[k][j] = (n < N && j < d) ? un[j] : 0.f;
+        for (int j = 0; j < kMaxDof; ++j) uv[k][j] = (n < N && j < d) ? __ldcg(un + j) : 0.f;
     }
 
     // ---- min finite cost and its lowest index
@@ -778,7 +783,7 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
         }
     }
     for (int n = tid + kUpdKeep * T; n < N; n += T) {
-        const float c = C[n];
+        const float c = __ldcg(C + n);
         if (isfinite(c) && c < bv) {
             bv = c;
             bi = n;
@@ -808,7 +813,7 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
             if (w > 0.f) lsc = fmaf(w, cv[k], lsc);
         }
         for (int n = tid + kUpdKeep * T; n < N; n += T) {
-            const float c = C[n];
+            const float c = __ldcg(C + n);
             const float w = weight(n, c);
             s_w[n] = w;
             ls += w;
@@ -835,7 +840,7 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
             const float* un = u + static_cast<size_t>(n) * O + h * d;
 #pragma unroll
             for (int j = 0; j < kMaxDof; ++j)
-                if (j < d) acc[j] = fmaf(w, un[j], acc[j]);
+                if (j < d) acc[j] = fmaf(w, __ldcg(un + j), acc[j]);
         }
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) {
@@ -871,7 +876,7 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
 #pragma unroll
             for (int j = 0; j < kMaxDof; ++j)
                 if (j < d) {
-                    const float e = un[j] - s_mu[j];
+                    const float e = __ldcg(un + j) - s_mu[j];
                     acc[j] = fmaf(w * e, e, acc[j]);
                 }
         }
@@ -916,7 +921,7 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
             float v = 0.f;
             for (int hh = 0; hh < pb.H; ++hh) v += s_var[hh * d + j];
             v = v / s / static_cast<float>(pb.H);
-            const float sg = pb.sigma[j];
+            const float sg = __ldcg(pb.sigma + j);
             float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
             var = fmaxf(var, pb.sigma_min * pb.sigma_min);
             pb.sigma[j] = sqrtf(var);
@@ -938,6 +943,8 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
          float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out,
          int finalize, UpdateScratch* scr)
 {
+    pdl_trigger();
+    pdl_wait();
     update_row(pb, C, u, weights_out, st, cmd_out, finalize, scr, blockIdx.x, gridDim.x);
 }
 
@@ -987,7 +994,11 @@ __device__ __forceinline__ void shift_body(const Problem& pb, StepState* st, int
     if (threadIdx.x == 0 && !force) st->status = 0;
 }
 
-__global__ void k_shift(Problem pb, StepState* st, int force) { shift_body(pb, st, force); }
+__global__ void k_shift(Problem pb, StepState* st, int force)
+{
+    pdl_trigger();
+    shift_body(pb, st, force);
+}
 
 // Batched forward kinematics (Eq. 8): one thread per configuration.
 __global__ void k_fk(Problem pb, const float* __restrict__ theta, int count, float* __restrict__ ee)
@@ -1578,6 +1589,7 @@ struct storm_handle {
     int threads = kThreads;  // rollout CTA size (CTA-wide mapping)
     int mapping = STORM_MAP_WARP;  // rollout work mapping
     int wpc = 2;                   // warps (warp mapping) or warp pairs (pair mapping) per CTA
+    bool dep_launch = false;       // step graph: rollouts and updates as programmatic dependents
     size_t warp_smem = 0;          // its dynamic shared memory
     int warp_grid = 0;
     // device allocations
@@ -1782,31 +1794,53 @@ int upload_world(storm_handle* h, const storm_world* w)
     return STORM_OK;
 }
 
+// A kernel launch; with dep set, as a programmatic dependent of the stream's
+// previous kernel (it may start before that kernel ends and must pdl_wait
+// before reading anything the predecessor writes).
+template <typename... Params, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(Params...), unsigned grid, unsigned block, size_t smem,
+                          cudaStream_t s, bool dep, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = dep ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// dep: launched as a dependent of the previous kernel.  Only the step graph
+// sets it, where the predecessor (the shift or a non-final update) never
+// advances the step counter that the rollout reads before its pdl_wait.
 int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const float* state,
                    const float* goal, int step_override, int iter, bool exact_self = false,
-                   int front_only = 0)
+                   int front_only = 0, bool dep = false)
 {
     Problem pb = h->pb;
     if (exact_self) pb.self_pred = nullptr;
+    pb.dep_launch = dep ? 1 : 0;
     if (h->mapping == STORM_MAP_WARP)
-        k_rollout_warp<false><<<h->warp_grid, h->wpc * 32, h->warp_smem, s>>>(pb, out, state, goal, h->d_st,
-                                                                             step_override, iter, front_only);
+        CK(launch_kernel(k_rollout_warp<false>, h->warp_grid, h->wpc * 32, h->warp_smem, s, dep, pb, out, state,
+                         goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
     else if (h->mapping == STORM_MAP_WARP_PAIR)
-        k_rollout_warp<true><<<h->warp_grid, h->wpc * 64, h->warp_smem, s>>>(pb, out, state, goal, h->d_st,
-                                                                            step_override, iter, front_only);
+        CK(launch_kernel(k_rollout_warp<true>, h->warp_grid, h->wpc * 64, h->warp_smem, s, dep, pb, out, state,
+                         goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
     else
-        k_rollout<<<h->grid, h->threads, h->rollout_smem, s>>>(pb, out, state, goal, h->d_st, step_override,
-                                                             iter, front_only);
-    CK(cudaGetLastError());
+        CK(launch_kernel(k_rollout, h->grid, h->threads, h->rollout_smem, s, dep, pb, out, state, goal,
+                         static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
     return STORM_OK;
 }
 
 int launch_update(storm_handle* h, cudaStream_t s, const float* C, const float* u, float* w,
-                  float* cmd, int finalize)
+                  float* cmd, int finalize, bool dep = false)
 {
-    k_update<<<h->pb.H, kUpdateThreads, h->update_smem, s>>>(h->pb, C, u, w, h->d_st, cmd, finalize,
-                                                              h->d_upd);
-    CK(cudaGetLastError());
+    CK(launch_kernel(k_update, h->pb.H, kUpdateThreads, h->update_smem, s, dep, h->pb, C, u, w, h->d_st, cmd,
+                     finalize, h->d_upd));
     return STORM_OK;
 }
 
@@ -1837,15 +1871,16 @@ int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
     for (int k = 0; k < h->K; ++k) {
         if (h->mlp) {  // surrogate: joint states, network, then the rollout proper
             RolloutOut front{h->d_u, h->d_theta, nullptr, nullptr, nullptr, nullptr, h->d_C};
-            int rc = launch_rollout(h, s, front, state, goal, -1, k, false, 1);
+            int rc = launch_rollout(h, s, front, state, goal, -1, k, false, 1, h->dep_launch);
             if (rc) return rc;
             rc = mlp_forward(h->mlp, *h->mlp_buf, h->d_theta, h->pb.N * h->pb.H, h->pb.d, false,
                              h->d_pred, s);
             if (rc) return fail(h, rc, "surrogate forward launch failed");
         }
-        int rc = launch_rollout(h, s, out, state, goal, -1, k);
+        int rc = launch_rollout(h, s, out, state, goal, -1, k, false, 0, h->dep_launch);
         if (rc) return rc;
-        rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1 && h->grad_steps == 0);
+        rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1 && h->grad_steps == 0,
+                           h->dep_launch);
         if (rc) return rc;
     }
     for (int g = 0; g < h->grad_steps; ++g) {  // gradient refinement of the mean
@@ -2510,6 +2545,16 @@ int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
 }
 
 int storm_get_launch_mapping(const storm_handle* h) { return h ? h->mapping : STORM_ERR_INVALID_ARG; }
+
+int storm_set_dependent_launch(storm_handle* h, int on)
+{
+    if (!h || (on != 0 && on != 1)) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    h->dep_launch = on == 1;
+    return build_graphs(h);
+}
+
+int storm_get_dependent_launch(const storm_handle* h) { return h ? (h->dep_launch ? 1 : 0) : STORM_ERR_INVALID_ARG; }
 
 static int set_launch_warp_impl(storm_handle* h, int wpc, bool rebuild, bool pair = false)
 {

@@ -46,6 +46,7 @@ struct Problem {
     const uint4* pblk;       // NPB: (a0, a1, b0, nb): spheres [a0, a1) x [b0, b0 + nb), nb <= 8
     const float4* lbound;    // d + 1: bounding sphere of each frame's spheres (local centre, radius)
     int broadphase;          // 1: exact sphere tests only where the link bounds overlap
+    int dep_launch;          // 1: this rollout launch is a programmatic dependent
     unsigned long long* trace;  // nullable: phase-boundary %globaltimer stamps of rollout CTA 0
     const uint4* tables;     // start of the contiguous per-problem tables (dhx .. basis)
     int table_bytes;         // their size, a multiple of 16
@@ -83,6 +84,14 @@ struct StepState {
     float best;      // min total cost of the last iteration
     float wmean;     // weighted mean total cost of the last iteration
 };
+
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream still runs:
+// pdl_wait blocks until that predecessor has completed and its writes are
+// visible to this grid; pdl_trigger lets this kernel's own dependent start
+// launching its CTAs.  Both are no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Phase stamp of the rollout trace (CTA 0, thread 0 only).
 __device__ __forceinline__ void trace_stamp(unsigned long long* trace, int phase)
@@ -128,11 +137,38 @@ __device__ __forceinline__ float2 gauss_pair(uint32_t a, uint32_t b)
 // ---------------------------------------------------------------- kinematics
 // One modified-DH link: T <- T RotX(alpha) TransX(a) RotZ(theta) TransZ(d),
 // with R row-major 3x3 and p the origin.  In place.
+// sin and cos of a joint angle, branch-free: Cody-Waite reduction by pi/2
+// (pi/2 split in three parts, the upper two with few enough significant bits
+// that q times them is exact for |q| < 2^13, each step one FMA), then the
+// Cephes single-precision minimax polynomials for sin and cos on
+// [-pi/4, pi/4] (S. L. Moshier, Cephes Math Library, sinf.c / cosf.c), swapped
+// and signed by the quadrant q mod 4.  Max error about 1e-7 absolute for
+// |x| < 10^4; NaN and infinities give NaN.  The chain calls it once per joint
+// of every (particle, step) item, so it is kept short and without a
+// large-argument branch.
+__device__ __forceinline__ void joint_sincos(float x, float& s, float& c)
+{
+    const float q = rintf(x * 0.636619772f);
+    float r = fmaf(-q, 1.5703125f, x);
+    r = fmaf(-q, 4.837512969970703125e-4f, r);
+    r = fmaf(-q, 7.54978995489188216e-8f, r);
+    const float z = r * r;
+    const float sp = fmaf(fmaf(fmaf(-1.9515295891e-4f, z, 8.3321608736e-3f), z, -1.6666654611e-1f), z * r, r);
+    const float cp = fmaf(fmaf(fmaf(2.443315711809948e-5f, z, -1.388731625493765e-3f), z, 4.166664568298827e-2f),
+                          z * z, fmaf(-0.5f, z, 1.0f));
+    const int k = static_cast<int>(q);
+    // x = k pi/2 + r: (sin, cos) = (sp, cp), (cp, -sp), (-sp, -cp), (-cp, sp) for k mod 4 = 0..3
+    const float s0 = (k & 1) ? cp : sp;
+    const float c0 = (k & 1) ? sp : cp;
+    s = (k & 2) ? -s0 : s0;
+    c = ((k + 1) & 2) ? -c0 : c0;
+}
+
 __device__ __forceinline__ void dh_step(float (&R)[9], float (&p)[3], float a, float ca, float sa,
                                         float dd, float theta)
 {
     float st, ct;
-    sincosf(theta, &st, &ct);
+    joint_sincos(theta, st, ct);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const float c0 = R[r * 3 + 0], c1 = R[r * 3 + 1], c2 = R[r * 3 + 2];

@@ -29,6 +29,7 @@ struct WarpPlan {
     int c;           // PW x H running costs
     int ba;          // PW x H x 2 ball in-plane gravity
     int ds, dw;      // PW x H self / world depths handed from warp B to A (pair variant)
+    int io;          // mu (H x d) | sigma (d) | state (3 x d) | goal (7), staged once per warp
     int floats;      // size of one warp's (pair's) region
 };
 
@@ -55,6 +56,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
     w.ba = take(w.PW * pb.H * 2);
     w.ds = take(w.PW * pb.H);
     w.dw = take(w.PW * pb.H);
+    w.io = take(pb.H * pb.d + 4 * pb.d + 7);
     w.floats = off;
     return w;
 }
@@ -155,15 +157,11 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     if (do_costs) {
     {
         // The grid is a single wave, so every warp meets this SM's L1 cold: pull
-        // the read-only tables (and the mean and sigma) into it now, while the
-        // noise is drawn, rather than one dependent miss at a time later.
+        // the read-only tables into it now, while the noise is drawn, rather
+        // than one dependent miss at a time later.
         const char* tb = reinterpret_cast<const char*>(pb.tables);
         for (int o = lane * 128; o < pb.table_bytes; o += 32 * 128)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(tb + o));
-        const char* mb = reinterpret_cast<const char*>(pb.mu);
-        for (int o = lane * 128; o < H * d * 4; o += 32 * 128)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(mb + o));
-        if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(pb.sigma));
     }
 
     // ---- noise eps[n][s][j] of the warp's particles
@@ -196,6 +194,28 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         __syncwarp();
     }
     trace_stamp(pb.trace, 1);
+    }
+    // The noise depends on (seed, step, iteration) only, so under a dependent
+    // launch it is drawn while the previous distribution update still runs;
+    // mu and sigma are read after it has finished (from L2).
+    pdl_wait();
+    // mu, sigma, the state and the goal: read by every lane, so staged with one
+    // coalesced pass per warp (the whole grid reads these same few lines)
+    float* s_mu = ws + W.io;
+    float* s_sig = s_mu + H * d;
+    float* s_st = s_sig + d;
+    float* s_goal = s_st + 3 * d;
+    if (pb.dep_launch) {  // the wait may have dropped the prefetched tables from L1
+        const char* tb = reinterpret_cast<const char*>(pb.tables);
+        for (int o = lane * 128; o < pb.table_bytes; o += 32 * 128)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(tb + o));
+    }
+    if (do_costs) {
+    for (int i = lane; i < H * d; i += 32) s_mu[i] = __ldcg(pb.mu + i);
+    if (lane < d) s_sig[lane] = __ldcg(pb.sigma + lane);
+    if (lane < 3 * d) s_st[lane] = state[lane];
+    if (lane < 7) s_goal[lane] = goal[lane];
+    __syncwarp();
 
     // ---- controls u = mu + sigma o (B eps) of the lane's own steps, null particles zero
     for (int slot = 0; slot < W.SL; ++slot) {
@@ -225,7 +245,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) {
             if (j < d) {
-                const float uu = null ? 0.f : fmaf(pb.sigma[j], e[j], pb.mu[h * d + j]);
+                const float uu = null ? 0.f : fmaf(s_sig[j], e[j], s_mu[h * d + j]);
                 su[j] = uu;
                 gu[j] = uu;
             }
@@ -235,7 +255,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     // ---- integration per (particle, joint), Eq. 7: the k_rollout recurrence
     if (lane < np_w * d) {
         const int p = lane / d, j = lane - p * d;
-        float v = state[d + j], q = state[j];
+        float v = s_st[d + j], q = s_st[j];
 #pragma unroll 6
         for (int h = 0; h < H; ++h) {
             const int idx = (p * H + h) * d + j;
@@ -262,8 +282,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     float4 lbf[kMaxDof + 1];
 #pragma unroll
     for (int f = 0; f <= kMaxDof; ++f) lbf[f] = f < F ? pb.lbound[f] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float g[12];  // goal rotation (row-major), then position
-    {
+    float g[12] = {};  // goal rotation (row-major), then position (cost warp only)
+    if (do_costs) {
+        const float* goal = s_goal;
         const float qn = rsqrtf(goal[3] * goal[3] + goal[4] * goal[4] + goal[5] * goal[5] + goal[6] * goal[6]);
         const float w = goal[3] * qn, x = goal[4] * qn, y = goal[5] * qn, z = goal[6] * qn;
         g[0] = 1.f - 2.f * (y * y + z * z);
@@ -294,7 +315,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         const float* th = s_th + (pl * H + hc) * d;
         const float* thd = s_thd + (pl * H + hc) * d;
         const float* uh = s_u + (pl * H + hc) * d;
-        const float* up = (hc == 0) ? state + 2 * d : uh - d;
+        const float* up = (hc == 0) ? s_st + 2 * d : uh - d;
         const size_t gi = static_cast<size_t>(n) * H + hc;  // global item (valid lanes)
 
         // ---- FK frames, Jacobian columns, bounding centres
@@ -706,6 +727,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
     const int warp = threadIdx.x >> 5;
     const int unit = kPair ? warp >> 1 : warp;  // the warp, or warp pair, of a particle group
     const int units = kPair ? (blockDim.x >> 6) : (blockDim.x >> 5);
+    pdl_trigger();
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
     rollout_warp_body<kPair>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
                              wsm + unit * W.floats);

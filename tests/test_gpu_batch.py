@@ -70,7 +70,7 @@ def test_batch_autotune_keeps_results():
         t = b.autotune()
         assert 0 < t < 1e5
         items, threads = b.get_launch()
-        if b.launch_mapping == "cta":
+        if b.launch_mapping() == "cta":
             assert items in (32, 48, 64, 96, 128) and threads in (128, 256, 512)
         else:
             assert items == threads and threads in (32, 64, 128, 256)
@@ -93,12 +93,12 @@ def test_batch_mappings_bitwise_identical():
     runs = []
     for shape in (("warp", 4), ("cta", 64, 256), ("warp", 1), ("warp", 8), ("cta", 32, 128)):
         with BatchController(*args) as b:
-            assert b.launch_mapping == "warp"
+            assert b.launch_mapping() == "warp"
             if shape[0] == "warp":
                 b.set_launch_warp(shape[1])
             else:
                 b.set_launch(shape[1], shape[2])
-            assert b.launch_mapping == shape[0]
+            assert b.launch_mapping() == shape[0]
             cmds = [b.step(states, goals)[0] for _ in range(2)]
             runs.append((cmds, [b.get_distribution(i) for i in range(len(wls))]))
     for cmds, dists in runs[1:]:
@@ -118,7 +118,7 @@ def test_batch_launch_shapes_are_validated():
         for items, threads in ((0, 128), (64, 48), (64, 1024)):
             with pytest.raises(StormError):
                 b.set_launch(items, threads)
-        assert b.launch_mapping == "warp"
+        assert b.launch_mapping() == "warp"
 
 
 def test_full_size_batch_runs():

@@ -236,6 +236,34 @@ def test_forward_kinematics_matches_oracle():
     assert max_rel(ee, o, 1.0) < TOL_STATE
 
 
+def test_joint_sin_cos_accuracy():
+    """The chain's sin / cos of a joint angle, read out through a one-joint
+    chain with a = alpha = d = 0 (its frame is Rz(theta): R[0,0] = cos theta,
+    R[1,0] = sin theta), against the FP64 values of the same float32 angles:
+    within 1.5e-7 absolute over |theta| <= 40 (multiples of pi/2 and their
+    neighbours included) and up to 1e4, odd symmetry exact, NaN for NaN / inf."""
+    robot = W.Robot(dh=np.zeros((1, 4)), q_min=np.array([-3.0]), q_max=np.array([3.0]),
+                    sphere_link=np.array([1], np.int32), spheres=np.array([[0.0, 0.0, 0.0, 0.05]]),
+                    pairs=np.zeros((0, 2), np.int32))
+    world = W.World(boxes=np.zeros((0, 6)), spheres=np.zeros((0, 4)))
+    quarter = np.arange(-25, 26) * (np.pi / 2)
+    th = np.concatenate([np.linspace(-40.0, 40.0, 400_001), quarter, np.nextafter(quarter, 0),
+                         np.nextafter(quarter, 100), np.linspace(-1e4, 1e4, 20_001),
+                         [0.0, 1e-30, -1e-30, 1e-8, np.pi / 4, -np.pi / 4]]).astype(np.float32)
+    with Controller(robot, world, W.Params(N=4, H=4, n_knots=0, dt=np.full(4, 0.02))) as ctl:
+        R = host(ctl.forward_kinematics(cuda(th[:, None])))
+        c, s = R[:, 0, 0].astype(np.float64), R[:, 1, 0].astype(np.float64)
+        x = th.astype(np.float64)
+        assert np.abs(s - np.sin(x)).max() < 1.5e-7
+        assert np.abs(c - np.cos(x)).max() < 1.5e-7
+        Rm = host(ctl.forward_kinematics(cuda(-th[:, None])))
+        assert np.array_equal(Rm[:, 1, 0], -R[:, 1, 0]) and np.array_equal(Rm[:, 0, 0], R[:, 0, 0])
+        small = np.abs(x) < 1e-4  # sin x = x to within an ulp near zero
+        assert np.all(np.abs(s[small] - x[small]) <= np.spacing(np.abs(th[small])).astype(np.float64))
+        bad = host(ctl.forward_kinematics(cuda(np.array([[np.nan], [np.inf], [-np.inf]], np.float32))))
+        assert np.isnan(bad[:, 0, 0]).all() and np.isnan(bad[:, 1, 0]).all()
+
+
 def test_checkpoint_resume_is_bitwise():
     wl, p = VARIANTS["small"]
     state, goal = f32(wl.state), f32(wl.goal)
@@ -405,6 +433,38 @@ def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
         assert {"self", "world"} <= active, active
     if name == "dense_world":
         assert "world" in active, active
+
+
+@pytest.mark.parametrize("mapping", ["cta", "warp", "pair"])
+def test_dependent_launch_is_bitwise_identical(mapping):
+    """The step graph with its rollouts and updates launched as programmatic
+    dependents and launched ordinarily (the default): the same commands, means,
+    sigmas and step records, bit for bit, over several closed-loop steps of
+    K = 3 iterations."""
+    wl = W.config_paper(2)
+    p = wl.params.replace(N=300)
+    goal = f32(wl.goal)
+    runs = []
+    for dep in (True, False):
+        with _ctl(wl, p) as ctl:
+            assert not ctl.dependent_launch()
+            {"cta": lambda: ctl.set_launch(4, 256), "warp": lambda: ctl.set_launch_warp(4),
+             "pair": lambda: ctl.set_launch_warp_pair(2)}[mapping]()
+            ctl.set_dependent_launch(dep)
+            assert ctl.dependent_launch() == dep
+            state = f32(wl.state)
+            out = []
+            for _ in range(6):
+                cmd, info, rc = ctl.step(state, goal)
+                mu, sig = ctl.get_distribution()
+                out.append((cmd, mu, sig, info["best_cost"], info["mean_weighted_cost"], rc))
+                state[2] = cmd
+                state[1] += 0.02 * cmd
+                state[0] += 0.02 * state[1]
+            runs.append(out)
+    for a, b in zip(*runs):
+        for x, y in zip(a, b):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
 
 
 @pytest.mark.parametrize("seed,world", [(0, None), (3, (64, 64)), (5, (8, 0))])
