@@ -663,13 +663,6 @@ __device__ float block_sum(float v, float* sh)
     return sh[0];
 }
 
-// Scratch of the multi-CTA distribution update (device, owned by the handle).
-struct UpdateScratch {
-    unsigned int count;  // CTAs finished in the current launch (reset by the last one)
-    unsigned int pad[63];
-    float var[1];        // H x d weighted squared deviations (Eq. 5), grown to H*d
-};
-
 // Block-wide (min value, lowest index) over all threads; result in every thread.
 __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
 {
@@ -731,59 +724,105 @@ __device__ __forceinline__ float2 block_sum2(float a, float b, float2* sh)
     return sh[32];
 }
 
-// update_distribution (Eqs. 4-6), one CTA per horizon step h.  Every CTA
-// forms the min-shifted exponential weights of all N particles (Eq. 6), then
-// the weighted mean of row h (Eq. 4) and row h's weighted squared deviations
-// about the new mean.  Each thread loads its particles' costs and row-h
-// controls once, up front (kUpdKeep particles in registers; any beyond are
-// re-read), so the L2 round trips overlap.  The last CTA to finish sums the
-// deviations over h in fixed order into the per-joint sigma (Eq. 5) and, at
+// update_distribution (Eqs. 4-6) on one thread-block cluster of kUpdCluster
+// CTAs per problem, as weighted sums over the particles of the N x (H d)
+// control matrix (one row per particle, contiguous).  Every CTA forms the
+// min-shifted exponential weights of all N particles (Eq. 6); CTA c then sums
+// its own contiguous chunk of particles into two partials per column (h, j),
+// thread k holding column k so that each particle row is one coalesced read:
+// A1 = sum w (u - mu_old) and A2 = sum w (u - mu_old)^2, about the mean the
+// iteration started from.  Rank 0 adds the partials of the cluster over
+// distributed shared memory, in rank order, and forms the new mean (Eq. 4)
+// mu_old + alpha_mu A1 / s and the squared deviation about it,
+// A2 - (2 alpha_mu - alpha_mu^2) A1^2 / s (the same quantity as the sum of
+// w (u - mu_new)^2, in one pass), then adds those over h into the per-joint
+// sigma (Eq. 5), records the iteration's best and weighted-mean cost and, at
 // the last iteration of a step, writes next_command and advances the step
-// counter.  All reductions run in a fixed order: bitwise reproducible.
-constexpr int kUpdKeep = 2;
+// counter; a second barrier keeps the CTAs resident until it has read them.
+// Every sum runs in a fixed order (weights: particles n = tid, tid + T, ...
+// per thread, a butterfly per warp, the warps in order; columns: the chunk's
+// particles in order, interleaved over kUpdGroups thread groups added in
+// order, then the CTAs in rank order; sigma: the rows in order): bitwise
+// reproducible, whatever the grid around the cluster.
+constexpr int kUpdCluster = 8;
+constexpr int kUpdGroups = kUpdateThreads / 256;  // particle interleave when H d <= 256
+constexpr int kUpdBatch = 32;                     // loads in flight per thread
+static_assert(STORM_MAX_H * kMaxDof <= kUpdateThreads, "one column per thread");
 
-__device__ __forceinline__ void update_row(const Problem& pb, const float* __restrict__ C,
-                                           const float* __restrict__ u, float* __restrict__ weights_out,
-                                           StepState* st, float* __restrict__ cmd_out, int finalize,
-                                           UpdateScratch* scr, int h, unsigned int rows)
+__device__ __forceinline__ unsigned cluster_rank()
 {
-    extern __shared__ __align__(16) float s_w[];  // N weights
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster; shared-memory writes before it are
+// visible to the cluster after it.
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Generic address of `local`'s counterpart in the shared memory of cluster CTA
+// `rank` (plain loads through it; the cluster barrier orders them).
+__device__ __forceinline__ const float* cluster_peer(const float* local, unsigned rank)
+{
+    uint64_t remote;
+    asm("mapa.u64 %0, %1, %2;" : "=l"(remote) : "l"(reinterpret_cast<uint64_t>(local)), "r"(rank));
+    return reinterpret_cast<const float*>(remote);
+}
+
+// Sum over the cluster's CTAs, in rank order, of the float at `local`'s offset
+// (all kUpdCluster loads in flight together).
+__device__ __forceinline__ float cluster_sum(const float* local)
+{
+    float v[kUpdCluster];
+#pragma unroll
+    for (int r = 0; r < kUpdCluster; ++r) v[r] = *cluster_peer(local, static_cast<unsigned>(r));
+    float a = 0.f;
+#pragma unroll
+    for (int r = 0; r < kUpdCluster; ++r) a += v[r];
+    return a;
+}
+
+__device__ __forceinline__ void update_cluster(const Problem& pb, const float* __restrict__ C,
+                                               const float* __restrict__ u, float* __restrict__ weights_out,
+                                               StepState* st, float* __restrict__ cmd_out, int finalize)
+{
+    extern __shared__ __align__(16) float s_w[];  // N costs, then weights
     __shared__ float s_redf[32];
     __shared__ int s_redi[32];
     __shared__ float2 s_red2[33];
-    __shared__ float s_acc[kMaxDof][33];
-    __shared__ float s_mu[kMaxDof];
-    __shared__ int s_last;
-    const int N = pb.N, d = pb.d, O = pb.H * pb.d;
-    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
-
-    // ---- this thread's costs and row-h controls (and the old mean of row h), loaded together
-    // (all through L2: under a dependent launch this CTA may have started
-    // before the rollout that wrote them finished)
-    const float mu_old = tid < d ? __ldcg(pb.mu + h * d + tid) : 0.f;
-    float cv[kUpdKeep], uv[kUpdKeep][kMaxDof];
+    __shared__ float2 s_grp[kUpdGroups][kUpdateThreads];  // the thread groups' (A1, A2) per column
+    __shared__ float s_a1[kUpdateThreads], s_a2[kUpdateThreads];  // this CTA's partials, read by rank 0
+    __shared__ float s_dev[kUpdateThreads];                       // rank 0: squared deviation per column
+    __shared__ float s_mu[kMaxDof];                               // rank 0: new mean of row 0
+    const int N = pb.N, d = pb.d, H = pb.H, O = H * d;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const unsigned rank = cluster_rank();
+    const int chunk = (N + kUpdCluster - 1) / kUpdCluster;
+    const int n0 = min(N, static_cast<int>(rank) * chunk), n1 = min(N, n0 + chunk);
+    const int G = O <= T / kUpdGroups ? kUpdGroups : 1;  // thread groups interleaving the chunk
+    const int k = G > 1 ? tid % (T / kUpdGroups) : tid, g = G > 1 ? tid / (T / kUpdGroups) : 0;
+    const bool col = k < O && g < G;
+    // (costs, controls and the mean through L2: under a dependent launch this
+    // CTA may have started before the rollout that wrote them finished)
+    const float mu_k = col ? __ldcg(pb.mu + k) : 0.f;  // the column's mean before this update
+    // this thread's particles n0 + g, n0 + g + G, ... of the chunk: the first
+    // kUpdBatch of them are loaded now, while the weights are formed
+    const int cnt = col ? max(0, (n1 - n0 - g + G - 1) / G) : 0;
+    const float* up = u + static_cast<size_t>(n0 + g) * O + k;
+    const int stride = G * O;
+    float x[kUpdBatch];
 #pragma unroll
-    for (int k = 0; k < kUpdKeep; ++k) {
-        const int n = tid + k * T;
-        cv[k] = n < N ? __ldcg(C + n) : INFINITY;
-        const float* un = u + static_cast<size_t>(n < N ? n : 0) * O + h * d;
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) uv[k][j] = (n < N && j < d) ? __ldcg(un + j) : 0.f;
-    }
+    for (int q = 0; q < kUpdBatch; ++q) x[q] = q < cnt ? up[q * stride] : 0.f;
 
     // ---- min finite cost and its lowest index
     float bv = INFINITY;
     int bi = INT_MAX;
-#pragma unroll
-    for (int k = 0; k < kUpdKeep; ++k) {
-        const int n = tid + k * T;
-        if (n < N && isfinite(cv[k]) && cv[k] < bv) {
-            bv = cv[k];
-            bi = n;
-        }
-    }
-    for (int n = tid + kUpdKeep * T; n < N; n += T) {
+    for (int n = tid; n < N; n += T) {
         const float c = __ldcg(C + n);
+        s_w[n] = c;
         if (isfinite(c) && c < bv) {
             bv = c;
             bi = n;
@@ -796,25 +835,12 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
 
     float s = 1.f, sc = 0.f;
     if (!degenerate) {
-        // ---- weights, Eq. 6
-        auto weight = [&](int n, float c) {
-            if (!isfinite(c)) return 0.f;
-            if (pb.beta > 0.f) return expf(-(c - m) / pb.beta);
-            return (n == arg) ? 1.f : 0.f;
-        };
-        float ls = 0.f, lsc = 0.f, wk[kUpdKeep];
-#pragma unroll
-        for (int k = 0; k < kUpdKeep; ++k) {
-            const int n = tid + k * T;
-            const float w = n < N ? weight(n, cv[k]) : 0.f;
-            wk[k] = w;
-            if (n < N) s_w[n] = w;
-            ls += w;
-            if (w > 0.f) lsc = fmaf(w, cv[k], lsc);
-        }
-        for (int n = tid + kUpdKeep * T; n < N; n += T) {
-            const float c = __ldcg(C + n);
-            const float w = weight(n, c);
+        // ---- weights, Eq. 6 (each thread rewrites its own entries)
+        float ls = 0.f, lsc = 0.f;
+        for (int n = tid; n < N; n += T) {
+            const float c = s_w[n];
+            float w = 0.f;
+            if (isfinite(c)) w = pb.beta > 0.f ? expf(-(c - m) / pb.beta) : (n == arg ? 1.f : 0.f);
             s_w[n] = w;
             ls += w;
             if (w > 0.f) lsc = fmaf(w, c, lsc);
@@ -822,130 +848,92 @@ __device__ __forceinline__ void update_row(const Problem& pb, const float* __res
         const float2 tot = block_sum2(ls, lsc, s_red2);
         s = tot.x;
         sc = tot.y;
-        const float inv_s = 1.f / s;
-        if (weights_out && h == 0)
-            for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * inv_s;
+        if (weights_out && rank == 0)
+            for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * (1.f / s);
 
-        // ---- weighted mean of row h, Eq. 4
-        float acc[kMaxDof];
+        // ---- the chunk's column sums about the old mean, particles in order
+        if (col) {
+            float a1 = 0.f, a2 = 0.f;
+            const float* wp = s_w + n0 + g;
+            for (int q0 = 0; q0 < cnt; q0 += kUpdBatch) {
+                if (q0 > 0) {
 #pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) acc[j] = 0.f;
+                    for (int q = 0; q < kUpdBatch; ++q) x[q] = q0 + q < cnt ? up[(q0 + q) * stride] : 0.f;
+                }
 #pragma unroll
-        for (int k = 0; k < kUpdKeep; ++k)
-#pragma unroll
-            for (int j = 0; j < kMaxDof; ++j)
-                if (j < d) acc[j] = fmaf(wk[k], uv[k][j], acc[j]);
-        for (int n = tid + kUpdKeep * T; n < N; n += T) {
-            const float w = s_w[n];
-            const float* un = u + static_cast<size_t>(n) * O + h * d;
-#pragma unroll
-            for (int j = 0; j < kMaxDof; ++j)
-                if (j < d) acc[j] = fmaf(w, __ldcg(un + j), acc[j]);
+                for (int q = 0; q < kUpdBatch; ++q) {
+                    if (q0 + q < cnt) {
+                        const float w = wp[(q0 + q) * G], e = x[q] - mu_k;
+                        a1 = fmaf(w, e, a1);
+                        a2 = fmaf(w * e, e, a2);
+                    }
+                }
+            }
+            s_grp[g][k] = make_float2(a1, a2);
         }
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) {
-            if (j < d) {
-                const float v = warp_sum(acc[j]);
-                if (lane == 0) s_acc[j][wid] = v;
+        __syncthreads();
+        if (tid < O) {
+            float2 p = s_grp[0][tid];
+            for (int q = 1; q < G; ++q) {
+                p.x += s_grp[q][tid].x;
+                p.y += s_grp[q][tid].y;
+            }
+            s_a1[tid] = p.x;
+            s_a2[tid] = p.y;
+        }
+    }
+
+    // ---- rank 0: the new mean (Eq. 4) and sigma (Eq. 5) from the cluster's partials
+    cluster_barrier();
+    if (rank == 0) {
+        if (degenerate) {
+            if (tid == 0) {
+                st->status |= STORM_WARN_DEGENERATE;
+                st->best = INFINITY;
+                st->wmean = INFINITY;
+            }
+            if (weights_out)
+                for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
+        } else {
+            const float inv_s = 1.f / s, al = pb.alpha_mu;
+            if (tid < O) {  // here k == tid
+                const float A1 = cluster_sum(s_a1 + tid), A2 = cluster_sum(s_a2 + tid);
+                const float mnew = fmaf(al * A1, inv_s, mu_k);
+                pb.mu[tid] = mnew;
+                if (tid < d) s_mu[tid] = mnew;
+                s_dev[tid] = fmaxf(0.f, A2 - (2.f * al - al * al) * (A1 * A1) * inv_s);
+            }
+            __syncthreads();
+            if (tid < d) {
+                const int j = tid;
+                float v = 0.f;
+                for (int hh = 0; hh < H; ++hh) v += s_dev[hh * d + j];
+                v = v * inv_s / static_cast<float>(H);
+                const float sg = __ldcg(pb.sigma + j);
+                float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
+                var = fmaxf(var, pb.sigma_min * pb.sigma_min);
+                pb.sigma[j] = sqrtf(var);
+            }
+            if (tid == 0) {
+                st->best = m;
+                st->wmean = sc / s;
             }
         }
-        __syncthreads();
-        if (tid < d) {
-            float a = 0.f;
-            for (int k = 0; k < (T >> 5); ++k) a += s_acc[tid][k];
-            const float mnew = (1.f - pb.alpha_mu) * mu_old + pb.alpha_mu * (a * inv_s);
-            s_mu[tid] = mnew;
-            pb.mu[h * d + tid] = mnew;  // row h belongs to this CTA alone
-        }
-        __syncthreads();
-
-        // ---- weighted squared deviation of row h about the new mean, Eq. 5
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) acc[j] = 0.f;
-#pragma unroll
-        for (int k = 0; k < kUpdKeep; ++k)
-#pragma unroll
-            for (int j = 0; j < kMaxDof; ++j)
-                if (j < d) {
-                    const float e = uv[k][j] - s_mu[j];
-                    acc[j] = fmaf(wk[k] * e, e, acc[j]);
-                }
-        for (int n = tid + kUpdKeep * T; n < N; n += T) {
-            const float w = s_w[n];
-            const float* un = u + static_cast<size_t>(n) * O + h * d;
-#pragma unroll
-            for (int j = 0; j < kMaxDof; ++j)
-                if (j < d) {
-                    const float e = __ldcg(un + j) - s_mu[j];
-                    acc[j] = fmaf(w * e, e, acc[j]);
-                }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) {
-            if (j < d) {
-                const float v = warp_sum(acc[j]);
-                if (lane == 0) s_acc[j][wid] = v;
-            }
-        }
-        __syncthreads();
-        if (tid < d) {
-            float a = 0.f;
-            for (int k = 0; k < (T >> 5); ++k) a += s_acc[tid][k];
-            scr->var[h * d + tid] = a;
+        if (finalize) {
+            if (tid < d) cmd_out[tid] = degenerate ? __ldcg(pb.mu + tid) : s_mu[tid];
+            if (tid == 0) st->step += 1;
         }
     }
-
-    // ---- the last CTA to finish combines the rows
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&scr->count, 1u) == rows - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (degenerate) {
-        if (tid == 0) {
-            st->status |= STORM_WARN_DEGENERATE;
-            st->best = INFINITY;
-            st->wmean = INFINITY;
-        }
-        if (weights_out)
-            for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
-    } else {
-        // the rows' deviations in one parallel round of loads, then summed in fixed order
-        __shared__ float s_var[STORM_MAX_H * kMaxDof];
-        for (int i = tid; i < pb.H * d; i += T) s_var[i] = __ldcg(scr->var + i);
-        __syncthreads();
-        if (tid < d) {
-            const int j = tid;
-            float v = 0.f;
-            for (int hh = 0; hh < pb.H; ++hh) v += s_var[hh * d + j];
-            v = v / s / static_cast<float>(pb.H);
-            const float sg = __ldcg(pb.sigma + j);
-            float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
-            var = fmaxf(var, pb.sigma_min * pb.sigma_min);
-            pb.sigma[j] = sqrtf(var);
-        }
-        if (tid == 0) {
-            st->best = m;
-            st->wmean = sc / s;
-        }
-    }
-    if (finalize) {
-        if (tid < d) cmd_out[tid] = __ldcg(pb.mu + tid);
-        if (tid == 0) st->step += 1;
-    }
-    if (tid == 0) scr->count = 0;
+    cluster_barrier();  // rank 0 has read every CTA's partials
 }
 
-__global__ void __launch_bounds__(kUpdateThreads)
+__global__ void __cluster_dims__(kUpdCluster, 1, 1) __launch_bounds__(kUpdateThreads)
 k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
-         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out,
-         int finalize, UpdateScratch* scr)
+         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out, int finalize)
 {
     pdl_trigger();
     pdl_wait();
-    update_row(pb, C, u, weights_out, st, cmd_out, finalize, scr, blockIdx.x, gridDim.x);
+    update_cluster(pb, C, u, weights_out, st, cmd_out, finalize);
 }
 
 #include "storm_adjoint.cuh"
@@ -1186,7 +1174,6 @@ struct BatchInstance {
     const float* goal;    // 7
     float* cmd;           // d
     StepState* st;
-    UpdateScratch* upd;
     int K;
     int pad[3];
 };
@@ -1262,16 +1249,16 @@ k_rollout_warp_batch(const BatchInstance* __restrict__ insts, const int2* __rest
     }
 }
 
-// Distribution update of every instance: one CTA per (instance, horizon step).
-__global__ void __launch_bounds__(kUpdateThreads)
-k_update_batch(const BatchInstance* __restrict__ insts, const int2* __restrict__ rows, int iter)
+// Distribution update of every instance: cluster i (CTAs 8 i .. 8 i + 7) runs
+// the single-handle update of instance i.
+__global__ void __cluster_dims__(kUpdCluster, 1, 1) __launch_bounds__(kUpdateThreads)
+k_update_batch(const BatchInstance* __restrict__ insts, int iter)
 {
     __shared__ Problem s_pb;
-    const int2 r = rows[blockIdx.x];
-    const BatchInstance& I = insts[r.x];
-    if (iter >= I.K) return;
+    const BatchInstance& I = insts[blockIdx.x / kUpdCluster];
+    if (iter >= I.K) return;  // the whole cluster
     load_problem(I.pb, s_pb);
-    update_row(s_pb, I.C, I.u, nullptr, I.st, I.cmd, iter == I.K - 1, I.upd, r.y, s_pb.H);
+    update_cluster(s_pb, I.C, I.u, nullptr, I.st, I.cmd, iter == I.K - 1);
 }
 
 // ============================================================================ surrogate network host side
@@ -1598,7 +1585,6 @@ struct storm_handle {
     float* d_C = nullptr;
     float* d_io = nullptr;     // state 3d | goal 7 | cmd d | StepState
     StepState* d_st = nullptr;
-    UpdateScratch* d_upd = nullptr;  // multi-CTA update: counter + H x d partials
     float* d_adj = nullptr;          // adjoint partial rows: N x (H*d + 1)
     storm_mlp* mlp = nullptr;        // learned self-collision surrogate (not owned)
     MlpBuffers* mlp_buf = nullptr;   // its inference activations for N x H rows
@@ -1839,8 +1825,8 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
 int launch_update(storm_handle* h, cudaStream_t s, const float* C, const float* u, float* w,
                   float* cmd, int finalize, bool dep = false)
 {
-    CK(launch_kernel(k_update, h->pb.H, kUpdateThreads, h->update_smem, s, dep, h->pb, C, u, w, h->d_st, cmd,
-                     finalize, h->d_upd));
+    CK(launch_kernel(k_update, kUpdCluster, kUpdateThreads, h->update_smem, s, dep, h->pb, C, u, w, h->d_st, cmd,
+                     finalize));
     return STORM_OK;
 }
 
@@ -1974,7 +1960,6 @@ void free_all(storm_handle* h)
     if (h->d_u) cudaFree(h->d_u);
     if (h->d_C) cudaFree(h->d_C);
     if (h->d_io) cudaFree(h->d_io);
-    if (h->d_upd) cudaFree(h->d_upd);
     if (h->d_adj) cudaFree(h->d_adj);
     if (h->d_theta) cudaFree(h->d_theta);
     if (h->d_pred) cudaFree(h->d_pred);
@@ -2232,9 +2217,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     pb.ball = h->d_ball;  // the ball state of storm_set_ball (zero until set)
     CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
     CK(cudaMallocHost(&h->h_io, sizeof(float) * io_floats(pb)));
-    CK(cudaMalloc(&h->d_upd, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d));
     CK(cudaMalloc(&h->d_adj, sizeof(float) * size_t(pb.N) * (pb.H * pb.d + 1)));
-    CK(cudaMemsetAsync(h->d_upd, 0, sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d, h->stream));
     std::memset(h->h_io, 0, sizeof(float) * io_floats(pb));
     h->d_st = reinterpret_cast<StepState*>(h->d_io + io_st(pb));
     CK(cudaMemsetAsync(h->d_io, 0, sizeof(float) * io_floats(pb), h->stream));
@@ -2973,8 +2956,7 @@ struct storm_batch {
     BatchTile* d_tiles = nullptr;
     int2* d_tasks = nullptr;  // (instance, particle group) of the warp mapping
     int n_tasks = 0, warp_floats = 0;
-    int2* d_rows = nullptr;
-    int n_tiles = 0, n_rows = 0, grid = 0;
+    int n_tiles = 0, grid = 0;
     float* d_in = nullptr;   // states | goals
     float* d_out = nullptr;  // cmds | StepState x n
     float* h_in = nullptr;
@@ -3133,7 +3115,7 @@ int batch_enqueue(storm_batch* b, cudaStream_t s)
     BK(cudaGetLastError());
     for (int k = 0; k < b->Kmax; ++k) {
         BK(batch_launch_rollout(b, s, k));
-        k_update_batch<<<b->n_rows, kUpdateThreads, b->update_smem, s>>>(b->d_inst, b->d_rows, k);
+        k_update_batch<<<b->n * kUpdCluster, kUpdateThreads, b->update_smem, s>>>(b->d_inst, k);
         BK(cudaGetLastError());
     }
     return STORM_OK;
@@ -3183,7 +3165,6 @@ void batch_free(storm_batch* b)
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_tasks) cudaFree(b->d_tasks);
-    if (b->d_rows) cudaFree(b->d_rows);
     if (b->d_in) cudaFree(b->d_in);
     if (b->d_out) cudaFree(b->d_out);
     if (b->h_in) cudaFreeHost(b->h_in);
@@ -3226,8 +3207,7 @@ int batch_create_impl(storm_batch* b, int n, const storm_robot* r, const storm_w
         off[i] = total;
         const Problem& pb = I.pb;
         total += align256(plans[i].total) + align256(sizeof(float) * size_t(pb.N) * pb.H * pb.d) +
-                 align256(sizeof(float) * pb.N) +
-                 align256(sizeof(UpdateScratch) + sizeof(float) * pb.H * pb.d);
+                 align256(sizeof(float) * pb.N);
         b->update_smem = std::max(b->update_smem, sizeof(float) * ((pb.N + 3) & ~size_t(3)));
     }
     BK(cudaMalloc(&b->arena, total));
@@ -3240,7 +3220,6 @@ int batch_create_impl(storm_batch* b, int n, const storm_robot* r, const storm_w
     BK(cudaMemsetAsync(b->d_in, 0, sizeof(float) * (b->state_floats + 7 * n), b->stream));
     BK(cudaMemsetAsync(b->d_out, 0, out_bytes, b->stream));
     StepState* st = reinterpret_cast<StepState*>(reinterpret_cast<char*>(b->d_out) + out_st_offset(b));
-    std::vector<int2> rows;
     for (int i = 0; i < n; ++i) {
         BatchInstance& I = b->inst[i];
         char* base = static_cast<char*>(b->arena) + off[i];
@@ -3249,20 +3228,13 @@ int batch_create_impl(storm_batch* b, int n, const storm_robot* r, const storm_w
         I.u = reinterpret_cast<float*>(q);
         q += align256(sizeof(float) * size_t(I.pb.N) * I.pb.H * I.pb.d);
         I.C = reinterpret_cast<float*>(q);
-        q += align256(sizeof(float) * I.pb.N);
-        I.upd = reinterpret_cast<UpdateScratch*>(q);
         I.state = b->d_in + b->state_off[i];
         I.goal = b->d_in + b->state_floats + 7 * i;
         I.cmd = b->d_out + b->cmd_off[i];
         I.st = st + i;
         std::vector<float> sg(I.pb.d, static_cast<float>(p[i].sigma_init));
         BK(cudaMemcpyAsync(I.pb.sigma, sg.data(), 4 * I.pb.d, cudaMemcpyHostToDevice, b->stream));
-        for (int hh = 0; hh < I.pb.H; ++hh) rows.push_back(make_int2(i, hh));
     }
-    b->n_rows = static_cast<int>(rows.size());
-    BK(cudaMalloc(&b->d_rows, sizeof(int2) * rows.size()));
-    BK(cudaMemcpyAsync(b->d_rows, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice,
-                       b->stream));
     BK(cudaMalloc(&b->d_inst, sizeof(BatchInstance) * n));
     int optin = 0;
     BK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
