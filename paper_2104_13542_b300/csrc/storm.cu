@@ -2203,7 +2203,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     h->cap_wsph = STORM_MAX_OBSTACLES;
     h->grid = (pb.N + pb.ppc - 1) / pb.ppc;
     {
-        const WarpPlan wp = warp_plan(pb);
+        const WarpPlan wp = warp_plan(pb, h->mapping == STORM_MAP_WARP_PAIR);
         h->warp_smem = sizeof(float) * size_t(wp.floats) * h->wpc;
         h->warp_grid = (pb.N + wp.PW * h->wpc - 1) / (wp.PW * h->wpc);
     }
@@ -2518,7 +2518,7 @@ int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
 {
     if (!h) return STORM_ERR_INVALID_ARG;
     if (h->mapping == STORM_MAP_WARP || h->mapping == STORM_MAP_WARP_PAIR) {
-        if (ppc) *ppc = h->wpc * warp_plan(h->pb).PW;
+        if (ppc) *ppc = h->wpc * warp_plan(h->pb, false).PW;
         if (threads) *threads = h->wpc * (h->mapping == STORM_MAP_WARP_PAIR ? 64 : 32);
     } else {
         if (ppc) *ppc = h->pb.ppc;
@@ -2543,7 +2543,7 @@ static int set_launch_warp_impl(storm_handle* h, int wpc, bool rebuild, bool pai
 {
     if (wpc < 1 || wpc > (pair ? kWarpMaxWarps / 2 : kWarpMaxWarps))
         return fail(h, STORM_ERR_INVALID_ARG, "warps per CTA out of range");
-    const WarpPlan wp = warp_plan(h->pb);
+    const WarpPlan wp = warp_plan(h->pb, pair);
     const size_t bytes = sizeof(float) * size_t(wp.floats) * wpc;
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
@@ -3055,7 +3055,7 @@ int batch_apply_launch_warp(storm_batch* b, int wpc)
     int floats = 0;
     for (int i = 0; i < b->n; ++i) {
         const Problem& pb = b->inst[i].pb;
-        const WarpPlan wp = warp_plan(pb);
+        const WarpPlan wp = warp_plan(pb, false);
         floats = std::max(floats, wp.floats);
         const double per_item = 100.0 + pb.M * (pb.B + pb.O) + 49.0 * pb.NPB + pb.P;
         for (int g = 0; g * wp.PW < pb.N; ++g)

@@ -13,27 +13,29 @@
 // axis-aligned box enclosing every link bound of the warp's items.
 //
 // The pair variant (kPair) gives each particle group two warps: warp A draws
-// the controls and integrates them, then both run FK; A takes the pose,
-// joint, end-effector and manipulability terms while B takes world and self
-// collision, and the two meet at one named barrier per step slot.  The
-// critical path is then the longer branch, not their sum.
+// the controls and integrates them, then both run FK, each into its own copy
+// of the link frames; A takes the pose, joint, end-effector and
+// manipulability terms and world collision while B takes self collision, and
+// the two meet at one named barrier per step slot.  The critical path is then
+// the longer branch, not their sum.
 #pragma once
 
 // Per-warp shared-memory plan (float offsets).
 struct WarpPlan {
     int Lp, PW, SL;  // lanes per particle, particles per warp, items per lane
     int frame;       // F x 12 x 32: link frames, row-major [R | p] rows, lane-minor
+    int frame_b;     // the same for warp B of a pair (its own copy), else = frame
     int cb;          // F x 3 x 32: link bounding-sphere centres, lane-minor
     int eps;         // PW x S x d noise
     int u, th, thd;  // PW x H x d controls and joint states
     int c;           // PW x H running costs
     int ba;          // PW x H x 2 ball in-plane gravity
-    int ds, dw;      // PW x H self / world depths handed from warp B to A (pair variant)
+    int ds;          // PW x H self-collision depths handed from warp B to A (pair variant)
     int io;          // mu (H x d) | sigma (d) | state (3 x d) | goal (7), staged once per warp
     int floats;      // size of one warp's (pair's) region
 };
 
-__host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
+__host__ __device__ inline WarpPlan warp_plan(const Problem& pb, bool pair)
 {
     WarpPlan w;
     w.Lp = pb.H > 16 ? 32 : (pb.H > 8 ? 16 : 8);
@@ -47,6 +49,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
         return o;
     };
     w.frame = take(F * 12 * 32);
+    w.frame_b = pair ? take(F * 12 * 32) : w.frame;
     w.cb = take(F * 3 * 32);
     w.eps = take(w.PW * pb.S * pb.d);
     w.u = take(w.PW * pb.H * pb.d);
@@ -55,13 +58,20 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb)
     w.c = take(w.PW * pb.H);
     w.ba = take(w.PW * pb.H * 2);
     w.ds = take(w.PW * pb.H);
-    w.dw = take(w.PW * pb.H);
     w.io = take(pb.H * pb.d + 4 * pb.d + 7);
     w.floats = off;
     return w;
 }
 
 constexpr int kWarpMaxWarps = 8;  // largest CTA of the warp mapping (warps)
+
+// Asynchronous 4-byte copy global -> shared (completed by cp.async.wait_all).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
 
 // Exact depth of the spheres [s0, s1) of one frame against box b (centre,
 // half extents) -- the per-sphere formula of k_rollout.
@@ -134,14 +144,14 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                                                   const float* __restrict__ state, const float* __restrict__ goal,
                                                   uint32_t step, int iter, int front_only, int wg, int unit, float* ws)
 {
-    const WarpPlan W = warp_plan(pb);
+    const WarpPlan W = warp_plan(pb, kPair);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool do_costs = !kPair || (warp & 1) == 0;  // A: controls, integration, non-collision costs
-    const bool do_coll = !kPair || (warp & 1) == 1;   // B: world and self collision
+    const bool do_costs = !kPair || (warp & 1) == 0;  // A: controls, integration, costs, world collision
+    const bool do_selfc = !kPair || (warp & 1) == 1;  // B: self collision
     const int nw0 = wg * W.PW;  // first particle of this unit
     if (nw0 >= pb.N) return;    // uniform over the unit (both warps of a pair)
-    float* s_fr = ws + W.frame;
+    float* s_fr = ws + (do_costs ? W.frame : W.frame_b);  // this warp's own frames
     float* s_cb = ws + W.cb;
     float* s_eps = ws + W.eps;
     float* s_u = ws + W.u;
@@ -154,6 +164,25 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     const int n = nw0 + seg;
     const bool pvalid = seg < np_w;
     trace_stamp(pb.trace, 0);
+    // mu, sigma, the state and the goal: read by every lane, so staged with one
+    // coalesced pass per warp (the whole grid reads these same few lines)
+    float* s_mu = ws + W.io;
+    float* s_sig = s_mu + H * d;
+    float* s_st = s_sig + d;
+    float* s_goal = s_st + 3 * d;
+    auto stage_inputs = [&]() {
+        for (int i = lane; i < H * d; i += 32) s_mu[i] = __ldcg(pb.mu + i);
+        if (lane < d) s_sig[lane] = __ldcg(pb.sigma + lane);
+        if (lane < 3 * d) s_st[lane] = state[lane];
+        if (lane < 7) s_goal[lane] = goal[lane];
+    };
+    auto stage_inputs_async = [&]() {  // the same copies, in flight while the noise is drawn
+        for (int i = lane; i < H * d; i += 32) cp_async4(s_mu + i, pb.mu + i);
+        if (lane < d) cp_async4(s_sig + lane, pb.sigma + lane);
+        if (lane < 3 * d) cp_async4(s_st + lane, state + lane);
+        if (lane < 7) cp_async4(s_goal + lane, goal + lane);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     if (do_costs) {
     {
         // The grid is a single wave, so every warp meets this SM's L1 cold: pull
@@ -163,6 +192,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         for (int o = lane * 128; o < pb.table_bytes; o += 32 * 128)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(tb + o));
     }
+    // launched ordinarily, the inputs are final: their loads overlap the noise
+    if (!pb.dep_launch) stage_inputs_async();
 
     // ---- noise eps[n][s][j] of the warp's particles
     const int per = S * d;
@@ -199,22 +230,16 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     // launch it is drawn while the previous distribution update still runs;
     // mu and sigma are read after it has finished (from L2).
     pdl_wait();
-    // mu, sigma, the state and the goal: read by every lane, so staged with one
-    // coalesced pass per warp (the whole grid reads these same few lines)
-    float* s_mu = ws + W.io;
-    float* s_sig = s_mu + H * d;
-    float* s_st = s_sig + d;
-    float* s_goal = s_st + 3 * d;
     if (pb.dep_launch) {  // the wait may have dropped the prefetched tables from L1
         const char* tb = reinterpret_cast<const char*>(pb.tables);
         for (int o = lane * 128; o < pb.table_bytes; o += 32 * 128)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(tb + o));
     }
     if (do_costs) {
-    for (int i = lane; i < H * d; i += 32) s_mu[i] = __ldcg(pb.mu + i);
-    if (lane < d) s_sig[lane] = __ldcg(pb.sigma + lane);
-    if (lane < 3 * d) s_st[lane] = state[lane];
-    if (lane < 7) s_goal[lane] = goal[lane];
+    if (pb.dep_launch)
+        stage_inputs();  // after the previous update has finished
+    else
+        asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
 
     // ---- controls u = mu + sigma o (B eps) of the lane's own steps, null particles zero
@@ -326,9 +351,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         float cbx[kMaxDof + 1], cby[kMaxDof + 1], cbz[kMaxDof + 1];
         {
             const float fr0[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
-            if (do_coll)
 #pragma unroll
-                for (int k = 0; k < 12; ++k) s_fr[k * 32 + lane] = fr0[k];
+            for (int k = 0; k < 12; ++k) s_fr[k * 32 + lane] = fr0[k];
             cbx[0] = fmaf(1.f, lbf[0].x, fmaf(0.f, lbf[0].y, fmaf(0.f, lbf[0].z, 0.f)));
             cby[0] = fmaf(0.f, lbf[0].x, fmaf(1.f, lbf[0].y, fmaf(0.f, lbf[0].z, 0.f)));
             cbz[0] = fmaf(0.f, lbf[0].x, fmaf(0.f, lbf[0].y, fmaf(1.f, lbf[0].z, 0.f)));
@@ -338,7 +362,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             if (i < d) {
                 const float* dh = pb.dhx + i * 8;
                 dh_step(R, pp, dh[0], dh[1], dh[2], dh[3], th[i] + dh[4]);
-                if (do_coll) {
+                {
                     float* fr = s_fr + (i + 1) * 12 * 32 + lane;
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
@@ -368,7 +392,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         }
 #pragma unroll
         for (int f = 0; f <= kMaxDof; ++f) {
-            if (f < F && do_coll) {
+            if (f < F && do_selfc) {
                 s_cb[(f * 3 + 0) * 32 + lane] = cbx[f];
                 s_cb[(f * 3 + 1) * 32 + lane] = cby[f];
                 s_cb[(f * 3 + 2) * 32 + lane] = cbz[f];
@@ -471,7 +495,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
 
         // ---- world collision, Eq. 14 reading
         float dworld = 0.f;
-        if (do_coll && NO > 0 && pb.M > 0) {
+        if (do_costs && NO > 0 && pb.M > 0) {
             if (pb.broadphase) {
                 // box enclosing every link bound of the warp's items, padded 1 mm
                 float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -565,7 +589,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         // (register tests over the compile-time list of pairs), then their
         // pair blocks exactly; then the leftover pairs
         float dself = 0.f;
-        const bool do_self = do_coll && valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
+        const bool do_self = do_selfc && valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
         if (valid && pred && pb.self_direct) dself = fmaxf(0.f, pred[gi]);  // Eq. 13's learned term
         uint32_t lp_hit = 0u;  // bit t: frame pair t has blocks and its bounds overlap
         if (do_self) {
@@ -669,16 +693,10 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         trace_stamp(pb.trace, 5);
 
         // ---- running cost (Eq. 15)
-        if (kPair) {  // B hands its depths to A
-            if (do_coll && valid) {
-                ws[W.ds + pl * H + h] = dself;
-                ws[W.dw + pl * H + h] = dworld;
-            }
+        if (kPair) {  // B hands its self-collision depths to A
+            if (do_selfc && valid) ws[W.ds + pl * H + h] = dself;
             pair_sync(unit);
-            if (do_costs && valid) {
-                dself = ws[W.ds + pl * H + h];
-                dworld = ws[W.dw + pl * H + h];
-            }
+            if (do_costs && valid) dself = ws[W.ds + pl * H + h];
         }
         if (do_costs) {
             const float c = part + pb.w_coll * (dself + dworld);
@@ -723,7 +741,7 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
                const StepState* __restrict__ st, int step_override, int iter, int front_only)
 {
     extern __shared__ __align__(16) float wsm[];
-    const WarpPlan W = warp_plan(pb);
+    const WarpPlan W = warp_plan(pb, kPair);
     const int warp = threadIdx.x >> 5;
     const int unit = kPair ? warp >> 1 : warp;  // the warp, or warp pair, of a particle group
     const int units = kPair ? (blockDim.x >> 6) : (blockDim.x >> 5);
