@@ -74,7 +74,8 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-ROLLOUT_KERNELS = {"cta": "k_rollout", "warp": "k_rollout_warp<false>", "pair": "k_rollout_warp<true>"}
+ROLLOUT_KERNELS = {"cta": "k_rollout", "warp": "k_rollout_warp<1>", "pair": "k_rollout_warp<2>",
+                   "quad": "k_rollout_warp<4>"}
 
 
 def rollout_traffic(kernel: str):
@@ -208,6 +209,8 @@ def run_gpu(args, rank, world_size):
             ctl.set_launch_warp(int(shape))
         elif kind == "pair":
             ctl.set_launch_warp_pair(int(shape))
+        elif kind == "quad":
+            ctl.set_launch_warp_quad(int(shape))
         else:
             ppc, threads = (int(x) for x in shape.split(","))
             ctl.set_launch(ppc, threads)
@@ -632,7 +635,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--launch", default="auto",
                     help="rollout launch shape: auto (autotuned), warp:W (W warps per CTA), pair:W (W warp "
-                         "pairs per CTA) or cta:P,T")
+                         "pairs per CTA), quad:W (W four-warp groups per CTA) or cta:P,T")
     ap.add_argument("--dep-launch", action="store_true",
                     help="launch the step graph's rollouts and updates as programmatic dependents")
     ap.add_argument("--mlp-forward", type=int, default=0, metavar="ROWS",

@@ -272,7 +272,7 @@ int storm_set_ball(storm_handle* h, const float* ball_pos_vel);
 
 /* ---------------------------------------------------------------- launch shape */
 
-/* Rollout work mappings.  Both compute bitwise the same results; they differ
+/* Rollout work mappings.  All compute bitwise the same results; they differ
  * only in how the (particle, step) items are spread over threads:
  *   STORM_MAP_CTA   a CTA takes a group of particles and runs each phase
  *                   (noise, controls, integration, FK and costs, world and
@@ -282,11 +282,15 @@ int storm_set_ball(storm_handle* h, const float* ball_pos_vel);
  *                   / 8), one lane per step (two steps per lane when H > 32),
  *                   with warp-level synchronisation only; the default;
  *   STORM_MAP_WARP_PAIR  the same with two warps per particle group: one for
- *                   the controls and the non-collision costs, one for world
- *                   and self collision, meeting once per step slot. */
+ *                   the controls, the cost terms and world collision, one
+ *                   for self collision, meeting once per step slot;
+ *   STORM_MAP_WARP_QUAD  four warps per particle group: the controls and the
+ *                   pose / joint / end-effector terms; world collision and
+ *                   manipulability; two halves of self collision. */
 #define STORM_MAP_CTA 0
 #define STORM_MAP_WARP 1
 #define STORM_MAP_WARP_PAIR 2
+#define STORM_MAP_WARP_QUAD 3
 
 /* CTA mapping and its shape: particles per CTA (1..N) and threads per CTA (a
  * multiple of 32 in 64..512).  Re-captures the step graph.  Errors:
@@ -298,9 +302,13 @@ int storm_set_launch(storm_handle* h, int particles_per_cta, int threads_per_cta
 int storm_set_launch_warp(storm_handle* h, int warps_per_cta);
 /* Warp-pair mapping with 1..4 pairs per CTA.  Errors as storm_set_launch_warp. */
 int storm_set_launch_warp_pair(storm_handle* h, int pairs_per_cta);
+/* Warp-quad mapping with 1..2 groups of four warps per CTA.  Errors as
+ * storm_set_launch_warp. */
+int storm_set_launch_warp_quad(storm_handle* h, int groups_per_cta);
 /* Shape of the active mapping: particles and threads per CTA. */
 int storm_get_launch(const storm_handle* h, int* particles_per_cta, int* threads_per_cta);
-/* STORM_MAP_CTA, STORM_MAP_WARP or STORM_MAP_WARP_PAIR; INVALID_ARG for a NULL handle. */
+/* STORM_MAP_CTA, STORM_MAP_WARP, STORM_MAP_WARP_PAIR or STORM_MAP_WARP_QUAD;
+ * INVALID_ARG for a NULL handle. */
 int storm_get_launch_mapping(const storm_handle* h);
 
 /* Dependent launch in the step graph (on = 1; off = 0, the default): every

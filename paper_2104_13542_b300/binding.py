@@ -32,6 +32,7 @@ STORM_ERR_STATE = -6
 STORM_MAP_CTA = 0
 STORM_MAP_WARP = 1
 STORM_MAP_WARP_PAIR = 2
+STORM_MAP_WARP_QUAD = 3
 NTERMS = 11
 
 EXPORTED = [
@@ -40,7 +41,7 @@ EXPORTED = [
     "storm_sample_noise", "storm_generate_rollouts", "storm_update_distribution", "storm_get_distribution",
     "storm_set_distribution", "storm_set_world", "storm_forward_kinematics", "storm_get_state",
     "storm_set_state", "storm_rollout_costs_noalloc", "storm_set_launch", "storm_get_launch", "storm_set_launch_warp", "storm_get_launch_mapping",
-    "storm_ee_twist", "storm_set_ball", "storm_set_launch_warp_pair",
+    "storm_ee_twist", "storm_set_ball", "storm_set_launch_warp_pair", "storm_set_launch_warp_quad",
     "storm_autotune", "storm_cost_grad", "storm_batch_create", "storm_batch_destroy",
     "storm_batch_last_error", "storm_batch_sizes", "storm_batch_step", "storm_batch_step_resident",
     "storm_batch_device_io", "storm_batch_sync", "storm_batch_get_distribution",
@@ -145,6 +146,7 @@ def lib():
         L.storm_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.storm_set_launch_warp.argtypes = [vp, C.c_int]
         L.storm_set_launch_warp_pair.argtypes = [vp, C.c_int]
+        L.storm_set_launch_warp_quad.argtypes = [vp, C.c_int]
         L.storm_ee_twist.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp]
         L.storm_set_ball.argtypes = [vp, C.POINTER(C.c_float)]
         L.storm_get_launch_mapping.argtypes = [vp]
@@ -449,11 +451,15 @@ class Controller:
         """Warp-pair mapping (a cost warp and a collision warp per particle group)."""
         self._check(lib().storm_set_launch_warp_pair(self.h, int(pairs_per_cta)))
 
+    def set_launch_warp_quad(self, groups_per_cta: int):
+        """Warp-quad mapping (cost, world + manipulability and two self-collision warps per group)."""
+        self._check(lib().storm_set_launch_warp_quad(self.h, int(groups_per_cta)))
+
     def launch_mapping(self) -> str:
         m = lib().storm_get_launch_mapping(self.h)
         if m < 0:
             self._check(m)
-        return {STORM_MAP_WARP: "warp", STORM_MAP_WARP_PAIR: "pair"}.get(m, "cta")
+        return {STORM_MAP_WARP: "warp", STORM_MAP_WARP_PAIR: "pair", STORM_MAP_WARP_QUAD: "quad"}.get(m, "cta")
 
     def set_dependent_launch(self, on: bool):
         """Programmatic dependent launch of the step graph's rollouts and updates."""

@@ -1243,7 +1243,7 @@ k_rollout_warp_batch(const BatchInstance* __restrict__ insts, const int2* __rest
             loaded = task.x;
         }
         const RolloutOut out{I.u, nullptr, nullptr, nullptr, nullptr, nullptr, I.C};
-        rollout_warp_body<false>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
+        rollout_warp_body<1>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
                                  wsm + size_t(warp) * warp_floats);
         __syncwarp();
     }
@@ -1780,6 +1780,12 @@ int upload_world(storm_handle* h, const storm_world* w)
     return STORM_OK;
 }
 
+// Warps per particle group of a warp mapping.
+int warps_per_group(int mapping)
+{
+    return mapping == STORM_MAP_WARP_QUAD ? 4 : mapping == STORM_MAP_WARP_PAIR ? 2 : 1;
+}
+
 // A kernel launch; with dep set, as a programmatic dependent of the stream's
 // previous kernel (it may start before that kernel ends and must pdl_wait
 // before reading anything the predecessor writes).
@@ -1811,10 +1817,13 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
     if (exact_self) pb.self_pred = nullptr;
     pb.dep_launch = dep ? 1 : 0;
     if (h->mapping == STORM_MAP_WARP)
-        CK(launch_kernel(k_rollout_warp<false>, h->warp_grid, h->wpc * 32, h->warp_smem, s, dep, pb, out, state,
+        CK(launch_kernel(k_rollout_warp<1>, h->warp_grid, h->wpc * 32, h->warp_smem, s, dep, pb, out, state,
                          goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
     else if (h->mapping == STORM_MAP_WARP_PAIR)
-        CK(launch_kernel(k_rollout_warp<true>, h->warp_grid, h->wpc * 64, h->warp_smem, s, dep, pb, out, state,
+        CK(launch_kernel(k_rollout_warp<2>, h->warp_grid, h->wpc * 64, h->warp_smem, s, dep, pb, out, state,
+                         goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
+    else if (h->mapping == STORM_MAP_WARP_QUAD)
+        CK(launch_kernel(k_rollout_warp<4>, h->warp_grid, h->wpc * 128, h->warp_smem, s, dep, pb, out, state,
                          goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
     else
         CK(launch_kernel(k_rollout, h->grid, h->threads, h->rollout_smem, s, dep, pb, out, state, goal,
@@ -1885,11 +1894,14 @@ int allow_smem(storm_handle* h)
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     cudaFuncAttributes ra, ua, aa, wa;
     CK(cudaFuncGetAttributes(&ra, k_rollout));
-    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<false>));
-    CK(cudaFuncSetAttribute(k_rollout_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<1>));
+    CK(cudaFuncSetAttribute(k_rollout_warp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             optin - static_cast<int>(wa.sharedSizeBytes)));
-    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<true>));
-    CK(cudaFuncSetAttribute(k_rollout_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<2>));
+    CK(cudaFuncSetAttribute(k_rollout_warp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            optin - static_cast<int>(wa.sharedSizeBytes)));
+    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<4>));
+    CK(cudaFuncSetAttribute(k_rollout_warp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             optin - static_cast<int>(wa.sharedSizeBytes)));
     CK(cudaFuncGetAttributes(&ua, k_update));
     CK(cudaFuncGetAttributes(&aa, k_adjoint));
@@ -2203,7 +2215,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     h->cap_wsph = STORM_MAX_OBSTACLES;
     h->grid = (pb.N + pb.ppc - 1) / pb.ppc;
     {
-        const WarpPlan wp = warp_plan(pb, h->mapping == STORM_MAP_WARP_PAIR);
+        const WarpPlan wp = warp_plan(pb, warps_per_group(h->mapping));
         h->warp_smem = sizeof(float) * size_t(wp.floats) * h->wpc;
         h->warp_grid = (pb.N + wp.PW * h->wpc - 1) / (wp.PW * h->wpc);
     }
@@ -2517,9 +2529,9 @@ int storm_set_broadphase(storm_handle* h, int on)
 int storm_get_launch(const storm_handle* h, int* ppc, int* threads)
 {
     if (!h) return STORM_ERR_INVALID_ARG;
-    if (h->mapping == STORM_MAP_WARP || h->mapping == STORM_MAP_WARP_PAIR) {
-        if (ppc) *ppc = h->wpc * warp_plan(h->pb, false).PW;
-        if (threads) *threads = h->wpc * (h->mapping == STORM_MAP_WARP_PAIR ? 64 : 32);
+    if (h->mapping != STORM_MAP_CTA) {
+        if (ppc) *ppc = h->wpc * warp_plan(h->pb, 1).PW;
+        if (threads) *threads = h->wpc * 32 * warps_per_group(h->mapping);
     } else {
         if (ppc) *ppc = h->pb.ppc;
         if (threads) *threads = h->threads;
@@ -2539,16 +2551,16 @@ int storm_set_dependent_launch(storm_handle* h, int on)
 
 int storm_get_dependent_launch(const storm_handle* h) { return h ? (h->dep_launch ? 1 : 0) : STORM_ERR_INVALID_ARG; }
 
-static int set_launch_warp_impl(storm_handle* h, int wpc, bool rebuild, bool pair = false)
+static int set_launch_warp_impl(storm_handle* h, int wpc, bool rebuild, int mapping = STORM_MAP_WARP)
 {
-    if (wpc < 1 || wpc > (pair ? kWarpMaxWarps / 2 : kWarpMaxWarps))
-        return fail(h, STORM_ERR_INVALID_ARG, "warps per CTA out of range");
-    const WarpPlan wp = warp_plan(h->pb, pair);
+    const int kw = warps_per_group(mapping);
+    if (wpc < 1 || wpc > kWarpMaxWarps / kw) return fail(h, STORM_ERR_INVALID_ARG, "warps per CTA out of range");
+    const WarpPlan wp = warp_plan(h->pb, kw);
     const size_t bytes = sizeof(float) * size_t(wp.floats) * wpc;
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (bytes > size_t(optin)) return fail(h, STORM_ERR_INVALID_ARG, "launch shape needs too much shared memory");
-    h->mapping = pair ? STORM_MAP_WARP_PAIR : STORM_MAP_WARP;
+    h->mapping = mapping;
     h->wpc = wpc;
     h->warp_smem = bytes;
     h->warp_grid = (h->pb.N + wp.PW * wpc - 1) / (wp.PW * wpc);
@@ -2566,7 +2578,14 @@ int storm_set_launch_warp_pair(storm_handle* h, int pairs_per_cta)
 {
     if (!h) return STORM_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(h->stream));
-    return set_launch_warp_impl(h, pairs_per_cta, true, true);
+    return set_launch_warp_impl(h, pairs_per_cta, true, STORM_MAP_WARP_PAIR);
+}
+
+int storm_set_launch_warp_quad(storm_handle* h, int groups_per_cta)
+{
+    if (!h) return STORM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    return set_launch_warp_impl(h, groups_per_cta, true, STORM_MAP_WARP_QUAD);
 }
 
 static int set_launch_impl(storm_handle* h, int ppc, int threads, bool rebuild)
@@ -2602,6 +2621,7 @@ int storm_autotune(storm_handle* h, float* best_us)
     const int ths[] = {128, 256, 512};
     const int wpcs[] = {1, 2, 4, 8};
     const int pairs[] = {1, 2, 4};
+    const int quads[] = {1, 2};
     const int old_map = h->mapping, old_ppc = h->pb.ppc, old_threads = h->threads, old_wpc = h->wpc;
     float best = INFINITY;
     int best_map = old_map, best_ppc = old_ppc, best_threads = old_threads, best_wpc = old_wpc;
@@ -2655,12 +2675,23 @@ int storm_autotune(storm_handle* h, float* best_us)
     }
     for (int w : pairs) {
         if (rc) break;
-        if (set_launch_warp_impl(h, w, false, true) != STORM_OK) continue;
+        if (set_launch_warp_impl(h, w, false, STORM_MAP_WARP_PAIR) != STORM_OK) continue;
         const float med = measure();
         if (rc) break;
         if (med < best) {
             best = med;
             best_map = STORM_MAP_WARP_PAIR;
+            best_wpc = w;
+        }
+    }
+    for (int w : quads) {
+        if (rc) break;
+        if (set_launch_warp_impl(h, w, false, STORM_MAP_WARP_QUAD) != STORM_OK) continue;
+        const float med = measure();
+        if (rc) break;
+        if (med < best) {
+            best = med;
+            best_map = STORM_MAP_WARP_QUAD;
             best_wpc = w;
         }
     }
@@ -2670,7 +2701,7 @@ int storm_autotune(storm_handle* h, float* best_us)
     if (rc) {
         if (old_map != STORM_MAP_CTA) {
             set_launch_impl(h, old_ppc, old_threads, false);
-            set_launch_warp_impl(h, old_wpc, true, old_map == STORM_MAP_WARP_PAIR);
+            set_launch_warp_impl(h, old_wpc, true, old_map);
         } else {
             set_launch_warp_impl(h, old_wpc, false);
             set_launch_impl(h, old_ppc, old_threads, true);
@@ -2680,7 +2711,7 @@ int storm_autotune(storm_handle* h, float* best_us)
     if (best_us) *best_us = best;
     if (best_map != STORM_MAP_CTA) {
         set_launch_impl(h, best_ppc, best_threads, false);  // keep the CTA-mapping shape consistent
-        return set_launch_warp_impl(h, best_wpc, true, best_map == STORM_MAP_WARP_PAIR);
+        return set_launch_warp_impl(h, best_wpc, true, best_map);
     }
     set_launch_warp_impl(h, best_wpc, false);
     return set_launch_impl(h, best_ppc, best_threads, true);
@@ -3055,7 +3086,7 @@ int batch_apply_launch_warp(storm_batch* b, int wpc)
     int floats = 0;
     for (int i = 0; i < b->n; ++i) {
         const Problem& pb = b->inst[i].pb;
-        const WarpPlan wp = warp_plan(pb, false);
+        const WarpPlan wp = warp_plan(pb, 1);
         floats = std::max(floats, wp.floats);
         const double per_item = 100.0 + pb.M * (pb.B + pb.O) + 49.0 * pb.NPB + pb.P;
         for (int g = 0; g * wp.PW < pb.N; ++g)

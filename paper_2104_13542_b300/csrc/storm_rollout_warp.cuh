@@ -12,30 +12,34 @@
 // centres in registers, and world obstacles culled once per warp against the
 // axis-aligned box enclosing every link bound of the warp's items.
 //
-// The pair variant (kPair) gives each particle group two warps: warp A draws
-// the controls and integrates them, then both run FK, each into its own copy
-// of the link frames; A takes the pose, joint, end-effector and
-// manipulability terms and world collision while B takes self collision, and
-// the two meet at one named barrier per step slot.  The critical path is then
-// the longer branch, not their sum.
+// The pair and quad variants (kW = 2 or 4 warps per particle group) split
+// each item's work across warps.  Warp A draws the controls and integrates
+// them; then every warp of the group runs FK into its own copy of the link
+// frames.  Pair: A takes the pose, joint, end-effector and manipulability
+// terms and world collision, B self collision.  Quad: A the pose, joint and
+// end-effector terms, B world collision and manipulability, C and D alternate
+// halves of each lane's overlapping self-collision frame pairs.  The warps
+// meet at one named barrier per step slot, where A gathers the depths (a max
+// over the same tests, in any order) and adds the terms in the single-warp
+// order; the critical path is the longest branch, not their sum.
 #pragma once
 
 // Per-warp shared-memory plan (float offsets).
 struct WarpPlan {
     int Lp, PW, SL;  // lanes per particle, particles per warp, items per lane
-    int frame;       // F x 12 x 32: link frames, row-major [R | p] rows, lane-minor
-    int frame_b;     // the same for warp B of a pair (its own copy), else = frame
-    int cb;          // F x 3 x 32: link bounding-sphere centres, lane-minor
+    int frame;       // kW x F x 12 x 32: link frames, row-major [R | p] rows, lane-minor, one copy per warp
+    int cb;          // kW x F x 3 x 32: link bounding-sphere centres, lane-minor, one copy per warp
+    int fstride, cstride;  // one warp's frame / centre copy
     int eps;         // PW x S x d noise
     int u, th, thd;  // PW x H x d controls and joint states
     int c;           // PW x H running costs
     int ba;          // PW x H x 2 ball in-plane gravity
-    int ds;          // PW x H self-collision depths handed from warp B to A (pair variant)
-    int io;          // mu (H x d) | sigma (d) | state (3 x d) | goal (7), staged once per warp
+    int hand;        // 4 x PW x H handed to warp A: self depths (C, D), world depth, manipulability cost
+    int io;          // mu (H x d) | sigma (d) | state (3 x d) | goal (7) | dt (H) | gamma^h (H), staged per warp
     int floats;      // size of one warp's (pair's) region
 };
 
-__host__ __device__ inline WarpPlan warp_plan(const Problem& pb, bool pair)
+__host__ __device__ inline WarpPlan warp_plan(const Problem& pb, int kw)
 {
     WarpPlan w;
     w.Lp = pb.H > 16 ? 32 : (pb.H > 8 ? 16 : 8);
@@ -48,17 +52,18 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb, bool pair)
         off += (n + 3) & ~3;
         return o;
     };
-    w.frame = take(F * 12 * 32);
-    w.frame_b = pair ? take(F * 12 * 32) : w.frame;
-    w.cb = take(F * 3 * 32);
+    w.fstride = F * 12 * 32;
+    w.cstride = F * 3 * 32;
+    w.frame = take(kw * w.fstride);
+    w.cb = take(kw * w.cstride);
     w.eps = take(w.PW * pb.S * pb.d);
     w.u = take(w.PW * pb.H * pb.d);
     w.th = take(w.PW * pb.H * pb.d);
     w.thd = take(w.PW * pb.H * pb.d);
     w.c = take(w.PW * pb.H);
     w.ba = take(w.PW * pb.H * 2);
-    w.ds = take(w.PW * pb.H);
-    w.io = take(pb.H * pb.d + 4 * pb.d + 7);
+    w.hand = take(4 * w.PW * pb.H);
+    w.io = take(pb.H * pb.d + 4 * pb.d + 7 + 2 * pb.H);
     w.floats = off;
     return w;
 }
@@ -131,28 +136,34 @@ __device__ __forceinline__ float3 frame_point(const float* __restrict__ fr, int 
                        fmaf(fr[8 * 32 + lane], q.x, fmaf(fr[9 * 32 + lane], q.y, fmaf(fr[10 * 32 + lane], q.z, fr[11 * 32 + lane]))));
 }
 
-// The two warps of pair `unit` meet (named barrier 1 + unit, 64 threads).
-__device__ __forceinline__ void pair_sync(int unit)
+// The warps of group `unit` meet (named barrier 1 + unit, `threads` threads).
+__device__ __forceinline__ void unit_sync(int unit, int threads)
 {
-    asm volatile("barrier.sync %0, 64;" ::"r"(unit + 1) : "memory");
+    asm volatile("barrier.sync %0, %1;" ::"r"(unit + 1), "r"(threads) : "memory");
 }
 
 // The rollout of particle group `wg` (particles wg*PW ..) of problem pb by
-// this warp (or warp pair `unit`), in the warp's shared-memory region ws.
-template <bool kPair>
+// this warp (or the kW warps of group `unit`), in the group's shared-memory
+// region ws.
+template <int kW>
 __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state, const float* __restrict__ goal,
                                                   uint32_t step, int iter, int front_only, int wg, int unit, float* ws)
 {
-    const WarpPlan W = warp_plan(pb, kPair);
+    static_assert(kW == 1 || kW == 2 || kW == 4, "one, two or four warps per particle group");
+    const WarpPlan W = warp_plan(pb, kW);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool do_costs = !kPair || (warp & 1) == 0;  // A: controls, integration, costs, world collision
-    const bool do_selfc = !kPair || (warp & 1) == 1;  // B: self collision
+    const int role = kW == 1 ? 0 : warp % kW;
+    const bool do_costs = role == 0;  // A: controls, integration, the cost terms
+    const bool do_world = kW == 1 || (kW == 2 ? role == 0 : role == 1);
+    const bool do_manipw = kW <= 2 ? role == 0 : role == 1;
+    const bool do_selfc = kW == 1 || (kW == 2 ? role == 1 : role >= 2);
+    const int self_half = kW == 4 ? role - 2 : -1;  // quad: which alternate hits; -1: all of them
     const int nw0 = wg * W.PW;  // first particle of this unit
-    if (nw0 >= pb.N) return;    // uniform over the unit (both warps of a pair)
-    float* s_fr = ws + (do_costs ? W.frame : W.frame_b);  // this warp's own frames
-    float* s_cb = ws + W.cb;
+    if (nw0 >= pb.N) return;    // uniform over the unit (all its warps)
+    float* s_fr = ws + W.frame + role * W.fstride;  // this warp's own frames
+    float* s_cb = ws + W.cb + role * W.cstride;
     float* s_eps = ws + W.eps;
     float* s_u = ws + W.u;
     float* s_th = ws + W.th;
@@ -170,17 +181,27 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     float* s_sig = s_mu + H * d;
     float* s_st = s_sig + d;
     float* s_goal = s_st + 3 * d;
+    float* s_dt = s_goal + 7;  // the time steps and discount powers, read in dependent chains
+    float* s_gp = s_dt + H;
     auto stage_inputs = [&]() {
         for (int i = lane; i < H * d; i += 32) s_mu[i] = __ldcg(pb.mu + i);
         if (lane < d) s_sig[lane] = __ldcg(pb.sigma + lane);
         if (lane < 3 * d) s_st[lane] = state[lane];
         if (lane < 7) s_goal[lane] = goal[lane];
+        for (int i = lane; i < H; i += 32) {
+            s_dt[i] = pb.dt[i];
+            s_gp[i] = pb.gpow[i];
+        }
     };
     auto stage_inputs_async = [&]() {  // the same copies, in flight while the noise is drawn
         for (int i = lane; i < H * d; i += 32) cp_async4(s_mu + i, pb.mu + i);
         if (lane < d) cp_async4(s_sig + lane, pb.sigma + lane);
         if (lane < 3 * d) cp_async4(s_st + lane, state + lane);
         if (lane < 7) cp_async4(s_goal + lane, goal + lane);
+        for (int i = lane; i < H; i += 32) {
+            cp_async4(s_dt + i, pb.dt + i);
+            cp_async4(s_gp + i, pb.gpow + i);
+        }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (do_costs) {
@@ -284,8 +305,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
 #pragma unroll 6
         for (int h = 0; h < H; ++h) {
             const int idx = (p * H + h) * d + j;
-            v = fmaf(pb.dt[h], s_u[idx], v);
-            q = fmaf(pb.dt[h], v, q);
+            v = fmaf(s_dt[h], s_u[idx], v);
+            q = fmaf(s_dt[h], v, q);
             s_thd[idx] = v;
             s_th[idx] = q;
         }
@@ -297,7 +318,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     if (out.theta_dot)
         for (int i = lane; i < np_w * HD; i += 32) out.theta_dot[static_cast<size_t>(nw0) * HD + i] = s_thd[i];
     }
-    if (kPair) pair_sync(unit);  // B reads the controls and joint states
+    if (kW > 1) unit_sync(unit, kW * 32);  // the other warps read the controls and joint states
     if (front_only) return;
 
     // ---- per-problem constants in registers
@@ -482,20 +503,21 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             t[9] = c_ee.y;
             t[10] = 0.f;
         }
+        }  // do_costs
         // manipulability (Eq. 12)
-        if (want_manip) {
+        float c_manip = 0.f;
+        if (do_manipw && want_manip) {
             const float m = manipulability_mgs(J, d);
-            const float c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
-            part += pb.w_manip * c_manip;
+            c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
+            if (kW <= 2) part += pb.w_manip * c_manip;  // the quad's A adds it at the hand-off
             if (valid && out.terms) out.terms[gi * STORM_NTERMS + 4] = c_manip;
         }
-        }  // do_costs
         __syncwarp();
         trace_stamp(pb.trace, 3);
 
         // ---- world collision, Eq. 14 reading
         float dworld = 0.f;
-        if (do_costs && NO > 0 && pb.M > 0) {
+        if (do_world && NO > 0 && pb.M > 0) {
             if (pb.broadphase) {
                 // box enclosing every link bound of the warp's items, padded 1 mm
                 float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -610,9 +632,11 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                 }
             }
         }
+        int hit_no = 0;  // the quad's C and D take alternate hits of each lane
         while (lp_hit) {
             const int t = __ffs(lp_hit) - 1;
             lp_hit &= lp_hit - 1;
+            if (self_half >= 0 && (hit_no++ & 1) != self_half) continue;
             int bk0 = 0, bk1 = 0;  // the pair's block range, read with constant indices only
 #pragma unroll
             for (int u = 0; u < kLinkPairs; ++u) {
@@ -670,7 +694,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             }
         }
         if (do_self) {
-            for (int k = 0; k < pb.P; ++k) {
+            for (int k = self_half > 0 ? 1 : 0; k < pb.P; k += self_half >= 0 ? 2 : 1) {
                 const uint32_t pr = pb.pairs[k];
                 const int a = pr & 0xffff, b = pr >> 16;
                 int la = 0, lk = 0;
@@ -693,10 +717,26 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         trace_stamp(pb.trace, 5);
 
         // ---- running cost (Eq. 15)
-        if (kPair) {  // B hands its self-collision depths to A
-            if (do_selfc && valid) ws[W.ds + pl * H + h] = dself;
-            pair_sync(unit);
-            if (do_costs && valid) dself = ws[W.ds + pl * H + h];
+        if (kW > 1) {  // the other warps hand their results to A
+            float* hand = ws + W.hand;
+            const int PH = W.PW * H, ix = pl * H + h;
+            if (valid) {
+                if (do_selfc) hand[(self_half > 0 ? PH : 0) + ix] = dself;
+                if (kW == 4 && do_world) {
+                    hand[2 * PH + ix] = dworld;
+                    hand[3 * PH + ix] = c_manip;
+                }
+            }
+            unit_sync(unit, kW * 32);
+            if (do_costs && valid) {
+                if (kW == 2) {
+                    dself = hand[ix];
+                } else {
+                    dself = fmaxf(hand[ix], hand[PH + ix]);
+                    dworld = hand[2 * PH + ix];
+                    if (want_manip) part += pb.w_manip * hand[3 * PH + ix];
+                }
+            }
         }
         if (do_costs) {
             const float c = part + pb.w_coll * (dself + dworld);
@@ -729,24 +769,24 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     if (lane < np_w) {
         float C = 0.f;
 #pragma unroll 6
-        for (int h = 0; h < H; ++h) C = fmaf(pb.gpow[h], s_c[lane * H + h], C);
+        for (int h = 0; h < H; ++h) C = fmaf(s_gp[h], s_c[lane * H + h], C);
         out.Ctot[nw0 + lane] = C;
     }
     trace_stamp(pb.trace, 6);
 }
 
-template <bool kPair>
+template <int kW>
 __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
 k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
                const StepState* __restrict__ st, int step_override, int iter, int front_only)
 {
     extern __shared__ __align__(16) float wsm[];
-    const WarpPlan W = warp_plan(pb, kPair);
+    const WarpPlan W = warp_plan(pb, kW);
     const int warp = threadIdx.x >> 5;
-    const int unit = kPair ? warp >> 1 : warp;  // the warp, or warp pair, of a particle group
-    const int units = kPair ? (blockDim.x >> 6) : (blockDim.x >> 5);
+    const int unit = warp / kW;  // the kW warps of a particle group
+    const int units = (blockDim.x >> 5) / kW;
     pdl_trigger();
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
-    rollout_warp_body<kPair>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
+    rollout_warp_body<kW>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
                              wsm + unit * W.floats);
 }

@@ -94,11 +94,9 @@ def test_mappings_bitwise_identical(name):
         ctl.set_distribution(mu, sig)
         ctl.set_launch(2, 256)
         ref = {k: host(v) for k, v in ctl.generate_rollouts(cuda(state), cuda(goal), 3, 0).items()}
-        for mapping, count in (("warp", 1), ("warp", 3), ("pair", 1), ("pair", 2)):
-            if mapping == "warp":
-                ctl.set_launch_warp(count)
-            else:
-                ctl.set_launch_warp_pair(count)
+        for mapping, count in (("warp", 1), ("warp", 3), ("pair", 1), ("pair", 2), ("quad", 1), ("quad", 2)):
+            {"warp": ctl.set_launch_warp, "pair": ctl.set_launch_warp_pair,
+             "quad": ctl.set_launch_warp_quad}[mapping](count)
             g = {k: host(v) for k, v in ctl.generate_rollouts(cuda(state), cuda(goal), 3, 0).items()}
             for k in ref:
                 assert np.array_equal(g[k], ref[k]), (mapping, count, k)

@@ -410,14 +410,13 @@ def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
         ref = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 3, 1).items()}
         for bp in (True, False):
             ctl.set_broadphase(bp)
-            for mapping, count in (("warp", 1), ("warp", 3), ("warp", 8), ("pair", 1), ("pair", 3)):
-                if mapping == "warp":
-                    ctl.set_launch_warp(count)
-                else:
-                    ctl.set_launch_warp_pair(count)
+            for mapping, count in (("warp", 1), ("warp", 3), ("warp", 8), ("pair", 1), ("pair", 3),
+                                   ("quad", 1), ("quad", 2)):
+                {"warp": ctl.set_launch_warp, "pair": ctl.set_launch_warp_pair,
+                 "quad": ctl.set_launch_warp_quad}[mapping](count)
                 assert ctl.launch_mapping() == mapping
                 ppc, threads = ctl.get_launch()
-                assert threads == (32 if mapping == "warp" else 64) * count
+                assert threads == {"warp": 32, "pair": 64, "quad": 128}[mapping] * count
                 g = {k: host(v) for k, v in ctl.generate_rollouts(state, goal, 3, 1).items()}
                 for k in ref:
                     assert np.array_equal(g[k], ref[k]), (bp, mapping, count, k)
@@ -427,6 +426,8 @@ def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
             ctl.set_launch_warp(9)
         with pytest.raises(StormError):
             ctl.set_launch_warp_pair(5)
+        with pytest.raises(StormError):
+            ctl.set_launch_warp_quad(3)
     active = {nm for t, nm in enumerate(W.TERM_NAMES) if (ref["terms"][..., t] > 0).any()}
     assert {"pos", "rot", "manip"} <= active
     if name == "paper_terms":  # both collision phases exercised (checked on the oracle)
