@@ -280,10 +280,11 @@ int storm_set_ball(storm_handle* h, const float* ball_pos_vel);
  *                   with a CTA barrier between phases;
  *   STORM_MAP_WARP  a warp takes one particle (or 2 / 4 of them when H <= 16
  *                   / 8), one lane per step (two steps per lane when H > 32),
- *                   with warp-level synchronisation only; the default;
+ *                   with warp-level synchronisation only;
  *   STORM_MAP_WARP_PAIR  the same with two warps per particle group: one for
  *                   the controls, the cost terms and world collision, one
- *                   for self collision, meeting once per step slot;
+ *                   for self collision, meeting once per step slot (the
+ *                   default, one pair per CTA);
  *   STORM_MAP_WARP_QUAD  four warps per particle group: the controls and the
  *                   pose / joint / end-effector terms; world collision and
  *                   manipulability; two halves of self collision. */

@@ -704,26 +704,6 @@ __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
     bi = shi[0];
 }
 
-// Block-wide sums of two values (fixed order: butterfly per warp, then warp 0
-// over the warps); results in every thread.
-__device__ __forceinline__ float2 block_sum2(float a, float b, float2* sh)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    a = warp_sum(a);
-    b = warp_sum(b);
-    __syncthreads();
-    if (lane == 0) sh[wid] = make_float2(a, b);
-    __syncthreads();
-    if (wid == 0) {
-        float2 x = lane < nw ? sh[lane] : make_float2(0.f, 0.f);
-        x.x = warp_sum(x.x);
-        x.y = warp_sum(x.y);
-        if (lane == 0) sh[32] = x;
-    }
-    __syncthreads();
-    return sh[32];
-}
-
 // update_distribution (Eqs. 4-6) on one thread-block cluster of kUpdCluster
 // CTAs per problem, as weighted sums over the particles of the N x (H d)
 // control matrix (one row per particle, contiguous).  Every CTA forms the
@@ -789,15 +769,16 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
                                                const float* __restrict__ u, float* __restrict__ weights_out,
                                                StepState* st, float* __restrict__ cmd_out, int finalize)
 {
-    extern __shared__ __align__(16) float s_w[];  // N costs, then weights
+    extern __shared__ __align__(16) float s_w[];  // N weights (the chunk's), then N costs
     __shared__ float s_redf[32];
     __shared__ int s_redi[32];
-    __shared__ float2 s_red2[33];
     __shared__ float2 s_grp[kUpdGroups][kUpdateThreads];  // the thread groups' (A1, A2) per column
-    __shared__ float s_a1[kUpdateThreads], s_a2[kUpdateThreads];  // this CTA's partials, read by rank 0
+    __shared__ float s_a1[kUpdateThreads + 1], s_a2[kUpdateThreads + 1];  // this CTA's partials (column O:
+                                                                          // sum w, sum w c), read by rank 0
     __shared__ float s_dev[kUpdateThreads];                       // rank 0: squared deviation per column
     __shared__ float s_mu[kMaxDof];                               // rank 0: new mean of row 0
     const int N = pb.N, d = pb.d, H = pb.H, O = H * d;
+    float* s_cost = s_w + ((N + 3) & ~3);
     const int tid = threadIdx.x, T = blockDim.x;
     const unsigned rank = cluster_rank();
     const int chunk = (N + kUpdCluster - 1) / kUpdCluster;
@@ -822,7 +803,7 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     int bi = INT_MAX;
     for (int n = tid; n < N; n += T) {
         const float c = __ldcg(C + n);
-        s_w[n] = c;
+        s_cost[n] = c;
         if (isfinite(c) && c < bv) {
             bv = c;
             bi = n;
@@ -833,23 +814,31 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     const int arg = bi;
     const bool degenerate = (arg == INT_MAX);
 
-    float s = 1.f, sc = 0.f;
+    auto weight = [&](int n, float c) {  // Eq. 6
+        if (!isfinite(c)) return 0.f;
+        return pb.beta > 0.f ? expf(-(c - m) / pb.beta) : (n == arg ? 1.f : 0.f);
+    };
     if (!degenerate) {
-        // ---- weights, Eq. 6 (each thread rewrites its own entries)
-        float ls = 0.f, lsc = 0.f;
-        for (int n = tid; n < N; n += T) {
-            const float c = s_w[n];
-            float w = 0.f;
-            if (isfinite(c)) w = pb.beta > 0.f ? expf(-(c - m) / pb.beta) : (n == arg ? 1.f : 0.f);
-            s_w[n] = w;
-            ls += w;
-            if (w > 0.f) lsc = fmaf(w, c, lsc);
+        // ---- the chunk's weights, Eq. 6; the last warp (no columns of its own
+        // when H d <= 224) sums them and w c for rank 0
+        __syncthreads();  // every cost is in s_cost
+        for (int n = n0 + tid; n < n1; n += T) s_w[n] = weight(n, s_cost[n]);
+        __syncthreads();
+        if (tid >= T - 32) {
+            const int l = tid - (T - 32);
+            float ls = 0.f, lsc = 0.f;
+            for (int n = n0 + l; n < n1; n += 32) {
+                const float w = s_w[n];
+                ls += w;
+                if (w > 0.f) lsc = fmaf(w, s_cost[n], lsc);
+            }
+            ls = warp_sum(ls);
+            lsc = warp_sum(lsc);
+            if (l == 0) {
+                s_a1[O] = ls;
+                s_a2[O] = lsc;
+            }
         }
-        const float2 tot = block_sum2(ls, lsc, s_red2);
-        s = tot.x;
-        sc = tot.y;
-        if (weights_out && rank == 0)
-            for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * (1.f / s);
 
         // ---- the chunk's column sums about the old mean, particles in order
         if (col) {
@@ -895,7 +884,10 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             if (weights_out)
                 for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
         } else {
+            const float s = cluster_sum(s_a1 + O), sc = cluster_sum(s_a2 + O);
             const float inv_s = 1.f / s, al = pb.alpha_mu;
+            if (weights_out)
+                for (int n = tid; n < N; n += T) weights_out[n] = weight(n, s_cost[n]) * inv_s;
             if (tid < O) {  // here k == tid
                 const float A1 = cluster_sum(s_a1 + tid), A2 = cluster_sum(s_a2 + tid);
                 const float mnew = fmaf(al * A1, inv_s, mu_k);
@@ -1574,8 +1566,8 @@ struct storm_handle {
     size_t rollout_smem = 0, update_smem = 0;
     int grid = 0;
     int threads = kThreads;  // rollout CTA size (CTA-wide mapping)
-    int mapping = STORM_MAP_WARP;  // rollout work mapping
-    int wpc = 2;                   // warps (warp mapping) or warp pairs (pair mapping) per CTA
+    int mapping = STORM_MAP_WARP_PAIR;  // rollout work mapping
+    int wpc = 1;                        // warps, warp pairs or four-warp groups per CTA
     bool dep_launch = false;       // step graph: rollouts and updates as programmatic dependents
     size_t warp_smem = 0;          // its dynamic shared memory
     int warp_grid = 0;
@@ -2237,7 +2229,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
 
     const RolloutLayout L = rollout_layout(pb);
     h->rollout_smem = L.bytes;
-    h->update_smem = sizeof(float) * ((pb.N + 3) & ~3);
+    h->update_smem = sizeof(float) * 2 * ((pb.N + 3) & ~3);
     h->adjoint_smem = adjoint_layout(pb).bytes;
     int rc = allow_smem(h);
     if (rc) return rc;
@@ -3239,7 +3231,7 @@ int batch_create_impl(storm_batch* b, int n, const storm_robot* r, const storm_w
         const Problem& pb = I.pb;
         total += align256(plans[i].total) + align256(sizeof(float) * size_t(pb.N) * pb.H * pb.d) +
                  align256(sizeof(float) * pb.N);
-        b->update_smem = std::max(b->update_smem, sizeof(float) * ((pb.N + 3) & ~size_t(3)));
+        b->update_smem = std::max(b->update_smem, sizeof(float) * 2 * ((pb.N + 3) & ~size_t(3)));
     }
     BK(cudaMalloc(&b->arena, total));
     BK(cudaMemsetAsync(b->arena, 0, total, b->stream));

@@ -403,7 +403,7 @@ def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
     state, goal = cuda(f32(state)), cuda(f32(wl.goal))
     mu, sig = f32(W.make_mean(sseed, p.H, 7, 0.8)), f32(W.make_sigma(sseed, 7, 0.2, 0.6))
     with _ctl(wl, p) as ctl:
-        assert ctl.launch_mapping() == "warp"
+        assert ctl.launch_mapping() == "pair" and ctl.get_launch()[1] == 64
         ctl.set_distribution(mu, sig)
         ctl.set_launch(2, 256)
         assert ctl.launch_mapping() == "cta"
