@@ -706,23 +706,20 @@ __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
 
 // update_distribution (Eqs. 4-6) on one thread-block cluster of kUpdCluster
 // CTAs per problem, as weighted sums over the particles of the N x (H d)
-// control matrix (one row per particle, contiguous).  Every CTA forms the
-// min-shifted exponential weights of all N particles (Eq. 6); CTA c then sums
-// its own contiguous chunk of particles into two partials per column (h, j),
+// control matrix (one row per particle, contiguous).  Every CTA finds the
+// minimum cost of all N particles, then weighs its own contiguous chunk of
+// particles (Eq. 6) and sums the chunk into one partial per column (h, j),
 // thread k holding column k so that each particle row is one coalesced read:
-// A1 = sum w (u - mu_old) and A2 = sum w (u - mu_old)^2, about the mean the
-// iteration started from.  Rank 0 adds the partials of the cluster over
-// distributed shared memory, in rank order, and forms the new mean (Eq. 4)
-// mu_old + alpha_mu A1 / s and the squared deviation about it,
-// A2 - (2 alpha_mu - alpha_mu^2) A1^2 / s (the same quantity as the sum of
-// w (u - mu_new)^2, in one pass), then adds those over h into the per-joint
-// sigma (Eq. 5), records the iteration's best and weighted-mean cost and, at
-// the last iteration of a step, writes next_command and advances the step
-// counter; a second barrier keeps the CTAs resident until it has read them.
-// Every sum runs in a fixed order (weights: particles n = tid, tid + T, ...
-// per thread, a butterfly per warp, the warps in order; columns: the chunk's
-// particles in order, interleaved over kUpdGroups thread groups added in
-// order, then the CTAs in rank order; sigma: the rows in order): bitwise
+// first sum w (u - mu_old), from which every CTA forms the new mean (Eq. 4)
+// mu_old + alpha_mu A1 / s out of the cluster's partials (read over
+// distributed shared memory, in rank order); then, from the values still in
+// registers, sum w (u - mu_new)^2, which rank 0 adds over the cluster and over
+// h into the per-joint sigma (Eq. 5).  Rank 0 also records the iteration's
+// best and weighted-mean cost and, at the last iteration of a step, writes
+// next_command and advances the step counter; a last barrier keeps the CTAs
+// resident until it has read them.  Every sum runs in a fixed order (the
+// chunk's particles in order, interleaved over kUpdGroups thread groups added
+// in order, then the CTAs in rank order; sigma: the rows in order): bitwise
 // reproducible, whatever the grid around the cluster.
 constexpr int kUpdCluster = 8;
 constexpr int kUpdGroups = kUpdateThreads / 256;  // particle interleave when H d <= 256
@@ -772,11 +769,11 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     extern __shared__ __align__(16) float s_w[];  // N weights (the chunk's), then N costs
     __shared__ float s_redf[32];
     __shared__ int s_redi[32];
-    __shared__ float2 s_grp[kUpdGroups][kUpdateThreads];  // the thread groups' (A1, A2) per column
+    __shared__ float s_grp[kUpdGroups][kUpdateThreads];  // the thread groups' column sums
     __shared__ float s_a1[kUpdateThreads + 1], s_a2[kUpdateThreads + 1];  // this CTA's partials (column O:
-                                                                          // sum w, sum w c), read by rank 0
+                                                                          // sum w, sum w c), read over the cluster
     __shared__ float s_dev[kUpdateThreads];                       // rank 0: squared deviation per column
-    __shared__ float s_mu[kMaxDof];                               // rank 0: new mean of row 0
+    __shared__ float s_mu[kUpdateThreads];                        // the new mean, every column
     const int N = pb.N, d = pb.d, H = pb.H, O = H * d;
     float* s_cost = s_w + ((N + 3) & ~3);
     const int tid = threadIdx.x, T = blockDim.x;
@@ -797,6 +794,8 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     float x[kUpdBatch];
 #pragma unroll
     for (int q = 0; q < kUpdBatch; ++q) x[q] = q < cnt ? up[q * stride] : 0.f;
+    float wv[kUpdBatch];                // the same particles' weights (pass 1 reads them)
+    const float* wp = s_w + n0 + g;
 
     // ---- min finite cost and its lowest index
     float bv = INFINITY;
@@ -840,39 +839,71 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             }
         }
 
-        // ---- the chunk's column sums about the old mean, particles in order
+        // ---- pass 1: the chunk's sum w (u - mu_old) per column, particles in order
+        // (each batch's weights are read into registers together, then summed)
         if (col) {
-            float a1 = 0.f, a2 = 0.f;
-            const float* wp = s_w + n0 + g;
+            float a1 = 0.f;
             for (int q0 = 0; q0 < cnt; q0 += kUpdBatch) {
                 if (q0 > 0) {
 #pragma unroll
                     for (int q = 0; q < kUpdBatch; ++q) x[q] = q0 + q < cnt ? up[(q0 + q) * stride] : 0.f;
                 }
 #pragma unroll
-                for (int q = 0; q < kUpdBatch; ++q) {
-                    if (q0 + q < cnt) {
-                        const float w = wp[(q0 + q) * G], e = x[q] - mu_k;
-                        a1 = fmaf(w, e, a1);
-                        a2 = fmaf(w * e, e, a2);
-                    }
-                }
+                for (int q = 0; q < kUpdBatch; ++q) wv[q] = q0 + q < cnt ? wp[(q0 + q) * G] : 0.f;
+#pragma unroll
+                for (int q = 0; q < kUpdBatch; ++q)
+                    if (q0 + q < cnt) a1 = fmaf(wv[q], x[q] - mu_k, a1);
             }
-            s_grp[g][k] = make_float2(a1, a2);
+            s_grp[g][k] = a1;
         }
         __syncthreads();
         if (tid < O) {
-            float2 p = s_grp[0][tid];
-            for (int q = 1; q < G; ++q) {
-                p.x += s_grp[q][tid].x;
-                p.y += s_grp[q][tid].y;
+            float p = s_grp[0][tid];
+            for (int q = 1; q < G; ++q) p += s_grp[q][tid];
+            s_a1[tid] = p;
+        }
+    }
+    cluster_barrier();  // the mean partials and the normalisers are complete
+
+    float s = 1.f, inv_s = 1.f;
+    if (!degenerate) {
+        // ---- the new mean, Eq. 4, in every CTA from the cluster's partials
+        s = cluster_sum(s_a1 + O);
+        inv_s = 1.f / s;
+        if (tid < O) s_mu[tid] = fmaf(pb.alpha_mu * cluster_sum(s_a1 + tid), inv_s, mu_k);  // k == tid here
+        __syncthreads();
+        if (rank == 0 && tid < O) pb.mu[tid] = s_mu[tid];
+
+        // ---- pass 2: the chunk's sum w (u - mu_new)^2 per column, Eq. 5
+        if (col) {
+            const float mk = s_mu[k];
+            float a2 = 0.f;
+            for (int q0 = 0; q0 < cnt; q0 += kUpdBatch) {
+                if (cnt > kUpdBatch) {  // more than one batch: x and wv hold the last one
+#pragma unroll
+                    for (int q = 0; q < kUpdBatch; ++q) x[q] = q0 + q < cnt ? up[(q0 + q) * stride] : 0.f;
+#pragma unroll
+                    for (int q = 0; q < kUpdBatch; ++q) wv[q] = q0 + q < cnt ? wp[(q0 + q) * G] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < kUpdBatch; ++q) {
+                    if (q0 + q < cnt) {
+                        const float e = x[q] - mk;
+                        a2 = fmaf(wv[q] * e, e, a2);
+                    }
+                }
             }
-            s_a1[tid] = p.x;
-            s_a2[tid] = p.y;
+            s_grp[g][k] = a2;
+        }
+        __syncthreads();
+        if (tid < O) {
+            float p = s_grp[0][tid];
+            for (int q = 1; q < G; ++q) p += s_grp[q][tid];
+            s_a2[tid] = p;
         }
     }
 
-    // ---- rank 0: the new mean (Eq. 4) and sigma (Eq. 5) from the cluster's partials
+    // ---- rank 0: sigma (Eq. 5) from the cluster's deviation partials
     cluster_barrier();
     if (rank == 0) {
         if (degenerate) {
@@ -884,17 +915,9 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             if (weights_out)
                 for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
         } else {
-            const float s = cluster_sum(s_a1 + O), sc = cluster_sum(s_a2 + O);
-            const float inv_s = 1.f / s, al = pb.alpha_mu;
             if (weights_out)
                 for (int n = tid; n < N; n += T) weights_out[n] = weight(n, s_cost[n]) * inv_s;
-            if (tid < O) {  // here k == tid
-                const float A1 = cluster_sum(s_a1 + tid), A2 = cluster_sum(s_a2 + tid);
-                const float mnew = fmaf(al * A1, inv_s, mu_k);
-                pb.mu[tid] = mnew;
-                if (tid < d) s_mu[tid] = mnew;
-                s_dev[tid] = fmaxf(0.f, A2 - (2.f * al - al * al) * (A1 * A1) * inv_s);
-            }
+            if (tid < O) s_dev[tid] = cluster_sum(s_a2 + tid);
             __syncthreads();
             if (tid < d) {
                 const int j = tid;
@@ -908,7 +931,7 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             }
             if (tid == 0) {
                 st->best = m;
-                st->wmean = sc / s;
+                st->wmean = cluster_sum(s_a2 + O) / s;
             }
         }
         if (finalize) {

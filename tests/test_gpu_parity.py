@@ -144,6 +144,51 @@ def test_update_stage_parity(N, H, beta, amu, asg):
     assert max_rel(sig, osig, max(osig.max(), 1e-3)) < TOL_UPDATE
 
 
+def _update_explicit(C, u, mu0, sig0, beta, **kw):
+    wl = W.config_small(0)
+    N, H = u.shape[:2]
+    p = wl.params.replace(N=N, H=H, beta=beta, **kw)
+    orc = oracle.Oracle(wl.robot, wl.world, p)
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(f32(mu0), f32(sig0))
+        ctl.update_distribution(cuda(f32(C)), cuda(f32(u)))
+        mu, sig = ctl.get_distribution()
+    omu, osig, ost, ow = orc.update(f32(C), f32(u), f32(mu0), f32(sig0))
+    return mu, sig, omu, osig
+
+
+@pytest.mark.parametrize("case", ["zero_controls_win", "far_tight_cloud", "uniform_far"])
+def test_update_far_from_old_mean(case):
+    """Eq. 5 evaluated far from the mean the iteration started from: the weight on
+    zero controls (null particles) while |mu_old| >> sigma, and tight clouds of
+    samples several units from mu_old (sigma floor 0, so nothing masks an error
+    in the deviation sum)."""
+    rng = np.random.default_rng(7)
+    N, H = 300, 12
+    mu0 = np.full((H, 7), 3.0) + rng.normal(0, 0.1, (H, 7))
+    sig0 = np.full(7, 0.05)
+    if case == "zero_controls_win":
+        u = mu0 + 0.05 * rng.normal(size=(N, H, 7))
+        u[:10] = 0.0
+        C = np.where(np.arange(N) < 10, 1.0, 40.0) + rng.uniform(0, 0.5, N)
+        beta = 1.0
+    elif case == "far_tight_cloud":
+        u = mu0 + 5.0 + 1e-3 * rng.normal(size=(N, H, 7))
+        C = rng.uniform(0, 5, N)
+        beta = 2.0
+    else:
+        u = mu0 - 4.0 + 1e-2 * rng.normal(size=(N, H, 7))
+        C = np.full(N, 3.0)
+        beta = 10.0
+    mu, sig, omu, osig = _update_explicit(C, u, mu0, sig0, beta, sigma_min=0.0, alpha_sigma=1.0)
+    assert max_rel(mu, omu, max(1.0, np.abs(omu).max())) < TOL_UPDATE
+    # sigma to the update tolerance, or to the FP32 resolution of the mean it is
+    # measured about (a few ulps of max|mu|), whichever is larger; the deviation
+    # sum formed in one pass about mu_old misses this by ~1e-3 in the first case
+    bound = max(TOL_UPDATE * osig.max(), 4 * np.finfo(np.float32).eps * np.abs(mu0).max())
+    assert np.abs(sig - osig).max() <= bound, (sig, osig, bound)
+
+
 def test_update_zero_temperature_and_ties():
     C = np.full(50, 9.0)
     C[[7, 30]] = 2.0  # tie: lowest index wins
