@@ -724,6 +724,7 @@ __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
 constexpr int kUpdCluster = 8;
 constexpr int kUpdGroups = kUpdateThreads / 256;  // particle interleave when H d <= 256
 constexpr int kUpdBatch = 32;                     // loads in flight per thread
+constexpr int kUpdCostRegs = 2;                   // costs a thread loads ahead (N <= 1024 in one round)
 static_assert(STORM_MAX_H * kMaxDof <= kUpdateThreads, "one column per thread");
 
 __device__ __forceinline__ unsigned cluster_rank()
@@ -786,6 +787,10 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     // (costs, controls and the mean through L2: under a dependent launch this
     // CTA may have started before the rollout that wrote them finished)
     const float mu_k = col ? __ldcg(pb.mu + k) : 0.f;  // the column's mean before this update
+    // the costs first (the argmin waits on them), kUpdCostRegs per thread
+    float cr[kUpdCostRegs];
+#pragma unroll
+    for (int r = 0; r < kUpdCostRegs; ++r) cr[r] = tid + r * T < N ? __ldcg(C + tid + r * T) : INFINITY;
     // this thread's particles n0 + g, n0 + g + G, ... of the chunk: the first
     // kUpdBatch of them are loaded now, while the weights are formed
     const int cnt = col ? max(0, (n1 - n0 - g + G - 1) / G) : 0;
@@ -800,14 +805,17 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     // ---- min finite cost and its lowest index
     float bv = INFINITY;
     int bi = INT_MAX;
-    for (int n = tid; n < N; n += T) {
-        const float c = __ldcg(C + n);
+    auto visit = [&](int n, float c) {
         s_cost[n] = c;
         if (isfinite(c) && c < bv) {
             bv = c;
             bi = n;
         }
-    }
+    };
+#pragma unroll
+    for (int r = 0; r < kUpdCostRegs; ++r)
+        if (tid + r * T < N) visit(tid + r * T, cr[r]);
+    for (int n = tid + kUpdCostRegs * T; n < N; n += T) visit(n, __ldcg(C + n));
     block_argmin(bv, bi, s_redf, s_redi);
     const float m = bv;
     const int arg = bi;
