@@ -605,7 +605,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     __syncthreads();
     if (ball_on) {  // the ball along each particle's horizon
         for (int p = tid; p < np; p += nt)
-            ball_scan(pb, *s_ball0, s_ba + 2 * p * H, s_dt, s_part + p * H,
+            ball_scan(H, pb.w_ball, pb.tray[0], pb.tray[1], *s_ball0, s_ba + 2 * p * H, s_dt, s_part + p * H,
                       out.terms ? out.terms + (static_cast<size_t>(n0 + p) * H) * STORM_NTERMS + 10 : nullptr,
                       STORM_NTERMS);
         __syncthreads();

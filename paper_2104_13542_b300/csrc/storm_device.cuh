@@ -371,18 +371,18 @@ __device__ __forceinline__ float2 ball_accel(const float (&R)[9], const float (&
 // One particle's ball along the horizon (Eq. 7's semi-implicit recurrence on the
 // in-plane accelerations a[h * 2 .. +1]); c[h] += w_ball * |x_h - tray|, and the
 // unweighted term to term[h * term_stride] when term is not null.
-__device__ __forceinline__ void ball_scan(const Problem& pb, float4 s0, const float* a, const float* dt, float* c,
-                                          float* term, int term_stride)
+__device__ __forceinline__ void ball_scan(int H, float w_ball, float tray_x, float tray_y, float4 s0, const float* a,
+                                          const float* dt, float* c, float* term, int term_stride)
 {
     float vx = s0.z, vy = s0.w, x = s0.x, y = s0.y;
-    for (int h = 0; h < pb.H; ++h) {
+    for (int h = 0; h < H; ++h) {
         vx = fmaf(dt[h], a[2 * h], vx);
         vy = fmaf(dt[h], a[2 * h + 1], vy);
         x = fmaf(dt[h], vx, x);
         y = fmaf(dt[h], vy, y);
-        const float ex = x - pb.tray[0], ey = y - pb.tray[1];
+        const float ex = x - tray_x, ey = y - tray_y;
         const float cb = sqrtf(fmaf(ex, ex, ey * ey));
-        c[h] = fmaf(pb.w_ball, cb, c[h]);
+        c[h] = fmaf(w_ball, cb, c[h]);
         if (term) term[static_cast<size_t>(h) * term_stride] = cb;
     }
 }

@@ -128,6 +128,57 @@ __device__ __forceinline__ float ball_depth(const float* __restrict__ fr, int la
     return depth;
 }
 
+// World collision without the broad phase: every sphere of every frame against
+// every obstacle (the same tests in the same order as the inline form).  Out of
+// line, so that this cold path does not sit in the hot instruction stream.
+__device__ __noinline__ float world_brute_force(const float* __restrict__ s_fr, int lane,
+                                                const int* __restrict__ link_first, const float4* __restrict__ sph,
+                                                int F, const float* __restrict__ boxes, int B,
+                                                const float4* __restrict__ wsph, int O, float dworld)
+{
+    for (int f = 0; f < F; ++f) {
+        const int s0 = link_first[f], s1 = link_first[f + 1];
+        if (s0 >= s1) continue;
+        for (int b = 0; b < B; ++b) dworld = box_depth(s_fr + f * 12 * 32, lane, sph, s0, s1, boxes + b * 6, dworld);
+        for (int k = 0; k < O; ++k) dworld = ball_depth(s_fr + f * 12 * 32, lane, sph, s0, s1, wsph[k], dworld);
+    }
+    return dworld;
+}
+
+// The end-effector speed / acceleration limit terms of one item (Eq. 8), out of
+// line so that this path stays out of the hot instruction stream when the terms
+// are off.  The joint axes and origins (and the end-effector point) are read back
+// from this warp's frames, which hold the very values of the FK registers.
+__device__ __noinline__ float2 ee_terms_from_frames(const float* __restrict__ s_fr, int lane, int d,
+                                                    const float* thd, const float* thdd, float vmax, float amax)
+{
+    float z[kMaxDof][3], o[kMaxDof][3], p[3];
+#pragma unroll
+    for (int i = 0; i < kMaxDof; ++i) {
+        const float* fr = s_fr + (i + 1) * 12 * 32 + lane;
+        const bool in = i < d;
+        z[i][0] = in ? fr[2 * 32] : 0.f, z[i][1] = in ? fr[6 * 32] : 0.f, z[i][2] = in ? fr[10 * 32] : 0.f;
+        o[i][0] = in ? fr[3 * 32] : 0.f, o[i][1] = in ? fr[7 * 32] : 0.f, o[i][2] = in ? fr[11 * 32] : 0.f;
+    }
+    const float* fe = s_fr + d * 12 * 32 + lane;
+    p[0] = fe[3 * 32], p[1] = fe[7 * 32], p[2] = fe[11 * 32];
+    float xd[6], xdd[6];
+    ee_twist(z, o, p, thd, thdd, d, xd, xdd);
+    const float sp = sqrtf(fmaf(xd[0], xd[0], fmaf(xd[1], xd[1], xd[2] * xd[2])));
+    const float ac = sqrtf(fmaf(xdd[0], xdd[0], fmaf(xdd[1], xdd[1], xdd[2] * xdd[2])));
+    return make_float2(fmaxf(0.f, sp - vmax), fmaxf(0.f, ac - amax));
+}
+
+// The ball along one particle's horizon (initial state from the current pose, then
+// the scan), out of line: only ball-balancing problems take it.
+__device__ __noinline__ void ball_tail(const float* dhx, int d, const float* state, const float* ball, int H,
+                                       float w_ball, float tray_x, float tray_y, const float* a, const float* dt,
+                                       float* c, float* term)
+{
+    const float4 s0 = ball_initial(dhx, d, state, ball);
+    ball_scan(H, w_ball, tray_x, tray_y, s0, a, dt, c, term, STORM_NTERMS);
+}
+
 // Centre of sphere q in frame fr (the k_rollout expression).
 __device__ __forceinline__ float3 frame_point(const float* __restrict__ fr, int lane, float4 q)
 {
@@ -468,12 +519,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                pb.w_smooth * c_smooth;
         float2 c_ee = make_float2(0.f, 0.f);
         if (want_ee) {  // task-space limits on X_dot, X_ddot (Eq. 8), theta_ddot = u
-            float zc[kMaxDof][3];
-#pragma unroll
-            for (int i = 0; i < kMaxDof; ++i) zc[i][0] = J[3][i], zc[i][1] = J[4][i], zc[i][2] = J[5][i];
-            float xd[6], xdd[6];
-            ee_twist(zc, oc, pp, thd, uh, d, xd, xdd);
-            c_ee = ee_limit_terms(pb, xd, xdd);
+            c_ee = ee_terms_from_frames(s_fr, lane, d, thd, uh, pb.ee_vel_max, pb.ee_acc_max);
             if (pb.w_ee_vel != 0.f) part = fmaf(pb.w_ee_vel, c_ee.x, part);
             if (pb.w_ee_acc != 0.f) part = fmaf(pb.w_ee_acc, c_ee.y, part);
         }
@@ -591,18 +637,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                     }
                 }
             } else if (valid) {
-                // brute force: every sphere against every obstacle
-#pragma unroll
-                for (int f = 0; f <= kMaxDof; ++f) {
-                    if (f < F && first[f] < first[f + 1]) {
-                        for (int b = 0; b < pb.B; ++b)
-                            dworld = box_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
-                                               pb.boxes + b * 6, dworld);
-                        for (int k = 0; k < pb.O; ++k)
-                            dworld = ball_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
-                                                pb.wsph[k], dworld);
-                    }
-                }
+                dworld = world_brute_force(s_fr, lane, pb.link_first, pb.sph, F, pb.boxes, pb.B, pb.wsph, pb.O,
+                                           dworld);
             }
         }
         trace_stamp(pb.trace, 4);
@@ -753,10 +789,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     if (!do_costs) return;  // B is done
     if (ball_on) {  // the ball along each particle's horizon
         if (lane < np_w) {
-            const float4 s0 = ball_initial(pb.dhx, d, state, pb.ball);
-            ball_scan(pb, s0, s_ba + lane * H * 2, pb.dt, s_c + lane * H,
-                      out.terms ? out.terms + (static_cast<size_t>(nw0 + lane) * H) * STORM_NTERMS + 10 : nullptr,
-                      STORM_NTERMS);
+            ball_tail(pb.dhx, d, state, pb.ball, H, pb.w_ball, pb.tray[0], pb.tray[1], s_ba + lane * H * 2, pb.dt,
+                      s_c + lane * H,
+                      out.terms ? out.terms + (static_cast<size_t>(nw0 + lane) * H) * STORM_NTERMS + 10 : nullptr);
         }
         __syncwarp();
     }
