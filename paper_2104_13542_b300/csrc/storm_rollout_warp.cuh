@@ -35,7 +35,8 @@ struct WarpPlan {
     int c;           // PW x H running costs
     int ba;          // PW x H x 2 ball in-plane gravity
     int hand;        // 4 x PW x H handed to warp A: self depths (C, D), world depth, manipulability cost
-    int io;          // mu (H x d) | sigma (d) | state (3 x d) | goal (7) | dt (H) | gamma^h (H), staged per warp
+    int io;          // mu (H x d) | sigma (d) | state (3 x d) | goal (7) | dt (H) | gamma^h (H) |
+                     // B-spline basis (H x nk), staged per warp
     int floats;      // size of one warp's (pair's) region
 };
 
@@ -63,7 +64,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb, int kw)
     w.c = take(w.PW * pb.H);
     w.ba = take(w.PW * pb.H * 2);
     w.hand = take(4 * w.PW * pb.H);
-    w.io = take(pb.H * pb.d + 4 * pb.d + 7 + 2 * pb.H);
+    w.io = take(pb.H * pb.d + 4 * pb.d + 7 + 2 * pb.H + pb.H * pb.nk);
     w.floats = off;
     return w;
 }
@@ -234,6 +235,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     float* s_goal = s_st + 3 * d;
     float* s_dt = s_goal + 7;  // the time steps and discount powers, read in dependent chains
     float* s_gp = s_dt + H;
+    float* s_basis = s_gp + H;  // H x nk
     auto stage_inputs = [&]() {
         for (int i = lane; i < H * d; i += 32) s_mu[i] = __ldcg(pb.mu + i);
         if (lane < d) s_sig[lane] = __ldcg(pb.sigma + lane);
@@ -243,6 +245,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             s_dt[i] = pb.dt[i];
             s_gp[i] = pb.gpow[i];
         }
+        for (int i = lane; i < H * pb.nk; i += 32) s_basis[i] = pb.basis[i];
     };
     auto stage_inputs_async = [&]() {  // the same copies, in flight while the noise is drawn
         for (int i = lane; i < H * d; i += 32) cp_async4(s_mu + i, pb.mu + i);
@@ -253,6 +256,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             cp_async4(s_dt + i, pb.dt + i);
             cp_async4(s_gp + i, pb.gpow + i);
         }
+        for (int i = lane; i < H * pb.nk; i += 32) cp_async4(s_basis + i, pb.basis + i);
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (do_costs) {
@@ -326,7 +330,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             const int nk = pb.nk;
 #pragma unroll 2
             for (int s = 0; s < nk; ++s) {
-                const float b = pb.basis[h * nk + s];
+                const float b = s_basis[h * nk + s];
 #pragma unroll
                 for (int j = 0; j < kMaxDof; ++j)
                     if (j < d) e[j] = fmaf(b, eps[s * d + j], e[j]);
