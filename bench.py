@@ -333,7 +333,7 @@ def run_gpu(args, rank, world_size):
                                 f"{sm_mhz:.0f} MHz (unit count x SM max clock; MEASURED_PEAKS has "
                                 f"no FP32 figure)"},
         clocks=clocks,
-        gpu_launches=(1 + 2 * p.K) * args.steps,
+        gpu_launches=2 * p.K * args.steps,
         wall_s=wall,
     )
     ctl.close()

@@ -132,7 +132,8 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         uint4* dst = reinterpret_cast<uint4*>(smem + L.tab);
         for (int i = tid; i < pb.table_bytes / 16; i += nt) dst[i] = src[i];
     }
-    for (int i = tid; i < HD; i += nt) s_mu[i] = __ldcg(pb.mu + i);
+    const int mu_off = (pb.shift_view && step > 0) ? d : 0;  // the shifted mean at a step's start
+    for (int i = tid; i < HD; i += nt) s_mu[i] = i + mu_off < HD ? __ldcg(pb.mu + i + mu_off) : 0.f;
     for (int i = tid; i < d; i += nt) s_sigma[i] = __ldcg(pb.sigma + i);
     for (int i = tid; i < 3 * d; i += nt) s_state[i] = state[i];
     if (tid == 0) {
@@ -763,9 +764,12 @@ __device__ __forceinline__ float cluster_sum(const float* local)
     return a;
 }
 
+// shift: the first update of a step -- mu_old is the shifted mean (Alg. 1's
+// shift, read as in the rollout before it; see Problem::shift_view), written back
+// whole even when the iteration is degenerate, and the step's status starts at 0.
 __device__ __forceinline__ void update_cluster(const Problem& pb, const float* __restrict__ C,
                                                const float* __restrict__ u, float* __restrict__ weights_out,
-                                               StepState* st, float* __restrict__ cmd_out, int finalize)
+                                               StepState* st, float* __restrict__ cmd_out, int finalize, int shift)
 {
     extern __shared__ __align__(16) float s_w[];  // N weights (the chunk's), then N costs
     __shared__ float s_redf[32];
@@ -786,7 +790,9 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     const bool col = k < O && g < G;
     // (costs, controls and the mean through L2: under a dependent launch this
     // CTA may have started before the rollout that wrote them finished)
-    const float mu_k = col ? __ldcg(pb.mu + k) : 0.f;  // the column's mean before this update
+    const int mu_off = (shift && st->step > 0) ? d : 0;
+    const float mu_k = col ? (k + mu_off < O ? __ldcg(pb.mu + k + mu_off) : 0.f) : 0.f;  // mean before the update
+    if (shift && rank == 0 && tid == 0) st->status = 0;
     // the costs first (the argmin waits on them), kUpdCostRegs per thread
     float cr[kUpdCostRegs];
 #pragma unroll
@@ -922,6 +928,7 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             }
             if (weights_out)
                 for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
+            if (mu_off && tid < O) pb.mu[tid] = mu_k;  // the shifted mean, kept (k == tid here)
         } else {
             if (weights_out)
                 for (int n = tid; n < N; n += T) weights_out[n] = weight(n, s_cost[n]) * inv_s;
@@ -943,7 +950,7 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             }
         }
         if (finalize) {
-            if (tid < d) cmd_out[tid] = degenerate ? __ldcg(pb.mu + tid) : s_mu[tid];
+            if (tid < d) cmd_out[tid] = degenerate ? mu_k : s_mu[tid];
             if (tid == 0) st->step += 1;
         }
     }
@@ -952,11 +959,11 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
 
 __global__ void __cluster_dims__(kUpdCluster, 1, 1) __launch_bounds__(kUpdateThreads)
 k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
-         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out, int finalize)
+         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out, int finalize, int shift)
 {
     pdl_trigger();
     pdl_wait();
-    update_cluster(pb, C, u, weights_out, st, cmd_out, finalize);
+    update_cluster(pb, C, u, weights_out, st, cmd_out, finalize, shift);
 }
 
 #include "storm_adjoint.cuh"
@@ -1281,7 +1288,7 @@ k_update_batch(const BatchInstance* __restrict__ insts, int iter)
     const BatchInstance& I = insts[blockIdx.x / kUpdCluster];
     if (iter >= I.K) return;  // the whole cluster
     load_problem(I.pb, s_pb);
-    update_cluster(s_pb, I.C, I.u, nullptr, I.st, I.cmd, iter == I.K - 1);
+    update_cluster(s_pb, I.C, I.u, nullptr, I.st, I.cmd, iter == I.K - 1, 0);
 }
 
 // ============================================================================ surrogate network host side
@@ -1834,11 +1841,12 @@ cudaError_t launch_kernel(void (*kernel)(Params...), unsigned grid, unsigned blo
 // advances the step counter that the rollout reads before its pdl_wait.
 int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const float* state,
                    const float* goal, int step_override, int iter, bool exact_self = false,
-                   int front_only = 0, bool dep = false)
+                   int front_only = 0, bool dep = false, bool shift = false)
 {
     Problem pb = h->pb;
     if (exact_self) pb.self_pred = nullptr;
     pb.dep_launch = dep ? 1 : 0;
+    pb.shift_view = shift ? 1 : 0;
     if (h->mapping == STORM_MAP_WARP)
         CK(launch_kernel(k_rollout_warp<1>, h->warp_grid, h->wpc * 32, h->warp_smem, s, dep, pb, out, state,
                          goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
@@ -1854,11 +1862,12 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
     return STORM_OK;
 }
 
+// shift: the first update of a step graph (see update_cluster).
 int launch_update(storm_handle* h, cudaStream_t s, const float* C, const float* u, float* w,
-                  float* cmd, int finalize, bool dep = false)
+                  float* cmd, int finalize, bool dep = false, bool shift = false)
 {
     CK(launch_kernel(k_update, kUpdCluster, kUpdateThreads, h->update_smem, s, dep, h->pb, C, u, w, h->d_st, cmd,
-                     finalize));
+                     finalize, shift ? 1 : 0));
     return STORM_OK;
 }
 
@@ -1876,12 +1885,11 @@ int launch_adjoint(storm_handle* h, cudaStream_t s, const float* state, const fl
     return STORM_OK;
 }
 
-// Enqueue the kernels of one control step (device inputs in d_io).
+// Enqueue the kernels of one control step (device inputs in d_io).  Alg. 1's
+// shift is folded into the first iteration: its rollouts and update read the
+// shifted mean and the update stores it (no kernel of its own).
 int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
 {
-    const int O = h->pb.H * h->pb.d;
-    k_shift<<<1, std::max(32, ((O + 3) / 4 + 31) / 32 * 32), 0, s>>>(h->pb, h->d_st, 0);
-    CK(cudaGetLastError());
     RolloutOut out{h->d_u, nullptr, nullptr, nullptr, nullptr, nullptr, h->d_C};
     const float* state = h->d_io + io_state(h->pb);
     const float* goal = h->d_io + io_goal(h->pb);
@@ -1889,16 +1897,16 @@ int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
     for (int k = 0; k < h->K; ++k) {
         if (h->mlp) {  // surrogate: joint states, network, then the rollout proper
             RolloutOut front{h->d_u, h->d_theta, nullptr, nullptr, nullptr, nullptr, h->d_C};
-            int rc = launch_rollout(h, s, front, state, goal, -1, k, false, 1, h->dep_launch);
+            int rc = launch_rollout(h, s, front, state, goal, -1, k, false, 1, h->dep_launch, k == 0);
             if (rc) return rc;
             rc = mlp_forward(h->mlp, *h->mlp_buf, h->d_theta, h->pb.N * h->pb.H, h->pb.d, false,
                              h->d_pred, s);
             if (rc) return fail(h, rc, "surrogate forward launch failed");
         }
-        int rc = launch_rollout(h, s, out, state, goal, -1, k, false, 0, h->dep_launch);
+        int rc = launch_rollout(h, s, out, state, goal, -1, k, false, 0, h->dep_launch, k == 0);
         if (rc) return rc;
         rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1 && h->grad_steps == 0,
-                           h->dep_launch);
+                           h->dep_launch, k == 0);
         if (rc) return rc;
     }
     for (int g = 0; g < h->grad_steps; ++g) {  // gradient refinement of the mean

@@ -47,6 +47,8 @@ struct Problem {
     const float4* lbound;    // d + 1: bounding sphere of each frame's spheres (local centre, radius)
     int broadphase;          // 1: exact sphere tests only where the link bounds overlap
     int dep_launch;          // 1: this rollout launch is a programmatic dependent
+    int shift_view;          // 1: read mu shifted (row h = stored row h + 1, last row 0) once the
+                             // step counter is > 0 -- the first rollout of a step (Alg. 1's shift)
     unsigned long long* trace;  // nullable: phase-boundary %globaltimer stamps of rollout CTA 0
     const uint4* tables;     // start of the contiguous per-problem tables (dhx .. basis)
     int table_bytes;         // their size, a multiple of 16

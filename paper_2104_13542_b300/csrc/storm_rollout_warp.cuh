@@ -236,8 +236,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     float* s_dt = s_goal + 7;  // the time steps and discount powers, read in dependent chains
     float* s_gp = s_dt + H;
     float* s_basis = s_gp + H;  // H x nk
+    const int mu_off = (pb.shift_view && step > 0) ? d : 0;  // the shifted mean at a step's start
     auto stage_inputs = [&]() {
-        for (int i = lane; i < H * d; i += 32) s_mu[i] = __ldcg(pb.mu + i);
+        for (int i = lane; i < H * d; i += 32) s_mu[i] = i + mu_off < H * d ? __ldcg(pb.mu + i + mu_off) : 0.f;
         if (lane < d) s_sig[lane] = __ldcg(pb.sigma + lane);
         if (lane < 3 * d) s_st[lane] = state[lane];
         if (lane < 7) s_goal[lane] = goal[lane];
@@ -248,7 +249,12 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         for (int i = lane; i < H * pb.nk; i += 32) s_basis[i] = pb.basis[i];
     };
     auto stage_inputs_async = [&]() {  // the same copies, in flight while the noise is drawn
-        for (int i = lane; i < H * d; i += 32) cp_async4(s_mu + i, pb.mu + i);
+        for (int i = lane; i < H * d; i += 32) {
+            if (i + mu_off < H * d)
+                cp_async4(s_mu + i, pb.mu + i + mu_off);
+            else
+                s_mu[i] = 0.f;
+        }
         if (lane < d) cp_async4(s_sig + lane, pb.sigma + lane);
         if (lane < 3 * d) cp_async4(s_st + lane, state + lane);
         if (lane < 7) cp_async4(s_goal + lane, goal + lane);

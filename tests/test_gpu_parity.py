@@ -189,6 +189,25 @@ def test_update_far_from_old_mean(case):
     assert np.abs(sig - osig).max() <= bound, (sig, osig, bound)
 
 
+def test_degenerate_step_keeps_the_shifted_mean():
+    """Alg. 1's shift is folded into the first iteration of a step; an iteration with
+    no finite total (a NaN sigma, no null particles) still leaves the shifted mean
+    (rows h + 1, the last row zero) and commands its first row."""
+    wl = W.config_paper(0)
+    p = wl.params.replace(N=64, n_null=0, K=1)
+    st, gl = f32(wl.state), f32(wl.goal)
+    with _ctl(wl, p) as ctl:
+        ctl.step(st, gl)
+        mu1, _ = ctl.get_distribution()
+        ctl.set_distribution(mu1, np.full(7, np.nan, np.float32))
+        cmd, info, rc = ctl.step(st, gl)
+        mu2, _ = ctl.get_distribution()
+    assert rc == 1 and info["status"] == 1
+    shifted = np.vstack([mu1[1:], np.zeros((1, 7), np.float32)])
+    assert np.array_equal(mu2, shifted)
+    assert np.array_equal(cmd, shifted[0])
+
+
 def test_update_zero_temperature_and_ties():
     C = np.full(50, 9.0)
     C[[7, 30]] = 2.0  # tie: lowest index wins
