@@ -129,6 +129,21 @@ __device__ __forceinline__ float ball_depth(const float* __restrict__ fr, int la
     return depth;
 }
 
+// The exact sphere tests of one frame against one box / obstacle sphere, out of
+// line: the broad phase calls them only where a link bound meets the obstacle, so
+// one shared copy keeps the per-frame call sites small.
+__device__ __noinline__ float box_depth_cold(const float* __restrict__ fr, int lane, const float4* __restrict__ sph,
+                                             int s0, int s1, const float* __restrict__ box, float depth)
+{
+    return box_depth(fr, lane, sph, s0, s1, box, depth);
+}
+
+__device__ __noinline__ float ball_depth_cold(const float* __restrict__ fr, int lane, const float4* __restrict__ sph,
+                                              int s0, int s1, float4 w, float depth)
+{
+    return ball_depth(fr, lane, sph, s0, s1, w, depth);
+}
+
 // World collision without the broad phase: every sphere of every frame against
 // every obstacle (the same tests in the same order as the inline form).  Out of
 // line, so that this cold path does not sit in the hot instruction stream.
@@ -627,8 +642,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                                     const float ey = cby[f] - fminf(fmaxf(cby[f], loy), hiy);
                                     const float ez = cbz[f] - fminf(fmaxf(cbz[f], loz), hiz);
                                     if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < lbf[f].w * lbf[f].w)
-                                        dworld = box_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
-                                                           box, dworld);
+                                        dworld = box_depth_cold(s_fr + f * 12 * 32, lane, pb.sph, first[f],
+                                                                first[f + 1], box, dworld);
                                 }
                             }
                         } else {
@@ -639,8 +654,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                                     const float ex = cbx[f] - w.x, ey = cby[f] - w.y, ez = cbz[f] - w.z;
                                     const float rb = lbf[f].w + w.w;
                                     if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rb * rb)
-                                        dworld = ball_depth(s_fr + f * 12 * 32, lane, pb.sph, first[f], first[f + 1],
-                                                            w, dworld);
+                                        dworld = ball_depth_cold(s_fr + f * 12 * 32, lane, pb.sph, first[f],
+                                                                 first[f + 1], w, dworld);
                                 }
                             }
                         }
