@@ -11,6 +11,7 @@
 
 struct AdjointLayout {
     int frame, cent, sph, wsph, boxlh, pblk, keyw, keys;                 // 16/8-byte arrays
+    int lb, lcent, mask;                                                 // broad phase
     int mu, sigma, eps, u, th, thd, basis, dt, gpow, vmax, dhx, qlo, qhi;  // float arrays
     int boxes, cost, goal, state, gth, gthd, gu, gup;
     int first, slink, pairs;
@@ -30,6 +31,9 @@ __host__ __device__ inline AdjointLayout adjoint_layout(const Problem& pb)
     L.pblk = take_(off, pb.NPB * 16);
     L.keyw = take_(off, I * 8);
     L.keys = take_(off, I * 8);
+    L.lb = take_(off, (pb.d + 1) * 16);         // link bounding spheres (local centre, radius)
+    L.lcent = take_(off, I * (pb.d + 1) * 16);  // their centres per step
+    L.mask = take_(off, I * (pb.d + 1) * 16);   // per (step, frame): boxes, obstacle spheres met
     L.mu = take_(off, pb.H * pb.d * 4);
     L.sigma = take_(off, pb.d * 4);
     L.eps = take_(off, pb.S * pb.d * 4);
@@ -100,6 +104,9 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     uint4* s_pblk = reinterpret_cast<uint4*>(smem + L.pblk);
     unsigned long long* s_keyw = reinterpret_cast<unsigned long long*>(smem + L.keyw);
     unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(smem + L.keys);
+    float4* s_lb = reinterpret_cast<float4*>(smem + L.lb);
+    float4* s_lcent = reinterpret_cast<float4*>(smem + L.lcent);
+    unsigned long long* s_mask = reinterpret_cast<unsigned long long*>(smem + L.mask);
     float* s_mu = reinterpret_cast<float*>(smem + L.mu);
     float* s_sigma = reinterpret_cast<float*>(smem + L.sigma);
     float* s_eps = reinterpret_cast<float*>(smem + L.eps);
@@ -150,6 +157,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         for (int i = tid; i < H * S; i += nt) s_basis[i] = pb.basis[i];
     for (int i = tid; i < d * 8; i += nt) s_dhx[i] = pb.dhx[i];
     for (int i = tid; i < d + 2; i += nt) s_first[i] = pb.link_first[i];
+    for (int i = tid; i < F; i += nt) s_lb[i] = pb.lbound[i];
     for (int i = tid; i < M; i += nt) {
         s_sph[i] = pb.sph[i];
         int f = 0;
@@ -448,6 +456,43 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     }
     __syncthreads();
 
+    // ---- broad phase (as in the rollout kernels): each step's link-bound centres
+    // and, per (step, frame), the boxes and obstacle spheres its bound meets.  A
+    // sphere can only touch what its link's bound touches, so the exact tests
+    // below skip nothing that penetrates: the same depths and minimisers.
+    const bool bp = pb.broadphase != 0;
+    const unsigned long long all_b = pb.B >= 64 ? ~0ull : (1ull << pb.B) - 1ull;
+    const unsigned long long all_o = pb.O >= 64 ? ~0ull : (1ull << pb.O) - 1ull;
+    if (bp) {
+        for (int idx = tid; idx < I * F; idx += nt) {
+            const int item = idx / F, f = idx - item * F;
+            const float4 q = s_lb[f];
+            const float4* T = s_frame + (item * F + f) * 3;
+            const float4 r0 = T[0], r1 = T[1], r2 = T[2];
+            const float cx = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
+            const float cy = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
+            const float cz = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
+            s_lcent[idx] = make_float4(cx, cy, cz, q.w);
+            unsigned long long mb = 0ull, mo = 0ull;
+            for (int b = 0; b < pb.B; ++b) {
+                const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
+                const float ex = cx - fminf(fmaxf(cx, lo.x), hi.x);
+                const float ey = cy - fminf(fmaxf(cy, lo.y), hi.y);
+                const float ez = cz - fminf(fmaxf(cz, lo.z), hi.z);
+                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < q.w * q.w) mb |= 1ull << b;
+            }
+            for (int k = 0; k < pb.O; ++k) {
+                const float4 w = s_wsph[k];
+                const float ex = cx - w.x, ey = cy - w.y, ez = cz - w.z;
+                const float rb = q.w + w.w;
+                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rb * rb) mo |= 1ull << k;
+            }
+            s_mask[2 * idx] = mb;
+            s_mask[2 * idx + 1] = mo;
+        }
+        __syncthreads();
+    }
+
     // ---- sphere centres; world collision with its minimiser (sphere, obstacle)
     for (int idx = tid; idx < I * M; idx += nt) {
         const int item = idx / M, s = idx - item * M;
@@ -462,7 +507,14 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         s_cent[idx] = c;
         float depth = 0.f;
         int best = -1;
-        for (int b = 0; b < pb.B; ++b) {
+        unsigned long long mb = all_b, mo = all_o;
+        if (bp) {
+            mb = s_mask[2 * (item * F + s_slink[s])];
+            mo = s_mask[2 * (item * F + s_slink[s]) + 1];
+        }
+        while (mb) {  // ascending obstacle index, as the plain loop
+            const int b = __ffsll(static_cast<long long>(mb)) - 1;
+            mb &= mb - 1ull;
             const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
             const float ex = c.x - fminf(fmaxf(c.x, lo.x), hi.x);
             const float ey = c.y - fminf(fmaxf(c.y, lo.y), hi.y);
@@ -480,7 +532,9 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                 }
             }
         }
-        for (int k = 0; k < pb.O; ++k) {
+        while (mo) {
+            const int k = __ffsll(static_cast<long long>(mo)) - 1;
+            mo &= mo - 1ull;
             const float4 w = s_wsph[k];
             const float ex = c.x - w.x, ey = c.y - w.y, ez = c.z - w.z;
             const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
@@ -498,6 +552,12 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     for (int idx = tid; idx < I * pb.NPB; idx += nt) {
         const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
         const uint4 blk = s_pblk[bk];
+        if (bp) {  // the two links' bounds apart: no pair of the block touches
+            const float4 A = s_lcent[item * F + s_slink[blk.x]], B2 = s_lcent[item * F + s_slink[blk.z]];
+            const float ex = A.x - B2.x, ey = A.y - B2.y, ez = A.z - B2.z;
+            const float rr = A.w + B2.w;
+            if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rr * rr) continue;
+        }
         const float4* ci = s_cent + item * M;
         float depth = 0.f;
         int best = -1;

@@ -44,6 +44,31 @@ def test_cost_grad_matches_oracle(name, N, kw):
     assert max_rel(g, og, scale) < 1e-4, max_rel(g, og, scale)
 
 
+@pytest.mark.parametrize("world", [(20, 10), (64, 64)])
+def test_cost_grad_broadphase_is_exact(world):
+    """The adjoint's collision broad phase (link bounds against obstacles and
+    against each other) skips only tests that cannot penetrate: the gradient, J
+    and every particle's total are bitwise those of the brute-force tests, on
+    the paper world and on a dense one."""
+    wl = W.config_paper(4)
+    wl.world = W.make_world(4, *world)
+    p = wl.params.replace(N=96)
+    mu, sig = f32(W.make_mean(4, p.H, 7, 0.8)), f32(W.make_sigma(4, 7))
+    state, goal = cuda(f32(W.make_state(34, 7))), cuda(f32(wl.goal))
+    out = []
+    for bp in (True, False):
+        with Controller(wl.robot, wl.world, p) as ctl:
+            ctl.set_broadphase(bp)
+            ctl.set_distribution(mu, sig)
+            J, g, Cn = ctl.cost_grad(cuda(mu), state, goal, 5, 2, want_C=True)
+            torch.cuda.synchronize()
+            out.append((host(J), host(g), host(Cn)))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    # the case has world and self contacts (some totals carry collision cost)
+    assert (out[0][2] > 100.0).any()
+
+
 def test_autograd_function_matches_adjoint():
     wl = W.config_paper(3)
     p = wl.params.replace(N=128)
