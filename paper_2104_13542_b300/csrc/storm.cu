@@ -1273,7 +1273,7 @@ k_rollout_warp_batch(const BatchInstance* __restrict__ insts, const int2* __rest
             loaded = task.x;
         }
         const RolloutOut out{I.u, nullptr, nullptr, nullptr, nullptr, nullptr, I.C};
-        rollout_warp_body<1>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
+        rollout_warp_body<1, true>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
                                  wsm + size_t(warp) * warp_floats);
         __syncwarp();
     }
@@ -1847,15 +1847,17 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
     if (exact_self) pb.self_pred = nullptr;
     pb.dep_launch = dep ? 1 : 0;
     pb.shift_view = shift ? 1 : 0;
+    const bool ee = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms;  // the variant with those terms
+    const StepState* st = h->d_st;
     if (h->mapping == STORM_MAP_WARP)
-        CK(launch_kernel(k_rollout_warp<1>, h->warp_grid, h->wpc * 32, h->warp_smem, s, dep, pb, out, state,
-                         goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
+        CK(launch_kernel(ee ? k_rollout_warp<1, true> : k_rollout_warp<1, false>, h->warp_grid, h->wpc * 32,
+                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
     else if (h->mapping == STORM_MAP_WARP_PAIR)
-        CK(launch_kernel(k_rollout_warp<2>, h->warp_grid, h->wpc * 64, h->warp_smem, s, dep, pb, out, state,
-                         goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
+        CK(launch_kernel(ee ? k_rollout_warp<2, true> : k_rollout_warp<2, false>, h->warp_grid, h->wpc * 64,
+                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
     else if (h->mapping == STORM_MAP_WARP_QUAD)
-        CK(launch_kernel(k_rollout_warp<4>, h->warp_grid, h->wpc * 128, h->warp_smem, s, dep, pb, out, state,
-                         goal, static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
+        CK(launch_kernel(ee ? k_rollout_warp<4, true> : k_rollout_warp<4, false>, h->warp_grid, h->wpc * 128,
+                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
     else
         CK(launch_kernel(k_rollout, h->grid, h->threads, h->rollout_smem, s, dep, pb, out, state, goal,
                          static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
@@ -1925,15 +1927,14 @@ int allow_smem(storm_handle* h)
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     cudaFuncAttributes ra, ua, aa, wa;
     CK(cudaFuncGetAttributes(&ra, k_rollout));
-    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<1>));
-    CK(cudaFuncSetAttribute(k_rollout_warp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            optin - static_cast<int>(wa.sharedSizeBytes)));
-    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<2>));
-    CK(cudaFuncSetAttribute(k_rollout_warp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            optin - static_cast<int>(wa.sharedSizeBytes)));
-    CK(cudaFuncGetAttributes(&wa, k_rollout_warp<4>));
-    CK(cudaFuncSetAttribute(k_rollout_warp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            optin - static_cast<int>(wa.sharedSizeBytes)));
+    using WarpKernel = void (*)(Problem, RolloutOut, const float*, const float*, const StepState*, int, int, int);
+    const WarpKernel warp_kernels[] = {k_rollout_warp<1, false>, k_rollout_warp<1, true>, k_rollout_warp<2, false>,
+                                       k_rollout_warp<2, true>,  k_rollout_warp<4, false>, k_rollout_warp<4, true>};
+    for (WarpKernel kf : warp_kernels) {
+        CK(cudaFuncGetAttributes(&wa, kf));
+        CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - static_cast<int>(wa.sharedSizeBytes)));
+    }
     CK(cudaFuncGetAttributes(&ua, k_update));
     CK(cudaFuncGetAttributes(&aa, k_adjoint));
     if (h->rollout_smem + ra.sharedSizeBytes > size_t(optin) ||

@@ -161,30 +161,6 @@ __device__ __noinline__ float world_brute_force(const float* __restrict__ s_fr, 
     return dworld;
 }
 
-// The end-effector speed / acceleration limit terms of one item (Eq. 8), out of
-// line so that this path stays out of the hot instruction stream when the terms
-// are off.  The joint axes and origins (and the end-effector point) are read back
-// from this warp's frames, which hold the very values of the FK registers.
-__device__ __noinline__ float2 ee_terms_from_frames(const float* __restrict__ s_fr, int lane, int d,
-                                                    const float* thd, const float* thdd, float vmax, float amax)
-{
-    float z[kMaxDof][3], o[kMaxDof][3], p[3];
-#pragma unroll
-    for (int i = 0; i < kMaxDof; ++i) {
-        const float* fr = s_fr + (i + 1) * 12 * 32 + lane;
-        const bool in = i < d;
-        z[i][0] = in ? fr[2 * 32] : 0.f, z[i][1] = in ? fr[6 * 32] : 0.f, z[i][2] = in ? fr[10 * 32] : 0.f;
-        o[i][0] = in ? fr[3 * 32] : 0.f, o[i][1] = in ? fr[7 * 32] : 0.f, o[i][2] = in ? fr[11 * 32] : 0.f;
-    }
-    const float* fe = s_fr + d * 12 * 32 + lane;
-    p[0] = fe[3 * 32], p[1] = fe[7 * 32], p[2] = fe[11 * 32];
-    float xd[6], xdd[6];
-    ee_twist(z, o, p, thd, thdd, d, xd, xdd);
-    const float sp = sqrtf(fmaf(xd[0], xd[0], fmaf(xd[1], xd[1], xd[2] * xd[2])));
-    const float ac = sqrtf(fmaf(xdd[0], xdd[0], fmaf(xdd[1], xdd[1], xdd[2] * xdd[2])));
-    return make_float2(fmaxf(0.f, sp - vmax), fmaxf(0.f, ac - amax));
-}
-
 // The ball along one particle's horizon (initial state from the current pose, then
 // the scan), out of line: only ball-balancing problems take it.
 __device__ __noinline__ void ball_tail(const float* dhx, int d, const float* state, const float* ball, int H,
@@ -211,8 +187,9 @@ __device__ __forceinline__ void unit_sync(int unit, int threads)
 
 // The rollout of particle group `wg` (particles wg*PW ..) of problem pb by
 // this warp (or the kW warps of group `unit`), in the group's shared-memory
-// region ws.
-template <int kW>
+// region ws.  kEE: the end-effector limit terms are compiled in (a problem
+// without them runs the kernel without that code in its instruction stream).
+template <int kW, bool kEE>
 __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state, const float* __restrict__ goal,
                                                   uint32_t step, int iter, int front_only, int wg, int unit, float* ws)
@@ -423,7 +400,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         g[11] = goal[2];
     }
     const bool want_manip = pb.w_manip != 0.f || out.terms;
-    const bool want_ee = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms;
+    const bool want_ee = kEE && (pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms);
     const bool ball_on = pb.ball && pb.w_ball != 0.f;
     float* s_ba = ws + W.ba;
     const float* pred = pb.self_pred;
@@ -544,7 +521,12 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                pb.w_smooth * c_smooth;
         float2 c_ee = make_float2(0.f, 0.f);
         if (want_ee) {  // task-space limits on X_dot, X_ddot (Eq. 8), theta_ddot = u
-            c_ee = ee_terms_from_frames(s_fr, lane, d, thd, uh, pb.ee_vel_max, pb.ee_acc_max);
+            float zc[kMaxDof][3];
+#pragma unroll
+            for (int i = 0; i < kMaxDof; ++i) zc[i][0] = J[3][i], zc[i][1] = J[4][i], zc[i][2] = J[5][i];
+            float xd[6], xdd[6];
+            ee_twist(zc, oc, pp, thd, uh, d, xd, xdd);
+            c_ee = ee_limit_terms(pb, xd, xdd);
             if (pb.w_ee_vel != 0.f) part = fmaf(pb.w_ee_vel, c_ee.x, part);
             if (pb.w_ee_acc != 0.f) part = fmaf(pb.w_ee_acc, c_ee.y, part);
         }
@@ -835,7 +817,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     trace_stamp(pb.trace, 6);
 }
 
-template <int kW>
+template <int kW, bool kEE>
 __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
 k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
                const StepState* __restrict__ st, int step_override, int iter, int front_only)
@@ -847,6 +829,6 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
     const int units = (blockDim.x >> 5) / kW;
     pdl_trigger();
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
-    rollout_warp_body<kW>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
+    rollout_warp_body<kW, kEE>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
                              wsm + unit * W.floats);
 }
