@@ -187,9 +187,11 @@ __device__ __forceinline__ void unit_sync(int unit, int threads)
 
 // The rollout of particle group `wg` (particles wg*PW ..) of problem pb by
 // this warp (or the kW warps of group `unit`), in the group's shared-memory
-// region ws.  kEE: the end-effector limit terms are compiled in (a problem
-// without them runs the kernel without that code in its instruction stream).
-template <int kW, bool kEE>
+// region ws.  kFull: the end-effector limit terms, the ball and the per-item
+// outputs of the single-stage calls are compiled in; the step graph of a problem
+// without them runs the lean instantiation, without that code in its
+// instruction stream.
+template <int kW, bool kFull>
 __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state, const float* __restrict__ goal,
                                                   uint32_t step, int iter, int front_only, int wg, int unit, float* ws)
@@ -366,9 +368,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     }
     __syncwarp();
     trace_stamp(pb.trace, 2);
-    if (out.theta)
+    if (kFull && out.theta)
         for (int i = lane; i < np_w * HD; i += 32) out.theta[static_cast<size_t>(nw0) * HD + i] = s_th[i];
-    if (out.theta_dot)
+    if (kFull && out.theta_dot)
         for (int i = lane; i < np_w * HD; i += 32) out.theta_dot[static_cast<size_t>(nw0) * HD + i] = s_thd[i];
     }
     if (kW > 1) unit_sync(unit, kW * 32);  // the other warps read the controls and joint states
@@ -399,9 +401,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         g[10] = goal[1];
         g[11] = goal[2];
     }
-    const bool want_manip = pb.w_manip != 0.f || out.terms;
-    const bool want_ee = kEE && (pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms);
-    const bool ball_on = pb.ball && pb.w_ball != 0.f;
+    const bool want_manip = pb.w_manip != 0.f || (kFull && out.terms);
+    const bool want_ee = kFull && (pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms);
+    const bool ball_on = kFull && pb.ball && pb.w_ball != 0.f;
     float* s_ba = ws + W.ba;
     const float* pred = pb.self_pred;
     const int NO = pb.B + pb.O;
@@ -535,7 +537,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             s_ba[(pl * H + h) * 2] = a.x;
             s_ba[(pl * H + h) * 2 + 1] = a.y;
         }
-        if (valid && out.ee) {
+        if (kFull && valid && out.ee) {
             float* e = out.ee + gi * 12;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -545,7 +547,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                 e[r * 4 + 3] = pp[r];
             }
         }
-        if (valid && out.terms) {
+        if (kFull && valid && out.terms) {
             float* t = out.terms + gi * STORM_NTERMS;
             t[0] = c_pos;
             t[1] = c_rot;
@@ -563,7 +565,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             const float m = manipulability_mgs(J, d);
             c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
             if (kW <= 2) part += pb.w_manip * c_manip;  // the quad's A adds it at the hand-off
-            if (valid && out.terms) out.terms[gi * STORM_NTERMS + 4] = c_manip;
+            if (kFull && valid && out.terms) out.terms[gi * STORM_NTERMS + 4] = c_manip;
         }
         __syncwarp();
         trace_stamp(pb.trace, 3);
@@ -785,7 +787,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             const float c = part + pb.w_coll * (dself + dworld);
             if (valid) {
                 s_c[pl * H + h] = c;
-                if (out.terms) {
+                if (kFull && out.terms) {
                     out.terms[gi * STORM_NTERMS + 5] = dself;
                     out.terms[gi * STORM_NTERMS + 6] = dworld;
                 }
@@ -802,7 +804,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         }
         __syncwarp();
     }
-    if (out.cost)
+    if (kFull && out.cost)
         for (int slot = 0; slot < W.SL; ++slot) {
             const int h = slot * Lp + hl;
             if (pvalid && h < H) out.cost[static_cast<size_t>(n) * H + h] = s_c[seg * H + h];
@@ -817,7 +819,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     trace_stamp(pb.trace, 6);
 }
 
-template <int kW, bool kEE>
+template <int kW, bool kFull>
 __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
 k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
                const StepState* __restrict__ st, int step_override, int iter, int front_only)
@@ -829,6 +831,6 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
     const int units = (blockDim.x >> 5) / kW;
     pdl_trigger();
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
-    rollout_warp_body<kW, kEE>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
+    rollout_warp_body<kW, kFull>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
                              wsm + unit * W.floats);
 }
