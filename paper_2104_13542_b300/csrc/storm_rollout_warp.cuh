@@ -187,10 +187,11 @@ __device__ __forceinline__ void unit_sync(int unit, int threads)
 
 // The rollout of particle group `wg` (particles wg*PW ..) of problem pb by
 // this warp (or the kW warps of group `unit`), in the group's shared-memory
-// region ws.  kFull: the end-effector limit terms, the ball and the per-item
-// outputs of the single-stage calls are compiled in; the step graph of a problem
-// without them runs the lean instantiation, without that code in its
-// instruction stream.
+// region ws.  kFull: the end-effector limit terms, the ball, the comb / mixed
+// filters, the Frobenius rotation cost and the per-item outputs of the
+// single-stage calls are compiled in; a problem without them (the default
+// filter, the quaternion rotation cost) runs the lean instantiation, without
+// that code in its instruction stream.
 template <int kW, bool kFull>
 __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state, const float* __restrict__ goal,
@@ -293,7 +294,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         for (int i = lane; i < np_w * per; i += 32) s_eps[i] = pb.halton[static_cast<size_t>(nw0) * per + i];
     }
     __syncwarp();
-    if (pb.filter != STORM_FILTER_DEFAULT) {  // comb-filtered particles, one sample per step (S = H)
+    if (kFull && pb.filter != STORM_FILTER_DEFAULT) {  // comb-filtered particles, one sample per step (S = H)
         if (lane < np_w * d) {
             const int p = lane / d, j = lane - p * d;
             if (smoothing_of(pb, nw0 + p) == 2) comb_column(s_eps + p * S * d + j, H, d, pb.comb);
@@ -487,7 +488,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         }
         c_pos = sqrtf(c_pos);
         float c_rot = 0.f;
-        if (pb.rot_mode == STORM_ROT_QUAT) {
+        if (!kFull || pb.rot_mode == STORM_ROT_QUAT) {
             float tr = 0.f;
 #pragma unroll
             for (int k = 0; k < 9; ++k) tr = fmaf(g[k], R[k], tr);
