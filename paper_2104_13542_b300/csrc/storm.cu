@@ -1848,18 +1848,19 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
     pb.dep_launch = dep ? 1 : 0;
     pb.shift_view = shift ? 1 : 0;
     // the full instantiation where the problem or the call needs its extra code
-    const bool ee = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || (pb.ball && pb.w_ball != 0.f) ||
-                    pb.filter != STORM_FILTER_DEFAULT || pb.rot_mode != STORM_ROT_QUAT || out.theta || out.theta_dot ||
-                    out.ee || out.terms || out.cost;
+    const bool full = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || (pb.ball && pb.w_ball != 0.f) ||
+                    pb.filter != STORM_FILTER_DEFAULT || pb.rot_mode != STORM_ROT_QUAT ||
+                    pb.sampler != STORM_SAMPLER_PHILOX || pb.self_pred || out.theta || out.theta_dot || out.ee ||
+                    out.terms || out.cost;
     const StepState* st = h->d_st;
     if (h->mapping == STORM_MAP_WARP)
-        CK(launch_kernel(ee ? k_rollout_warp<1, true> : k_rollout_warp<1, false>, h->warp_grid, h->wpc * 32,
+        CK(launch_kernel(full ? k_rollout_warp<1, true> : k_rollout_warp<1, false>, h->warp_grid, h->wpc * 32,
                          h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
     else if (h->mapping == STORM_MAP_WARP_PAIR)
-        CK(launch_kernel(ee ? k_rollout_warp<2, true> : k_rollout_warp<2, false>, h->warp_grid, h->wpc * 64,
+        CK(launch_kernel(full ? k_rollout_warp<2, true> : k_rollout_warp<2, false>, h->warp_grid, h->wpc * 64,
                          h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
     else if (h->mapping == STORM_MAP_WARP_QUAD)
-        CK(launch_kernel(ee ? k_rollout_warp<4, true> : k_rollout_warp<4, false>, h->warp_grid, h->wpc * 128,
+        CK(launch_kernel(full ? k_rollout_warp<4, true> : k_rollout_warp<4, false>, h->warp_grid, h->wpc * 128,
                          h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
     else
         CK(launch_kernel(k_rollout, h->grid, h->threads, h->rollout_smem, s, dep, pb, out, state, goal,

@@ -188,10 +188,11 @@ __device__ __forceinline__ void unit_sync(int unit, int threads)
 // The rollout of particle group `wg` (particles wg*PW ..) of problem pb by
 // this warp (or the kW warps of group `unit`), in the group's shared-memory
 // region ws.  kFull: the end-effector limit terms, the ball, the comb / mixed
-// filters, the Frobenius rotation cost and the per-item outputs of the
-// single-stage calls are compiled in; a problem without them (the default
-// filter, the quaternion rotation cost) runs the lean instantiation, without
-// that code in its instruction stream.
+// filters, the Halton sampler, the Frobenius rotation cost, the surrogate
+// self-collision network and the per-item outputs of the single-stage calls are
+// compiled in; a problem without them (Philox noise, the default filter, the
+// quaternion rotation cost, exact self collision) runs the lean instantiation,
+// without that code in its instruction stream.
 template <int kW, bool kFull>
 __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state, const float* __restrict__ goal,
@@ -274,7 +275,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
 
     // ---- noise eps[n][s][j] of the warp's particles
     const int per = S * d;
-    if (pb.sampler == STORM_SAMPLER_PHILOX) {
+    if (!kFull || pb.sampler == STORM_SAMPLER_PHILOX) {
         const uint32_t e0 = static_cast<uint32_t>(nw0) * per;
         const uint32_t e1 = static_cast<uint32_t>(nw0 + np_w) * per;
         const uint32_t b0 = e0 >> 2, b1 = (e1 + 3) >> 2;
@@ -406,7 +407,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     const bool want_ee = kFull && (pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms);
     const bool ball_on = kFull && pb.ball && pb.w_ball != 0.f;
     float* s_ba = ws + W.ba;
-    const float* pred = pb.self_pred;
+    const float* pred = kFull ? pb.self_pred : nullptr;
     const int NO = pb.B + pb.O;
 
     for (int slot = 0; slot < W.SL; ++slot) {
