@@ -1250,7 +1250,9 @@ k_rollout_batch(const BatchInstance* __restrict__ insts, const BatchTile* __rest
 // Rollout of every instance on the warp mapping: each warp takes (instance,
 // particle group) tasks from the list (sorted by decreasing work), copies the
 // instance's Problem into its own shared slot and runs the single-handle warp
-// body, so each instance's results are bitwise those of its own handle.
+// body, so each instance's results are bitwise those of its own handle
+// (kFull: the full instantiation, where an instance needs it).
+template <bool kFull>
 __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
 k_rollout_warp_batch(const BatchInstance* __restrict__ insts, const int2* __restrict__ tasks, int n_tasks,
                      int iter, int warp_floats)
@@ -1273,7 +1275,7 @@ k_rollout_warp_batch(const BatchInstance* __restrict__ insts, const int2* __rest
             loaded = task.x;
         }
         const RolloutOut out{I.u, nullptr, nullptr, nullptr, nullptr, nullptr, I.C};
-        rollout_warp_body<1, true>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
+        rollout_warp_body<1, kFull>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
                                  wsm + size_t(warp) * warp_floats);
         __syncwarp();
     }
@@ -1810,6 +1812,14 @@ int upload_world(storm_handle* h, const storm_world* w)
     return STORM_OK;
 }
 
+// A problem the lean warp rollout does not cover (see rollout_warp_body).
+bool needs_full_rollout(const Problem& pb)
+{
+    return pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || (pb.ball && pb.w_ball != 0.f) ||
+           pb.filter != STORM_FILTER_DEFAULT || pb.rot_mode != STORM_ROT_QUAT || pb.sampler != STORM_SAMPLER_PHILOX ||
+           pb.self_pred != nullptr;
+}
+
 // Warps per particle group of a warp mapping.
 int warps_per_group(int mapping)
 {
@@ -1848,10 +1858,7 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
     pb.dep_launch = dep ? 1 : 0;
     pb.shift_view = shift ? 1 : 0;
     // the full instantiation where the problem or the call needs its extra code
-    const bool full = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || (pb.ball && pb.w_ball != 0.f) ||
-                    pb.filter != STORM_FILTER_DEFAULT || pb.rot_mode != STORM_ROT_QUAT ||
-                    pb.sampler != STORM_SAMPLER_PHILOX || pb.self_pred || out.theta || out.theta_dot || out.ee ||
-                    out.terms || out.cost;
+    const bool full = needs_full_rollout(pb) || out.theta || out.theta_dot || out.ee || out.terms || out.cost;
     const StepState* st = h->d_st;
     if (h->mapping == STORM_MAP_WARP)
         CK(launch_kernel(full ? k_rollout_warp<1, true> : k_rollout_warp<1, false>, h->warp_grid, h->wpc * 32,
@@ -3013,6 +3020,7 @@ struct storm_batch {
     int n = 0, Kmax = 1;
     int threads = kThreads, items = 64;
     int mapping = STORM_MAP_WARP;  // rollout work mapping (CTA tiles or warp tasks)
+    bool full = false;             // an instance needs the full warp rollout (see rollout_warp_body)
     int wpc = 4;                   // warps per CTA of the warp mapping
     std::vector<BatchInstance> inst;  // host mirror of d_inst
     std::vector<int> dof, state_off, cmd_off;
@@ -3135,16 +3143,17 @@ int batch_apply_launch_warp(storm_batch* b, int wpc)
     int optin = 0, sms = 0;
     BK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
     BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    const auto kernel = b->full ? k_rollout_warp_batch<true> : k_rollout_warp_batch<false>;
     cudaFuncAttributes fa;
-    BK(cudaFuncGetAttributes(&fa, k_rollout_warp_batch));
+    BK(cudaFuncGetAttributes(&fa, kernel));
     if (smem + fa.sharedSizeBytes > size_t(optin)) {
         b->err = "warp shape needs too much shared memory";
         return STORM_ERR_INVALID_ARG;
     }
-    BK(cudaFuncSetAttribute(k_rollout_warp_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    BK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             optin - static_cast<int>(fa.sharedSizeBytes)));
     int per_sm = 0;
-    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rollout_warp_batch, wpc * 32, smem));
+    BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, wpc * 32, smem));
     if (per_sm < 1) {
         b->err = "warp shape does not fit an SM";
         return STORM_ERR_INVALID_ARG;
@@ -3168,9 +3177,12 @@ int batch_apply_launch_warp(storm_batch* b, int wpc)
 
 cudaError_t batch_launch_rollout(storm_batch* b, cudaStream_t s, int iter)
 {
-    if (b->mapping == STORM_MAP_WARP)
-        k_rollout_warp_batch<<<b->grid, b->wpc * 32, b->rollout_smem, s>>>(b->d_inst, b->d_tasks, b->n_tasks,
-                                                                           iter, b->warp_floats);
+    if (b->mapping == STORM_MAP_WARP && b->full)
+        k_rollout_warp_batch<true><<<b->grid, b->wpc * 32, b->rollout_smem, s>>>(b->d_inst, b->d_tasks, b->n_tasks,
+                                                                                 iter, b->warp_floats);
+    else if (b->mapping == STORM_MAP_WARP)
+        k_rollout_warp_batch<false><<<b->grid, b->wpc * 32, b->rollout_smem, s>>>(b->d_inst, b->d_tasks,
+                                                                                  b->n_tasks, iter, b->warp_floats);
     else
         k_rollout_batch<<<b->grid, b->threads, b->rollout_smem, s>>>(b->d_inst, b->d_tiles, b->n_tiles, iter);
     return cudaGetLastError();
@@ -3261,6 +3273,7 @@ int batch_create_impl(storm_batch* b, int n, const storm_robot* r, const storm_w
         BatchInstance& I = b->inst[i];
         I = BatchInstance{};
         fill_problem(r + i, w + i, p + i, I.pb, ht[i]);
+        b->full = b->full || needs_full_rollout(I.pb);
         I.K = p[i].K;
         b->Kmax = std::max(b->Kmax, I.K);
         b->dof.push_back(r[i].dof);
