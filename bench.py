@@ -9,10 +9,14 @@ spheres against 20 boxes + 10 spheres.  Synthetic, seeded inputs (no dataset).
 One JSON line on rank 0:
   value  rollout-steps/s (N * H * K per control step / device time per step),
          inputs resident in HBM, each step timed with CUDA events on the
-         controller's stream, L2 flushed (256 MB write) before every step
+         controller's stream, L2 flushed (256 MB write) before every step;
+         the inputs are the closed-loop sequence of the e2e run (the step's
+         work grows as the arm's links come close to each other)
   e2e    the same metric through the host API storm_step in a closed loop
-         (pinned H2D of state + goal, D2H of the command, host wall clock)
+         (pinned H2D of state + goal, D2H of the command, host wall clock):
+         the arm driving to five goals on an ideal double-integrator plant
   latency_ms  p50 / p99 of the device-timed step
+  latency_rest_ms  the same with the arm at rest at its start configuration
   roofline    the rollout kernel (ALU bound) against the FP32 FMA peak
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
 
@@ -220,78 +224,21 @@ def run_gpu(args, rank, world_size):
         ctl.set_dependent_launch(True)
     ctl.reset()
 
-    # ---------------- device-resident timing (value)
-    s_ptr, g_ptr, _ = ctl.device_io_ptrs()
-    import ctypes
-    st_host = np.ascontiguousarray(state0, dtype=np.float32)
-    torch.cuda.synchronize()
-    st_dev = torch.as_tensor(st_host, device="cuda").reshape(-1)
-    gl_dev = torch.as_tensor(goals[0], device="cuda")
-    cmd_dev = torch.zeros(wl.robot.dof, device="cuda")
-    # place the inputs in the handle's own buffers once (resident)
-    ctl.step_async(st_dev, gl_dev, cmd_dev)
-    ctl.sync()
-    for _ in range(args.warmup):
-        ctl.step_resident()
-    ctl.sync()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    if world_size > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            with torch.cuda.stream(ctl.stream):
-                flush.fill_(float(i))
-            ev[i][0].record(ctl.stream)
-            ctl.step_resident()
-            ev[i][1].record(ctl.stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    ms = np.array([a.elapsed_time(b) for a, b in ev])
-    dev_time_s = max_over_ranks(float(ms.sum() / 1e3), world_size)
-    clocks = clk.summary()
-
-    # ---------------- rollout-kernel roofline: kernel time from the step's share
-    # (the rollout kernel alone, timed with events on the controller's stream)
-    from paper_2104_13542_b300.binding import lib
-    st_d = torch.as_tensor(st_host, device="cuda").reshape(-1)
-
-    def rollout_ms():
-        rk = []
-        for i in range(max(20, min(args.steps, 200))):
-            with torch.cuda.stream(ctl.stream):
-                flush.fill_(float(i))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(ctl.stream)
-            lib().storm_generate_rollouts(ctl.h, ctypes.c_void_p(st_d.data_ptr()),
-                                          ctypes.c_void_p(gl_dev.data_ptr()), 0, 0, None, None, None,
-                                          None, None, None, None)
-            b.record(ctl.stream)
-            rk.append((a, b))
-        torch.cuda.synchronize()
-        return float(np.mean([a.elapsed_time(b) for a, b in rk]))
-
-    rk_ms = rollout_ms()
-    ctl.set_broadphase(False)  # the same kernel doing every exact collision test
-    rk_bf_ms = rollout_ms()
-    ctl.set_broadphase(True)
-    flops_launch = algorithmic_flops_per_item(p, wl.robot, wl.world) * p.N * p.H
-    sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
-    peak = fp32_peak_tflops(sm_mhz)
-    achieved = flops_launch / (rk_ms * 1e-3) / 1e12
-    achieved_bf = flops_launch / (rk_bf_ms * 1e-3) / 1e12
-
     # ---------------- end-to-end closed loop through the host API (e2e)
-    ctl.reset()
+    # The arm drives to five goals in turn on an ideal double-integrator plant;
+    # every step's inputs are recorded, and the device-resident timing below
+    # replays the same sequence (the step's work depends on the configuration:
+    # the collision broad phase prunes less as links come close).
+    import ctypes
+    dof = wl.robot.dof
     state = state0.astype(np.float32).copy()
     dt = float(p.dt[0])
-    e2e_ms, pos_err = [], []
+    e2e_ms, pos_err, seq_state, seq_goal = [], [], [], []
     seg = max(1, (args.steps + args.warmup) // len(goals))
     for i in range(args.warmup + args.steps):
         goal = goals[min(i // seg, len(goals) - 1)]
+        seq_state.append(state.reshape(-1).copy())
+        seq_goal.append(np.asarray(goal, dtype=np.float32))
         with torch.cuda.stream(ctl.stream):
             flush.fill_(float(i))
         ctl.stream.synchronize()
@@ -310,11 +257,95 @@ def run_gpu(args, rank, world_size):
     e2e_ms = np.array(e2e_ms)
     e2e_time_s = max_over_ranks(float(e2e_ms.sum() / 1e3), world_size)
 
+    # ---------------- device-resident timing (value): the same input sequence,
+    # staged in HBM beforehand; before each step (outside its events) the step's
+    # state and goal are copied into the handle's own input buffers
+    s_ptr, g_ptr, _ = ctl.device_io_ptrs()
+    io_state = torch.as_tensor(_DeviceFloats(s_ptr, 3 * dof), device="cuda")
+    io_goal = torch.as_tensor(_DeviceFloats(g_ptr, 7), device="cuda")
+    seq_state_d = torch.as_tensor(np.stack(seq_state), device="cuda")
+    seq_goal_d = torch.as_tensor(np.stack(seq_goal), device="cuda")
+    ctl.reset()
+
+    def place(i):
+        with torch.cuda.stream(ctl.stream):
+            io_state.copy_(seq_state_d[i], non_blocking=True)
+            io_goal.copy_(seq_goal_d[i], non_blocking=True)
+
+    for i in range(args.warmup):
+        place(i)
+        ctl.step_resident()
+    ctl.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            with torch.cuda.stream(ctl.stream):
+                flush.fill_(float(i))
+            place(args.warmup + i)
+            ev[i][0].record(ctl.stream)
+            ctl.step_resident()
+            ev[i][1].record(ctl.stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    dev_time_s = max_over_ranks(float(ms.sum() / 1e3), world_size)
+    clocks = clk.summary()
+
+    # the arm at rest at its start configuration, the first goal, every step
+    # (the lightest collision load: for reference next to the trajectory)
+    st_dev = torch.as_tensor(np.ascontiguousarray(state0, dtype=np.float32), device="cuda").reshape(-1)
+    gl_dev = torch.as_tensor(goals[0], device="cuda")
+    ctl.reset()
+    with torch.cuda.stream(ctl.stream):
+        io_state.copy_(st_dev)
+        io_goal.copy_(gl_dev)
+    for _ in range(args.warmup):
+        ctl.step_resident()
+    ms_rest = _time_steps(ctl.step_resident, ctl.stream, flush, min(args.steps, 200))
+
+    # ---------------- rollout-kernel roofline: the rollout kernel alone, timed
+    # with events on the controller's stream, at the trajectory's states
+    from paper_2104_13542_b300.binding import lib
+    n_rk = max(20, min(args.steps, 200))
+    picks = np.linspace(args.warmup, args.warmup + args.steps - 1, n_rk).round().astype(int)
+
+    def rollout_ms():
+        rk = []
+        for j, i in enumerate(picks):
+            with torch.cuda.stream(ctl.stream):
+                flush.fill_(float(j))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctl.stream)
+            lib().storm_generate_rollouts(ctl.h, ctypes.c_void_p(seq_state_d[i].data_ptr()),
+                                          ctypes.c_void_p(seq_goal_d[i].data_ptr()), 0, 0, None, None, None,
+                                          None, None, None, None)
+            b.record(ctl.stream)
+            rk.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in rk]))
+
+    rk_ms = rollout_ms()
+    ctl.set_broadphase(False)  # the same kernel doing every exact collision test
+    rk_bf_ms = rollout_ms()
+    ctl.set_broadphase(True)
+    flops_launch = algorithmic_flops_per_item(p, wl.robot, wl.world) * p.N * p.H
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
+    peak = fp32_peak_tflops(sm_mhz)
+    achieved = flops_launch / (rk_ms * 1e-3) / 1e12
+    achieved_bf = flops_launch / (rk_bf_ms * 1e-3) / 1e12
+
     res = dict(
         value=job_throughput(units_per_step, args.steps, world_size, dev_time_s),
         ms_per_step=float(ms.mean()),
         latency_ms={"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                     "max": float(ms.max())},
+        latency_rest_ms={"p50": float(np.percentile(ms_rest, 50)), "p99": float(np.percentile(ms_rest, 99))},
         e2e={"value": job_throughput(units_per_step, args.steps, world_size, e2e_time_s), "unit": UNIT,
              "h2d_bytes_per_step": 4 * (3 * wl.robot.dof + 7),
              "d2h_bytes_per_step": 4 * wl.robot.dof + 16,
@@ -339,6 +370,15 @@ def run_gpu(args, rank, world_size):
     )
     ctl.close()
     return res, wl
+
+
+class _DeviceFloats:
+    """A float32 device buffer of the library (raw pointer), seen by torch
+    without a copy."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False),
+                                         "version": 3, "strides": None}
 
 
 def _time_steps(step_fn, stream, flush, n):
@@ -687,8 +727,11 @@ def main():
                    "boxes": int(wl.world.boxes.shape[0]),
                    "obstacle_spheres": int(wl.world.spheres.shape[0]),
                    "l2": "flushed (256 MB write) before every timed step",
+                   "inputs": "the closed-loop sequence of the e2e run (the arm driving to 5 goals), "
+                             "replayed from HBM",
                    "parallelism": f"replicas x{world_size}"},
-        "latency_ms": res["latency_ms"], "e2e": res["e2e"], "roofline": res["roofline"],
+        "latency_ms": res["latency_ms"], "latency_rest_ms": res["latency_rest_ms"],
+        "e2e": res["e2e"], "roofline": res["roofline"],
         "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
     }
     if world_size == 1 and not args.no_variants:

@@ -16,7 +16,13 @@
 // each item's work across warps.  Warp A draws the controls and integrates
 // them; then every warp of the group runs FK into its own copy of the link
 // frames.  Pair: A takes the pose, joint, end-effector and manipulability
-// terms and world collision, B self collision.  Quad: A the pose, joint and
+// terms and world collision, B self collision, and A, once its own terms are
+// done, joins in: B publishes each item's mask of overlapping frame pairs in
+// shared memory, and the pairs are claimed one at a time from a per-item
+// counter, B from the first pair, A from the last, so that every pair is
+// tested exactly once and the two warps finish together however the work
+// falls (the arm folded onto itself makes self collision several times the
+// rest of the item's work).  Quad: A the pose, joint and
 // end-effector terms, B world collision and manipulability, C and D alternate
 // halves of each lane's overlapping self-collision frame pairs.  The warps
 // meet at one named barrier per step slot, where A gathers the depths (a max
@@ -35,6 +41,9 @@ struct WarpPlan {
     int c;           // PW x H running costs
     int ba;          // PW x H x 2 ball in-plane gravity
     int hand;        // 4 x PW x H handed to warp A: self depths (C, D), world depth, manipulability cost
+    int claim;       // 3 x SL x 32 ints (pair mapping), per item: B's mask of the overlapping frame pairs
+                     // (bit 31: published), the pairs B has started (from the first), A has started
+                     // (from the last)
     int io;          // mu (H x d) | sigma (d) | state (3 x d) | goal (7) | dt (H) | gamma^h (H) |
                      // B-spline basis (H x nk), staged per warp
     int floats;      // size of one warp's (pair's) region
@@ -64,6 +73,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb, int kw)
     w.c = take(w.PW * pb.H);
     w.ba = take(w.PW * pb.H * 2);
     w.hand = take(4 * w.PW * pb.H);
+    w.claim = take(3 * w.SL * 32);
     w.io = take(pb.H * pb.d + 4 * pb.d + 7 + 2 * pb.H + pb.H * pb.nk);
     w.floats = off;
     return w;
@@ -206,10 +216,15 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     const bool do_costs = role == 0;  // A: controls, integration, the cost terms
     const bool do_world = kW == 1 || (kW == 2 ? role == 0 : role == 1);
     const bool do_manipw = kW <= 2 ? role == 0 : role == 1;
-    const bool do_selfc = kW == 1 || (kW == 2 ? role == 1 : role >= 2);
+    // self collision: the single warp; both warps of a pair (B takes each item's
+    // overlapping frame pairs from the first, A, once its own terms are done,
+    // from the last, one claim at a time); the quad's C and D (alternate pairs)
+    const bool do_selfc = kW <= 2 || role >= 2;
     const int self_half = kW == 4 ? role - 2 : -1;  // quad: which alternate hits; -1: all of them
     const int nw0 = wg * W.PW;  // first particle of this unit
     if (nw0 >= pb.N) return;    // uniform over the unit (all its warps)
+    if (kW == 2 && role == 1)   // (ordered before any claim by the unit barrier after the prefix)
+        for (int i = lane; i < 3 * W.SL * 32; i += 32) reinterpret_cast<int*>(ws + W.claim)[i] = 0;
     float* s_fr = ws + W.frame + role * W.fstride;  // this warp's own frames
     float* s_cb = ws + W.cb + role * W.cstride;
     float* s_eps = ws + W.eps;
@@ -661,7 +676,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         const bool do_self = do_selfc && valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
         if (valid && pred && pb.self_direct) dself = fmaxf(0.f, pred[gi]);  // Eq. 13's learned term
         uint32_t lp_hit = 0u;  // bit t: frame pair t has blocks and its bounds overlap
-        if (do_self) {
+        const bool joins = kW == 2 && do_costs;  // the pair's A: B's mask, when published in time
+        if (do_self && !joins) {
 #pragma unroll
             for (int la = 0; la < kMaxDof; ++la) {
 #pragma unroll
@@ -679,11 +695,43 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                 }
             }
         }
+        static_assert(kLinkPairs <= 31, "bit 31 of a published mask marks it published");
         int hit_no = 0;  // the quad's C and D take alternate hits of each lane
+        // pair: B publishes the item's mask, then works from its first pair, A
+        // from its last; each announces a pair before testing it and stops where
+        // the other has announced.  A stale read only repeats a test (the depth
+        // is a max), never skips one.
+        volatile int* item = reinterpret_cast<volatile int*>(ws + W.claim) + slot * 32 + lane;
+        volatile int* started_b = item + W.SL * 32;
+        volatile int* started_a = item + 2 * W.SL * 32;
+        if (kW == 2 && do_self) {
+            if (joins) {  // not yet published: B takes every pair
+                const uint32_t m = static_cast<uint32_t>(*item);
+                lp_hit = (m >> 31) ? (m & 0x7fffffffu) : 0u;
+            } else {
+                *item = static_cast<int>(lp_hit | 0x80000000u);
+            }
+        }
+        const int n_hit = __popc(lp_hit);
+        int taken = 0;  // pairs this warp has started
         while (lp_hit) {
-            const int t = __ffs(lp_hit) - 1;
-            lp_hit &= lp_hit - 1;
-            if (self_half >= 0 && (hit_no++ & 1) != self_half) continue;
+            int t;
+            if (kW == 2) {
+                if (joins) {
+                    if (n_hit - 1 - taken < *started_b) break;
+                    t = 31 - __clz(lp_hit);
+                    *started_a = ++taken;
+                } else {
+                    if (taken >= n_hit - *started_a) break;
+                    t = __ffs(lp_hit) - 1;
+                    *started_b = ++taken;
+                }
+                lp_hit &= ~(1u << t);
+            } else {
+                t = __ffs(lp_hit) - 1;
+                lp_hit &= lp_hit - 1;
+                if (self_half >= 0 && (hit_no++ & 1) != self_half) continue;
+            }
             int bk0 = 0, bk1 = 0;  // the pair's block range, read with constant indices only
 #pragma unroll
             for (int u = 0; u < kLinkPairs; ++u) {
@@ -740,7 +788,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                 }
             }
         }
-        if (do_self) {
+        if (do_self && !(kW == 2 && do_costs)) {  // the leftover pairs: not the pair's A
             for (int k = self_half > 0 ? 1 : 0; k < pb.P; k += self_half >= 0 ? 2 : 1) {
                 const uint32_t pr = pb.pairs[k];
                 const int a = pr & 0xffff, b = pr >> 16;
@@ -768,7 +816,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             float* hand = ws + W.hand;
             const int PH = W.PW * H, ix = pl * H + h;
             if (valid) {
-                if (do_selfc) hand[(self_half > 0 ? PH : 0) + ix] = dself;
+                if (do_selfc && !do_costs) hand[(self_half > 0 ? PH : 0) + ix] = dself;
                 if (kW == 4 && do_world) {
                     hand[2 * PH + ix] = dworld;
                     hand[3 * PH + ix] = c_manip;
@@ -777,7 +825,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             unit_sync(unit, kW * 32);
             if (do_costs && valid) {
                 if (kW == 2) {
-                    dself = hand[ix];
+                    dself = fmaxf(dself, hand[ix]);  // A's own pairs, then B's
                 } else {
                     dself = fmaxf(hand[ix], hand[PH + ix]);
                     dworld = hand[2 * PH + ix];

@@ -131,9 +131,12 @@ def _update_pair(N, H, beta, C=None, seed=0, **kw):
     return (mu, sig, w, st), (omu, osig, ow, ost), mu0, sig0, u
 
 
+# (4096, 30): 512 particle rows per CTA of the update's cluster, more than one
+# batch of loads in flight per thread; (37, 7): chunks of 5 rows of 49 floats
 @pytest.mark.parametrize("N,H,beta,amu,asg", [(64, 20, 0.1, 1.0, 0.5), (500, 30, 10.0, 1.0, 0.5),
                                               (1000, 30, 1.0, 0.7, 0.3), (37, 7, 3.0, 0.5, 1.0),
-                                              (1, 5, 1.0, 1.0, 0.5), (2048, 10, 2.0, 1.0, 0.5)])
+                                              (1, 5, 1.0, 1.0, 0.5), (2048, 10, 2.0, 1.0, 0.5),
+                                              (4096, 30, 1.0, 1.0, 0.5)])
 def test_update_stage_parity(N, H, beta, amu, asg):
     (mu, sig, w, st), (omu, osig, ow, ost), *_ = _update_pair(N, H, beta, alpha_mu=amu,
                                                              alpha_sigma=asg)
@@ -452,7 +455,22 @@ def _mapping_cases():
                                                     rot_axis_w=(0.5, 1.0, 2.0)), 4),
         "H50_N23": (paper, paper.params.replace(N=23, H=50, n_knots=10), 5),
         "H64_N3": (paper, paper.params.replace(N=3, H=64, n_knots=0), 6),
+        # the arm folded onto itself: many overlapping frame pairs per item, so
+        # the pair mapping's two warps share the self-collision tests
+        "folded_arm": (paper, paper.params.replace(N=48), 77),
     }
+
+
+def _folded_state(wl, seed=77, draws=200):
+    """The configuration, of `draws` uniform ones, closest to (or deepest in)
+    self-collision (chosen on the oracle), at rest."""
+    orc = oracle.Oracle(wl.robot, wl.world, wl.params)
+    rng = np.random.default_rng([seed, 5])
+    th = rng.uniform(-2.6, 2.6, (draws, 7))
+    sd = np.array([orc.self_min_sd_theta(t) for t in th])
+    state = np.zeros((3, 7))
+    state[0] = th[int(np.argmin(sd))]
+    return state
 
 
 @pytest.mark.parametrize("name", list(_mapping_cases()))
@@ -461,7 +479,7 @@ def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
     same bits in every output (controls, joint states, EE poses, cost terms,
     running and total costs)."""
     wl, p, sseed = _mapping_cases()[name]
-    state = W.make_state(sseed, 7)
+    state = W.make_state(sseed, 7) if sseed != 77 else _folded_state(wl)
     if sseed == 21:
         state[0, 3], state[1, 3] = 2.2, 0.8
     state, goal = cuda(f32(state)), cuda(f32(wl.goal))
@@ -498,6 +516,8 @@ def test_warp_mapping_is_bitwise_identical_to_cta_mapping(name):
         assert {"self", "world"} <= active, active
     if name == "dense_world":
         assert "world" in active, active
+    if name == "folded_arm":
+        assert "self" in active, active
 
 
 @pytest.mark.parametrize("mapping", ["cta", "warp", "pair"])
