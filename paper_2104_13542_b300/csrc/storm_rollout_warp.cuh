@@ -41,6 +41,7 @@ struct WarpPlan {
     int c;           // PW x H running costs
     int ba;          // PW x H x 2 ball in-plane gravity
     int hand;        // 4 x PW x H handed to warp A: self depths (C, D), world depth, manipulability cost
+    int lpb;         // kLinkPairs + 1 ints: the frame pairs' block ranges (Problem::lp_begin)
     int claim;       // 3 x SL x 32 ints (pair mapping), per item: B's mask of the overlapping frame pairs
                      // (bit 31: published), the pairs B has started (from the first), A has started
                      // (from the last)
@@ -73,6 +74,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb, int kw)
     w.c = take(w.PW * pb.H);
     w.ba = take(w.PW * pb.H * 2);
     w.hand = take(4 * w.PW * pb.H);
+    w.lpb = take(kLinkPairs + 1);
     w.claim = take(3 * w.SL * 32);
     w.io = take(pb.H * pb.d + 4 * pb.d + 7 + 2 * pb.H + pb.H * pb.nk);
     w.floats = off;
@@ -225,6 +227,14 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     if (nw0 >= pb.N) return;    // uniform over the unit (all its warps)
     if (kW == 2 && role == 1)   // (ordered before any claim by the unit barrier after the prefix)
         for (int i = lane; i < 3 * W.SL * 32; i += 32) reinterpret_cast<int*>(ws + W.claim)[i] = 0;
+    if (kW == 1 || role == 1) {  // the block ranges, for reads at an item's own frame pairs
+        static_assert(kLinkPairs < 32, "one lane per frame pair");
+        int v = 0;
+#pragma unroll
+        for (int u = 0; u <= kLinkPairs; ++u)
+            if (u == lane) v = pb.lp_begin[u];
+        if (lane <= kLinkPairs) reinterpret_cast<int*>(ws + W.lpb)[lane] = v;
+    }
     float* s_fr = ws + W.frame + role * W.fstride;  // this warp's own frames
     float* s_cb = ws + W.cb + role * W.cstride;
     float* s_eps = ws + W.eps;
@@ -732,34 +742,28 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                 lp_hit &= lp_hit - 1;
                 if (self_half >= 0 && (hit_no++ & 1) != self_half) continue;
             }
-            int bk0 = 0, bk1 = 0;  // the pair's block range, read with constant indices only
+            const int* lpb = reinterpret_cast<const int*>(ws + W.lpb);
+            const int bk0 = lpb[t], bk1 = lpb[t + 1];  // the pair's blocks: spheres of frame la x frame lk
+            int la = 0;  // t = link_pair_index(la, lk)
 #pragma unroll
-            for (int u = 0; u < kLinkPairs; ++u) {
-                if (u == t) {
-                    bk0 = pb.lp_begin[u];
-                    bk1 = pb.lp_begin[u + 1];
-                }
-            }
+            for (int f = 1; f < kMaxDof; ++f) la += t >= link_pair_index(f, f + 1);
+            const int lk = t - link_pair_index(la, la + 1) + la + 1;
+            const float4 bb = pb.lbound[lk];
+            const float ckx = s_cb[(lk * 3 + 0) * 32 + lane], cky = s_cb[(lk * 3 + 1) * 32 + lane],
+                        ckz = s_cb[(lk * 3 + 2) * 32 + lane];
+            float fa[12];  // the first frame, for every sphere of its blocks
+#pragma unroll
+            for (int k = 0; k < 12; ++k) fa[k] = s_fr[(la * 12 + k) * 32 + lane];
+            const float* fb = s_fr + lk * 12 * 32;
             for (int bk = bk0; bk < bk1; ++bk) {
                 const uint4 blk = pb.pblk[bk];  // a0, a1, b0, nb
-                int la = 0, lk = 0;
-#pragma unroll
-                for (int f = 1; f <= kMaxDof; ++f) {
-                    if (f <= d) {
-                        la += static_cast<int>(blk.x) >= first[f];
-                        lk += static_cast<int>(blk.z) >= first[f];
-                    }
-                }
-                const float4 bb = pb.lbound[lk];
-                const float ckx = s_cb[(lk * 3 + 0) * 32 + lane], cky = s_cb[(lk * 3 + 1) * 32 + lane],
-                            ckz = s_cb[(lk * 3 + 2) * 32 + lane];
-                const float* fa = s_fr + la * 12 * 32;
-                const float* fb = s_fr + lk * 12 * 32;
                 float4 cbk[8];
                 bool have_b = false;  // second-frame centres, computed on first need
                 for (uint32_t a = blk.x; a < blk.y; ++a) {
                     const float4 q = pb.sph[a];
-                    const float3 c = frame_point(fa, lane, q);
+                    const float3 c = make_float3(fmaf(fa[0], q.x, fmaf(fa[1], q.y, fmaf(fa[2], q.z, fa[3]))),
+                                                 fmaf(fa[4], q.x, fmaf(fa[5], q.y, fmaf(fa[6], q.z, fa[7]))),
+                                                 fmaf(fa[8], q.x, fmaf(fa[9], q.y, fmaf(fa[10], q.z, fa[11]))));
                     if (pb.broadphase) {  // sphere a apart from the second frame's bound: no pair touches
                         const float ex = c.x - ckx, ey = c.y - cky, ez = c.z - ckz;
                         const float rr = q.w + bb.w;
