@@ -757,7 +757,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             const float* fb = s_fr + lk * 12 * 32;
             for (int bk = bk0; bk < bk1; ++bk) {
                 const uint4 blk = pb.pblk[bk];  // a0, a1, b0, nb
-                float4 cbk[8];
+                // second-frame spheres in pairs (k, k + 4) for the packed tests: negated
+                // centre coordinates and radii
+                float2 nbx[4], nby[4], nbz[4], rb[4];
                 bool have_b = false;  // second-frame centres, computed on first need
                 for (uint32_t a = blk.x; a < blk.y; ++a) {
                     const float4 q = pb.sph[a];
@@ -772,22 +774,33 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                     if (!have_b) {
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
+                            float4 cb4 = make_float4(-1e30f, -1e30f, -1e30f, 0.f);
                             if (k < static_cast<int>(blk.w)) {
                                 const float4 qb = pb.sph[blk.z + k];
                                 const float3 cb = frame_point(fb, lane, qb);
-                                cbk[k] = make_float4(cb.x, cb.y, cb.z, qb.w);
+                                cb4 = make_float4(-cb.x, -cb.y, -cb.z, qb.w);
+                            }
+                            if (k < 4) {
+                                nbx[k].x = cb4.x, nby[k].x = cb4.y, nbz[k].x = cb4.z, rb[k].x = cb4.w;
                             } else {
-                                cbk[k] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                                nbx[k - 4].y = cb4.x, nby[k - 4].y = cb4.y, nbz[k - 4].y = cb4.z, rb[k - 4].y = cb4.w;
                             }
                         }
                         have_b = true;
                     }
+                    // the exact tests two at a time (Blackwell's paired FP32 operations:
+                    // per half the same IEEE operations in the same order as one test)
+                    const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y),
+                                 cz = make_float2(c.z, c.z), qw = make_float2(q.w, q.w);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const float ex = c.x - cbk[k].x, ey = c.y - cbk[k].y, ez = c.z - cbk[k].z;
-                        const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        const float rs = q.w + cbk[k].w;
-                        if (dist2 < rs * rs) dself = fmaxf(dself, rs - sqrtf(dist2));
+                    for (int k = 0; k < 4; ++k) {
+                        const float2 ex = __fadd2_rn(cx, nbx[k]), ey = __fadd2_rn(cy, nby[k]),
+                                     ez = __fadd2_rn(cz, nbz[k]);
+                        const float2 dist2 = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, __fmul2_rn(ez, ez)));
+                        const float2 rs = __fadd2_rn(qw, rb[k]);
+                        const float2 rr = __fmul2_rn(rs, rs);
+                        if (dist2.x < rr.x) dself = fmaxf(dself, rs.x - sqrtf(dist2.x));
+                        if (dist2.y < rr.y) dself = fmaxf(dself, rs.y - sqrtf(dist2.y));
                     }
                 }
             }
