@@ -751,6 +751,15 @@ __device__ __forceinline__ const float* cluster_peer(const float* local, unsigne
     return reinterpret_cast<const float*>(remote);
 }
 
+// Writable counterpart of `local` in cluster CTA `rank` (plain stores through
+// it; the next cluster barrier publishes them).
+__device__ __forceinline__ float* cluster_peer_w(float* local, unsigned rank)
+{
+    uint64_t remote;
+    asm("mapa.u64 %0, %1, %2;" : "=l"(remote) : "l"(reinterpret_cast<uint64_t>(local)), "r"(rank));
+    return reinterpret_cast<float*>(remote);
+}
+
 // Sum over the cluster's CTAs, in rank order, of the float at `local`'s offset
 // (all kUpdCluster loads in flight together).
 __device__ __forceinline__ float cluster_sum(const float* local)
@@ -778,6 +787,7 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     __shared__ float s_a1[kUpdateThreads + 1], s_a2[kUpdateThreads + 1];  // this CTA's partials (column O:
                                                                           // sum w, sum w c), read over the cluster
     __shared__ float s_dev[kUpdateThreads];                       // rank 0: squared deviation per column
+    __shared__ float s_in2[kUpdCluster][STORM_MAX_H * kMaxDof + 1];  // rank 0: every CTA's deviation partials
     __shared__ float s_mu[kUpdateThreads];                        // the new mean, every column
     const int N = pb.N, d = pb.d, H = pb.H, O = H * d;
     float* s_cost = s_w + ((N + 3) & ~3);
@@ -910,16 +920,19 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             s_grp[g][k] = a2;
         }
         __syncthreads();
-        if (tid < O) {
+        if (tid < O) {  // into rank 0's receive area (distributed shared memory)
             float p = s_grp[0][tid];
             for (int q = 1; q < G; ++q) p += s_grp[q][tid];
-            s_a2[tid] = p;
+            *cluster_peer_w(&s_in2[rank][tid], 0) = p;
         }
+        if (tid == O) *cluster_peer_w(&s_in2[rank][O], 0) = s_a2[O];  // sum w c
     }
 
-    // ---- rank 0: sigma (Eq. 5) from the cluster's deviation partials
+    // ---- rank 0: sigma (Eq. 5) from the cluster's deviation partials, now in
+    // its own shared memory: the other CTAs are done
     cluster_barrier();
-    if (rank == 0) {
+    if (rank != 0) return;
+    {
         if (degenerate) {
             if (tid == 0) {
                 st->status |= STORM_WARN_DEGENERATE;
@@ -932,7 +945,12 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
         } else {
             if (weights_out)
                 for (int n = tid; n < N; n += T) weights_out[n] = weight(n, s_cost[n]) * inv_s;
-            if (tid < O) s_dev[tid] = cluster_sum(s_a2 + tid);
+            if (tid < O) {
+                float a = 0.f;
+#pragma unroll
+                for (int r = 0; r < kUpdCluster; ++r) a += s_in2[r][tid];
+                s_dev[tid] = a;
+            }
             __syncthreads();
             if (tid < d) {
                 const int j = tid;
@@ -945,8 +963,11 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
                 pb.sigma[j] = sqrtf(var);
             }
             if (tid == 0) {
+                float a = 0.f;
+#pragma unroll
+                for (int r = 0; r < kUpdCluster; ++r) a += s_in2[r][O];
                 st->best = m;
-                st->wmean = cluster_sum(s_a2 + O) / s;
+                st->wmean = a / s;
             }
         }
         if (finalize) {
@@ -954,7 +975,6 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             if (tid == 0) st->step += 1;
         }
     }
-    cluster_barrier();  // rank 0 has read every CTA's partials
 }
 
 __global__ void __cluster_dims__(kUpdCluster, 1, 1) __launch_bounds__(kUpdateThreads)
