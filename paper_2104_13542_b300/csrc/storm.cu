@@ -712,13 +712,15 @@ __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
 // particles (Eq. 6) and sums the chunk into one partial per column (h, j),
 // thread k holding column k so that each particle row is one coalesced read:
 // first sum w (u - mu_old), from which every CTA forms the new mean (Eq. 4)
-// mu_old + alpha_mu A1 / s out of the cluster's partials (read over
-// distributed shared memory, in rank order); then, from the values still in
-// registers, sum w (u - mu_new)^2, which rank 0 adds over the cluster and over
-// h into the per-joint sigma (Eq. 5).  Rank 0 also records the iteration's
-// best and weighted-mean cost and, at the last iteration of a step, writes
-// next_command and advances the step counter; a last barrier keeps the CTAs
-// resident until it has read them.  Every sum runs in a fixed order (the
+// mu_old + alpha_mu A1 / s out of the cluster's partials (in rank order); then,
+// from the values still in registers, sum w (u - mu_new)^2, which rank 0 adds
+// over the cluster and over h into the per-joint sigma (Eq. 5).  Rank 0 also
+// records the iteration's best and weighted-mean cost and, at the last
+// iteration of a step, writes next_command and advances the step counter.
+// The partials travel by stores into the receivers' shared memory (every
+// CTA's mean partials into every CTA, the deviation partials into rank 0)
+// ahead of a cluster barrier, so that after it every read is local and the
+// other CTAs may end while rank 0 finishes.  Every sum runs in a fixed order (the
 // chunk's particles in order, interleaved over kUpdGroups thread groups added
 // in order, then the CTAs in rank order; sigma: the rows in order): bitwise
 // reproducible, whatever the grid around the cluster.
@@ -742,13 +744,16 @@ __device__ __forceinline__ void cluster_barrier()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Generic address of `local`'s counterpart in the shared memory of cluster CTA
-// `rank` (plain loads through it; the cluster barrier orders them).
-__device__ __forceinline__ const float* cluster_peer(const float* local, unsigned rank)
+// The two halves of a cluster barrier that orders nothing but the CTAs'
+// start: after the wait every CTA of the cluster is running, so its shared
+// memory may be written.
+__device__ __forceinline__ void cluster_arrive_start()
 {
-    uint64_t remote;
-    asm("mapa.u64 %0, %1, %2;" : "=l"(remote) : "l"(reinterpret_cast<uint64_t>(local)), "r"(rank));
-    return reinterpret_cast<const float*>(remote);
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_start()
+{
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
 }
 
 // Writable counterpart of `local` in cluster CTA `rank` (plain stores through
@@ -758,19 +763,6 @@ __device__ __forceinline__ float* cluster_peer_w(float* local, unsigned rank)
     uint64_t remote;
     asm("mapa.u64 %0, %1, %2;" : "=l"(remote) : "l"(reinterpret_cast<uint64_t>(local)), "r"(rank));
     return reinterpret_cast<float*>(remote);
-}
-
-// Sum over the cluster's CTAs, in rank order, of the float at `local`'s offset
-// (all kUpdCluster loads in flight together).
-__device__ __forceinline__ float cluster_sum(const float* local)
-{
-    float v[kUpdCluster];
-#pragma unroll
-    for (int r = 0; r < kUpdCluster; ++r) v[r] = *cluster_peer(local, static_cast<unsigned>(r));
-    float a = 0.f;
-#pragma unroll
-    for (int r = 0; r < kUpdCluster; ++r) a += v[r];
-    return a;
 }
 
 // shift: the first update of a step -- mu_old is the shifted mean (Alg. 1's
@@ -787,12 +779,14 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     __shared__ float s_a1[kUpdateThreads + 1], s_a2[kUpdateThreads + 1];  // this CTA's partials (column O:
                                                                           // sum w, sum w c), read over the cluster
     __shared__ float s_dev[kUpdateThreads];                       // rank 0: squared deviation per column
+    __shared__ float s_in1[kUpdCluster][STORM_MAX_H * kMaxDof + 1];  // every CTA's mean partials (col. O: sum w)
     __shared__ float s_in2[kUpdCluster][STORM_MAX_H * kMaxDof + 1];  // rank 0: every CTA's deviation partials
     __shared__ float s_mu[kUpdateThreads];                        // the new mean, every column
     const int N = pb.N, d = pb.d, H = pb.H, O = H * d;
     float* s_cost = s_w + ((N + 3) & ~3);
     const int tid = threadIdx.x, T = blockDim.x;
     const unsigned rank = cluster_rank();
+    cluster_arrive_start();  // (waited for before the first write to a peer)
     const int chunk = (N + kUpdCluster - 1) / kUpdCluster;
     const int n0 = min(N, static_cast<int>(rank) * chunk), n1 = min(N, n0 + chunk);
     const int G = O <= T / kUpdGroups ? kUpdGroups : 1;  // thread groups interleaving the chunk
@@ -881,20 +875,33 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             s_grp[g][k] = a1;
         }
         __syncthreads();
-        if (tid < O) {
-            float p = s_grp[0][tid];
-            for (int q = 1; q < G; ++q) p += s_grp[q][tid];
-            s_a1[tid] = p;
+        cluster_wait_start();
+        if (tid <= O) {  // into every CTA's receive area (distributed shared memory)
+            float p = s_a1[O];  // sum w
+            if (tid < O) {
+                p = s_grp[0][tid];
+                for (int q = 1; q < G; ++q) p += s_grp[q][tid];
+            }
+#pragma unroll
+            for (int r = 0; r < kUpdCluster; ++r) *cluster_peer_w(&s_in1[rank][tid], r) = p;
         }
+    } else {
+        cluster_wait_start();
     }
-    cluster_barrier();  // the mean partials and the normalisers are complete
+    cluster_barrier();  // every CTA's mean partials and normaliser are in every CTA
 
     float s = 1.f, inv_s = 1.f;
     if (!degenerate) {
         // ---- the new mean, Eq. 4, in every CTA from the cluster's partials
-        s = cluster_sum(s_a1 + O);
+        auto cluster_sum1 = [&](int c) {  // in rank order
+            float a = 0.f;
+#pragma unroll
+            for (int r = 0; r < kUpdCluster; ++r) a += s_in1[r][c];
+            return a;
+        };
+        s = cluster_sum1(O);
         inv_s = 1.f / s;
-        if (tid < O) s_mu[tid] = fmaf(pb.alpha_mu * cluster_sum(s_a1 + tid), inv_s, mu_k);  // k == tid here
+        if (tid < O) s_mu[tid] = fmaf(pb.alpha_mu * cluster_sum1(tid), inv_s, mu_k);  // k == tid here
         __syncthreads();
         if (rank == 0 && tid < O) pb.mu[tid] = s_mu[tid];
 
