@@ -287,6 +287,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (do_costs) {
+    // launched ordinarily, the inputs are final: their loads overlap the noise
+    // (issued first: the controls wait on them)
+    if (!pb.dep_launch) stage_inputs_async();
     {
         // The grid is a single wave, so every warp meets this SM's L1 cold: pull
         // the read-only tables into it now, while the noise is drawn, rather
@@ -295,8 +298,6 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         for (int o = lane * 128; o < pb.table_bytes; o += 32 * 128)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(tb + o));
     }
-    // launched ordinarily, the inputs are final: their loads overlap the noise
-    if (!pb.dep_launch) stage_inputs_async();
 
     // ---- noise eps[n][s][j] of the warp's particles
     const int per = S * d;
