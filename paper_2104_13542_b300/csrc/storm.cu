@@ -770,7 +770,9 @@ __device__ __forceinline__ float* cluster_peer_w(float* local, unsigned rank)
 // whole even when the iteration is degenerate, and the step's status starts at 0.
 __device__ __forceinline__ void update_cluster(const Problem& pb, const float* __restrict__ C,
                                                const float* __restrict__ u, float* __restrict__ weights_out,
-                                               StepState* st, float* __restrict__ cmd_out, int finalize, int shift)
+                                               StepState* st, float* __restrict__ cmd_out, int finalize, int shift,
+                                               float* __restrict__ host_cmd = nullptr,
+                                               StepState* host_st = nullptr)
 {
     extern __shared__ __align__(16) float s_w[];  // N weights (the chunk's), then N costs
     __shared__ float s_redf[32];
@@ -978,19 +980,25 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             }
         }
         if (finalize) {
-            if (tid < d) cmd_out[tid] = degenerate ? mu_k : s_mu[tid];
+            const float c = degenerate ? mu_k : s_mu[tid < d ? tid : 0];
+            if (tid < d) cmd_out[tid] = c;
             if (tid == 0) st->step += 1;
+            // the step's outputs straight into pinned host memory as well (host
+            // calls: no device-to-host copy after the kernel)
+            if (host_cmd && tid < d) host_cmd[tid] = c;
+            if (host_st && tid == 0) *host_st = *st;
         }
     }
 }
 
 __global__ void __cluster_dims__(kUpdCluster, 1, 1) __launch_bounds__(kUpdateThreads)
 k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
-         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out, int finalize, int shift)
+         float* __restrict__ weights_out, StepState* st, float* __restrict__ cmd_out, int finalize, int shift,
+         float* __restrict__ host_cmd, StepState* host_st)
 {
     pdl_trigger();
     pdl_wait();
-    update_cluster(pb, C, u, weights_out, st, cmd_out, finalize, shift);
+    update_cluster(pb, C, u, weights_out, st, cmd_out, finalize, shift, host_cmd, host_st);
 }
 
 #include "storm_adjoint.cuh"
@@ -1655,6 +1663,7 @@ struct storm_handle {
     int grad_steps = 0;
     float grad_eta = 0.f;
     float* h_io = nullptr;     // pinned mirror of d_io
+    float* h_io_dev = nullptr; // the mirror's device address
     cudaGraphExec_t g_dev = nullptr, g_host = nullptr;
     std::string err = "no error";
     std::vector<double> host_sigma_init;
@@ -1903,11 +1912,15 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
 }
 
 // shift: the first update of a step graph (see update_cluster).
+// host_out: also write the command and the step record into the pinned mirror
+// (at the last iteration).
 int launch_update(storm_handle* h, cudaStream_t s, const float* C, const float* u, float* w,
-                  float* cmd, int finalize, bool dep = false, bool shift = false)
+                  float* cmd, int finalize, bool dep = false, bool shift = false, bool host_out = false)
 {
+    float* host_cmd = host_out ? h->h_io_dev + io_cmd(h->pb) : nullptr;
+    StepState* host_st = host_out ? reinterpret_cast<StepState*>(h->h_io_dev + io_st(h->pb)) : nullptr;
     CK(launch_kernel(k_update, kUpdCluster, kUpdateThreads, h->update_smem, s, dep, h->pb, C, u, w, h->d_st, cmd,
-                     finalize, shift ? 1 : 0));
+                     finalize, shift ? 1 : 0, host_cmd, host_st));
     return STORM_OK;
 }
 
@@ -1927,8 +1940,10 @@ int launch_adjoint(storm_handle* h, cudaStream_t s, const float* state, const fl
 
 // Enqueue the kernels of one control step (device inputs in d_io).  Alg. 1's
 // shift is folded into the first iteration: its rollouts and update read the
-// shifted mean and the update stores it (no kernel of its own).
-int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
+// shifted mean and the update stores it (no kernel of its own).  host_out: the
+// update that finishes the step also writes the command and the step record
+// into the pinned mirror (see step_outputs_by_kernel).
+int enqueue_step_kernels(storm_handle* h, cudaStream_t s, bool host_out = false)
 {
     RolloutOut out{h->d_u, nullptr, nullptr, nullptr, nullptr, nullptr, h->d_C};
     const float* state = h->d_io + io_state(h->pb);
@@ -1945,8 +1960,8 @@ int enqueue_step_kernels(storm_handle* h, cudaStream_t s)
         }
         int rc = launch_rollout(h, s, out, state, goal, -1, k, false, 0, h->dep_launch, k == 0);
         if (rc) return rc;
-        rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, k == h->K - 1 && h->grad_steps == 0,
-                           h->dep_launch, k == 0);
+        const bool last = k == h->K - 1 && h->grad_steps == 0;
+        rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, last, h->dep_launch, k == 0, host_out && last);
         if (rc) return rc;
     }
     for (int g = 0; g < h->grad_steps; ++g) {  // gradient refinement of the mean
@@ -1995,6 +2010,11 @@ void destroy_graphs(storm_handle* h)
     h->g_dev = h->g_host = nullptr;
 }
 
+// The host graph's outputs (command, step record) written by the update that
+// finishes the step straight into the pinned mirror, with no copy node: when
+// no gradient refinement follows the last update.
+bool step_outputs_by_kernel(const storm_handle* h) { return h->grad_steps == 0; }
+
 int build_graphs(storm_handle* h)
 {
     destroy_graphs(h);
@@ -2008,8 +2028,8 @@ int build_graphs(storm_handle* h)
                      ? STORM_ERR_CUDA
                      : STORM_OK;
         }
-        if (!rc) rc = enqueue_step_kernels(h, h->cap_stream);
-        if (!rc && with_io) {
+        if (!rc) rc = enqueue_step_kernels(h, h->cap_stream, with_io && step_outputs_by_kernel(h));
+        if (!rc && with_io && !step_outputs_by_kernel(h)) {
             const size_t off = io_cmd(h->pb);
             const size_t bytes = sizeof(float) * (io_floats(h->pb) - off);
             rc = cudaMemcpyAsync(h->h_io + off, h->d_io + off, bytes, cudaMemcpyDeviceToHost,
@@ -2299,6 +2319,7 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     pb.ball = h->d_ball;  // the ball state of storm_set_ball (zero until set)
     CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
     CK(cudaMallocHost(&h->h_io, sizeof(float) * io_floats(pb)));
+    CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->h_io_dev), h->h_io, 0));
     CK(cudaMalloc(&h->d_adj, sizeof(float) * size_t(pb.N) * (pb.H * pb.d + 1)));
     std::memset(h->h_io, 0, sizeof(float) * io_floats(pb));
     h->d_st = reinterpret_cast<StepState*>(h->d_io + io_st(pb));
