@@ -275,6 +275,20 @@ class _Marshal:
         return s
 
 
+class _StepIO:
+    """Host buffers of Controller.step, reused across calls with their C pointers
+    formed once (marshalling cost per call: two copies in, one out)."""
+
+    def __init__(self, d):
+        self.st = np.zeros(3 * d, dtype=np.float32)
+        self.g = np.zeros(7, dtype=np.float32)
+        self.cmd = np.zeros(d, dtype=np.float32)
+        self.info = storm_step_info()
+        self.p_st, self.p_g, self.p_cmd = _p(self.st, _fp), _p(self.g, _fp), _p(self.cmd, _fp)
+        self.p_info = C.byref(self.info)
+        self.fn = lib().storm_step
+
+
 class Controller:
     """One STORM MPC handle (``storm_create`` ... ``storm_destroy``)."""
 
@@ -295,6 +309,7 @@ class Controller:
         if rc != 0:
             raise StormError(rc, "storm_create failed (see stderr)")
         self.h = h
+        self._io = _StepIO(self.d)
 
     # ------------------------------------------------------------------ plumbing
     def _check(self, rc, allow_warn=True):
@@ -330,16 +345,16 @@ class Controller:
     # ------------------------------------------------------------------ control step
     def step(self, state, goal):
         """Host-buffer control step -> (cmd (d,), info dict, status)."""
-        st = _f32(state).reshape(-1)
-        g = _f32(goal).reshape(-1)
-        if st.size != 3 * self.d or g.size != 7:
+        io = self._io
+        if np.size(state) != 3 * self.d or np.size(goal) != 7:
             raise ValueError("state must have 3*dof values and goal 7")
-        cmd = np.zeros(self.d, dtype=np.float32)
-        info = storm_step_info()
-        rc = lib().storm_step(self.h, _p(st, _fp), _p(g, _fp), _p(cmd, _fp), C.byref(info))
+        io.st[:] = np.ravel(state)  # (float32 conversion into the reused buffers)
+        io.g[:] = np.ravel(goal)
+        rc = io.fn(self.h, io.p_st, io.p_g, io.p_cmd, io.p_info)
         self._check(rc)
-        return cmd, dict(best_cost=info.best_cost, mean_weighted_cost=info.mean_weighted_cost,
-                         status=info.status, step=info.step), rc
+        info = io.info
+        return io.cmd.copy(), dict(best_cost=info.best_cost, mean_weighted_cost=info.mean_weighted_cost,
+                                   status=info.status, step=info.step), rc
 
     def step_async(self, state_dev, goal_dev, cmd_dev):
         self._join()
