@@ -687,7 +687,26 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         const bool do_self = do_selfc && valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
         if (valid && pred && pb.self_direct) dself = fmaxf(0.f, pred[gi]);  // Eq. 13's learned term
         uint32_t lp_hit = 0u;  // bit t: frame pair t has blocks and its bounds overlap
-        const bool joins = kW == 2 && do_costs;  // the pair's A: B's mask, when published in time
+        // pair: B publishes the item's mask, then works from its first pair, A
+        // from its last; each announces a pair before testing it and stops where
+        // the other has announced.  A stale read only repeats a test (the depth
+        // is a max), never skips one.  A joins only where B's mask is published
+        // (bit 31) by the time A's own terms are done.
+        static_assert(kLinkPairs <= 31, "bit 31 of a published mask marks it published");
+        int hit_no = 0;  // the quad's C and D take alternate hits of each lane
+        volatile int* item = reinterpret_cast<volatile int*>(ws + W.claim) + slot * 32 + lane;
+        volatile int* started_b = item + W.SL * 32;
+        volatile int* started_a = item + 2 * W.SL * 32;
+        const bool joins = kW == 2 && do_costs;  // the pair's A
+        if (kW == 2 && joins) __syncwarp();  // (A's read stays after its own terms)
+        if (joins && do_self) {
+            uint32_t m;
+            asm volatile("ld.volatile.shared.u32 %0, [%1];"
+                         : "=r"(m)
+                         : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(const_cast<int*>(item))))
+                         : "memory");
+            lp_hit = (m >> 31) ? (m & 0x7fffffffu) : 0u;
+        }
         if (do_self && !joins) {
 #pragma unroll
             for (int la = 0; la < kMaxDof; ++la) {
@@ -706,23 +725,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                 }
             }
         }
-        static_assert(kLinkPairs <= 31, "bit 31 of a published mask marks it published");
-        int hit_no = 0;  // the quad's C and D take alternate hits of each lane
-        // pair: B publishes the item's mask, then works from its first pair, A
-        // from its last; each announces a pair before testing it and stops where
-        // the other has announced.  A stale read only repeats a test (the depth
-        // is a max), never skips one.
-        volatile int* item = reinterpret_cast<volatile int*>(ws + W.claim) + slot * 32 + lane;
-        volatile int* started_b = item + W.SL * 32;
-        volatile int* started_a = item + 2 * W.SL * 32;
-        if (kW == 2 && do_self) {
-            if (joins) {  // not yet published: B takes every pair
-                const uint32_t m = static_cast<uint32_t>(*item);
-                lp_hit = (m >> 31) ? (m & 0x7fffffffu) : 0u;
-            } else {
-                *item = static_cast<int>(lp_hit | 0x80000000u);
-            }
-        }
+        if (kW == 2 && do_self && !joins) *item = static_cast<int>(lp_hit | 0x80000000u);
         const int n_hit = __popc(lp_hit);
         int taken = 0;  // pairs this warp has started
         while (lp_hit) {
