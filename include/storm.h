@@ -178,10 +178,14 @@ int storm_reset(storm_handle* h);
 
 /* One control step of Algorithm 1 from host buffers: state (3 x dof, host),
  * goal (7, host) -> cmd (dof, host) = first action of the optimised mean
- * (next_command).  Copies in and out through pinned staging inside the call
- * and waits for completion.  `info` may be NULL.  Errors: INVALID_ARG,
- * NONFINITE (state or goal), CUDA; returns WARN_DEGENERATE when an iteration
- * had no finite total cost. */
+ * (next_command).  The inputs go in through pinned staging; the step's last
+ * kernel writes the command and the step record into pinned memory itself
+ * (its step counter last), and the call returns as soon as they are there —
+ * the handle's stream may still be retiring that kernel, which every later
+ * call on the handle is ordered after (with gradient refinement the outputs
+ * are copied out and the call waits for the stream).  `info` may be NULL.
+ * Errors: INVALID_ARG, NONFINITE (state or goal), CUDA; returns
+ * WARN_DEGENERATE when an iteration had no finite total cost. */
 int storm_step(storm_handle* h, const float* state, const float* goal, float* cmd,
                storm_step_info* info);
 

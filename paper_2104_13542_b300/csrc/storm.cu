@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <map>
 #include <utility>
 #include <mutex>
@@ -984,9 +986,19 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             if (tid < d) cmd_out[tid] = c;
             if (tid == 0) st->step += 1;
             // the step's outputs straight into pinned host memory as well (host
-            // calls: no device-to-host copy after the kernel)
-            if (host_cmd && tid < d) host_cmd[tid] = c;
-            if (host_st && tid == 0) *host_st = *st;
+            // calls: no device-to-host copy after the kernel), the step counter
+            // last: the host returns once it sees it change
+            if (host_cmd) {
+                __syncthreads();  // (the command in cmd_out)
+                if (tid == 0) {
+                    for (int j = 0; j < d; ++j) host_cmd[j] = cmd_out[j];
+                    host_st->status = st->status;
+                    host_st->best = st->best;
+                    host_st->wmean = st->wmean;
+                    __threadfence_system();
+                    *reinterpret_cast<volatile uint32_t*>(&host_st->step) = st->step;
+                }
+            }
         }
     }
 }
@@ -2010,6 +2022,9 @@ void destroy_graphs(storm_handle* h)
     h->g_dev = h->g_host = nullptr;
 }
 
+constexpr uint32_t kStepPending = 0xffffffffu;  // host mirror's step field while a host call runs
+constexpr int kStepPollMs = 2000;               // then the stream is synchronised instead
+
 // The host graph's outputs (command, step record) written by the update that
 // finishes the step straight into the pinned mirror, with no copy node: when
 // no gradient refinement follows the last update.
@@ -2412,10 +2427,25 @@ int storm_step(storm_handle* h, const float* state, const float* goal, float* cm
         if (!std::isfinite(goal[i])) return fail(h, STORM_ERR_NONFINITE, "non-finite goal");
     std::memcpy(h->h_io + io_state(h->pb), state, sizeof(float) * 3 * d);
     std::memcpy(h->h_io + io_goal(h->pb), goal, sizeof(float) * 7);
+    StepState* st = reinterpret_cast<StepState*>(h->h_io + io_st(h->pb));
+    volatile uint32_t* st_step = &st->step;
+    const bool poll = step_outputs_by_kernel(h);
+    if (poll) *st_step = kStepPending;  // the last update overwrites it, last of the outputs
     CK(cudaGraphLaunch(h->g_host, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    if (poll) {
+        // wait for the outputs in pinned memory rather than for the stream to
+        // drain; past a bound (or on any device error) the stream decides
+        const auto t0 = std::chrono::steady_clock::now();
+        while (*st_step == kStepPending) {
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(kStepPollMs)) break;
+        }
+        std::atomic_thread_fence(std::memory_order_acquire);
+        if (*st_step == kStepPending) CK(cudaStreamSynchronize(h->stream));
+        if (*st_step == kStepPending) return fail(h, STORM_ERR_CUDA, "step outputs did not arrive");
+    } else {
+        CK(cudaStreamSynchronize(h->stream));
+    }
     std::memcpy(cmd, h->h_io + io_cmd(h->pb), sizeof(float) * d);
-    const StepState* st = reinterpret_cast<const StepState*>(h->h_io + io_st(h->pb));
     if (info) {
         info->best_cost = st->best;
         info->mean_weighted_cost = st->wmean;
