@@ -69,12 +69,14 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 
 
 def kernel_source_hash() -> str:
-    import glob
+    """Hash of what the warp rollout kernels are compiled from: the two headers
+    that define them (and everything they call) and the compiler flags."""
     import hashlib
+    from paper_2104_13542_b300.binding import NVCC_FLAGS
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2104_13542_b300", "csrc", "*.cu")) +
-                    glob.glob(os.path.join(ROOT, "paper_2104_13542_b300", "csrc", "*.cuh"))):
-        h.update(open(f, "rb").read())
+    for f in ("storm_device.cuh", "storm_rollout_warp.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2104_13542_b300", "csrc", f), "rb").read())
+    h.update(" ".join(NVCC_FLAGS).encode())
     return h.hexdigest()[:16]
 
 
