@@ -410,6 +410,55 @@ def test_step_async_device_buffers_match_host_step():
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("grad_steps", [0, 2])
+def test_host_step_outputs_match_the_device_step(grad_steps):
+    """storm_step's outputs (the command and the step record, written into pinned
+    memory by the step's last update and awaited there; with gradient refinement,
+    copied out after the stream) equal the device-resident step's, bit for bit,
+    over a closed loop that includes a degenerate step (NaN sigma, no null
+    particles: every total non-finite)."""
+    wl = W.config_paper(1)
+    p = wl.params.replace(N=96, n_null=0, grad_steps=grad_steps, grad_eta=0.01)
+    goal = f32(wl.goal)
+    runs = []
+    for host in (True, False):
+        with _ctl(wl, p) as ctl:
+            state = f32(wl.state)
+            s, g, c = cuda(state.reshape(-1)), cuda(goal), torch.zeros(7, device="cuda")
+            out = []
+            for k in range(5):
+                if k == 3:  # a degenerate step; the next one starts from a sane sigma again
+                    mu, sig = ctl.get_distribution()
+                    ctl.set_distribution(mu, np.full(7, np.nan, np.float32))
+                if k == 4:
+                    mu, sig = ctl.get_distribution()
+                    ctl.set_distribution(mu, np.full(7, 0.3, np.float32))
+                if host:
+                    cmd, info, rc = ctl.step(state, goal)
+                else:
+                    s.copy_(torch.as_tensor(state.reshape(-1)))
+                    ctl.step_async(s, g, c)
+                    info, rc = ctl.sync()
+                    cmd = c.cpu().numpy().copy()
+                out.append((cmd, info["best_cost"], info["mean_weighted_cost"], info["status"], info["step"], rc))
+                state = state.copy()
+                state[2] = np.nan_to_num(cmd)
+                state[1] += 0.02 * state[2]
+                state[0] += 0.02 * state[1]
+            runs.append(out)
+    for k, (a, b) in enumerate(zip(*runs)):
+        assert np.array_equal(a[0], b[0], equal_nan=True), k
+        assert np.array_equal(np.asarray(a[1:3]), np.asarray(b[1:3]), equal_nan=True), (k, a[1:3], b[1:3])
+        assert a[3:] == b[3:], (k, a[3:], b[3:])
+    assert [r[4] for r in runs[0]] == [0, 1, 2, 3, 4]
+    assert runs[0][3][3] == 1 and runs[0][3][5] == 1  # STORM_WARN_DEGENERATE
+    if grad_steps == 0:  # the distribution was kept: the next step is sane again
+        assert all(r[3] == 0 for k, r in enumerate(runs[0]) if k != 3)
+    # (with refinement the gradient of the sample-average cost, J(mu) over
+    # mu + sigma o eps, carries the NaN sigma into the mean: garbage in, and
+    # both paths report it the same way)
+
+
 # ----------------------------------------------------------------------------- launch shapes
 
 def test_launch_shapes_are_bitwise_identical_and_autotune():
