@@ -465,7 +465,7 @@ def run_variants(args, seed: int):
     margin = 0.05
     with Controller(wl.robot, wl.world, wl.params.replace(N=8)) as lab:
         rng = np.random.default_rng([seed, 77])
-        th = torch.as_tensor(rng.uniform(-2.8, 2.8, (262_144, 7)).astype(np.float32), device="cuda")
+        th = torch.as_tensor(rng.uniform(-2.8, 2.8, (1 << 20, 7)).astype(np.float32), device="cuda")
         th_te = torch.as_tensor(rng.uniform(-2.8, 2.8, (65_536, 7)).astype(np.float32), device="cuda")
         sd, sd_te = lab.self_distance(th), lab.self_distance(th_te)
     net = SurrogateMLP(seed=seed)
