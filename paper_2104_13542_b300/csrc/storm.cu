@@ -1940,7 +1940,10 @@ int launch_adjoint(storm_handle* h, cudaStream_t s, const float* state, const fl
                    const float* mean, int step_override, int iter, float* grad, float* J, float* Ctot,
                    float eta, float* cmd, int finalize)
 {
-    const int threads = std::max(64, std::min(128, (h->pb.H + 31) / 32 * 32));
+    // 128 threads: the per-(step, sphere) and per-(step, pair block) collision
+    // loops split four warps' ways; at 125 registers 4 CTAs fit an SM, so the
+    // paper workload's 500 particles stay one wave
+    const int threads = 128;
     k_adjoint<<<h->pb.N, threads, h->adjoint_smem, s>>>(h->pb, mean, state, goal, h->d_st,
                                                          step_override, iter, h->d_adj, Ctot);
     CK(cudaGetLastError());
