@@ -238,17 +238,12 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     }
     __syncthreads();
 
-    // ---- per step h: FK frames, non-collision costs and their gradients
+    // ---- per step h: FK frames
     for (int h = tid; h < I; h += nt) {
         const float* th = s_th + h * d;
-        const float* thd = s_thd + h * d;
-        const float* uh = s_u + h * d;
-        const float* up = (h == 0) ? s_state + 2 * d : uh - d;
         float4* fr = s_frame + h * F * 3;
         float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
         float pp[3] = {0.f, 0.f, 0.f};
-        GramFactor G;
-        G.zero();
         fr[0] = make_float4(1.f, 0.f, 0.f, 0.f);
         fr[1] = make_float4(0.f, 1.f, 0.f, 0.f);
         fr[2] = make_float4(0.f, 0.f, 1.f, 0.f);
@@ -260,9 +255,43 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
                     fr[(i + 1) * 3 + r] = make_float4(R[r * 3 + 0], R[r * 3 + 1], R[r * 3 + 2], pp[r]);
-                const float zx = R[2], zy = R[5], zz = R[8];
-                float x[6] = {pp[1] * zz - pp[2] * zy, pp[2] * zx - pp[0] * zz, pp[0] * zy - pp[1] * zx,
-                              zx, zy, zz};
+            }
+        }
+    }
+    __syncthreads();
+
+    // From here two groups of warps work side by side until the next CTA
+    // barrier: the first ceil(I / 32) warps take the non-collision costs and
+    // their gradients, one step per thread; the others the collision broad
+    // phase and the world and self minimisers (their own named barrier between
+    // passes).  Neither reads what the other writes.
+    const int cost_warps = (I + 31) / 32;
+    const int coll_threads = nt - cost_warps * 32;  // > 0: I <= 64 < nt / 32 * 32 - 32
+    const bool cost_warp = tid < cost_warps * 32;
+    const int ct = tid - cost_warps * 32;  // collision thread index
+    auto coll_sync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(coll_threads) : "memory"); };
+
+    // ---- per step h: non-collision costs and their gradients
+    for (int h = tid; cost_warp && h < I; h += cost_warps * 32) {
+        const float* th = s_th + h * d;
+        const float* thd = s_thd + h * d;
+        const float* uh = s_u + h * d;
+        const float* up = (h == 0) ? s_state + 2 * d : uh - d;
+        const float4* fr = s_frame + h * F * 3;
+        float R[9], pp[3];  // the end effector's frame
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float4 q = fr[d * 3 + r];
+            R[r * 3 + 0] = q.x, R[r * 3 + 1] = q.y, R[r * 3 + 2] = q.z, pp[r] = q.w;
+        }
+        GramFactor G;  // J J^T of the geometric Jacobian, column by column in joint order
+        G.zero();
+#pragma unroll
+        for (int i = 0; i < kMaxDof; ++i) {
+            if (i < d) {
+                const float4 r0 = fr[(i + 1) * 3], r1 = fr[(i + 1) * 3 + 1], r2 = fr[(i + 1) * 3 + 2];
+                const float zx = r0.z, zy = r1.z, zz = r2.z;
+                float x[6] = {r1.w * zz - r2.w * zy, r2.w * zx - r0.w * zz, r0.w * zy - r1.w * zx, zx, zy, zz};
                 G.add(x);
             }
         }
@@ -454,7 +483,6 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
             }
         }
     }
-    __syncthreads();
 
     // ---- broad phase (as in the rollout kernels): each step's link-bound centres
     // and, per (step, frame), the boxes and obstacle spheres its bound meets.  A
@@ -463,8 +491,9 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     const bool bp = pb.broadphase != 0;
     const unsigned long long all_b = pb.B >= 64 ? ~0ull : (1ull << pb.B) - 1ull;
     const unsigned long long all_o = pb.O >= 64 ? ~0ull : (1ull << pb.O) - 1ull;
+    if (!cost_warp) {  // the collision warps
     if (bp) {
-        for (int idx = tid; idx < I * F; idx += nt) {
+        for (int idx = ct; idx < I * F; idx += coll_threads) {
             const int item = idx / F, f = idx - item * F;
             const float4 q = s_lb[f];
             const float4* T = s_frame + (item * F + f) * 3;
@@ -490,11 +519,11 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
             s_mask[2 * idx] = mb;
             s_mask[2 * idx + 1] = mo;
         }
-        __syncthreads();
+        coll_sync();
     }
 
     // ---- sphere centres; world collision with its minimiser (sphere, obstacle)
-    for (int idx = tid; idx < I * M; idx += nt) {
+    for (int idx = ct; idx < I * M; idx += coll_threads) {
         const int item = idx / M, s = idx - item * M;
         const float4 q = s_sph[s];
         const float4* T = s_frame + (item * F + s_slink[s]) * 3;
@@ -547,9 +576,9 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         if (best >= 0)
             atomicMax(s_keyw + item, depth_key(depth, static_cast<uint32_t>(s * NO + best)));
     }
-    __syncthreads();
+    coll_sync();
     // ---- self collision with its minimiser
-    for (int idx = tid; idx < I * pb.NPB; idx += nt) {
+    for (int idx = ct; idx < I * pb.NPB; idx += coll_threads) {
         const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
         const uint4 blk = s_pblk[bk];
         if (bp) {  // the two links' bounds apart: no pair of the block touches
@@ -576,7 +605,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         }
         if (best >= 0) atomicMax(s_keys + item, depth_key(depth, static_cast<uint32_t>(bk * 64 + best)));
     }
-    for (int idx = tid; idx < I * pb.P; idx += nt) {
+    for (int idx = ct; idx < I * pb.P; idx += coll_threads) {
         const int item = idx / pb.P, k = idx - item * pb.P;
         const uint32_t pr = s_pairs[k];
         const float4 ca = s_cent[item * M + (pr & 0xffff)], cb = s_cent[item * M + (pr >> 16)];
@@ -586,6 +615,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         if (dist2 < rs * rs)
             atomicMax(s_keys + item, depth_key(rs - sqrtf(dist2), static_cast<uint32_t>((1u << 24) + k)));
     }
+    }  // the collision warps
     __syncthreads();
 
     // ---- collision gradients of each step's minimiser
