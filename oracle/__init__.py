@@ -85,7 +85,9 @@ class _Params(C.Structure):
                 ("filter", C.c_int), ("comb", C.c_double * 3), ("mix_bspline", C.c_double),
                 ("w_ee_vel", C.c_double), ("w_ee_acc", C.c_double), ("ee_vel_max", C.c_double),
                 ("ee_acc_max", C.c_double), ("w_ball", C.c_double), ("gravity", C.c_double * 3),
-                ("tray_center", C.c_double * 3), ("ball", _dp), ("halton_scramble", C.c_int)]
+                ("tray_center", C.c_double * 3), ("ball", _dp), ("halton_scramble", C.c_int),
+                ("mlp_mode", C.c_int), ("mlp_params", _dp), ("mlp_enc", C.c_int), ("mlp_h1", C.c_int),
+                ("mlp_h2", C.c_int), ("mlp_h3", C.c_int), ("mlp_margin", C.c_double)]
 
 
 def _declare(L):
@@ -399,7 +401,23 @@ class Oracle:
         s.tray_center[:] = [float(c) for c in p.tray_center]
         s.ball = None
         s.halton_scramble = int(p.halton_scramble)
+        s.mlp_mode, s.mlp_params = 0, None
         return s
+
+    def set_surrogate(self, arch, params, margin=None):
+        """The learned self-collision network (Sec. 4.2) in the rollout's self term:
+        with `margin`, a gate (the exact check only where the predicted distance is
+        below it); without, the Eq. 13 cost max(0, net) with no exact check.
+        `params` = None restores the exact check."""
+        if params is None:
+            self.P.mlp_mode, self.P.mlp_params = 0, None
+            return
+        self._mlp = _f64(params).ravel()
+        assert self._mlp.size == mlp_arch_param_count(arch)
+        self.P.mlp_params = _ptr(self._mlp)
+        self.P.mlp_enc, self.P.mlp_h1, self.P.mlp_h2, self.P.mlp_h3 = (int(a) for a in arch)
+        self.P.mlp_mode = 2 if margin is None else 1
+        self.P.mlp_margin = 0.0 if margin is None else float(margin)
 
     def set_ball(self, pos, vel):
         """Ball position and velocity (world frame) at the current robot state."""

@@ -746,7 +746,18 @@ void orc_running_cost(const orc_robot* R, const orc_world* W, const orc_params* 
 
     const double sd_self = orc_self_min_sd(R, frames);
     const double sd_world = orc_world_min_sd(R, W, frames);
-    const double c_self = sd_self < 0.0 ? -sd_self : 0.0;
+    double c_self = sd_self < 0.0 ? -sd_self : 0.0;
+    if (P->mlp_mode != 0) {
+        /* the learned network of Sec. 4.2 on this configuration, with the BF16
+         * rounding of a tensor-core forward pass */
+        const orc_mlp_arch A = {P->mlp_enc, P->mlp_h1, P->mlp_h2, P->mlp_h3};
+        double y = 0.0;
+        orc_mlp_arch_forward(&A, P->mlp_params, theta_h, 1, d, 1, &y);
+        if (P->mlp_mode == 2)
+            c_self = y > 0.0 ? y : 0.0;  /* Eq. 13: the network's depth is the cost */
+        else if (y >= P->mlp_margin)
+            c_self = 0.0;  /* predicted clear by the margin: the exact check is skipped */
+    }
     const double c_world = sd_world < 0.0 ? -sd_world : 0.0;
 
     /* task-space speed and acceleration limits on Eq. 8's X_dot, X_ddot (theta_ddot = u) */

@@ -93,6 +93,17 @@ typedef struct {
     double tray_center[3];  /* tray centre in the end-effector frame */
     const double* ball;     /* 6: ball position, velocity (world) at the current state; NULL: none */
     int halton_scramble;    /* Halton sampler: linearly scrambled digits (multipliers from the seed) */
+    /* learned self-collision network (Sec. 4.2, Eq. 13), evaluated per (particle, step)
+     * by orc_mlp_arch_forward with its BF16 rounding points:
+     *   mlp_mode 0  the exact sphere check (default);
+     *            1  gate: the exact check only where the prediction (distance, positive
+     *               apart) is below mlp_margin, elsewhere the self term is 0;
+     *            2  cost: the self term is max(0, prediction), the network predicting the
+     *               penetration depth (positive when colliding), no exact check */
+    int mlp_mode;
+    const double* mlp_params;          /* flat parameters, orc_mlp_arch layout */
+    int mlp_enc, mlp_h1, mlp_h2, mlp_h3; /* its architecture (see orc_mlp_arch) */
+    double mlp_margin;
 } orc_params;
 
 /* ---- noise ---- */

@@ -154,3 +154,76 @@ def test_jointnerf_bf16_mode_close_to_fp64():
     y16 = oracle.mlp_arch_forward(NERF, p, th, bf16=True)
     assert np.abs(y16 - y64).max() < 0.03 * max(1.0, np.abs(y64).max())
     assert not np.array_equal(y16, y64)
+
+
+# ----------------------------------------------------------------------------- network in the rollout
+
+def _collision_rollout(mode=None, params=None, margin=None):
+    """Paper workload, a start whose rollouts self-collide, a few particles."""
+    from paper_2104_13542_b300 import workloads as W
+    wl = W.config_paper(0)
+    p = wl.params.replace(N=12)
+    orc = oracle.Oracle(wl.robot, wl.world, p)
+    if params is not None:
+        orc.set_surrogate(oracle.ARCH_DISTANCE, params, margin)
+    state = W.make_state(21, 7)
+    state[0, 3], state[1, 3] = 2.2, 0.8
+    mu, sig = W.make_mean(3, p.H, 7, 0.5), W.make_sigma(3, 7)
+    return p, orc.rollout(state, wl.goal, mu, sig, orc.noise(2, 1))
+
+
+def _constant_net(c):
+    p = np.zeros(P)
+    p[-1] = c  # b4: the output is c whatever the input
+    return p
+
+
+def test_learned_cost_mode_is_max_of_zero_and_the_network():
+    """Eq. 13 mode: every self term is max(0, net); the other terms and the
+    running cost otherwise are the exact rollout's."""
+    p, ex = _collision_rollout()
+    assert (ex["terms"][..., 5] > 0).any()  # the exact check finds contact here
+    for c in (0.03, -0.2):
+        _, got = _collision_rollout(params=_constant_net(c))
+        assert np.all(got["terms"][..., 5] == max(0.0, c))
+        for t in range(oracle.NTERMS):
+            if t != 5:
+                assert np.array_equal(got["terms"][..., t], ex["terms"][..., t])
+        shift = p.w_coll * (max(0.0, c) - ex["terms"][..., 5])
+        assert np.allclose(got["cost"], ex["cost"] + shift, rtol=1e-12, atol=1e-9)
+
+
+def test_gate_mode_constant_networks():
+    """Gate mode: a network predicting 'clear' (at or above the margin) drops every
+    self term; one predicting 'near' keeps the exact check everywhere."""
+    p, ex = _collision_rollout()
+    _, far = _collision_rollout(params=_constant_net(0.05), margin=0.05)
+    assert np.all(far["terms"][..., 5] == 0.0)
+    assert np.allclose(far["cost"], ex["cost"] - p.w_coll * ex["terms"][..., 5], rtol=1e-12, atol=1e-9)
+    _, near = _collision_rollout(params=_constant_net(0.049), margin=0.05)
+    assert np.array_equal(near["terms"], ex["terms"]) and np.array_equal(near["C"], ex["C"])
+
+
+def test_gate_mode_decides_per_item():
+    """A hand-routed network y = 3 relu(theta_3 / 3 - 0.8) = max(0, theta_3 - 2.4)
+    (BF16 rounds the bias weight -0.8 to -0.80078125 and theta_3 / 3 by up to
+    2^-9 relative, so the switch sits at theta_3 = 2.4523 +- 0.006 for the 5 cm
+    margin): items clearly above it lose their self term, the others keep the
+    exact one."""
+    net = np.zeros(P)
+    d = _split(net)
+    d["W1"][0 * I + 3] = 1.0   # unit 0: x3 = theta_3 / 3 ...
+    d["W1"][0 * I + 7] = -0.8  # ... minus 0.8 (x7 = 1 carries the bias)
+    d["W2"][0 * H + 0] = 1.0
+    d["W3"][0 * H + 0] = 1.0
+    d["w4"][0] = 3.0
+    margin = 0.05
+    p, ex = _collision_rollout()
+    _, got = _collision_rollout(params=net, margin=margin)
+    th3 = ex["theta"][..., 3]
+    switch = 3 * 0.80078125 + margin
+    above, below = th3 > switch + 0.02, th3 < switch - 0.02
+    assert above.sum() > 20 and below.sum() > 20
+    assert (ex["terms"][..., 5][above] > 0).any()  # the gate really drops contact there
+    assert np.all(got["terms"][..., 5][above] == 0.0)
+    assert np.array_equal(got["terms"][..., 5][below], ex["terms"][..., 5][below])
