@@ -41,6 +41,7 @@ sys.path.insert(0, ROOT)
 from paper_2104_13542_b300 import workloads as W  # noqa: E402
 
 METRIC = "MPC step latency p50/p99 (ms) and rollout-steps/s, 500x30 7-DOF, vs oracle"
+LOOP_WARMUP, LOOP_STEPS = 50, 1000  # the closed loop every run records (five goals)
 UNIT = "rollout-steps/s"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
@@ -62,6 +63,18 @@ def algorithmic_flops_per_item(p: W.Params, robot: W.Robot, world: W.World) -> f
     manip = sum(28 * k + 22 for k in range(6)) if p.w_manip else 0
     return (48 * d + 18 * M + 12 * d + manip + 100 + M * (14 * B + 8 * O) + 8 * P +
             2 * S * d + 4 * d)
+
+
+def adjoint_flops_per_item(p: W.Params, robot: W.Robot, world: W.World) -> float:
+    """FP32 flops of one (particle, step) item of the adjoint kernel, counted from
+    the method: the forward pass it recomputes (algorithmic_flops_per_item), then
+    the reverse pass -- twice the forward work of FK, the Jacobian,
+    manipulability and the non-collision costs (reverse mode of each), the
+    collision gradient at the minimising pair or sphere-obstacle (centres and
+    distance, 2 x 30), and the integration adjoint (4 d)."""
+    d = robot.dof
+    manip = sum(28 * k + 22 for k in range(6)) if p.w_manip else 0
+    return algorithmic_flops_per_item(p, robot, world) + 2 * (48 * d + 12 * d + manip + 100) + 2 * 60 + 4 * d
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
@@ -103,58 +116,96 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks + throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks + throttle reasons, sampled every 100 ms from before the
+    measured part until after it.  mark() records the edges of a window (the
+    device-timed steps); summary() reports the samples inside it, or, when the
+    window is shorter than the sampling period, those of the whole measured
+    part (saying so).  The GPU is named by its UUID, so the sample is this
+    process's GPU whatever CUDA_VISIBLE_DEVICES maps."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
+        import tempfile
         self.dev = device_index
         self.proc = None
-        import tempfile
+        self.error = None
+        self.marks = {}
         self.path = os.path.join(tempfile.gettempdir(), f"storm_bench_clocks_{os.getpid()}.csv")
+
+    def _gpu_id(self):
+        try:
+            import torch
+            u = getattr(torch.cuda.get_device_properties(self.dev), "uuid", None)
+            if u:
+                u = str(u)
+                return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [x.strip() for x in cvd.split(",") if x.strip()]
+        return ids[self.dev] if self.dev < len(ids) else str(self.dev)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", f"--id={self._gpu_id()}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=self.fh, stderr=subprocess.DEVNULL)
-        except Exception:
+                stdout=self.fh, stderr=subprocess.PIPE)
+            t0 = time.time()
+            while time.time() - t0 < 5.0:  # until the first sample is in
+                if self.proc.poll() is not None:
+                    self.error = "nvidia-smi exited: " + self.proc.stderr.read().decode(errors="replace")[:200]
+                    self.proc = None
+                    break
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.05)
+        except Exception as e:  # no nvidia-smi: the record says why
+            self.error = f"{type(e).__name__}: {e}"
             self.proc = None
         return self
 
+    def mark(self, name):
+        import datetime
+        self.marks[name] = datetime.datetime.now()
+
     def __exit__(self, *exc):
         if self.proc is not None:
+            time.sleep(0.25)  # one more sample after the last timed step
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if getattr(self, "fh", None):
             self.fh.close()
 
-    def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
-            return None
-        rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
-        sm, smax, reasons = [], [], set()
+    def summary(self, window=("start", "end")):
+        import datetime
+        if not os.path.exists(self.path) or os.path.getsize(self.path) == 0:
+            return {"unavailable": self.error or "no nvidia-smi samples"}
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        for line in open(self.path):
+            r = [x.strip() for x in line.strip().split(",")]
             try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-                for k, nm in enumerate(names):
-                    if r[5 + k].strip().lower() == "active":
-                        reasons.add(nm)
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(r[1]), float(r[2]),
+                             {nm for k, nm in enumerate(names) if r[5 + k].lower() == "active"}))
             except (ValueError, IndexError):
                 continue
-        if not sm:
-            return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "samples": len(sm), "reasons": sorted(reasons)}
+        if not rows:
+            return {"unavailable": "unparsable nvidia-smi samples"}
+        a, b = self.marks.get(window[0]), self.marks.get(window[1])
+        inside = [x for x in rows if a and b and a <= x[0] <= b]
+        use, scope = (inside, "device-timed steps") if inside else (rows, "whole measured part")
+        return {"sm_mhz": float(np.median([x[1] for x in use])), "sm_max_mhz": float(max(x[2] for x in use)),
+                "reasons": sorted(set().union(*[x[3] for x in use])), "samples": len(use),
+                "samples_total": len(rows), "scope": scope}
 
 
 def goals_for(ctl, robot, seed: int, count: int, with_theta: bool = False):
@@ -227,56 +278,68 @@ def run_gpu(args, rank, world_size):
         ctl.set_dependent_launch(True)
     ctl.reset()
 
-    # ---------------- end-to-end closed loop through the host API (e2e)
-    # The arm drives to five goals in turn on an ideal double-integrator plant;
-    # every step's inputs are recorded, and the device-resident timing below
-    # replays the same sequence (the step's work depends on the configuration:
-    # the collision broad phase prunes less as links come close).
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.__enter__()
+    # ---------------- the closed loop through the host API (e2e): a fixed
+    # LOOP_WARMUP + LOOP_STEPS steps whatever --steps is, the arm driving to five
+    # goals in turn (LOOP_STEPS / 5 steps each) on an ideal double-integrator
+    # plant stepped outside the timed call.  Every step's state and goal and the
+    # controller's state before it (storm_get_state: mu, sigma, step counter) are
+    # recorded, so the device-timed steps below replay exact steps of this loop.
     import ctypes
     dof = wl.robot.dof
     state = state0.astype(np.float32).copy()
     dt = float(p.dt[0])
-    e2e_ms, pos_err, seq_state, seq_goal = [], [], [], []
-    seg = max(1, (args.steps + args.warmup) // len(goals))
-    for i in range(args.warmup + args.steps):
-        goal = goals[min(i // seg, len(goals) - 1)]
+    n_all = LOOP_WARMUP + LOOP_STEPS
+    seg = LOOP_STEPS // len(goals)
+    picks = np.linspace(LOOP_WARMUP, n_all - 1, args.steps).round().astype(int)
+    want_blob = set(picks.tolist())
+    e2e_ms, seq_state, seq_goal, blobs, final_err = [], [], [], {}, []
+    for i in range(n_all):
+        goal = goals[0] if i < LOOP_WARMUP else goals[min((i - LOOP_WARMUP) // seg, len(goals) - 1)]
         seq_state.append(state.reshape(-1).copy())
         seq_goal.append(np.asarray(goal, dtype=np.float32))
+        if i in want_blob:
+            blobs[i] = ctl.get_state()
         with torch.cuda.stream(ctl.stream):
             flush.fill_(float(i))
         ctl.stream.synchronize()
         t0 = time.perf_counter()
         cmd, info, rc = ctl.step(state, goal)
         t1 = time.perf_counter()
-        if i >= args.warmup:
+        if i >= LOOP_WARMUP:
             e2e_ms.append((t1 - t0) * 1e3)
         # ideal double-integrator plant
         state[2] = cmd
         state[1] = state[1] + dt * cmd
         state[0] = state[0] + dt * state[1]
-        if (i + 1) % seg == 0 or i == args.warmup + args.steps - 1:
-            ee = ctl.forward_kinematics(torch.as_tensor(state[0:1], device="cuda")).cpu().numpy()[0]
-            pos_err.append(float(np.linalg.norm(ee[:, 3] - goal[:3])))
+        if i >= LOOP_WARMUP and (i - LOOP_WARMUP + 1) % seg == 0:
+            T = ctl.forward_kinematics(torch.as_tensor(state[0:1], device="cuda")).cpu().numpy()[0]
+            q = _quat_from_rot(T[:, :3].astype(np.float64))
+            final_err.append({"pos_m": float(np.linalg.norm(T[:, 3] - goal[:3])),
+                              "quat": float(1.0 - abs(np.dot(q, np.asarray(goal[3:], np.float64))))})
     e2e_ms = np.array(e2e_ms)
     e2e_time_s = max_over_ranks(float(e2e_ms.sum() / 1e3), world_size)
 
-    # ---------------- device-resident timing (value): the same input sequence,
-    # staged in HBM beforehand; before each step (outside its events) the step's
-    # state and goal are copied into the handle's own input buffers
+    # ---------------- device-resident timing (value): --steps steps of the loop,
+    # evenly spaced over its LOOP_STEPS (after its warm-up), each replayed
+    # exactly: before its events the controller's recorded state is restored
+    # and the step's state and goal are copied into the handle's input buffers
+    # (from HBM), and L2 is flushed
     s_ptr, g_ptr, _ = ctl.device_io_ptrs()
     io_state = torch.as_tensor(_DeviceFloats(s_ptr, 3 * dof), device="cuda")
     io_goal = torch.as_tensor(_DeviceFloats(g_ptr, 7), device="cuda")
     seq_state_d = torch.as_tensor(np.stack(seq_state), device="cuda")
     seq_goal_d = torch.as_tensor(np.stack(seq_goal), device="cuda")
-    ctl.reset()
 
     def place(i):
+        ctl.set_state(blobs[i])
         with torch.cuda.stream(ctl.stream):
             io_state.copy_(seq_state_d[i], non_blocking=True)
             io_goal.copy_(seq_goal_d[i], non_blocking=True)
 
-    for i in range(args.warmup):
-        place(i)
+    for w in range(args.warmup):
+        place(int(picks[w % len(picks)]))
         ctl.step_resident()
     ctl.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -285,22 +348,22 @@ def run_gpu(args, rank, world_size):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        t0 = time.perf_counter()
-        torch.cuda.nvtx.range_push("timed_steps")  # (profilers select the timed launches by this range)
-        for i in range(args.steps):
-            with torch.cuda.stream(ctl.stream):
-                flush.fill_(float(i))
-            place(args.warmup + i)
-            ev[i][0].record(ctl.stream)
-            ctl.step_resident()
-            ev[i][1].record(ctl.stream)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+    clk.mark("start")
+    t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed_steps")  # (profilers select the timed launches by this range)
+    for k, i in enumerate(picks):
+        with torch.cuda.stream(ctl.stream):
+            flush.fill_(float(k))
+        place(int(i))
+        ev[k][0].record(ctl.stream)
+        ctl.step_resident()
+        ev[k][1].record(ctl.stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk.mark("end")
     ms = np.array([a.elapsed_time(b) for a, b in ev])
     dev_time_s = max_over_ranks(float(ms.sum() / 1e3), world_size)
-    clocks = clk.summary()
 
     # the arm at rest at its start configuration, the first goal, every step
     # (the lightest collision load: for reference next to the trajectory)
@@ -312,17 +375,17 @@ def run_gpu(args, rank, world_size):
         io_goal.copy_(gl_dev)
     for _ in range(args.warmup):
         ctl.step_resident()
-    ms_rest = _time_steps(ctl.step_resident, ctl.stream, flush, min(args.steps, 200))
+    ms_rest = _time_steps(ctl.step_resident, ctl.stream, flush, min(max(args.steps, 20), 200))
 
     # ---------------- rollout-kernel roofline: the rollout kernel alone, timed
-    # with events on the controller's stream, at the trajectory's states
-    from paper_2104_13542_b300.binding import lib
+    # with events on the controller's stream, at states of the loop
+    from paper_2104_13542_b300.binding import fp32_peak, lib
     n_rk = max(20, min(args.steps, 200))
-    picks = np.linspace(args.warmup, args.warmup + args.steps - 1, n_rk).round().astype(int)
+    rk_picks = np.linspace(LOOP_WARMUP, n_all - 1, n_rk).round().astype(int)
 
     def rollout_ms():
         rk = []
-        for j, i in enumerate(picks):
+        for j, i in enumerate(rk_picks):
             with torch.cuda.stream(ctl.stream):
                 flush.fill_(float(j))
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -339,9 +402,14 @@ def run_gpu(args, rank, world_size):
     ctl.set_broadphase(False)  # the same kernel doing every exact collision test
     rk_bf_ms = rollout_ms()
     ctl.set_broadphase(True)
+    clk.mark("fma_start")
+    fma = fp32_peak(8192)  # this GPU's FP32 FMA rate, measured now
+    clk.mark("fma_end")
+    clk.__exit__(None, None, None)
+    clocks = clk.summary(("start", "end"))
+    fma_clocks = clk.summary(("fma_start", "fma_end"))
     flops_launch = algorithmic_flops_per_item(p, wl.robot, wl.world) * p.N * p.H
-    sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
-    peak = fp32_peak_tflops(sm_mhz)
+    peak = max(fma["scalar_tflops"], fma["paired_tflops"])
     achieved = flops_launch / (rk_ms * 1e-3) / 1e12
     achieved_bf = flops_launch / (rk_bf_ms * 1e-3) / 1e12
 
@@ -351,12 +419,14 @@ def run_gpu(args, rank, world_size):
         latency_ms={"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                     "max": float(ms.max())},
         latency_rest_ms={"p50": float(np.percentile(ms_rest, 50)), "p99": float(np.percentile(ms_rest, 99))},
-        e2e={"value": job_throughput(units_per_step, args.steps, world_size, e2e_time_s), "unit": UNIT,
+        e2e={"value": job_throughput(units_per_step, len(e2e_ms), world_size, e2e_time_s), "unit": UNIT,
              "h2d_bytes_per_step": 4 * (3 * wl.robot.dof + 7),
              "d2h_bytes_per_step": 4 * wl.robot.dof + 16,
              "latency_ms": {"p50": float(np.percentile(e2e_ms, 50)),
                             "p99": float(np.percentile(e2e_ms, 99))},
-             "closed_loop_final_pos_err_m": pos_err},
+             "closed_loop": {"warmup_steps": LOOP_WARMUP, "steps": LOOP_STEPS, "goals": len(goals),
+                             "steps_per_goal": seg,
+                             "final_error_per_goal": final_err}},
         roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                   "frac": achieved / peak, "traffic": rollout_traffic(ROLLOUT_KERNELS[ctl.launch_mapping()]),
                   "kernel": ROLLOUT_KERNELS[ctl.launch_mapping()], "kernel_ms": rk_ms,
@@ -366,9 +436,11 @@ def run_gpu(args, rank, world_size):
                   "brute_force_kernel_ms": rk_bf_ms, "brute_force_frac": achieved_bf / peak,
                   "launch_shape": list(ctl.get_launch()), "autotune_us": tuned_us,
                   "dependent_launch": ctl.dependent_launch(),
-                  "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                                f"{sm_mhz:.0f} MHz (unit count x SM max clock; MEASURED_PEAKS has "
-                                f"no FP32 figure)"},
+                  "peak_basis": "measured: storm_fp32_peak (independent FMA chains on every SM), "
+                                "the better of one and two FMAs per instruction, this run",
+                  "fp32_peak_measured": fma, "fp32_peak_clocks": fma_clocks,
+                  "fp32_peak_unit_count_tflops": fp32_peak_tflops(
+                      (fma_clocks or {}).get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2032.0))},
         clocks=clocks,
         gpu_launches=2 * p.K * args.steps,
         wall_s=wall,
@@ -401,7 +473,7 @@ def _time_steps(step_fn, stream, flush, n):
     return np.array([a.elapsed_time(b) for a, b in ev])
 
 
-def run_variants(args, seed: int):
+def run_variants(args, seed: int, fp32_peak: float | None = None):
     """The gradient-refined, batched and surrogate forms next to the plain step,
     same GPU, same timing rules (device time per step, L2 flushed before each)."""
     import torch
@@ -424,6 +496,14 @@ def run_variants(args, seed: int):
                 mu, _ = c.get_distribution()
                 m = torch.as_tensor(mu, device="cuda")
                 s_d, g_d = torch.as_tensor(st.reshape(-1), device="cuda"), torch.as_tensor(gl, device="cuda")
+                # the adjoint alone (k_adjoint + its fixed-order reduce), against the FP32 peak
+                adj_ms = _time_steps(lambda: c.cost_grad(m, s_d, g_d, 7, 0), c.stream, flush, n)
+                fl = adjoint_flops_per_item(p, wl.robot, wl.world) * p.N * p.H
+                entry["adjoint"] = {"ms_p50": float(np.percentile(adj_ms, 50)),
+                                    "flops_per_launch": fl,
+                                    "tflops": fl / (float(np.percentile(adj_ms, 50)) * 1e-3) / 1e12}
+                if fp32_peak:
+                    entry["adjoint"]["frac_fp32_peak"] = entry["adjoint"]["tflops"] / fp32_peak
                 J0, g = c.cost_grad(m, s_d, g_d, 7, 0)
                 Js = [float(J0[0])]
                 for _ in range(p.grad_steps):
@@ -547,8 +627,9 @@ def run_ablation(args):
 
 def run_mlp_forward(args):
     """Forward passes of both surrogate networks on `--mlp-forward` random
-    configurations (device time per pass, CUDA events, 3 warm-up passes), with
-    the tensor-core throughput of the three GEMM layers."""
+    configurations (device time per pass, CUDA events, 3 warm-up passes): the
+    fused whole-network kernel and the layer-by-layer kernels, with the
+    tensor-core throughput of the three layers for each."""
     import torch
     from paper_2104_13542_b300 import SurrogateMLP
     rows = args.mlp_forward
@@ -558,21 +639,23 @@ def run_mlp_forward(args):
     out = {}
     for arch, widths in (("distance", (256, 256, 256)), ("jointnerf", (256, 128, 64))):
         net = SurrogateMLP(seed=args.seed, arch=arch)
-        for _ in range(3):
-            net.predict(th)
-        ev = []
-        for _ in range(10):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(net.stream)
-            net.predict(th)
-            b.record(net.stream)
-            ev.append((a, b))
-        torch.cuda.synchronize()
-        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
         flops = 2.0 * R * (16 * widths[0] + widths[0] * widths[1] + widths[1] * widths[2])
-        out[arch] = {"ms": ms, "gemm_tflops": flops / (ms * 1e-3) / 1e12, "rows": rows}
+        for mode in ("fused", "layers"):
+            layers = mode == "layers"
+            for _ in range(3):
+                net.predict(th, layers=layers)
+            ev = []
+            for _ in range(10):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(net.stream)
+                net.predict(th, layers=layers)
+                b.record(net.stream)
+                ev.append((a, b))
+            torch.cuda.synchronize()
+            ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+            out[f"{arch}_{mode}"] = {"ms": ms, "gemm_tflops": flops / (ms * 1e-3) / 1e12, "rows": rows}
         net.close()
-    return {"mlp_forward": out, "note": "per predict call, including encode and the output copy"}
+    return {"mlp_forward": out, "note": "per predict call (layers: including the encode and the output copy)"}
 
 
 def _local_goals(ctl, theta0, seed: int, count: int):
@@ -607,53 +690,97 @@ def _rot_from_quat(q):
                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
 
 
-def cpu_baseline(wl, budget_s: float = 12.0, n_sample: int | None = None):
-    """Time the FP64 oracle's control step on a bounded particle sample."""
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_steps(wl, n, budget_s, threads):
+    """Control steps of the FP64 oracle on n particles with `threads` host threads
+    in its rollout loop, until budget_s seconds or 50 steps."""
     import oracle
     p = wl.params
-    n = n_sample or p.N
-    ps = p.replace(N=n)
-    orc = oracle.Oracle(wl.robot, wl.world, ps)
+    orc = oracle.Oracle(wl.robot, wl.world, p.replace(N=n))
     mu, sig = np.zeros((p.H, wl.robot.dof)), np.full(wl.robot.dof, p.sigma_init)
+    prev = oracle.get_threads()
+    oracle.set_threads(threads)
     times = []
-    t_start = time.perf_counter()
-    step = 0
-    while True:
-        t0 = time.perf_counter()
-        _, mu, sig, _, _ = orc.step(wl.state, wl.goal, step, mu, sig)
-        times.append(time.perf_counter() - t0)
-        step += 1
-        if time.perf_counter() - t_start > budget_s or step >= 50:
-            break
-    t = np.array(times)
-    return {"value": n * p.H * p.K / float(t.mean()), "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": f"{len(t)} control steps of the FP64 oracle with {n} of {p.N} particles "
-                      f"(H={p.H}, K={p.K}), single thread",
-            "latency_ms": {"p50": float(np.percentile(t, 50) * 1e3),
-                           "p99": float(np.percentile(t, 99) * 1e3)}}
+    try:
+        t_start = time.perf_counter()
+        step = 0
+        while True:
+            t0 = time.perf_counter()
+            _, mu, sig, _, _ = orc.step(wl.state, wl.goal, step, mu, sig)
+            times.append(time.perf_counter() - t0)
+            step += 1
+            if time.perf_counter() - t_start > budget_s or step >= 50:
+                break
+    finally:
+        oracle.set_threads(prev)
+    return np.array(times)
+
+
+def cpu_baseline(wl, budget_s: float = 12.0, n_sample: int | None = None):
+    """Time the FP64 oracle's control step on the host cores: all cores (OpenMP
+    over particles; the same bits as one thread) and a single thread, each for
+    about budget_s / 2 seconds."""
+    p = wl.params
+    n = n_sample or p.N
+    cores = os.cpu_count() or 1
+    legs = {}
+    for name, threads in (("all_cores", cores), ("single_thread", 1)):
+        t = _oracle_steps(wl, n, budget_s / 2, threads)
+        legs[name] = {"value": n * p.H * p.K / float(t.mean()), "unit": UNIT, "cores": threads,
+                      "steps": len(t),
+                      "latency_ms": {"p50": float(np.percentile(t, 50) * 1e3),
+                                     "p99": float(np.percentile(t, 99) * 1e3)}}
+    out = dict(legs["all_cores"])
+    out.update({"kind": "oracle", "cpu_model": cpu_model(),
+                "sample": f"{legs['all_cores']['steps']} control steps of the FP64 oracle with {n} of {p.N} "
+                          f"particles (H={p.H}, K={p.K}) on {cores} threads (rollout loop over particles, "
+                          f"OpenMP); single-thread leg: {legs['single_thread']['steps']} steps",
+                "single_thread": legs["single_thread"]})
+    return out
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores, bounded samples."""
+    """The reference arm: the FP64 oracle on all the host cores (OpenMP over
+    particles), each step one oracle control step -- on all the workload's
+    particles when (warm-up + steps) of them fit in about 150 s, else on the
+    largest particle sample that does (--ref-particles N fixes the sample)."""
     import oracle
     wl = W.config_paper(seed=args.seed)
     p = wl.params
-    n = args.ref_particles
-    ps = p.replace(N=n)
-    orc = oracle.Oracle(wl.robot, wl.world, ps)
-    mu, sig = np.zeros((p.H, wl.robot.dof)), np.full(wl.robot.dof, p.sigma_init)
-    for w in range(args.warmup):
-        _, mu, sig, _, _ = orc.step(wl.state, wl.goal, w, mu, sig)
-    times = []
-    for i in range(args.steps):
-        t0 = time.perf_counter()
-        _, mu, sig, _, _ = orc.step(wl.state, wl.goal, args.warmup + i, mu, sig)
-        times.append(time.perf_counter() - t0)
+    cores = os.cpu_count() or 1
+    prev = oracle.get_threads()
+    oracle.set_threads(cores)
+    try:
+        n = args.ref_particles
+        if n <= 0:  # size the sample from one full step
+            t1 = _oracle_steps(wl, p.N, 0.0, cores)[0]
+            total = (args.warmup + args.steps) * t1
+            n = p.N if total <= 150.0 else max(8, int(p.N * 150.0 / total))
+        ps = p.replace(N=n)
+        orc = oracle.Oracle(wl.robot, wl.world, ps)
+        mu, sig = np.zeros((p.H, wl.robot.dof)), np.full(wl.robot.dof, p.sigma_init)
+        for w in range(args.warmup):
+            _, mu, sig, _, _ = orc.step(wl.state, wl.goal, w, mu, sig)
+        times = []
+        for i in range(args.steps):
+            t0 = time.perf_counter()
+            _, mu, sig, _, _ = orc.step(wl.state, wl.goal, args.warmup + i, mu, sig)
+            times.append(time.perf_counter() - t0)
+    finally:
+        oracle.set_threads(prev)
     t = np.array(times)
     value = n * p.H * p.K * len(t) / float(t.sum())
     sample = (f"each step: one FP64 oracle control step on {n} of the {p.N} particles "
-              f"(H={p.H}, K={p.K}), single thread")
+              f"(H={p.H}, K={p.K}), {cores} threads (OpenMP over particles)")
     return {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(t.mean() * 1e3), "higher_is_better": True, "scaling": "weak",
@@ -662,8 +789,8 @@ def run_reference(args):
                        "sample_particles": n},
             "latency_ms": {"p50": float(np.percentile(t, 50) * 1e3),
                            "p99": float(np.percentile(t, 99) * 1e3)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -675,7 +802,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--ref-particles", type=int, default=25)
+    ap.add_argument("--ref-particles", type=int, default=0,
+                    help="reference arm: particles per oracle step (0: all of them when the run fits "
+                         "in about 150 s, else the largest sample that does)")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -740,7 +869,7 @@ def main():
         "clocks": res["clocks"], "gpu_launches": res["gpu_launches"],
     }
     if world_size == 1 and not args.no_variants:
-        line["variants"] = run_variants(args, args.seed)
+        line["variants"] = run_variants(args, args.seed, res["roofline"]["peak"])
     if world_size == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget_s)
     print(json.dumps(line))

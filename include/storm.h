@@ -164,9 +164,13 @@ typedef struct {
 int storm_create(const storm_robot* robot, const storm_world* world,
                  const storm_params* params, void* cuda_stream, storm_handle** out);
 
-/* Release every resource of the handle (NULL is a no-op). */
+/* Release every resource of the handle (NULL is a no-op).  The controller of
+ * Algorithm 1 has no explicit teardown; this ends the lifetime storm_create
+ * began. */
 void storm_destroy(storm_handle* h);
 
+/* Static text of a storm_status value (never NULL).  The paper has no
+ * counterpart: status codes are this library's error reporting. */
 const char* storm_status_string(int status);
 /* Message of the last error on this handle (never NULL). */
 const char* storm_last_error(const storm_handle* h);
@@ -216,9 +220,20 @@ int storm_shift(storm_handle* h);
  * Halton sampler: the table drawn at storm_create.  Enqueued (no wait). */
 int storm_sample_noise(storm_handle* h, uint32_t step, int iter, float* eps_dev);
 
+/* The raw 32-bit words of that Philox noise stream, for checking the integer
+ * stream bit for bit: block first_block + i (i < count) of the counter
+ * (block, step, instance << 8 | iter, 0) under key (seed lo, seed hi) into
+ * words_dev[4 i .. 4 i + 3] (device, 16-byte aligned, count x 4 uint32).
+ * Philox4x32-10 is Salmon et al., SC'11; the paper samples with a
+ * pseudo-random generator it does not name (Sec. 4.3).  Enqueued (no wait).
+ * Errors: INVALID_ARG (NULL, bad iter, count outside 1..2^24, misaligned). */
+int storm_philox_words(storm_handle* h, uint32_t step, int iter, uint32_t first_block, int count,
+                       uint32_t* words_dev);
+
 /* sample_controls + generate_rollouts (Algorithm 1; Eqs. 2, 7-15) for
  * iteration `iter` of control step `step` on the current distribution, from
- * device state_dev / goal_dev.  The noise is the Philox stream of (step, iter)
+ * device state_dev / goal_dev, with the handle's self-collision network when
+ * one is set (storm_set_surrogate, storm_set_surrogate_cost).  The noise is the Philox stream of (step, iter)
  * or the Halton table.  Outputs are device buffers in the layouts above; any
  * of them may be NULL except that u_dev and Ctot_dev are always written when
  * given.  Enqueued on the handle's stream (no wait). */
@@ -254,7 +269,12 @@ int storm_cost_grad(storm_handle* h, const float* state_dev, const float* goal_d
 int storm_get_distribution(storm_handle* h, float* mean, float* sigma);
 int storm_set_distribution(storm_handle* h, const float* mean, const float* sigma);
 
-/* Replace the obstacles (counts within the STORM_MAX_OBSTACLES limits). */
+/* Replace the obstacles of the world-collision term (Eq. 14), with counts
+ * within the STORM_MAX_OBSTACLES limits.  The paper builds its scene once per
+ * run and leaves moving scenes to future work (appendix, State Estimation and
+ * Perception); this call lets the obstacles change between control steps.
+ * Takes effect from the next step; waits for the copies.  Errors: INVALID_ARG
+ * (NULL, counts out of range, non-finite values), CUDA. */
 int storm_set_world(storm_handle* h, const storm_world* world);
 
 /* Batched forward kinematics (Eq. 8) on device buffers: theta_dev (count x dof)
@@ -357,8 +377,10 @@ int storm_autotune(storm_handle* h, float* best_us);
 /* ---------------------------------------------------------------- batched instances */
 
 /* Many independent controllers of uneven sizes (particles, horizon, joints,
- * obstacles) stepped together: every kernel of a control step is launched
- * once for the whole batch, with the rollout work cut into tiles that
+ * obstacles) stepped together, each one the control step of Algorithm 1
+ * (shift, K x (sample_controls, generate_rollouts with Eqs. 2 and 7-15,
+ * update_distribution with Eqs. 4-6), next_command): every kernel of a
+ * control step is launched once for the whole batch, with the rollout work cut into tiles that
  * persistent CTAs deal out across the GPU.  The paper runs one controller;
  * batching is an added capability.  Instance i computes exactly what a
  * handle created from robots[i], worlds[i], params[i] computes (its Philox
@@ -457,8 +479,15 @@ const char* storm_mlp_last_error(const storm_mlp* m);
 int storm_mlp_get_params(storm_mlp* m, float* params);
 int storm_mlp_set_params(storm_mlp* m, const float* params);
 /* Predicted distances for theta_dev (count x dof, dof <= 7) into out_dev
- * (count); device buffers, waits.  count <= STORM_MLP_MAX_ROWS. */
+ * (count); device buffers, waits.  count <= STORM_MLP_MAX_ROWS.  One kernel
+ * runs the whole network per 128-row tile with the activations on chip
+ * (weights streamed through shared memory by bulk asynchronous copies); the
+ * result is bitwise that of storm_mlp_predict_layers. */
 int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev);
+/* The same predictions through the layer-by-layer tensor-core kernels of the
+ * training forward pass (each layer's BF16 activations written to and read
+ * back from global memory).  Same arguments, errors and waiting. */
+int storm_mlp_predict_layers(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev);
 /* Mean squared error against target_dev (count) and its gradient (host,
  * storm_mlp_param_count floats, nullable); waits. */
 int storm_mlp_loss_grad(storm_mlp* m, const float* theta_dev, const float* target_dev, int count,
@@ -470,32 +499,67 @@ int storm_mlp_loss_grad(storm_mlp* m, const float* theta_dev, const float* targe
 int storm_mlp_train(storm_mlp* m, const float* theta_dev, const float* target_dev, int count,
                     int dof, int batch, int epochs, float lr, uint64_t seed, float* epoch_loss);
 
+/* Failure-path check of the tensor-core kernels' bounded waits (the paper has
+ * no counterpart: this is the library's own failure detection).  Runs one
+ * CTA that takes tensor memory and waits, with the routine every tensor-core
+ * kernel uses, on an mbarrier that nothing ever completes, giving up after
+ * limit_us microseconds (1..1,000,000) instead of the kernels' 1 s.  It then
+ * flags the timeout, frees its tensor memory and ends, so the call returns
+ * STORM_ERR_TIMEOUT with the network, its stream and the context still usable
+ * (the flag is cleared on the way out).  Waits.  Errors: INVALID_ARG, CUDA. */
+int storm_mlp_wait_probe(storm_mlp* m, unsigned int limit_us);
+
 /* Exact self-collision label of the handle's robot: the minimum signed
  * distance over its self pairs for each configuration of theta_dev
  * (count x dof) into sd_dev (count).  Device buffers, enqueued. */
 int storm_self_distance(storm_handle* h, const float* theta_dev, int count, float* sd_dev);
 
-/* Use `mlp` (NULL: stop using it) in this handle's rollouts: each iteration
- * first evaluates the network on every (particle, step) configuration, and
- * the exact self-collision check runs only where the prediction is below
- * `margin` metres (elsewhere the self term is 0).  The network must outlive
- * its use and must not run concurrently with this handle's steps. */
+/* Use `mlp` (NULL: stop using it) in this handle's rollouts (the steps and
+ * storm_generate_rollouts): the rollout kernel evaluates the network on every
+ * (particle, step) configuration on the tensor cores, between the integration
+ * and the costs, and runs the exact self-collision check only where the
+ * prediction is below `margin` metres (elsewhere the self term is 0).  The
+ * rollout then takes four particle groups per CTA of five warps (whatever
+ * launch shape was set).  If a tensor-core wait of that kernel runs out, its
+ * CTA falls back to the exact check for all its items and sets the network's
+ * error flag (reported by the network's next call).  The network must live on
+ * the handle's device, outlive its use and not be trained while this handle
+ * steps; its weights are read at each step.  Allocates nothing.  Waits.
+ * Errors: INVALID_ARG (NaN margin, another device, a problem whose fused
+ * shared-memory plan exceeds a CTA), CUDA.  The adjoint (storm_cost_grad)
+ * always differentiates the exact self-collision term. */
 int storm_set_surrogate(storm_handle* h, storm_mlp* mlp, double margin);
 
 /* The paper's own use of the network (Eq. 13): the self-collision term of each
  * (particle, step) is max(0, mlp(theta)) with the network predicting the
  * penetration depth (positive when colliding), and no exact self check runs.
- * NULL stops it.  Same lifetime rules as storm_set_surrogate. */
+ * NULL stops it.  Same kernel, rules and errors as storm_set_surrogate. */
 int storm_set_surrogate_cost(storm_handle* h, storm_mlp* mlp);
 
 /* ---------------------------------------------------------------- checkpoint */
 
-/* Serialise mu, sigma and the step counter (the Philox key is fixed by the
- * params), so that a resumed handle reproduces the same steps bit for bit.
+/* Serialise the controller's state between steps -- the sampling
+ * distribution (mean mu and per-joint sigma of Eqs. 4-5, Sec. 4.3) and the step
+ * counter that indexes the noise (the Philox key is fixed by the params) -- so
+ * that a resumed handle reproduces the same steps bit for bit.  The paper has no
+ * checkpoint; the distribution is the state Algorithm 1 carries from one step
+ * to the next.
  * With buf == NULL, *len receives the size needed.  Errors: INVALID_ARG when
  * *len is too small; STATE when a blob does not match the handle's shape. */
 int storm_get_state(storm_handle* h, void* buf, size_t* len);
 int storm_set_state(storm_handle* h, const void* buf, size_t len);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* The FP32 fused multiply-add rate of the current device in TFLOP/s (the paper
+ * has no counterpart: this is the peak the rollout kernel's ALU roofline is
+ * quoted against).  Every thread of 8 x 256 threads per SM runs sixteen
+ * independent FMA chains of `iters` steps on registers; tflops_scalar with one
+ * FMA per instruction, tflops_paired with the paired FP32 FMA (two per
+ * instruction); each the best of five timed launches after a warm-up, with CUDA
+ * events on a private stream.  Allocates a few bytes; waits.  Errors:
+ * INVALID_ARG (iters outside 1..2^24, NULL), CUDA. */
+int storm_fp32_peak(int iters, float* tflops_scalar, float* tflops_paired);
 
 /* ---------------------------------------------------------------- without allocation */
 
@@ -526,14 +590,24 @@ int storm_set_state(storm_handle* h, const void* buf, size_t len);
  *
  * The first call on a device looks up the scratch array's device address with
  * cudaGetSymbolAddress (with that device current) and raises the rollout
- * kernel's shared-memory limit; make that first call before any stream capture.
- * Every call copies the model tables from host memory into the scratch and
- * rewrites every table the kernel reads, so no earlier contents are relied on.
+ * kernel's shared-memory limit.  Every call builds the model tables on the host
+ * exactly as storm_create does (spheres sorted by link, link-pair blocks, link
+ * bounding spheres, collision broad phase on), copies them into the scratch and
+ * rewrites every table the kernel reads, so no earlier contents are relied on;
+ * the rollout runs the CTA mapping of storm_set_launch (bitwise the totals of
+ * every other mapping).  Those copies come from pageable host memory, so each
+ * call blocks the calling thread until its host tables have been staged for
+ * the copy engine (not until the rollout ends), and a stream that is being
+ * captured into a graph is refused (INVALID_ARG): the host memory the copies
+ * read is freed when the call returns.
  * All calls share the one array: calls whose GPU work overlaps (other streams,
  * other host threads) race on it and must be serialised by the caller.
- * Errors: INVALID_ARG (as storm_create, NULL device pointer, bad iter, or a
- * problem whose tables plus controls exceed the scratch: 4*N*H*dof bytes of
- * controls plus about 40 KB of tables, e.g. N*H <= ~270,000 at dof 7), CUDA. */
+ * Errors: INVALID_ARG (as storm_create, NULL device pointer, bad iter, a
+ * capturing stream, or a problem whose tables plus controls exceed the
+ * scratch), CUDA.  The scratch holds, each rounded up to 256 bytes: about
+ * 40 KB of model tables; with STORM_SAMPLER_HALTON the Halton noise,
+ * 4*N*S*dof bytes (S = n_knots, or H without smoothing); and the controls,
+ * 4*N*H*dof bytes -- e.g. N*H <= ~270,000 at dof 7 with the Philox sampler. */
 int storm_rollout_costs_noalloc(const storm_robot* robot, const storm_world* world,
                                 const storm_params* params, const float* state_dev,
                                 const float* goal_dev, const float* mean_dev,

@@ -52,6 +52,7 @@ EXPORTED = [
     "storm_mlp_set_params", "storm_mlp_predict", "storm_mlp_loss_grad", "storm_mlp_train",
     "storm_self_distance", "storm_set_surrogate", "storm_set_broadphase", "storm_set_trace",
     "storm_mlp_create_arch", "storm_mlp_param_count", "storm_set_surrogate_cost",
+    "storm_philox_words", "storm_mlp_wait_probe", "storm_mlp_predict_layers", "storm_fp32_peak",
 ]
 MLP_PARAMS = 135937
 
@@ -136,6 +137,9 @@ def lib():
                                               vp, vp]
         L.storm_update_distribution.argtypes = [vp, vp, vp, vp]
         L.storm_sample_noise.argtypes = [vp, C.c_uint32, C.c_int, vp]
+        L.storm_philox_words.argtypes = [vp, C.c_uint32, C.c_int, C.c_uint32, C.c_int, vp]
+        L.storm_mlp_wait_probe.argtypes = [vp, C.c_uint]
+        L.storm_fp32_peak.argtypes = [C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         L.storm_get_distribution.argtypes = [vp, _fp, _fp]
         L.storm_set_distribution.argtypes = [vp, _fp, _fp]
         L.storm_set_world.argtypes = [vp, C.POINTER(storm_world)]
@@ -184,6 +188,7 @@ def lib():
         L.storm_mlp_get_params.argtypes = [vp, _fp]
         L.storm_mlp_set_params.argtypes = [vp, _fp]
         L.storm_mlp_predict.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+        L.storm_mlp_predict_layers.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.storm_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, C.c_int, _fp, _fp]
         L.storm_mlp_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                                       C.c_uint64, _fp]
@@ -193,6 +198,16 @@ def lib():
         L.storm_set_trace.argtypes = [vp, vp]
         _lib = L
     return _lib
+
+
+def fp32_peak(iters: int = 8192) -> dict:
+    """storm_fp32_peak: measured FP32 FMA TFLOP/s of the current device (scalar and
+    paired FMA instructions)."""
+    a, b = C.c_float(), C.c_float()
+    rc = lib().storm_fp32_peak(int(iters), C.byref(a), C.byref(b))
+    if rc != 0:
+        raise StormError(rc, "storm_fp32_peak failed")
+    return {"scalar_tflops": a.value, "paired_tflops": b.value}
 
 
 def status_string(code: int) -> str:
@@ -390,6 +405,16 @@ class Controller:
         self._check(lib().storm_sample_noise(self.h, int(step), int(it), _dptr(eps)))
         self.stream.synchronize()
         return eps
+
+    def philox_words(self, step: int, it: int, first_block: int, count: int):
+        """Raw Philox4x32-10 words of the noise stream (count x 4 uint32, host)."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            out = torch.empty((count, 4), dtype=torch.int32, device="cuda")
+        self._check(lib().storm_philox_words(self.h, int(step), int(it), int(first_block), int(count),
+                                             _dptr(out)))
+        self.stream.synchronize()
+        return out.cpu().numpy().view(np.uint32)
 
     def generate_rollouts(self, state_dev, goal_dev, step: int, it: int, debug: bool = True):
         N, H, d = self.N, self.H, self.d
@@ -747,13 +772,21 @@ class SurrogateMLP:
         assert p.size == self.n_params
         self._check(lib().storm_mlp_set_params(self.h, _p(p, _fp)))
 
-    def predict(self, theta_dev):
+    def predict(self, theta_dev, layers: bool = False):
+        """Predictions for theta_dev (count x dof): the fused whole-network kernel,
+        or with layers=True the layer-by-layer kernels of the training pass."""
         n, dof = int(theta_dev.shape[0]), int(theta_dev.shape[1])
         with self.torch.cuda.stream(self.stream):
             out = self.torch.empty(n, dtype=self.torch.float32, device="cuda")
         self._sync_in()
-        self._check(lib().storm_mlp_predict(self.h, _dptr(theta_dev.contiguous()), n, dof, _dptr(out)))
+        fn = lib().storm_mlp_predict_layers if layers else lib().storm_mlp_predict
+        self._check(fn(self.h, _dptr(theta_dev.contiguous()), n, dof, _dptr(out)))
         return out
+
+    def wait_probe(self, limit_us: int) -> int:
+        """storm_mlp_wait_probe: the bounded tensor-core wait run out on purpose;
+        returns the status (STORM_ERR_TIMEOUT when the bound works)."""
+        return int(lib().storm_mlp_wait_probe(self.h, int(limit_us)))
 
     def loss_grad(self, theta_dev, target_dev):
         n, dof = int(theta_dev.shape[0]), int(theta_dev.shape[1])

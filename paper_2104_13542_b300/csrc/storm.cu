@@ -102,8 +102,7 @@ struct RolloutOut {
 __device__ __forceinline__ void rollout_particles(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state,
                                                   const float* __restrict__ goal, uint32_t step,
-                                                  int iter, int n0, int np, unsigned char* smem,
-                                                  int front_only = 0)
+                                                  int iter, int n0, int np, unsigned char* smem)
 {
     const RolloutLayout L = rollout_layout(pb);
     float4* s_frame = reinterpret_cast<float4*>(smem + L.frame);
@@ -250,7 +249,6 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     if (out.theta_dot)
         for (int i = tid; i < np * HD; i += nt)
             out.theta_dot[static_cast<size_t>(n0) * HD + i] = s_thd[i];
-    if (front_only) return;  // joint states only (surrogate input)
 
     // ---- per (particle, step): FK frames, Jacobian, non-collision costs
     const bool want_ee = pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms;
@@ -355,9 +353,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
             s_ba[2 * item + 1] = a.y;
         }
         s_part[item] = part;
-        // the learned term of Eq. 13 replaces the exact self check
-        s_dself[item] = (pb.self_pred && pb.self_direct)
-                            ? fmaxf(0.f, pb.self_pred[static_cast<size_t>(n0) * H + item]) : 0.f;
+        s_dself[item] = 0.f;
         s_dworld[item] = 0.f;
         const size_t g = static_cast<size_t>(n0) * H + item;
         if (out.ee) {
@@ -519,11 +515,10 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
     trace_stamp(pb.trace, 4);
     // ---- self collision, Eq. 13 reading.  Pair blocks (every sphere of one
     // link against up to 8 spheres of another) keep the 8 centres in registers
-    // while streaming the first link's spheres; leftover pairs one by one.
-    const float* pred = pb.self_pred ? pb.self_pred + static_cast<size_t>(n0) * H : nullptr;
+    // while streaming the first link's spheres; leftover pairs one by one.  (A
+    // problem with the learned self-collision network runs k_rollout_mlp.)
     for (int idx = tid; idx < I * pb.NPB; idx += nt) {
         const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
-        if (pred && (pb.self_direct || pred[item] >= pb.self_margin)) continue;  // surrogate
         const uint4 blk = s_pblk[bk];  // a0, a1, b0, nb
         const int la = s_slink[blk.x], lbk = s_slink[blk.z];
         const float4* fa = s_frame + (item * F + la) * 3;
@@ -578,7 +573,6 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
         const float rs = qa.w + qb.w;
         const float rs2 = rs * rs;
         for (int item = 0; item < I; ++item) {
-            if (pred && (pb.self_direct || pred[item] >= pb.self_margin)) continue;
             const float4* fa = s_frame + (item * F + s_slink[a]) * 3;
             const float4* fb = s_frame + (item * F + s_slink[b]) * 3;
             const float ex = (fmaf(fa[0].x, qa.x, fmaf(fa[0].y, qa.y, fmaf(fa[0].z, qa.z, fa[0].w)))) -
@@ -627,7 +621,7 @@ __device__ __forceinline__ void rollout_particles(const Problem& pb, const Rollo
 __global__ void __launch_bounds__(kMaxThreads)
 k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
           const float* __restrict__ goal, const StepState* __restrict__ st, int step_override,
-          int iter, int front_only)
+          int iter)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n0 = blockIdx.x * pb.ppc;
@@ -636,7 +630,7 @@ k_rollout(Problem pb, RolloutOut out, const float* __restrict__ state,
     pdl_wait();
     if (np <= 0) return;
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
-    rollout_particles(pb, out, state, goal, step, iter, n0, np, smem, front_only);
+    rollout_particles(pb, out, state, goal, step, iter, n0, np, smem);
 }
 
 #include "storm_rollout_warp.cuh"
@@ -1015,6 +1009,7 @@ k_update(Problem pb, const float* __restrict__ C, const float* __restrict__ u,
 
 #include "storm_adjoint.cuh"
 #include "storm_mlp.cuh"
+#include "storm_rollout_mlp.cuh"
 
 // Raw noise of sample_controls: one thread per Philox block (4 values).
 __global__ void k_noise(Problem pb, uint32_t step, int iter, float* __restrict__ eps)
@@ -1034,6 +1029,19 @@ __global__ void k_noise(Problem pb, uint32_t step, int iter, float* __restrict__
 #pragma unroll
     for (int l = 0; l < 4; ++l)
         if (4 * b + l < total) eps[4 * b + l] = z[l];
+}
+
+// The raw Philox4x32-10 words behind that noise: block first + i of the noise
+// stream of (step, iter), four words per block.
+__global__ void k_philox_words(Problem pb, uint32_t step, int iter, uint32_t first, int count,
+                               uint32_t* __restrict__ words)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint4 x = philox4x32_10(make_uint4(first + static_cast<uint32_t>(i), step,
+                                             (pb.instance << 8) | static_cast<uint32_t>(iter), 0u),
+                                  pb.seed_lo, pb.seed_hi);
+    reinterpret_cast<uint4*>(words)[i] = x;
 }
 
 // shift (Algorithm 1): mu_h <- mu_{h+1}, mu_{H-1} <- 0.  As the first node of a
@@ -1322,7 +1330,7 @@ k_rollout_warp_batch(const BatchInstance* __restrict__ insts, const int2* __rest
             loaded = task.x;
         }
         const RolloutOut out{I.u, nullptr, nullptr, nullptr, nullptr, nullptr, I.C};
-        rollout_warp_body<1, kFull>(pb, out, I.state, I.goal, I.st->step, iter, 0, task.y, warp,
+        rollout_warp_body<1, kFull>(pb, out, I.state, I.goal, I.st->step, iter, task.y, warp,
                                  wsm + size_t(warp) * warp_floats);
         __syncwarp();
     }
@@ -1360,12 +1368,14 @@ struct storm_mlp {
     bool own_stream = false;
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
     __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w2t = nullptr, *w3 = nullptr, *w3t = nullptr;
+    __nv_bfloat16 *w1p = nullptr, *w2p = nullptr, *w3p = nullptr;  // packed blocks (tc::MlpView)
     MlpBuffers buf;
     float *th_b = nullptr, *t_b = nullptr, *loss_hist = nullptr;
     int* idx = nullptr;
     int cap_batch = 0, cap_idx = 0, cap_hist = 0;
     int* err = nullptr;
     int t = 0;
+    int sms = 1;  // SMs of the device: the grid of the fused forward
     std::string msg = "no error";
 };
 
@@ -1637,7 +1647,16 @@ int mlp_cast(storm_mlp* m, cudaStream_t s)
     const MlpArch& A = m->a;
     const int n = std::max(A.h1 * kMlpIn, std::max(A.h2 * A.h1, A.h3 * A.h2));
     k_mlp_cast<<<(n + 255) / 256, 256, 0, s>>>(m->p, A, m->w1, m->w2, m->w2t, m->w3, m->w3t);
+    k_mlp_pack<<<(n + 255) / 256, 256, 0, s>>>(m->w1, m->w2, m->w3, A.h1, A.h2, A.h3, m->w1p, m->w2p, m->w3p);
     return cudaGetLastError() == cudaSuccess ? STORM_OK : STORM_ERR_CUDA;
+}
+
+// The network as the fused kernels read it.
+tc::MlpView mlp_view(const storm_mlp* m)
+{
+    const MlpArch& A = m->a;
+    return tc::MlpView{m->w1p, m->w2p, m->w3p, m->p + A.ob2, m->p + A.ob3, m->p + A.ow4, m->p + A.ob4,
+                       A.enc, A.h1, A.h2, A.h3, m->err};
 }
 
 // ============================================================================ host runtime
@@ -1666,9 +1685,7 @@ struct storm_handle {
     StepState* d_st = nullptr;
     float* d_adj = nullptr;          // adjoint partial rows: N x (H*d + 1)
     storm_mlp* mlp = nullptr;        // learned self-collision surrogate (not owned)
-    MlpBuffers* mlp_buf = nullptr;   // its inference activations for N x H rows
-    float* d_theta = nullptr;        // N x H x d joint states for the surrogate
-    float* d_pred = nullptr;         // N x H (padded) predicted self distances
+    size_t mlp_smem = 0;             // k_rollout_mlp's dynamic shared memory
     float* d_ball = nullptr;         // 8: ball position, velocity (world frame), padding
     float h_ball[8] = {};
     size_t adjoint_smem = 0;
@@ -1865,7 +1882,7 @@ bool needs_full_rollout(const Problem& pb)
 {
     return pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || (pb.ball && pb.w_ball != 0.f) ||
            pb.filter != STORM_FILTER_DEFAULT || pb.rot_mode != STORM_ROT_QUAT || pb.sampler != STORM_SAMPLER_PHILOX ||
-           pb.self_pred != nullptr;
+           pb.self_mode != 0;
 }
 
 // Warps per particle group of a warp mapping.
@@ -1898,28 +1915,34 @@ cudaError_t launch_kernel(void (*kernel)(Params...), unsigned grid, unsigned blo
 // sets it, where the predecessor (the shift or a non-final update) never
 // advances the step counter that the rollout reads before its pdl_wait.
 int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const float* state,
-                   const float* goal, int step_override, int iter, bool exact_self = false,
-                   int front_only = 0, bool dep = false, bool shift = false)
+                   const float* goal, int step_override, int iter, bool dep = false, bool shift = false)
 {
     Problem pb = h->pb;
-    if (exact_self) pb.self_pred = nullptr;
     pb.dep_launch = dep ? 1 : 0;
     pb.shift_view = shift ? 1 : 0;
+    if (pb.self_mode != 0 && h->mlp) {  // the learned self collision: the network inside the rollout
+        pb.dep_launch = 0;
+        const WarpPlan wp = warp_plan(pb, 1);
+        const int grid = (pb.N + wp.PW * kMlpWarps - 1) / (wp.PW * kMlpWarps);
+        CK(launch_kernel(k_rollout_mlp, grid, tc::tile_threads(kMlpEpi), h->mlp_smem, s, false, pb, out, state, goal,
+                         static_cast<const StepState*>(h->d_st), step_override, iter, mlp_view(h->mlp)));
+        return STORM_OK;
+    }
     // the full instantiation where the problem or the call needs its extra code
     const bool full = needs_full_rollout(pb) || out.theta || out.theta_dot || out.ee || out.terms || out.cost;
     const StepState* st = h->d_st;
     if (h->mapping == STORM_MAP_WARP)
         CK(launch_kernel(full ? k_rollout_warp<1, true> : k_rollout_warp<1, false>, h->warp_grid, h->wpc * 32,
-                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
+                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter));
     else if (h->mapping == STORM_MAP_WARP_PAIR)
         CK(launch_kernel(full ? k_rollout_warp<2, true> : k_rollout_warp<2, false>, h->warp_grid, h->wpc * 64,
-                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
+                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter));
     else if (h->mapping == STORM_MAP_WARP_QUAD)
         CK(launch_kernel(full ? k_rollout_warp<4, true> : k_rollout_warp<4, false>, h->warp_grid, h->wpc * 128,
-                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter, front_only));
+                         h->warp_smem, s, dep, pb, out, state, goal, st, step_override, iter));
     else
         CK(launch_kernel(k_rollout, h->grid, h->threads, h->rollout_smem, s, dep, pb, out, state, goal,
-                         static_cast<const StepState*>(h->d_st), step_override, iter, front_only));
+                         static_cast<const StepState*>(h->d_st), step_override, iter));
     return STORM_OK;
 }
 
@@ -1965,15 +1988,7 @@ int enqueue_step_kernels(storm_handle* h, cudaStream_t s, bool host_out = false)
     const float* goal = h->d_io + io_goal(h->pb);
     float* cmd = h->d_io + io_cmd(h->pb);
     for (int k = 0; k < h->K; ++k) {
-        if (h->mlp) {  // surrogate: joint states, network, then the rollout proper
-            RolloutOut front{h->d_u, h->d_theta, nullptr, nullptr, nullptr, nullptr, h->d_C};
-            int rc = launch_rollout(h, s, front, state, goal, -1, k, false, 1, h->dep_launch, k == 0);
-            if (rc) return rc;
-            rc = mlp_forward(h->mlp, *h->mlp_buf, h->d_theta, h->pb.N * h->pb.H, h->pb.d, false,
-                             h->d_pred, s);
-            if (rc) return fail(h, rc, "surrogate forward launch failed");
-        }
-        int rc = launch_rollout(h, s, out, state, goal, -1, k, false, 0, h->dep_launch, k == 0);
+        int rc = launch_rollout(h, s, out, state, goal, -1, k, h->dep_launch, k == 0);
         if (rc) return rc;
         const bool last = k == h->K - 1 && h->grad_steps == 0;
         rc = launch_update(h, s, h->d_C, h->d_u, nullptr, cmd, last, h->dep_launch, k == 0, host_out && last);
@@ -1995,7 +2010,7 @@ int allow_smem(storm_handle* h)
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     cudaFuncAttributes ra, ua, aa, wa;
     CK(cudaFuncGetAttributes(&ra, k_rollout));
-    using WarpKernel = void (*)(Problem, RolloutOut, const float*, const float*, const StepState*, int, int, int);
+    using WarpKernel = void (*)(Problem, RolloutOut, const float*, const float*, const StepState*, int, int);
     const WarpKernel warp_kernels[] = {k_rollout_warp<1, false>, k_rollout_warp<1, true>, k_rollout_warp<2, false>,
                                        k_rollout_warp<2, true>,  k_rollout_warp<4, false>, k_rollout_warp<4, true>};
     for (WarpKernel kf : warp_kernels) {
@@ -2081,13 +2096,7 @@ void free_all(storm_handle* h)
     if (h->d_C) cudaFree(h->d_C);
     if (h->d_io) cudaFree(h->d_io);
     if (h->d_adj) cudaFree(h->d_adj);
-    if (h->d_theta) cudaFree(h->d_theta);
-    if (h->d_pred) cudaFree(h->d_pred);
     if (h->d_ball) cudaFree(h->d_ball);
-    if (h->mlp_buf) {
-        mlp_free_buffers(*h->mlp_buf);
-        delete h->mlp_buf;
-    }
     if (h->h_io) cudaFreeHost(h->h_io);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -2518,6 +2527,19 @@ int storm_sample_noise(storm_handle* h, uint32_t step, int iter, float* eps_dev)
     return STORM_OK;
 }
 
+int storm_philox_words(storm_handle* h, uint32_t step, int iter, uint32_t first_block, int count,
+                       uint32_t* words_dev)
+{
+    if (!h || !words_dev) return fail(h, STORM_ERR_INVALID_ARG, "NULL argument");
+    if (iter < 0 || iter > 255 || count < 1 || count > (1 << 24))
+        return fail(h, STORM_ERR_INVALID_ARG, "bad iter or count");
+    if (reinterpret_cast<uintptr_t>(words_dev) % 16 != 0)
+        return fail(h, STORM_ERR_INVALID_ARG, "words_dev must be 16-byte aligned");
+    k_philox_words<<<(count + 255) / 256, 256, 0, h->stream>>>(h->pb, step, iter, first_block, count, words_dev);
+    CK(cudaGetLastError());
+    return STORM_OK;
+}
+
 int storm_generate_rollouts(storm_handle* h, const float* state_dev, const float* goal_dev,
                             uint32_t step, int iter, float* u_dev, float* theta_dev,
                             float* theta_dot_dev, float* ee_dev, float* terms_dev,
@@ -2527,7 +2549,7 @@ int storm_generate_rollouts(storm_handle* h, const float* state_dev, const float
     if (iter < 0 || iter > 255 || step > 0x7fffffffu) return fail(h, STORM_ERR_INVALID_ARG, "bad iter/step");
     RolloutOut out{u_dev ? u_dev : h->d_u, theta_dev, theta_dot_dev, ee_dev, terms_dev, cost_dev,
                    Ctot_dev ? Ctot_dev : h->d_C};
-    return launch_rollout(h, h->stream, out, state_dev, goal_dev, static_cast<int>(step), iter, true);
+    return launch_rollout(h, h->stream, out, state_dev, goal_dev, static_cast<int>(step), iter);
 }
 
 int storm_cost_grad(storm_handle* h, const float* state_dev, const float* goal_dev,
@@ -2889,6 +2911,92 @@ int storm_set_state(storm_handle* h, const void* buf, size_t len)
 
 }  // extern "C"
 
+// ============================================================================ FP32 peak
+//
+// The FP32 FMA rate of this GPU, measured: every thread runs eight independent
+// chains of fused multiply-adds on registers (no memory traffic), either one
+// FMA per instruction or Blackwell's paired FMA (two per instruction), with the
+// whole GPU occupied.  The ALU roofline of the rollout kernel divides by it.
+template <bool kPaired>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, float seed, float* __restrict__ sink)
+{
+    const float m = 0.9999f, c = 1e-7f;
+    float acc = 0.f;
+    if (kPaired) {
+        float2 a[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = make_float2(seed + threadIdx.x + k, seed - k);
+        const float2 m2 = make_float2(m, m), c2 = make_float2(c, -c);
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = __ffma2_rn(a[k], m2, c2);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc += a[k].x + a[k].y;
+    } else {
+        float a[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = seed + threadIdx.x + k;
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a[k] = fmaf(a[k], m, c);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc += a[k];
+    }
+    if (acc == seed) sink[blockIdx.x] = acc;  // keeps the chains live; never true in practice
+}
+
+extern "C" int storm_fp32_peak(int iters, float* tflops_scalar, float* tflops_paired)
+{
+    if (iters < 1 || iters > (1 << 24) || !tflops_scalar || !tflops_paired) return STORM_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return STORM_ERR_CUDA;
+    }
+    const int blocks = sms * 8;  // 2048 threads per SM
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float* sink = nullptr;
+    int rc = STORM_OK;
+    auto ck = [&](cudaError_t e) {
+        if (rc == STORM_OK && e != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = STORM_ERR_CUDA;
+        }
+    };
+    ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ck(cudaEventCreate(&e0));
+    ck(cudaEventCreate(&e1));
+    ck(cudaMalloc(&sink, sizeof(float) * blocks));
+    const double flops = 2.0 * 16.0 * iters * blocks * 256.0;  // 16 FMAs per iteration per thread
+    for (int paired = 0; paired < 2 && rc == STORM_OK; ++paired) {
+        auto launch = [&]() {
+            if (paired)
+                k_fma_peak<true><<<blocks, 256, 0, s>>>(iters, 1.0f, sink);
+            else
+                k_fma_peak<false><<<blocks, 256, 0, s>>>(iters, 1.0f, sink);
+        };
+        launch();  // warm-up
+        ck(cudaGetLastError());
+        float best = 0.f;
+        for (int r = 0; r < 5 && rc == STORM_OK; ++r) {
+            ck(cudaEventRecord(e0, s));
+            launch();
+            ck(cudaEventRecord(e1, s));
+            ck(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1));
+            if (rc == STORM_OK && ms > 0.f) best = std::max(best, static_cast<float>(flops / (ms * 1e-3) / 1e12));
+        }
+        (paired ? *tflops_paired : *tflops_scalar) = best;
+    }
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    return rc;
+}
+
 // ============================================================================ no allocation
 //
 // storm_rollout_costs_noalloc: the rollout kernel launched on tables and a
@@ -2949,71 +3057,26 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
     if (!state_dev || !goal_dev || !mean_dev || !sigma_dev || !Ctot_dev) return STORM_ERR_INVALID_ARG;
     if (iter < 0 || iter > 255 || step > 0x7fffffffu) return STORM_ERR_INVALID_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    {
+        // the table copies below read pageable host vectors that die with this
+        // call: a captured graph would replay copies from freed memory
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            (void)cudaGetLastError();
+            fprintf(stderr, "storm_rollout_costs_noalloc: the stream is being captured (not supported)\n");
+            return STORM_ERR_INVALID_ARG;
+        }
+    }
 
+    // the problem and its host tables exactly as storm_create builds them
+    // (spheres sorted by link, link-pair blocks, link bounds, broad phase on)
     Problem pb{};
-    pb.N = p->N;
-    pb.H = p->H;
-    pb.d = r->dof;
-    fill_sampling(p, pb);
-    pb.sampler = p->sampler;
-    pb.n_null = p->n_null;
-    pb.rot_mode = p->rot_mode;
-    pb.M = r->n_spheres;
-    pb.P = r->n_pairs;
-    pb.B = w->n_boxes;
-    pb.O = w->n_spheres;
-    pb.beta = static_cast<float>(p->beta);
-    pb.w_pos = static_cast<float>(p->w_pos);
-    pb.w_rot = static_cast<float>(p->w_rot);
-    pb.w_stop = static_cast<float>(p->w_stop);
-    pb.w_joint = static_cast<float>(p->w_joint);
-    pb.w_manip = static_cast<float>(p->w_manip);
-    pb.w_coll = static_cast<float>(p->w_coll);
-    pb.w_smooth = static_cast<float>(p->w_smooth);
-    for (int i = 0; i < 3; ++i) {
-        pb.pos_w[i] = static_cast<float>(p->pos_axis_w[i]);
-        pb.rot_w[i] = static_cast<float>(p->rot_axis_w[i]);
-    }
-    pb.k_m = static_cast<float>(p->k_m);
-    pb.seed_lo = static_cast<uint32_t>(p->seed & 0xffffffffu);
-    pb.seed_hi = static_cast<uint32_t>(p->seed >> 32);
-    pb.instance = p->instance;
-    pb.ppc = std::max(1, std::min(pb.N, 64 / pb.H));
-    pb.mu = const_cast<float*>(mean_dev);  // read only by the rollout kernel
-    pb.sigma = const_cast<float*>(sigma_dev);
+    HostTables ht;
+    fill_problem(r, w, p, pb, ht);
 
-    // host-side tables: spheres sorted by link, pairs remapped, raw doubles
-    std::vector<int> order(pb.M);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return r->sphere_link[a] < r->sphere_link[b]; });
-    std::vector<int> rank(pb.M);
-    for (int i = 0; i < pb.M; ++i) rank[order[i]] = i;
-    std::vector<float> sph(4 * std::max(pb.M, 1), 0.f);
-    std::vector<int> first(pb.d + 2, 0);
-    for (int i = 0; i < pb.M; ++i) {
-        for (int k = 0; k < 4; ++k) sph[4 * i + k] = static_cast<float>(r->spheres[4 * order[i] + k]);
-        first[r->sphere_link[order[i]] + 1]++;
-    }
-    for (int f = 0; f <= pb.d; ++f) first[f + 1] += first[f];
-    std::vector<uint32_t> pairs(std::max(pb.P, 1), 0u);
-    for (int k = 0; k < pb.P; ++k) {
-        uint32_t a = rank[r->pairs[2 * k]], b = rank[r->pairs[2 * k + 1]];
-        if (a > b) std::swap(a, b);
-        pairs[k] = a | (b << 16);
-    }
-    std::vector<float> boxes(6 * std::max(pb.B, 1), 0.f), ws(4 * std::max(pb.O, 1), 0.f);
-    for (int i = 0; i < 6 * pb.B; ++i) boxes[i] = static_cast<float>(w->boxes[i]);
-    for (int i = 0; i < 4 * pb.O; ++i) ws[i] = static_cast<float>(w->spheres[i]);
-    std::vector<double> raw;
-    raw.insert(raw.end(), r->dh, r->dh + 4 * pb.d);
-    raw.insert(raw.end(), r->q_min, r->q_min + pb.d);
-    raw.insert(raw.end(), r->q_max, r->q_max + pb.d);
-    raw.insert(raw.end(), p->dt, p->dt + pb.H);
-
-    // scratch plan: the model tables, then the N x H x d control batch
-    const TablePlan t = plan_tables(pb, std::max(pb.B, 1), std::max(pb.O, 1), static_cast<int>(raw.size()));
-    pb.table_bytes = static_cast<int>(t.prefix);  // the shared-memory plan below depends on it
+    // scratch plan: the model tables (with the Halton noise when that sampler
+    // is chosen), then the N x H x d control batch
+    const TablePlan t = plan_tables(pb, std::max(pb.B, 1), std::max(pb.O, 1), static_cast<int>(ht.raw.size()));
     const size_t u_off = (t.total + 255) & ~size_t(255);
     const size_t u_bytes = sizeof(float) * size_t(pb.N) * pb.H * pb.d;
     if (u_off + u_bytes > STORM_NOALLOC_SCRATCH_BYTES) {
@@ -3023,7 +3086,6 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
                 u_off + u_bytes, STORM_NOALLOC_SCRATCH_BYTES);
         return STORM_ERR_INVALID_ARG;
     }
-    const RolloutLayout L = rollout_layout(pb);
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
@@ -3037,51 +3099,18 @@ extern "C" int storm_rollout_costs_noalloc(const storm_robot* r, const storm_wor
         return rc;
     }
     char* base = static_cast<char*>(addr);
-    pb.dhx = reinterpret_cast<float*>(base + t.dhx);
-    pb.qlo = reinterpret_cast<float*>(base + t.qlo);
-    pb.qhi = reinterpret_cast<float*>(base + t.qhi);
-    pb.sph = reinterpret_cast<float4*>(base + t.sph);
-    pb.link_first = reinterpret_cast<int*>(base + t.first);
-    pb.pairs = reinterpret_cast<uint32_t*>(base + t.pairs);
-    pb.boxes = reinterpret_cast<float*>(base + t.boxes);
-    pb.wsph = reinterpret_cast<float4*>(base + t.wsph);
-    pb.dt = reinterpret_cast<float*>(base + t.dt);
-    pb.gpow = reinterpret_cast<float*>(base + t.gpow);
-    pb.vmax = reinterpret_cast<float*>(base + t.vmax);
-    pb.basis = reinterpret_cast<float*>(base + t.basis);
-    pb.halton = reinterpret_cast<float*>(base + t.halton);
-    pb.tables = reinterpret_cast<const uint4*>(base);
-    pb.table_bytes = static_cast<int>(t.prefix);
-    int* d_prime = reinterpret_cast<int*>(base + t.prime);
-    double* d_raw = reinterpret_cast<double*>(base + t.raw);
     float* d_u = reinterpret_cast<float*>(base + u_off);
-
-    cudaError_t e = cudaSuccess;
-    auto put = [&](void* dst, const void* src, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
-    };
-    put(const_cast<float4*>(pb.sph), sph.data(), 16 * sph.size() / 4);
-    put(const_cast<int*>(pb.link_first), first.data(), 4 * first.size());
-    put(const_cast<uint32_t*>(pb.pairs), pairs.data(), 4 * pairs.size());
-    put(const_cast<float*>(pb.boxes), boxes.data(), 4 * boxes.size());
-    put(const_cast<float4*>(pb.wsph), ws.data(), 4 * ws.size());
-    put(d_raw, raw.data(), 8 * raw.size());
+    // every table the rollout reads is rewritten here (host copies, then the
+    // set-up kernels), so nothing an earlier call left in the scratch is used
+    cudaError_t e = upload_problem(pb, ht, base, t, stream);
     if (e == cudaSuccess) {
-        InitArgs ia{d_raw, d_raw + 4 * pb.d, d_raw + 5 * pb.d, d_raw + 6 * pb.d, p->k_jl,
-                    p->qdd_max, p->gamma};
-        k_init_tables<<<1, 64, 0, stream>>>(pb, ia);
-        if (pb.sampler == STORM_SAMPLER_HALTON) {
-            const int D = pb.S * pb.d;
-            k_primes<<<(D + 127) / 128, 128, 0, stream>>>(D, d_prime);
-            const size_t total = size_t(pb.N) * pb.S * pb.d;
-            k_halton<<<static_cast<unsigned>((total + 255) / 256), 256, 0, stream>>>(
-                pb.N, pb.S, pb.d, d_prime, p->halton_scramble, pb.seed_lo, pb.seed_hi,
-                const_cast<float*>(pb.halton));
-        }
+        pb.mu = const_cast<float*>(mean_dev);  // read only by the rollout kernel
+        pb.sigma = const_cast<float*>(sigma_dev);
+        const RolloutLayout L = rollout_layout(pb);
         RolloutOut out{d_u, nullptr, nullptr, nullptr, nullptr, nullptr, Ctot_dev};
         const int grid = (pb.N + pb.ppc - 1) / pb.ppc;
         k_rollout<<<grid, kThreads, L.bytes, stream>>>(pb, out, state_dev, goal_dev, nullptr,
-                                                      static_cast<int>(step), iter, 0);
+                                                      static_cast<int>(step), iter);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
@@ -3639,7 +3668,7 @@ void mlp_free(storm_mlp* m)
     float* fl[] = {m->p, m->g, m->m, m->v, m->loss, m->th_b, m->t_b, m->loss_hist};
     for (auto* q : fl)
         if (q) cudaFree(q);
-    __nv_bfloat16* bf[] = {m->w1, m->w2, m->w2t, m->w3, m->w3t};
+    __nv_bfloat16* bf[] = {m->w1, m->w2, m->w2t, m->w3, m->w3t, m->w1p, m->w2p, m->w3p};
     for (auto* q : bf)
         if (q) cudaFree(q);
     if (m->idx) cudaFree(m->idx);
@@ -3695,6 +3724,10 @@ int storm_mlp_create_arch(uint64_t seed, int arch, void* cuda_stream, storm_mlp*
         }
     };
     try_(cudaGetDevice(&m->device), "cudaGetDevice");
+    try_(cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device), "SM count");
+    try_(cudaFuncSetAttribute(k_mlp_forward_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(tc::kTileSmem)),
+         "fused forward shared memory");
     if (cuda_stream) {
         m->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -3714,6 +3747,9 @@ int storm_mlp_create_arch(uint64_t seed, int arch, void* cuda_stream, storm_mlp*
     try_(cudaMalloc(&m->w2t, hh), "w2t");
     try_(cudaMalloc(&m->w3, hh), "w3");
     try_(cudaMalloc(&m->w3t, hh), "w3t");
+    try_(cudaMalloc(&m->w1p, sizeof(__nv_bfloat16) * kMlpHid * kMlpIn), "w1p");
+    try_(cudaMalloc(&m->w2p, hh), "w2p");
+    try_(cudaMalloc(&m->w3p, hh), "w3p");
     if (rc) return fail_m(rc);
     try_(cudaMemsetAsync(m->m, 0, P, m->stream), "memset");
     try_(cudaMemsetAsync(m->v, 0, P, m->stream), "memset");
@@ -3756,7 +3792,26 @@ int storm_mlp_set_params(storm_mlp* m, const float* params)
     return STORM_OK;
 }
 
+int storm_mlp_wait_probe(storm_mlp* m, unsigned int limit_us)
+{
+    if (!m || limit_us < 1 || limit_us > 1000000) return STORM_ERR_INVALID_ARG;
+    tc::k_wait_probe<<<1, tc::kThreads, 0, m->stream>>>(m->err, 1000ull * limit_us);
+    MK(cudaGetLastError());
+    return mlp_check_err(m);
+}
+
 int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev)
+{
+    if (!m || !theta_dev || !out_dev || count < 1 || count > STORM_MLP_MAX_ROWS || dof < 1 || dof > 7)
+        return STORM_ERR_INVALID_ARG;
+    const int tiles = (count + tc::kBM - 1) / tc::kBM;
+    k_mlp_forward_tiles<<<std::min(tiles, m->sms), tc::tile_threads(kFwdEpi), tc::kTileSmem, m->stream>>>(
+        mlp_view(m), theta_dev, count, dof, out_dev);
+    MK(cudaGetLastError());
+    return mlp_check_err(m);
+}
+
+int storm_mlp_predict_layers(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev)
 {
     if (!m || !theta_dev || !out_dev || count < 1 || count > STORM_MLP_MAX_ROWS || dof < 1 || dof > 7)
         return STORM_ERR_INVALID_ARG;
@@ -3858,33 +3913,38 @@ int storm_self_distance(storm_handle* h, const float* theta_dev, int count, floa
     return STORM_OK;
 }
 
-int storm_set_surrogate_cost(storm_handle* h, storm_mlp* mlp)
-{
-    const int rc = storm_set_surrogate(h, mlp, 0.0);
-    if (rc) return rc;
-    h->pb.self_direct = mlp ? 1 : 0;
-    return build_graphs(h);
-}
-
-int storm_set_surrogate(storm_handle* h, storm_mlp* mlp, double margin)
+// Self-collision mode (Problem::self_mode) with `mlp`: check the fused kernel's
+// shared-memory plan against the device, then re-capture the step graph.
+static int set_self_mode(storm_handle* h, storm_mlp* mlp, int mode, double margin)
 {
     if (!h || std::isnan(margin)) return fail(h, STORM_ERR_INVALID_ARG, "bad argument");
     CK(cudaStreamSynchronize(h->stream));
-    h->mlp = mlp;
-    h->pb.self_direct = 0;
     if (mlp) {
-        const int rows = h->pb.N * h->pb.H;
-        const int R = (rows + tc::kBM - 1) / tc::kBM * tc::kBM;
-        if (!h->mlp_buf) h->mlp_buf = new MlpBuffers();
-        CK(mlp_reserve(*h->mlp_buf, R, false));
-        if (!h->d_theta) CK(cudaMalloc(&h->d_theta, sizeof(float) * size_t(rows) * h->pb.d));
-        if (!h->d_pred) CK(cudaMalloc(&h->d_pred, sizeof(float) * R));
-        h->pb.self_pred = h->d_pred;
-        h->pb.self_margin = static_cast<float>(margin);
-    } else {
-        h->pb.self_pred = nullptr;
+        if (mlp->device != h->device) return fail(h, STORM_ERR_INVALID_ARG, "network on another device");
+        const MlpRolloutPlan P = mlp_rollout_plan(h->pb);
+        int optin = 0;
+        cudaFuncAttributes fa;
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+        CK(cudaFuncGetAttributes(&fa, k_rollout_mlp));
+        if (static_cast<size_t>(P.bytes) + fa.sharedSizeBytes > static_cast<size_t>(optin))
+            return fail(h, STORM_ERR_INVALID_ARG, "problem too large for the fused network rollout");
+        CK(cudaFuncSetAttribute(k_rollout_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - static_cast<int>(fa.sharedSizeBytes)));
+        h->mlp_smem = P.bytes;
+        // the network's own stream may still be writing its weights
+        CK(cudaStreamSynchronize(mlp->stream));
     }
+    h->mlp = mlp;
+    h->pb.self_mode = mlp ? mode : 0;
+    h->pb.self_margin = static_cast<float>(margin);
     return build_graphs(h);
+}
+
+int storm_set_surrogate_cost(storm_handle* h, storm_mlp* mlp) { return set_self_mode(h, mlp, 2, 0.0); }
+
+int storm_set_surrogate(storm_handle* h, storm_mlp* mlp, double margin)
+{
+    return set_self_mode(h, mlp, 1, margin);
 }
 
 }  // extern "C"

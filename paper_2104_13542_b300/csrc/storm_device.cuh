@@ -17,6 +17,7 @@ constexpr int kThreads = 256;        // default rollout CTA size
 constexpr int kMaxThreads = 512;     // largest rollout CTA size the tuner may pick
 constexpr int kUpdateThreads = 512;  // distribution-update CTA size (one CTA per horizon step)
 constexpr int kLinkPairs = (kMaxDof + 1) * kMaxDof / 2;  // frame pairs (la < lb) of a chain
+constexpr int kMlpRows = 128;       // rows of a tensor-core tile of the self-collision network
 
 // Position of frame pair (la, lb), la < lb <= kMaxDof, in lexicographic order.
 __host__ __device__ constexpr int link_pair_index(int la, int lb)
@@ -61,9 +62,12 @@ struct Problem {
     const float* halton;     // N x S x d normal noise (Halton sampler only)
     float* mu;               // H x d
     float* sigma;            // d
-    const float* self_pred;  // N x H surrogate outputs (nullable)
-    float self_margin;       // exact self check only where self_pred < self_margin
-    int self_direct;         // 1: self term = max(0, self_pred) (Eq. 13), no exact check
+    // learned self collision (Sec. 4.2), evaluated inside the rollout kernel: 0 the exact
+    // check; 1 the exact check only where the network's predicted distance is below
+    // self_margin (elsewhere the self term is 0); 2 the self term is max(0, network), the
+    // network predicting the penetration depth (Eq. 13), no exact check
+    int self_mode;
+    float self_margin;
     // pair blocks of frames (la, lb), la < lb, are [lp_begin[t], lp_begin[t + 1]) with
     // t = link_pair_index(la, lb); the blocks are sorted by (la, lb)
     uint16_t lp_begin[kLinkPairs + 1];

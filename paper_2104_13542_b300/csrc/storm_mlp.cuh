@@ -76,21 +76,37 @@ __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
 }
 
-// Wait for the phase with parity `parity` to complete; false after kWaitNs.
+// One non-blocking probe: has the phase with parity `parity` completed?
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with parity `parity` to complete; false once limit_ns
+// nanoseconds of %globaltimer have passed without it.  A phase that has
+// already completed costs one probe; the timer (slow to read) is read only
+// once the wait is real, and then every 64 probes.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t addr, uint32_t parity, unsigned long long limit_ns)
+{
+    if (mbar_try(addr, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (uint32_t n = 1;; ++n) {
+        if (mbar_try(addr, parity)) return true;
+        if ((n & 63u) == 0u && now_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// The bound every tensor-core wait of the library uses.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
 {
-    const unsigned long long t0 = now_ns();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.b32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (now_ns() - t0 > kWaitNs) return false;
-    }
+    return mbar_wait_for(addr, parity, kWaitNs);
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
@@ -291,7 +307,9 @@ template <int BN>
 __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, int row, int warp,
                                               const float* bias, const float* head_w)
 {
-    float yacc = 0.f;
+    // the dot head sums each half of the columns in column order and adds the
+    // halves (the order of the whole-network tile's two epilogue warps)
+    float yacc = 0.f, yacc0 = 0.f;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
@@ -316,9 +334,14 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, 
                     if (!(__bfloat162float(mb[i]) > 0.f)) v[q * 8 + i] = 0.f;
             }
         }
-        if (head_w)
+        if (head_w) {
+            if (c0 == BN / 2) {
+                yacc0 = yacc;
+                yacc = 0.f;
+            }
 #pragma unroll
             for (int i = 0; i < 32; ++i) yacc = fmaf(head_w[c0 + i], v[i], yacc);
+        }
         if (g.out_f) {
             float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
 #pragma unroll
@@ -340,7 +363,7 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, 
                 g.out_bfT[static_cast<size_t>(c0 + i) * g.ldoT + row] = __float2bfloat16_rn(v[i]);
         }
     }
-    if (head_w) g.head_y[row] = *g.head_b + yacc;
+    if (head_w) g.head_y[row] = *g.head_b + (yacc0 + yacc);
 }
 
 template <int BN>
@@ -650,6 +673,405 @@ __global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
                      : "memory");
 }
 
+// Failure-path check of the bounded waits: one CTA takes TMEM and waits, with
+// the same routine as every tensor-core kernel above, on an mbarrier that no
+// copy or MMA will ever complete.  The wait gives up after limit_ns; the CTA
+// then sets *err (as the real kernels do), frees its TMEM and ends, so the
+// context stays usable.  Nothing here faults or hangs.
+__global__ void __launch_bounds__(kThreads, 1) k_wait_probe(int* err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(32)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const bool ok = __syncthreads_and(mbar_wait_for(smem_u32(&mbar), 0u, limit_ns));
+    if (!ok && err && threadIdx.x == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
+    (void)lane;
+}
+
+// ---------------------------------------------------------------- the whole network on one tile
+// The three layers of a network on one 128-row tile with the activations kept
+// on chip.  The layer-1 inputs sit in a small shared-memory tile; each later
+// layer's BF16 inputs in one activation tile (128 rows x up to 256 columns, in
+// 32-column blocks of the core-matrix layout); the FP32 accumulators in two
+// 256-column TMEM regions that the layers alternate between.  The weights
+// stream from global memory (L2) through a ring of four shared-memory buffers,
+// one 32-column block per bulk asynchronous copy (cp.async.bulk, completion
+// counted in bytes on an mbarrier), each block already packed in the layout
+// the MMA descriptors read.
+//
+// Roles (warp-specialised, no CTA-wide barrier inside a tile):
+//   epilogue warps (kEpi = 4 or 8; warp w drains TMEM lane quarter w % 4, and
+//     with 8 warps half the columns of each block): wait for a layer's
+//     accumulator (mbarrier `done`), then write the next layer's inputs one
+//     32-column block at a time (bias, ReLU, BF16), announcing each block on
+//     its own mbarrier a[j]; after layer 3 the head (bias, ReLU, linear output).
+//   one issuing thread (lane 0 of warp kEpi): keeps the weight ring full and
+//     issues each block's MMAs as soon as its inputs are announced and its
+//     weights have landed, so the tensor core works while the epilogue goes on.
+// The MMA sequence (K steps of 16 in column order) and the epilogue arithmetic
+// are those of k_gemm_ws, so a tile computes bitwise what the layer-by-layer
+// kernels compute.
+
+// Packed BF16 weights and FP32 vectors of one network.  Blocks, each contiguous:
+//   w1p  W1, h1 x 16, core-matrix layout with 8-row groups 256 bytes apart
+//   w2p  h1 / 32 blocks, block j = W2[:, 32 j .. 32 j + 31] (h2 x 32, groups 512 bytes apart)
+//   w3p  h2 / 32 blocks of W3 (h3 x 32)
+struct MlpView {
+    const __nv_bfloat16* w1p;
+    const __nv_bfloat16* w2p;
+    const __nv_bfloat16* w3p;
+    const float* b2;
+    const float* b3;
+    const float* w4;
+    const float* b4;
+    int enc, h1, h2, h3;
+    int* err;  // set to 1 when a wait runs out
+};
+
+constexpr int kRingDepth = 4;                  // weight buffers
+constexpr int kBlockK = 32;                    // input columns per weight block of layers 2 and 3
+constexpr int kMaxBlocks = 256 / kBlockK;      // activation blocks
+constexpr int kTileRing = 256 * kBlockK * 2;   // one staged weight block (at most 256 x 32 BF16)
+constexpr int kTileA1 = kBM * 16 * 2;          // layer-1 inputs
+constexpr int kTileSub = kBM * kBlockK * 2;    // one 32-column block of the activations
+constexpr int kTileA = kBM * 256 * 2;          // the activation tile
+constexpr int kTileVec = 3 * 256 * 4 + 2 * kBM * 4;  // b2, b3, w4; the head's two partial sums per row
+// the engine's shared memory: ring | layer-1 inputs | activations | vectors | head partials
+constexpr int kOffA1 = kRingDepth * kTileRing;
+constexpr int kOffA = kOffA1 + kTileA1;
+constexpr int kOffVec = kOffA + kTileA;
+constexpr size_t kTileSmem = kOffVec + kTileVec;
+// mbarriers: full[kRingDepth], empty[kRingDepth], done, a1, a[kMaxBlocks]
+constexpr int kTileBars = 2 * kRingDepth + 2 + kMaxBlocks;
+constexpr uint32_t kTileCols = 512;            // two accumulators
+
+// Threads of a CTA running the engine with kEpi epilogue warps: those, then the issuing warp.
+__host__ __device__ constexpr int tile_threads(int kEpi) { return (kEpi + 1) * 32; }
+
+__host__ __device__ inline int mlp_blocks(const MlpView& v) { return 1 + v.h1 / kBlockK + v.h2 / kBlockK; }
+
+// Start the bulk copy of block b of the network (0 = W1, then W2's, then W3's)
+// into the ring buffer at dst, completing on full_bar.  One thread.
+__device__ __forceinline__ void mlp_issue_block(const MlpView& v, int b, uint32_t dst, uint32_t full_bar)
+{
+    const int n2 = v.h1 / kBlockK;
+    const __nv_bfloat16* src;
+    uint32_t bytes;
+    if (b == 0) {
+        src = v.w1p;
+        bytes = static_cast<uint32_t>(v.h1) * 16 * 2;
+    } else if (b <= n2) {
+        src = v.w2p + static_cast<size_t>(b - 1) * v.h2 * kBlockK;
+        bytes = static_cast<uint32_t>(v.h2) * kBlockK * 2;
+    } else {
+        src = v.w3p + static_cast<size_t>(b - 1 - n2) * v.h3 * kBlockK;
+        bytes = static_cast<uint32_t>(v.h3) * kBlockK * 2;
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full_bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(full_bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cta(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// Pipeline state of one CTA's tiles.  Weight blocks are numbered across tiles:
+// block g lives in ring buffer g % kRingDepth and completes phase
+// (g / kRingDepth) & 1 of full[that buffer] (landed) and of empty[that buffer]
+// (its MMAs done).  Barrier addresses are computed, not indexed, so that the
+// state stays in registers.  next / issued / apar / tiles belong to the issuing
+// thread; layers (phases of `done`) to the epilogue threads.
+struct MlpTiles {
+    uint32_t ring, sA1, sA;  // shared addresses
+    uint32_t bars;           // the mbarriers, 8 bytes apart in the order above
+    uint32_t tmem;           // kTileCols columns
+    int next;                // next weight block to multiply
+    int issued;              // blocks whose copy has been started
+    int total;               // blocks this CTA will multiply in all
+    int layers;              // layers completed
+    uint32_t apar;           // bit j: parity of a[j]'s next phase
+    int tiles;               // tiles issued
+};
+
+__device__ __forceinline__ uint32_t tile_full(const MlpTiles& t, int b) { return t.bars + 8 * b; }
+__device__ __forceinline__ uint32_t tile_empty(const MlpTiles& t, int b) { return t.bars + 8 * (kRingDepth + b); }
+__device__ __forceinline__ uint32_t tile_done(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth); }
+__device__ __forceinline__ uint32_t tile_a1(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth + 1); }
+__device__ __forceinline__ uint32_t tile_a(const MlpTiles& t, int j) { return t.bars + 8 * (2 * kRingDepth + 2 + j); }
+
+// Every thread of the CTA: addresses, then (warp 0) the TMEM columns and (the
+// issuing thread) the barriers and the first kRingDepth block copies.  The
+// caller then runs the TMEM-allocation fence / barrier / fence sequence and
+// reads *tmem_slot.
+template <int kEpi>
+__device__ __forceinline__ void mlp_tiles_init(MlpTiles& t, const MlpView& v, uint32_t smem_base, uint64_t* bars,
+                                               uint32_t* tmem_slot, int total)
+{
+    t.ring = smem_base;
+    t.sA1 = smem_base + kOffA1;
+    t.sA = smem_base + kOffA;
+    t.bars = smem_u32(bars);
+    t.tmem = 0;
+    t.next = t.issued = t.layers = t.tiles = 0;
+    t.apar = 0u;
+    t.total = total;
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTileCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == kEpi * 32) {
+        for (int b = 0; b < 2 * kRingDepth + 1; ++b) mbar_init(t.bars + 8 * b, 1);  // ring, done: one arrival
+        mbar_init(tile_a1(t), kBM / 32);                                             // the four encoding warps
+        for (int j = 0; j < kMaxBlocks; ++j) mbar_init(tile_a(t, j), kEpi);         // every epilogue warp
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const int nb = mlp_blocks(v);
+        for (; t.issued < kRingDepth && t.issued < t.total; ++t.issued)
+            mlp_issue_block(v, t.issued % nb, t.ring + t.issued * kTileRing, tile_full(t, t.issued));
+    }
+}
+
+// The issuing thread: the MMAs of the next weight block (A block at a0 with
+// 8-row groups sbo_a bytes apart, kb input columns) into accumulator d,
+// committed to the block's empty barrier; then the buffer of the block before
+// it, whose MMAs were issued earlier, is refilled with the block kRingDepth - 1
+// ahead.  False when a wait ran out.
+__device__ __forceinline__ bool mlp_mma_block(const MlpView& v, MlpTiles& t, uint32_t a0, uint32_t sbo_a, int kb,
+                                              uint32_t d, uint32_t idesc, bool first)
+{
+    const int g = t.next, buf = g % kRingDepth;
+    if (!mbar_wait(tile_full(t, buf), (g / kRingDepth) & 1)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t b0 = t.ring + buf * kTileRing, sbo_b = (kb / 8) * 128;
+    for (int kk = 0; kk < kb / 16; ++kk) {
+        const uint64_t da = smem_desc(a0 + kk * 256, 128, sbo_a);
+        const uint64_t db = smem_desc(b0 + kk * 256, 128, sbo_b);
+        const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tile_empty(t, buf))
+                 : "memory");
+    ++t.next;
+    if (g >= 1 && t.issued < t.total) {
+        const int gp = g - 1, bp = gp % kRingDepth;
+        if (!mbar_wait(tile_empty(t, bp), (gp / kRingDepth) & 1)) return false;
+        mlp_issue_block(v, t.issued % mlp_blocks(v), t.ring + bp * kTileRing, tile_full(t, bp));
+        ++t.issued;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mlp_commit_done(const MlpTiles& t)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tile_done(t))
+                 : "memory");
+}
+
+// The issuing thread's part of one tile: layer 1 once the encoding warps have
+// announced the inputs, then each block of layers 2 and 3 once the epilogue
+// warps have announced it, each layer committed to `done`.  False when a wait
+// ran out (the epilogue warps then time out on `done`).
+__device__ __forceinline__ bool mlp_tile_issue(const MlpView& v, MlpTiles& t)
+{
+    const uint32_t RA = t.tmem, RB = t.tmem + 256;  // layers 1 and 3 | layer 2
+    if (!mbar_wait(tile_a1(t), t.tiles & 1)) return false;
+    ++t.tiles;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!mlp_mma_block(v, t, t.sA1, 256, 16, RA, instr_desc(kBM, v.h1), true)) return false;
+    mlp_commit_done(t);
+    for (int L = 2; L <= 3; ++L) {
+        const int K = L == 2 ? v.h1 : v.h2, N = L == 2 ? v.h2 : v.h3;
+        const uint32_t idesc = instr_desc(kBM, N);
+        for (int j = 0; j < K / kBlockK; ++j) {
+            if (!mbar_wait(tile_a(t, j), (t.apar >> j) & 1u)) return false;
+            t.apar ^= 1u << j;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!mlp_mma_block(v, t, t.sA + j * kTileSub, kTileSub / 16, kBlockK, L == 2 ? RB : RA, idesc, j == 0))
+                return false;
+        }
+        mlp_commit_done(t);
+    }
+    return true;
+}
+
+// TMEM -> registers, 16 consecutive FP32 columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One thread's 16 columns of one row of a 32-column activation block: the
+// accumulator's columns at taddr, + bias (nullable), ReLU, BF16, as two 8-column
+// core-matrix rows at dst (the second 128 bytes after the first).
+__device__ __forceinline__ void mlp_act_half(uint32_t taddr, const float* bias, uint32_t dst)
+{
+    uint32_t r[16];
+    tmem_ld16(taddr, r);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float x0 = __uint_as_float(r[q * 8 + 2 * i]), x1 = __uint_as_float(r[q * 8 + 2 * i + 1]);
+            if (bias) {
+                x0 += bias[q * 8 + 2 * i];
+                x1 += bias[q * 8 + 2 * i + 1];
+            }
+            x0 = fmaxf(x0, 0.f);
+            x1 = fmaxf(x1, 0.f);
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(x0), b1 = __float2bfloat16_rn(x1);
+            w[i] = static_cast<uint32_t>(__bfloat16_as_ushort(b0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b1)) << 16);
+        }
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + q * 128), "r"(w[0]), "r"(w[1]),
+                     "r"(w[2]), "r"(w[3])
+                     : "memory");
+    }
+}
+
+// Every epilogue thread: wait until the layer the issuing thread committed to
+// `done` has completed.  False (on this thread) when the wait ran out.
+__device__ __forceinline__ bool mlp_wait_layer(MlpTiles& t)
+{
+    const bool ok = mbar_wait(tile_done(t), t.layers & 1);
+    ++t.layers;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return ok;
+}
+
+// Announce an activation block (or the layer-1 inputs) to the issuing thread:
+// this warp's generic shared-memory writes made visible to the tensor core's
+// async proxy, its TMEM reads ordered before the MMAs that follow, one arrival
+// per warp.
+__device__ __forceinline__ void mlp_announce(uint32_t bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive_cta(bar);
+}
+
+// The epilogue warps' part of one tile, after the encoding warps (0-3) have
+// written the layer-1 inputs to t.sA1 and announced them on a1: layers 1 and 2's
+// outputs into the activation blocks, then the head.  Warp w drains TMEM lane
+// quarter w % 4 (row = 32 (w % 4) + lane); with 8 warps, half w / 4 of each
+// block's columns.  The head sums each half of layer 3's columns in column
+// order and adds the halves; rows 0..127 get their output in *y (threads
+// 0..127).  bar_id: a named barrier free for the kEpi warps (8 warps only).
+// False (on every epilogue thread) when a wait ran out.
+template <int kEpi>
+__device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t, const float* s_b2, const float* s_b3,
+                                                  const float* s_w4, float* s_part, float b4, float* y)
+{
+    static_assert(kEpi == 4 || kEpi == 8, "four or eight epilogue warps");
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, row = quarter * 32 + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+    const uint32_t RA = t.tmem, RB = t.tmem + 256;
+    bool ok = mlp_wait_layer(t);  // layer 1
+    for (int L = 2; L <= 3 && ok; ++L) {
+        const int K = L == 2 ? v.h1 : v.h2;
+        const uint32_t src = (L == 2 ? RA : RB) + lane_off;
+        const float* bias = L == 2 ? nullptr : s_b2;
+        for (int j = 0; j < K / kBlockK; ++j) {
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                if (kEpi == 8 && hf != (warp >> 2)) continue;
+                const int c = j * kBlockK + 16 * hf;
+                mlp_act_half(src + c, bias ? bias + c : nullptr,
+                             t.sA + j * kTileSub + (row >> 3) * (kTileSub / 16) + (row & 7) * 16 + (2 * hf) * 128);
+            }
+            mlp_announce(tile_a(t, j));
+        }
+        ok = mlp_wait_layer(t);  // layer L
+    }
+    // head: each half of layer 3's columns in column order, then the halves added
+    const int hh = v.h3 / 2;
+    float part[2] = {0.f, 0.f};
+    if (ok) {
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            if (kEpi == 8 && hf != (warp >> 2)) continue;
+            float yacc = 0.f;
+#pragma unroll 1
+            for (int c0 = hf * hh; c0 < (hf + 1) * hh; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(RA + lane_off + c0, r);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float x = fmaxf(__uint_as_float(r[i]) + s_b3[c0 + i], 0.f);
+                    yacc = fmaf(s_w4[c0 + i], x, yacc);
+                }
+            }
+            part[hf] = yacc;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");  // these TMEM reads before the next tile's MMAs
+    if (kEpi == 8) {
+        if (warp >= 4) s_part[row] = part[1];
+        asm volatile("bar.sync 1, %0;" ::"n"(kEpi * 32) : "memory");
+        if (warp < 4) part[1] = s_part[row];
+        asm volatile("bar.sync 1, %0;" ::"n"(kEpi * 32) : "memory");  // s_part free again
+    }
+    if (tid < kBM) *y = b4 + (part[0] + part[1]);
+    return ok;
+}
+
+// AND of v over the `threads` threads meeting at named barrier `id`.
+__device__ __forceinline__ bool bar_and(int id, int threads, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, %2, %3, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+// After a failed tile, the issuing thread: wait (bounded) for the copies and
+// MMAs still in flight, so that nothing writes this CTA's shared memory or TMEM
+// once it moves on.
+__device__ __forceinline__ void mlp_tiles_drain(MlpTiles& t)
+{
+    for (int g = t.next; g < t.issued; ++g) mbar_wait(tile_full(t, g % kRingDepth), (g / kRingDepth) & 1);
+    if (t.next > 0) {
+        const int g = t.next - 1;
+        mbar_wait(tile_empty(t, g % kRingDepth), (g / kRingDepth) & 1);
+    }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- MLP helpers
@@ -682,6 +1104,30 @@ __host__ __device__ inline MlpArch mlp_arch(int enc, int h1, int h2, int h3)
     return a;
 }
 
+// The encoded inputs of one configuration theta (dof <= 7 joints).
+__device__ __forceinline__ void mlp_encode_row(const float* th, int dof, int enc, float (&v)[kMlpIn])
+{
+#pragma unroll
+    for (int i = 0; i < kMlpIn; ++i) v[i] = 0.f;
+    if (enc == 1) {
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            if (j < dof) {
+                float sj, cj;
+                sincosf(th[j], &sj, &cj);
+                v[j] = sj;
+                v[7 + j] = cj;
+            }
+        }
+        v[14] = 1.f;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+            if (j < dof) v[j] = th[j] / 3.f;
+        v[7] = 1.f;
+    }
+}
+
 // Inputs of the encoding; rows count..rows_pad-1 are zero.
 // x: rows_pad x 16; xT (nullable): 16 x rows_pad.
 __global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof, int rows_pad, int enc,
@@ -690,21 +1136,11 @@ __global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows_pad) return;
     float v[kMlpIn];
-#pragma unroll
-    for (int i = 0; i < kMlpIn; ++i) v[i] = 0.f;
     if (r < count) {
-        if (enc == 1) {
-            for (int j = 0; j < dof && j < 7; ++j) {
-                float sj, cj;
-                sincosf(theta[static_cast<size_t>(r) * dof + j], &sj, &cj);
-                v[j] = sj;
-                v[7 + j] = cj;
-            }
-            v[14] = 1.f;
-        } else {
-            for (int j = 0; j < dof && j < 7; ++j) v[j] = theta[static_cast<size_t>(r) * dof + j] / 3.f;
-            v[7] = 1.f;
-        }
+        mlp_encode_row(theta + static_cast<size_t>(r) * dof, dof, enc, v);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) v[i] = 0.f;
     }
 #pragma unroll
     for (int i = 0; i < kMlpIn; ++i) {
@@ -712,6 +1148,113 @@ __global__ void k_mlp_encode(const float* __restrict__ theta, int count, int dof
         x[static_cast<size_t>(r) * kMlpIn + i] = b;
         if (xT) xT[static_cast<size_t>(i) * rows_pad + r] = b;
     }
+}
+
+// Row `row` (0..127) of a tile's layer-1 inputs (128 x 16 BF16, 8-row groups 256
+// bytes apart, the two 8-column halves 128 bytes apart) from encoded values v.
+__device__ __forceinline__ void mlp_store_input_row(uint32_t sA, int row, const float (&v)[kMlpIn])
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(v[2 * i]), b1 = __float2bfloat16_rn(v[2 * i + 1]);
+        w[i] = static_cast<uint32_t>(__bfloat16_as_ushort(b0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b1)) << 16);
+    }
+    const uint32_t a = sA + (row >> 3) * 256 + (row & 7) * 16;
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a + 128), "r"(w[4]), "r"(w[5]), "r"(w[6]),
+                 "r"(w[7])
+                 : "memory");
+}
+
+// BF16 weights (row-major, out x in) -> the packed blocks of tc::MlpView.
+__global__ void k_mlp_pack(const __nv_bfloat16* __restrict__ w1, const __nv_bfloat16* __restrict__ w2,
+                           const __nv_bfloat16* __restrict__ w3, int h1, int h2, int h3,
+                           __nv_bfloat16* __restrict__ w1p, __nv_bfloat16* __restrict__ w2p,
+                           __nv_bfloat16* __restrict__ w3p)
+{
+    constexpr int KB = tc::kBlockK;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < h1 * kMlpIn) {  // (n, k): 8-row groups of 128 elements, rows of 8, two halves of K
+        const int n = i / kMlpIn, k = i - n * kMlpIn;
+        w1p[(n >> 3) * 128 + (n & 7) * 8 + (k >> 3) * 64 + (k & 7)] = w1[i];
+    }
+    if (i < h2 * h1) {  // block k / 32: h2 x 32, 8-row groups of 256 elements
+        const int n = i / h1, k = i - n * h1, kk = k % KB;
+        w2p[static_cast<size_t>(k / KB) * h2 * KB + (n >> 3) * (8 * KB) + (n & 7) * 8 + (kk >> 3) * 64 + (kk & 7)] = w2[i];
+    }
+    if (i < h3 * h2) {
+        const int n = i / h2, k = i - n * h2, kk = k % KB;
+        w3p[static_cast<size_t>(k / KB) * h3 * KB + (n >> 3) * (8 * KB) + (n & 7) * 8 + (kk >> 3) * 64 + (kk & 7)] = w3[i];
+    }
+}
+
+// Inference on count configurations with the whole network per 128-row tile
+// (tc::mlp_tile_*): one persistent CTA per SM walks the tiles with eight
+// epilogue warps and one issuing warp; the rows' encoded inputs go straight
+// from theta into shared memory, and nothing but y is written.  y gets rows
+// 0..count-1.  Bitwise what mlp_forward computes.
+constexpr int kFwdEpi = 8;
+
+__global__ void __launch_bounds__(tc::tile_threads(kFwdEpi), 1)
+k_mlp_forward_tiles(tc::MlpView v, const float* __restrict__ theta, int count, int dof, float* __restrict__ y)
+{
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    __shared__ __align__(8) uint64_t bars[tc::kTileBars];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tiles = (count + tc::kBM - 1) / tc::kBM;
+    const int my_tiles = tiles > static_cast<int>(blockIdx.x) ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    float* s_b2 = reinterpret_cast<float*>(tile_smem + tc::kOffVec);
+    float* s_b3 = s_b2 + 256;
+    float* s_w4 = s_b3 + 256;
+    float* s_part = s_w4 + 256;
+    tc::MlpTiles t;
+    tc::mlp_tiles_init<kFwdEpi>(t, v, tc::smem_u32(tile_smem), bars, &tmem_slot, my_tiles * tc::mlp_blocks(v));
+    for (int n = tid; n < 256; n += blockDim.x) {
+        s_b2[n] = n < v.h2 ? v.b2[n] : 0.f;
+        s_b3[n] = n < v.h3 ? v.b3[n] : 0.f;
+        s_w4[n] = n < v.h3 ? v.w4[n] : 0.f;
+    }
+    const float b4 = *v.b4;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    t.tmem = tmem_slot;
+    bool ok = true;
+    if (warp == kFwdEpi) {  // the issuing warp: one thread
+        if ((tid & 31) == 0) {
+            for (int k = 0; k < my_tiles && ok; ++k) ok = tc::mlp_tile_issue(v, t);
+            if (!ok) {
+                if (v.err) atomicExch(v.err, 1);
+                tc::mlp_tiles_drain(t);
+            }
+        }
+    } else {
+        for (int k = 0; k < my_tiles && ok; ++k) {
+            const int row = (blockIdx.x + k * gridDim.x) * tc::kBM + tid;  // threads 0..127
+            if (tid < tc::kBM) {  // the four encoding warps
+                float in[kMlpIn];
+                if (row < count) {
+                    mlp_encode_row(theta + static_cast<size_t>(row) * dof, dof, v.enc, in);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < kMlpIn; ++i) in[i] = 0.f;
+                }
+                mlp_store_input_row(t.sA1, tid, in);
+                tc::mlp_announce(tc::tile_a1(t));
+            }
+            float out = 0.f;
+            ok = tc::mlp_tile_epilogue<kFwdEpi>(v, t, s_b2, s_b3, s_w4, s_part, b4, &out);
+            ok = tc::bar_and(2, kFwdEpi * 32, ok);  // the same decision on every epilogue thread
+            if (ok && tid < tc::kBM && row < count) y[row] = out;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem), "r"(tc::kTileCols) : "memory");
 }
 
 // FP32 master weights -> BF16 operands: W1, W2, W3 and the transposes W2^T (h1 x h2), W3^T (h2 x h3).

@@ -200,15 +200,21 @@ __device__ __forceinline__ void unit_sync(int unit, int threads)
 // The rollout of particle group `wg` (particles wg*PW ..) of problem pb by
 // this warp (or the kW warps of group `unit`), in the group's shared-memory
 // region ws.  kFull: the end-effector limit terms, the ball, the comb / mixed
-// filters, the Halton sampler, the Frobenius rotation cost, the surrogate
-// self-collision network and the per-item outputs of the single-stage calls are
+// filters, the Halton sampler, the Frobenius rotation cost, the learned
+// self-collision term and the per-item outputs of the single-stage calls are
 // compiled in; a problem without them (Philox noise, the default filter, the
 // quaternion rotation cost, exact self collision) runs the lean instantiation,
 // without that code in its instruction stream.
-template <int kW, bool kFull>
+// kPhase: 0 the whole rollout; 1 up to the joint states (noise, controls,
+// Eq. 7); 2 the rest, on the joint states phase 1 left in ws.  lane_pred (kFull
+// only; nullable): the learned self-collision network's output for this lane's
+// items, item slot s at lane_pred[s * kMlpRows] (pb.self_mode says how it is
+// used).
+template <int kW, bool kFull, int kPhase = 0>
 __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state, const float* __restrict__ goal,
-                                                  uint32_t step, int iter, int front_only, int wg, int unit, float* ws)
+                                                  uint32_t step, int iter, int wg, int unit, float* ws,
+                                                  const float* lane_pred = nullptr)
 {
     static_assert(kW == 1 || kW == 2 || kW == 4, "one, two or four warps per particle group");
     const WarpPlan W = warp_plan(pb, kW);
@@ -225,9 +231,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     const int self_half = kW == 4 ? role - 2 : -1;  // quad: which alternate hits; -1: all of them
     const int nw0 = wg * W.PW;  // first particle of this unit
     if (nw0 >= pb.N) return;    // uniform over the unit (all its warps)
-    if (kW == 2 && role == 1)   // (ordered before any claim by the unit barrier after the prefix)
+    if (kPhase != 2 && kW == 2 && role == 1)   // (ordered before any claim by the unit barrier after the prefix)
         for (int i = lane; i < 3 * W.SL * 32; i += 32) reinterpret_cast<int*>(ws + W.claim)[i] = 0;
-    if (kW == 1 || role == 1) {  // the block ranges, for reads at an item's own frame pairs
+    if (kPhase != 2 && (kW == 1 || role == 1)) {  // the block ranges, for reads at an item's own frame pairs
         static_assert(kLinkPairs < 32, "one lane per frame pair");
         int v = 0;
 #pragma unroll
@@ -286,7 +292,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         for (int i = lane; i < H * pb.nk; i += 32) cp_async4(s_basis + i, pb.basis + i);
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    if (do_costs) {
+    if (kPhase != 2 && do_costs) {
     // launched ordinarily, the inputs are final: their loads overlap the noise
     // (issued first: the controls wait on them)
     if (!pb.dep_launch) stage_inputs_async();
@@ -333,13 +339,13 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     // The noise depends on (seed, step, iteration) only, so under a dependent
     // launch it is drawn while the previous distribution update still runs;
     // mu and sigma are read after it has finished (from L2).
-    pdl_wait();
-    if (pb.dep_launch) {  // the wait may have dropped the prefetched tables from L1
+    if (kPhase != 2) pdl_wait();
+    if (kPhase != 2 && pb.dep_launch) {  // the wait may have dropped the prefetched tables from L1
         const char* tb = reinterpret_cast<const char*>(pb.tables);
         for (int o = lane * 128; o < pb.table_bytes; o += 32 * 128)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(tb + o));
     }
-    if (do_costs) {
+    if (kPhase != 2 && do_costs) {
     if (pb.dep_launch)
         stage_inputs();  // after the previous update has finished
     else
@@ -401,8 +407,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     if (kFull && out.theta_dot)
         for (int i = lane; i < np_w * HD; i += 32) out.theta_dot[static_cast<size_t>(nw0) * HD + i] = s_thd[i];
     }
-    if (kW > 1) unit_sync(unit, kW * 32);  // the other warps read the controls and joint states
-    if (front_only) return;
+    if (kPhase != 2 && kW > 1) unit_sync(unit, kW * 32);  // the other warps read the controls and joint states
+    if (kPhase == 1) return;
 
     // ---- per-problem constants in registers
     int first[kMaxDof + 2];
@@ -433,7 +439,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     const bool want_ee = kFull && (pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms);
     const bool ball_on = kFull && pb.ball && pb.w_ball != 0.f;
     float* s_ba = ws + W.ba;
-    const float* pred = kFull ? pb.self_pred : nullptr;
+    const float* pred = kFull && pb.self_mode != 0 ? lane_pred : nullptr;
     const int NO = pb.B + pb.O;
 
     for (int slot = 0; slot < W.SL; ++slot) {
@@ -684,8 +690,9 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         // (register tests over the compile-time list of pairs), then their
         // pair blocks exactly; then the leftover pairs
         float dself = 0.f;
-        const bool do_self = do_selfc && valid && !(pred && (pb.self_direct || pred[gi] >= pb.self_margin));
-        if (valid && pred && pb.self_direct) dself = fmaxf(0.f, pred[gi]);  // Eq. 13's learned term
+        const float pv = pred && valid ? pred[slot * kMlpRows] : 0.f;
+        const bool do_self = do_selfc && valid && !(pred && (pb.self_mode == 2 || pv >= pb.self_margin));
+        if (valid && pred && pb.self_mode == 2) dself = fmaxf(0.f, pv);  // Eq. 13's learned term
         uint32_t lp_hit = 0u;  // bit t: frame pair t has blocks and its bounds overlap
         // pair: B publishes the item's mask, then works from its first pair, A
         // from its last; each announces a pair before testing it and stops where
@@ -893,7 +900,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
 template <int kW, bool kFull>
 __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1)
 k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
-               const StepState* __restrict__ st, int step_override, int iter, int front_only)
+               const StepState* __restrict__ st, int step_override, int iter)
 {
     extern __shared__ __align__(16) float wsm[];
     const WarpPlan W = warp_plan(pb, kW);
@@ -902,6 +909,6 @@ k_rollout_warp(Problem pb, RolloutOut out, const float* __restrict__ state, cons
     const int units = (blockDim.x >> 5) / kW;
     pdl_trigger();
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
-    rollout_warp_body<kW, kFull>(pb, out, state, goal, step, iter, front_only, blockIdx.x * units + unit, unit,
+    rollout_warp_body<kW, kFull>(pb, out, state, goal, step, iter, blockIdx.x * units + unit, unit,
                              wsm + unit * W.floats);
 }

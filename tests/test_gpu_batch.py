@@ -137,3 +137,40 @@ def test_full_size_batch_runs():
                 r2 = c.step(states[i], goals[i])[0]
             assert np.array_equal(cmds[i], r1) and np.array_equal(cmds2[i], r2)
     assert len(cmds) == 256 and all(np.all(np.isfinite(c)) for c in cmds)
+
+
+def test_full_size_batch_matches_oracle():
+    """The 256-instance uneven batch at its drawn sizes (N up to 1024, H up to 50,
+    6 and 7 joints, 0 to 64 obstacles), stepped once as one batch, against the
+    oracle's control step of a spread of its instances: the largest N x H, the
+    largest N and H, both joint counts, the most and the fewest obstacles, and
+    the smallest N."""
+    wls = W.config_batch(0, 256)
+    states = [f32(wl.state) for wl in wls]
+    goals = np.stack([f32(wl.goal) for wl in wls])
+    with BatchController([w.robot for w in wls], [w.world for w in wls],
+                         [w.params for w in wls]) as b:
+        cmds, st = b.step(states, goals)
+        dists = [b.get_distribution(i) for i in range(len(wls))]
+    assert all(s == 0 for s in st)
+    size = [wl.params.N * wl.params.H for wl in wls]
+    n_obs = [len(wl.world.boxes) + len(wl.world.spheres) for wl in wls]
+    dof = [wl.robot.dof for wl in wls]
+    pick = {int(np.argmax(size)), int(np.argmax([wl.params.N for wl in wls])),
+            int(np.argmax([wl.params.H for wl in wls])), int(np.argmax(n_obs)), int(np.argmin(n_obs)),
+            int(np.argmin([wl.params.N for wl in wls])),
+            next(i for i in range(len(wls)) if dof[i] == 6), next(i for i in range(len(wls)) if dof[i] == 7)}
+    picked = [wls[i] for i in sorted(pick)]
+    assert max(w.params.N for w in picked) >= 1000 and max(w.params.H for w in picked) >= 48
+    assert {w.robot.dof for w in picked} == {6, 7} and max(n_obs[i] for i in pick) >= 60
+    for i in sorted(pick):
+        wl, p = wls[i], wls[i].params
+        o = oracle.Oracle(wl.robot, wl.world, p)
+        ocmd, omu, osig, ost, obest = o.step(states[i], goals[i], 0, np.zeros((p.H, wl.robot.dof)),
+                                             np.full(wl.robot.dof, f32(p.sigma_init)))
+        assert ost == 0
+        tol = mu_tolerance([obest], p.beta)
+        scale = max(1.0, np.abs(omu).max())
+        assert max_rel(dists[i][0], omu, scale) < tol, (i, wl.name)
+        assert max_rel(cmds[i], ocmd, scale) < tol, (i, wl.name)
+        assert max_rel(dists[i][1], osig, max(1e-3, osig.max())) < tol, (i, wl.name)

@@ -134,6 +134,60 @@ def test_learned_cost_replaces_the_exact_check():
     pos.close()
 
 
+def test_learned_cost_rollout_matches_oracle():
+    """Eq. 13 as the paper uses it, with a trained jointNERF inside the rollout
+    kernel: every item's self term is max(0, jointNERF(theta)), against the
+    oracle rollout whose self term is the same BF16 network
+    (orc_mlp_arch_forward).  The self term may differ by the BF16 forward
+    tolerance (5e-3 of the largest output), the running cost by w_coll times
+    that; every other term within the cost tolerance.  On the GPU side the term
+    is exactly max(0, prediction) of storm_mlp_predict on the kernel's own joint
+    states."""
+    wl = W.config_paper(0)
+    p = wl.params
+    with Controller(wl.robot, wl.world, p.replace(N=8)) as lab:
+        th, dep = _depth_labels(lab, 262_144, 51)
+    net = SurrogateMLP(seed=13, arch="jointnerf")
+    net.train(th, dep, batch=4096, epochs=6, lr=2e-3, seed=4)
+    params = net.get_params().astype(np.float64)
+    step, it, seed = 2, 1, 3
+    mu, sig = f32(W.make_mean(seed, p.H, 7, 0.5)), f32(W.make_sigma(seed, 7))
+    state = W.make_state(21, 7)  # rollouts from here run from clear into self contact
+    state[0, 3], state[1, 3] = 1.4, 0.8
+    state, goal = f32(state), f32(wl.goal)
+    with Controller(wl.robot, wl.world, p) as ctl:
+        ctl.set_distribution(mu, sig)
+        ctl.set_surrogate_cost(net)
+        g = {k: host(v) for k, v in ctl.generate_rollouts(cuda(state), cuda(goal), step, it).items()}
+        pg = host(net.predict(cuda(g["theta"].reshape(-1, 7)))).reshape(p.N, p.H)
+    assert np.array_equal(g["terms"][..., 5], np.maximum(0.0, pg).astype(np.float32).astype(np.float64))
+    n_or = 96
+    orc = oracle.Oracle(wl.robot, wl.world, p.replace(N=n_or))
+    orc.set_surrogate(NERF, params)
+    o = orc.rollout(state, goal, mu, sig, orc.noise(step, it))
+    y_o = oracle.mlp_arch_forward(NERF, params, o["theta"].reshape(-1, 7)).reshape(n_or, p.H)
+    assert (y_o > 0).any() and (y_o <= 0).any()  # both sides of the hinge occur
+    gs = {k: v[:n_or] for k, v in g.items()}
+    band = 5e-3 * max(1e-3, np.abs(y_o).max())
+    assert np.abs(gs["terms"][..., 5] - o["terms"][..., 5]).max() < band
+    from gpu_helpers import TOL_COST, manip_flips
+    flip, ok = manip_flips(orc, o["theta"], p.k_m, gs["terms"], o["terms"])
+    assert ok and flip.mean() <= 1e-3
+    keep = ~flip
+    for t in range(W.NTERMS):
+        if t == 5:
+            continue
+        tscale = max(1.0, np.abs(o["terms"][..., t]).max())
+        assert max_rel(gs["terms"][..., t][keep], o["terms"][..., t][keep], tscale) < TOL_COST, W.TERM_NAMES[t]
+    cscale = max(1.0, np.abs(o["cost"]).max())
+    assert np.abs(gs["cost"][keep] - o["cost"][keep]).max() < TOL_COST * cscale + p.w_coll * band
+    rows = ~flip.any(axis=1)
+    disc = float(np.sum(p.gamma ** np.arange(p.H)))
+    Cscale = max(1.0, np.abs(o["C"]).max())
+    assert np.abs(gs["C"][rows] - o["C"][rows]).max() < TOL_COST * Cscale + p.w_coll * band * disc
+    net.close()
+
+
 def test_jointnerf_against_the_distance_network(record_property):
     """Same labels (sign flipped for jointNERF), same training budget: the
     accuracy of the paper's architecture next to the 256-256-256 network.

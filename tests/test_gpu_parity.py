@@ -59,6 +59,25 @@ def test_noise_matches_oracle(name):
             assert err.max() < 2e-6, (step, it, err.max())
 
 
+@pytest.mark.parametrize("name", ["small", "paper", "paper_ragged_N37"])
+def test_philox_words_bit_exact(name):
+    """The integer Philox4x32-10 stream behind the noise, GPU against the oracle's
+    own implementation of the published generator (itself pinned by the Random123
+    known-answer vectors), word for word, over every block of a step's noise and
+    a far block range (counter words past 2^31)."""
+    wl, p = VARIANTS[name]
+    blocks = (p.N * (p.n_knots if p.n_knots > 0 else p.H) * 7 + 3) // 4
+    key = [p.seed & 0xFFFFFFFF, p.seed >> 32]
+    with _ctl(wl, p) as ctl:
+        for step, it, first, count in [(0, 0, 0, blocks), (3, 2, 0, blocks), (17, 1, 0, blocks),
+                                       (2**31 - 5, 255, 2**31 + 7, 1000)]:
+            g = ctl.philox_words(step, it, first, count)
+            o = np.array([oracle.philox([first + b, step, (p.instance << 8) | it, 0], key)
+                          for b in range(count)], dtype=np.uint32)
+            assert g.dtype == np.uint32 and g.shape == (count, 4)
+            assert np.array_equal(g, o), (step, it, int(np.sum(g != o)))
+
+
 # ----------------------------------------------------------------------------- rollouts
 
 def _rollout_pair(wl, p, seed=0, step=2, it=1, state=None):
@@ -270,6 +289,13 @@ def test_step_parity(name):
 
 
 def test_multi_step_parity_with_shift():
+    """Four steps, the GPU and the oracle each carrying its own distribution
+    forward (no oracle input comes from the GPU).  The bound after step t is
+    (t + 1) times the one-step bound: a mean update with alpha_mu = 1 is
+    mu_t = sum_n w_n (shift(mu_{t-1}) + sigma eps_n) with sum_n w_n = 1, so a
+    difference in mu_{t-1} reappears in mu_t with gain one, plus the step's own
+    error; the weights' response to that difference is of the same size as the
+    FP32 cost error the one-step bound already covers."""
     wl, p = VARIANTS["small"]
     res = _step_pair(wl, p, n_steps=4)
     for t, (cmd, info, rc, mu, sig, ocmd, omu, osig, ost, obest) in enumerate(res):

@@ -678,3 +678,25 @@ def test_halton_multipliers_and_decorrelation():
     assert r_plain > 0.95 and abs(r_scr) < 0.5, (r_plain, r_scr)
     # marginals stay standard normal-like
     assert abs(scr.mean()) < 0.05 and abs(scr.std() - 1.0) < 0.1
+
+
+def test_rollout_threads_give_the_same_bits():
+    """The particle-parallel rollout loop (the all-cores CPU baseline) computes
+    exactly what the sequential loop computes: particles are independent and no
+    reduction crosses them."""
+    from paper_2104_13542_b300 import workloads as W
+    wl = W.config_paper(1)
+    p = wl.params.replace(N=24)
+    orc = oracle.Oracle(wl.robot, wl.world, p)
+    mu, sig = W.make_mean(2, p.H, 7, 0.4), W.make_sigma(2, 7)
+    eps = orc.noise(1, 0)
+    prev = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        a = orc.rollout(wl.state, wl.goal, mu, sig, eps)
+        oracle.set_threads(4)
+        b = orc.rollout(wl.state, wl.goal, mu, sig, eps)
+    finally:
+        oracle.set_threads(prev)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
