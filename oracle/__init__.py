@@ -24,12 +24,13 @@ NTERMS = 11
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc -O2 (no fast-math) into oracle/libstorm_oracle.so."""
+    """Compile the oracle with gcc -O2 (no fast-math; OpenMP for the optional
+    particle-parallel rollout loop) into oracle/libstorm_oracle.so."""
     if force or not os.path.exists(_LIB_PATH) or \
             os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
                                                os.path.getmtime(_SRC[:-2] + ".h")):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC,
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC,
                                "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -90,7 +91,19 @@ class _Params(C.Structure):
                 ("mlp_h2", C.c_int), ("mlp_h3", C.c_int), ("mlp_margin", C.c_double)]
 
 
+def set_threads(n: int) -> None:
+    """Threads of the rollout's particle loop (1 = sequential; same bits for any count)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
 def _declare(L):
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_set_threads.restype = None
+    L.orc_get_threads.restype = C.c_int
     L.orc_philox4x32_10.argtypes = [_up, _up, _up]
     L.orc_uniform_from_bits.argtypes = [C.c_uint32]
     L.orc_uniform_from_bits.restype = C.c_double

@@ -792,6 +792,14 @@ void orc_running_cost(const orc_robot* R, const orc_world* W, const orc_params* 
 /* at h = H-1).  Any output pointer may be NULL.                              */
 /*   ee: N x H x 12 (row-major 3x4 [R | p]); terms: N x H x ORC_NTERMS         */
 /* ------------------------------------------------------------------------- */
+/* Host threads of orc_rollout's particle loop (1 = sequential).  Particles are
+ * independent and each writes only its own outputs, and no reduction crosses
+ * particles, so every thread count gives bitwise the sequential results. */
+static int g_orc_threads = 1;
+
+void orc_set_threads(int n) { g_orc_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return g_orc_threads; }
+
 int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
                 const double* state, const double* goal, const double* mu,
                 const double* sigma, const double* eps, double* u_out, double* theta_out,
@@ -801,13 +809,14 @@ int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
     const int N = P->N, H = P->H, d = R->dof;
     if (N <= 0 || H <= 0 || d <= 0 || d > 8) return -1;
     double* u = (double*)malloc(sizeof(double) * (size_t)N * H * d);
-    double* th = (double*)malloc(sizeof(double) * (size_t)H * d);
-    double* thd = (double*)malloc(sizeof(double) * (size_t)H * d);
-    double* frames = (double*)malloc(sizeof(double) * 16 * (d + 1));
-    double* xb = (double*)malloc(sizeof(double) * 3 * H);
-    double* vb = (double*)malloc(sizeof(double) * 3 * H);
     orc_smooth_controls(P, d, mu, sigma, eps, u);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_orc_threads) if (g_orc_threads > 1)
     for (int n = 0; n < N; ++n) {
+        double* th = (double*)malloc(sizeof(double) * (size_t)H * d);
+        double* thd = (double*)malloc(sizeof(double) * (size_t)H * d);
+        double* frames = (double*)malloc(sizeof(double) * 16 * (d + 1));
+        double* xb = (double*)malloc(sizeof(double) * 3 * H);
+        double* vb = (double*)malloc(sizeof(double) * 3 * H);
         const double* un = u + (size_t)n * H * d;
         orc_integrate(H, d, P->dt, state, un, th, thd);
         const int with_ball = P->w_ball != 0.0 && P->ball;
@@ -836,14 +845,14 @@ int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
         if (theta_out) memcpy(theta_out + (size_t)n * H * d, th, sizeof(double) * H * d);
         if (theta_dot_out) memcpy(theta_dot_out + (size_t)n * H * d, thd, sizeof(double) * H * d);
         if (Ctot) Ctot[n] = C;
+        free(th);
+        free(thd);
+        free(frames);
+        free(xb);
+        free(vb);
     }
     if (u_out) memcpy(u_out, u, sizeof(double) * (size_t)N * H * d);
     free(u);
-    free(th);
-    free(thd);
-    free(frames);
-    free(xb);
-    free(vb);
     return 0;
 }
 

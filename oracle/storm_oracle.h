@@ -144,6 +144,10 @@ void orc_running_cost(const orc_robot* R, const orc_world* W, const orc_params* 
                       const double* goal, int h, const double* theta_h,
                       const double* theta_dot_h, const double* u_h, const double* u_prev,
                       double* terms, double* total);
+/* Threads of orc_rollout's loop over particles (default 1; results are the
+ * same bits for every count). */
+void orc_set_threads(int n);
+int orc_get_threads(void);
 int orc_rollout(const orc_robot* R, const orc_world* W, const orc_params* P,
                 const double* state, const double* goal, const double* mu,
                 const double* sigma, const double* eps, double* u, double* theta,
