@@ -540,35 +540,52 @@ def run_variants(args, seed: int, fp32_peak: float | None = None):
                               "instances": len(wls), "rollout_steps_per_step": units,
                               "mapping": b.launch_mapping(), "tile": b.get_launch(),
                               "autotune_rollout_us": t_tune}
-    # learned self-collision surrogate at 1000 x 30
+    # learned self-collision surrogate at 1000 x 30, inside the rollout kernel,
+    # next to the exact check; then the crossover: denser link spheres (more
+    # self pairs) and the exact check without its broad phase
     wl = W.config_paper(seed, N=1000, H=30)
     margin = 0.05
-    with Controller(wl.robot, wl.world, wl.params.replace(N=8)) as lab:
-        rng = np.random.default_rng([seed, 77])
-        th = torch.as_tensor(rng.uniform(-2.8, 2.8, (1 << 20, 7)).astype(np.float32), device="cuda")
-        th_te = torch.as_tensor(rng.uniform(-2.8, 2.8, (65_536, 7)).astype(np.float32), device="cuda")
-        sd, sd_te = lab.self_distance(th), lab.self_distance(th_te)
-    net = SurrogateMLP(seed=seed)
-    t0 = time.perf_counter()
-    losses = net.train(th, torch.clamp(sd, max=0.5), batch=4096, epochs=8, lr=2e-3, seed=seed)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    y, ref = net.predict(th_te).cpu().numpy(), sd_te.cpu().numpy()
-    near, coll = ref < 0.5, ref < 0.0
-    acc = {"mae_m": float(np.abs(y[near] - ref[near]).mean()),
-           "false_negative_rate": float(np.mean(y[coll] >= margin)) if coll.any() else 0.0,
-           "skip_fraction": float(np.mean(y >= margin)), "margin_m": margin,
-           "train_s": train_s, "train_samples": int(th.shape[0]), "epochs": len(losses),
-           "final_loss": float(losses[-1])}
-    for name in ("exact_1000x30", "surrogate_1000x30"):
-        with Controller(wl.robot, wl.world, wl.params) as c:
-            if name.startswith("surrogate"):
-                c.set_surrogate(net, margin)
-            c.step(wl.state.astype(np.float32), wl.goal.astype(np.float32))
-            ms = _time_steps(c.step_resident, c.stream, flush, n)
-            out[name] = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99))}
-    out["surrogate_1000x30"].update(acc)
-    net.close()
+    cross = {}
+    for spl in (7, 9):
+        robot = wl.robot if spl == 7 else W.make_robot(seed, 7, spheres_per_link=spl)
+        with Controller(robot, wl.world, wl.params.replace(N=8)) as lab:
+            rng = np.random.default_rng([seed, 77])
+            th = torch.as_tensor(rng.uniform(-2.8, 2.8, (1 << 20, 7)).astype(np.float32), device="cuda")
+            th_te = torch.as_tensor(rng.uniform(-2.8, 2.8, (65_536, 7)).astype(np.float32), device="cuda")
+            sd, sd_te = lab.self_distance(th), lab.self_distance(th_te)
+        net = SurrogateMLP(seed=seed)
+        t0 = time.perf_counter()
+        losses = net.train(th, torch.clamp(sd, max=0.5), batch=4096, epochs=8, lr=2e-3, seed=seed)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        y, ref = net.predict(th_te).cpu().numpy(), sd_te.cpu().numpy()
+        near, coll = ref < 0.5, ref < 0.0
+        acc = {"mae_m": float(np.abs(y[near] - ref[near]).mean()),
+               "false_negative_rate": float(np.mean(y[coll] >= margin)) if coll.any() else 0.0,
+               "skip_fraction": float(np.mean(y >= margin)), "margin_m": margin,
+               "train_s": train_s, "train_samples": int(th.shape[0]), "epochs": len(losses),
+               "final_loss": float(losses[-1])}
+        row = {"spheres": int(robot.spheres.shape[0]), "self_pairs": int(robot.pairs.shape[0])}
+        for mode in ("exact", "surrogate"):
+            for bp in (True, False):
+                with Controller(robot, wl.world, wl.params) as c:
+                    if mode == "surrogate":
+                        c.set_surrogate(net, margin)
+                    c.set_broadphase(bp)
+                    c.step(wl.state.astype(np.float32), wl.goal.astype(np.float32))
+                    ms = _time_steps(c.step_resident, c.stream, flush, n)
+                key = f"{mode}_{'broadphase' if bp else 'bruteforce'}_ms_p50"
+                row[key] = float(np.percentile(ms, 50))
+                if spl == 7 and bp:
+                    out[f"{mode}_1000x30"] = {"ms_p50": float(np.percentile(ms, 50)),
+                                              "ms_p99": float(np.percentile(ms, 99))}
+        if spl == 7:
+            out["surrogate_1000x30"].update(acc)
+        else:
+            row.update(acc)
+        cross[f"{spl}_spheres_per_link"] = row
+        net.close()
+    out["surrogate_crossover_1000x30"] = cross
     return out
 
 

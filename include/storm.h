@@ -519,7 +519,7 @@ int storm_self_distance(storm_handle* h, const float* theta_dev, int count, floa
  * (particle, step) configuration on the tensor cores, between the integration
  * and the costs, and runs the exact self-collision check only where the
  * prediction is below `margin` metres (elsewhere the self term is 0).  The
- * rollout then takes four particle groups per CTA of five warps (whatever
+ * rollout then takes four particle groups per CTA of six warps (whatever
  * launch shape was set).  If a tensor-core wait of that kernel runs out, its
  * CTA falls back to the exact check for all its items and sets the network's
  * error flag (reported by the network's next call).  The network must live on

@@ -724,9 +724,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_wait_probe(int* err, unsigned l
 //     accumulator (mbarrier `done`), then write the next layer's inputs one
 //     32-column block at a time (bias, ReLU, BF16), announcing each block on
 //     its own mbarrier a[j]; after layer 3 the head (bias, ReLU, linear output).
-//   one issuing thread (lane 0 of warp kEpi): keeps the weight ring full and
-//     issues each block's MMAs as soon as its inputs are announced and its
-//     weights have landed, so the tensor core works while the epilogue goes on.
+//   one MMA-issuing thread (lane 0 of warp kEpi): issues each block's MMAs as
+//     soon as its inputs are announced and its weights have landed, so the
+//     tensor core works while the epilogue goes on;
+//   one loading thread (lane 0 of warp kEpi + 1): starts each weight block's
+//     copy as soon as the buffer it reuses has been released by the MMAs.
 // The MMA sequence (K steps of 16 in column order) and the epilogue arithmetic
 // are those of k_gemm_ws, so a tile computes bitwise what the layer-by-layer
 // kernels compute.
@@ -764,8 +766,10 @@ constexpr size_t kTileSmem = kOffVec + kTileVec;
 constexpr int kTileBars = 2 * kRingDepth + 2 + kMaxBlocks;
 constexpr uint32_t kTileCols = 512;            // two accumulators
 
-// Threads of a CTA running the engine with kEpi epilogue warps: those, then the issuing warp.
-__host__ __device__ constexpr int tile_threads(int kEpi) { return (kEpi + 1) * 32; }
+// Threads of a CTA running the engine with kEpi epilogue warps: those, then the
+// MMA-issuing warp (warp kEpi), then the weight-loading warp (warp kEpi + 1);
+// one thread of each of the last two does the work.
+__host__ __device__ constexpr int tile_threads(int kEpi) { return (kEpi + 2) * 32; }
 
 __host__ __device__ inline int mlp_blocks(const MlpView& v) { return 1 + v.h1 / kBlockK + v.h2 / kBlockK; }
 
@@ -801,8 +805,9 @@ __device__ __forceinline__ void mbar_arrive_cta(uint32_t addr)
 // block g lives in ring buffer g % kRingDepth and completes phase
 // (g / kRingDepth) & 1 of full[that buffer] (landed) and of empty[that buffer]
 // (its MMAs done).  Barrier addresses are computed, not indexed, so that the
-// state stays in registers.  next / issued / apar / tiles belong to the issuing
-// thread; layers (phases of `done`) to the epilogue threads.
+// state stays in registers.  next / apar / tiles belong to the MMA-issuing
+// thread, issued to the loading thread, layers (phases of `done`) to the
+// epilogue threads.
 struct MlpTiles {
     uint32_t ring, sA1, sA;  // shared addresses
     uint32_t bars;           // the mbarriers, 8 bytes apart in the order above
@@ -822,9 +827,9 @@ __device__ __forceinline__ uint32_t tile_a1(const MlpTiles& t) { return t.bars +
 __device__ __forceinline__ uint32_t tile_a(const MlpTiles& t, int j) { return t.bars + 8 * (2 * kRingDepth + 2 + j); }
 
 // Every thread of the CTA: addresses, then (warp 0) the TMEM columns and (the
-// issuing thread) the barriers and the first kRingDepth block copies.  The
-// caller then runs the TMEM-allocation fence / barrier / fence sequence and
-// reads *tmem_slot.
+// MMA-issuing thread) the barriers.  The caller then runs the TMEM-allocation
+// fence / barrier / fence sequence, reads *tmem_slot, and has the loading thread
+// run mlp_load_all.
 template <int kEpi>
 __device__ __forceinline__ void mlp_tiles_init(MlpTiles& t, const MlpView& v, uint32_t smem_base, uint64_t* bars,
                                                uint32_t* tmem_slot, int total)
@@ -848,17 +853,28 @@ __device__ __forceinline__ void mlp_tiles_init(MlpTiles& t, const MlpView& v, ui
         mbar_init(tile_a1(t), kBM / 32);                                             // the four encoding warps
         for (int j = 0; j < kMaxBlocks; ++j) mbar_init(tile_a(t, j), kEpi);         // every epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const int nb = mlp_blocks(v);
-        for (; t.issued < kRingDepth && t.issued < t.total; ++t.issued)
-            mlp_issue_block(v, t.issued % nb, t.ring + t.issued * kTileRing, tile_full(t, t.issued));
     }
 }
 
+// The loading thread: the copies of the weight blocks this CTA will multiply
+// (those before block `upto`), in order, each as soon as the ring buffer it
+// reuses is free (the MMAs of the block kRingDepth before it are done).  False
+// when a wait ran out.
+__device__ __forceinline__ bool mlp_load_all(const MlpView& v, MlpTiles& t, int upto = 1 << 30)
+{
+    const int nb = mlp_blocks(v);
+    for (; t.issued < t.total && t.issued < upto; ++t.issued) {
+        const int b = t.issued % kRingDepth;
+        if (t.issued >= kRingDepth && !mbar_wait(tile_empty(t, b), ((t.issued / kRingDepth) - 1) & 1)) return false;
+        mlp_issue_block(v, t.issued % nb, t.ring + b * kTileRing, tile_full(t, b));
+    }
+    return true;
+}
+
 // The issuing thread: the MMAs of the next weight block (A block at a0 with
-// 8-row groups sbo_a bytes apart, kb input columns) into accumulator d,
-// committed to the block's empty barrier; then the buffer of the block before
-// it, whose MMAs were issued earlier, is refilled with the block kRingDepth - 1
-// ahead.  False when a wait ran out.
+// 8-row groups sbo_a bytes apart, kb input columns) into accumulator d, once
+// its weights have landed, committed to the block's empty barrier (which
+// frees its buffer for the loading thread).  False when a wait ran out.
 __device__ __forceinline__ bool mlp_mma_block(const MlpView& v, MlpTiles& t, uint32_t a0, uint32_t sbo_a, int kb,
                                               uint32_t d, uint32_t idesc, bool first)
 {
@@ -879,12 +895,6 @@ __device__ __forceinline__ bool mlp_mma_block(const MlpView& v, MlpTiles& t, uin
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tile_empty(t, buf))
                  : "memory");
     ++t.next;
-    if (g >= 1 && t.issued < t.total) {
-        const int gp = g - 1, bp = gp % kRingDepth;
-        if (!mbar_wait(tile_empty(t, bp), (gp / kRingDepth) & 1)) return false;
-        mlp_issue_block(v, t.issued % mlp_blocks(v), t.ring + bp * kTileRing, tile_full(t, bp));
-        ++t.issued;
-    }
     return true;
 }
 
@@ -1060,12 +1070,17 @@ __device__ __forceinline__ bool bar_and(int id, int threads, bool v)
     return r != 0;
 }
 
-// After a failed tile, the issuing thread: wait (bounded) for the copies and
-// MMAs still in flight, so that nothing writes this CTA's shared memory or TMEM
-// once it moves on.
-__device__ __forceinline__ void mlp_tiles_drain(MlpTiles& t)
+// After a failure: the loading thread waits (bounded) for the copies it started
+// and the MMA-issuing thread for its last MMAs, so that nothing writes this
+// CTA's shared memory or TMEM once it moves on.  Each waits on its own state.
+__device__ __forceinline__ void mlp_drain_loads(MlpTiles& t)
 {
-    for (int g = t.next; g < t.issued; ++g) mbar_wait(tile_full(t, g % kRingDepth), (g / kRingDepth) & 1);
+    for (int g = t.issued - kRingDepth > 0 ? t.issued - kRingDepth : 0; g < t.issued; ++g)
+        mbar_wait(tile_full(t, g % kRingDepth), (g / kRingDepth) & 1);
+}
+
+__device__ __forceinline__ void mlp_drain_mmas(MlpTiles& t)
+{
     if (t.next > 0) {
         const int g = t.next - 1;
         mbar_wait(tile_empty(t, g % kRingDepth), (g / kRingDepth) & 1);
@@ -1223,12 +1238,17 @@ k_mlp_forward_tiles(tc::MlpView v, const float* __restrict__ theta, int count, i
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     t.tmem = tmem_slot;
     bool ok = true;
-    if (warp == kFwdEpi) {  // the issuing warp: one thread
+    if (warp == kFwdEpi + 1) {  // the loading warp: one thread
+        if ((tid & 31) == 0 && !tc::mlp_load_all(v, t)) {
+            if (v.err) atomicExch(v.err, 1);
+            tc::mlp_drain_loads(t);
+        }
+    } else if (warp == kFwdEpi) {  // the MMA-issuing warp: one thread
         if ((tid & 31) == 0) {
             for (int k = 0; k < my_tiles && ok; ++k) ok = tc::mlp_tile_issue(v, t);
             if (!ok) {
                 if (v.err) atomicExch(v.err, 1);
-                tc::mlp_tiles_drain(t);
+                tc::mlp_drain_mmas(t);
             }
         }
     } else {

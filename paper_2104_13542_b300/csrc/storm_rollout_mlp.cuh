@@ -1,10 +1,11 @@
 // storm_rollout_mlp.cuh -- generate_rollouts with the learned self-collision
 // network (Sec. 4.2, Eq. 13) evaluated inside the rollout kernel.
 //
-// One CTA of five warps: four take warp-mapped particle groups (one particle per
+// One CTA of six warps: four take warp-mapped particle groups (one particle per
 // warp for H > 16), so that each item slot of theirs is one 128-row tile of the
 // network (row 32 w + lane is warp w's lane), and drain the tensor core's
-// accumulators; the fifth keeps the weights streaming and issues the MMAs.  The warps first draw the
+// accumulators; the fifth issues the MMAs; the sixth keeps the weights
+// streaming.  The warps first draw the
 // noise, form the controls and integrate them (Eq. 7) exactly as the warp
 // mapping does; then the CTA encodes each row's joint state into shared memory
 // and runs the whole network on the tile on the tensor cores
@@ -52,7 +53,7 @@ k_rollout_mlp(Problem pb, RolloutOut out, const float* __restrict__ state, const
     const WarpPlan W = warp_plan(pb, 1);
     const MlpRolloutPlan P = mlp_rollout_plan(pb);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool roller = warp < kMlpWarps;  // warps 0-3 roll out; warp 4 issues the copies and MMAs
+    const bool roller = warp < kMlpWarps;  // warps 0-3 roll out; warp 4 issues the MMAs, warp 5 the copies
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
     float* ws = reinterpret_cast<float*>(smem + P.roll) + (roller ? warp : 0) * W.floats;
     float* s_pred = reinterpret_cast<float*>(smem + P.pred);
@@ -101,15 +102,19 @@ k_rollout_mlp(Problem pb, RolloutOut out, const float* __restrict__ state, const
             float y = 0.f;
             mine = tc::mlp_tile_epilogue<kMlpEpi>(net, t, s_b2, s_b3, s_w4, s_part, b4, &y);
             s_pred[slot * kMlpRows + tid] = y;
-        } else if (lane == 0) {
+        } else if (warp == kMlpEpi && lane == 0) {
             mine = tc::mlp_tile_issue(net, t);
+        } else if (warp == kMlpEpi + 1 && lane == 0) {
+            mine = tc::mlp_load_all(net, t, (slot + 1) * tc::mlp_blocks(net));  // this slot's weight blocks
         }
         ok = __syncthreads_and(mine);  // the same decision on every thread
     }
     if (!ok) {
         if (tid == kMlpEpi * 32) {
             if (net.err) atomicExch(net.err, 1);
-            tc::mlp_tiles_drain(t);
+            tc::mlp_drain_mmas(t);
+        } else if (tid == (kMlpEpi + 1) * 32) {
+            tc::mlp_drain_loads(t);
         }
         __syncthreads();
     }
