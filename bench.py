@@ -583,8 +583,22 @@ def run_variants(args, seed: int, fp32_peak: float | None = None):
             out["surrogate_1000x30"].update(acc)
         else:
             row.update(acc)
-        cross[f"{spl}_spheres_per_link"] = row
         net.close()
+        # the paper's own use (Eq. 13): jointNERF's depth as the self-collision
+        # cost, no exact check at all
+        nerf = SurrogateMLP(seed=seed, arch="jointnerf")
+        nerf.train(th, torch.clamp(-sd, min=-0.5), batch=4096, epochs=8, lr=2e-3, seed=seed)
+        d_te = -nerf.predict(th_te).cpu().numpy()
+        row["learned_cost_jointnerf_mae_m"] = float(np.abs(d_te[near] - ref[near]).mean())
+        for bp in (True, False):
+            with Controller(robot, wl.world, wl.params) as c:
+                c.set_surrogate_cost(nerf)
+                c.set_broadphase(bp)
+                c.step(wl.state.astype(np.float32), wl.goal.astype(np.float32))
+                ms = _time_steps(c.step_resident, c.stream, flush, n)
+            row[f"learned_cost_jointnerf_{'broadphase' if bp else 'bruteforce'}_ms_p50"] = float(np.percentile(ms, 50))
+        nerf.close()
+        cross[f"{spl}_spheres_per_link"] = row
     out["surrogate_crossover_1000x30"] = cross
     return out
 

@@ -1881,8 +1881,7 @@ int upload_world(storm_handle* h, const storm_world* w)
 bool needs_full_rollout(const Problem& pb)
 {
     return pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || (pb.ball && pb.w_ball != 0.f) ||
-           pb.filter != STORM_FILTER_DEFAULT || pb.rot_mode != STORM_ROT_QUAT || pb.sampler != STORM_SAMPLER_PHILOX ||
-           pb.self_mode != 0;
+           pb.filter != STORM_FILTER_DEFAULT || pb.rot_mode != STORM_ROT_QUAT || pb.sampler != STORM_SAMPLER_PHILOX;
 }
 
 // Warps per particle group of a warp mapping.
@@ -1920,16 +1919,17 @@ int launch_rollout(storm_handle* h, cudaStream_t s, const RolloutOut& out, const
     Problem pb = h->pb;
     pb.dep_launch = dep ? 1 : 0;
     pb.shift_view = shift ? 1 : 0;
+    // the full instantiation where the problem or the call needs its extra code
+    const bool full = needs_full_rollout(pb) || out.theta || out.theta_dot || out.ee || out.terms || out.cost;
     if (pb.self_mode != 0 && h->mlp) {  // the learned self collision: the network inside the rollout
         pb.dep_launch = 0;
         const WarpPlan wp = warp_plan(pb, 1);
         const int grid = (pb.N + wp.PW * kMlpWarps - 1) / (wp.PW * kMlpWarps);
-        CK(launch_kernel(k_rollout_mlp, grid, tc::tile_threads(kMlpEpi), h->mlp_smem, s, false, pb, out, state, goal,
-                         static_cast<const StepState*>(h->d_st), step_override, iter, mlp_view(h->mlp)));
+        CK(launch_kernel(full ? k_rollout_mlp<true> : k_rollout_mlp<false>, grid, tc::tile_threads(kMlpEpi),
+                         h->mlp_smem, s, false, pb, out, state, goal, static_cast<const StepState*>(h->d_st),
+                         step_override, iter, mlp_view(h->mlp)));
         return STORM_OK;
     }
-    // the full instantiation where the problem or the call needs its extra code
-    const bool full = needs_full_rollout(pb) || out.theta || out.theta_dot || out.ee || out.terms || out.cost;
     const StepState* st = h->d_st;
     if (h->mapping == STORM_MAP_WARP)
         CK(launch_kernel(full ? k_rollout_warp<1, true> : k_rollout_warp<1, false>, h->warp_grid, h->wpc * 32,
@@ -3923,13 +3923,15 @@ static int set_self_mode(storm_handle* h, storm_mlp* mlp, int mode, double margi
         if (mlp->device != h->device) return fail(h, STORM_ERR_INVALID_ARG, "network on another device");
         const MlpRolloutPlan P = mlp_rollout_plan(h->pb);
         int optin = 0;
-        cudaFuncAttributes fa;
         CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-        CK(cudaFuncGetAttributes(&fa, k_rollout_mlp));
-        if (static_cast<size_t>(P.bytes) + fa.sharedSizeBytes > static_cast<size_t>(optin))
-            return fail(h, STORM_ERR_INVALID_ARG, "problem too large for the fused network rollout");
-        CK(cudaFuncSetAttribute(k_rollout_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                optin - static_cast<int>(fa.sharedSizeBytes)));
+        for (auto kf : {k_rollout_mlp<false>, k_rollout_mlp<true>}) {
+            cudaFuncAttributes fa;
+            CK(cudaFuncGetAttributes(&fa, kf));
+            if (static_cast<size_t>(P.bytes) + fa.sharedSizeBytes > static_cast<size_t>(optin))
+                return fail(h, STORM_ERR_INVALID_ARG, "problem too large for the fused network rollout");
+            CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - static_cast<int>(fa.sharedSizeBytes)));
+        }
         h->mlp_smem = P.bytes;
         // the network's own stream may still be writing its weights
         CK(cudaStreamSynchronize(mlp->stream));

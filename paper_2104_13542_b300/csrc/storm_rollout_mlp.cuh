@@ -42,6 +42,9 @@ __host__ __device__ inline MlpRolloutPlan mlp_rollout_plan(const Problem& pb)
 
 constexpr int kMlpEpi = kMlpWarps;  // the rolling warps are the network's epilogue warps
 
+// kFull: as for k_rollout_warp (the lean instantiation when the problem and the
+// call need nothing beyond the default path and the network).
+template <bool kFull>
 __global__ void __launch_bounds__(tc::tile_threads(kMlpEpi), 1)
 k_rollout_mlp(Problem pb, RolloutOut out, const float* __restrict__ state, const float* __restrict__ goal,
               const StepState* __restrict__ st, int step_override, int iter, tc::MlpView net)
@@ -78,7 +81,7 @@ k_rollout_mlp(Problem pb, RolloutOut out, const float* __restrict__ state, const
     t.tmem = tmem_slot;
 
     // ---- noise, controls, integration (Eq. 7): each rolling warp's joint states in its region
-    if (roller) rollout_warp_body<1, true, 1>(pb, out, state, goal, step, iter, wg, warp, ws);
+    if (roller) rollout_warp_body<1, kFull, 1>(pb, out, state, goal, step, iter, wg, warp, ws);
     __syncwarp();
 
     // ---- the network on every item slot's tile (row 32 w + lane = rolling warp w's lane)
@@ -121,7 +124,7 @@ k_rollout_mlp(Problem pb, RolloutOut out, const float* __restrict__ state, const
 
     // ---- the rest of the rollout, the exact self check where the prediction asks for it
     if (roller)
-        rollout_warp_body<1, true, 2>(pb, out, state, goal, step, iter, wg, warp, ws, ok ? s_pred + tid : nullptr);
+        rollout_warp_body<1, kFull, 2>(pb, out, state, goal, step, iter, wg, warp, ws, ok ? s_pred + tid : nullptr);
 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -206,10 +206,10 @@ __device__ __forceinline__ void unit_sync(int unit, int threads)
 // quaternion rotation cost, exact self collision) runs the lean instantiation,
 // without that code in its instruction stream.
 // kPhase: 0 the whole rollout; 1 up to the joint states (noise, controls,
-// Eq. 7); 2 the rest, on the joint states phase 1 left in ws.  lane_pred (kFull
-// only; nullable): the learned self-collision network's output for this lane's
-// items, item slot s at lane_pred[s * kMlpRows] (pb.self_mode says how it is
-// used).
+// Eq. 7); 2 the rest, on the joint states phase 1 left in ws.  lane_pred (phase
+// 2 or kFull; nullable): the learned self-collision network's output for this
+// lane's items, item slot s at lane_pred[s * kMlpRows] (pb.self_mode says how
+// it is used).
 template <int kW, bool kFull, int kPhase = 0>
 __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const RolloutOut& out,
                                                   const float* __restrict__ state, const float* __restrict__ goal,
@@ -439,7 +439,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     const bool want_ee = kFull && (pb.w_ee_vel != 0.f || pb.w_ee_acc != 0.f || out.terms);
     const bool ball_on = kFull && pb.ball && pb.w_ball != 0.f;
     float* s_ba = ws + W.ba;
-    const float* pred = kFull && pb.self_mode != 0 ? lane_pred : nullptr;
+    const float* pred = (kFull || kPhase == 2) && pb.self_mode != 0 ? lane_pred : nullptr;
     const int NO = pb.B + pb.O;
 
     for (int slot = 0; slot < W.SL; ++slot) {
