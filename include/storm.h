@@ -484,6 +484,10 @@ int storm_mlp_set_params(storm_mlp* m, const float* params);
  * (weights streamed through shared memory by bulk asynchronous copies); the
  * result is bitwise that of storm_mlp_predict_layers. */
 int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev);
+/* storm_mlp_predict enqueued on the network's stream without waiting (for
+ * pipelined callers and timing); a tensor-core wait that ran out is reported by
+ * the network's next waiting call.  Errors: INVALID_ARG, CUDA. */
+int storm_mlp_predict_async(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev);
 /* The same predictions through the layer-by-layer tensor-core kernels of the
  * training forward pass (each layer's BF16 activations written to and read
  * back from global memory).  Same arguments, errors and waiting. */

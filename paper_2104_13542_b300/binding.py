@@ -53,6 +53,7 @@ EXPORTED = [
     "storm_self_distance", "storm_set_surrogate", "storm_set_broadphase", "storm_set_trace",
     "storm_mlp_create_arch", "storm_mlp_param_count", "storm_set_surrogate_cost",
     "storm_philox_words", "storm_mlp_wait_probe", "storm_mlp_predict_layers", "storm_fp32_peak",
+    "storm_mlp_predict_async",
 ]
 MLP_PARAMS = 135937
 
@@ -189,6 +190,7 @@ def lib():
         L.storm_mlp_set_params.argtypes = [vp, _fp]
         L.storm_mlp_predict.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.storm_mlp_predict_layers.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+        L.storm_mlp_predict_async.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.storm_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, C.c_int, _fp, _fp]
         L.storm_mlp_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                                       C.c_uint64, _fp]
@@ -772,14 +774,20 @@ class SurrogateMLP:
         assert p.size == self.n_params
         self._check(lib().storm_mlp_set_params(self.h, _p(p, _fp)))
 
-    def predict(self, theta_dev, layers: bool = False):
+    def predict(self, theta_dev, layers: bool = False, out=None, wait: bool = True):
         """Predictions for theta_dev (count x dof): the fused whole-network kernel,
-        or with layers=True the layer-by-layer kernels of the training pass."""
+        or with layers=True the layer-by-layer kernels of the training pass.
+        wait=False (fused kernel only) enqueues on the network's stream and
+        returns at once."""
         n, dof = int(theta_dev.shape[0]), int(theta_dev.shape[1])
-        with self.torch.cuda.stream(self.stream):
-            out = self.torch.empty(n, dtype=self.torch.float32, device="cuda")
+        if out is None:
+            with self.torch.cuda.stream(self.stream):
+                out = self.torch.empty(n, dtype=self.torch.float32, device="cuda")
         self._sync_in()
-        fn = lib().storm_mlp_predict_layers if layers else lib().storm_mlp_predict
+        if layers:
+            fn = lib().storm_mlp_predict_layers
+        else:
+            fn = lib().storm_mlp_predict if wait else lib().storm_mlp_predict_async
         self._check(fn(self.h, _dptr(theta_dev.contiguous()), n, dof, _dptr(out)))
         return out
 

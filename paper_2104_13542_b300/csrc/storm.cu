@@ -3800,7 +3800,7 @@ int storm_mlp_wait_probe(storm_mlp* m, unsigned int limit_us)
     return mlp_check_err(m);
 }
 
-int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev)
+int storm_mlp_predict_async(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev)
 {
     if (!m || !theta_dev || !out_dev || count < 1 || count > STORM_MLP_MAX_ROWS || dof < 1 || dof > 7)
         return STORM_ERR_INVALID_ARG;
@@ -3808,7 +3808,13 @@ int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, 
     k_mlp_forward_tiles<<<std::min(tiles, m->sms), tc::tile_threads(kFwdEpi), tc::kTileSmem, m->stream>>>(
         mlp_view(m), theta_dev, count, dof, out_dev);
     MK(cudaGetLastError());
-    return mlp_check_err(m);
+    return STORM_OK;
+}
+
+int storm_mlp_predict(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev)
+{
+    const int rc = storm_mlp_predict_async(m, theta_dev, count, dof, out_dev);
+    return rc ? rc : mlp_check_err(m);
 }
 
 int storm_mlp_predict_layers(storm_mlp* m, const float* theta_dev, int count, int dof, float* out_dev)
