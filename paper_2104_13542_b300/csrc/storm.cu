@@ -1683,7 +1683,7 @@ struct storm_handle {
     float* d_C = nullptr;
     float* d_io = nullptr;     // state 3d | goal 7 | cmd d | StepState
     StepState* d_st = nullptr;
-    float* d_adj = nullptr;          // adjoint partial rows: N x (H*d + 1)
+    void* d_adj = nullptr;           // adjoint sums: H*d + 1 64-bit fixed-point values, count, flag
     storm_mlp* mlp = nullptr;        // learned self-collision surrogate (not owned)
     size_t mlp_smem = 0;             // k_rollout_mlp's dynamic shared memory
     float* d_ball = nullptr;         // 8: ball position, velocity (world frame), padding
@@ -1965,13 +1965,15 @@ int launch_adjoint(storm_handle* h, cudaStream_t s, const float* state, const fl
 {
     // 128 threads: the per-(step, sphere) and per-(step, pair block) collision
     // loops split four warps' ways; at 125 registers 4 CTAs fit an SM, so the
-    // paper workload's 500 particles stay one wave
+    // paper workload's 500 particles stay one wave.  The CTA that finishes
+    // last turns the fixed-point sums into grad and J (no second kernel).
     const int threads = 128;
-    k_adjoint<<<h->pb.N, threads, h->adjoint_smem, s>>>(h->pb, mean, state, goal, h->d_st,
-                                                         step_override, iter, h->d_adj, Ctot);
-    CK(cudaGetLastError());
-    k_adjoint_reduce<<<h->pb.H * h->pb.d + 1, 128, 0, s>>>(h->pb, h->d_adj, grad, J, eta, h->d_st,
-                                                           cmd, finalize);
+    const int HD = h->pb.H * h->pb.d;
+    AdjAcc acc{reinterpret_cast<unsigned long long*>(h->d_adj),
+               reinterpret_cast<unsigned int*>(reinterpret_cast<unsigned long long*>(h->d_adj) + HD + 1),
+               reinterpret_cast<int*>(reinterpret_cast<unsigned long long*>(h->d_adj) + HD + 1) + 1};
+    k_adjoint<<<h->pb.N, threads, h->adjoint_smem, s>>>(h->pb, mean, state, goal, h->d_st, step_override, iter,
+                                                         acc, Ctot, grad, J, eta, cmd, finalize);
     CK(cudaGetLastError());
     return STORM_OK;
 }
@@ -2347,7 +2349,11 @@ int create_impl(storm_handle* h, const storm_robot* r, const storm_world* w, con
     CK(cudaMalloc(&h->d_io, sizeof(float) * io_floats(pb)));
     CK(cudaMallocHost(&h->h_io, sizeof(float) * io_floats(pb)));
     CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->h_io_dev), h->h_io, 0));
-    CK(cudaMalloc(&h->d_adj, sizeof(float) * size_t(pb.N) * (pb.H * pb.d + 1)));
+    {
+        const size_t adj_bytes = sizeof(unsigned long long) * (pb.H * pb.d + 2);
+        CK(cudaMalloc(&h->d_adj, adj_bytes));
+        CK(cudaMemsetAsync(h->d_adj, 0, adj_bytes, h->stream));
+    }
     std::memset(h->h_io, 0, sizeof(float) * io_floats(pb));
     h->d_st = reinterpret_cast<StepState*>(h->d_io + io_st(pb));
     CK(cudaMemsetAsync(h->d_io, 0, sizeof(float) * io_floats(pb), h->stream));

@@ -18,12 +18,21 @@ struct AdjointLayout {
     int bytes;
 };
 
+// Float4s per step of the frame array: the F x 3 rows of its link frames, padded
+// to an odd count so that the threads of a warp, one step each, read their
+// frames from different shared-memory banks.
+__host__ __device__ inline int adjoint_frame_stride(const Problem& pb)
+{
+    const int r = (pb.d + 1) * 3;
+    return r + ((r & 1) ? 0 : 1);
+}
+
 __host__ __device__ inline AdjointLayout adjoint_layout(const Problem& pb)
 {
     AdjointLayout L;
     int off = 0;
     const int I = pb.H;  // one particle per CTA
-    L.frame = take_(off, I * (pb.d + 1) * 3 * 16);
+    L.frame = take_(off, I * adjoint_frame_stride(pb) * 16);
     L.cent = take_(off, I * pb.M * 16);
     L.sph = take_(off, pb.M * 16);
     L.wsph = take_(off, pb.O * 16);
@@ -85,14 +94,42 @@ __device__ __forceinline__ void add_point_grad(const float4* fr, int f, float cx
     }
 }
 
+// The sums of grad = (1/N) sum_{n >= n_null} dC_n/du_n and J = (1/N) sum_n C_n,
+// kept in 64-bit fixed point: integer additions give the same bits in any
+// order, so the particles' CTAs add their rows with atomics and the result is
+// still deterministic (and, with 2^-30 resolution per gradient entry and 2^-20
+// per cost, finer than an FP32 sum).  Zero between launches (the CTA that
+// finishes a launch clears them).
+struct AdjAcc {
+    unsigned long long* sum;  // H*d gradient sums, then the cost sum
+    unsigned int* count;      // CTAs that have added their row this launch
+    int* bad;                 // a non-finite or out-of-range value was seen
+};
+
+constexpr double kAdjGradScale = 1073741824.0;  // 2^30
+constexpr double kAdjCostScale = 1048576.0;     // 2^20
+
+__device__ __forceinline__ void adj_add(unsigned long long* sum, float v, double scale, int* bad)
+{
+    const double x = static_cast<double>(v) * scale;
+    if (!(fabs(x) < 4.0e18 / 16384.0)) {  // NaN, infinite, or a sum of up to 2^14 rows that could overflow
+        atomicExch(bad, 1);
+        return;
+    }
+    atomicAdd(sum, static_cast<unsigned long long>(__double2ll_rn(x)));
+}
+
 // One particle per CTA: forward rollout, per-step gradients, reverse scans,
-// then the CTA's dC/du rows and C go to the partial buffers; the last CTA
-// sums the partials in CTA order into grad = (1/N) sum_{n >= n_null} dC_n/du_n
-// and J = (1/N) sum_n C_n, and with eta != 0 also steps mu <- mu - eta grad.
+// then the CTA adds its dC/du row and C to the fixed-point sums; the CTA that
+// arrives last turns them into grad and J (and with eta != 0 steps
+// mu <- mu - eta grad; with `finalize` the control step ends there: the command
+// from the refined mean, the step counter advanced).  A non-finite value makes
+// grad and J NaN and leaves mu as it was.
 __global__ void __launch_bounds__(128)
 k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ state,
-          const float* __restrict__ goal, const StepState* __restrict__ st, int step_override,
-          int iter, float* __restrict__ part, float* __restrict__ Ctot)
+          const float* __restrict__ goal, StepState* st, int step_override,
+          int iter, AdjAcc acc, float* __restrict__ Ctot, float* __restrict__ grad_out,
+          float* __restrict__ J_out, float eta, float* __restrict__ cmd_out, int finalize)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const AdjointLayout L = adjoint_layout(pb);
@@ -134,65 +171,53 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int d = pb.d, H = pb.H, S = pb.S, M = pb.M, F = pb.d + 1, HD = pb.H * pb.d;
+    const int FS = adjoint_frame_stride(pb);
     const int n = blockIdx.x, I = H;
     const uint32_t step = step_override >= 0 ? static_cast<uint32_t>(step_override) : st->step;
     const int NO = pb.B + pb.O;
 
-    // ---- stage
-    for (int i = tid; i < HD; i += nt) s_mu[i] = mean[i];
-    for (int i = tid; i < d; i += nt) {
-        s_sigma[i] = pb.sigma[i];
-        s_qlo[i] = pb.qlo[i];
-        s_qhi[i] = pb.qhi[i];
+    // ---- stage: every table this CTA reads, as asynchronous copies issued at
+    // once (they land while the noise is drawn); the goal goes through s_cost,
+    // which the cost phase overwrites later
+    {
+        auto cp4 = [](void* dst, const void* src) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                         "l"(src)
+                         : "memory");
+        };
+        auto cp16 = [](void* dst, const void* src) {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                         "l"(src)
+                         : "memory");
+        };
+        for (int i = tid; i < HD; i += nt) cp4(s_mu + i, mean + i);
+        for (int i = tid; i < d; i += nt) {
+            cp4(s_sigma + i, pb.sigma + i);
+            cp4(s_qlo + i, pb.qlo + i);
+            cp4(s_qhi + i, pb.qhi + i);
+        }
+        for (int i = tid; i < 3 * d; i += nt) cp4(s_state + i, state + i);
+        for (int i = tid; i < 7; i += nt) cp4(s_cost + i, goal + i);
+        for (int i = tid; i < H; i += nt) {
+            cp4(s_dt + i, pb.dt + i);
+            cp4(s_gpow + i, pb.gpow + i);
+            cp4(s_vmax + i, pb.vmax + i);
+        }
+        if (pb.spline)
+            for (int i = tid; i < H * S; i += nt) cp4(s_basis + i, pb.basis + i);
+        for (int i = tid; i < d * 8; i += nt) cp4(s_dhx + i, pb.dhx + i);
+        for (int i = tid; i < d + 2; i += nt) cp4(s_first + i, pb.link_first + i);
+        for (int i = tid; i < F; i += nt) cp16(s_lb + i, pb.lbound + i);
+        for (int i = tid; i < M; i += nt) cp16(s_sph + i, pb.sph + i);
+        for (int i = tid; i < pb.P; i += nt) cp4(s_pairs + i, pb.pairs + i);
+        for (int i = tid; i < pb.NPB; i += nt) cp16(s_pblk + i, pb.pblk + i);
+        for (int i = tid; i < 6 * pb.B; i += nt) cp4(s_boxes + i, pb.boxes + i);
+        for (int i = tid; i < pb.O; i += nt) cp16(s_wsph + i, pb.wsph + i);
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    for (int i = tid; i < 3 * d; i += nt) s_state[i] = state[i];
     for (int i = tid; i < H; i += nt) {
-        s_dt[i] = pb.dt[i];
-        s_gpow[i] = pb.gpow[i];
-        s_vmax[i] = pb.vmax[i];
         s_keyw[i] = 0ull;
         s_keys[i] = 0ull;
-    }
-    if (pb.spline)
-        for (int i = tid; i < H * S; i += nt) s_basis[i] = pb.basis[i];
-    for (int i = tid; i < d * 8; i += nt) s_dhx[i] = pb.dhx[i];
-    for (int i = tid; i < d + 2; i += nt) s_first[i] = pb.link_first[i];
-    for (int i = tid; i < F; i += nt) s_lb[i] = pb.lbound[i];
-    for (int i = tid; i < M; i += nt) {
-        s_sph[i] = pb.sph[i];
-        int f = 0;
-        while (f < d && i >= pb.link_first[f + 1]) ++f;
-        s_slink[i] = f;
-    }
-    for (int i = tid; i < pb.P; i += nt) s_pairs[i] = pb.pairs[i];
-    for (int i = tid; i < pb.NPB; i += nt) s_pblk[i] = pb.pblk[i];
-    for (int i = tid; i < pb.B; i += nt) {
-        float b[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            b[k] = pb.boxes[i * 6 + k];
-            s_boxes[i * 6 + k] = b[k];
-        }
-        s_boxlh[2 * i] = make_float4(b[0] - b[3], b[1] - b[4], b[2] - b[5], 0.f);
-        s_boxlh[2 * i + 1] = make_float4(b[0] + b[3], b[1] + b[4], b[2] + b[5], 0.f);
-    }
-    for (int i = tid; i < pb.O; i += nt) s_wsph[i] = pb.wsph[i];
-    if (tid == 0) {
-        const float qn = rsqrtf(goal[3] * goal[3] + goal[4] * goal[4] + goal[5] * goal[5] +
-                                goal[6] * goal[6]);
-        const float w = goal[3] * qn, x = goal[4] * qn, y = goal[5] * qn, z = goal[6] * qn;
-        s_goal[0] = 1.f - 2.f * (y * y + z * z);
-        s_goal[1] = 2.f * (x * y - w * z);
-        s_goal[2] = 2.f * (x * z + w * y);
-        s_goal[3] = 2.f * (x * y + w * z);
-        s_goal[4] = 1.f - 2.f * (x * x + z * z);
-        s_goal[5] = 2.f * (y * z - w * x);
-        s_goal[6] = 2.f * (x * z - w * y);
-        s_goal[7] = 2.f * (y * z + w * x);
-        s_goal[8] = 1.f - 2.f * (x * x + y * y);
-        s_goal[9] = goal[0];
-        s_goal[10] = goal[1];
-        s_goal[11] = goal[2];
     }
     // ---- noise of particle n (same stream as the rollout)
     const int per = S * d;
@@ -214,7 +239,40 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     } else {
         for (int i = tid; i < per; i += nt) s_eps[i] = pb.halton[static_cast<size_t>(n) * per + i];
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
+    // ---- derived tables: sphere -> frame, box bounds, the goal rotation
+    for (int i = tid; i < M; i += nt) {
+        int f = 0;
+        while (f < d && i >= s_first[f + 1]) ++f;
+        s_slink[i] = f;
+    }
+    for (int i = tid; i < pb.B; i += nt) {
+        const float* b = s_boxes + i * 6;
+        s_boxlh[2 * i] = make_float4(b[0] - b[3], b[1] - b[4], b[2] - b[5], 0.f);
+        s_boxlh[2 * i + 1] = make_float4(b[0] + b[3], b[1] + b[4], b[2] + b[5], 0.f);
+    }
+    if (tid == 0) {
+        const float* goal_s = s_cost;
+        const float qn = rsqrtf(goal_s[3] * goal_s[3] + goal_s[4] * goal_s[4] + goal_s[5] * goal_s[5] +
+                                goal_s[6] * goal_s[6]);
+        const float w = goal_s[3] * qn, x = goal_s[4] * qn, y = goal_s[5] * qn, z = goal_s[6] * qn;
+        float gr[12];
+        gr[0] = 1.f - 2.f * (y * y + z * z);
+        gr[1] = 2.f * (x * y - w * z);
+        gr[2] = 2.f * (x * z + w * y);
+        gr[3] = 2.f * (x * y + w * z);
+        gr[4] = 1.f - 2.f * (x * x + z * z);
+        gr[5] = 2.f * (y * z - w * x);
+        gr[6] = 2.f * (x * z - w * y);
+        gr[7] = 2.f * (y * z + w * x);
+        gr[8] = 1.f - 2.f * (x * x + y * y);
+        gr[9] = goal_s[0];
+        gr[10] = goal_s[1];
+        gr[11] = goal_s[2];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s_goal[k] = gr[k];
+    }
     for (int i = tid; i < HD; i += nt) {
         const int h = i / d, j = i - h * d;
         float e;
@@ -241,7 +299,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     // ---- per step h: FK frames
     for (int h = tid; h < I; h += nt) {
         const float* th = s_th + h * d;
-        float4* fr = s_frame + h * F * 3;
+        float4* fr = s_frame + h * FS;
         float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
         float pp[3] = {0.f, 0.f, 0.f};
         fr[0] = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -277,7 +335,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         const float* thd = s_thd + h * d;
         const float* uh = s_u + h * d;
         const float* up = (h == 0) ? s_state + 2 * d : uh - d;
-        const float4* fr = s_frame + h * F * 3;
+        const float4* fr = s_frame + h * FS;
         float R[9], pp[3];  // the end effector's frame
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -496,7 +554,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         for (int idx = ct; idx < I * F; idx += coll_threads) {
             const int item = idx / F, f = idx - item * F;
             const float4 q = s_lb[f];
-            const float4* T = s_frame + (item * F + f) * 3;
+            const float4* T = s_frame + item * FS + f * 3;
             const float4 r0 = T[0], r1 = T[1], r2 = T[2];
             const float cx = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
             const float cy = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
@@ -526,7 +584,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     for (int idx = ct; idx < I * M; idx += coll_threads) {
         const int item = idx / M, s = idx - item * M;
         const float4 q = s_sph[s];
-        const float4* T = s_frame + (item * F + s_slink[s]) * 3;
+        const float4* T = s_frame + item * FS + s_slink[s] * 3;
         const float4 r0 = T[0], r1 = T[1], r2 = T[2];
         float4 c;
         c.x = fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w)));
@@ -620,7 +678,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
 
     // ---- collision gradients of each step's minimiser
     for (int h = tid; h < I; h += nt) {
-        const float4* fr = s_frame + h * F * 3;
+        const float4* fr = s_frame + h * FS;
         float gth[kMaxDof];
 #pragma unroll
         for (int k = 0; k < kMaxDof; ++k) gth[k] = (k < d) ? s_gth[h * d + k] : 0.f;
@@ -706,43 +764,46 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     }
     __syncthreads();
 
-    // ---- this particle's row of partials: dC_n/du_n (zero for null particles), C_n
-    float* row = part + static_cast<size_t>(n) * (HD + 1);
-    for (int o = tid; o < HD; o += nt) row[o] = (n >= pb.n_null) ? s_u[o] : 0.f;
+    // ---- this particle's row: dC_n/du_n (none for null particles), C_n
+    if (n >= pb.n_null)
+        for (int o = tid; o < HD; o += nt) adj_add(acc.sum + o, s_u[o], kAdjGradScale, acc.bad);
+    __shared__ int s_last;
     if (tid == 0) {
         float C = 0.f;
         for (int h = 0; h < H; ++h) C = fmaf(s_gpow[h], s_cost[h], C);
-        row[HD] = C;
         if (Ctot) Ctot[n] = C;
+        adj_add(acc.sum + HD, C, kAdjCostScale, acc.bad);
     }
-}
-
-// Column sums of the partial rows in a fixed order: block o < H*d gives
-// grad[o] = (1/N) sum_n dC_n/du_n[o] (and with eta != 0 steps mu[o] by
-// -eta grad[o]); block H*d gives J = (1/N) sum_n C_n.  With `finalize` the
-// step ends here: next_command from the refined mean and the step counter.
-__global__ void __launch_bounds__(128)
-k_adjoint_reduce(Problem pb, const float* __restrict__ part, float* __restrict__ grad_out,
-                 float* __restrict__ J_out, float eta, StepState* st, float* __restrict__ cmd_out,
-                 int finalize)
-{
-    __shared__ float sh[32];
-    const int HD = pb.H * pb.d, o = blockIdx.x;
-    float acc = 0.f;
-    for (int n = threadIdx.x; n < pb.N; n += blockDim.x) acc += part[static_cast<size_t>(n) * (HD + 1) + o];
-    const float tot = block_sum(acc, sh) / static_cast<float>(pb.N);
-    if (threadIdx.x != 0) return;
-    if (o < HD) {
-        if (grad_out) grad_out[o] = tot;
-        if (eta != 0.f) {
-            const float m = pb.mu[o] - eta * tot;
-            pb.mu[o] = m;
-            if (finalize && o < pb.d) cmd_out[o] = m;
-        } else if (finalize && o < pb.d) {
-            cmd_out[o] = pb.mu[o];
+    __syncthreads();  // every add of this CTA issued
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(acc.count, 1u) == static_cast<unsigned int>(pb.N - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // ---- the last CTA: the sums are complete
+    __threadfence();
+    const bool bad = *reinterpret_cast<volatile int*>(acc.bad) != 0;
+    const float invN = 1.f / static_cast<float>(pb.N);
+    for (int o = tid; o <= HD; o += nt) {
+        const long long v = static_cast<long long>(atomicExch(acc.sum + o, 0ull));  // read and clear
+        const float tot = bad ? NAN
+                              : static_cast<float>(static_cast<double>(v) / (o < HD ? kAdjGradScale : kAdjCostScale)) * invN;
+        if (o < HD) {
+            if (grad_out) grad_out[o] = tot;
+            float m = pb.mu[o];
+            if (eta != 0.f && !bad) {
+                m -= eta * tot;
+                pb.mu[o] = m;
+            }
+            if (finalize && o < d) cmd_out[o] = m;
+        } else {
+            if (J_out) *J_out = tot;
         }
-    } else {
-        if (J_out) *J_out = tot;
+    }
+    if (tid == 0) {
+        *acc.count = 0u;
+        *acc.bad = 0;
         if (finalize) st->step += 1;
     }
 }
