@@ -215,6 +215,14 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         for (int i = tid; i < pb.O; i += nt) cp16(s_wsph + i, pb.wsph + i);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
+    __shared__ int s_task_v;
+    __shared__ int s_cflag_v;
+    int* s_task = &s_task_v;
+    volatile int* s_cflag = &s_cflag_v;
+    if (tid == 0) {
+        s_task_v = 0;
+        s_cflag_v = 0;
+    }
     for (int i = tid; i < H; i += nt) {
         s_keyw[i] = 0ull;
         s_keys[i] = 0ull;
@@ -328,6 +336,48 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     const bool cost_warp = tid < cost_warps * 32;
     const int ct = tid - cost_warps * 32;  // collision thread index
     auto coll_sync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(coll_threads) : "memory"); };
+    const bool bp = pb.broadphase != 0;
+    // the self-collision tasks, dealt a warp's worth at a time
+    auto coll_self_tasks = [&]() {
+        const int lane = tid & 31, ntask = I * pb.NPB;
+        while (true) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(s_task, 32);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= ntask) break;
+            const int idx = base + lane;
+            if (idx >= ntask) continue;
+            const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
+            const uint4 blk = s_pblk[bk];
+            if (bp) {  // the two links' bounds apart: no pair of the block touches
+                const float4 A = s_lcent[item * F + s_slink[blk.x]], B2 = s_lcent[item * F + s_slink[blk.z]];
+                const float ex = A.x - B2.x, ey = A.y - B2.y, ez = A.z - B2.z;
+                const float rr = A.w + B2.w;
+                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rr * rr) continue;
+            }
+            const float4* ci = s_cent + item * M;
+            float depth = 0.f;
+            int best = -1;
+            float4 cb[8];  // the second link's spheres of the block, in registers (absent ones far away)
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                cb[k] = k < static_cast<int>(blk.w) ? ci[blk.z + k] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            for (uint32_t a = blk.x; a < blk.y; ++a) {
+                const float4 ca = ci[a];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float ex = ca.x - cb[k].x, ey = ca.y - cb[k].y, ez = ca.z - cb[k].z;
+                    const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const float rs = ca.w + cb[k].w;
+                    if (dist2 < rs * rs && rs - sqrtf(dist2) > depth) {
+                        depth = rs - sqrtf(dist2);
+                        best = static_cast<int>((a - blk.x) * 8 + k);
+                    }
+                }
+            }
+            if (best >= 0) atomicMax(s_keys + item, depth_key(depth, static_cast<uint32_t>(bk * 64 + best)));
+        }
+    };
 
     // ---- per step h: non-collision costs and their gradients
     for (int h = tid; cost_warp && h < I; h += cost_warps * 32) {
@@ -477,14 +527,18 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         if (m < pb.k_m) {
             c_manip = 1.f - m;
             if (m > 0.f && pb.w_manip != 0.f) {
-                float Jp[kMaxDof][6];
+                // column i of J0^+ (6 values, then dropped) contributes to tr_k for every k < i;
+                // each tr_k is still summed over i in ascending order
+                float tr[kMaxDof];
+#pragma unroll
+                for (int k = 0; k < kMaxDof; ++k) tr[k] = 0.f;
 #pragma unroll
                 for (int i = 0; i < kMaxDof; ++i) {
                     if (i < d) {
-                        const float4 r0 = fr[(i + 1) * 3], r1 = fr[(i + 1) * 3 + 1], r2 = fr[(i + 1) * 3 + 2];
-                        float x[6] = {r1.w * r2.z - r2.w * r1.z, r2.w * r0.z - r0.w * r2.z,
-                                      r0.w * r1.z - r1.w * r0.z, r0.z, r1.z, r2.z};
-                        float y[6];
+                        const float4 a0 = fr[(i + 1) * 3], a1 = fr[(i + 1) * 3 + 1], a2 = fr[(i + 1) * 3 + 2];
+                        float x[6] = {a1.w * a2.z - a2.w * a1.z, a2.w * a0.z - a0.w * a2.z,
+                                      a0.w * a1.z - a1.w * a0.z, a0.z, a1.z, a2.z};
+                        float y[6], jp[6];
 #pragma unroll
                         for (int a = 0; a < 6; ++a) {  // R^T y = x (R^T lower triangular)
                             float sacc = x[a];
@@ -493,23 +547,16 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                             y[a] = sacc / G.r[GramFactor::at(a, a)];
                         }
 #pragma unroll
-                        for (int a = 5; a >= 0; --a) {  // R x = y
+                        for (int a = 5; a >= 0; --a) {  // R jp = y
                             float sacc = y[a];
 #pragma unroll
-                            for (int b = a + 1; b < 6; ++b) sacc = fmaf(-G.r[GramFactor::at(a, b)], Jp[i][b], sacc);
-                            Jp[i][a] = sacc / G.r[GramFactor::at(a, a)];
+                            for (int b = a + 1; b < 6; ++b) sacc = fmaf(-G.r[GramFactor::at(a, b)], jp[b], sacc);
+                            jp[a] = sacc / G.r[GramFactor::at(a, a)];
                         }
-                    }
-                }
 #pragma unroll
-                for (int k = 0; k < kMaxDof; ++k) {
-                    if (k < d) {
-                        const float4 k0 = fr[(k + 1) * 3], k1 = fr[(k + 1) * 3 + 1], k2 = fr[(k + 1) * 3 + 2];
-                        float tr = 0.f;
-#pragma unroll
-                        for (int i = k + 1; i < kMaxDof; ++i) {
-                            if (i < d) {
-                                const float4 a0 = fr[(i + 1) * 3], a1 = fr[(i + 1) * 3 + 1], a2 = fr[(i + 1) * 3 + 2];
+                        for (int k = 0; k < kMaxDof; ++k) {
+                            if (k < i) {
+                                const float4 k0 = fr[(k + 1) * 3], k1 = fr[(k + 1) * 3 + 1], k2 = fr[(k + 1) * 3 + 2];
                                 // dz = z_k x z_i ; do = z_k x (o_i - o_k)
                                 const float dzx = k1.z * a2.z - k2.z * a1.z, dzy = k2.z * a0.z - k0.z * a2.z,
                                             dzz = k0.z * a1.z - k1.z * a0.z;
@@ -520,13 +567,14 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                                 const float vx = (doy * a2.z - doz * a1.z) + (a1.w * dzz - a2.w * dzy);
                                 const float vy = (doz * a0.z - dox * a2.z) + (a2.w * dzx - a0.w * dzz);
                                 const float vz = (dox * a1.z - doy * a0.z) + (a0.w * dzy - a1.w * dzx);
-                                tr += Jp[i][0] * vx + Jp[i][1] * vy + Jp[i][2] * vz + Jp[i][3] * dzx +
-                                      Jp[i][4] * dzy + Jp[i][5] * dzz;
+                                tr[k] += jp[0] * vx + jp[1] * vy + jp[2] * vz + jp[3] * dzx + jp[4] * dzy + jp[5] * dzz;
                             }
                         }
-                        gth[k] -= pb.w_manip * m * tr;
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < kMaxDof; ++k)
+                    if (k < d) gth[k] -= pb.w_manip * m * tr[k];
             }
         }
         s_cost[h] = pb.w_pos * c_pos + pb.w_rot * c_rot + pb.w_stop * c_stop + pb.w_joint * c_joint +
@@ -542,11 +590,29 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         }
     }
 
+    if (cost_warp) {  // the cost warp: join the self-collision tasks once they are open (bounded wait)
+        auto now = []() {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            return t;
+        };
+        bool open = false;
+        if ((tid & 31) == 0) {
+            open = *s_cflag != 0;
+            const unsigned long long t0 = open ? 0ull : now();
+            for (uint32_t k = 1; !open; ++k) {
+                open = *s_cflag != 0;
+                if (!open && (k & 63u) == 0u && now() - t0 > 100000ull) break;  // 100 us: then leave it to them
+            }
+        }
+        open = __shfl_sync(0xffffffffu, open, 0);
+        __threadfence_block();  // (acquire: the centres and bounds written before the flag)
+        if (open) coll_self_tasks();
+    }
     // ---- broad phase (as in the rollout kernels): each step's link-bound centres
     // and, per (step, frame), the boxes and obstacle spheres its bound meets.  A
     // sphere can only touch what its link's bound touches, so the exact tests
     // below skip nothing that penetrates: the same depths and minimisers.
-    const bool bp = pb.broadphase != 0;
     const unsigned long long all_b = pb.B >= 64 ? ~0ull : (1ull << pb.B) - 1ull;
     const unsigned long long all_o = pb.O >= 64 ? ~0ull : (1ull << pb.O) - 1ull;
     if (!cost_warp) {  // the collision warps
@@ -635,34 +701,15 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
             atomicMax(s_keyw + item, depth_key(depth, static_cast<uint32_t>(s * NO + best)));
     }
     coll_sync();
-    // ---- self collision with its minimiser
-    for (int idx = ct; idx < I * pb.NPB; idx += coll_threads) {
-        const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
-        const uint4 blk = s_pblk[bk];
-        if (bp) {  // the two links' bounds apart: no pair of the block touches
-            const float4 A = s_lcent[item * F + s_slink[blk.x]], B2 = s_lcent[item * F + s_slink[blk.z]];
-            const float ex = A.x - B2.x, ey = A.y - B2.y, ez = A.z - B2.z;
-            const float rr = A.w + B2.w;
-            if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rr * rr) continue;
-        }
-        const float4* ci = s_cent + item * M;
-        float depth = 0.f;
-        int best = -1;
-        for (uint32_t a = blk.x; a < blk.y; ++a) {
-            const float4 ca = ci[a];
-            for (uint32_t k = 0; k < blk.w; ++k) {
-                const float4 cb = ci[blk.z + k];
-                const float ex = ca.x - cb.x, ey = ca.y - cb.y, ez = ca.z - cb.z;
-                const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                const float rs = ca.w + cb.w;
-                if (dist2 < rs * rs && rs - sqrtf(dist2) > depth) {
-                    depth = rs - sqrtf(dist2);
-                    best = static_cast<int>((a - blk.x) * 8 + k);
-                }
-            }
-        }
-        if (best >= 0) atomicMax(s_keys + item, depth_key(depth, static_cast<uint32_t>(bk * 64 + best)));
+    // ---- self collision with its minimiser: (step, pair block) tasks dealt
+    // 32 at a time from a shared counter; the cost warp joins once its own work
+    // is done (every task is taken once whoever takes it, and the minimiser is
+    // an atomic max: the same result in any order)
+    if (ct == 0) {  // (after the barrier that ended the world phase; release: the centres and bounds)
+        __threadfence_block();
+        *s_cflag = 1;
     }
+    coll_self_tasks();
     for (int idx = ct; idx < I * pb.P; idx += coll_threads) {
         const int item = idx / pb.P, k = idx - item * pb.P;
         const uint32_t pr = s_pairs[k];
