@@ -529,9 +529,11 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
             if (m > 0.f && pb.w_manip != 0.f) {
                 // column i of J0^+ (6 values, then dropped) contributes to tr_k for every k < i;
                 // each tr_k is still summed over i in ascending order
-                float tr[kMaxDof];
+                float tr[kMaxDof], inv_r[6];  // the factor's diagonal, inverted once for the solves
 #pragma unroll
                 for (int k = 0; k < kMaxDof; ++k) tr[k] = 0.f;
+#pragma unroll
+                for (int a = 0; a < 6; ++a) inv_r[a] = 1.f / G.r[GramFactor::at(a, a)];
 #pragma unroll
                 for (int i = 0; i < kMaxDof; ++i) {
                     if (i < d) {
@@ -544,14 +546,14 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                             float sacc = x[a];
 #pragma unroll
                             for (int b = 0; b < a; ++b) sacc = fmaf(-G.r[GramFactor::at(b, a)], y[b], sacc);
-                            y[a] = sacc / G.r[GramFactor::at(a, a)];
+                            y[a] = sacc * inv_r[a];
                         }
 #pragma unroll
                         for (int a = 5; a >= 0; --a) {  // R jp = y
                             float sacc = y[a];
 #pragma unroll
                             for (int b = a + 1; b < 6; ++b) sacc = fmaf(-G.r[GramFactor::at(a, b)], jp[b], sacc);
-                            jp[a] = sacc / G.r[GramFactor::at(a, a)];
+                            jp[a] = sacc * inv_r[a];
                         }
 #pragma unroll
                         for (int k = 0; k < kMaxDof; ++k) {
