@@ -71,6 +71,11 @@ __host__ __device__ inline AdjointLayout adjoint_layout(const Problem& pb)
     return L;
 }
 
+// Minimiser ids of a pair block: (first-link sphere - first) * 8 + second-link
+// slot, below 64 * 8 = 512 for up to 64 spheres on the first link; the
+// leftover pairs' ids start at 2^24, above every block's.
+constexpr uint32_t kSelfBlockIds = 512;
+
 __device__ __forceinline__ unsigned long long depth_key(float depth, uint32_t idx)
 {
     return (static_cast<unsigned long long>(__float_as_uint(depth)) << 32) | (0xffffffffu - idx);
@@ -337,45 +342,70 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     const int ct = tid - cost_warps * 32;  // collision thread index
     auto coll_sync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(coll_threads) : "memory"); };
     const bool bp = pb.broadphase != 0;
-    // the self-collision tasks, dealt a warp's worth at a time
+    // the self-collision tasks: (step, pair block) dealt a warp's worth at a
+    // time; the blocks whose link bounds overlap are taken four at a time, eight
+    // lanes each (lane r of a group tests the block's first-link spheres r, r + 8,
+    // ... against its second-link spheres), so that the exact tests are spread
+    // over the warp instead of one lane per block
     auto coll_self_tasks = [&]() {
         const int lane = tid & 31, ntask = I * pb.NPB;
+        const int grp = lane >> 3, r8 = lane & 7;
         while (true) {
             int base = 0;
             if (lane == 0) base = atomicAdd(s_task, 32);
             base = __shfl_sync(0xffffffffu, base, 0);
             if (base >= ntask) break;
             const int idx = base + lane;
-            if (idx >= ntask) continue;
-            const int item = idx / pb.NPB, bk = idx - item * pb.NPB;
-            const uint4 blk = s_pblk[bk];
-            if (bp) {  // the two links' bounds apart: no pair of the block touches
+            bool live = idx < ntask;
+            if (live && bp) {  // the two links' bounds apart: no pair of the block touches
+                const int item = idx / pb.NPB;
+                const uint4 blk = s_pblk[idx - item * pb.NPB];
                 const float4 A = s_lcent[item * F + s_slink[blk.x]], B2 = s_lcent[item * F + s_slink[blk.z]];
                 const float ex = A.x - B2.x, ey = A.y - B2.y, ez = A.z - B2.z;
                 const float rr = A.w + B2.w;
-                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rr * rr) continue;
+                live = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rr * rr;
             }
-            const float4* ci = s_cent + item * M;
-            float depth = 0.f;
-            int best = -1;
-            float4 cb[8];  // the second link's spheres of the block, in registers (absent ones far away)
+            unsigned alive = __ballot_sync(0xffffffffu, live);
+            while (alive) {
+                const unsigned src = __fns(alive, 0, grp + 1);  // this group's block: the (grp+1)-th live lane
+                const int tix = __shfl_sync(0xffffffffu, idx, static_cast<int>(src & 31u));
+                unsigned long long key = 0ull;
+                int item = 0;
+                if (src != 0xffffffffu) {
+                    item = tix / pb.NPB;
+                    const int bk = tix - item * pb.NPB;
+                    const uint4 blk = s_pblk[bk];
+                    const float4* ci = s_cent + item * M;
+                    float4 cb[8];  // the block's second-link spheres (absent ones far away)
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                cb[k] = k < static_cast<int>(blk.w) ? ci[blk.z + k] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
-            for (uint32_t a = blk.x; a < blk.y; ++a) {
-                const float4 ca = ci[a];
+                    for (int k = 0; k < 8; ++k)
+                        cb[k] = k < static_cast<int>(blk.w) ? ci[blk.z + k] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                    float depth = 0.f;
+                    int best = -1;
+                    for (uint32_t a = blk.x + r8; a < blk.y; a += 8) {
+                        const float4 ca = ci[a];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const float ex = ca.x - cb[k].x, ey = ca.y - cb[k].y, ez = ca.z - cb[k].z;
-                    const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    const float rs = ca.w + cb[k].w;
-                    if (dist2 < rs * rs && rs - sqrtf(dist2) > depth) {
-                        depth = rs - sqrtf(dist2);
-                        best = static_cast<int>((a - blk.x) * 8 + k);
+                        for (int k = 0; k < 8; ++k) {
+                            const float ex = ca.x - cb[k].x, ey = ca.y - cb[k].y, ez = ca.z - cb[k].z;
+                            const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                            const float rs = ca.w + cb[k].w;
+                            if (dist2 < rs * rs && rs - sqrtf(dist2) > depth) {
+                                depth = rs - sqrtf(dist2);
+                                best = static_cast<int>((a - blk.x) * 8 + k);
+                            }
+                        }
                     }
+                    if (best >= 0) key = depth_key(depth, static_cast<uint32_t>(bk * kSelfBlockIds + best));
                 }
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) {  // the group's deepest pair (lowest id on a tie)
+                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+                    key = other > key ? other : key;
+                }
+                if (r8 == 0 && key) atomicMax(s_keys + item, key);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) alive &= alive - 1u;  // the four blocks just taken
             }
-            if (best >= 0) atomicMax(s_keys + item, depth_key(depth, static_cast<uint32_t>(bk * 64 + best)));
         }
     };
 
@@ -629,6 +659,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
             const float cz = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
             s_lcent[idx] = make_float4(cx, cy, cz, q.w);
             unsigned long long mb = 0ull, mo = 0ull;
+#pragma unroll 4
             for (int b = 0; b < pb.B; ++b) {
                 const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
                 const float ex = cx - fminf(fmaxf(cx, lo.x), hi.x);
@@ -636,6 +667,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                 const float ez = cz - fminf(fmaxf(cz, lo.z), hi.z);
                 if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < q.w * q.w) mb |= 1ull << b;
             }
+#pragma unroll 4
             for (int k = 0; k < pb.O; ++k) {
                 const float4 w = s_wsph[k];
                 const float ex = cx - w.x, ey = cy - w.y, ez = cz - w.z;
@@ -778,8 +810,8 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                 a = pr & 0xffff;
                 b = pr >> 16;
             } else {
-                const uint4 blk = s_pblk[id / 64];
-                const uint32_t r = id % 64;
+                const uint4 blk = s_pblk[id / kSelfBlockIds];
+                const uint32_t r = id % kSelfBlockIds;
                 a = blk.x + r / 8;
                 b = blk.z + r % 8;
             }
