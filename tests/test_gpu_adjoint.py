@@ -125,3 +125,56 @@ def test_refined_step_matches_oracle(N):
         ctl0.step(state, goal)
         mu0, _ = ctl0.get_distribution()
     assert np.abs(mu - mu0).max() > 1e-4
+
+
+def _swap_spheres(robot, a, b):
+    """The robot with spheres a and b (of one link) exchanged, pairs renumbered."""
+    order = np.arange(len(robot.sphere_link))
+    order[[a, b]] = order[[b, a]]
+    pairs = np.sort(order[np.asarray(robot.pairs)], axis=1)
+    return W.Robot(robot.dh, robot.q_min, robot.q_max, np.asarray(robot.sphere_link)[order],
+                   np.asarray(robot.spheres)[order], pairs)
+
+
+def test_cost_grad_more_than_eight_spheres_per_link():
+    """Nine spheres per link, so that a pair block's first link has more rows
+    than the eight slots of its second.  In this folded case every item
+    self-collides, and with spheres 16 and 17 of link 2 exchanged the deepest
+    pair of most items lies in that link's ninth row (checked on the oracle's
+    FK).  The gradient and J match the oracle's adjoint, and the broad phase on
+    and off give the same bits."""
+    wl = W.config_paper(5)
+    wl.robot = _swap_spheres(W.make_robot(5, 7, spheres_per_link=9), 16, 17)
+    p = wl.params.replace(N=64)
+    seed, step, it = 5, 3, 1
+    mu, sig = f32(W.make_mean(seed, p.H, 7, 0.8)), f32(W.make_sigma(seed, 7))
+    state, goal = f32(W.make_state(seed, 7)), f32(wl.goal)
+    o = oracle.Oracle(wl.robot, wl.world, p)
+    eps = o.noise(step, it)
+    roll = o.rollout(state, goal, mu, sig, eps)
+    active = roll["terms"][..., 5] > 0
+    assert active.mean() > 0.5
+    sl, sp, pairs = np.asarray(wl.robot.sphere_link), np.asarray(wl.robot.spheres), np.asarray(wl.robot.pairs)
+    first = {int(l): int(np.argmax(sl == l)) for l in np.unique(sl)}
+    late = 0
+    for n, h in list(zip(*np.nonzero(active)))[::8]:
+        fr = o.fk(roll["theta"][n, h])
+        c = np.array([(fr[sl[s]] @ np.append(sp[s, :3], 1.0))[:3] for s in range(len(sl))])
+        depth = sp[pairs[:, 0], 3] + sp[pairs[:, 1], 3] - np.linalg.norm(c[pairs[:, 0]] - c[pairs[:, 1]], axis=1)
+        a = pairs[int(np.argmax(depth)), 0]
+        late += a - first[int(sl[a])] >= 8
+    assert late > 10
+    oJ, og = o.cost_grad(state, goal, mu, sig, eps)
+    out = []
+    for bp in (True, False):
+        with Controller(wl.robot, wl.world, p) as ctl:
+            ctl.set_broadphase(bp)
+            ctl.set_distribution(mu, sig)
+            J, g = ctl.cost_grad(cuda(mu), cuda(state), cuda(goal), step, it)
+            torch.cuda.synchronize()
+            out.append((float(host(J)[0]), host(g)))
+    assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
+    J, g = out[0]
+    assert abs(J - oJ) <= TOL_COST * max(1.0, abs(oJ))
+    scale = max(1e-6, np.abs(og).max())
+    assert max_rel(g, og, scale) < 1e-4, max_rel(g, og, scale)
