@@ -141,21 +141,6 @@ __device__ __forceinline__ float ball_depth(const float* __restrict__ fr, int la
     return depth;
 }
 
-// The exact sphere tests of one frame against one box / obstacle sphere, out of
-// line: the broad phase calls them only where a link bound meets the obstacle, so
-// one shared copy keeps the per-frame call sites small.
-__device__ __noinline__ float box_depth_cold(const float* __restrict__ fr, int lane, const float4* __restrict__ sph,
-                                             int s0, int s1, const float* __restrict__ box, float depth)
-{
-    return box_depth(fr, lane, sph, s0, s1, box, depth);
-}
-
-__device__ __noinline__ float ball_depth_cold(const float* __restrict__ fr, int lane, const float4* __restrict__ sph,
-                                              int s0, int s1, float4 w, float depth)
-{
-    return ball_depth(fr, lane, sph, s0, s1, w, depth);
-}
-
 // World collision without the broad phase: every sphere of every frame against
 // every obstacle (the same tests in the same order as the inline form).  Out of
 // line, so that this cold path does not sit in the hot instruction stream.
@@ -622,6 +607,8 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                         hi[2] = fmaxf(hi[2], cbz[f] + r);
                     }
                 }
+                // the lane's own box (its item's link bounds), kept before the warp's union
+                const float llo0 = lo[0], llo1 = lo[1], llo2 = lo[2], lhi0 = hi[0], lhi1 = hi[1], lhi2 = hi[2];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -653,28 +640,56 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                             const float* box = pb.boxes + kk * 6;
                             const float lox = box[0] - box[3], loy = box[1] - box[4], loz = box[2] - box[5];
                             const float hix = box[0] + box[3], hiy = box[1] + box[4], hiz = box[2] + box[5];
+                            // clear of the lane's box: no link bound of the item meets the box
+                            if (!(lox <= lhi0 && hix >= llo0 && loy <= lhi1 && hiy >= llo1 && loz <= lhi2 &&
+                                  hiz >= llo2))
+                                continue;
+                            unsigned fm = 0u;  // the frames whose bound meets the box
 #pragma unroll
                             for (int f = 0; f <= kMaxDof; ++f) {
                                 if (f < F && first[f] < first[f + 1]) {
                                     const float ex = cbx[f] - fminf(fmaxf(cbx[f], lox), hix);
                                     const float ey = cby[f] - fminf(fmaxf(cby[f], loy), hiy);
                                     const float ez = cbz[f] - fminf(fmaxf(cbz[f], loz), hiz);
-                                    if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < lbf[f].w * lbf[f].w)
-                                        dworld = box_depth_cold(s_fr + f * 12 * 32, lane, pb.sph, first[f],
-                                                                first[f + 1], box, dworld);
+                                    if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < lbf[f].w * lbf[f].w) fm |= 1u << f;
                                 }
+                            }
+                            // each lane its own frames, the lanes side by side (depths combine by max:
+                            // any order gives the same bits)
+                            while (fm) {
+                                const int f = __ffs(fm) - 1;
+                                fm &= fm - 1u;
+                                int s0 = 0, s1 = 0;
+#pragma unroll
+                                for (int g = 0; g <= kMaxDof; ++g)
+                                    if (g == f) s0 = first[g], s1 = first[g + 1];
+                                dworld = box_depth(s_fr + f * 12 * 32, lane, pb.sph, s0, s1, box, dworld);
                             }
                         } else {
                             const float4 w = pb.wsph[kk - pb.B];
+                            {  // clear of the lane's box: no link bound of the item reaches the ball
+                                const float ex = w.x - fminf(fmaxf(w.x, llo0), lhi0);
+                                const float ey = w.y - fminf(fmaxf(w.y, llo1), lhi1);
+                                const float ez = w.z - fminf(fmaxf(w.z, llo2), lhi2);
+                                if (!(fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= w.w * w.w)) continue;
+                            }
+                            unsigned fm = 0u;
 #pragma unroll
                             for (int f = 0; f <= kMaxDof; ++f) {
                                 if (f < F && first[f] < first[f + 1]) {
                                     const float ex = cbx[f] - w.x, ey = cby[f] - w.y, ez = cbz[f] - w.z;
                                     const float rb = lbf[f].w + w.w;
-                                    if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rb * rb)
-                                        dworld = ball_depth_cold(s_fr + f * 12 * 32, lane, pb.sph, first[f],
-                                                                 first[f + 1], w, dworld);
+                                    if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rb * rb) fm |= 1u << f;
                                 }
+                            }
+                            while (fm) {
+                                const int f = __ffs(fm) - 1;
+                                fm &= fm - 1u;
+                                int s0 = 0, s1 = 0;
+#pragma unroll
+                                for (int g = 0; g <= kMaxDof; ++g)
+                                    if (g == f) s0 = first[g], s1 = first[g + 1];
+                                dworld = ball_depth(s_fr + f * 12 * 32, lane, pb.sph, s0, s1, w, dworld);
                             }
                         }
                     }
