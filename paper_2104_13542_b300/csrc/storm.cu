@@ -1823,7 +1823,7 @@ int validate(const storm_robot* r, const storm_world* w, const storm_params* p, 
 
 // Tables live in one device block; offsets in bytes, 256-aligned.
 struct TablePlan {
-    size_t dhx, qlo, qhi, sph, first, pairs, pblk, lbound, boxes, wsph, dt, gpow, vmax, basis, halton,
+    size_t dhx, qlo, qhi, sph, first, pairs, pblk, lbound, lcap, boxes, wsph, dt, gpow, vmax, basis, halton,
         mu, sigma, prefix, prime, raw, total;
 };
 
@@ -1844,6 +1844,7 @@ TablePlan plan_tables(const Problem& pb, int cap_boxes, int cap_wsph, int raw_do
     t.pairs = take(std::max(pb.P, 1) * 4);
     t.pblk = take(std::max(pb.NPB, 1) * 16);
     t.lbound = take((pb.d + 1) * 16);
+    t.lcap = take((pb.d + 1) * 32);
     t.boxes = take(std::max(cap_boxes, 1) * 6 * 4);
     t.wsph = take(std::max(cap_wsph, 1) * 16);
     t.dt = take(pb.H * 4);
@@ -2140,6 +2141,7 @@ struct HostTables {
     std::vector<uint32_t> pairs;
     std::vector<uint4> blocks;
     std::vector<float4> lbound;  // per frame: bounding sphere of its spheres (local)
+    std::vector<float4> lcap;    // per frame: capsule of its spheres (local), two float4
     std::vector<double> raw;  // dh | q_min | q_max | dt, read by the set-up kernel
     double k_jl = 0, qdd_max = 0, gamma = 0;
     int halton_scramble = 0;
@@ -2242,6 +2244,42 @@ void fill_problem(const storm_robot* r, const storm_world* w, const storm_params
         ht.lbound[f] = make_float4(static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
                                    static_cast<float>(R + 1e-4));
     }
+    // per frame: a capsule (the points within R of a segment) holding every
+    // sphere of the frame; the segment joins the two sphere centres farthest
+    // apart, R reaches the farthest sphere surface, padded by 1 mm, which covers
+    // FP32 rounding in the device's segment distances (their worst case, nearly
+    // parallel segments, is below 0.3 mm for links up to 1 m)
+    ht.lcap.assign(2 * (pb.d + 1), make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int f = 0; f <= pb.d; ++f) {
+        const int a = ht.first[f], b = ht.first[f + 1];
+        if (a == b) continue;
+        auto ctr = [&](int i, int k) { return static_cast<double>(ht.sph[4 * i + k]); };
+        int e0 = a, e1 = a;
+        double far = -1.0;
+        for (int i = a; i < b; ++i)
+            for (int j = i; j < b; ++j) {
+                double d2 = 0.0;
+                for (int k = 0; k < 3; ++k) d2 += (ctr(i, k) - ctr(j, k)) * (ctr(i, k) - ctr(j, k));
+                if (d2 > far) far = d2, e0 = i, e1 = j;
+            }
+        double seg[3], len2 = 0.0;
+        for (int k = 0; k < 3; ++k) seg[k] = ctr(e1, k) - ctr(e0, k), len2 += seg[k] * seg[k];
+        double R = 0.0;
+        for (int i = a; i < b; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += (ctr(i, k) - ctr(e0, k)) * seg[k];
+            s = len2 > 0.0 ? std::min(1.0, std::max(0.0, s / len2)) : 0.0;
+            double d2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double e = ctr(i, k) - (ctr(e0, k) + s * seg[k]);
+                d2 += e * e;
+            }
+            R = std::max(R, std::sqrt(d2) + ht.sph[4 * i + 3]);
+        }
+        ht.lcap[2 * f] = make_float4(ht.sph[4 * e0], ht.sph[4 * e0 + 1], ht.sph[4 * e0 + 2],
+                                     static_cast<float>(R + 1e-3));
+        ht.lcap[2 * f + 1] = make_float4(ht.sph[4 * e1], ht.sph[4 * e1 + 1], ht.sph[4 * e1 + 2], 0.f);
+    }
     pb.broadphase = 1;
     ht.boxes.assign(6 * std::max(pb.B, 1), 0.f);
     ht.wsph.assign(4 * std::max(pb.O, 1), 0.f);
@@ -2294,6 +2332,8 @@ cudaError_t upload_problem(Problem& pb, const HostTables& ht, char* base, const 
     put(pb.pblk, ht.blocks.data(), 16 * ht.blocks.size());
     pb.lbound = reinterpret_cast<float4*>(base + t.lbound);
     put(pb.lbound, ht.lbound.data(), 16 * ht.lbound.size());
+    pb.lcap = reinterpret_cast<float4*>(base + t.lcap);
+    put(pb.lcap, ht.lcap.data(), 16 * ht.lcap.size());
     put(pb.boxes, ht.boxes.data(), 4 * ht.boxes.size());
     put(pb.wsph, ht.wsph.data(), 4 * ht.wsph.size());
     put(d_raw, ht.raw.data(), 8 * ht.raw.size());

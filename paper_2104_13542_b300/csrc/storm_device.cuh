@@ -46,6 +46,7 @@ struct Problem {
     int NPB;                 // pair blocks
     const uint4* pblk;       // NPB: (a0, a1, b0, nb): spheres [a0, a1) x [b0, b0 + nb), nb <= 8
     const float4* lbound;    // d + 1: bounding sphere of each frame's spheres (local centre, radius)
+    const float4* lcap;      // 2 (d + 1): capsule of each frame's spheres, local: (end 0, radius), (end 1, 0)
     int broadphase;          // 1: exact sphere tests only where the link bounds overlap
     int dep_launch;          // 1: this rollout launch is a programmatic dependent
     int shift_view;          // 1: read mu shifted (row h = stored row h + 1, last row 0) once the

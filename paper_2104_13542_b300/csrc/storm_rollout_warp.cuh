@@ -9,8 +9,9 @@
 // (particle, joint)), the same FK / Jacobian / cost expressions, exact sphere
 // tests with the same formulas, and the same sequential discounted sum.  What
 // changes is the work schedule: no CTA barriers, Jacobian and bounding-sphere
-// centres in registers, and world obstacles culled once per warp against the
-// axis-aligned box enclosing every link bound of the warp's items.
+// centres in registers, world obstacles culled once per warp against the
+// axis-aligned box enclosing every link bound of the warp's items, and self
+// collision culled by link capsules (segment + radius) after the spheres.
 //
 // The pair and quad variants (kW = 2 or 4 warps per particle group) split
 // each item's work across warps.  Warp A draws the controls and integrates
@@ -34,8 +35,7 @@
 struct WarpPlan {
     int Lp, PW, SL;  // lanes per particle, particles per warp, items per lane
     int frame;       // kW x F x 12 x 32: link frames, row-major [R | p] rows, lane-minor, one copy per warp
-    int cb;          // kW x F x 3 x 32: link bounding-sphere centres, lane-minor, one copy per warp
-    int fstride, cstride;  // one warp's frame / centre copy
+    int fstride;     // one warp's frame copy
     int eps;         // PW x S x d noise
     int u, th, thd;  // PW x H x d controls and joint states
     int c;           // PW x H running costs
@@ -64,9 +64,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Problem& pb, int kw)
         return o;
     };
     w.fstride = F * 12 * 32;
-    w.cstride = F * 3 * 32;
     w.frame = take(kw * w.fstride);
-    w.cb = take(kw * w.cstride);
     w.eps = take(w.PW * pb.S * pb.d);
     w.u = take(w.PW * pb.H * pb.d);
     w.th = take(w.PW * pb.H * pb.d);
@@ -176,6 +174,47 @@ __device__ __forceinline__ float3 frame_point(const float* __restrict__ fr, int 
                        fmaf(fr[8 * 32 + lane], q.x, fmaf(fr[9 * 32 + lane], q.y, fmaf(fr[10 * 32 + lane], q.z, fr[11 * 32 + lane]))));
 }
 
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
+
+// Squared distance between segments p0 + s (p1 - p0) and q0 + t (q1 - q0),
+// s, t in [0, 1]: the stationary point of the squared distance for s, t
+// inside, else the best t for the clamped s, or the best s at a clamped end of
+// t.  Each clamp keeps one point the nearest to the other, so in the nearly
+// parallel case, where the solve for s loses its digits, the result is off by
+// at most the segment length times the sine of their angle (that angle being
+// what makes the solve poor); the capsule radii are padded for it.
+__device__ __forceinline__ float seg_seg_dist2(float3 p0, float3 p1, float3 q0, float3 q1)
+{
+    const float3 d1 = make_float3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z);
+    const float3 d2 = make_float3(q1.x - q0.x, q1.y - q0.y, q1.z - q0.z);
+    const float3 r = make_float3(p0.x - q0.x, p0.y - q0.y, p0.z - q0.z);
+    const float a = fmaf(d1.x, d1.x, fmaf(d1.y, d1.y, d1.z * d1.z));
+    const float e = fmaf(d2.x, d2.x, fmaf(d2.y, d2.y, d2.z * d2.z));
+    const float b = fmaf(d1.x, d2.x, fmaf(d1.y, d2.y, d1.z * d2.z));
+    const float c = fmaf(d1.x, r.x, fmaf(d1.y, r.y, d1.z * r.z));
+    const float f = fmaf(d2.x, r.x, fmaf(d2.y, r.y, d2.z * r.z));
+    float s = 0.f, t = 0.f;
+    if (a > 1e-12f && e > 1e-12f) {
+        const float den = fmaf(a, e, -b * b);
+        s = den > 0.f ? clamp01(__fdividef(fmaf(b, f, -c * e), den)) : 0.f;
+        t = __fdividef(fmaf(b, s, f), e);
+        if (t < 0.f) {
+            t = 0.f;
+            s = clamp01(__fdividef(-c, a));
+        } else if (t > 1.f) {
+            t = 1.f;
+            s = clamp01(__fdividef(b - c, a));
+        }
+    } else if (e > 1e-12f) {
+        t = clamp01(__fdividef(f, e));
+    } else if (a > 1e-12f) {
+        s = clamp01(__fdividef(-c, a));
+    }
+    const float x = fmaf(d1.x, s, fmaf(-d2.x, t, r.x)), y = fmaf(d1.y, s, fmaf(-d2.y, t, r.y)),
+                z = fmaf(d1.z, s, fmaf(-d2.z, t, r.z));
+    return fmaf(x, x, fmaf(y, y, z * z));
+}
+
 // The warps of group `unit` meet (named barrier 1 + unit, `threads` threads).
 __device__ __forceinline__ void unit_sync(int unit, int threads)
 {
@@ -227,7 +266,6 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         if (lane <= kLinkPairs) reinterpret_cast<int*>(ws + W.lpb)[lane] = v;
     }
     float* s_fr = ws + W.frame + role * W.fstride;  // this warp's own frames
-    float* s_cb = ws + W.cb + role * W.cstride;
     float* s_eps = ws + W.eps;
     float* s_u = ws + W.u;
     float* s_th = ws + W.th;
@@ -485,14 +523,6 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                 cbx[i + 1] = cby[i + 1] = cbz[i + 1] = 0.f;
             }
         }
-#pragma unroll
-        for (int f = 0; f <= kMaxDof; ++f) {
-            if (f < F && do_selfc) {
-                s_cb[(f * 3 + 0) * 32 + lane] = cbx[f];
-                s_cb[(f * 3 + 1) * 32 + lane] = cby[f];
-                s_cb[(f * 3 + 2) * 32 + lane] = cbz[f];
-            }
-        }
 
         float part = 0.f;
         if (do_costs) {
@@ -701,9 +731,11 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         }
         trace_stamp(pb.trace, 4);
 
-        // ---- self collision, Eq. 13 reading: frame pairs whose bounds overlap
-        // (register tests over the compile-time list of pairs), then their
-        // pair blocks exactly; then the leftover pairs
+        // ---- self collision, Eq. 13 reading: frame pairs whose bounding
+        // spheres overlap (register tests over the compile-time list of pairs)
+        // and whose capsules meet, then their pair blocks exactly, each
+        // first-frame sphere first tested against the second frame's capsule;
+        // then the leftover pairs
         float dself = 0.f;
         const float pv = pred && valid ? pred[slot * kMlpRows] : 0.f;
         const bool do_self = do_selfc && valid && !(pred && (pb.self_mode == 2 || pv >= pb.self_margin));
@@ -746,6 +778,25 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                     }
                 }
             }
+            if (pb.broadphase) {  // of those, the frame pairs whose capsules meet too
+                uint32_t m = lp_hit;
+                while (m) {
+                    const int t = __ffs(m) - 1;
+                    m &= m - 1;
+                    int la = 0;  // t = link_pair_index(la, lk)
+#pragma unroll
+                    for (int f = 1; f < kMaxDof; ++f) la += t >= link_pair_index(f, f + 1);
+                    const int lk = t - link_pair_index(la, la + 1) + la + 1;
+                    const float4 a0 = pb.lcap[2 * la], a1 = pb.lcap[2 * la + 1];
+                    const float4 b0 = pb.lcap[2 * lk], b1 = pb.lcap[2 * lk + 1];
+                    const float* fa = s_fr + la * 12 * 32;
+                    const float* fb = s_fr + lk * 12 * 32;
+                    const float rr = a0.w + b0.w;
+                    if (seg_seg_dist2(frame_point(fa, lane, a0), frame_point(fa, lane, a1), frame_point(fb, lane, b0),
+                                      frame_point(fb, lane, b1)) >= rr * rr)
+                        lp_hit &= ~(1u << t);
+                }
+            }
         }
         if (kW == 2 && do_self && !joins) *item = static_cast<int>(lp_hit | 0x80000000u);
         const int n_hit = __popc(lp_hit);
@@ -774,9 +825,13 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
 #pragma unroll
             for (int f = 1; f < kMaxDof; ++f) la += t >= link_pair_index(f, f + 1);
             const int lk = t - link_pair_index(la, la + 1) + la + 1;
-            const float4 bb = pb.lbound[lk];
-            const float ckx = s_cb[(lk * 3 + 0) * 32 + lane], cky = s_cb[(lk * 3 + 1) * 32 + lane],
-                        ckz = s_cb[(lk * 3 + 2) * 32 + lane];
+            // the second frame's capsule: segment k0 + s e, radius rk
+            const float4 kc0 = pb.lcap[2 * lk], kc1 = pb.lcap[2 * lk + 1];
+            const float3 k0 = frame_point(s_fr + lk * 12 * 32, lane, kc0);
+            const float3 k1 = frame_point(s_fr + lk * 12 * 32, lane, kc1);
+            const float3 ke = make_float3(k1.x - k0.x, k1.y - k0.y, k1.z - k0.z);
+            const float kee = fmaf(ke.x, ke.x, fmaf(ke.y, ke.y, ke.z * ke.z));
+            const float kinv = kee > 1e-12f ? __frcp_rn(kee) : 0.f;
             float fa[12];  // the first frame, for every sphere of its blocks
 #pragma unroll
             for (int k = 0; k < 12; ++k) fa[k] = s_fr[(la * 12 + k) * 32 + lane];
@@ -792,9 +847,11 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
                     const float3 c = make_float3(fmaf(fa[0], q.x, fmaf(fa[1], q.y, fmaf(fa[2], q.z, fa[3]))),
                                                  fmaf(fa[4], q.x, fmaf(fa[5], q.y, fmaf(fa[6], q.z, fa[7]))),
                                                  fmaf(fa[8], q.x, fmaf(fa[9], q.y, fmaf(fa[10], q.z, fa[11]))));
-                    if (pb.broadphase) {  // sphere a apart from the second frame's bound: no pair touches
-                        const float ex = c.x - ckx, ey = c.y - cky, ez = c.z - ckz;
-                        const float rr = q.w + bb.w;
+                    if (pb.broadphase) {  // sphere a apart from the second frame's capsule: no pair touches
+                        const float dx = c.x - k0.x, dy = c.y - k0.y, dz = c.z - k0.z;
+                        const float sp = clamp01(fmaf(dx, ke.x, fmaf(dy, ke.y, dz * ke.z)) * kinv);
+                        const float ex = fmaf(-sp, ke.x, dx), ey = fmaf(-sp, ke.y, dy), ez = fmaf(-sp, ke.z, dz);
+                        const float rr = q.w + kc0.w;
                         if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= rr * rr) continue;
                     }
                     if (!have_b) {
