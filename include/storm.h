@@ -359,19 +359,27 @@ int storm_get_dependent_launch(const storm_handle* h);
 int storm_set_trace(storm_handle* h, unsigned long long* trace_dev);
 
 /* Collision broad phase (on by default): each link's spheres are enclosed in
- * one bounding sphere (fixed in the link frame, padded by 1e-4 m), and the
- * exact sphere-obstacle and sphere-pair tests run only where two such bounds,
- * or a bound and an obstacle, overlap.  The costs are identical either way;
- * off runs every exact test (brute force).  Re-captures the step graph. */
+ * one bounding sphere (fixed in the link frame, padded by 1e-4 m) and in one
+ * capsule (a segment between two of its sphere centres and a radius, padded
+ * by 1 mm), and the exact sphere-obstacle and sphere-pair tests run only where
+ * two such bounds, or a bound and an obstacle, overlap (self collision under
+ * the warp mappings: the bounding spheres, then the capsules, then each
+ * first-link sphere against the second link's capsule).  The costs are
+ * identical either way; off runs every exact test (brute force).  Re-captures
+ * the step graph. */
 int storm_set_broadphase(storm_handle* h, int on);
 
 /* Autotuner: times this handle's rollout kernel (sample_controls +
  * generate_rollouts) with CUDA events on its stream for every candidate shape
  * -- CTA mapping with particles per CTA 1, 2, 3, 4, 6, 8, 12, 16 (at most N
  * and 512/H) x threads 128, 256, 512, warp mapping with 1, 2, 4, 8 warps per
- * CTA, pair mapping with 1, 2, 4 pairs per CTA -- on the state and goal of the handle's input buffers (call it after a
- * first step), keeps the fastest and re-captures the step graph.  best_us (nullable) receives the median time of the chosen
- * shape.  Waits. */
+ * CTA, pair mapping with 1, 2, 4 pairs per CTA, quad mapping with 1, 2 quads
+ * per CTA -- on the state and goal of the handle's input buffers (call it
+ * after a first step), keeps the fastest, except that the fastest pair shape
+ * is kept when it is within 5 % of the fastest (one state is not every state:
+ * the pair mapping shares collision-heavy items between its two warps), and
+ * re-captures the step graph.  best_us (nullable) receives the median time of
+ * the chosen shape.  Waits. */
 int storm_autotune(storm_handle* h, float* best_us);
 
 /* ---------------------------------------------------------------- batched instances */
