@@ -11,7 +11,7 @@
 
 struct AdjointLayout {
     int frame, cent, sph, wsph, boxlh, pblk, keyw, keys;                 // 16/8-byte arrays
-    int lb, lcent, mask;                                                 // broad phase
+    int lb, lcent, mask, lcap;                                           // broad phase
     int mu, sigma, eps, u, th, thd, basis, dt, gpow, vmax, dhx, qlo, qhi;  // float arrays
     int boxes, cost, goal, state, gth, gthd, gu, gup;
     int first, slink, pairs;
@@ -43,6 +43,7 @@ __host__ __device__ inline AdjointLayout adjoint_layout(const Problem& pb)
     L.lb = take_(off, (pb.d + 1) * 16);         // link bounding spheres (local centre, radius)
     L.lcent = take_(off, I * (pb.d + 1) * 16);  // their centres per step
     L.mask = take_(off, I * (pb.d + 1) * 16);   // per (step, frame): boxes, obstacle spheres met
+    L.lcap = take_(off, 2 * (pb.d + 1) * 16);   // link capsules (local ends, radius)
     L.mu = take_(off, pb.H * pb.d * 4);
     L.sigma = take_(off, pb.d * 4);
     L.eps = take_(off, pb.S * pb.d * 4);
@@ -69,6 +70,15 @@ __host__ __device__ inline AdjointLayout adjoint_layout(const Problem& pb)
     L.pairs = take_(off, pb.P * 4);
     L.bytes = off;
     return L;
+}
+
+// A point of a link frame in world coordinates (the frame's three [R | p] rows).
+__device__ __forceinline__ float3 frame_apply(const float4* T, float4 q)
+{
+    const float4 r0 = T[0], r1 = T[1], r2 = T[2];
+    return make_float3(fmaf(r0.x, q.x, fmaf(r0.y, q.y, fmaf(r0.z, q.z, r0.w))),
+                       fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w))),
+                       fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w))));
 }
 
 // Minimiser ids of a pair block: (first-link sphere - first) * 8 + second-link
@@ -149,6 +159,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     float4* s_lb = reinterpret_cast<float4*>(smem + L.lb);
     float4* s_lcent = reinterpret_cast<float4*>(smem + L.lcent);
     unsigned long long* s_mask = reinterpret_cast<unsigned long long*>(smem + L.mask);
+    float4* s_lcap = reinterpret_cast<float4*>(smem + L.lcap);
     float* s_mu = reinterpret_cast<float*>(smem + L.mu);
     float* s_sigma = reinterpret_cast<float*>(smem + L.sigma);
     float* s_eps = reinterpret_cast<float*>(smem + L.eps);
@@ -213,6 +224,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         for (int i = tid; i < d * 8; i += nt) cp4(s_dhx + i, pb.dhx + i);
         for (int i = tid; i < d + 2; i += nt) cp4(s_first + i, pb.link_first + i);
         for (int i = tid; i < F; i += nt) cp16(s_lb + i, pb.lbound + i);
+        for (int i = tid; i < 2 * F; i += nt) cp16(s_lcap + i, pb.lcap + i);
         for (int i = tid; i < M; i += nt) cp16(s_sph + i, pb.sph + i);
         for (int i = tid; i < pb.P; i += nt) cp4(s_pairs + i, pb.pairs + i);
         for (int i = tid; i < pb.NPB; i += nt) cp16(s_pblk + i, pb.pblk + i);
@@ -364,6 +376,16 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                 const float ex = A.x - B2.x, ey = A.y - B2.y, ez = A.z - B2.z;
                 const float rr = A.w + B2.w;
                 live = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rr * rr;
+                if (live) {  // the bounding spheres meet: do the links' capsules?
+                    const int fa = s_slink[blk.x], fb = s_slink[blk.z];
+                    const float4 a0 = s_lcap[2 * fa], a1 = s_lcap[2 * fa + 1];
+                    const float4 b0 = s_lcap[2 * fb], b1 = s_lcap[2 * fb + 1];
+                    const float4* Ta = s_frame + item * FS + fa * 3;
+                    const float4* Tb = s_frame + item * FS + fb * 3;
+                    const float rc = a0.w + b0.w;
+                    live = seg_seg_dist2(frame_apply(Ta, a0), frame_apply(Ta, a1), frame_apply(Tb, b0),
+                                         frame_apply(Tb, b1)) < rc * rc;
+                }
             }
             unsigned alive = __ballot_sync(0xffffffffu, live);
             while (alive) {

@@ -174,47 +174,6 @@ __device__ __forceinline__ float3 frame_point(const float* __restrict__ fr, int 
                        fmaf(fr[8 * 32 + lane], q.x, fmaf(fr[9 * 32 + lane], q.y, fmaf(fr[10 * 32 + lane], q.z, fr[11 * 32 + lane]))));
 }
 
-__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
-
-// Squared distance between segments p0 + s (p1 - p0) and q0 + t (q1 - q0),
-// s, t in [0, 1]: the stationary point of the squared distance for s, t
-// inside, else the best t for the clamped s, or the best s at a clamped end of
-// t.  Each clamp keeps one point the nearest to the other, so in the nearly
-// parallel case, where the solve for s loses its digits, the result is off by
-// at most the segment length times the sine of their angle (that angle being
-// what makes the solve poor); the capsule radii are padded for it.
-__device__ __forceinline__ float seg_seg_dist2(float3 p0, float3 p1, float3 q0, float3 q1)
-{
-    const float3 d1 = make_float3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z);
-    const float3 d2 = make_float3(q1.x - q0.x, q1.y - q0.y, q1.z - q0.z);
-    const float3 r = make_float3(p0.x - q0.x, p0.y - q0.y, p0.z - q0.z);
-    const float a = fmaf(d1.x, d1.x, fmaf(d1.y, d1.y, d1.z * d1.z));
-    const float e = fmaf(d2.x, d2.x, fmaf(d2.y, d2.y, d2.z * d2.z));
-    const float b = fmaf(d1.x, d2.x, fmaf(d1.y, d2.y, d1.z * d2.z));
-    const float c = fmaf(d1.x, r.x, fmaf(d1.y, r.y, d1.z * r.z));
-    const float f = fmaf(d2.x, r.x, fmaf(d2.y, r.y, d2.z * r.z));
-    float s = 0.f, t = 0.f;
-    if (a > 1e-12f && e > 1e-12f) {
-        const float den = fmaf(a, e, -b * b);
-        s = den > 0.f ? clamp01(__fdividef(fmaf(b, f, -c * e), den)) : 0.f;
-        t = __fdividef(fmaf(b, s, f), e);
-        if (t < 0.f) {
-            t = 0.f;
-            s = clamp01(__fdividef(-c, a));
-        } else if (t > 1.f) {
-            t = 1.f;
-            s = clamp01(__fdividef(b - c, a));
-        }
-    } else if (e > 1e-12f) {
-        t = clamp01(__fdividef(f, e));
-    } else if (a > 1e-12f) {
-        s = clamp01(__fdividef(-c, a));
-    }
-    const float x = fmaf(d1.x, s, fmaf(-d2.x, t, r.x)), y = fmaf(d1.y, s, fmaf(-d2.y, t, r.y)),
-                z = fmaf(d1.z, s, fmaf(-d2.z, t, r.z));
-    return fmaf(x, x, fmaf(y, y, z * z));
-}
-
 // The warps of group `unit` meet (named barrier 1 + unit, `threads` threads).
 __device__ __forceinline__ void unit_sync(int unit, int threads)
 {
