@@ -16,8 +16,8 @@
 // The pair and quad variants (kW = 2 or 4 warps per particle group) split
 // each item's work across warps.  Warp A draws the controls and integrates
 // them; then every warp of the group runs FK into its own copy of the link
-// frames.  Pair: A takes the pose, joint, end-effector and manipulability
-// terms and world collision, B self collision, and A, once its own terms are
+// frames.  Pair: A takes the pose, joint and end-effector terms and world
+// collision, B the manipulability term and self collision, and A, once its own terms are
 // done, joins in: B publishes each item's mask of overlapping frame pairs in
 // shared memory, and the pairs are claimed one at a time from a per-item
 // counter, B from the first pair, A from the last, so that every pair is
@@ -206,7 +206,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
     const int role = kW == 1 ? 0 : warp % kW;
     const bool do_costs = role == 0;  // A: controls, integration, the cost terms
     const bool do_world = kW == 1 || (kW == 2 ? role == 0 : role == 1);
-    const bool do_manipw = kW <= 2 ? role == 0 : role == 1;
+    const bool do_manipw = kW == 1 || role == 1;  // pair and quad: B (A's chain is the longer)
     // self collision: the single warp; both warps of a pair (B takes each item's
     // overlapping frame pairs from the first, A, once its own terms are done,
     // from the last, one claim at a time); the quad's C and D (alternate pairs)
@@ -572,7 +572,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
         if (do_manipw && want_manip) {
             const float m = manipulability_mgs(J, d);
             c_manip = (m < pb.k_m) ? 1.f - m : 0.f;
-            if (kW <= 2) part += pb.w_manip * c_manip;  // the quad's A adds it at the hand-off
+            if (kW == 1) part += pb.w_manip * c_manip;  // pair and quad: A adds it at the hand-off
             if (kFull && valid && out.terms) out.terms[gi * STORM_NTERMS + 4] = c_manip;
         }
         __syncwarp();
@@ -876,19 +876,17 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
             const int PH = W.PW * H, ix = pl * H + h;
             if (valid) {
                 if (do_selfc && !do_costs) hand[(self_half > 0 ? PH : 0) + ix] = dself;
-                if (kW == 4 && do_world) {
-                    hand[2 * PH + ix] = dworld;
-                    hand[3 * PH + ix] = c_manip;
-                }
+                if (kW == 4 && do_world) hand[2 * PH + ix] = dworld;
+                if (do_manipw) hand[3 * PH + ix] = c_manip;
             }
             unit_sync(unit, kW * 32);
             if (do_costs && valid) {
+                if (want_manip) part += pb.w_manip * hand[3 * PH + ix];  // the single-warp order
                 if (kW == 2) {
                     dself = fmaxf(dself, hand[ix]);  // A's own pairs, then B's
                 } else {
                     dself = fmaxf(hand[ix], hand[PH + ix]);
                     dworld = hand[2 * PH + ix];
-                    if (want_manip) part += pb.w_manip * hand[3 * PH + ix];
                 }
             }
         }
