@@ -703,28 +703,53 @@ __device__ void block_argmin(float& bv, int& bi, float* shf, int* shi)
 
 // update_distribution (Eqs. 4-6) on one thread-block cluster of kUpdCluster
 // CTAs per problem, as weighted sums over the particles of the N x (H d)
-// control matrix (one row per particle, contiguous).  Every CTA finds the
-// minimum cost of all N particles, then weighs its own contiguous chunk of
-// particles (Eq. 6) and sums the chunk into one partial per column (h, j),
-// thread k holding column k so that each particle row is one coalesced read:
-// first sum w (u - mu_old), from which every CTA forms the new mean (Eq. 4)
-// mu_old + alpha_mu A1 / s out of the cluster's partials (in rank order); then,
-// from the values still in registers, sum w (u - mu_new)^2, which rank 0 adds
-// over the cluster and over h into the per-joint sigma (Eq. 5).  Rank 0 also
-// records the iteration's best and weighted-mean cost and, at the last
-// iteration of a step, writes next_command and advances the step counter.
-// The partials travel by stores into the receivers' shared memory (every
-// CTA's mean partials into every CTA, the deviation partials into rank 0)
-// ahead of a cluster barrier, so that after it every read is local and the
-// other CTAs may end while rank 0 finishes.  Every sum runs in a fixed order (the
-// chunk's particles in order, interleaved over kUpdGroups thread groups added
-// in order, then the CTAs in rank order; sigma: the rows in order): bitwise
-// reproducible, whatever the grid around the cluster.
+// control matrix (one row per particle, contiguous).  The columns (h, j) are
+// split into kUpdCluster contiguous ranges, one per CTA, so that all of a
+// column's sums over the N particles are formed inside one CTA.  Every CTA
+// finds the minimum cost of all N particles and forms all N weights (Eq. 6)
+// and their sums -- the same operations in every CTA, so the same bits; its
+// threads, one column and one of G interleaved particle groups each, sum
+// w (u - mu_old), the groups added in order, into the new mean of its columns
+// (Eq. 4), then, from the values still in registers, w (u - mu_new)^2 into each
+// column's squared deviation, which the CTA adds per joint over its columns
+// (Eq. 5).  One cluster barrier: ahead of it each CTA stores its per-joint
+// sums (and, at the last iteration, the new mean's first row) into rank 0's
+// shared memory; after it each CTA writes its columns of the mean (every CTA
+// has read the old mean by then) and rank 0 forms sigma, records the
+// iteration's best and weighted-mean cost and, at the last iteration of a
+// step, writes next_command and advances the step counter.  Every sum runs in
+// a fixed order: bitwise reproducible, whatever the grid around the cluster.
 constexpr int kUpdCluster = 8;
-constexpr int kUpdGroups = kUpdateThreads / 256;  // particle interleave when H d <= 256
-constexpr int kUpdBatch = 32;                     // loads in flight per thread
-constexpr int kUpdCostRegs = 2;                   // costs a thread loads ahead (N <= 1024 in one round)
-static_assert(STORM_MAX_H * kMaxDof <= kUpdateThreads, "one column per thread");
+constexpr int kUpdBatch = 32;     // loads in flight per thread
+constexpr int kUpdCostRegs = 2;   // costs a thread loads ahead (N <= 1024 in one round)
+constexpr int kUpdMaxCols = (STORM_MAX_H * kMaxDof + kUpdCluster - 1) / kUpdCluster;  // columns of one CTA
+static_assert(kUpdMaxCols <= kUpdateThreads, "a thread per column of a CTA");
+
+// Deterministic block sums of two values (fixed butterflies, then warp 0 over
+// the warps); sh holds 64 floats.  The results in every thread.
+__device__ float2 block_sum2(float a, float b, float* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    __syncthreads();
+    if (lane == 0) {
+        sh[wid] = a;
+        sh[32 + wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        float x = lane < nw ? sh[lane] : 0.f, y = lane < nw ? sh[32 + lane] : 0.f;
+        x = warp_sum(x);
+        y = warp_sum(y);
+        if (lane == 0) {
+            sh[0] = x;
+            sh[32] = y;
+        }
+    }
+    __syncthreads();
+    return make_float2(sh[0], sh[32]);
+}
 
 __device__ __forceinline__ unsigned cluster_rank()
 {
@@ -770,26 +795,25 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
                                                float* __restrict__ host_cmd = nullptr,
                                                StepState* host_st = nullptr)
 {
-    extern __shared__ __align__(16) float s_w[];  // N weights (the chunk's), then N costs
-    __shared__ float s_redf[32];
+    extern __shared__ __align__(16) float s_w[];  // N weights, then N costs
+    __shared__ float s_red[64];
     __shared__ int s_redi[32];
-    __shared__ float s_grp[kUpdGroups][kUpdateThreads];  // the thread groups' column sums
-    __shared__ float s_a1[kUpdateThreads + 1], s_a2[kUpdateThreads + 1];  // this CTA's partials (column O:
-                                                                          // sum w, sum w c), read over the cluster
-    __shared__ float s_dev[kUpdateThreads];                       // rank 0: squared deviation per column
-    __shared__ float s_in1[kUpdCluster][STORM_MAX_H * kMaxDof + 1];  // every CTA's mean partials (col. O: sum w)
-    __shared__ float s_in2[kUpdCluster][STORM_MAX_H * kMaxDof + 1];  // rank 0: every CTA's deviation partials
-    __shared__ float s_mu[kUpdateThreads];                        // the new mean, every column
+    __shared__ float s_grp[kUpdateThreads];           // the groups' column sums, [group][column]
+    __shared__ float s_mu[kUpdMaxCols];               // the new mean of this CTA's columns
+    __shared__ float s_dev[kUpdMaxCols];              // their squared deviations
+    __shared__ float s_jdev[kUpdCluster][kMaxDof];    // rank 0: every CTA's per-joint deviation sums
+    __shared__ float s_cmd[kMaxDof];                  // rank 0: the new mean's first row
     const int N = pb.N, d = pb.d, H = pb.H, O = H * d;
     float* s_cost = s_w + ((N + 3) & ~3);
     const int tid = threadIdx.x, T = blockDim.x;
     const unsigned rank = cluster_rank();
     cluster_arrive_start();  // (waited for before the first write to a peer)
-    const int chunk = (N + kUpdCluster - 1) / kUpdCluster;
-    const int n0 = min(N, static_cast<int>(rank) * chunk), n1 = min(N, n0 + chunk);
-    const int G = O <= T / kUpdGroups ? kUpdGroups : 1;  // thread groups interleaving the chunk
-    const int k = G > 1 ? tid % (T / kUpdGroups) : tid, g = G > 1 ? tid / (T / kUpdGroups) : 0;
-    const bool col = k < O && g < G;
+    const int cpc = (O + kUpdCluster - 1) / kUpdCluster;  // columns per CTA
+    const int c0 = min(O, static_cast<int>(rank) * cpc), c1 = min(O, c0 + cpc);
+    const int G = T / cpc;  // particle groups per column
+    const int cl = tid % cpc, g = tid / cpc, k = c0 + cl;
+    const bool col = g < G && k < c1;
+    const bool lead = tid < cpc && k < c1;  // group 0 of a column: forms its totals
     // (costs, controls and the mean through L2: under a dependent launch this
     // CTA may have started before the rollout that wrote them finished)
     const int mu_off = (shift && st->step > 0) ? d : 0;
@@ -799,16 +823,16 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     float cr[kUpdCostRegs];
 #pragma unroll
     for (int r = 0; r < kUpdCostRegs; ++r) cr[r] = tid + r * T < N ? __ldcg(C + tid + r * T) : INFINITY;
-    // this thread's particles n0 + g, n0 + g + G, ... of the chunk: the first
-    // kUpdBatch of them are loaded now, while the weights are formed
-    const int cnt = col ? max(0, (n1 - n0 - g + G - 1) / G) : 0;
-    const float* up = u + static_cast<size_t>(n0 + g) * O + k;
-    const int stride = G * O;
+    // this thread's particles g, g + G, ... of its column: the first kUpdBatch
+    // of them are loaded now, while the weights are formed
+    const int cnt = col ? (N - g + G - 1) / G : 0;
+    const float* up = u + static_cast<size_t>(col ? g : 0) * O + (col ? k : 0);
+    const size_t stride = static_cast<size_t>(G) * O;
     float x[kUpdBatch];
 #pragma unroll
     for (int q = 0; q < kUpdBatch; ++q) x[q] = q < cnt ? up[q * stride] : 0.f;
-    float wv[kUpdBatch];                // the same particles' weights (pass 1 reads them)
-    const float* wp = s_w + n0 + g;
+    float wv[kUpdBatch];  // the same particles' weights
+    const float* wp = s_w + g;
 
     // ---- min finite cost and its lowest index
     float bv = INFINITY;
@@ -824,7 +848,7 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
     for (int r = 0; r < kUpdCostRegs; ++r)
         if (tid + r * T < N) visit(tid + r * T, cr[r]);
     for (int n = tid + kUpdCostRegs * T; n < N; n += T) visit(n, __ldcg(C + n));
-    block_argmin(bv, bi, s_redf, s_redi);
+    block_argmin(bv, bi, s_red, s_redi);  // (its barriers also publish s_cost)
     const float m = bv;
     const int arg = bi;
     const bool degenerate = (arg == INT_MAX);
@@ -833,166 +857,131 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
         if (!isfinite(c)) return 0.f;
         return pb.beta > 0.f ? expf(-(c - m) / pb.beta) : (n == arg ? 1.f : 0.f);
     };
+    float s = 1.f, inv_s = 1.f, swc = 0.f;
     if (!degenerate) {
-        // ---- the chunk's weights, Eq. 6; the last warp (no columns of its own
-        // when H d <= 224) sums them and w c for rank 0
-        __syncthreads();  // every cost is in s_cost
-        for (int n = n0 + tid; n < n1; n += T) s_w[n] = weight(n, s_cost[n]);
-        __syncthreads();
-        if (tid >= T - 32) {
-            const int l = tid - (T - 32);
-            float ls = 0.f, lsc = 0.f;
-            for (int n = n0 + l; n < n1; n += 32) {
-                const float w = s_w[n];
-                ls += w;
-                if (w > 0.f) lsc = fmaf(w, s_cost[n], lsc);
-            }
-            ls = warp_sum(ls);
-            lsc = warp_sum(lsc);
-            if (l == 0) {
-                s_a1[O] = ls;
-                s_a2[O] = lsc;
-            }
+        // ---- all N weights (Eq. 6) and their sums, the same in every CTA
+        float ls = 0.f, lsc = 0.f;
+        for (int n = tid; n < N; n += T) {
+            const float w = weight(n, s_cost[n]);
+            s_w[n] = w;
+            ls += w;
+            if (w > 0.f) lsc = fmaf(w, s_cost[n], lsc);
         }
+        const float2 sums = block_sum2(ls, lsc, s_red);  // (its barriers also publish s_w)
+        s = sums.x;
+        swc = sums.y;
+        inv_s = 1.f / s;
 
-        // ---- pass 1: the chunk's sum w (u - mu_old) per column, particles in order
-        // (each batch's weights are read into registers together, then summed)
-        if (col) {
-            float a1 = 0.f;
-            for (int q0 = 0; q0 < cnt; q0 += kUpdBatch) {
-                if (q0 > 0) {
+        // ---- pass 1: the column's sum w (u - mu_old) over the group's particles in order
+        float a1 = 0.f;
+        for (int q0 = 0; q0 < cnt; q0 += kUpdBatch) {
+            if (q0 > 0) {
 #pragma unroll
-                    for (int q = 0; q < kUpdBatch; ++q) x[q] = q0 + q < cnt ? up[(q0 + q) * stride] : 0.f;
-                }
+                for (int q = 0; q < kUpdBatch; ++q) x[q] = q0 + q < cnt ? up[(q0 + q) * stride] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < kUpdBatch; ++q) wv[q] = q0 + q < cnt ? wp[(q0 + q) * G] : 0.f;
+#pragma unroll
+            for (int q = 0; q < kUpdBatch; ++q)
+                if (q0 + q < cnt) a1 = fmaf(wv[q], x[q] - mu_k, a1);
+        }
+        if (g < G) s_grp[tid] = a1;  // [g][cl]
+        __syncthreads();
+        if (lead) {  // the groups in order: the new mean, Eq. 4
+            float A1 = 0.f;
+            for (int q = 0; q < G; ++q) A1 += s_grp[q * cpc + tid];
+            s_mu[tid] = fmaf(pb.alpha_mu * A1, inv_s, mu_k);
+        }
+        __syncthreads();
+
+        // ---- pass 2: the column's sum w (u - mu_new)^2, Eq. 5
+        const float mk = col ? s_mu[cl] : 0.f;
+        float a2 = 0.f;
+        for (int q0 = 0; q0 < cnt; q0 += kUpdBatch) {
+            if (cnt > kUpdBatch) {  // more than one batch: x and wv hold the last one
+#pragma unroll
+                for (int q = 0; q < kUpdBatch; ++q) x[q] = q0 + q < cnt ? up[(q0 + q) * stride] : 0.f;
 #pragma unroll
                 for (int q = 0; q < kUpdBatch; ++q) wv[q] = q0 + q < cnt ? wp[(q0 + q) * G] : 0.f;
-#pragma unroll
-                for (int q = 0; q < kUpdBatch; ++q)
-                    if (q0 + q < cnt) a1 = fmaf(wv[q], x[q] - mu_k, a1);
             }
-            s_grp[g][k] = a1;
+#pragma unroll
+            for (int q = 0; q < kUpdBatch; ++q) {
+                if (q0 + q < cnt) {
+                    const float e = x[q] - mk;
+                    a2 = fmaf(wv[q] * e, e, a2);
+                }
+            }
+        }
+        if (g < G) s_grp[tid] = a2;  // (every pass-1 read of s_grp is behind the barrier above)
+        __syncthreads();
+        if (lead) {
+            float A2 = 0.f;
+            for (int q = 0; q < G; ++q) A2 += s_grp[q * cpc + tid];
+            s_dev[tid] = A2;
         }
         __syncthreads();
         cluster_wait_start();
-        if (tid <= O) {  // into every CTA's receive area (distributed shared memory)
-            float p = s_a1[O];  // sum w
-            if (tid < O) {
-                p = s_grp[0][tid];
-                for (int q = 1; q < G; ++q) p += s_grp[q][tid];
-            }
-#pragma unroll
-            for (int r = 0; r < kUpdCluster; ++r) *cluster_peer_w(&s_in1[rank][tid], r) = p;
+        if (tid < d) {  // joint tid's deviation over this CTA's columns, in h order, into rank 0
+            float P = 0.f;
+            for (int c = ((tid - c0 % d) % d + d) % d; c < c1 - c0; c += d) P += s_dev[c];
+            *cluster_peer_w(&s_jdev[rank][tid], 0) = P;
         }
+        if (finalize && lead && k < d) *cluster_peer_w(&s_cmd[k], 0) = s_mu[tid];
     } else {
         cluster_wait_start();
+        if (finalize && lead && k < d) *cluster_peer_w(&s_cmd[k], 0) = mu_k;  // the (shifted) mean kept
     }
-    cluster_barrier();  // every CTA's mean partials and normaliser are in every CTA
-
-    float s = 1.f, inv_s = 1.f;
-    if (!degenerate) {
-        // ---- the new mean, Eq. 4, in every CTA from the cluster's partials
-        auto cluster_sum1 = [&](int c) {  // in rank order
-            float a = 0.f;
-#pragma unroll
-            for (int r = 0; r < kUpdCluster; ++r) a += s_in1[r][c];
-            return a;
-        };
-        s = cluster_sum1(O);
-        inv_s = 1.f / s;
-        if (tid < O) s_mu[tid] = fmaf(pb.alpha_mu * cluster_sum1(tid), inv_s, mu_k);  // k == tid here
-        __syncthreads();
-        if (rank == 0 && tid < O) pb.mu[tid] = s_mu[tid];
-
-        // ---- pass 2: the chunk's sum w (u - mu_new)^2 per column, Eq. 5
-        if (col) {
-            const float mk = s_mu[k];
-            float a2 = 0.f;
-            for (int q0 = 0; q0 < cnt; q0 += kUpdBatch) {
-                if (cnt > kUpdBatch) {  // more than one batch: x and wv hold the last one
-#pragma unroll
-                    for (int q = 0; q < kUpdBatch; ++q) x[q] = q0 + q < cnt ? up[(q0 + q) * stride] : 0.f;
-#pragma unroll
-                    for (int q = 0; q < kUpdBatch; ++q) wv[q] = q0 + q < cnt ? wp[(q0 + q) * G] : 0.f;
-                }
-#pragma unroll
-                for (int q = 0; q < kUpdBatch; ++q) {
-                    if (q0 + q < cnt) {
-                        const float e = x[q] - mk;
-                        a2 = fmaf(wv[q] * e, e, a2);
-                    }
-                }
-            }
-            s_grp[g][k] = a2;
-        }
-        __syncthreads();
-        if (tid < O) {  // into rank 0's receive area (distributed shared memory)
-            float p = s_grp[0][tid];
-            for (int q = 1; q < G; ++q) p += s_grp[q][tid];
-            *cluster_peer_w(&s_in2[rank][tid], 0) = p;
-        }
-        if (tid == O) *cluster_peer_w(&s_in2[rank][O], 0) = s_a2[O];  // sum w c
+    cluster_barrier();  // every CTA has read the old mean; rank 0 holds the per-joint sums
+    // ---- every CTA: its columns of the mean (the shifted old mean, kept, when
+    // the first iteration of a step is degenerate)
+    if (lead) {
+        if (!degenerate)
+            pb.mu[k] = s_mu[tid];
+        else if (mu_off)
+            pb.mu[k] = mu_k;
     }
-
-    // ---- rank 0: sigma (Eq. 5) from the cluster's deviation partials, now in
-    // its own shared memory: the other CTAs are done
-    cluster_barrier();
     if (rank != 0) return;
-    {
-        if (degenerate) {
-            if (tid == 0) {
-                st->status |= STORM_WARN_DEGENERATE;
-                st->best = INFINITY;
-                st->wmean = INFINITY;
-            }
-            if (weights_out)
-                for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
-            if (mu_off && tid < O) pb.mu[tid] = mu_k;  // the shifted mean, kept (k == tid here)
-        } else {
-            if (weights_out)
-                for (int n = tid; n < N; n += T) weights_out[n] = weight(n, s_cost[n]) * inv_s;
-            if (tid < O) {
-                float a = 0.f;
-#pragma unroll
-                for (int r = 0; r < kUpdCluster; ++r) a += s_in2[r][tid];
-                s_dev[tid] = a;
-            }
-            __syncthreads();
-            if (tid < d) {
-                const int j = tid;
-                float v = 0.f;
-                for (int hh = 0; hh < H; ++hh) v += s_dev[hh * d + j];
-                v = v * inv_s / static_cast<float>(H);
-                const float sg = __ldcg(pb.sigma + j);
-                float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
-                var = fmaxf(var, pb.sigma_min * pb.sigma_min);
-                pb.sigma[j] = sqrtf(var);
-            }
-            if (tid == 0) {
-                float a = 0.f;
-#pragma unroll
-                for (int r = 0; r < kUpdCluster; ++r) a += s_in2[r][O];
-                st->best = m;
-                st->wmean = a / s;
-            }
+    // ---- rank 0: sigma (Eq. 5) from the cluster's per-joint sums, in rank order
+    if (degenerate) {
+        if (tid == 0) {
+            st->status |= STORM_WARN_DEGENERATE;
+            st->best = INFINITY;
+            st->wmean = INFINITY;
         }
-        if (finalize) {
-            const float c = degenerate ? mu_k : s_mu[tid < d ? tid : 0];
-            if (tid < d) cmd_out[tid] = c;
-            if (tid == 0) st->step += 1;
-            // the step's outputs straight into pinned host memory as well (host
-            // calls: no device-to-host copy after the kernel), the step counter
-            // last: the host returns once it sees it change
-            if (host_cmd) {
-                __syncthreads();  // (the command in cmd_out)
-                if (tid == 0) {
-                    for (int j = 0; j < d; ++j) host_cmd[j] = cmd_out[j];
-                    host_st->status = st->status;
-                    host_st->best = st->best;
-                    host_st->wmean = st->wmean;
-                    __threadfence_system();
-                    *reinterpret_cast<volatile uint32_t*>(&host_st->step) = st->step;
-                }
-            }
+        if (weights_out)
+            for (int n = tid; n < N; n += T) weights_out[n] = 0.f;
+    } else {
+        if (weights_out)
+            for (int n = tid; n < N; n += T) weights_out[n] = s_w[n] * inv_s;
+        if (tid < d) {
+            const int j = tid;
+            float v = 0.f;
+#pragma unroll
+            for (int r = 0; r < kUpdCluster; ++r) v += s_jdev[r][j];
+            v = v * inv_s / static_cast<float>(H);
+            const float sg = __ldcg(pb.sigma + j);
+            float var = (1.f - pb.alpha_sigma) * sg * sg + pb.alpha_sigma * v;
+            var = fmaxf(var, pb.sigma_min * pb.sigma_min);
+            pb.sigma[j] = sqrtf(var);
+        }
+        if (tid == 0) {
+            st->best = m;
+            st->wmean = swc / s;
+        }
+    }
+    if (finalize) {
+        if (tid < d) cmd_out[tid] = s_cmd[tid];
+        if (tid == 0) st->step += 1;
+        // the step's outputs straight into pinned host memory as well (host
+        // calls: no device-to-host copy after the kernel), the step counter
+        // last: the host returns once it sees it change
+        if (host_cmd && tid == 0) {
+            for (int j = 0; j < d; ++j) host_cmd[j] = s_cmd[j];
+            host_st->status = st->status;
+            host_st->best = st->best;
+            host_st->wmean = st->wmean;
+            __threadfence_system();
+            *reinterpret_cast<volatile uint32_t*>(&host_st->step) = st->step;
         }
     }
 }
