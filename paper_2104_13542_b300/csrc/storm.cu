@@ -9,6 +9,7 @@
 #include "storm.h"
 #include "storm_device.cuh"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1454,6 +1455,45 @@ cudaError_t gemm(const tc::GemmArgs& g, cudaStream_t s, int splits = 1)
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point
+// (the library does not link the driver library itself).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled()
+{
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a rows x cols BF16 matrix (row pitch ld elements) for boxes of
+// box_cols x box_rows, with or without the 128-byte shared-memory swizzle.
+cudaError_t bf16_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_cols, int box_rows,
+                     bool swizzle128)
+{
+    const EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
+    const cuuint32_t step[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, step,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Layer with the weights resident in shared memory: N = 64, 128 or 256 and
 // K = 16, 64, 128 or 256.
 template <int BN>
@@ -1476,7 +1516,23 @@ cudaError_t gemm_rw_bn(const tc::GemmArgs& g, cudaStream_t s)
     // on an SM, so no allocation ever waits for a co-resident CTA.
     const size_t floor_smem = BN == 256 ? 116u * 1024 : (BN == 128 ? 80u * 1024 : 48u * 1024);
     const size_t smem = std::max(tc::gemm_ws_smem(BN, g.K), floor_smem);
-    tc::k_gemm_ws<BN><<<grid, tc::kThreadsWS, smem, s>>>(g);
+    // the operand's TMA loads, and the epilogue's TMA stores: 64-column x 32-row
+    // boxes of the output (128-byte swizzle), 32-row x 64-column boxes of its
+    // transpose
+    CUtensorMap map_a{}, map_out{}, map_outT{};
+    if (g.K % tc::kKB == 0) {  // A tiles of 128 rows x 64 K by TMA, 128-byte swizzle
+        const cudaError_t e = bf16_map(&map_a, g.A, g.M, g.K, g.lda, tc::kKB, tc::kBM, true);
+        if (e != cudaSuccess) return e;
+    }
+    if (g.out_bf) {
+        const cudaError_t e = bf16_map(&map_out, g.out_bf, g.M, g.N, g.ldo, 64, 32, true);
+        if (e != cudaSuccess) return e;
+    }
+    if (g.out_bfT) {
+        const cudaError_t e = bf16_map(&map_outT, g.out_bfT, g.N, g.M, g.ldoT, 32, 64, false);
+        if (e != cudaSuccess) return e;
+    }
+    tc::k_gemm_ws<BN><<<grid, tc::kThreadsWS, smem, s>>>(g, map_a, map_out, map_outT);
     return cudaGetLastError();
 }
 

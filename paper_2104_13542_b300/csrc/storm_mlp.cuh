@@ -10,6 +10,7 @@
 // wait is bounded in time and reports through an error flag.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 namespace tc {
@@ -62,6 +63,28 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) |
            (static_cast<uint64_t>((lbo & 0x3FFFFu) >> 4) << 16) |
            (static_cast<uint64_t>((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// Descriptor of a K-major operand in the 128-byte swizzled layout that TMA
+// writes: rows of 64 BF16 (128 bytes), 16-byte chunk c of row r at chunk
+// c ^ (r mod 8), 8-row groups 1024 bytes apart (the stride field; the leading
+// field is unused for this layout), layout code 2 at bits 61-63; the K steps of
+// 16 elements advance the start address by 32 bytes within the rows.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (static_cast<uint64_t>(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+// Bulk tensor load (TMA) of the box at element coordinates (x, y) of the tensor
+// map's 2-D view into shared memory, completing its bytes on mbarrier mbar.
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint32_t dst, uint32_t mbar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(y)
+        : "memory");
 }
 
 // Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, N, M.
@@ -300,6 +323,64 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The same load without its wait: the registers are valid after tmem_ld_wait
+// on them (which waits for every load this thread has issued), so a thread
+// can work on one block while the next is in flight.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
+}
+
+// One 32-column block of the epilogue (this thread: row `row`, its 32 TMEM
+// values r): bias, ReLU and mask into v, and the dot head's running sums (each
+// half of the columns summed in column order, the halves added at the end: the
+// order of the whole-network tile's two epilogue warps).
+template <int BN>
+__device__ __forceinline__ void epilogue_block(const GemmArgs& g, const uint32_t (&r)[32], int row, int c0,
+                                               const float* bias, const float* head_w, float (&v)[32],
+                                               float& yacc, float& yacc0)
+{
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int n = c0 + i;
+        float x = __uint_as_float(r[i]);
+        if (bias) x += bias[n];
+        if (g.relu) x = fmaxf(x, 0.f);
+        v[i] = x;
+    }
+    if (g.mask) {
+        const uint4* mk = reinterpret_cast<const uint4*>(g.mask + static_cast<size_t>(row) * g.ldm + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 w = mk[q];
+            const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (!(__bfloat162float(mb[i]) > 0.f)) v[q * 8 + i] = 0.f;
+        }
+    }
+    if (head_w) {
+        if (c0 == BN / 2) {
+            yacc0 = yacc;
+            yacc = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) yacc = fmaf(head_w[c0 + i], v[i], yacc);
+    }
+    if (g.out_f) {
+        float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+}
+
 // Epilogue of one 128-row tile (this thread: row `row`, TMEM lanes of `warp`):
 // bias, ReLU, mask, BF16 / FP32 / transposed stores and the dot head, 32
 // columns per TMEM load.
@@ -307,46 +388,13 @@ template <int BN>
 __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, int row, int warp,
                                               const float* bias, const float* head_w)
 {
-    // the dot head sums each half of the columns in column order and adds the
-    // halves (the order of the whole-network tile's two epilogue warps)
     float yacc = 0.f, yacc0 = 0.f;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, r);
         float v[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int n = c0 + i;
-            float x = __uint_as_float(r[i]);
-            if (bias) x += bias[n];
-            if (g.relu) x = fmaxf(x, 0.f);
-            v[i] = x;
-        }
-        if (g.mask) {
-            const uint4* mk = reinterpret_cast<const uint4*>(g.mask + static_cast<size_t>(row) * g.ldm + c0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 w = mk[q];
-                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&w);
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    if (!(__bfloat162float(mb[i]) > 0.f)) v[q * 8 + i] = 0.f;
-            }
-        }
-        if (head_w) {
-            if (c0 == BN / 2) {
-                yacc0 = yacc;
-                yacc = 0.f;
-            }
-#pragma unroll
-            for (int i = 0; i < 32; ++i) yacc = fmaf(head_w[c0 + i], v[i], yacc);
-        }
-        if (g.out_f) {
-            float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
+        epilogue_block<BN>(g, r, row, c0, bias, head_w, v, yacc, yacc0);
         if (g.out_bf) {
             uint4* o = reinterpret_cast<uint4*>(g.out_bf + static_cast<size_t>(row) * g.ldo + c0);
 #pragma unroll
@@ -362,6 +410,95 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, uint32_t tmem, 
             for (int i = 0; i < 32; ++i)
                 g.out_bfT[static_cast<size_t>(c0 + i) * g.ldoT + row] = __float2bfloat16_rn(v[i]);
         }
+    }
+    if (head_w) g.head_y[row] = *g.head_b + (yacc0 + yacc);
+}
+
+// Bulk tensor store (TMA) of a shared-memory box to global memory at element
+// coordinates (x, y) of the tensor map's 2-D view; completion is tracked by
+// the issuing thread's bulk groups.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+
+// Shared-memory staging of one epilogue warp: its 32 rows x 64 columns of the
+// BF16 output (128-byte rows, the 128-byte swizzle the store's tensor map
+// names: 16-byte chunk c of row r at chunk c ^ (r mod 8)), then the same block
+// transposed (64 rows of 32 BF16, unswizzled).  1024-byte aligned.
+constexpr int kEpiStage = 32 * 128 + 64 * 64;
+
+// The epilogue of k_gemm_ws: the arithmetic of gemm_epilogue, the BF16 tiles
+// written to shared memory and stored by TMA, one 64-column block per bulk
+// group (full 128-byte lines to global memory instead of per-row pieces, and
+// 64 shared-memory stores for the transposed copy instead of 32-bit-strided
+// global ones).  row0: the warp's first row; lane 0 issues the stores.
+template <int BN>
+__device__ __forceinline__ void gemm_epilogue_tma(const GemmArgs& g, const CUtensorMap* map_out,
+                                                  const CUtensorMap* map_outT, uint32_t tmem, int row0, int warp,
+                                                  const float* bias, const float* head_w, unsigned char* stage)
+{
+    static_assert(BN % 64 == 0, "64-column store blocks");
+    const int lane = threadIdx.x & 31, row = row0 + lane;
+    const uint32_t s_bf = smem_u32(stage), s_t = s_bf + 32 * 128;
+    const uint32_t tl = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    float yacc = 0.f, yacc0 = 0.f;
+    // one half of a 64-column block into the staging tiles; the second half
+    // also stores the block
+    auto half_block = [&](const uint32_t (&r)[32], int c0, int half) {
+        float v[32];
+        epilogue_block<BN>(g, r, row, c0, bias, head_w, v, yacc, yacc0);
+        if (half == 0) {  // the previous block's stores have read the staging tiles
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            __syncwarp();
+        }
+        if (g.out_bf) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[q * 8 + i]);
+                const uint4 w = *reinterpret_cast<const uint4*>(b);
+                const uint32_t a = s_bf + lane * 128 + (((half * 4 + q) ^ (lane & 7)) << 4);
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w.x), "r"(w.y), "r"(w.z),
+                             "r"(w.w)
+                             : "memory");
+            }
+        }
+        if (g.out_bfT) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(v[i]);
+                asm volatile("st.shared.b16 [%0], %1;" ::"r"(s_t + (half * 32 + i) * 64 + lane * 2),
+                             "h"(*reinterpret_cast<const unsigned short*>(&b))
+                             : "memory");
+            }
+        }
+        if (half == 1) {  // a full 64-column block: to global memory
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                if (g.out_bf) tma_store_2d(map_out, s_bf, c0 - 32, row0);
+                if (g.out_bfT) tma_store_2d(map_outT, s_t, row0, c0 - 32);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+        }
+    };
+    // each block's TMEM load is in flight while the block before it is worked on
+    uint32_t ra[32], rb[32];
+    tmem_ld32_async(tl, ra);
+    tmem_ld_wait(ra);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 64) {
+        tmem_ld32_async(tl + c0 + 32, rb);
+        half_block(ra, c0, 0);
+        tmem_ld_wait(rb);
+        if (c0 + 64 < BN) tmem_ld32_async(tl + c0 + 64, ra);
+        half_block(rb, c0 + 32, 1);
+        if (c0 + 64 < BN) tmem_ld_wait(ra);
     }
     if (head_w) g.head_y[row] = *g.head_b + (yacc0 + yacc);
 }
@@ -509,12 +646,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
 // Every wait is bounded (1 s): on a timeout the role sets *err and leaves its
 // loop; the others time out in turn, and the CTA still meets at the final
 // barrier before the TMEM is freed.
-constexpr int kStagesWS = 6, kLagWS = 3;
+constexpr int kStagesWS = 4, kLagWS = 3;
 constexpr int kThreadsWS = 192;
 
 __host__ __device__ constexpr size_t gemm_ws_smem(int BN, int K)
 {
-    return static_cast<size_t>(BN) * K * 2 + static_cast<size_t>(kStagesWS) * kBM * (K < kKB ? K : kKB) * 2;
+    return static_cast<size_t>(BN) * K * 2 + static_cast<size_t>(kStagesWS) * kBM * (K < kKB ? K : kKB) * 2 +
+           4 * kEpiStage;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t addr)
@@ -523,18 +661,28 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr)
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
+__global__ void __launch_bounds__(kThreadsWS, 1)
+    k_gemm_ws(GemmArgs g, const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_out,
+              const __grid_constant__ CUtensorMap map_outT)
 {
     constexpr uint32_t kCols = 2 * BN;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[kStagesWS], empty[kStagesWS], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full[kStagesWS], empty[kStagesWS], tfull[2], tempty[2], wready;
     __shared__ uint32_t tmem_slot;
     __shared__ float s_bias[BN], s_headw[BN];  // the epilogue's per-column vectors, read by every row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = g.K, kb = K < kKB ? K : kKB, nk = K / kb;
+    // A tiles of 64 K columns come by TMA in the 128-byte swizzled layout (the
+    // swizzle's phase is the shared address, so the block must start on 1 KB)
+    const bool tma_a = kb == kKB;
+    if ((smem_u32(smem) & 1023u) != 0u) {  // (uniform over the CTA: nothing allocated yet)
+        if (threadIdx.x == 0 && g.err) atomicExch(g.err, 1);
+        return;
+    }
     unsigned char* sW = smem;
     unsigned char* sA = smem + static_cast<size_t>(BN) * K * 2;
     const int stageA = kBM * kb * 2, blockW = BN * kb * 2;
+    unsigned char* sE = sA + kStagesWS * stageA;  // the epilogue warps' staging tiles
     const uint32_t sbo = (kb / 8) * 128;
     const int tiles = g.M / kBM, bx = blockIdx.x, gx = gridDim.x;
     const int my_tiles = tiles > bx ? (tiles - 1 - bx) / gx + 1 : 0;
@@ -560,6 +708,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
             mbar_init(smem_u32(&tfull[b]), 1);
             mbar_init(smem_u32(&tempty[b]), 4);
         }
+        mbar_init(smem_u32(&wready), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -570,7 +719,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
 
     if (warp == 0) {
         // ---- producer
-        {
+        {  // the weights, resident for the CTA's tiles: cp.async by the whole warp
             const int chunks = kb / 8;
             for (int c = lane; c < nk * BN * chunks; c += 32) {
                 const int j = c / (BN * chunks), rem = c - j * BN * chunks;
@@ -580,38 +729,74 @@ __global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
-        auto signal = [&](int item) {  // item's copies (and all older ones) are complete
+        if (tma_a) {
+            // one thread posts each stage's byte count on the stage's mbarrier and
+            // starts its TMA copy, which completes the count (no waiting on copies
+            // here); the weights are waited for once the first stages are in
+            // flight, and announced on wready
+            auto issue = [&](int i) {
+                const int stage = i % kStagesWS, t = bx + (i / nk) * gx, j = i % nk;
+                const uint32_t fb = smem_u32(&full[stage]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stageA)
+                             : "memory");
+                tma_load_2d(&map_a, smem_u32(sA + stage * stageA), fb, j * kb, t * kBM);
+            };
+            const int first = total < kStagesWS ? total : kStagesWS;
+            if (lane == 0)
+                for (int i = 0; i < first; ++i) issue(i);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&full[item % kStagesWS]));
-        };
-        for (int i = 0; i < total && ok; ++i) {
-            const int stage = i % kStagesWS;
-            if (i >= kStagesWS)  // the MMAs of item i - kStagesWS released the stage
-                ok = mbar_wait(smem_u32(&empty[stage]), ((i / kStagesWS) - 1) & 1);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            const int t = bx + (i / nk) * gx, j = i % nk;
-            const __nv_bfloat16* src = g.A + static_cast<size_t>(t) * kBM * g.lda + j * kb;
-            const uint32_t dst = smem_u32(sA + stage * stageA);
-            const int chunks = kb / 8;
-            for (int c = lane; c < kBM * chunks; c += 32) {
-                const int r = c / chunks, kg = c - r * chunks;
-                cp_async16(dst + (r >> 3) * sbo + (r & 7) * 16 + kg * 128, src + static_cast<size_t>(r) * g.lda + kg * 8);
+            if (lane == 0) {
+                mbar_arrive(smem_u32(&wready));
+                int issued = first;
+                for (int i = first; i < total && ok; ++i) {
+                    const int stage = i % kStagesWS;  // the MMAs of item i - kStagesWS released the stage
+                    ok = mbar_wait(smem_u32(&empty[stage]), ((i / kStagesWS) - 1) & 1);
+                    if (ok) issue(i), issued = i + 1;
+                }
+                // copies still in flight land before the CTA may end (each wait bounded;
+                // a phase the MMA thread has already consumed answers at once)
+                for (int i = issued > kStagesWS ? issued - kStagesWS : 0; i < issued; ++i)
+                    if (!mbar_wait(smem_u32(&full[i % kStagesWS]), (i / kStagesWS) & 1)) ok = false;
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            if (i >= kLagWS) {
-                asm volatile("cp.async.wait_group %0;" ::"n"(kLagWS) : "memory");
-                signal(i - kLagWS);
+            __syncwarp();
+        } else {
+            auto signal = [&](int item) {  // item's copies (and all older ones) are complete
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&full[item % kStagesWS]));
+            };
+            for (int i = 0; i < total && ok; ++i) {
+                const int stage = i % kStagesWS;
+                if (i >= kStagesWS)  // the MMAs of item i - kStagesWS released the stage
+                    ok = mbar_wait(smem_u32(&empty[stage]), ((i / kStagesWS) - 1) & 1);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                const int t = bx + (i / nk) * gx, j = i % nk;
+                const __nv_bfloat16* src = g.A + static_cast<size_t>(t) * kBM * g.lda + j * kb;
+                const uint32_t dst = smem_u32(sA + stage * stageA);
+                const int chunks = kb / 8;
+                for (int c = lane; c < kBM * chunks; c += 32) {
+                    const int r = c / chunks, kg = c - r * chunks;
+                    cp_async16(dst + (r >> 3) * sbo + (r & 7) * 16 + kg * 128,
+                               src + static_cast<size_t>(r) * g.lda + kg * 8);
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                if (i >= kLagWS) {
+                    asm volatile("cp.async.wait_group %0;" ::"n"(kLagWS) : "memory");
+                    signal(i - kLagWS);
+                }
             }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (ok)
+                for (int i = total > kLagWS ? total - kLagWS : 0; i < total; ++i) signal(i);
         }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        if (ok)
-            for (int i = total > kLagWS ? total - kLagWS : 0; i < total; ++i) signal(i);
     } else if (warp == 1) {
         // ---- MMA issue (one thread)
         if (lane == 0) {
             const uint32_t idesc = instr_desc(kBM, BN);
+            if (tma_a && my_tiles > 0) ok = mbar_wait(smem_u32(&wready), 0);  // the resident weights
             for (int tl = 0; tl < my_tiles && ok; ++tl) {
                 const int buf = tl & 1;
                 if (tl >= 2) ok = mbar_wait(smem_u32(&tempty[buf]), ((tl >> 1) - 1) & 1);
@@ -625,7 +810,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem_u32(sA + stage * stageA), b0 = smem_u32(sW + j * blockW);
                     for (int kk = 0; kk < kb / 16; ++kk) {
-                        const uint64_t da = smem_desc(a0 + kk * 256, 128, sbo);
+                        const uint64_t da = tma_a ? smem_desc_sw128(a0 + kk * 32) : smem_desc(a0 + kk * 256, 128, sbo);
                         const uint64_t db = smem_desc(b0 + kk * 256, 128, sbo);
                         const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
                         asm volatile(
@@ -658,12 +843,14 @@ __global__ void __launch_bounds__(kThreadsWS, 1) k_gemm_ws(GemmArgs g)
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            gemm_epilogue<BN>(g, tmem + buf * BN, (bx + tl * gx) * kBM + q * 32 + lane, q,
-                              g.bias ? s_bias : nullptr, g.head_w ? s_headw : nullptr);
+            gemm_epilogue_tma<BN>(g, &map_out, &map_outT, tmem + buf * BN, (bx + tl * gx) * kBM + q * 32, q,
+                                  g.bias ? s_bias : nullptr, g.head_w ? s_headw : nullptr, sE + q * kEpiStage);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
         }
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the stores are done
+        __syncwarp();
     }
     if (!ok && g.err && lane == 0) atomicExch(g.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
