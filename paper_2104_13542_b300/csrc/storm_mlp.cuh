@@ -3,11 +3,13 @@
 // The paper replaces its exact self-collision check by a learned distance
 // network (Sec. 4.2, Eq. 13).  Here: 16 encoded inputs -> 256 -> 256 -> 256 -> 1
 // with ReLU, BF16 operands and FP32 accumulation.  Every GEMM runs on the 5th
-// generation tensor cores: operands staged in shared memory by cp.async in the
-// no-swizzle K-major core-matrix layout, one elected thread issues
-// tcgen05.mma with the accumulator in tensor memory (TMEM), tcgen05.commit
-// signals an mbarrier, and the epilogue reads TMEM with tcgen05.ld.  Every
-// wait is bounded in time and reports through an error flag.
+// generation tensor cores: operands staged in shared memory (by cp.async in the
+// no-swizzle K-major core-matrix layout, or, for the warp-specialised layer
+// kernel's 64-column K tiles, by TMA tensor loads in the 128-byte swizzled
+// layout), one elected thread issues tcgen05.mma with the accumulator in tensor
+// memory (TMEM), tcgen05.commit signals an mbarrier, and the epilogue reads TMEM
+// with tcgen05.ld (the layer kernel writes its tiles back by TMA tensor
+// stores).  Every wait is bounded in time and reports through an error flag.
 #pragma once
 
 #include <cuda.h>
