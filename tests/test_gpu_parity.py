@@ -644,3 +644,26 @@ def test_broadphase_is_bitwise_identical(seed, world):
     for k in outs[0]:
         assert np.array_equal(outs[0][k], outs[1][k]), k
     assert (outs[0]["terms"][..., 5] > 0).any() or (outs[0]["terms"][..., 6] > 0).any()
+
+
+@pytest.mark.parametrize("per_link", [1, 2])
+def test_broadphase_with_point_and_short_capsules_is_bitwise_identical(per_link):
+    """Links with one sphere (the capsule's segment a point) and two spheres:
+    the capsule cull passes every pair that touches, so every output equals the
+    brute-force tests bit for bit, at a folded configuration (self collision)
+    among a dense world; the self and world terms are non-zero somewhere."""
+    wl = W.config_paper(6)
+    wl.robot = W.make_robot(6, 7, spheres_per_link=per_link)
+    wl.world = W.make_world(46, n_boxes=64, n_spheres=64)
+    p = wl.params.replace(N=200)
+    state, goal = cuda(f32(_folded_state(wl))), cuda(f32(wl.goal))
+    mu, sig = f32(W.make_mean(6, p.H, 7, 0.8)), f32(W.make_sigma(6, 7, 0.2, 0.6))
+    outs = []
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(mu, sig)
+        for on in (True, False):
+            ctl.set_broadphase(on)
+            outs.append({k: host(v) for k, v in ctl.generate_rollouts(state, goal, 2, 1).items()})
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    assert (outs[0]["terms"][..., 5] > 0).any() and (outs[0]["terms"][..., 6] > 0).any()
