@@ -233,6 +233,8 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     __shared__ int s_task_v;
+    __shared__ float s_ubox[4][6];  // the collision warps' boxes around the CTA's link bounds
+    __shared__ unsigned s_cand[4];  // obstacles that box meets: boxes 0-31, 32-63, spheres 0-31, 32-63
     __shared__ int s_cflag_v;
     int* s_task = &s_task_v;
     volatile int* s_cflag = &s_cflag_v;
@@ -671,6 +673,10 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     const unsigned long long all_o = pb.O >= 64 ? ~0ull : (1ull << pb.O) - 1ull;
     if (!cost_warp) {  // the collision warps
     if (bp) {
+        // the bounds' centres, and one box around every bound of the CTA's steps;
+        // the obstacles that box meets are the only candidates for any (step,
+        // frame) below (a conservative cull: the same masks as testing all)
+        float ulo[3] = {INFINITY, INFINITY, INFINITY}, uhi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int idx = ct; idx < I * F; idx += coll_threads) {
             const int item = idx / F, f = idx - item * F;
             const float4 q = s_lb[f];
@@ -680,20 +686,69 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
             const float cy = fmaf(r1.x, q.x, fmaf(r1.y, q.y, fmaf(r1.z, q.z, r1.w)));
             const float cz = fmaf(r2.x, q.x, fmaf(r2.y, q.y, fmaf(r2.z, q.z, r2.w)));
             s_lcent[idx] = make_float4(cx, cy, cz, q.w);
-            unsigned long long mb = 0ull, mo = 0ull;
-#pragma unroll 4
-            for (int b = 0; b < pb.B; ++b) {
-                const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
-                const float ex = cx - fminf(fmaxf(cx, lo.x), hi.x);
-                const float ey = cy - fminf(fmaxf(cy, lo.y), hi.y);
-                const float ez = cz - fminf(fmaxf(cz, lo.z), hi.z);
-                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < q.w * q.w) mb |= 1ull << b;
+            if (q.w > 0.f) {  // (a frame without spheres has an empty bound)
+                ulo[0] = fminf(ulo[0], cx - q.w), uhi[0] = fmaxf(uhi[0], cx + q.w);
+                ulo[1] = fminf(ulo[1], cy - q.w), uhi[1] = fmaxf(uhi[1], cy + q.w);
+                ulo[2] = fminf(ulo[2], cz - q.w), uhi[2] = fmaxf(uhi[2], cz + q.w);
             }
-#pragma unroll 4
-            for (int k = 0; k < pb.O; ++k) {
+        }
+        const int lane = tid & 31, cw = ct >> 5, ncw = coll_threads >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                ulo[a] = fminf(ulo[a], __shfl_xor_sync(0xffffffffu, ulo[a], o));
+                uhi[a] = fmaxf(uhi[a], __shfl_xor_sync(0xffffffffu, uhi[a], o));
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s_ubox[cw][a] = ulo[a], s_ubox[cw][3 + a] = uhi[a];
+        coll_sync();
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            ulo[a] = s_ubox[0][a], uhi[a] = s_ubox[0][3 + a];
+            for (int w = 1; w < ncw; ++w) ulo[a] = fminf(ulo[a], s_ubox[w][a]), uhi[a] = fmaxf(uhi[a], s_ubox[w][3 + a]);
+        }
+        // candidate words: boxes 0-31, 32-63, obstacle spheres 0-31, 32-63
+        for (int k0 = cw * 32; k0 < 4 * 32; k0 += coll_threads) {
+            const int k = k0 + lane;
+            bool near = false;
+            if (k < 64) {
+                if (k < pb.B) {
+                    const float4 lo = s_boxlh[2 * k], hi = s_boxlh[2 * k + 1];
+                    near = lo.x <= uhi[0] && hi.x >= ulo[0] && lo.y <= uhi[1] && hi.y >= ulo[1] && lo.z <= uhi[2] &&
+                           hi.z >= ulo[2];
+                }
+            } else if (k - 64 < pb.O) {
+                const float4 w = s_wsph[k - 64];
+                const float ex = w.x - fminf(fmaxf(w.x, ulo[0]), uhi[0]);
+                const float ey = w.y - fminf(fmaxf(w.y, ulo[1]), uhi[1]);
+                const float ez = w.z - fminf(fmaxf(w.z, ulo[2]), uhi[2]);
+                near = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= w.w * w.w;
+            }
+            const unsigned word = __ballot_sync(0xffffffffu, near);
+            if (lane == 0) s_cand[k0 >> 5] = word;
+        }
+        coll_sync();
+        const unsigned long long cb = s_cand[0] | (static_cast<unsigned long long>(s_cand[1]) << 32);
+        const unsigned long long co = s_cand[2] | (static_cast<unsigned long long>(s_cand[3]) << 32);
+        for (int idx = ct; idx < I * F; idx += coll_threads) {
+            const float4 c = s_lcent[idx];
+            unsigned long long mb = 0ull, mo = 0ull;
+            for (unsigned long long m = cb; m; m &= m - 1ull) {
+                const int b = __ffsll(static_cast<long long>(m)) - 1;
+                const float4 lo = s_boxlh[2 * b], hi = s_boxlh[2 * b + 1];
+                const float ex = c.x - fminf(fmaxf(c.x, lo.x), hi.x);
+                const float ey = c.y - fminf(fmaxf(c.y, lo.y), hi.y);
+                const float ez = c.z - fminf(fmaxf(c.z, lo.z), hi.z);
+                if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < c.w * c.w) mb |= 1ull << b;
+            }
+            for (unsigned long long m = co; m; m &= m - 1ull) {
+                const int k = __ffsll(static_cast<long long>(m)) - 1;
                 const float4 w = s_wsph[k];
-                const float ex = cx - w.x, ey = cy - w.y, ez = cz - w.z;
-                const float rb = q.w + w.w;
+                const float ex = c.x - w.x, ey = c.y - w.y, ez = c.z - w.z;
+                const float rb = c.w + w.w;
                 if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < rb * rb) mo |= 1ull << k;
             }
             s_mask[2 * idx] = mb;
