@@ -667,3 +667,49 @@ def test_broadphase_with_point_and_short_capsules_is_bitwise_identical(per_link)
     for k in outs[0]:
         assert np.array_equal(outs[0][k], outs[1][k]), k
     assert (outs[0]["terms"][..., 5] > 0).any() and (outs[0]["terms"][..., 6] > 0).any()
+
+
+@pytest.mark.parametrize("dof", [1, 2, 3, 4])
+def test_short_chains(dof):
+    """Chains of one to four joints (one to five frames; self-collision pairs
+    only from three joints on), in a world of boxes and spheres: every rollout
+    mapping gives the same bits, with the broad phase on and off, and the
+    control step matches the oracle.  The manipulability weight is 0: with
+    fewer than six joints J J^T is singular and m is 0 up to rounding."""
+    s = 30 + dof
+    robot = W.make_robot(s, dof)
+    world = W.make_world(s, n_boxes=12, n_spheres=6)
+    p = W.config_paper(0).params.replace(N=48, H=12, n_knots=4, dt=np.full(12, 0.02), w_manip=0.0)
+    wl = W.Workload(f"chain{dof}", robot, world, p, W.make_state(s, dof), W.make_goal(s))
+    state, goal = f32(wl.state), f32(wl.goal)
+    mu0, sig0 = f32(W.make_mean(s, p.H, dof, 0.8)), f32(W.make_sigma(s, dof, 0.2, 0.6))
+    with _ctl(wl, p) as ctl:
+        ctl.set_distribution(mu0, sig0)
+        ref = None
+        for bp in (True, False):
+            ctl.set_broadphase(bp)
+            for mapping, count in (("cta", 0), ("warp", 1), ("pair", 1), ("quad", 1)):
+                if mapping == "cta":
+                    ctl.set_launch(2, 128)
+                else:
+                    {"warp": ctl.set_launch_warp, "pair": ctl.set_launch_warp_pair,
+                     "quad": ctl.set_launch_warp_quad}[mapping](count)
+                g = {k: host(v) for k, v in ctl.generate_rollouts(cuda(state), cuda(goal), 1, 0).items()}
+                if ref is None:
+                    ref = g
+                for k in ref:
+                    assert np.array_equal(g[k], ref[k]), (bp, mapping, k)
+        ctl.set_broadphase(True)
+        ctl.set_launch_warp_pair(1)
+        ctl.reset()
+        cmd, info, rc = ctl.step(state, goal)
+        mu, sig = ctl.get_distribution()
+    orc = oracle.Oracle(robot, world, p)
+    ocmd, omu, osig, ost, obest = orc.step(state, goal, 0, np.zeros((p.H, dof)), np.full(dof, f32(p.sigma_init)))
+    assert rc == ost == 0
+    tol = mu_tolerance([obest, info["mean_weighted_cost"]], p.beta)
+    scale = max(1.0, np.abs(omu).max())
+    assert max_rel(mu, omu, scale) < tol
+    assert max_rel(cmd, ocmd, scale) < tol
+    assert max_rel(sig, osig, max(1e-3, osig.max())) < tol
+    assert abs(info["best_cost"] - obest) <= TOL_COST * max(1.0, abs(obest))
