@@ -17,8 +17,8 @@
 // each item's work across warps.  Warp A draws the controls and integrates
 // them; then every warp of the group runs FK into its own copy of the link
 // frames.  Pair: A takes the pose, joint and end-effector terms and world
-// collision, B the manipulability term and self collision, and A, once its own terms are
-// done, joins in: B publishes each item's mask of overlapping frame pairs in
+// collision, B the manipulability term and self collision, and A, once its
+// own terms are done, joins in: B publishes each item's mask of overlapping frame pairs in
 // shared memory, and the pairs are claimed one at a time from a per-item
 // counter, B from the first pair, A from the last, so that every pair is
 // tested exactly once and the two warps finish together however the work
@@ -784,7 +784,7 @@ __device__ __forceinline__ void rollout_warp_body(const Problem& pb, const Rollo
 #pragma unroll
             for (int f = 1; f < kMaxDof; ++f) la += t >= link_pair_index(f, f + 1);
             const int lk = t - link_pair_index(la, la + 1) + la + 1;
-            // the second frame's capsule: segment k0 + s e, radius rk
+            // the second frame's capsule: the segment k0 + s ke, s in [0, 1], radius kc0.w
             const float4 kc0 = pb.lcap[2 * lk], kc1 = pb.lcap[2 * lk + 1];
             const float3 k0 = frame_point(s_fr + lk * 12 * 32, lane, kc0);
             const float3 k1 = frame_point(s_fr + lk * 12 * 32, lane, kc1);
