@@ -568,6 +568,10 @@ def run_variants(args, seed: int, fp32_peak: float | None = None):
             th = torch.as_tensor(rng.uniform(-2.8, 2.8, (1 << 20, 7)).astype(np.float32), device="cuda")
             th_te = torch.as_tensor(rng.uniform(-2.8, 2.8, (65_536, 7)).astype(np.float32), device="cuda")
             sd, sd_te = lab.self_distance(th), lab.self_distance(th_te)
+        if spl == 7:  # the first training call of the process also loads its kernels: untimed
+            warm = SurrogateMLP(seed=seed + 1)
+            warm.train(th[:8192], torch.clamp(sd[:8192], max=0.5), batch=4096, epochs=1, lr=2e-3, seed=seed)
+            warm.close()
         net = SurrogateMLP(seed=seed)
         t0 = time.perf_counter()
         losses = net.train(th, torch.clamp(sd, max=0.5), batch=4096, epochs=8, lr=2e-3, seed=seed)
