@@ -364,6 +364,10 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     auto coll_self_tasks = [&]() {
         const int lane = tid & 31, ntask = I * pb.NPB;
         const int grp = lane >> 3, r8 = lane & 7;
+        // task -> step without a division: (task + 1/2) / NPB is at least 1/(2 NPB)
+        // from an integer, far beyond FP32's error for the task counts here
+        const float inv_npb = 1.f / static_cast<float>(pb.NPB > 0 ? pb.NPB : 1);
+        auto step_of = [&](int task) { return __float2int_rd((static_cast<float>(task) + 0.5f) * inv_npb); };
         while (true) {
             int base = 0;
             if (lane == 0) base = atomicAdd(s_task, 32);
@@ -372,7 +376,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
             const int idx = base + lane;
             bool live = idx < ntask;
             if (live && bp) {  // the two links' bounds apart: no pair of the block touches
-                const int item = idx / pb.NPB;
+                const int item = step_of(idx);
                 const uint4 blk = s_pblk[idx - item * pb.NPB];
                 const float4 A = s_lcent[item * F + s_slink[blk.x]], B2 = s_lcent[item * F + s_slink[blk.z]];
                 const float ex = A.x - B2.x, ey = A.y - B2.y, ez = A.z - B2.z;
@@ -396,7 +400,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
                 unsigned long long key = 0ull;
                 int item = 0;
                 if (src != 0xffffffffu) {
-                    item = tix / pb.NPB;
+                    item = step_of(tix);
                     const int bk = tix - item * pb.NPB;
                     const uint4 blk = s_pblk[bk];
                     const float4* ci = s_cent + item * M;
@@ -677,8 +681,12 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         // the obstacles that box meets are the only candidates for any (step,
         // frame) below (a conservative cull: the same masks as testing all)
         float ulo[3] = {INFINITY, INFINITY, INFINITY}, uhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        const int bp_dq = coll_threads / F, bp_dr = coll_threads - bp_dq * F;
+        int bp_item = ct / F, bp_f = ct - bp_item * F;
         for (int idx = ct; idx < I * F; idx += coll_threads) {
-            const int item = idx / F, f = idx - item * F;
+            const int item = bp_item, f = bp_f;
+            bp_item += bp_dq, bp_f += bp_dr;
+            if (bp_f >= F) bp_f -= F, ++bp_item;
             const float4 q = s_lb[f];
             const float4* T = s_frame + item * FS + f * 3;
             const float4 r0 = T[0], r1 = T[1], r2 = T[2];
@@ -757,9 +765,14 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
         coll_sync();
     }
 
-    // ---- sphere centres; world collision with its minimiser (sphere, obstacle)
+    // ---- sphere centres; world collision with its minimiser (sphere, obstacle);
+    // each thread's (step, sphere) advances by coll_threads tasks without a division
+    const int sph_dq = coll_threads / M, sph_dr = coll_threads - sph_dq * M;
+    int sph_item = ct / M, sph_s = ct - sph_item * M;
     for (int idx = ct; idx < I * M; idx += coll_threads) {
-        const int item = idx / M, s = idx - item * M;
+        const int item = sph_item, s = sph_s;
+        sph_item += sph_dq, sph_s += sph_dr;
+        if (sph_s >= M) sph_s -= M, ++sph_item;
         const float4 q = s_sph[s];
         const float4* T = s_frame + item * FS + s_slink[s] * 3;
         const float4 r0 = T[0], r1 = T[1], r2 = T[2];
