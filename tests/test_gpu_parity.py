@@ -376,6 +376,25 @@ def test_checkpoint_resume_is_bitwise():
     assert np.array_equal(mu_a, mu_b) and np.array_equal(sig_a, sig_b)
 
 
+def test_rewound_handle_reruns_bitwise():
+    """A handle rewound to a checkpoint of its own (set_state after further
+    steps) reruns those steps bit for bit: nothing of the later steps (the
+    step counter, the mean, sigma) leaks into the rerun."""
+    wl, p = VARIANTS["paper"]
+    state, goal = f32(wl.state), f32(wl.goal)
+    with _ctl(wl, p) as a:
+        a.step(state, goal)
+        blob = a.get_state()
+        ref = [a.step(state, goal)[0] for _ in range(3)]
+        mu_a, sig_a = a.get_distribution()
+        a.set_state(blob)
+        got = [a.step(state, goal)[0] for _ in range(3)]
+        mu_b, sig_b = a.get_distribution()
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    assert np.array_equal(mu_a, mu_b) and np.array_equal(sig_a, sig_b)
+
+
 def test_determinism_across_handles():
     wl, p = VARIANTS["paper"]
     state, goal = f32(wl.state), f32(wl.goal)
