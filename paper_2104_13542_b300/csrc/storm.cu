@@ -1519,9 +1519,10 @@ cudaError_t gemm_rw_bn(const tc::GemmArgs& g, cudaStream_t s)
     // the operand's TMA loads, and the epilogue's TMA stores: 64-column x 32-row
     // boxes of the output (128-byte swizzle), 32-row x 64-column boxes of its
     // transpose
-    CUtensorMap map_a{}, map_out{}, map_outT{};
-    if (g.K % tc::kKB == 0) {  // A tiles of 128 rows x 64 K by TMA, 128-byte swizzle
-        const cudaError_t e = bf16_map(&map_a, g.A, g.M, g.K, g.lda, tc::kKB, tc::kBM, true);
+    CUtensorMap map_a{}, map_b{}, map_out{}, map_outT{};
+    if (g.K % tc::kKB == 0) {  // A tiles of 128 rows x 64 K and the weights' BN x 64 K blocks by TMA, 128-byte swizzle
+        cudaError_t e = bf16_map(&map_a, g.A, g.M, g.K, g.lda, tc::kKB, tc::kBM, true);
+        if (e == cudaSuccess) e = bf16_map(&map_b, g.B, g.N, g.K, g.ldb, tc::kKB, BN, true);
         if (e != cudaSuccess) return e;
     }
     if (g.out_bf) {
@@ -1532,7 +1533,7 @@ cudaError_t gemm_rw_bn(const tc::GemmArgs& g, cudaStream_t s)
         const cudaError_t e = bf16_map(&map_outT, g.out_bfT, g.N, g.M, g.ldoT, 32, 64, false);
         if (e != cudaSuccess) return e;
     }
-    tc::k_gemm_ws<BN><<<grid, tc::kThreadsWS, smem, s>>>(g, map_a, map_out, map_outT);
+    tc::k_gemm_ws<BN><<<grid, tc::kThreadsWS, smem, s>>>(g, map_a, map_b, map_out, map_outT);
     return cudaGetLastError();
 }
 

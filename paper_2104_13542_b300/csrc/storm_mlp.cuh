@@ -344,18 +344,43 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32])
 // values r): bias, ReLU and mask into v, and the dot head's running sums (each
 // half of the columns summed in column order, the halves added at the end: the
 // order of the whole-network tile's two epilogue warps).
-template <int BN>
+// kShared: bias and head_w are 16-byte aligned shared-memory vectors, read as
+// float4 broadcasts (otherwise any pointers, read element by element).
+__device__ __forceinline__ float4 lds4(const float* p)
+{
+    float4 x;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w)
+                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))));
+    return x;
+}
+
+template <int BN, bool kShared = false>
 __device__ __forceinline__ void epilogue_block(const GemmArgs& g, const uint32_t (&r)[32], int row, int c0,
                                                const float* bias, const float* head_w, float (&v)[32],
                                                float& yacc, float& yacc0)
 {
+    if (kShared) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const int n = c0 + i;
-        float x = __uint_as_float(r[i]);
-        if (bias) x += bias[n];
-        if (g.relu) x = fmaxf(x, 0.f);
-        v[i] = x;
+        for (int q = 0; q < 8; ++q) {
+            const float4 b = bias ? lds4(bias + c0 + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float bq[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                float x = __uint_as_float(r[4 * q + l]);
+                if (bias) x += bq[l];
+                if (g.relu) x = fmaxf(x, 0.f);
+                v[4 * q + l] = x;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int n = c0 + i;
+            float x = __uint_as_float(r[i]);
+            if (bias) x += bias[n];
+            if (g.relu) x = fmaxf(x, 0.f);
+            v[i] = x;
+        }
     }
     if (g.mask) {
         const uint4* mk = reinterpret_cast<const uint4*>(g.mask + static_cast<size_t>(row) * g.ldm + c0);
@@ -373,8 +398,19 @@ __device__ __forceinline__ void epilogue_block(const GemmArgs& g, const uint32_t
             yacc0 = yacc;
             yacc = 0.f;
         }
+        if (kShared) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) yacc = fmaf(head_w[c0 + i], v[i], yacc);
+            for (int q = 0; q < 8; ++q) {
+                const float4 w = lds4(head_w + c0 + 4 * q);
+                yacc = fmaf(w.x, v[4 * q], yacc);
+                yacc = fmaf(w.y, v[4 * q + 1], yacc);
+                yacc = fmaf(w.z, v[4 * q + 2], yacc);
+                yacc = fmaf(w.w, v[4 * q + 3], yacc);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) yacc = fmaf(head_w[c0 + i], v[i], yacc);
+        }
     }
     if (g.out_f) {
         float4* o = reinterpret_cast<float4*>(g.out_f + static_cast<size_t>(row) * g.ldf + c0);
@@ -452,7 +488,7 @@ __device__ __forceinline__ void gemm_epilogue_tma(const GemmArgs& g, const CUten
     // also stores the block
     auto half_block = [&](const uint32_t (&r)[32], int c0, int half) {
         float v[32];
-        epilogue_block<BN>(g, r, row, c0, bias, head_w, v, yacc, yacc0);
+        epilogue_block<BN, true>(g, r, row, c0, bias, head_w, v, yacc, yacc0);
         if (half == 0) {  // the previous block's stores have read the staging tiles
             if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             __syncwarp();
@@ -460,10 +496,11 @@ __device__ __forceinline__ void gemm_epilogue_tma(const GemmArgs& g, const CUten
         if (g.out_bf) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                __align__(16) __nv_bfloat16 b[8];
+                __nv_bfloat162 b[4];  // (round to nearest per element, as __float2bfloat16_rn)
 #pragma unroll
-                for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[q * 8 + i]);
-                const uint4 w = *reinterpret_cast<const uint4*>(b);
+                for (int i = 0; i < 4; ++i) b[i] = __floats2bfloat162_rn(v[q * 8 + 2 * i], v[q * 8 + 2 * i + 1]);
+                const uint4 w = make_uint4(*reinterpret_cast<const uint32_t*>(&b[0]), *reinterpret_cast<const uint32_t*>(&b[1]),
+                                           *reinterpret_cast<const uint32_t*>(&b[2]), *reinterpret_cast<const uint32_t*>(&b[3]));
                 const uint32_t a = s_bf + lane * 128 + (((half * 4 + q) ^ (lane & 7)) << 4);
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w.x), "r"(w.y), "r"(w.z),
                              "r"(w.w)
@@ -635,9 +672,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
 // The same layer as k_gemm_rw (weights resident, N = BN) with the roles split
 // across warps so that loading, multiplying and draining overlap:
 //   warp 0     producer: the weights once, then the A tiles through kStagesWS
-//              shared-memory stages with cp.async; it waits for its own copies
-//              kLagWS groups behind, fences them into the async proxy and
-//              signals full[stage];
+//              shared-memory stages.  K a multiple of 64: both by TMA into the
+//              128-byte swizzled layout (the weights' boxes complete wready,
+//              each A stage its full[stage]); K = 16: cp.async into core
+//              matrices, waited for kLagWS groups behind, fenced into the
+//              async proxy, then full[stage] signalled;
 //   warp 1     one thread issues the tcgen05.mma of each K block once
 //              full[stage] completes, commits to empty[stage] (the stage is
 //              free again when those MMAs finish) and, at a tile's end, to
@@ -664,14 +703,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr)
 
 template <int BN>
 __global__ void __launch_bounds__(kThreadsWS, 1)
-    k_gemm_ws(GemmArgs g, const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_out,
-              const __grid_constant__ CUtensorMap map_outT)
+    k_gemm_ws(GemmArgs g, const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+              const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_outT)
 {
     constexpr uint32_t kCols = 2 * BN;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kStagesWS], empty[kStagesWS], tfull[2], tempty[2], wready;
     __shared__ uint32_t tmem_slot;
-    __shared__ float s_bias[BN], s_headw[BN];  // the epilogue's per-column vectors, read by every row
+    __shared__ __align__(16) float s_bias[BN];   // the epilogue's per-column vectors, read by every row
+    __shared__ __align__(16) float s_headw[BN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = g.K, kb = K < kKB ? K : kKB, nk = K / kb;
     // A tiles of 64 K columns come by TMA in the 128-byte swizzled layout (the
@@ -721,7 +761,19 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
 
     if (warp == 0) {
         // ---- producer
-        {  // the weights, resident for the CTA's tiles: cp.async by the whole warp
+        // the weights, resident for the CTA's tiles.  64-K blocks: one TMA box of
+        // BN rows each, in the A tiles' 128-byte swizzled layout, completing on
+        // wready (every CTA reads the same lines: one warp's cp.async stream of
+        // them took longer than the whole main loop); else core matrices by
+        // cp.async from the whole warp.
+        if (tma_a) {
+            if (lane == 0) {
+                const uint32_t wb = smem_u32(&wready);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wb), "r"(nk * blockW)
+                             : "memory");
+                for (int j = 0; j < nk; ++j) tma_load_2d(&map_b, smem_u32(sW + j * blockW), wb, j * kb, 0);
+            }
+        } else {
             const int chunks = kb / 8;
             for (int c = lane; c < nk * BN * chunks; c += 32) {
                 const int j = c / (BN * chunks), rem = c - j * BN * chunks;
@@ -734,8 +786,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         if (tma_a) {
             // one thread posts each stage's byte count on the stage's mbarrier and
             // starts its TMA copy, which completes the count (no waiting on copies
-            // here); the weights are waited for once the first stages are in
-            // flight, and announced on wready
+            // here)
             auto issue = [&](int i) {
                 const int stage = i % kStagesWS, t = bx + (i / nk) * gx, j = i % nk;
                 const uint32_t fb = smem_u32(&full[stage]);
@@ -744,13 +795,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 tma_load_2d(&map_a, smem_u32(sA + stage * stageA), fb, j * kb, t * kBM);
             };
             const int first = total < kStagesWS ? total : kStagesWS;
-            if (lane == 0)
-                for (int i = 0; i < first; ++i) issue(i);
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
             if (lane == 0) {
-                mbar_arrive(smem_u32(&wready));
+                for (int i = 0; i < first; ++i) issue(i);
                 int issued = first;
                 for (int i = first; i < total && ok; ++i) {
                     const int stage = i % kStagesWS;  // the MMAs of item i - kStagesWS released the stage
@@ -761,6 +807,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 // a phase the MMA thread has already consumed answers at once)
                 for (int i = issued > kStagesWS ? issued - kStagesWS : 0; i < issued; ++i)
                     if (!mbar_wait(smem_u32(&full[i % kStagesWS]), (i / kStagesWS) & 1)) ok = false;
+                if (!mbar_wait(smem_u32(&wready), 0)) ok = false;
             }
             __syncwarp();
         } else {
@@ -813,7 +860,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     const uint32_t a0 = smem_u32(sA + stage * stageA), b0 = smem_u32(sW + j * blockW);
                     for (int kk = 0; kk < kb / 16; ++kk) {
                         const uint64_t da = tma_a ? smem_desc_sw128(a0 + kk * 32) : smem_desc(a0 + kk * 256, 128, sbo);
-                        const uint64_t db = smem_desc(b0 + kk * 256, 128, sbo);
+                        const uint64_t db = tma_a ? smem_desc_sw128(b0 + kk * 32) : smem_desc(b0 + kk * 256, 128, sbo);
                         const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
