@@ -473,11 +473,14 @@ constexpr int kEpiStage = 32 * 128 + 64 * 64;
 // written to shared memory and stored by TMA, one 64-column block per bulk
 // group (full 128-byte lines to global memory instead of per-row pieces, and
 // 64 shared-memory stores for the transposed copy instead of 32-bit-strided
-// global ones).  row0: the warp's first row; lane 0 issues the stores.
+// global ones).  row0: the warp's first row; lane 0 issues the stores.  The
+// warp takes columns [c_lo, c_hi) (64-column blocks) and returns its part of
+// the dot head: the running sums of epilogue_block added, first half + second.
 template <int BN>
-__device__ __forceinline__ void gemm_epilogue_tma(const GemmArgs& g, const CUtensorMap* map_out,
-                                                  const CUtensorMap* map_outT, uint32_t tmem, int row0, int warp,
-                                                  const float* bias, const float* head_w, unsigned char* stage)
+__device__ __forceinline__ float gemm_epilogue_tma(const GemmArgs& g, const CUtensorMap* map_out,
+                                                   const CUtensorMap* map_outT, uint32_t tmem, int row0, int warp,
+                                                   const float* bias, const float* head_w, unsigned char* stage,
+                                                   int c_lo, int c_hi)
 {
     static_assert(BN % 64 == 0, "64-column store blocks");
     const int lane = threadIdx.x & 31, row = row0 + lane;
@@ -528,18 +531,18 @@ __device__ __forceinline__ void gemm_epilogue_tma(const GemmArgs& g, const CUten
     };
     // each block's TMEM load is in flight while the block before it is worked on
     uint32_t ra[32], rb[32];
-    tmem_ld32_async(tl, ra);
+    tmem_ld32_async(tl + c_lo, ra);
     tmem_ld_wait(ra);
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 64) {
+    for (int c0 = c_lo; c0 < c_hi; c0 += 64) {
         tmem_ld32_async(tl + c0 + 32, rb);
         half_block(ra, c0, 0);
         tmem_ld_wait(rb);
-        if (c0 + 64 < BN) tmem_ld32_async(tl + c0 + 64, ra);
+        if (c0 + 64 < c_hi) tmem_ld32_async(tl + c0 + 64, ra);
         half_block(rb, c0 + 32, 1);
-        if (c0 + 64 < BN) tmem_ld_wait(ra);
+        if (c0 + 64 < c_hi) tmem_ld_wait(ra);
     }
-    if (head_w) g.head_y[row] = *g.head_b + (yacc0 + yacc);
+    return yacc0 + yacc;
 }
 
 template <int BN>
@@ -682,13 +685,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_rw(GemmArgs g)
 //              free again when those MMAs finish) and, at a tile's end, to
 //              tfull[buf] (accumulator buffer buf = tile parity, 2 x BN TMEM
 //              columns);
-//   warps 2-5  the epilogue: warp w drains TMEM lanes 32 (w % 4) .. +31 of
-//              buffer buf, then arrives on tempty[buf].
+//   warps 2-9  the epilogue: warp w drains TMEM lanes 32 (w % 4) .. +31 of
+//              buffer buf, then arrives on tempty[buf].  Eight warps (two per
+//              lane quarter, half the columns each) when no transposed copy is
+//              written, else warps 2-5 alone (the others have no work).
 // Every wait is bounded (1 s): on a timeout the role sets *err and leaves its
 // loop; the others time out in turn, and the CTA still meets at the final
 // barrier before the TMEM is freed.
 constexpr int kStagesWS = 4, kLagWS = 3;
-constexpr int kThreadsWS = 192;
+constexpr int kThreadsWS = 320;
 
 __host__ __device__ constexpr size_t gemm_ws_smem(int BN, int K)
 {
@@ -729,6 +734,10 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
     const int tiles = g.M / kBM, bx = blockIdx.x, gx = gridDim.x;
     const int my_tiles = tiles > bx ? (tiles - 1 - bx) / gx + 1 : 0;
     const int total = my_tiles * nk;
+    // epilogue warps: eight (two per TMEM lane quarter, half the columns each)
+    // when the second staging tile is free (no transposed copy) and the halves
+    // are whole 64-column blocks, else four
+    const int nepi = (g.out_bfT == nullptr && BN >= 128) ? 8 : 4;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -737,10 +746,6 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int n = threadIdx.x; n < BN; n += blockDim.x) {
-        s_bias[n] = g.bias ? g.bias[n] : 0.f;
-        s_headw[n] = g.head_w ? g.head_w[n] : 0.f;
-    }
     if (threadIdx.x == 32) {
         for (int i = 0; i < kStagesWS; ++i) {
             mbar_init(smem_u32(&full[i]), 1);
@@ -748,7 +753,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
-            mbar_init(smem_u32(&tempty[b]), 4);
+            mbar_init(smem_u32(&tempty[b]), nepi);
         }
         mbar_init(smem_u32(&wready), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -883,20 +888,44 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 ok = mbar_wait(smem_u32(&tfull[(my_tiles - 1) & 1]), ((my_tiles - 1) >> 1) & 1);
         }
         __syncwarp();
-    } else {
-        // ---- epilogue warps 2..5: TMEM lanes 32 (warp % 4) + lane
-        const int q = warp & 3;
-        for (int tl = 0; tl < my_tiles && ok; ++tl) {
-            const int buf = tl & 1;
-            ok = mbar_wait(smem_u32(&tfull[buf]), (tl >> 1) & 1);
+    } else if (warp - 2 < nepi) {
+        // ---- epilogue warps: TMEM lanes 32 (warp % 4) + lane; with eight, warp
+        // 2 + e takes the first half of the columns (e < 4) or the second,
+        // staging in the quarter's second tile, and the pair adds its head parts
+        // in that order (the second half's part passed through head_y: its rows
+        // are the tile's own).  A warp whose wait ran out goes on through the
+        // tiles without work, so that its partner never waits for it at the
+        // pair's barrier.
+        const int q = warp & 3, h = (warp - 2) >> 2, cw = BN * 4 / nepi;
+        const bool pair_head = g.head_w && nepi == 8;
+        // the per-column vectors, read only here: loaded by these warps while the
+        // first copies and MMAs go on (not before the CTA's opening barrier)
+        for (int n = threadIdx.x - 64; n < BN; n += nepi * 32) {
+            s_bias[n] = g.bias ? g.bias[n] : 0.f;
+            s_headw[n] = g.head_w ? g.head_w[n] : 0.f;
+        }
+        asm volatile("bar.sync 5, %0;" ::"r"(nepi * 32) : "memory");
+        for (int tl = 0; tl < my_tiles; ++tl) {
+            const int buf = tl & 1, row0 = (bx + tl * gx) * kBM + q * 32;
+            float part = 0.f;
+            if (ok) ok = mbar_wait(smem_u32(&tfull[buf]), (tl >> 1) & 1);
             ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            gemm_epilogue_tma<BN>(g, &map_out, &map_outT, tmem + buf * BN, (bx + tl * gx) * kBM + q * 32, q,
-                                  g.bias ? s_bias : nullptr, g.head_w ? s_headw : nullptr, sE + q * kEpiStage);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+            if (ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                part = gemm_epilogue_tma<BN>(g, &map_out, &map_outT, tmem + buf * BN, row0, q,
+                                             g.bias ? s_bias : nullptr, g.head_w ? s_headw : nullptr,
+                                             sE + q * kEpiStage + h * (32 * 128), h * cw, h * cw + cw);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+            }
+            if (pair_head) {
+                if (h == 1) g.head_y[row0 + lane] = part;
+                asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");
+                if (h == 0) g.head_y[row0 + lane] = *g.head_b + (part + g.head_y[row0 + lane]);
+            } else if (g.head_w && ok) {
+                g.head_y[row0 + lane] = *g.head_b + part;
+            }
+            if (ok && lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
         }
         if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the stores are done
         __syncwarp();
