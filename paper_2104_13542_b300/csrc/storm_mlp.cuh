@@ -1196,38 +1196,51 @@ __device__ __forceinline__ bool mlp_tile_issue(const MlpView& v, MlpTiles& t)
     return true;
 }
 
-// TMEM -> registers, 16 consecutive FP32 columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+// TMEM -> registers, 16 consecutive FP32 columns of this thread's lane, without
+// the wait: the registers are valid after tmem_ld16_wait on them (which waits
+// for every load this thread has issued).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16])
 {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// One thread's 16 columns of one row of a 32-column activation block: the
-// accumulator's columns at taddr, + bias (nullable), ReLU, BF16, as two 8-column
-// core-matrix rows at dst (the second 128 bytes after the first).
-__device__ __forceinline__ void mlp_act_half(uint32_t taddr, const float* bias, uint32_t dst)
+__device__ __forceinline__ void tmem_ld16_wait(uint32_t (&r)[16])
 {
-    uint32_t r[16];
-    tmem_ld16(taddr, r);
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])::"memory");
+}
+
+// One thread's 16 columns of one row of a 32-column activation block, from the
+// accumulator values r: + bias (nullable; 16-byte aligned shared memory), ReLU,
+// BF16, as two 8-column core-matrix rows at dst (the second 128 bytes after the
+// first).
+__device__ __forceinline__ void mlp_act_regs(const uint32_t (&r)[16], const float* bias, uint32_t dst)
+{
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
+        float b[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (bias) {
+            const float4 lo = lds4(bias + q * 8), hi = lds4(bias + q * 8 + 4);
+            b[0] = lo.x, b[1] = lo.y, b[2] = lo.z, b[3] = lo.w, b[4] = hi.x, b[5] = hi.y, b[6] = hi.z, b[7] = hi.w;
+        }
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float x0 = __uint_as_float(r[q * 8 + 2 * i]), x1 = __uint_as_float(r[q * 8 + 2 * i + 1]);
             if (bias) {
-                x0 += bias[q * 8 + 2 * i];
-                x1 += bias[q * 8 + 2 * i + 1];
+                x0 += b[2 * i];
+                x1 += b[2 * i + 1];
             }
             x0 = fmaxf(x0, 0.f);
             x1 = fmaxf(x1, 0.f);
-            const __nv_bfloat16 b0 = __float2bfloat16_rn(x0), b1 = __float2bfloat16_rn(x1);
-            w[i] = static_cast<uint32_t>(__bfloat16_as_ushort(b0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b1)) << 16);
+            const __nv_bfloat162 p = __floats2bfloat162_rn(x0, x1);  // (x0 in the low half)
+            w[i] = *reinterpret_cast<const uint32_t*>(&p);
         }
         asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + q * 128), "r"(w[0]), "r"(w[1]),
                      "r"(w[2]), "r"(w[3])
@@ -1275,19 +1288,35 @@ __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t,
     const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
     const uint32_t RA = t.tmem, RB = t.tmem + 256;
     bool ok = mlp_wait_layer(t);  // layer 1
+    // the warp's 16-column pieces of a layer in order: piece u is half hf of
+    // block u / H (with 8 warps one half, warp / 4, of every block); each piece's
+    // TMEM load is in flight while the piece before it is worked on, and a
+    // block is announced once its last piece is stored
+    constexpr int H = kEpi == 8 ? 1 : 2;
     for (int L = 2; L <= 3 && ok; ++L) {
-        const int K = L == 2 ? v.h1 : v.h2;
+        const int K = L == 2 ? v.h1 : v.h2, nu = (K / kBlockK) * H;
         const uint32_t src = (L == 2 ? RA : RB) + lane_off;
         const float* bias = L == 2 ? nullptr : s_b2;
-        for (int j = 0; j < K / kBlockK; ++j) {
-#pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {
-                if (kEpi == 8 && hf != (warp >> 2)) continue;
-                const int c = j * kBlockK + 16 * hf;
-                mlp_act_half(src + c, bias ? bias + c : nullptr,
-                             t.sA + j * kTileSub + (row >> 3) * (kTileSub / 16) + (row & 7) * 16 + (2 * hf) * 128);
+        auto col = [&](int u) { return (u / H) * kBlockK + 16 * (kEpi == 8 ? (warp >> 2) : (u % H)); };
+        auto piece = [&](const uint32_t (&r)[16], int u) {
+            const int c = col(u), j = u / H, hf = (c % kBlockK) / 16;
+            mlp_act_regs(r, bias ? bias + c : nullptr,
+                         t.sA + j * kTileSub + (row >> 3) * (kTileSub / 16) + (row & 7) * 16 + (2 * hf) * 128);
+            if (u % H == H - 1) mlp_announce(tile_a(t, j));
+        };
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(src + col(0), ra);
+        tmem_ld16_wait(ra);
+#pragma unroll 1
+        for (int u = 0; u < nu; u += 2) {
+            if (u + 1 < nu) tmem_ld16_async(src + col(u + 1), rb);
+            piece(ra, u);
+            if (u + 1 < nu) {
+                tmem_ld16_wait(rb);
+                if (u + 2 < nu) tmem_ld16_async(src + col(u + 2), ra);
+                piece(rb, u + 1);
+                if (u + 2 < nu) tmem_ld16_wait(ra);
             }
-            mlp_announce(tile_a(t, j));
         }
         ok = mlp_wait_layer(t);  // layer L
     }
@@ -1299,14 +1328,32 @@ __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t,
         for (int hf = 0; hf < 2; ++hf) {
             if (kEpi == 8 && hf != (warp >> 2)) continue;
             float yacc = 0.f;
-#pragma unroll 1
-            for (int c0 = hf * hh; c0 < (hf + 1) * hh; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(RA + lane_off + c0, r);
+            auto acc16 = [&](const uint32_t (&r)[16], int c0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float x = fmaxf(__uint_as_float(r[i]) + s_b3[c0 + i], 0.f);
-                    yacc = fmaf(s_w4[c0 + i], x, yacc);
+                for (int q = 0; q < 4; ++q) {
+                    const float4 bq = lds4(s_b3 + c0 + 4 * q), wq = lds4(s_w4 + c0 + 4 * q);
+                    const float bb[4] = {bq.x, bq.y, bq.z, bq.w}, ww[4] = {wq.x, wq.y, wq.z, wq.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float x = fmaxf(__uint_as_float(r[4 * q + i]) + bb[i], 0.f);
+                        yacc = fmaf(ww[i], x, yacc);
+                    }
+                }
+            };
+            // the columns of this half in order, 16 at a time, the next load in flight
+            const int c_lo = hf * hh, c_hi = c_lo + hh;
+            uint32_t ra[16], rb[16];
+            tmem_ld16_async(RA + lane_off + c_lo, ra);
+            tmem_ld16_wait(ra);
+#pragma unroll 1
+            for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+                if (c0 + 16 < c_hi) tmem_ld16_async(RA + lane_off + c0 + 16, rb);
+                acc16(ra, c0);
+                if (c0 + 16 < c_hi) {
+                    tmem_ld16_wait(rb);
+                    if (c0 + 32 < c_hi) tmem_ld16_async(RA + lane_off + c0 + 32, ra);
+                    acc16(rb, c0 + 16);
+                    if (c0 + 32 < c_hi) tmem_ld16_wait(ra);
                 }
             }
             part[hf] = yacc;
