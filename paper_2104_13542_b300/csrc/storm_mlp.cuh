@@ -1027,8 +1027,8 @@ constexpr int kOffA1 = kRingDepth * kTileRing;
 constexpr int kOffA = kOffA1 + kTileA1;
 constexpr int kOffVec = kOffA + kTileA;
 constexpr size_t kTileSmem = kOffVec + kTileVec;
-// mbarriers: full[kRingDepth], empty[kRingDepth], done, a1, a[kMaxBlocks]
-constexpr int kTileBars = 2 * kRingDepth + 2 + kMaxBlocks;
+// mbarriers: full[kRingDepth], empty[kRingDepth], done, a1, a[kMaxBlocks], rfree
+constexpr int kTileBars = 2 * kRingDepth + 3 + kMaxBlocks;
 constexpr uint32_t kTileCols = 512;            // two accumulators
 
 // Threads of a CTA running the engine with kEpi epilogue warps: those, then the
@@ -1083,6 +1083,8 @@ struct MlpTiles {
     int layers;              // layers completed
     uint32_t apar;           // bit j: parity of a[j]'s next phase
     int tiles;               // tiles issued
+    bool rfree_on;           // the next tile's inputs may be announced before this tile's head has
+                             // read accumulator A: layer 1 then waits on rfree (set after init)
 };
 
 __device__ __forceinline__ uint32_t tile_full(const MlpTiles& t, int b) { return t.bars + 8 * b; }
@@ -1090,6 +1092,8 @@ __device__ __forceinline__ uint32_t tile_empty(const MlpTiles& t, int b) { retur
 __device__ __forceinline__ uint32_t tile_done(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth); }
 __device__ __forceinline__ uint32_t tile_a1(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth + 1); }
 __device__ __forceinline__ uint32_t tile_a(const MlpTiles& t, int j) { return t.bars + 8 * (2 * kRingDepth + 2 + j); }
+// accumulator A read by a tile's head (one arrival per epilogue warp)
+__device__ __forceinline__ uint32_t tile_rfree(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth + 2 + kMaxBlocks); }
 
 // Every thread of the CTA: addresses, then (warp 0) the TMEM columns and (the
 // MMA-issuing thread) the barriers.  The caller then runs the TMEM-allocation
@@ -1107,6 +1111,7 @@ __device__ __forceinline__ void mlp_tiles_init(MlpTiles& t, const MlpView& v, ui
     t.next = t.issued = t.layers = t.tiles = 0;
     t.apar = 0u;
     t.total = total;
+    t.rfree_on = false;
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTileCols)
@@ -1117,6 +1122,7 @@ __device__ __forceinline__ void mlp_tiles_init(MlpTiles& t, const MlpView& v, ui
         for (int b = 0; b < 2 * kRingDepth + 1; ++b) mbar_init(t.bars + 8 * b, 1);  // ring, done: one arrival
         mbar_init(tile_a1(t), kBM / 32);                                             // the four encoding warps
         for (int j = 0; j < kMaxBlocks; ++j) mbar_init(tile_a(t, j), kEpi);         // every epilogue warp
+        mbar_init(tile_rfree(t), kEpi);                                              // every epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
 }
@@ -1177,6 +1183,9 @@ __device__ __forceinline__ bool mlp_tile_issue(const MlpView& v, MlpTiles& t)
 {
     const uint32_t RA = t.tmem, RB = t.tmem + 256;  // layers 1 and 3 | layer 2
     if (!mbar_wait(tile_a1(t), t.tiles & 1)) return false;
+    // inputs announced early: layer 1 overwrites accumulator A only once the
+    // previous tile's head has read it
+    if (t.rfree_on && t.tiles > 0 && !mbar_wait(tile_rfree(t), (t.tiles - 1) & 1)) return false;
     ++t.tiles;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!mlp_mma_block(v, t, t.sA1, 256, 16, RA, instr_desc(kBM, v.h1), true)) return false;
@@ -1278,9 +1287,13 @@ __device__ __forceinline__ void mlp_announce(uint32_t bar)
 // order and adds the halves; rows 0..127 get their output in *y (threads
 // 0..127).  bar_id: a named barrier free for the kEpi warps (8 warps only).
 // False (on every epilogue thread) when a wait ran out.
-template <int kEpi>
+// after_e1 / after_e2: called on every epilogue thread once layer 1's / layer
+// 2's outputs are all stored, while the tensor core finishes the layer after
+// them (a window in which the epilogue warps would only wait).
+template <int kEpi, typename AfterE1, typename AfterE2>
 __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t, const float* s_b2, const float* s_b3,
-                                                  const float* s_w4, float* s_part, float b4, float* y)
+                                                  const float* s_w4, float* s_part, float b4, float* y,
+                                                  AfterE1&& after_e1, AfterE2&& after_e2)
 {
     static_assert(kEpi == 4 || kEpi == 8, "four or eight epilogue warps");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1318,6 +1331,10 @@ __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t,
                 if (u + 2 < nu) tmem_ld16_wait(ra);
             }
         }
+        if (L == 2)
+            after_e1();
+        else
+            after_e2();
         ok = mlp_wait_layer(t);  // layer L
     }
     // head: each half of layer 3's columns in column order, then the halves added
@@ -1360,6 +1377,10 @@ __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t,
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");  // these TMEM reads before the next tile's MMAs
+    if (t.rfree_on && ok) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cta(tile_rfree(t));
+    }
     if (kEpi == 8) {
         if (warp >= 4) s_part[row] = part[1];
         asm volatile("bar.sync 1, %0;" ::"n"(kEpi * 32) : "memory");
@@ -1368,6 +1389,13 @@ __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t,
     }
     if (tid < kBM) *y = b4 + (part[0] + part[1]);
     return ok;
+}
+
+template <int kEpi>
+__device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t, const float* s_b2, const float* s_b3,
+                                                  const float* s_w4, float* s_part, float b4, float* y)
+{
+    return mlp_tile_epilogue<kEpi>(v, t, s_b2, s_b3, s_w4, s_part, b4, y, [] {}, [] {});
 }
 
 // AND of v over the `threads` threads meeting at named barrier `id`.
@@ -1539,6 +1567,7 @@ k_mlp_forward_tiles(tc::MlpView v, const float* __restrict__ theta, int count, i
     float* s_part = s_w4 + 256;
     tc::MlpTiles t;
     tc::mlp_tiles_init<kFwdEpi>(t, v, tc::smem_u32(tile_smem), bars, &tmem_slot, my_tiles * tc::mlp_blocks(v));
+    t.rfree_on = true;  // the next tile's inputs are announced during this tile's last layer
     for (int n = tid; n < 256; n += blockDim.x) {
         s_b2[n] = n < v.h2 ? v.b2[n] : 0.f;
         s_b3[n] = n < v.h3 ? v.b3[n] : 0.f;
@@ -1564,21 +1593,39 @@ k_mlp_forward_tiles(tc::MlpView v, const float* __restrict__ theta, int count, i
             }
         }
     } else {
+        // The four encoding warps (threads 0..127, one row each) write a tile's
+        // layer-1 inputs.  Tile k + 1's are loaded once tile k's layer-1 outputs
+        // are stored and encoded once its layer-2 outputs are, while the tensor
+        // core finishes the next layer (its layer 1 has long read them).
+        float thr[7];
+        auto load_row = [&](int k) {
+            const int row = (blockIdx.x + k * gridDim.x) * tc::kBM + tid;
+#pragma unroll
+            for (int j = 0; j < 7; ++j) thr[j] = (row < count && j < dof) ? theta[static_cast<size_t>(row) * dof + j] : 0.f;
+        };
+        auto encode_row = [&](int k) {
+            const int row = (blockIdx.x + k * gridDim.x) * tc::kBM + tid;
+            float in[kMlpIn];
+            if (row < count) {
+                mlp_encode_row(thr, dof, v.enc, in);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kMlpIn; ++i) in[i] = 0.f;
+            }
+            mlp_store_input_row(t.sA1, tid, in);
+            tc::mlp_announce(tc::tile_a1(t));
+        };
+        if (tid < tc::kBM && my_tiles > 0) {
+            load_row(0);
+            encode_row(0);
+        }
         for (int k = 0; k < my_tiles && ok; ++k) {
             const int row = (blockIdx.x + k * gridDim.x) * tc::kBM + tid;  // threads 0..127
-            if (tid < tc::kBM) {  // the four encoding warps
-                float in[kMlpIn];
-                if (row < count) {
-                    mlp_encode_row(theta + static_cast<size_t>(row) * dof, dof, v.enc, in);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < kMlpIn; ++i) in[i] = 0.f;
-                }
-                mlp_store_input_row(t.sA1, tid, in);
-                tc::mlp_announce(tc::tile_a1(t));
-            }
+            const bool next = tid < tc::kBM && k + 1 < my_tiles;
             float out = 0.f;
-            ok = tc::mlp_tile_epilogue<kFwdEpi>(v, t, s_b2, s_b3, s_w4, s_part, b4, &out);
+            ok = tc::mlp_tile_epilogue<kFwdEpi>(v, t, s_b2, s_b3, s_w4, s_part, b4, &out,
+                                                [&] { if (next) load_row(k + 1); },
+                                                [&] { if (next) encode_row(k + 1); });
             ok = tc::bar_and(2, kFwdEpi * 32, ok);  // the same decision on every epilogue thread
             if (ok && tid < tc::kBM && row < count) y[row] = out;
         }
