@@ -314,7 +314,8 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     __syncthreads();
     for (int j = tid; j < d; j += nt) {
         float v = s_state[d + j], q = s_state[j];
-        for (int h = 0; h < H; ++h) {
+#pragma unroll 6
+        for (int h = 0; h < H; ++h) {  // (unrolled: later steps' loads issue ahead of the scan)
             v = fmaf(s_dt[h], s_u[h * d + j], v);
             q = fmaf(s_dt[h], v, q);
             s_thd[h * d + j] = v;
@@ -923,6 +924,9 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     // ---- reverse scans (adjoint of Eq. 7) per joint; dC/du overwrites u
     for (int j = tid; j < d; j += nt) {
         float s1 = 0.f, s2 = 0.f;
+        // (unrolled so that the loads of later steps issue ahead of the two
+        // running sums, which keep their order)
+#pragma unroll 6
         for (int h = H - 1; h >= 0; --h) {
             const float g = s_gpow[h];
             s1 = fmaf(g, s_gth[h * d + j], s1);
