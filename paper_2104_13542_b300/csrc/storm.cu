@@ -888,8 +888,9 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
         }
         if (g < G) s_grp[tid] = a1;  // [g][cl]
         __syncthreads();
-        if (lead) {  // the groups in order: the new mean, Eq. 4
+        if (lead) {  // the groups in order: the new mean, Eq. 4 (unrolled: the loads issue ahead of the sum)
             float A1 = 0.f;
+#pragma unroll 6
             for (int q = 0; q < G; ++q) A1 += s_grp[q * cpc + tid];
             s_mu[tid] = fmaf(pb.alpha_mu * A1, inv_s, mu_k);
         }
@@ -917,6 +918,7 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
         __syncthreads();
         if (lead) {
             float A2 = 0.f;
+#pragma unroll 6
             for (int q = 0; q < G; ++q) A2 += s_grp[q * cpc + tid];
             s_dev[tid] = A2;
         }

@@ -945,6 +945,7 @@ k_adjoint(Problem pb, const float* __restrict__ mean, const float* __restrict__ 
     __shared__ int s_last;
     if (tid == 0) {
         float C = 0.f;
+#pragma unroll 6
         for (int h = 0; h < H; ++h) C = fmaf(s_gpow[h], s_cost[h], C);
         if (Ctot) Ctot[n] = C;
         adj_add(acc.sum + HD, C, kAdjCostScale, acc.bad);
