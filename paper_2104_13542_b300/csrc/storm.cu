@@ -983,8 +983,9 @@ __device__ __forceinline__ void update_cluster(const Problem& pb, const float* _
             host_st->status = st->status;
             host_st->best = st->best;
             host_st->wmean = st->wmean;
-            __threadfence_system();
-            *reinterpret_cast<volatile uint32_t*>(&host_st->step) = st->step;
+            // the counter last, as a release at system scope: the host sees the
+            // outputs above once it sees the counter change
+            asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(&host_st->step), "r"(st->step) : "memory");
         }
     }
 }
