@@ -378,8 +378,8 @@ int storm_set_broadphase(storm_handle* h, int on);
  * after a first step), keeps the fastest, except that the fastest pair shape
  * is kept when it is within 5 % of the fastest (one state is not every state:
  * the pair mapping shares collision-heavy items between its two warps); among
- * pair shapes more pairs per CTA (fewer CTAs, idle SMs) must be 5 % faster.
- * Then it re-captures the step graph.  best_us (nullable) receives the median time of
+ * pair shapes one whose grid has fewer CTAs than the device has SMs must be
+ * 5 % faster.  Then it re-captures the step graph.  best_us (nullable) receives the median time of
  * the chosen shape.  Waits. */
 int storm_autotune(storm_handle* h, float* best_us);
 

@@ -2917,15 +2917,20 @@ int storm_autotune(storm_handle* h, float* best_us)
     // More pairs per CTA means fewer CTAs: at 500 particles four pairs a CTA leave
     // 23 of the 148 SMs idle, and the control step ran ~3 % slower than with one
     // pair a CTA although single rollouts timed here were within noise of each
-    // other.  So a larger CTA is taken only if it beats the smaller by 5 %.
+    // other (two pairs a CTA, 250 CTAs, ran the step 0.5 % faster than one).
+    // So a pair shape whose grid leaves SMs idle is taken only if it beats the
+    // best so far by 5 %.
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) rc = STORM_ERR_CUDA;
     float best_pair = INFINITY;
     int best_pair_wpc = 1;
     for (int w : pairs) {
         if (rc) break;
         if (set_launch_warp_impl(h, w, false, STORM_MAP_WARP_PAIR) != STORM_OK) continue;
+        const bool fills = h->warp_grid >= sms;
         const float med = measure();
         if (rc) break;
-        if (med < (best_pair == INFINITY ? INFINITY : 0.95f * best_pair)) {
+        if (med < (fills ? 1.f : 0.95f) * best_pair) {
             best_pair = med;
             best_pair_wpc = w;
         }
