@@ -1027,8 +1027,8 @@ constexpr int kOffA1 = kRingDepth * kTileRing;
 constexpr int kOffA = kOffA1 + kTileA1;
 constexpr int kOffVec = kOffA + kTileA;
 constexpr size_t kTileSmem = kOffVec + kTileVec;
-// mbarriers: full[kRingDepth], empty[kRingDepth], done, a1, a[kMaxBlocks], rfree
-constexpr int kTileBars = 2 * kRingDepth + 3 + kMaxBlocks;
+// mbarriers: full[kRingDepth], empty[kRingDepth], done, a1, a[kMaxBlocks]
+constexpr int kTileBars = 2 * kRingDepth + 2 + kMaxBlocks;
 constexpr uint32_t kTileCols = 512;            // two accumulators
 
 // Threads of a CTA running the engine with kEpi epilogue warps: those, then the
@@ -1083,8 +1083,6 @@ struct MlpTiles {
     int layers;              // layers completed
     uint32_t apar;           // bit j: parity of a[j]'s next phase
     int tiles;               // tiles issued
-    bool rfree_on;           // the next tile's inputs may be announced before this tile's head has
-                             // read accumulator A: layer 1 then waits on rfree (set after init)
 };
 
 __device__ __forceinline__ uint32_t tile_full(const MlpTiles& t, int b) { return t.bars + 8 * b; }
@@ -1092,8 +1090,12 @@ __device__ __forceinline__ uint32_t tile_empty(const MlpTiles& t, int b) { retur
 __device__ __forceinline__ uint32_t tile_done(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth); }
 __device__ __forceinline__ uint32_t tile_a1(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth + 1); }
 __device__ __forceinline__ uint32_t tile_a(const MlpTiles& t, int j) { return t.bars + 8 * (2 * kRingDepth + 2 + j); }
-// accumulator A read by a tile's head (one arrival per epilogue warp)
-__device__ __forceinline__ uint32_t tile_rfree(const MlpTiles& t) { return t.bars + 8 * (2 * kRingDepth + 2 + kMaxBlocks); }
+// Tile k's accumulator for layers 1 and 3 (which = 0) or for layer 2 (which = 1):
+// the two 256-column regions, their roles swapped on odd tiles.
+__device__ __forceinline__ uint32_t tile_acc(const MlpTiles& t, int k, int which)
+{
+    return t.tmem + (((k ^ which) & 1) ? 256u : 0u);
+}
 
 // Every thread of the CTA: addresses, then (warp 0) the TMEM columns and (the
 // MMA-issuing thread) the barriers.  The caller then runs the TMEM-allocation
@@ -1111,7 +1113,6 @@ __device__ __forceinline__ void mlp_tiles_init(MlpTiles& t, const MlpView& v, ui
     t.next = t.issued = t.layers = t.tiles = 0;
     t.apar = 0u;
     t.total = total;
-    t.rfree_on = false;
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTileCols)
@@ -1122,7 +1123,6 @@ __device__ __forceinline__ void mlp_tiles_init(MlpTiles& t, const MlpView& v, ui
         for (int b = 0; b < 2 * kRingDepth + 1; ++b) mbar_init(t.bars + 8 * b, 1);  // ring, done: one arrival
         mbar_init(tile_a1(t), kBM / 32);                                             // the four encoding warps
         for (int j = 0; j < kMaxBlocks; ++j) mbar_init(tile_a(t, j), kEpi);         // every epilogue warp
-        mbar_init(tile_rfree(t), kEpi);                                              // every epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
 }
@@ -1181,11 +1181,12 @@ __device__ __forceinline__ void mlp_commit_done(const MlpTiles& t)
 // ran out (the epilogue warps then time out on `done`).
 __device__ __forceinline__ bool mlp_tile_issue(const MlpView& v, MlpTiles& t)
 {
-    const uint32_t RA = t.tmem, RB = t.tmem + 256;  // layers 1 and 3 | layer 2
+    // the two accumulators swap roles from tile to tile: layer 1 of a tile goes
+    // where the tile before kept layer 2, free once its epilogue has announced
+    // all of layer 2's blocks (which this thread waited for before the last
+    // layer-3 MMAs), so it need not wait for that tile's head
+    const uint32_t RA = tile_acc(t, t.tiles, 0), RB = tile_acc(t, t.tiles, 1);  // layers 1 and 3 | layer 2
     if (!mbar_wait(tile_a1(t), t.tiles & 1)) return false;
-    // inputs announced early: layer 1 overwrites accumulator A only once the
-    // previous tile's head has read it
-    if (t.rfree_on && t.tiles > 0 && !mbar_wait(tile_rfree(t), (t.tiles - 1) & 1)) return false;
     ++t.tiles;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!mlp_mma_block(v, t, t.sA1, 256, 16, RA, instr_desc(kBM, v.h1), true)) return false;
@@ -1299,7 +1300,8 @@ __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t,
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, row = quarter * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-    const uint32_t RA = t.tmem, RB = t.tmem + 256;
+    const int tk = t.layers / 3;  // this tile's index among the CTA's tiles
+    const uint32_t RA = tile_acc(t, tk, 0), RB = tile_acc(t, tk, 1);  // layers 1 and 3 | layer 2
     bool ok = mlp_wait_layer(t);  // layer 1
     // the warp's 16-column pieces of a layer in order: piece u is half hf of
     // block u / H (with 8 warps one half, warp / 4, of every block); each piece's
@@ -1377,10 +1379,6 @@ __device__ __forceinline__ bool mlp_tile_epilogue(const MlpView& v, MlpTiles& t,
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");  // these TMEM reads before the next tile's MMAs
-    if (t.rfree_on && ok) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive_cta(tile_rfree(t));
-    }
     if (kEpi == 8) {
         if (warp >= 4) s_part[row] = part[1];
         asm volatile("bar.sync 1, %0;" ::"n"(kEpi * 32) : "memory");
@@ -1567,7 +1565,6 @@ k_mlp_forward_tiles(tc::MlpView v, const float* __restrict__ theta, int count, i
     float* s_part = s_w4 + 256;
     tc::MlpTiles t;
     tc::mlp_tiles_init<kFwdEpi>(t, v, tc::smem_u32(tile_smem), bars, &tmem_slot, my_tiles * tc::mlp_blocks(v));
-    t.rfree_on = true;  // the next tile's inputs are announced during this tile's last layer
     for (int n = tid; n < 256; n += blockDim.x) {
         s_b2[n] = n < v.h2 ? v.b2[n] : 0.f;
         s_b3[n] = n < v.h3 ? v.b3[n] : 0.f;
