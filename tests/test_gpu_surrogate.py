@@ -98,11 +98,13 @@ def test_training_learns_the_distance():
     net.close()
 
 
-@pytest.mark.parametrize("count", [1, 128, 1000, 65_536 + 77])
+@pytest.mark.parametrize("count", [1, 128, 1000, 65_536 + 77, 262_144 + 7])
 def test_fused_forward_equals_layer_kernels(count):
     """storm_mlp_predict (the whole network per tile, activations on chip) gives
     bitwise the predictions of the layer-by-layer kernels of the training pass,
-    for ragged tile counts and a grid of several persistent waves."""
+    for ragged tile counts and a grid of several persistent waves; the largest
+    count gives each CTA ~14 tiles, so the accumulators swap roles and the next
+    tile's inputs are announced early many times over."""
     p = _random_params(11)
     th = cuda(np.random.default_rng(count).uniform(-2.8, 2.8, (count, 7)))
     net = SurrogateMLP(seed=3)
